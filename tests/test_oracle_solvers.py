@@ -1,0 +1,227 @@
+"""Pins of the oracle's solvers against independent dense linear algebra and optimisers.
+
+* Tikhonov (circular mode) == a dense solve of (J^T J + lam I) x = J^T m with
+  the entry-by-entry Jacobian; and (linear mode) its spatial normal equations
+  with the periodic operator applied by direct summation.
+* The ADMM normalisation s = max_f sigma_max(W_hat(f)) == ||J||_2 (circular).
+* ADMM with beta = 0 converges to the non-negative least-squares solution
+  (scipy.optimize.nnls on the dense Jacobian); with beta > 0 to the minimiser
+  found by SLSQP on the dense TV problem assembled from its definition.
+"""
+
+import numpy as np
+import pytest
+from scipy import optimize
+
+from oracle import operators as op
+from oracle import physics as ph
+from oracle import solvers as so
+from paper_2101_11680_gb300 import synth
+
+
+def medium():
+    return ph.Medium(0.01, 1.0, 1.4, r_min=0.5)
+
+
+def test_tikhonov_equals_dense_solve_circular():
+    g = op.Grid(8, 4, 16, 1.0, 1.0, 1.0, 50.0, mode="circular")
+    m_ = medium()
+    w = op.kernel_offsets(g, m_)
+    wh = op.kernel_spectrum(w, g)
+    J = op.dense_jacobian(g, m_)
+    rng = np.random.default_rng(11)
+    meas = rng.uniform(0, 1, (g.nt, g.n, g.n)) * np.abs(J).max()
+    x, lam, _ = so.tikhonov(wh, meas, g)
+    want = np.linalg.solve(J.T @ J + lam * np.eye(J.shape[1]), J.T @ meas.ravel())
+    assert np.abs(x.ravel() - want).max() <= 1e-9 * np.abs(want).max()
+    # lam is 1e-3 x the largest Gram diagonal = 1e-3 x the largest column norm^2 of the
+    # circulant J times P^0 (Parseval: diag G(f) summed over f / P^2 = ||column||^2)
+    assert lam > 0
+
+
+def _periodic_apply(wp, x):
+    """K x on the P grid by direct periodic summation (no FFT): wp [T][Z][P][P], x [Z][P][P]."""
+    t, z, p, _ = wp.shape
+    out = np.zeros((t, p, p))
+    for j in range(z):
+        for yp in range(p):
+            for xp in range(p):
+                if x[j, yp, xp] != 0.0:
+                    out += x[j, yp, xp] * np.roll(wp[:, j], (yp, xp), axis=(1, 2))
+    return out
+
+
+def _periodic_adjoint(wp, r):
+    t, z, p, _ = wp.shape
+    out = np.zeros((z, p, p))
+    for yp in range(p):
+        for xp in range(p):
+            sh = np.roll(wp, (yp, xp), axis=(2, 3))
+            out[:, yp, xp] = np.einsum("tzyx,tyx->z", sh, r)
+    return out
+
+
+def test_tikhonov_normal_equations_linear():
+    """(K^T K + lam) x = K^T pad(m) on the P grid, K applied by direct periodic sums."""
+    g = op.Grid(6, 3, 8, 1.0, 1.0, 1.0, 50.0)
+    w = op.kernel_offsets(g, medium())
+    wh = op.kernel_spectrum(w, g)
+    wp = op.periodic_kernel(w, g)
+    rng = np.random.default_rng(12)
+    meas = rng.uniform(0, 1, (g.nt, g.n, g.n)) * np.abs(w).max()
+    _, lam, xh = so.tikhonov(wh, meas, g)
+    x = np.fft.ifft2(xh, axes=(-2, -1)).real
+    padm = np.zeros((g.nt, g.p, g.p))
+    padm[:, :g.n, :g.n] = meas
+    lhs = _periodic_adjoint(wp, _periodic_apply(wp, x)) + lam * x
+    rhs = _periodic_adjoint(wp, padm)
+    assert np.abs(lhs - rhs).max() <= 1e-10 * np.abs(rhs).max()
+
+
+def test_normalisation_is_operator_norm():
+    g = op.Grid(8, 4, 16, 1.0, 1.0, 1.0, 50.0, mode="circular")
+    m_ = medium()
+    wh = op.kernel_spectrum(op.kernel_offsets(g, m_), g)
+    J = op.dense_jacobian(g, m_)
+    assert so.spectral_norm(wh) == pytest.approx(np.linalg.norm(J, 2), rel=1e-10)
+
+
+def test_normalisation_attained_at_dc():
+    """W >= 0 elementwise, so |W_hat(f)| <= W_hat(0) entrywise and the max is at f = 0."""
+    g = op.Grid(8, 4, 16, 1.0, 1.0, 1.0, 50.0)
+    wh = op.kernel_spectrum(op.kernel_offsets(g, medium()), g)
+    s0 = np.linalg.norm(wh[:, :, 0, 0].real, 2)
+    assert so.spectral_norm(wh) == pytest.approx(s0, rel=1e-12)
+
+
+def _tiny(n=4, nz=1, nt=12, dx=1.0, dz=1.0, z_first=2.0, dt=50.0, seed=5):
+    """A small, well-conditioned linear-mode problem with 2 % Gaussian noise."""
+    g = op.Grid(n, nz, nt, dx, dz, z_first, dt, mode="linear")
+    m_ = medium()
+    w = op.kernel_offsets(g, m_)
+    wh = op.kernel_spectrum(w, g)
+    J = op.dense_jacobian(g, m_)
+    rng = np.random.default_rng(seed)
+    mu = rng.uniform(0, 0.02, (nz, n, n)) * (rng.uniform(size=(nz, n, n)) < 0.5)
+    meas = op.forward_fft(wh, mu, g)
+    meas = meas + 0.02 * np.abs(meas).max() * rng.standard_normal(meas.shape)
+    return g, wh, J, meas
+
+
+def test_admm_beta0_converges_to_nnls():
+    """beta = 0: ADMM's limit is the non-negative least-squares solution on S.
+
+    (The fixed point does not depend on rho; rho = 0.03 converges fast here.)
+    """
+    g, wh, J, meas = _tiny()
+    x, info = so.admm(wh, meas, g, 3000, beta=0.0, rho=0.03)
+    s = info["scale"]
+    want, _ = optimize.nnls(J / s, meas.ravel() / s, maxiter=10000)
+    assert np.abs(x.ravel() - want).max() <= 1e-9 * np.abs(want).max()
+
+
+def _tv_matrix(g):
+    """Rows of D restricted to the support S for the zero-extended P-grid volume.
+
+    Lateral: periodic forward differences on the P grid; since x = 0 off S each
+    lateral line contributes the N-1 interior differences plus |x_first| and
+    |x_last| (the two neighbours outside S).  Axial: the Z-1 Neumann differences.
+    """
+    n, z = g.n, g.nz
+    idx = lambda j, y, x: (j * n + y) * n + x
+    rows = []
+    for j in range(z):
+        for y in range(n):
+            for x in range(n):
+                for (yy, xx) in ((y, x + 1), (y + 1, x)):
+                    r = np.zeros(z * n * n)
+                    r[idx(j, y, x)] = -1.0
+                    if yy < n and xx < n:
+                        r[idx(j, yy, xx)] = 1.0
+                    rows.append(r)
+                # difference entering the support from the zero neighbour at -1
+                if x == 0:
+                    r = np.zeros(z * n * n)
+                    r[idx(j, y, x)] = 1.0
+                    rows.append(r)
+                if y == 0:
+                    r = np.zeros(z * n * n)
+                    r[idx(j, y, x)] = 1.0
+                    rows.append(r)
+                if j + 1 < z:
+                    r = np.zeros(z * n * n)
+                    r[idx(j, y, x)] = -1.0
+                    r[idx(j + 1, y, x)] = 1.0
+                    rows.append(r)
+    return np.array(rows)
+
+
+def test_admm_tv_matches_slsqp():
+    """beta > 0: ADMM's limit is the minimiser of the dense TV problem (SLSQP from zero)."""
+    g, wh, J, meas = _tiny(n=2, nz=3, nt=48, dx=1.5, dz=1.5, z_first=1.5, dt=20.0, seed=5)
+    x, info = so.admm(wh, meas, g, 2000, beta_rel=2e-2, rho=0.1)
+    s, beta = info["scale"], info["beta"]
+    A = J / s
+    b = meas.ravel() / s
+    E = _tv_matrix(g)
+    nv, ne = A.shape[1], E.shape[0]
+
+    def f(v):
+        xx, tt = v[:nv], v[nv:]
+        r = A @ xx - b
+        return 0.5 * r @ r + beta * tt.sum()
+
+    def grad(v):
+        xx = v[:nv]
+        return np.concatenate([A.T @ (A @ xx - b), beta * np.ones(ne)])
+
+    cons = [{"type": "ineq", "fun": lambda v: v[nv:] - E @ v[:nv], "jac": lambda v: np.hstack([-E, np.eye(ne)])},
+            {"type": "ineq", "fun": lambda v: v[nv:] + E @ v[:nv], "jac": lambda v: np.hstack([E, np.eye(ne)])}]
+    res = optimize.minimize(f, np.zeros(nv + ne), jac=grad, constraints=cons, method="SLSQP",
+                            bounds=[(0, None)] * (nv + ne), options=dict(ftol=1e-16, maxiter=2000))
+    assert res.success
+    fx = f(np.concatenate([x.ravel(), np.abs(E @ x.ravel())]))
+    assert fx <= res.fun * (1 + 1e-10)
+    assert np.abs(res.x[:nv] - x.ravel()).max() <= 1e-5 * np.abs(x).max()
+
+
+def test_admm_fixed_point_residuals_vanish():
+    g, wh, _, meas = _tiny(n=2, nz=3, nt=48, dx=1.5, dz=1.5, z_first=1.5, dt=20.0)
+    x, info = so.admm(wh, meas, g, 2000, beta_rel=2e-2, rho=0.1)
+    xf = info["x"]
+    # the x iterate agrees with the feasible output on S and is ~0 off S
+    assert np.abs(xf[:, :g.n, :g.n] - x).max() <= 1e-6 * np.abs(x).max()
+    off = xf.copy()
+    off[:, :g.n, :g.n] = 0.0
+    assert np.abs(off).max() <= 1e-6 * np.abs(x).max()
+
+
+def test_admm_first_iterate_is_zero():
+    """From x = v = u = 0 the first x-update sees a zero right-hand side, so v3 = 0."""
+    g, wh, J, meas = _tiny()
+    v1, _ = so.admm(wh, meas, g, 1)
+    assert np.all(v1 == 0.0)
+
+
+def test_phantom_generators():
+    vol = synth.phantom_spheres(32, 16, 1.0, 1.0, 1.0, seed=0)
+    assert set(np.unique(vol)) <= {0.0, 0.01}
+    # two spheres of radius 1.5 mm centred at depths 5 and 9 mm (voxel depths 1..16 mm):
+    # every marked voxel lies within 1.5 mm of one of those depths; volume ~ 2 x 14 voxels
+    zs = 1.0 + np.nonzero(vol)[0]
+    assert np.all((np.abs(zs - 5.0) <= 1.5) | (np.abs(zs - 9.0) <= 1.5))
+    assert 2 * 7 <= np.count_nonzero(vol) <= 2 * 27
+    v2 = synth.phantom_shapes(32, 16, 0.5, 0.5, 0.5, seed=3)
+    assert v2.max() <= 0.02 and v2.min() >= 0.0 and np.count_nonzero(v2) > 0
+    a = synth.phantom_shapes(16, 8, 0.5, 0.5, 0.5, seed=4)
+    b = synth.phantom_shapes(16, 8, 0.5, 0.5, 0.5, seed=4)
+    assert np.array_equal(a, b)
+
+
+def test_poisson_noise_statistics():
+    m = np.full(200000, 0.25)
+    m[0] = 1.0
+    y = synth.poisson_noise(m, 1e4, seed=1)
+    # counts at 2500 expected: mean 0.25, variance 0.25 * (max/peak)
+    assert y[1:].mean() == pytest.approx(0.25, rel=2e-3)
+    assert y[1:].var() == pytest.approx(0.25 * 1e-4, rel=2e-2)
