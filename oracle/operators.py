@@ -15,7 +15,7 @@ which depends only on the lateral offset: the convolutional approximation
 
 * linear (default): m[k][y][x] = sum_j sum_{y',x' < N} W[k][j][y-y'][x-x'] mu[j][y'][x'],
   offsets in [-(N-1), N-1], no truncation; evaluated by FFT on a P x P grid,
-  P = smallest power of two >= 2N, with the kernel placed at offset index
+  P = max(32, smallest power of two >= 2N), with the kernel placed at offset index
   p -> p mod P (zero at every index no offset reaches), then cropped to N x N;
 * circular: P = N, minimum-image offsets (the paper's "doubly circulant"
   statement, Section 4).
@@ -42,7 +42,10 @@ class Grid:
             raise ValueError(mode)
         self.mode = mode
         if mode == "linear":
-            p = 1
+            # any P >= 2N-1 gives the same linear convolution; the solvers work
+            # on the P x P periodic grid, so P is fixed here: the smallest power
+            # of two >= 2N, and at least 32.
+            p = 32
             while p < 2 * self.n:
                 p *= 2
             self.p = p
