@@ -1,0 +1,178 @@
+/*
+ * ctof.h -- C ABI of the GB300 confocal time-of-flight DOT library.
+ *
+ * The library implements the convolutional approximation of confocal
+ * time-of-flight diffuse optical tomography (arXiv 2101.11680):
+ *
+ *   Eq. 2, Eq. 6   m = J mu : differential measurements are linear in the
+ *                  absorption perturbation mu (Born approximation);
+ *   Eq. 5          J(r_s, r_d, r_v, t) = Phi0(r_v - r_s, t) (*)_t R(r_d - r_v, t);
+ *   Section 4      for confocal scans (source = detector) J is laterally
+ *                  shift-invariant, so the forward model is a per-depth 2-D
+ *                  convolution summed over depth (Eq. 9, Eq. 11):
+ *                    m(x,y,t) = sum_z W_z(x,y,t) (*) mu_z(x,y).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Units: mm, ps, 1/mm.
+ *  - Volumes mu are float32 [nz][ny][nx], measurements m are float32
+ *    [nt][ny][nx]; x is the fastest axis; C order, contiguous.  Scan points
+ *    sit on the lateral voxel-column centres (x_i = i dx, y_i = i dy).
+ *    Voxel depth z_j = z_first + j dz; time bin k covers [k dt, (k+1) dt).
+ *  - Pointers named d_* are device pointers (any allocation reachable by the
+ *    device of the handle); h_* are host pointers.  The caller owns every
+ *    data buffer; the library owns the handle and its workspaces.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = the legacy default
+ *    stream).  Calls are stream-ordered and asynchronous unless they say
+ *    otherwise; errors found on the host are returned at once.
+ *  - A handle is not re-entrant: calls on one handle must not overlap on the
+ *    device (issue them on one stream).  Separate handles are independent.
+ *  - Every function returns ctof_status (0 = success); nothing throws
+ *    across the ABI.  The GPU path has no CPU fallback: if no CUDA device is
+ *    usable, calls that compute return CTOF_ECUDA.
+ */
+#ifndef CTOF_H
+#define CTOF_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  CTOF_OK = 0,
+  CTOF_EINVAL = -1,        /* bad argument: null pointer, size, optics */
+  CTOF_ENOMEM = -2,        /* device allocation failed */
+  CTOF_ECUDA = -3,         /* a CUDA runtime call failed */
+  CTOF_ENONFINITE = -4,    /* a NaN/Inf was detected in an input or result */
+  CTOF_ETIMEOUT = -5,      /* a bounded device wait gave up */
+  CTOF_EUNSUPPORTED = -6   /* valid but not implemented (e.g. nx != ny) */
+} ctof_status;
+
+enum { CTOF_LINEAR = 0, CTOF_CIRCULAR = 1 };
+enum { CTOF_SOLVER_ADMM_TV = 0, CTOF_SOLVER_TIKHONOV = 1 };
+enum { CTOF_KEEP_W = 1 }; /* ctof_build_kernel flag: retain the FP64 kernel table */
+
+/* Background optics of the homogeneous semi-infinite medium (Section 3,
+ * "Analytical approximation"; the diffusion forms are the textbook
+ * extrapolated-boundary ones).  mua >= 0, musp > 0, n >= 1. */
+typedef struct {
+  double mua_mm;   /* absorption coefficient [1/mm] */
+  double musp_mm;  /* reduced scattering coefficient [1/mm] */
+  double n;        /* refractive index of the medium */
+  double z0_mm;    /* depth of the isotropic source; <= 0 selects 1/(mua+musp) */
+  int clamp_r;     /* 1: clamp source/voxel/detector distances to >= min(dx,dy,dz)/2 */
+} ctof_optics;
+
+/* Confocal scan / voxel grid.  nx == ny is required; conv_mode selects the
+ * lateral boundary: CTOF_LINEAR (zero-padded linear convolution, offsets in
+ * [-(n-1), n-1], FFT size P = max(32, smallest power of two >= 2n)) or
+ * CTOF_CIRCULAR (periodic, P = n, n a power of two).  Limits:
+ * 4 <= nx <= 256 (linear), 32 <= nx <= 512 (circular), 1 <= nz <= 64,
+ * 1 <= nt <= 1024, and one frequency class (nt x nz FP32 block plus its
+ * vectors) must fit in the 227 KB of shared memory of one CTA: about
+ * nt * (nz + 1) <= 40000 (nt <= 600 at nz = 64, nt <= 1024 at nz = 32). */
+typedef struct {
+  int nx, ny, nz, nt;
+  double dx_mm, dy_mm, dz_mm;
+  double z_first_mm;  /* depth of the first voxel layer (> 0) */
+  double dt_ps;       /* time-bin width */
+  int conv_mode;
+} ctof_grid;
+
+typedef struct ctof_kernel_s* ctof_kernel;
+
+/* Read-only facts about a built kernel. */
+typedef struct {
+  int p;            /* lateral FFT size */
+  int n_freq;       /* P * (P/2 + 1) half-plane frequencies */
+  int n_class;      /* frequency classes sharing one W_hat matrix */
+  int nt, nz;
+  double scale;     /* max_f sigma_max(W_hat(f)) (the ADMM normalisation) */
+  double gram_max_diag; /* max over f, j of (W_hat^T W_hat)_jj */
+  size_t device_bytes;  /* device memory held by the handle */
+} ctof_kernel_info;
+
+/* Solver choice and parameters.  ADMM_TV solves
+ *   min_x 1/2 ||C K x - m||^2 + beta ||D x||_1,  x >= 0,  x = 0 off the scan
+ * in units normalised by `scale` (K/scale has unit norm); Tikhonov solves
+ * per lateral frequency (G + lambda I) x_hat = W_hat^T m_hat. */
+typedef struct {
+  int solver;             /* CTOF_SOLVER_ADMM_TV or CTOF_SOLVER_TIKHONOV */
+  int iters;              /* ADMM iterations (>= 1) */
+  double rho;             /* ADMM penalty (> 0), e.g. 1 */
+  double tv_beta;         /* TV weight in normalised units; < 0 selects
+                             beta_rel * max|A^T m| / scale^2 */
+  double beta_rel;        /* e.g. 1e-3 */
+  double tik_lambda_rel;  /* lambda = tik_lambda_rel * gram_max_diag, e.g. 1e-3 */
+} ctof_solver_params;
+
+typedef struct {
+  double scale;      /* normalisation used */
+  double beta;       /* TV weight used (normalised units) */
+  double lambda;     /* Tikhonov lambda used */
+  int iters_done;
+} ctof_report;
+
+/* Build the sensitivity kernel (Eq. 4-6 with the Section 4 convolutional
+ * approximation): evaluates W[k][j][|oy|][|ox|] = dx dy dz * int_bin_k
+ * (Phi0 (*)_t R)(rho, z_j, t) dt in FP64 on the device (closed-form time
+ * convolution, 8-node x 4-piece Gauss-Legendre bin rule), transforms it to
+ * the real lateral spectrum W_hat (FP64, stored FP32 per frequency class),
+ * forms the per-frequency Gram matrices and the ADMM normal matrices (FP64
+ * Cholesky, FP32 inverse).  Synchronous: returns when the handle is ready.
+ * flags: 0 or CTOF_KEEP_W.  On success *out owns device memory until
+ * ctof_kernel_destroy.  Errors: EINVAL (null pointer, non-positive sizes or
+ * pitches, optics out of range), EUNSUPPORTED (nx != ny, sizes beyond the
+ * limits above), ENOMEM, ECUDA. */
+ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, int flags,
+                              void* stream, ctof_kernel* out);
+
+void ctof_kernel_destroy(ctof_kernel k);
+
+ctof_status ctof_kernel_get_info(ctof_kernel k, ctof_kernel_info* info);
+
+/* Copy the FP64 kernel table W[nt][nz][ny][nx] (non-negative offsets |oy|, |ox|;
+ * for circular mode the table is [nt][nz][P/2+1][P/2+1]) to host memory.
+ * Needs CTOF_KEEP_W at build time (else EUNSUPPORTED).  Synchronous. */
+ctof_status ctof_kernel_get_w(ctof_kernel k, double* h_w);
+
+/* Copy the frequency-class table to host: h_members[n_class][4] half-plane
+ * frequency indices f = ky * (P/2+1) + kx of the frequencies sharing class c
+ * (-1 = unused slot).  Synchronous. */
+ctof_status ctof_kernel_get_classes(ctof_kernel k, int* h_members);
+
+/* Copy W_hat as float32 [n_class][nt][nz] (real: the kernel is even) to
+ * host memory.  Synchronous. */
+ctof_status ctof_kernel_get_what(ctof_kernel k, float* h_what);
+
+/* m = A mu (Eq. 11 with the linear or circular lateral boundary):
+ * d_mu [nz][ny][nx] -> d_m [nt][ny][nx].  Asynchronous on `stream`. */
+ctof_status ctof_forward(ctof_kernel k, const float* d_mu, float* d_m, void* stream);
+
+/* vol = A^T m: d_m [nt][ny][nx] -> d_vol [nz][ny][nx].  Asynchronous. */
+ctof_status ctof_adjoint(ctof_kernel k, const float* d_m, float* d_vol, void* stream);
+
+/* Reconstruct mu from m with the chosen solver: d_m [nt][ny][nx] ->
+ * d_mu [nz][ny][nx].  If `report` is non-NULL the call synchronises the
+ * stream and fills it; otherwise it is asynchronous.  ADMM runs as one
+ * captured CUDA graph per handle (captured on first use).  Errors: EINVAL,
+ * ECUDA; ENONFINITE (only with a report) if the result holds NaN/Inf. */
+ctof_status ctof_reconstruct(ctof_kernel k, const float* d_m, const ctof_solver_params* params,
+                             float* d_mu, ctof_report* report, void* stream);
+
+/* As ctof_reconstruct but with HOST buffers h_m [nt][ny][nx] and
+ * h_mu [nz][ny][nx]: copies in, reconstructs, copies out, and synchronises
+ * the stream before returning.  Pinned host memory gives the fastest copies. */
+ctof_status ctof_reconstruct_host(ctof_kernel k, const float* h_m, const ctof_solver_params* params,
+                                  float* h_mu, ctof_report* report, void* stream);
+
+const char* ctof_status_string(ctof_status s);
+
+/* Text of the last CUDA runtime error seen by this thread inside the library
+ * (empty if none).  The pointer stays valid until the next library call. */
+const char* ctof_last_error_message(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* CTOF_H */

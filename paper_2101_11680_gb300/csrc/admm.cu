@@ -1,0 +1,155 @@
+// Spatial-domain steps of the ADMM iteration (nonnegativity + anisotropic 3-D
+// TV, scaled form).  With a2 = D x + u2 and a3 = x + u3:
+//   v2 = soft(a2, beta/rho),  u2 <- a2 - v2,  w2 = v2 - u2 = 2 v2 - a2
+//   v3 = max(a3, 0) on the scan support S (0 off S),  u3 <- a3 - v3,  w3 = 2 v3 - a3
+//   s  = D^T w2 + w3      (the Z-side part of the next x-update right-hand side)
+// D: forward differences, lateral periodic on the P x P grid, axial Neumann
+// (Z-1 differences).  One CTA owns a 32 x 8 lateral tile and marches along z;
+// the backward differences of D^T need w2 of the left/upper neighbours, which
+// the tile-edge threads recompute from the previous u2 (hence u2 is double
+// buffered: blocks read the old copy, write the new one).
+#include <cuda_runtime.h>
+
+#include "ctof_internal.h"
+
+namespace {
+
+constexpr int TX = 32, TY = 8;
+
+__device__ __forceinline__ float soft(float a, float thr) {
+  const float m = fabsf(a) - thr;
+  return m > 0.f ? copysignf(m, a) : 0.f;
+}
+
+__global__ void __launch_bounds__(TX* TY) k_tv_stencil(const float* __restrict__ x, const float* __restrict__ u2o,
+                                                       float* __restrict__ u2n, float* __restrict__ u3,
+                                                       float* __restrict__ s_out, const double* __restrict__ beta,
+                                                       float inv_rho, int P, int nz, int n,
+                                                       float* __restrict__ out_crop) {
+  __shared__ float sX[TY + 2][TX + 2];
+  __shared__ float sW2x[TY][TX + 1];
+  __shared__ float sW2y[TY + 1][TX];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int gx = x0 + tx, gy = y0 + ty;
+  const size_t plane = (size_t)P * P;
+  const float thr = (float)(beta[0]) * inv_rho;
+  const bool in_s = gx < n && gy < n;
+  const int tid = ty * TX + tx;
+  float w2z_prev = 0.f;
+  for (int j = 0; j < nz; ++j) {
+    const float* xp = x + (size_t)j * plane;
+    for (int i = tid; i < (TY + 2) * (TX + 2); i += TX * TY) {
+      const int ly = i / (TX + 2), lx = i - ly * (TX + 2);
+      const int yy = (y0 + ly - 1 + P) & (P - 1), xx = (x0 + lx - 1 + P) & (P - 1);
+      sX[ly][lx] = xp[(size_t)yy * P + xx];
+    }
+    __syncthreads();
+    const size_t idx = (size_t)j * plane + (size_t)gy * P + gx;
+    const float c = sX[ty + 1][tx + 1];
+    float w2x, w2y, w2z;
+    {
+      const float a = (sX[ty + 1][tx + 2] - c) + u2o[idx];
+      const float v = soft(a, thr);
+      u2n[idx] = a - v;
+      w2x = 2.f * v - a;
+    }
+    {
+      const float a = (sX[ty + 2][tx + 1] - c) + u2o[plane * nz + idx];
+      const float v = soft(a, thr);
+      u2n[plane * nz + idx] = a - v;
+      w2y = 2.f * v - a;
+    }
+    if (j < nz - 1) {
+      const float a = (x[idx + plane] - c) + u2o[2 * plane * nz + idx];
+      const float v = soft(a, thr);
+      u2n[2 * plane * nz + idx] = a - v;
+      w2z = 2.f * v - a;
+    } else {
+      u2n[2 * plane * nz + idx] = 0.f;
+      w2z = 0.f;
+    }
+    const float a3 = c + u3[idx];
+    const float v3 = in_s ? fmaxf(a3, 0.f) : 0.f;
+    u3[idx] = a3 - v3;
+    const float w3 = 2.f * v3 - a3;
+    sW2x[ty][tx + 1] = w2x;
+    sW2y[ty + 1][tx] = w2y;
+    if (tx == 0) {
+      const int xl = (gx - 1 + P) & (P - 1);
+      const float a = (c - sX[ty + 1][0]) + u2o[(size_t)j * plane + (size_t)gy * P + xl];
+      sW2x[ty][0] = 2.f * soft(a, thr) - a;
+    }
+    if (ty == 0) {
+      const int yu = (gy - 1 + P) & (P - 1);
+      const float a = (c - sX[0][tx + 1]) + u2o[plane * nz + (size_t)j * plane + (size_t)yu * P + gx];
+      sW2y[0][tx] = 2.f * soft(a, thr) - a;
+    }
+    __syncthreads();
+    const float s = (sW2x[ty][tx] - sW2x[ty][tx + 1]) + (sW2y[ty][tx] - sW2y[ty + 1][tx]) + (w2z_prev - w2z) + w3;
+    s_out[idx] = s;
+    if (out_crop && in_s) out_crop[((size_t)j * n + gy) * n + gx] = v3;
+    w2z_prev = w2z;
+    __syncthreads();
+  }
+}
+
+__global__ void k_max_abs(const float* __restrict__ v, size_t count, unsigned int* __restrict__ out) {
+  float mx = 0.f;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    mx = fmaxf(mx, fabsf(v[i]));
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(mx));
+}
+
+__global__ void k_set_beta(double* scalars, double beta_fixed, double beta_rel, double inv_s2) {
+  if (threadIdx.x == 0) {
+    const unsigned int bits = reinterpret_cast<const unsigned int*>(scalars + 1)[0];
+    const double mx = (double)__uint_as_float(bits);
+    scalars[0] = beta_fixed >= 0.0 ? beta_fixed : beta_rel * mx * inv_s2;
+  }
+}
+
+__global__ void k_check_finite(const float* __restrict__ v, size_t count, int* __restrict__ flag) {
+  int bad = 0;
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    bad |= !isfinite(v[i]);
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
+}
+
+}  // namespace
+
+ctof_status admm_tv_stencil(const ctof_kernel_s* k, const float* x, const float* u2_old, float* u2_new, float* u3,
+                            float* s, const double* beta_dev, float rho, float* out_crop, cudaStream_t st) {
+  dim3 block(TX, TY);
+  dim3 grid(k->p / TX, k->p / TY);
+  k_tv_stencil<<<grid, block, 0, st>>>(x, u2_old, u2_new, u3, s, beta_dev, 1.0f / rho, k->p, k->nz, k->n, out_crop);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+// *out_dev (the second device scalar slot) receives max |v| as float bits; the
+// slot must be zeroed beforehand.
+ctof_status reduce_max_abs(const float* v, size_t count, double* out_dev, cudaStream_t st) {
+  int blocks = (int)((count + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  k_max_abs<<<blocks, 256, 0, st>>>(v, count, reinterpret_cast<unsigned int*>(out_dev));
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status admm_set_beta(double* scalars, double beta_fixed, double beta_rel, double inv_scale2, cudaStream_t st) {
+  k_set_beta<<<1, 32, 0, st>>>(scalars, beta_fixed, beta_rel, inv_scale2);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status check_finite(const float* v, size_t count, int* flag_dev, cudaStream_t st) {
+  int blocks = (int)((count + 255) / 256);
+  if (blocks > 152 * 8) blocks = 152 * 8;
+  if (blocks < 1) blocks = 1;
+  k_check_finite<<<blocks, 256, 0, st>>>(v, count, flag_dev);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}

@@ -1,0 +1,511 @@
+// One-time construction of the sensitivity kernel and its per-frequency
+// factorisations (Section 3: computing the sensitivity matrix is a one-time
+// process).  Everything here runs in FP64 on the device:
+//
+//  1. W[k][j][|oy|][|ox|] = dx dy dz * int_bin_k (Phi0 (*)_t R)(rho, z_j, t) dt
+//     (Eq. 5), the time convolution in closed form from the Laplace
+//     transforms of the semi-infinite extrapolated-boundary Green's
+//     functions, the bin integral by an 8-node Gauss-Legendre rule on each of
+//     4 equal pieces of the bin.
+//  2. W_hat = the 2-D DFT of the periodic kernel.  The kernel is even in x
+//     and y, so W_hat is real and is a separable cosine sum over the
+//     non-negative offsets: W_hat(a,b) = sum_{q,p} c_q c_p W[q][p]
+//     cos(2 pi b q/P) cos(2 pi a p/P) (c = multiplicity of +-offset), done as
+//     two batched FP64 GEMMs per (t,z) plane and gathered per frequency class.
+//  3. Gram G(f) = W_hat(f)^T W_hat(f) (FP64), the normalisation
+//     s = sigma_max(W_hat(0)) (the DC block dominates every other frequency
+//     entrywise since W >= 0), and the ADMM normal matrix
+//     H = G/s^2 + (|dx|^2 + |dy|^2 + 1) I + Dz^T Dz, Cholesky-factored and
+//     inverted in FP64, stored FP32.
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <vector>
+
+#include "ctof_internal.h"
+
+namespace {
+
+struct PhysParams {
+  double mua, D, c, kappa, zb, z0, rmin;
+  double dx, dy, dz, zfirst, dt, vol;
+  double gl_x[8], gl_w[8];
+};
+
+__global__ void k_w_quadrant(double* __restrict__ w, int t0, int tcount, int nz, int q, int symmetric,
+                             PhysParams prm) {
+  const long long npairs = symmetric ? (long long)q * (q + 1) / 2 : (long long)q * q;
+  const long long total = npairs * nz;
+  for (long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x; gid < total;
+       gid += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(gid / npairs);
+    const long long pr = gid - (long long)j * npairs;
+    int qy, qx;
+    if (symmetric) {
+      qy = (int)((sqrt(8.0 * (double)pr + 1.0) - 1.0) * 0.5);
+      while ((long long)(qy + 1) * (qy + 2) / 2 <= pr) ++qy;
+      while ((long long)qy * (qy + 1) / 2 > pr) --qy;
+      qx = (int)(pr - (long long)qy * (qy + 1) / 2);
+    } else {
+      qy = (int)(pr / q);
+      qx = (int)(pr - (long long)qy * q);
+    }
+    const double rho2 = (qx * prm.dx) * (qx * prm.dx) + (qy * prm.dy) * (qy * prm.dy);
+    const double z = prm.zfirst + j * prm.dz;
+    double r[4];
+    r[0] = sqrt(rho2 + (z - prm.z0) * (z - prm.z0));
+    r[1] = sqrt(rho2 + (z + prm.z0 + 2.0 * prm.zb) * (z + prm.z0 + 2.0 * prm.zb));
+    r[2] = sqrt(rho2 + z * z);
+    r[3] = sqrt(rho2 + (z + 2.0 * prm.zb) * (z + 2.0 * prm.zb));
+#pragma unroll
+    for (int i = 0; i < 4; ++i) r[i] = fmax(r[i], prm.rmin);
+    // four source/detector image pairs (i in {1,2}, j in {3,4})
+    double pre[4], a[4], a2[4], rj[4];
+    const double zz[2] = {z, z + 2.0 * prm.zb};
+    const double pi = 3.14159265358979323846;
+#pragma unroll
+    for (int ii = 0; ii < 2; ++ii) {
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        const int e = ii * 2 + jj;
+        const double ri = r[ii], rjj = r[2 + jj];
+        pre[e] = (ii == 0 ? 1.0 : -1.0) * zz[jj] / (16.0 * pi * pi * prm.D * ri * rjj * rjj * rjj);
+        a[e] = ri + rjj;
+        a2[e] = a[e] * a[e];
+        rj[e] = rjj;
+      }
+    }
+    const double base_c = 1.0 / (2.0 * sqrt(pi * prm.kappa));
+    const double hsub = prm.dt * 0.25;
+    const double muac = prm.mua * prm.c;
+    for (int tk = 0; tk < tcount; ++tk) {
+      const int kbin = t0 + tk;
+      double acc = 0.0;
+      for (int s = 0; s < 4; ++s) {
+        const double ta = kbin * prm.dt + s * hsub;
+#pragma unroll
+        for (int gi = 0; gi < 8; ++gi) {
+          const double t = ta + 0.5 * hsub * (prm.gl_x[gi] + 1.0);
+          const double inv4 = 1.0 / (4.0 * prm.kappa * t);
+          double val = 0.0;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const double arg = -a2[e] * inv4 - muac * t;
+            if (arg > -745.0) val += pre[e] * exp(arg) * (a[e] + rj[e] * (2.0 * a2[e] * inv4 - 1.0));
+          }
+          acc += 0.5 * hsub * prm.gl_w[gi] * base_c * val / (t * sqrt(t));
+        }
+      }
+      acc *= prm.vol;
+      w[(((size_t)tk * nz + j) * q + qy) * q + qx] = acc;
+      if (symmetric && qx != qy) w[(((size_t)tk * nz + j) * q + qx) * q + qy] = acc;
+    }
+  }
+}
+
+// Batched row-major FP64 GEMM C[b] = A[b] * B[b] (M x K times K x N), strides
+// per batch (0 = shared operand).  64 x 64 tile, 256 threads, 4 x 4 per thread.
+__global__ void __launch_bounds__(256) k_dgemm(const double* __restrict__ A, long long sA, int lda,
+                                               const double* __restrict__ B, long long sB, int ldb,
+                                               double* __restrict__ C, long long sC, int ldc, int M, int N,
+                                               int K) {
+  __shared__ double As[16][64 + 1];
+  __shared__ double Bs[16][64 + 1];
+  const int bz = blockIdx.z;
+  const double* a = A + bz * sA;
+  const double* b = B + bz * sB;
+  double* cmat = C + bz * sC;
+  const int m0 = blockIdx.y * 64, n0 = blockIdx.x * 64;
+  const int tx = threadIdx.x & 15, ty = threadIdx.x >> 4;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int i = threadIdx.x; i < 16 * 64; i += 256) {
+      const int kk = i & 15, mm = i >> 4;
+      const int gm = m0 + mm, gk = k0 + kk;
+      As[kk][mm] = (gm < M && gk < K) ? a[(size_t)gm * lda + gk] : 0.0;
+      const int nn = i & 63, kb = i >> 6;
+      const int gn = n0 + nn, gkb = k0 + kb;
+      Bs[kb][nn] = (gn < N && gkb < K) ? b[(size_t)gkb * ldb + gn] : 0.0;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double av[4], bv[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) av[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) bv[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn < N) cmat[(size_t)gm * ldc + gn] = acc[i][j];
+    }
+  }
+}
+
+// what64[c][plane0 + pl] = out[pl][b_c][a_c]
+__global__ void k_gather_classes(const double* __restrict__ out, int nplanes_chunk, int A,
+                                 const int2* __restrict__ ab, int nclass, double* __restrict__ what64,
+                                 long long ld_what, int plane0) {
+  const long long total = (long long)nplanes_chunk * nclass;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < total;
+       i += (long long)gridDim.x * blockDim.x) {
+    const int pl = (int)(i / nclass);
+    const int c = (int)(i - (long long)pl * nclass);
+    const int2 v = ab[c];
+    what64[(size_t)c * ld_what + plane0 + pl] = out[((size_t)pl * A + v.y) * A + v.x];
+  }
+}
+
+__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+    out[i] = (float)in[i];
+}
+
+// G[c] = sum_t what64[c][t][:]^T what64[c][t][:]
+__global__ void __launch_bounds__(256) k_gram(const double* __restrict__ what64, int nt, int nz,
+                                              double* __restrict__ gram) {
+  constexpr int TC = 16;
+  __shared__ double s[TC * 64];
+  const int c = blockIdx.x;
+  const double* src = what64 + (size_t)c * nt * nz;
+  const int npair = nz * nz;
+  double acc[16];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) acc[i] = 0.0;
+  for (int t0 = 0; t0 < nt; t0 += TC) {
+    const int tc = min(TC, nt - t0);
+    for (int i = threadIdx.x; i < tc * nz; i += blockDim.x) s[i] = src[(size_t)t0 * nz + i];
+    __syncthreads();
+#pragma unroll
+    for (int r = 0; r < 16; ++r) {
+      const int pidx = threadIdx.x + r * 256;
+      if (pidx < npair) {
+        const int z1 = pidx / nz, z2 = pidx - z1 * nz;
+        double v = acc[r];
+        for (int t = 0; t < tc; ++t) v = fma(s[t * nz + z1], s[t * nz + z2], v);
+        acc[r] = v;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    const int pidx = threadIdx.x + r * 256;
+    if (pidx < npair) gram[(size_t)c * npair + pidx] = acc[r];
+  }
+}
+
+// Largest eigenvalue of the (symmetric positive semi-definite) DC Gram block
+// by power iteration; writes sqrt(lambda_max) to *out.
+__global__ void k_power_iteration(const double* __restrict__ g, int nz, int iters, double* __restrict__ out) {
+  __shared__ double v[64], w[64], red[64];
+  const int z = threadIdx.x;
+  if (z < nz) v[z] = 1.0 / sqrt((double)nz);
+  __syncthreads();
+  double lam = 0.0;
+  for (int it = 0; it < iters; ++it) {
+    if (z < nz) {
+      double acc = 0.0;
+      for (int q = 0; q < nz; ++q) acc = fma(g[z * nz + q], v[q], acc);
+      w[z] = acc;
+      red[z] = acc * acc;
+    }
+    __syncthreads();
+    if (z == 0) {
+      double s = 0.0;
+      for (int q = 0; q < nz; ++q) s += red[q];
+      red[0] = sqrt(s);
+    }
+    __syncthreads();
+    const double nrm = red[0];
+    __syncthreads();
+    if (z < nz) v[z] = nrm > 0 ? w[z] / nrm : 0.0;
+    __syncthreads();
+  }
+  // Rayleigh quotient v^T G v
+  if (z < nz) {
+    double acc = 0.0;
+    for (int q = 0; q < nz; ++q) acc = fma(g[z * nz + q], v[q], acc);
+    red[z] = acc * v[z];
+  }
+  __syncthreads();
+  if (z == 0) {
+    for (int q = 0; q < nz; ++q) lam += red[q];
+    out[0] = sqrt(fmax(lam, 0.0));
+  }
+}
+
+__global__ void k_max_diag(const double* __restrict__ gram, int nclass, int nz, double* __restrict__ out) {
+  __shared__ double red[256];
+  double mx = 0.0;
+  for (long long i = threadIdx.x; i < (long long)nclass * nz; i += blockDim.x) {
+    const int c = (int)(i / nz), j = (int)(i - (long long)c * nz);
+    mx = fmax(mx, gram[((size_t)c * nz + j) * nz + j]);
+  }
+  red[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = blockDim.x / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) red[threadIdx.x] = fmax(red[threadIdx.x], red[threadIdx.x + s]);
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[0] = red[0];
+}
+
+// In-place lower Cholesky of the symmetric matrix in s_a ([nz][nz+1]).
+__device__ void block_cholesky(double* s_a, int nz) {
+  const int ld = nz + 1;
+  for (int j = 0; j < nz; ++j) {
+    if (threadIdx.x == 0) s_a[j * ld + j] = sqrt(s_a[j * ld + j]);
+    __syncthreads();
+    const double d = s_a[j * ld + j];
+    for (int i = j + 1 + threadIdx.x; i < nz; i += blockDim.x) s_a[i * ld + j] /= d;
+    __syncthreads();
+    const int rem = nz - j - 1;
+    for (int idx = threadIdx.x; idx < rem * rem; idx += blockDim.x) {
+      const int i = j + 1 + idx / rem, l = j + 1 + idx % rem;
+      if (l <= i) s_a[i * ld + l] -= s_a[i * ld + j] * s_a[l * ld + j];
+    }
+    __syncthreads();
+  }
+}
+
+// mode 0: ADMM  H = G/s^2 + (lap+1) I + Dz^T Dz  -> FP32 inverse into out32
+// mode 1: Tikhonov  G + lambda I -> FP64 lower Cholesky factor into out64
+__global__ void __launch_bounds__(128) k_factor(const double* __restrict__ gram, const float* __restrict__ lap,
+                                                int nz, double inv_s2, double lambda, int mode,
+                                                float* __restrict__ out32, double* __restrict__ out64) {
+  extern __shared__ double sm[];
+  const int ld = nz + 1;
+  double* s_a = sm;
+  double* s_l = sm + nz * ld;
+  const int c = blockIdx.x;
+  const double* g = gram + (size_t)c * nz * nz;
+  for (int idx = threadIdx.x; idx < nz * nz; idx += blockDim.x) {
+    const int i = idx / nz, j = idx - i * nz;
+    double v;
+    if (mode == 0) {
+      v = g[idx] * inv_s2;
+      if (i == j) v += (double)lap[c] + 1.0 + (i > 0 ? 1.0 : 0.0) + (i < nz - 1 ? 1.0 : 0.0);
+      if (j == i + 1 || i == j + 1) v -= 1.0;
+    } else {
+      v = g[idx] + (i == j ? lambda : 0.0);
+    }
+    s_a[i * ld + j] = v;
+  }
+  __syncthreads();
+  block_cholesky(s_a, nz);
+  if (mode == 1) {
+    for (int idx = threadIdx.x; idx < nz * nz; idx += blockDim.x) {
+      const int i = idx / nz, j = idx - i * nz;
+      out64[(size_t)c * nz * nz + idx] = j <= i ? s_a[i * ld + j] : 0.0;
+    }
+    return;
+  }
+  // L^-1 column by column (one thread per column), then H^-1 = L^-T L^-1.
+  for (int col = threadIdx.x; col < nz; col += blockDim.x) {
+    for (int i = 0; i < col; ++i) s_l[i * ld + col] = 0.0;
+    for (int i = col; i < nz; ++i) {
+      double acc = (i == col) ? 1.0 : 0.0;
+      for (int kk = col; kk < i; ++kk) acc -= s_a[i * ld + kk] * s_l[kk * ld + col];
+      s_l[i * ld + col] = acc / s_a[i * ld + i];
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < nz * nz; idx += blockDim.x) {
+    const int i = idx / nz, j = idx - i * nz;
+    double acc = 0.0;
+    for (int kk = (i > j ? i : j); kk < nz; ++kk) acc += s_l[kk * ld + i] * s_l[kk * ld + j];
+    out32[(size_t)c * nz * nz + idx] = (float)acc;
+  }
+}
+
+// Gauss-Legendre nodes/weights on [-1,1] by Newton's method on P_n (the
+// three-term recurrence gives P_n and P_n').
+void gauss_legendre(int n, double* x, double* w) {
+  const double pi = 3.14159265358979323846;
+  for (int i = 0; i < n; ++i) {
+    double z = cos(pi * (i + 0.75) / (n + 0.5));
+    double dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1;
+        p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (fabs(dz) < 1e-16) break;
+    }
+    x[i] = -z;
+    w[i] = 2.0 / ((1.0 - z * z) * dp * dp);
+  }
+}
+
+struct DevBuf {
+  void* p = nullptr;
+  ~DevBuf() {
+    if (p) cudaFree(p);
+  }
+  cudaError_t alloc(size_t bytes) { return cudaMalloc(&p, bytes); }
+  template <typename T>
+  T* as() const {
+    return static_cast<T*>(p);
+  }
+};
+
+}  // namespace
+
+ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st) {
+  const int nt = k->nt, nz = k->nz, q = k->q, P = k->p, A = P / 2 + 1;
+  const int nclass = k->nclass;
+
+  // ---- host tables: class (a, b) pairs and cosine-sum matrices ----
+  std::vector<int> members(nclass * 4);
+  CTOF_CUDA_TRY(cudaMemcpy(members.data(), k->d_members, members.size() * sizeof(int), cudaMemcpyDeviceToHost));
+  std::vector<int2> ab(nclass);
+  for (int c = 0; c < nclass; ++c) {
+    const int f = members[c * 4];
+    const int kx = f % k->h, ky = f / k->h;
+    const int b = ky <= P / 2 ? ky : P - ky;
+    ab[c] = make_int2(kx, b);  // W_hat(kx, |ky|): x index kx, y index |ky|
+  }
+  // multiplicity of each non-negative offset on the periodic grid
+  std::vector<double> mult(q);
+  for (int o = 0; o < q; ++o) {
+    if (k->grid.conv_mode == CTOF_LINEAR) mult[o] = o == 0 ? 1.0 : 2.0;
+    else mult[o] = (o == 0 || 2 * o == P) ? 1.0 : 2.0;
+  }
+  const double two_pi = 6.283185307179586476925286766559;
+  std::vector<double> cp((size_t)q * A), cqt((size_t)A * q);
+  for (int o = 0; o < q; ++o)
+    for (int a = 0; a < A; ++a) {
+      const long long ph = ((long long)a * o) % P;
+      const double v = mult[o] * cos(two_pi * (double)ph / (double)P);
+      cp[(size_t)o * A + a] = v;
+      cqt[(size_t)a * q + o] = v;
+    }
+
+  PhysParams prm;
+  {
+    const double n = k->optics.n, mua = k->optics.mua_mm, musp = k->optics.musp_mm;
+    prm.mua = mua;
+    prm.c = 0.299792458 / n;
+    prm.D = 1.0 / (3.0 * (mua + musp));
+    prm.kappa = prm.D * prm.c;
+    const double reff = -1.440 / (n * n) + 0.710 / n + 0.668 + 0.0636 * n;
+    const double Acoef = (1.0 + reff) / (1.0 - reff);
+    prm.zb = 2.0 * Acoef * prm.D;
+    prm.z0 = k->optics.z0_mm > 0 ? k->optics.z0_mm : 1.0 / (mua + musp);
+    prm.rmin = k->r_min;
+    prm.dx = k->grid.dx_mm;
+    prm.dy = k->grid.dy_mm;
+    prm.dz = k->grid.dz_mm;
+    prm.zfirst = k->grid.z_first_mm;
+    prm.dt = k->grid.dt_ps;
+    prm.vol = prm.dx * prm.dy * prm.dz;
+    gauss_legendre(8, prm.gl_x, prm.gl_w);
+  }
+
+  // ---- device temporaries, processed in chunks of time bins ----
+  const long long planes = (long long)nt * nz;
+  int tchunk = nt;
+  const long long max_plane_elems = 1LL << 28;  // ~2 GB of FP64 per temporary
+  while (tchunk > 1 && (long long)tchunk * nz * (long long)q * (q > A ? q : A) > max_plane_elems) tchunk = (tchunk + 1) / 2;
+  const long long chunk_planes = (long long)tchunk * nz;
+
+  DevBuf d_cp, d_cqt, d_ab, d_wq, d_t1, d_out, d_what64, d_scal;
+  CTOF_CUDA_TRY(d_cp.alloc(cp.size() * sizeof(double)));
+  CTOF_CUDA_TRY(d_cqt.alloc(cqt.size() * sizeof(double)));
+  CTOF_CUDA_TRY(d_ab.alloc(ab.size() * sizeof(int2)));
+  CTOF_CUDA_TRY(d_wq.alloc((size_t)chunk_planes * q * q * sizeof(double)));
+  CTOF_CUDA_TRY(d_t1.alloc((size_t)chunk_planes * q * A * sizeof(double)));
+  CTOF_CUDA_TRY(d_out.alloc((size_t)chunk_planes * A * A * sizeof(double)));
+  CTOF_CUDA_TRY(d_what64.alloc((size_t)nclass * planes * sizeof(double)));
+  CTOF_CUDA_TRY(d_scal.alloc(4 * sizeof(double)));
+  CTOF_CUDA_TRY(cudaMemcpyAsync(d_cp.p, cp.data(), cp.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CTOF_CUDA_TRY(cudaMemcpyAsync(d_cqt.p, cqt.data(), cqt.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+  CTOF_CUDA_TRY(cudaMemcpyAsync(d_ab.p, ab.data(), ab.size() * sizeof(int2), cudaMemcpyHostToDevice, st));
+
+  for (int t0 = 0; t0 < nt; t0 += tchunk) {
+    const int tc = (t0 + tchunk <= nt) ? tchunk : nt - t0;
+    const long long np = (long long)tc * nz;
+    {
+      const long long npairs = k->symmetric ? (long long)q * (q + 1) / 2 : (long long)q * q;
+      const long long work = npairs * nz;
+      int blocks = (int)((work + 127) / 128);
+      if (blocks > 152 * 64) blocks = 152 * 64;
+      k_w_quadrant<<<blocks, 128, 0, st>>>(d_wq.as<double>(), t0, tc, nz, q, k->symmetric, prm);
+      CTOF_CUDA_TRY(cudaGetLastError());
+    }
+    if (k->d_w) {
+      CTOF_CUDA_TRY(cudaMemcpyAsync(k->d_w + (size_t)t0 * nz * q * q, d_wq.p, (size_t)np * q * q * sizeof(double),
+                                    cudaMemcpyDeviceToDevice, st));
+    }
+    for (long long b0 = 0; b0 < np; b0 += 65535) {
+      const int nb = (int)((np - b0) < 65535 ? (np - b0) : 65535);
+      dim3 g1(ctof_div_up(A, 64), ctof_div_up(q, 64), nb);
+      k_dgemm<<<g1, 256, 0, st>>>(d_wq.as<double>() + b0 * q * q, (long long)q * q, q, d_cp.as<double>(), 0, A,
+                                  d_t1.as<double>() + b0 * q * A, (long long)q * A, A, q, A, q);
+      CTOF_CUDA_TRY(cudaGetLastError());
+      dim3 g2(ctof_div_up(A, 64), ctof_div_up(A, 64), nb);
+      k_dgemm<<<g2, 256, 0, st>>>(d_cqt.as<double>(), 0, q, d_t1.as<double>() + b0 * q * A, (long long)q * A, A,
+                                  d_out.as<double>() + b0 * A * A, (long long)A * A, A, A, A, q);
+      CTOF_CUDA_TRY(cudaGetLastError());
+    }
+    {
+      const long long work = np * nclass;
+      int blocks = (int)((work + 255) / 256);
+      if (blocks > 152 * 32) blocks = 152 * 32;
+      k_gather_classes<<<blocks, 256, 0, st>>>(d_out.as<double>(), (int)np, A, d_ab.as<int2>(), nclass,
+                                               d_what64.as<double>(), planes, (int)((long long)t0 * nz));
+      CTOF_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  // FP32 copy of W_hat (layout [c][t][z] == [c][plane])
+  k_to_float<<<152 * 8, 256, 0, st>>>(d_what64.as<double>(), k->d_what, (size_t)nclass * planes);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  k_gram<<<nclass, 256, 0, st>>>(d_what64.as<double>(), nt, nz, k->d_gram);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  // class 0 is the DC frequency
+  k_power_iteration<<<1, 64, 0, st>>>(k->d_gram, nz, 4000, d_scal.as<double>());
+  CTOF_CUDA_TRY(cudaGetLastError());
+  k_max_diag<<<1, 256, 0, st>>>(k->d_gram, nclass, nz, d_scal.as<double>() + 1);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  double scal[2];
+  CTOF_CUDA_TRY(cudaMemcpyAsync(scal, d_scal.p, 2 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CTOF_CUDA_TRY(cudaStreamSynchronize(st));
+  k->scale = scal[0];
+  k->gram_max = scal[1];
+  if (!(k->scale > 0.0) || !isfinite(k->scale)) return CTOF_ENONFINITE;
+  const size_t fsm = (size_t)2 * nz * (nz + 1) * sizeof(double);
+  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+  k_factor<<<nclass, 128, fsm, st>>>(k->d_gram, k->d_lap, nz, 1.0 / (k->scale * k->scale), 0.0, 0, k->d_hinv,
+                                     nullptr);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  CTOF_CUDA_TRY(cudaStreamSynchronize(st));
+  return CTOF_OK;
+}
+
+ctof_status build_tikhonov_factors(ctof_kernel_s* k, double lambda, cudaStream_t st) {
+  const int nz = k->nz;
+  const size_t fsm = (size_t)2 * nz * (nz + 1) * sizeof(double);
+  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
+  k_factor<<<k->nclass, 128, fsm, st>>>(k->d_gram, k->d_lap, nz, 0.0, lambda, 1, nullptr, k->d_tik_chol);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  k->tik_lambda = lambda;
+  return CTOF_OK;
+}

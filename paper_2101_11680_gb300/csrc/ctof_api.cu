@@ -1,0 +1,512 @@
+// C ABI entry points: argument validation, the handle and its workspaces, and
+// the orchestration of the forward / adjoint / reconstruction chains.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <vector>
+
+#include "ctof_internal.h"
+
+static thread_local char g_last_error[512] = "";
+
+void ctof_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line) {
+  snprintf(g_last_error, sizeof(g_last_error), "%s (%s) at %s:%d: %s", cudaGetErrorName(e), what, file, line,
+           cudaGetErrorString(e));
+}
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
+
+int next_pow2(int v) {
+  int p = 1;
+  while (p < v) p <<= 1;
+  return p;
+}
+
+ctof_status validate(const ctof_optics* o, const ctof_grid* g) {
+  if (!o || !g) return CTOF_EINVAL;
+  if (!(isfinite(o->mua_mm) && o->mua_mm >= 0.0) || !finite_pos(o->musp_mm) || !(isfinite(o->n) && o->n >= 1.0))
+    return CTOF_EINVAL;
+  if (!isfinite(o->z0_mm)) return CTOF_EINVAL;
+  if (g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || g->nt <= 0) return CTOF_EINVAL;
+  if (!finite_pos(g->dx_mm) || !finite_pos(g->dy_mm) || !finite_pos(g->dz_mm) || !finite_pos(g->z_first_mm) ||
+      !finite_pos(g->dt_ps))
+    return CTOF_EINVAL;
+  if (g->conv_mode != CTOF_LINEAR && g->conv_mode != CTOF_CIRCULAR) return CTOF_EINVAL;
+  if (g->nx != g->ny) return CTOF_EUNSUPPORTED;
+  if (g->nz > 64 || g->nt > 1024) return CTOF_EUNSUPPORTED;
+  // one frequency class (W_hat block, vectors, partial sums) must fit in shared memory
+  {
+    const size_t nt = (size_t)g->nt, nz = (size_t)g->nz;
+    const size_t w = (nt * (nz + 1) + 1) & ~(size_t)1;
+    const size_t admm = (w + ((nz * (nz + 1) + 1) & ~(size_t)1) + 1) * 4 + (4 * nt + 44 * nz) * 8;
+    const size_t tik = ((w * 4 + 4 * nt * 8 + 32 * nz * 8 + 7) & ~(size_t)7) + (nz * nz + 8 * nz) * 8;
+    if (admm > 227 * 1024 || tik > 227 * 1024) return CTOF_EUNSUPPORTED;
+  }
+  if (g->conv_mode == CTOF_LINEAR) {
+    if (g->nx < 4 || g->nx > 256) return CTOF_EUNSUPPORTED;
+  } else {
+    if (g->nx < 32 || g->nx > 512 || (g->nx & (g->nx - 1)) != 0) return CTOF_EUNSUPPORTED;
+  }
+  return CTOF_OK;
+}
+
+// Frequency classes: half-plane frequencies with equal W_hat.  The kernel is
+// even in x and y (and symmetric under x <-> y when dx == dy), so W_hat(kx,ky)
+// depends on (kx, |ky|) -- and on the unordered pair when symmetric.
+void make_classes(int P, bool symmetric, std::vector<int>& members, std::vector<float>& lap) {
+  const int h = P / 2 + 1;
+  const int A = h;
+  std::vector<int> key_to_class((size_t)A * A, -1);
+  std::vector<std::pair<int, int>> keys;
+  // enumerate keys in (b, a) order so that class 0 is the DC frequency
+  for (int b = 0; b < A; ++b)
+    for (int a = 0; a < A; ++a) {
+      if (symmetric && a > b) continue;
+      key_to_class[(size_t)b * A + a] = (int)keys.size();
+      keys.push_back({a, b});
+    }
+  const int nclass = (int)keys.size();
+  members.assign((size_t)nclass * 4, -1);
+  std::vector<int> count(nclass, 0);
+  for (int ky = 0; ky < P; ++ky)
+    for (int kx = 0; kx < h; ++kx) {
+      int a = kx, b = ky <= P / 2 ? ky : P - ky;
+      if (symmetric && a > b) std::swap(a, b);
+      const int c = key_to_class[(size_t)b * A + a];
+      const int f = ky * h + kx;
+      members[(size_t)c * 4 + count[c]++] = f;
+    }
+  // the class's first member must be (kx = a, |ky| = b) for the table gather
+  for (int c = 0; c < nclass; ++c) {
+    const int a = keys[c].first, b = keys[c].second;
+    for (int m = 0; m < count[c]; ++m) {
+      const int f = members[(size_t)c * 4 + m];
+      const int kx = f % h, ky = f / h;
+      if (kx == a && (ky == b || ky == (P - b) % P)) {
+        std::swap(members[(size_t)c * 4], members[(size_t)c * 4 + m]);
+        break;
+      }
+    }
+  }
+  lap.resize(nclass);
+  const double pi = 3.14159265358979323846;
+  for (int c = 0; c < nclass; ++c) {
+    const double sa = sin(pi * keys[c].first / P), sb = sin(pi * keys[c].second / P);
+    lap[c] = (float)(4.0 * sa * sa + 4.0 * sb * sb);
+  }
+}
+
+struct Carver {
+  size_t off = 0;
+  template <typename T>
+  size_t take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    const size_t at = off;
+    off += count * sizeof(T);
+    return at;
+  }
+};
+
+ctof_status forward_impl(ctof_kernel_s* k, const float* mu, float* m, cudaStream_t st) {
+  CTOF_TRY(fft_forward_planes(k, mu, k->nz, k->n, k->n, k->n, k->d_inter_z, k->d_spec_z, k->ldz, st));
+  CTOF_TRY(contract_forward(k, k->d_spec_z, k->d_spec_t, st));
+  return fft_inverse_planes(k, k->d_spec_t, k->ldt, k->nt, k->n, k->n, k->d_inter_t, m, k->n, st);
+}
+
+ctof_status adjoint_impl(ctof_kernel_s* k, const float* m, float* vol, cudaStream_t st) {
+  CTOF_TRY(fft_forward_planes(k, m, k->nt, k->n, k->n, k->n, k->d_inter_t, k->d_spec_t, k->ldt, st));
+  CTOF_TRY(contract_adjoint(k, k->d_spec_t, k->d_spec_z, st));
+  return fft_inverse_planes(k, k->d_spec_z, k->ldz, k->nz, k->n, k->n, k->d_inter_z, vol, k->n, st);
+}
+
+// ADMM on the staged measurement d_mstage; result (crop of v3) in d_vstage.
+ctof_status admm_enqueue(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st) {
+  const int nt = k->nt, nz = k->nz, n = k->n, P = k->p;
+  const size_t pp = (size_t)P * P;
+  const float inv_s = (float)(1.0 / k->scale);
+  const float rho = (float)prm->rho;
+  CTOF_CUDA_TRY(cudaMemsetAsync(k->d_scalars, 0, 16 * sizeof(double), st));
+  if (prm->tv_beta < 0) {
+    CTOF_TRY(adjoint_impl(k, k->d_mstage, k->d_vstage, st));
+    CTOF_TRY(reduce_max_abs(k->d_vstage, (size_t)nz * n * n, k->d_scalars + 1, st));
+  }
+  CTOF_TRY(admm_set_beta(k->d_scalars, prm->tv_beta, prm->beta_rel, 1.0 / (k->scale * k->scale), st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(k->d_spec_t2, 0, (size_t)k->nf * k->ldt * sizeof(float2), st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(k->d_spec_z, 0, (size_t)k->nf * k->ldz * sizeof(float2), st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(k->d_spec_z2, 0, (size_t)k->nf * k->ldz * sizeof(float2), st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(k->d_u1, 0, (size_t)nt * n * n * sizeof(float), st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(k->d_u2a, 0, 3 * nz * pp * sizeof(float), st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(k->d_u3, 0, nz * pp * sizeof(float), st));
+  float* u2[2] = {k->d_u2a, k->d_u2b};
+  for (int it = 0; it < prm->iters; ++it) {
+    const bool last = it == prm->iters - 1;
+    // x-update (per frequency class) and K x
+    CTOF_TRY(contract_admm(k, k->d_spec_t2, k->d_spec_z, k->d_spec_z2, k->d_spec_t, inv_s, st));
+    if (!last) {
+      // T side: K x -> v1/u1 -> c_hat
+      CTOF_TRY(fft_cols_inverse(k, k->d_spec_t, k->ldt, nt, n, k->d_inter_t, st));
+      CTOF_TRY(fft_rows_admm_t(k, k->d_inter_t, k->d_mstage, k->d_u1, inv_s, rho, st));
+      CTOF_TRY(fft_cols_forward(k, k->d_inter_t, nt, n, k->d_spec_t2, k->ldt, st));
+    }
+    // Z side: x -> TV / nonnegativity prox -> s_hat
+    CTOF_TRY(fft_cols_inverse(k, k->d_spec_z2, k->ldz, nz, P, k->d_inter_z, st));
+    CTOF_TRY(fft_rows_inverse(k, k->d_inter_z, nz, P, P, k->d_xs, P, st));
+    CTOF_TRY(admm_tv_stencil(k, k->d_xs, u2[it & 1], u2[(it + 1) & 1], k->d_u3, k->d_s, k->d_scalars, rho,
+                             last ? k->d_vstage : nullptr, st));
+    if (!last) {
+      CTOF_TRY(fft_rows_forward(k, k->d_s, nz, P, P, P, k->d_inter_z, st));
+      CTOF_TRY(fft_cols_forward(k, k->d_inter_z, nz, P, k->d_spec_z, k->ldz, st));
+    }
+  }
+  return CTOF_OK;
+}
+
+ctof_status admm_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st) {
+  const bool same = k->graph && k->graph_iters == prm->iters && k->graph_rho == prm->rho &&
+                    k->graph_beta == prm->tv_beta && k->graph_beta_rel == prm->beta_rel;
+  if (!same) {
+    if (k->graph) {
+      cudaGraphExecDestroy(k->graph);
+      k->graph = nullptr;
+    }
+    cudaStream_t cap = nullptr;
+    CTOF_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t g = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    if (e != cudaSuccess) {
+      cudaStreamDestroy(cap);
+      CTOF_CUDA_TRY(e);
+    }
+    const ctof_status s = admm_enqueue(k, prm, cap);
+    e = cudaStreamEndCapture(cap, &g);
+    cudaStreamDestroy(cap);
+    if (s != CTOF_OK) {
+      if (g) cudaGraphDestroy(g);
+      return s;
+    }
+    CTOF_CUDA_TRY(e);
+    e = cudaGraphInstantiate(&k->graph, g, 0);
+    cudaGraphDestroy(g);
+    CTOF_CUDA_TRY(e);
+    k->graph_iters = prm->iters;
+    k->graph_rho = prm->rho;
+    k->graph_beta = prm->tv_beta;
+    k->graph_beta_rel = prm->beta_rel;
+  }
+  CTOF_CUDA_TRY(cudaGraphLaunch(k->graph, st));
+  return CTOF_OK;
+}
+
+ctof_status tikhonov_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st, double* lambda_out) {
+  const double lambda = prm->tik_lambda_rel * k->gram_max;
+  if (!(lambda > 0.0) || !isfinite(lambda)) return CTOF_EINVAL;
+  if (!k->d_tik_chol) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)k->nclass * k->nz * k->nz * sizeof(double)) != cudaSuccess) return CTOF_ENOMEM;
+    k->d_tik_chol = static_cast<double*>(p);
+    k->tik_lambda = -1.0;
+  }
+  if (k->tik_lambda != lambda) CTOF_TRY(build_tikhonov_factors(k, lambda, st));
+  *lambda_out = lambda;
+  CTOF_TRY(fft_forward_planes(k, k->d_mstage, k->nt, k->n, k->n, k->n, k->d_inter_t, k->d_spec_t, k->ldt, st));
+  CTOF_TRY(contract_tikhonov(k, k->d_tik_chol, k->d_spec_t, k->d_spec_z, st));
+  return fft_inverse_planes(k, k->d_spec_z, k->ldz, k->nz, k->n, k->n, k->d_inter_z, k->d_vstage, k->n, st);
+}
+
+ctof_status validate_params(const ctof_solver_params* p) {
+  if (!p) return CTOF_EINVAL;
+  if (p->solver == CTOF_SOLVER_ADMM_TV) {
+    if (p->iters < 1 || p->iters > 100000) return CTOF_EINVAL;
+    if (!finite_pos(p->rho)) return CTOF_EINVAL;
+    if (!isfinite(p->tv_beta)) return CTOF_EINVAL;
+    if (p->tv_beta < 0 && !(isfinite(p->beta_rel) && p->beta_rel >= 0)) return CTOF_EINVAL;
+    return CTOF_OK;
+  }
+  if (p->solver == CTOF_SOLVER_TIKHONOV) return finite_pos(p->tik_lambda_rel) ? CTOF_OK : CTOF_EINVAL;
+  return CTOF_EINVAL;
+}
+
+// Runs the chosen solver on d_mstage, leaving the result in d_vstage.
+ctof_status solve_staged(ctof_kernel_s* k, const ctof_solver_params* prm, double* lambda, cudaStream_t st) {
+  *lambda = 0.0;
+  if (prm->solver == CTOF_SOLVER_ADMM_TV) return admm_run(k, prm, st);
+  return tikhonov_run(k, prm, st, lambda);
+}
+
+// Synchronising report: parameters used and a NaN/Inf scan of the result.
+ctof_status fill_report(ctof_kernel_s* k, const ctof_solver_params* prm, double lambda, ctof_report* rep,
+                        cudaStream_t st) {
+  int* flag = reinterpret_cast<int*>(k->d_scalars + 8);
+  CTOF_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+  CTOF_TRY(check_finite(k->d_vstage, (size_t)k->nz * k->n * k->n, flag, st));
+  double sc[9];
+  CTOF_CUDA_TRY(cudaMemcpyAsync(sc, k->d_scalars, 9 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  CTOF_CUDA_TRY(cudaStreamSynchronize(st));
+  int bad = 0;
+  memcpy(&bad, &sc[8], sizeof(int));
+  rep->scale = k->scale;
+  rep->beta = prm->solver == CTOF_SOLVER_ADMM_TV ? sc[0] : 0.0;
+  rep->lambda = lambda;
+  rep->iters_done = prm->solver == CTOF_SOLVER_ADMM_TV ? prm->iters : 1;
+  return bad ? CTOF_ENONFINITE : CTOF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* ctof_status_string(ctof_status s) {
+  switch (s) {
+    case CTOF_OK: return "ok";
+    case CTOF_EINVAL: return "invalid argument";
+    case CTOF_ENOMEM: return "out of device memory";
+    case CTOF_ECUDA: return "CUDA runtime error";
+    case CTOF_ENONFINITE: return "non-finite value";
+    case CTOF_ETIMEOUT: return "device wait timed out";
+    case CTOF_EUNSUPPORTED: return "unsupported configuration";
+  }
+  return "unknown status";
+}
+
+const char* ctof_last_error_message(void) { return g_last_error; }
+
+void ctof_kernel_destroy(ctof_kernel k) {
+  if (!k) return;
+  DeviceGuard guard(k->device);
+  if (k->graph) cudaGraphExecDestroy(k->graph);
+  if (k->d_tik_chol) cudaFree(k->d_tik_chol);
+  if (k->d_w) cudaFree(k->d_w);
+  if (k->d_base) cudaFree(k->d_base);
+  delete k;
+}
+
+ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, int flags, void* stream,
+                              ctof_kernel* out) {
+  if (!out) return CTOF_EINVAL;
+  *out = nullptr;
+  CTOF_TRY(validate(optics, grid));
+  if (flags & ~CTOF_KEEP_W) return CTOF_EINVAL;
+  int dev = 0;
+  CTOF_CUDA_TRY(cudaGetDevice(&dev));
+  ctof_kernel_s* k = new (std::nothrow) ctof_kernel_s();
+  if (!k) return CTOF_ENOMEM;
+  k->optics = *optics;
+  k->grid = *grid;
+  k->flags = flags;
+  k->device = dev;
+  k->n = grid->nx;
+  k->nt = grid->nt;
+  k->nz = grid->nz;
+  k->p = grid->conv_mode == CTOF_LINEAR ? std::max(32, next_pow2(2 * grid->nx)) : grid->nx;
+  k->h = k->p / 2 + 1;
+  k->hp = ctof_round_up(k->h, 4);
+  k->nf = k->p * k->h;
+  k->q = grid->conv_mode == CTOF_LINEAR ? grid->nx : k->p / 2 + 1;
+  k->ldt = ctof_round_up(k->nt, 8);
+  k->ldz = ctof_round_up(k->nz, 8);
+  k->symmetric = grid->dx_mm == grid->dy_mm;
+  k->r_min = optics->clamp_r ? 0.5 * std::min(grid->dx_mm, std::min(grid->dy_mm, grid->dz_mm)) : 0.0;
+  k->tik_lambda = -1.0;
+
+  std::vector<int> members;
+  std::vector<float> lap;
+  make_classes(k->p, k->symmetric != 0, members, lap);
+  k->nclass = (int)lap.size();
+
+  const int nt = k->nt, nz = k->nz, n = k->n, P = k->p;
+  const size_t pp = (size_t)P * P;
+  Carver cv;
+  const size_t o_members = cv.take<int>((size_t)k->nclass * 4);
+  const size_t o_lap = cv.take<float>(k->nclass);
+  const size_t o_what = cv.take<float>((size_t)k->nclass * nt * nz);
+  const size_t o_gram = cv.take<double>((size_t)k->nclass * nz * nz);
+  const size_t o_hinv = cv.take<float>((size_t)k->nclass * nz * nz);
+  const size_t o_tw = cv.take<float2>(P);
+  const size_t o_st = cv.take<float2>((size_t)k->nf * k->ldt);
+  const size_t o_st2 = cv.take<float2>((size_t)k->nf * k->ldt);
+  const size_t o_sz = cv.take<float2>((size_t)k->nf * k->ldz);
+  const size_t o_sz2 = cv.take<float2>((size_t)k->nf * k->ldz);
+  const size_t o_it = cv.take<float2>((size_t)nt * n * k->hp);
+  const size_t o_iz = cv.take<float2>((size_t)nz * P * k->hp);
+  const size_t o_u1 = cv.take<float>((size_t)nt * n * n);
+  const size_t o_ms = cv.take<float>((size_t)nt * n * n);
+  const size_t o_u2a = cv.take<float>(3 * nz * pp);
+  const size_t o_u2b = cv.take<float>(3 * nz * pp);
+  const size_t o_u3 = cv.take<float>(nz * pp);
+  const size_t o_xs = cv.take<float>(nz * pp);
+  const size_t o_s = cv.take<float>(nz * pp);
+  const size_t o_vs = cv.take<float>((size_t)nz * n * n);
+  const size_t o_sc = cv.take<double>(16);
+  k->bytes = cv.off;
+  if (cudaMalloc(&k->d_base, k->bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete k;
+    return CTOF_ENOMEM;
+  }
+  char* b = static_cast<char*>(k->d_base);
+  k->d_members = reinterpret_cast<int*>(b + o_members);
+  k->d_lap = reinterpret_cast<float*>(b + o_lap);
+  k->d_what = reinterpret_cast<float*>(b + o_what);
+  k->d_gram = reinterpret_cast<double*>(b + o_gram);
+  k->d_hinv = reinterpret_cast<float*>(b + o_hinv);
+  k->d_tw = reinterpret_cast<float2*>(b + o_tw);
+  k->d_spec_t = reinterpret_cast<float2*>(b + o_st);
+  k->d_spec_t2 = reinterpret_cast<float2*>(b + o_st2);
+  k->d_spec_z = reinterpret_cast<float2*>(b + o_sz);
+  k->d_spec_z2 = reinterpret_cast<float2*>(b + o_sz2);
+  k->d_inter_t = reinterpret_cast<float2*>(b + o_it);
+  k->d_inter_z = reinterpret_cast<float2*>(b + o_iz);
+  k->d_u1 = reinterpret_cast<float*>(b + o_u1);
+  k->d_mstage = reinterpret_cast<float*>(b + o_ms);
+  k->d_u2a = reinterpret_cast<float*>(b + o_u2a);
+  k->d_u2b = reinterpret_cast<float*>(b + o_u2b);
+  k->d_u3 = reinterpret_cast<float*>(b + o_u3);
+  k->d_xs = reinterpret_cast<float*>(b + o_xs);
+  k->d_s = reinterpret_cast<float*>(b + o_s);
+  k->d_vstage = reinterpret_cast<float*>(b + o_vs);
+  k->d_scalars = reinterpret_cast<double*>(b + o_sc);
+  if (flags & CTOF_KEEP_W) {
+    void* p = nullptr;
+    if (cudaMalloc(&p, (size_t)nt * nz * k->q * k->q * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      ctof_kernel_destroy(k);
+      return CTOF_ENOMEM;
+    }
+    k->d_w = static_cast<double*>(p);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::vector<float2> tw(P);
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int j = 0; j < P; ++j) tw[j] = make_float2((float)cos(two_pi * j / P), (float)-sin(two_pi * j / P));
+  ctof_status s = CTOF_OK;
+  do {
+    if (cudaMemcpyAsync(k->d_members, members.data(), members.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(k->d_lap, lap.data(), lap.size() * sizeof(float), cudaMemcpyHostToDevice, st) !=
+            cudaSuccess ||
+        cudaMemcpyAsync(k->d_tw, tw.data(), tw.size() * sizeof(float2), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess) {
+      s = CTOF_ECUDA;
+      break;
+    }
+    s = build_kernel_tables(k, st);
+  } while (0);
+  if (s != CTOF_OK) {
+    cudaStreamSynchronize(st);
+    ctof_kernel_destroy(k);
+    return s;
+  }
+  *out = k;
+  return CTOF_OK;
+}
+
+ctof_status ctof_kernel_get_info(ctof_kernel k, ctof_kernel_info* info) {
+  if (!k || !info) return CTOF_EINVAL;
+  info->p = k->p;
+  info->n_freq = k->nf;
+  info->n_class = k->nclass;
+  info->nt = k->nt;
+  info->nz = k->nz;
+  info->scale = k->scale;
+  info->gram_max_diag = k->gram_max;
+  info->device_bytes = k->bytes + (k->d_w ? (size_t)k->nt * k->nz * k->q * k->q * sizeof(double) : 0) +
+                       (k->d_tik_chol ? (size_t)k->nclass * k->nz * k->nz * sizeof(double) : 0);
+  return CTOF_OK;
+}
+
+ctof_status ctof_kernel_get_w(ctof_kernel k, double* h_w) {
+  if (!k || !h_w) return CTOF_EINVAL;
+  if (!k->d_w) return CTOF_EUNSUPPORTED;
+  DeviceGuard g(k->device);
+  CTOF_CUDA_TRY(cudaMemcpy(h_w, k->d_w, (size_t)k->nt * k->nz * k->q * k->q * sizeof(double), cudaMemcpyDeviceToHost));
+  return CTOF_OK;
+}
+
+ctof_status ctof_kernel_get_classes(ctof_kernel k, int* h_members) {
+  if (!k || !h_members) return CTOF_EINVAL;
+  DeviceGuard g(k->device);
+  CTOF_CUDA_TRY(cudaMemcpy(h_members, k->d_members, (size_t)k->nclass * 4 * sizeof(int), cudaMemcpyDeviceToHost));
+  return CTOF_OK;
+}
+
+ctof_status ctof_kernel_get_what(ctof_kernel k, float* h_what) {
+  if (!k || !h_what) return CTOF_EINVAL;
+  DeviceGuard g(k->device);
+  CTOF_CUDA_TRY(cudaMemcpy(h_what, k->d_what, (size_t)k->nclass * k->nt * k->nz * sizeof(float),
+                           cudaMemcpyDeviceToHost));
+  return CTOF_OK;
+}
+
+ctof_status ctof_forward(ctof_kernel k, const float* d_mu, float* d_m, void* stream) {
+  if (!k || !d_mu || !d_m) return CTOF_EINVAL;
+  DeviceGuard g(k->device);
+  if (!g.ok) return CTOF_ECUDA;
+  return forward_impl(k, d_mu, d_m, static_cast<cudaStream_t>(stream));
+}
+
+ctof_status ctof_adjoint(ctof_kernel k, const float* d_m, float* d_vol, void* stream) {
+  if (!k || !d_m || !d_vol) return CTOF_EINVAL;
+  DeviceGuard g(k->device);
+  if (!g.ok) return CTOF_ECUDA;
+  return adjoint_impl(k, d_m, d_vol, static_cast<cudaStream_t>(stream));
+}
+
+ctof_status ctof_reconstruct(ctof_kernel k, const float* d_m, const ctof_solver_params* params, float* d_mu,
+                             ctof_report* report, void* stream) {
+  if (!k || !d_m || !d_mu) return CTOF_EINVAL;
+  CTOF_TRY(validate_params(params));
+  DeviceGuard g(k->device);
+  if (!g.ok) return CTOF_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t mbytes = (size_t)k->nt * k->n * k->n * sizeof(float);
+  const size_t vbytes = (size_t)k->nz * k->n * k->n * sizeof(float);
+  double lambda = 0.0;
+  CTOF_CUDA_TRY(cudaMemcpyAsync(k->d_mstage, d_m, mbytes, cudaMemcpyDeviceToDevice, st));
+  CTOF_TRY(solve_staged(k, params, &lambda, st));
+  CTOF_CUDA_TRY(cudaMemcpyAsync(d_mu, k->d_vstage, vbytes, cudaMemcpyDeviceToDevice, st));
+  if (report) return fill_report(k, params, lambda, report, st);
+  return CTOF_OK;
+}
+
+ctof_status ctof_reconstruct_host(ctof_kernel k, const float* h_m, const ctof_solver_params* params, float* h_mu,
+                                  ctof_report* report, void* stream) {
+  if (!k || !h_m || !h_mu) return CTOF_EINVAL;
+  CTOF_TRY(validate_params(params));
+  DeviceGuard g(k->device);
+  if (!g.ok) return CTOF_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t mbytes = (size_t)k->nt * k->n * k->n * sizeof(float);
+  const size_t vbytes = (size_t)k->nz * k->n * k->n * sizeof(float);
+  double lambda = 0.0;
+  CTOF_CUDA_TRY(cudaMemcpyAsync(k->d_mstage, h_m, mbytes, cudaMemcpyHostToDevice, st));
+  CTOF_TRY(solve_staged(k, params, &lambda, st));
+  CTOF_CUDA_TRY(cudaMemcpyAsync(h_mu, k->d_vstage, vbytes, cudaMemcpyDeviceToHost, st));
+  if (report) return fill_report(k, params, lambda, report, st);
+  CTOF_CUDA_TRY(cudaStreamSynchronize(st));
+  return CTOF_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,117 @@
+// Internal state of a ctof handle and the launchers each translation unit
+// provides.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "common.cuh"
+
+// Device workspaces are carved from one allocation per handle.
+struct ctof_kernel_s {
+  ctof_optics optics;
+  ctof_grid grid;
+  int flags;
+  int device;
+
+  // geometry
+  int n;        // lateral scan size (nx == ny)
+  int p;        // lateral FFT size
+  int h;        // P/2 + 1 (half-plane width)
+  int hp;       // row pitch (complex) of row-pass intermediates
+  int nf;       // P * h half-plane frequencies
+  int q;        // kernel-table extent per lateral axis (n linear, P/2+1 circular)
+  int nt, nz;
+  int ldt, ldz; // frequency-major leading dims (complex) of T- and Z-side spectra
+  int nclass;
+  int symmetric;  // dx == dy: 8-fold lateral symmetry, classes hold up to 4 members
+
+  double scale;     // max_f sigma_max(W_hat(f))
+  double gram_max;  // max_{f,j} G_jj(f)
+  double r_min;
+
+  // one device allocation holds everything below
+  void* d_base;
+  size_t bytes;
+
+  int* d_members;      // [nclass][4]
+  float* d_lap;        // [nclass] 4 sin^2(pi a/P) + 4 sin^2(pi b/P)
+  float* d_what;       // [nclass][nt][nz]
+  double* d_gram;      // [nclass][nz][nz]
+  float* d_hinv;       // [nclass][nz][nz]  (ADMM normal matrix inverse, normalised units)
+  float2* d_tw;        // [p] forward twiddles exp(-2 pi i j / P)
+  double* d_w;         // optional FP64 kernel table [nt][nz][q][q]
+
+  float2* d_spec_t;    // [nf][ldt]
+  float2* d_spec_t2;   // [nf][ldt]
+  float2* d_spec_z;    // [nf][ldz]
+  float2* d_spec_z2;   // [nf][ldz]
+  float2* d_inter_t;   // [nt][n][hp]
+  float2* d_inter_z;   // [nz][p][hp]
+  float* d_u1;         // [nt][n][n]
+  float* d_mstage;     // [nt][n][n]
+  float* d_u2a;        // [3][nz][p][p]
+  float* d_u2b;        // [3][nz][p][p]
+  float* d_u3;         // [nz][p][p]
+  float* d_xs;         // [nz][p][p]
+  float* d_s;          // [nz][p][p]
+  float* d_vstage;     // [nz][n][n]
+  double* d_scalars;   // [16] device scalars (beta, max reductions, flags)
+
+  // Tikhonov cache: FP64 Cholesky factors of G + lambda I
+  double tik_lambda;
+  double* d_tik_chol;  // [nclass][nz][nz] (separate allocation, lazily made)
+
+  // ADMM graph cache
+  cudaGraphExec_t graph;
+  int graph_iters;
+  double graph_rho, graph_beta, graph_beta_rel;
+  cudaStream_t graph_stream;
+};
+
+// ---- fft.cu -------------------------------------------------------------
+// Forward R2C of planes of real rows [nplanes][rows_in][ld_in] (first cols_in
+// columns used, the rest of the P-wide row is zero) into frequency-major
+// spectra out[f][ldf] (plane index fastest).  Zero rows beyond rows_in.
+ctof_status fft_forward_planes(const ctof_kernel_s* k, const float* in, int nplanes, int rows_in,
+                               int cols_in, int ld_in, float2* inter, float2* out, int ldf,
+                               cudaStream_t st);
+// Inverse C2R of frequency-major spectra in[f][ldf] into real rows
+// out[nplanes][rows_out][ld_out] (first cols_out columns), scaled by 1/P^2.
+ctof_status fft_inverse_planes(const ctof_kernel_s* k, const float2* in, int ldf, int nplanes,
+                               int rows_out, int cols_out, float2* inter, float* out, int ld_out,
+                               cudaStream_t st);
+// Column passes alone (used by the fused ADMM chains).
+ctof_status fft_cols_forward(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows_in,
+                             float2* out, int ldf, cudaStream_t st);
+ctof_status fft_cols_inverse(const ctof_kernel_s* k, const float2* in, int ldf, int nplanes,
+                             int rows_out, float2* inter, cudaStream_t st);
+ctof_status fft_rows_forward(const ctof_kernel_s* k, const float* in, int nplanes, int rows,
+                             int cols_in, int ld_in, float2* inter, cudaStream_t st);
+ctof_status fft_rows_inverse(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows,
+                             int cols_out, float* out, int ld_out, cudaStream_t st);
+// ADMM T side: inverse rows of K x (crop) -> v1/u1 update -> forward rows of
+// the correction c, in place in `inter` ([nt][n][hp]).
+ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* m, float* u1,
+                            float inv_scale, float rho, cudaStream_t st);
+
+// ---- contract.cu --------------------------------------------------------
+ctof_status contract_forward(const ctof_kernel_s* k, const float2* in_z, float2* out_t, cudaStream_t st);
+ctof_status contract_adjoint(const ctof_kernel_s* k, const float2* in_t, float2* out_z, cudaStream_t st);
+ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const float2* s_hat,
+                          float2* x_hat, float2* kx_hat, float inv_scale, cudaStream_t st);
+ctof_status contract_tikhonov(const ctof_kernel_s* k, const double* chol, const float2* m_hat,
+                              float2* x_hat, cudaStream_t st);
+
+// ---- build.cu ----------------------------------------------------------
+ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st);
+ctof_status build_tikhonov_factors(ctof_kernel_s* k, double lambda, cudaStream_t st);
+
+// ---- admm.cu ------------------------------------------------------------
+ctof_status admm_tv_stencil(const ctof_kernel_s* k, const float* x, const float* u2_old,
+                            float* u2_new, float* u3, float* s, const double* beta_dev,
+                            float rho, float* out_crop, cudaStream_t st);
+ctof_status reduce_max_abs(const float* v, size_t count, double* out_dev, cudaStream_t st);
+ctof_status admm_set_beta(double* scalars, double beta_fixed, double beta_rel, double inv_scale2,
+                          cudaStream_t st);
+ctof_status check_finite(const float* v, size_t count, int* flag_dev, cudaStream_t st);

@@ -1,0 +1,464 @@
+// Lateral 2-D FFTs of the confocal planes (Section 4, "Computational
+// Complexity Analysis": the convolution with the K x K blur kernel runs via
+// FFTs).  Planes are P x P real (P a power of two, 32..512); spectra are the
+// R2C half plane P x (P/2+1) stored frequency-major, f = ky*(P/2+1) + kx, with
+// the plane index (time bin or depth) fastest, because the per-frequency
+// contraction reads whole T- or Z-vectors of one frequency.
+//
+// Two passes per direction:
+//   rows    (x axis, real <-> complex): one warp transforms two real rows packed
+//           as one complex row, then splits them with the Hermitian identities.
+//   columns (y axis, complex): a CTA stages a tile of 4 kx-columns x 8 planes
+//           in shared memory, each warp transforms whole columns, and the tile
+//           is written out transposed so that the frequency-major side moves in
+//           64-byte runs of consecutive planes.
+// Each 1-D transform of length P = 32 R lives in one warp: lane l register r
+// holds element l + 32 r; an R-point DIF over registers, a twiddle by
+// w_P^(l k2), and a 32-point DIF across lanes (shuffles) give element
+// R*bitrev5(l) + bitrev_R(r).  Twiddles exp(-2 pi i j/P) are computed on the
+// host in double precision and staged in shared memory.
+#include <cuda_runtime.h>
+
+#include "ctof_internal.h"
+
+namespace {
+
+constexpr int KB = 4;          // kx columns per column-pass tile
+constexpr int PB = 8;          // planes per column-pass tile
+constexpr int NC = KB * PB;    // columns per tile
+constexpr int COL_THREADS = 256;
+constexpr int ROW_WARPS = 8;
+
+__host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
+__host__ __device__ constexpr int bitrevc(int i, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b) r = (r << 1) | ((i >> b) & 1);
+  return r;
+}
+
+__device__ __forceinline__ int brev5(int l) { return (int)(__brev((unsigned)l) >> 27); }
+
+template <int P, bool INV>
+__device__ __forceinline__ float2 tw_get(const float2* tw, int j) {
+  float2 w = tw[j & (P - 1)];
+  return INV ? make_float2(w.x, -w.y) : w;
+}
+
+// Length-P DFT held by one warp (see file comment).  INV selects exp(+...).
+template <int P, bool INV>
+__device__ __forceinline__ void warp_fft(float2 (&v)[P / 32], int lane, const float2* tw) {
+  constexpr int R = P / 32;
+#pragma unroll
+  for (int s = R / 2; s >= 1; s >>= 1) {
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      if ((i & s) == 0) {
+        const float2 a = v[i], b = v[i + s];
+        v[i] = cadd(a, b);
+        v[i + s] = cmul(csub(a, b), tw_get<P, INV>(tw, (i & (s - 1)) * (P / (2 * s))));
+      }
+    }
+  }
+#pragma unroll
+  for (int i = 1; i < R; ++i) {
+    const int k2 = bitrevc(i, ilog2c(R));
+    v[i] = cmul(v[i], tw_get<P, INV>(tw, lane * k2));
+  }
+#pragma unroll
+  for (int s = 16; s >= 1; s >>= 1) {
+    const bool upper = (lane & s) != 0;
+    const float2 w = tw_get<P, INV>(tw, (lane & (s - 1)) * (P / (2 * s)));
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      float2 o;
+      o.x = __shfl_xor_sync(0xffffffffu, v[i].x, s);
+      o.y = __shfl_xor_sync(0xffffffffu, v[i].y, s);
+      v[i] = upper ? cmul(csub(o, v[i]), w) : cadd(v[i], o);
+    }
+  }
+}
+
+// Output position of register i of lane `lane` after warp_fft.
+template <int P>
+__device__ __forceinline__ int out_pos(int lane, int i) {
+  constexpr int R = P / 32;
+  return R * brev5(lane) + bitrevc(i, ilog2c(R));
+}
+
+template <int P>
+__device__ __forceinline__ void stage_twiddles(float2* s_tw, const float2* tw) {
+  for (int i = threadIdx.x; i < P; i += blockDim.x) s_tw[i] = tw[i];
+}
+
+// Split Z = FFT(a + i b) of two real rows into A = FFT(a), B = FFT(b), k <= P/2.
+template <int P>
+__device__ __forceinline__ void split_write(const float2* buf, int lane, float2* rowA, float2* rowB) {
+  for (int kk = lane; kk <= P / 2; kk += 32) {
+    const float2 zk = buf[kk];
+    const float2 zm = buf[(P - kk) & (P - 1)];
+    rowA[kk] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    if (rowB) rowB[kk] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+  }
+}
+
+// Build Z[n] = A[n] + i B[n] from the half spectra of two real rows (Hermitian
+// extension for n > P/2) for the registers of this lane.
+template <int P>
+__device__ __forceinline__ void load_pair_spectrum(float2 (&v)[P / 32], const float2* a, const float2* b,
+                                                   int lane) {
+  constexpr int R = P / 32;
+#pragma unroll
+  for (int i = 0; i < R; ++i) {
+    const int n = lane + 32 * i;
+    float2 A, B;
+    if (n <= P / 2) {
+      A = a[n];
+      B = b[n];
+    } else {
+      A = cconj(a[P - n]);
+      B = cconj(b[P - n]);
+    }
+    v[i] = make_float2(A.x - B.y, A.y + B.x);
+  }
+}
+
+// ---------------------------------------------------------------- rows ----
+
+template <int P>
+__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_fwd(const float* __restrict__ in, int total_rows,
+                                                             int cols_in, int ld_in, float2* __restrict__ inter,
+                                                             int hp, const float2* __restrict__ tw) {
+  constexpr int R = P / 32;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* buf = smem + P + warp * (P + 2);
+  stage_twiddles<P>(s_tw, tw);
+  __syncthreads();
+  const int npairs = (total_rows + 1) >> 1;
+  for (int pair = blockIdx.x * ROW_WARPS + warp; pair < npairs; pair += gridDim.x * ROW_WARPS) {
+    const int g0 = 2 * pair, g1 = g0 + 1;
+    const bool has1 = g1 < total_rows;
+    const float* r0 = in + (size_t)g0 * ld_in;
+    const float* r1 = in + (size_t)g1 * ld_in;
+    float2 v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int n = lane + 32 * i;
+      const float a = n < cols_in ? r0[n] : 0.f;
+      const float b = (has1 && n < cols_in) ? r1[n] : 0.f;
+      v[i] = make_float2(a, b);
+    }
+    warp_fft<P, false>(v, lane, s_tw);
+#pragma unroll
+    for (int i = 0; i < R; ++i) buf[out_pos<P>(lane, i)] = v[i];
+    __syncwarp();
+    split_write<P>(buf, lane, inter + (size_t)g0 * hp, has1 ? inter + (size_t)g1 * hp : nullptr);
+    __syncwarp();
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const float2* __restrict__ inter, int total_rows,
+                                                             int hp, int cols_out, float* __restrict__ out,
+                                                             int ld_out, float scale,
+                                                             const float2* __restrict__ tw) {
+  constexpr int R = P / 32;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* buf = smem + P + warp * (P + 2);
+  stage_twiddles<P>(s_tw, tw);
+  __syncthreads();
+  const int npairs = (total_rows + 1) >> 1;
+  for (int pair = blockIdx.x * ROW_WARPS + warp; pair < npairs; pair += gridDim.x * ROW_WARPS) {
+    const int g0 = 2 * pair, g1 = g0 + 1;
+    const bool has1 = g1 < total_rows;
+    float2* ba = buf;
+    float2* bb = buf + (P / 2 + 1);
+    for (int kk = lane; kk <= P / 2; kk += 32) {
+      ba[kk] = inter[(size_t)g0 * hp + kk];
+      bb[kk] = has1 ? inter[(size_t)g1 * hp + kk] : make_float2(0.f, 0.f);
+    }
+    __syncwarp();
+    float2 v[R];
+    load_pair_spectrum<P>(v, ba, bb, lane);
+    __syncwarp();
+    warp_fft<P, true>(v, lane, s_tw);
+#pragma unroll
+    for (int i = 0; i < R; ++i) buf[out_pos<P>(lane, i)] = v[i];
+    __syncwarp();
+    for (int c = lane; c < cols_out; c += 32) {
+      const float2 z = buf[c];
+      out[(size_t)g0 * ld_out + c] = z.x * scale;
+      if (has1) out[(size_t)g1 * ld_out + c] = z.y * scale;
+    }
+    __syncwarp();
+  }
+}
+
+// ADMM T side, per pair of measurement rows (time bin t, scan row y):
+//   Kx   = C2R(row spectra) on the N scan columns
+//   a1   = Kx + u1;  v1 = (m/scale + rho a1) / (1 + rho);  u1 <- a1 - v1
+//   c    = (v1 - u1) - Kx = 2 v1 - a1 - Kx      (zero off the scan)
+//   row spectra <- R2C(c zero-padded to P)
+// so that FFT(v1 - u1) = K x_hat + c_hat without a transform of the full
+// P x P plane.
+template <int P>
+__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restrict__ inter, int total_rows,
+                                                                int hp, int n, const float* __restrict__ m,
+                                                                float* __restrict__ u1, float scale,
+                                                                float inv_s, float rho,
+                                                                const float2* __restrict__ tw) {
+  constexpr int R = P / 32;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  float2* buf = smem + P + warp * (P + 2);
+  stage_twiddles<P>(s_tw, tw);
+  __syncthreads();
+  const float inv1r = 1.0f / (1.0f + rho);
+  const int npairs = (total_rows + 1) >> 1;
+  for (int pair = blockIdx.x * ROW_WARPS + warp; pair < npairs; pair += gridDim.x * ROW_WARPS) {
+    const int g0 = 2 * pair, g1 = g0 + 1;
+    const bool has1 = g1 < total_rows;
+    float2* ba = buf;
+    float2* bb = buf + (P / 2 + 1);
+    for (int kk = lane; kk <= P / 2; kk += 32) {
+      ba[kk] = inter[(size_t)g0 * hp + kk];
+      bb[kk] = has1 ? inter[(size_t)g1 * hp + kk] : make_float2(0.f, 0.f);
+    }
+    __syncwarp();
+    float2 v[R];
+    load_pair_spectrum<P>(v, ba, bb, lane);
+    __syncwarp();
+    warp_fft<P, true>(v, lane, s_tw);
+#pragma unroll
+    for (int i = 0; i < R; ++i) buf[out_pos<P>(lane, i)] = v[i];
+    __syncwarp();
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int c = lane + 32 * i;
+      float2 cc = make_float2(0.f, 0.f);
+      if (c < n) {
+        const float2 kx = cscale(buf[c], scale);
+        {
+          const size_t idx = (size_t)g0 * n + c;
+          const float a1 = kx.x + u1[idx];
+          const float v1 = (m[idx] * inv_s + rho * a1) * inv1r;
+          u1[idx] = a1 - v1;
+          cc.x = 2.f * v1 - a1 - kx.x;
+        }
+        if (has1) {
+          const size_t idx = (size_t)g1 * n + c;
+          const float a1 = kx.y + u1[idx];
+          const float v1 = (m[idx] * inv_s + rho * a1) * inv1r;
+          u1[idx] = a1 - v1;
+          cc.y = 2.f * v1 - a1 - kx.y;
+        }
+      }
+      v[i] = cc;
+    }
+    __syncwarp();
+    warp_fft<P, false>(v, lane, s_tw);
+#pragma unroll
+    for (int i = 0; i < R; ++i) buf[out_pos<P>(lane, i)] = v[i];
+    __syncwarp();
+    split_write<P>(buf, lane, inter + (size_t)g0 * hp, has1 ? inter + (size_t)g1 * hp : nullptr);
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------- columns ----
+
+template <int P>
+__global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restrict__ inter, int nplanes,
+                                                          int rows_in, int h, int hp,
+                                                          float2* __restrict__ out, int ldf,
+                                                          const float2* __restrict__ tw) {
+  constexpr int R = P / 32;
+  constexpr int LDT = NC + 1;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  float2* tile = smem + P;
+  const int kx0 = blockIdx.x * KB, pl0 = blockIdx.y * PB;
+  stage_twiddles<P>(s_tw, tw);
+  for (int idx = threadIdx.x; idx < rows_in * NC; idx += COL_THREADS) {
+    const int row = idx / NC, cc = idx % NC;
+    const int kxl = cc % KB, pll = cc / KB;
+    const int kx = kx0 + kxl, pl = pl0 + pll;
+    float2 val = make_float2(0.f, 0.f);
+    if (kx < h && pl < nplanes) val = inter[((size_t)pl * rows_in + row) * hp + kx];
+    tile[row * LDT + kxl * PB + pll] = val;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = warp; c < NC; c += COL_THREADS / 32) {
+    float2 v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int y = lane + 32 * i;
+      v[i] = y < rows_in ? tile[y * LDT + c] : make_float2(0.f, 0.f);
+    }
+    warp_fft<P, false>(v, lane, s_tw);
+#pragma unroll
+    for (int i = 0; i < R; ++i) tile[out_pos<P>(lane, i) * LDT + c] = v[i];
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
+    const int ky = idx / NC, cc = idx % NC;
+    const int pll = cc % PB, kxl = cc / PB;
+    const int kx = kx0 + kxl, pl = pl0 + pll;
+    if (kx < h && pl < nplanes) out[((size_t)ky * h + kx) * ldf + pl] = tile[ky * LDT + cc];
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restrict__ in, int ldf, int nplanes,
+                                                          int rows_out, int h, int hp,
+                                                          float2* __restrict__ inter,
+                                                          const float2* __restrict__ tw) {
+  constexpr int R = P / 32;
+  constexpr int LDT = NC + 1;
+  extern __shared__ float2 smem[];
+  float2* s_tw = smem;
+  float2* tile = smem + P;
+  const int kx0 = blockIdx.x * KB, pl0 = blockIdx.y * PB;
+  stage_twiddles<P>(s_tw, tw);
+  for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
+    const int ky = idx / NC, cc = idx % NC;
+    const int pll = cc % PB, kxl = cc / PB;
+    const int kx = kx0 + kxl, pl = pl0 + pll;
+    float2 val = make_float2(0.f, 0.f);
+    if (kx < h && pl < nplanes) val = in[((size_t)ky * h + kx) * ldf + pl];
+    tile[ky * LDT + cc] = val;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int c = warp; c < NC; c += COL_THREADS / 32) {
+    float2 v[R];
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = tile[(lane + 32 * i) * LDT + c];
+    warp_fft<P, true>(v, lane, s_tw);
+#pragma unroll
+    for (int i = 0; i < R; ++i) {
+      const int y = out_pos<P>(lane, i);
+      if (y < rows_out) tile[y * LDT + c] = v[i];
+    }
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < rows_out * NC; idx += COL_THREADS) {
+    const int row = idx / NC, cc = idx % NC;
+    const int kxl = cc % KB, pll = cc / KB;
+    const int kx = kx0 + kxl, pl = pl0 + pll;
+    if (kx < h && pl < nplanes) inter[((size_t)pl * rows_out + row) * hp + kx] = tile[row * LDT + kxl * PB + pll];
+  }
+}
+
+// ------------------------------------------------------------ launchers ----
+
+size_t row_smem(int p) { return (size_t)(p + ROW_WARPS * (p + 2)) * sizeof(float2); }
+size_t col_smem(int p) { return (size_t)(p + p * (NC + 1)) * sizeof(float2); }
+
+template <typename F>
+cudaError_t allow_smem(F* fn, size_t bytes) {
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+int row_grid(int total_rows) {
+  const int npairs = (total_rows + 1) / 2;
+  int g = (npairs + ROW_WARPS - 1) / ROW_WARPS;
+  const int cap = 152 * 8;
+  return g < 1 ? 1 : (g > cap ? cap : g);
+}
+
+#define CTOF_P_SWITCH(p, ...)                                    \
+  switch (p) {                                                   \
+    case 32: { constexpr int P_ = 32; __VA_ARGS__; } break;      \
+    case 64: { constexpr int P_ = 64; __VA_ARGS__; } break;      \
+    case 128: { constexpr int P_ = 128; __VA_ARGS__; } break;    \
+    case 256: { constexpr int P_ = 256; __VA_ARGS__; } break;    \
+    case 512: { constexpr int P_ = 512; __VA_ARGS__; } break;    \
+    default: return CTOF_EUNSUPPORTED;                           \
+  }
+}  // namespace
+
+ctof_status fft_rows_forward(const ctof_kernel_s* k, const float* in, int nplanes, int rows, int cols_in,
+                             int ld_in, float2* inter, cudaStream_t st) {
+  const int total = nplanes * rows;
+  if (total <= 0) return CTOF_OK;
+  const size_t sm = row_smem(k->p);
+  CTOF_P_SWITCH(k->p, {
+    CTOF_CUDA_TRY(allow_smem(k_rows_fwd<P_>, sm));
+    k_rows_fwd<P_><<<row_grid(total), ROW_WARPS * 32, sm, st>>>(in, total, cols_in, ld_in, inter, k->hp, k->d_tw);
+  });
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status fft_rows_inverse(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows, int cols_out,
+                             float* out, int ld_out, cudaStream_t st) {
+  const int total = nplanes * rows;
+  if (total <= 0) return CTOF_OK;
+  const size_t sm = row_smem(k->p);
+  const float scale = 1.0f / ((float)k->p * (float)k->p);
+  CTOF_P_SWITCH(k->p, {
+    CTOF_CUDA_TRY(allow_smem(k_rows_inv<P_>, sm));
+    k_rows_inv<P_><<<row_grid(total), ROW_WARPS * 32, sm, st>>>(inter, total, k->hp, cols_out, out, ld_out, scale,
+                                                                 k->d_tw);
+  });
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* m, float* u1, float inv_scale,
+                            float rho, cudaStream_t st) {
+  const int total = k->nt * k->n;
+  const size_t sm = row_smem(k->p);
+  const float scale = 1.0f / ((float)k->p * (float)k->p);
+  CTOF_P_SWITCH(k->p, {
+    CTOF_CUDA_TRY(allow_smem(k_rows_admm_t<P_>, sm));
+    k_rows_admm_t<P_><<<row_grid(total), ROW_WARPS * 32, sm, st>>>(inter, total, k->hp, k->n, m, u1, scale,
+                                                                    inv_scale, rho, k->d_tw);
+  });
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status fft_cols_forward(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows_in, float2* out,
+                             int ldf, cudaStream_t st) {
+  if (nplanes <= 0) return CTOF_OK;
+  const size_t sm = col_smem(k->p);
+  dim3 grid(ctof_div_up(k->h, KB), ctof_div_up(nplanes, PB));
+  CTOF_P_SWITCH(k->p, {
+    CTOF_CUDA_TRY(allow_smem(k_cols_fwd<P_>, sm));
+    k_cols_fwd<P_><<<grid, COL_THREADS, sm, st>>>(inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
+  });
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status fft_cols_inverse(const ctof_kernel_s* k, const float2* in, int ldf, int nplanes, int rows_out,
+                             float2* inter, cudaStream_t st) {
+  if (nplanes <= 0) return CTOF_OK;
+  const size_t sm = col_smem(k->p);
+  dim3 grid(ctof_div_up(k->h, KB), ctof_div_up(nplanes, PB));
+  CTOF_P_SWITCH(k->p, {
+    CTOF_CUDA_TRY(allow_smem(k_cols_inv<P_>, sm));
+    k_cols_inv<P_><<<grid, COL_THREADS, sm, st>>>(in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
+  });
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status fft_forward_planes(const ctof_kernel_s* k, const float* in, int nplanes, int rows_in, int cols_in,
+                               int ld_in, float2* inter, float2* out, int ldf, cudaStream_t st) {
+  CTOF_TRY(fft_rows_forward(k, in, nplanes, rows_in, cols_in, ld_in, inter, st));
+  return fft_cols_forward(k, inter, nplanes, rows_in, out, ldf, st);
+}
+
+ctof_status fft_inverse_planes(const ctof_kernel_s* k, const float2* in, int ldf, int nplanes, int rows_out,
+                               int cols_out, float2* inter, float* out, int ld_out, cudaStream_t st) {
+  CTOF_TRY(fft_cols_inverse(k, in, ldf, nplanes, rows_out, inter, st));
+  return fft_rows_inverse(k, inter, nplanes, rows_out, cols_out, out, ld_out, st);
+}

@@ -1,0 +1,231 @@
+"""Python binding of the ctof C ABI (``include/ctof.h``).
+
+Argument marshalling only: every step of the computation runs inside
+``libctof.so``.  PyTorch supplies device memory and streams; tensors are passed
+by ``data_ptr()`` and streams by their ``cuda_stream`` handle.  There is no
+CPU fallback: if the library is missing, ``load()`` raises.
+"""
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libctof.so")
+
+OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
+LINEAR, CIRCULAR = 0, 1
+SOLVER_ADMM_TV, SOLVER_TIKHONOV = 0, 1
+KEEP_W = 1
+
+
+class Optics(ctypes.Structure):
+    _fields_ = [("mua_mm", ctypes.c_double), ("musp_mm", ctypes.c_double), ("n", ctypes.c_double),
+                ("z0_mm", ctypes.c_double), ("clamp_r", ctypes.c_int)]
+
+
+class GridSpec(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("nt", ctypes.c_int),
+                ("dx_mm", ctypes.c_double), ("dy_mm", ctypes.c_double), ("dz_mm", ctypes.c_double),
+                ("z_first_mm", ctypes.c_double), ("dt_ps", ctypes.c_double), ("conv_mode", ctypes.c_int)]
+
+
+class KernelInfo(ctypes.Structure):
+    _fields_ = [("p", ctypes.c_int), ("n_freq", ctypes.c_int), ("n_class", ctypes.c_int), ("nt", ctypes.c_int),
+                ("nz", ctypes.c_int), ("scale", ctypes.c_double), ("gram_max_diag", ctypes.c_double),
+                ("device_bytes", ctypes.c_size_t)]
+
+
+class SolverParams(ctypes.Structure):
+    _fields_ = [("solver", ctypes.c_int), ("iters", ctypes.c_int), ("rho", ctypes.c_double),
+                ("tv_beta", ctypes.c_double), ("beta_rel", ctypes.c_double), ("tik_lambda_rel", ctypes.c_double)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("scale", ctypes.c_double), ("beta", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("iters_done", ctypes.c_int)]
+
+
+class CtofError(RuntimeError):
+    def __init__(self, status, where):
+        lib = load()
+        msg = lib.ctof_status_string(status).decode()
+        detail = lib.ctof_last_error_message().decode()
+        super().__init__(f"{where}: {msg} ({status}){': ' + detail if detail else ''}")
+        self.status = status
+
+
+_lib = None
+
+_P = ctypes.c_void_p
+_SIGNATURES = {
+    "ctof_build_kernel": (ctypes.c_int, [ctypes.POINTER(Optics), ctypes.POINTER(GridSpec), ctypes.c_int, _P,
+                                         ctypes.POINTER(_P)]),
+    "ctof_kernel_destroy": (None, [_P]),
+    "ctof_kernel_get_info": (ctypes.c_int, [_P, ctypes.POINTER(KernelInfo)]),
+    "ctof_kernel_get_w": (ctypes.c_int, [_P, _P]),
+    "ctof_kernel_get_classes": (ctypes.c_int, [_P, _P]),
+    "ctof_kernel_get_what": (ctypes.c_int, [_P, _P]),
+    "ctof_forward": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ctof_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ctof_reconstruct": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolverParams), _P, ctypes.POINTER(Report), _P]),
+    "ctof_reconstruct_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolverParams), _P, ctypes.POINTER(Report),
+                                             _P]),
+    "ctof_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "ctof_last_error_message": (ctypes.c_char_p, []),
+}
+
+
+def load():
+    """Load libctof.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"{LIB_PATH} is missing: build it with paper_2101_11680_gb300.build.build()")
+        lib = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in _SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+def _check(status, where):
+    if status != OK:
+        raise CtofError(status, where)
+
+
+def _stream_handle(stream):
+    import torch
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def _dev_ptr(t, shape, name):
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous float32 CUDA tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def make_optics(mua=0.01, musp=1.0, n=1.4, z0=0.0, clamp_r=True):
+    return Optics(float(mua), float(musp), float(n), float(z0), int(bool(clamp_r)))
+
+
+def make_grid(n, nz, nt, dx, dz, z_first, dt, dy=None, mode="linear"):
+    return GridSpec(int(n), int(n), int(nz), int(nt), float(dx), float(dx if dy is None else dy), float(dz),
+                    float(z_first), float(dt), LINEAR if mode == "linear" else CIRCULAR)
+
+
+def admm_params(iters=100, rho=1.0, tv_beta=-1.0, beta_rel=1e-3):
+    return SolverParams(SOLVER_ADMM_TV, int(iters), float(rho), float(tv_beta), float(beta_rel), 1e-3)
+
+
+def tikhonov_params(lambda_rel=1e-3):
+    return SolverParams(SOLVER_TIKHONOV, 1, 1.0, -1.0, 1e-3, float(lambda_rel))
+
+
+class Kernel:
+    """A built sensitivity kernel (``ctof_kernel``) bound to the current CUDA device."""
+
+    def __init__(self, optics, grid, keep_w=False, stream=None):
+        lib = load()
+        self._lib = lib
+        self.optics = optics
+        self.grid = grid
+        h = ctypes.c_void_p()
+        _check(lib.ctof_build_kernel(ctypes.byref(optics), ctypes.byref(grid), KEEP_W if keep_w else 0,
+                                     _stream_handle(stream), ctypes.byref(h)), "ctof_build_kernel")
+        self._h = h
+        info = KernelInfo()
+        _check(lib.ctof_kernel_get_info(h, ctypes.byref(info)), "ctof_kernel_get_info")
+        self.info = info
+
+    @property
+    def n(self):
+        return self.grid.nx
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.ctof_kernel_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # ---- parity accessors (synchronous) ----
+    def get_w(self):
+        import numpy as np
+        q = self.grid.nx if self.grid.conv_mode == LINEAR else self.info.p // 2 + 1
+        out = np.empty((self.grid.nt, self.grid.nz, q, q), dtype=np.float64)
+        _check(self._lib.ctof_kernel_get_w(self._h, out.ctypes.data_as(ctypes.c_void_p)), "ctof_kernel_get_w")
+        return out
+
+    def get_classes(self):
+        import numpy as np
+        out = np.empty((self.info.n_class, 4), dtype=np.int32)
+        _check(self._lib.ctof_kernel_get_classes(self._h, out.ctypes.data_as(ctypes.c_void_p)),
+               "ctof_kernel_get_classes")
+        return out
+
+    def get_what(self):
+        import numpy as np
+        out = np.empty((self.info.n_class, self.grid.nt, self.grid.nz), dtype=np.float32)
+        _check(self._lib.ctof_kernel_get_what(self._h, out.ctypes.data_as(ctypes.c_void_p)),
+               "ctof_kernel_get_what")
+        return out
+
+    # ---- operators ----
+    def _vol_shape(self):
+        return (self.grid.nz, self.grid.ny, self.grid.nx)
+
+    def _meas_shape(self):
+        return (self.grid.nt, self.grid.ny, self.grid.nx)
+
+    def forward(self, mu, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self._meas_shape(), device=mu.device, dtype=torch.float32)
+        _check(self._lib.ctof_forward(self._h, _dev_ptr(mu, self._vol_shape(), "mu"),
+                                      _dev_ptr(out, self._meas_shape(), "out"), _stream_handle(stream)),
+               "ctof_forward")
+        return out
+
+    def adjoint(self, m, out=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self._vol_shape(), device=m.device, dtype=torch.float32)
+        _check(self._lib.ctof_adjoint(self._h, _dev_ptr(m, self._meas_shape(), "m"),
+                                      _dev_ptr(out, self._vol_shape(), "out"), _stream_handle(stream)),
+               "ctof_adjoint")
+        return out
+
+    def reconstruct(self, m, params, out=None, report=False, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(self._vol_shape(), device=m.device, dtype=torch.float32)
+        rep = Report()
+        _check(self._lib.ctof_reconstruct(self._h, _dev_ptr(m, self._meas_shape(), "m"), ctypes.byref(params),
+                                          _dev_ptr(out, self._vol_shape(), "out"),
+                                          ctypes.byref(rep) if report else None, _stream_handle(stream)),
+               "ctof_reconstruct")
+        return (out, rep) if report else out
+
+    def reconstruct_host(self, m_host, params, out_host, report=False, stream=None):
+        """Host-buffer variant: m_host / out_host are CPU float32 tensors (pinned for speed)."""
+        import torch
+        for t, shp, nm in ((m_host, self._meas_shape(), "m_host"), (out_host, self._vol_shape(), "out_host")):
+            if t.is_cuda or t.dtype != torch.float32 or not t.is_contiguous() or tuple(t.shape) != shp:
+                raise TypeError(f"{nm} must be a contiguous float32 CPU tensor of shape {shp}")
+        rep = Report()
+        _check(self._lib.ctof_reconstruct_host(self._h, ctypes.c_void_p(m_host.data_ptr()), ctypes.byref(params),
+                                               ctypes.c_void_p(out_host.data_ptr()),
+                                               ctypes.byref(rep) if report else None, _stream_handle(stream)),
+               "ctof_reconstruct_host")
+        return (out_host, rep) if report else out_host

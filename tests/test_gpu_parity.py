@@ -1,0 +1,142 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerances: the kernel table is FP64 on both sides (1e-12 of its maximum);
+W_hat is stored FP32 (1e-6 of its maximum: one rounding of an FP64 value);
+the FP32 operators and solvers must agree to rel-L2 <= 1e-5, the bound the
+FP32 path is held to.
+"""
+
+import numpy as np
+import pytest
+
+from gpu_common import CASES, device_kernel, medium, oracle_kernel, rel_l2
+from oracle import operators as op
+from oracle import solvers as so
+from paper_2101_11680_gb300 import ctof, synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+ALL = ["sub", "cfg1", "ragged", "aniso", "circ"]
+
+
+@pytest.mark.parametrize("name", ALL)
+def test_kernel_table_fp64(name):
+    g, w, _ = oracle_kernel(name)
+    k = device_kernel(name)
+    wd = k.get_w()
+    n = g.n
+    if g.mode == "linear":
+        want = w[:, :, n - 1:, n - 1:]
+    else:
+        q = g.p // 2 + 1
+        want = w[:, :, n - 1:n - 1 + q, n - 1:n - 1 + q]
+    assert wd.shape == want.shape
+    assert np.abs(wd - want).max() <= 1e-12 * np.abs(want).max()
+    big = np.abs(want) > 1e-20 * np.abs(want).max()
+    assert np.all(np.abs(wd[big] - want[big]) <= 1e-10 * np.abs(want[big]))
+
+
+@pytest.mark.parametrize("name", ALL)
+def test_kernel_spectrum_classes(name):
+    g, _, wh = oracle_kernel(name)
+    k = device_kernel(name)
+    mem = k.get_classes()
+    what = k.get_what()
+    p, h = k.info.p, k.info.p // 2 + 1
+    assert p == g.p
+    seen = np.zeros(p * h, dtype=int)
+    scale = np.abs(wh).max()
+    for c in range(mem.shape[0]):
+        for f in mem[c]:
+            if f < 0:
+                continue
+            seen[f] += 1
+            ky, kx = divmod(int(f), h)
+            ref = wh[:, :, ky, kx]
+            assert np.abs(ref.imag).max() <= 1e-14 * scale
+            assert np.abs(what[c] - ref.real).max() <= 1e-6 * scale
+    assert np.all(seen == 1)  # every half-plane frequency in exactly one class
+    assert k.info.scale == pytest.approx(so.spectral_norm(wh), rel=1e-10)
+
+
+def _rand_vol(g, seed):
+    rng = np.random.default_rng(seed)
+    v = rng.uniform(0.0, 0.02, (g.nz, g.n, g.n))
+    return v * (rng.uniform(size=v.shape) < 0.3)
+
+
+@pytest.mark.parametrize("name", ALL)
+def test_forward_adjoint(name):
+    g, _, wh = oracle_kernel(name)
+    k = device_kernel(name)
+    mu = _rand_vol(g, 1)
+    want = op.forward_fft(wh, mu, g)
+    got = k.forward(torch.tensor(mu, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert rel_l2(got, want) <= 1e-5
+    assert np.abs(got - want).max() <= 1e-5 * np.abs(want).max()
+    rng = np.random.default_rng(2)
+    m = rng.standard_normal((g.nt, g.n, g.n)) * np.abs(want).max()
+    want_a = op.adjoint_fft(wh, m, g)
+    got_a = k.adjoint(torch.tensor(m, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert rel_l2(got_a, want_a) <= 1e-5
+
+
+@pytest.mark.parametrize("name", ["sub", "cfg1", "ragged"])
+def test_adjoint_identity_device(name):
+    g, _, _ = oracle_kernel(name)
+    k = device_kernel(name)
+    gen = torch.Generator(device="cuda").manual_seed(7)
+    x = torch.rand((g.nz, g.n, g.n), device="cuda", generator=gen)
+    y = torch.randn((g.nt, g.n, g.n), device="cuda", generator=gen)
+    ax = k.forward(x)
+    aty = k.adjoint(y)
+    lhs = float((ax.double() * y.double()).sum())
+    rhs = float((x.double() * aty.double()).sum())
+    assert abs(lhs - rhs) <= 1e-5 * float(ax.double().norm()) * float(y.double().norm())
+
+
+def _measurement(name, seed=0, peak=1e4):
+    g, _, wh = oracle_kernel(name)
+    if name == "cfg1":
+        mu = synth.phantom_spheres(g.n, g.nz, g.dx, g.dz, g.z_first, seed=seed)
+    else:
+        mu = synth.phantom_shapes(g.n, g.nz, g.dx, g.dz, g.z_first, seed=seed)
+    m = op.forward_fft(wh, mu, g)
+    return g, wh, mu, synth.poisson_noise(np.clip(m, 0, None), peak, seed + 100)
+
+
+@pytest.mark.parametrize("name", ["cfg1", "ragged", "circ"])
+def test_tikhonov(name):
+    g, wh, _, m = _measurement(name)
+    want, lam, _ = so.tikhonov(wh, m, g)
+    k = device_kernel(name)
+    got, rep = k.reconstruct(torch.tensor(m, dtype=torch.float32, device="cuda"), ctof.tikhonov_params(),
+                             report=True)
+    assert rep.lambda_ == pytest.approx(lam, rel=1e-10)
+    assert rel_l2(got.cpu().numpy(), want) <= 1e-5
+
+
+@pytest.mark.parametrize("name,iters", [("admm16", 100), ("ragged", 60), ("circ", 40)])
+def test_admm(name, iters):
+    g, wh, _, m = _measurement(name, seed=3, peak=1e5)
+    want, info = so.admm(wh, m, g, iters)
+    k = device_kernel(name)
+    got, rep = k.reconstruct(torch.tensor(m, dtype=torch.float32, device="cuda"), ctof.admm_params(iters=iters),
+                             report=True)
+    assert rep.beta == pytest.approx(info["beta"], rel=1e-5)
+    assert rel_l2(got.cpu().numpy(), want) <= 1e-5
+    # the handle's captured graph replays to the same result
+    got2 = k.reconstruct(torch.tensor(m, dtype=torch.float32, device="cuda"), ctof.admm_params(iters=iters))
+    assert torch.equal(got, got2)
+
+
+def test_reconstruct_host_buffers():
+    g, wh, _, m = _measurement("admm16", seed=4, peak=1e5)
+    k = device_kernel("admm16")
+    p = ctof.admm_params(iters=20)
+    dev = k.reconstruct(torch.tensor(m, dtype=torch.float32, device="cuda"), p).cpu()
+    mh = torch.tensor(m, dtype=torch.float32).pin_memory()
+    out = torch.empty((g.nz, g.n, g.n), dtype=torch.float32).pin_memory()
+    k.reconstruct_host(mh, p, out)
+    assert torch.equal(out, dev)
