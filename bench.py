@@ -1,0 +1,372 @@
+"""Benchmark: FP32 ADMM reconstructions of confocal ToF-DOT volumes on the GPU.
+
+Workload (default, "cfg2"): 128 x 128 confocal scan at 0.5 mm pitch,
+128 x 128 x 48 voxels of 0.5 mm (depths 0.5-24 mm), 256 time bins of 25 ps,
+optics mua = 0.01/mm, musp' = 1.0/mm, n = 1.4 (extrapolated boundary), seeded
+phantoms of 1-8 random ellipsoids/tubes (dmua U[0.005, 0.02]/mm), Poisson
+noise at a peak of 1e5 counts, 100 ADMM iterations (nonnegativity +
+anisotropic 3-D TV, rho = 1).  One step = one full reconstruction of one
+measurement volume through the C ABI; the sensitivity kernel is built once
+before timing (a one-time process).
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Prints one JSON line (rank 0).
+"""
+
+import argparse
+import json
+import os
+import resource
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "volumes/sec at 128x128x48 (256 bins) vs plain FP32 ADMM at equal error; %roofline"
+UNIT = "volumes/s"
+
+CONFIGS = {
+    "cfg2": dict(n=128, nz=48, nt=256, dx=0.5, dz=0.5, z_first=0.5, dt=25.0, iters=100, peak=1e5,
+                 workload="128x128 scan @0.5 mm, 128x128x48 voxels (0.5 mm, depths 0.5-24 mm), 256 bins x 25 ps, "
+                          "1-8 random ellipsoids/tubes, Poisson peak 1e5, 100 ADMM iterations (nonneg + 3D TV, rho=1), "
+                          "FP32"),
+    "cfg1": dict(n=32, nz=16, nt=64, dx=1.0, dz=1.0, z_first=1.0, dt=50.0, iters=100, peak=1e4,
+                 workload="32x32 scan @1 mm, 32x32x16 voxels (1-16 mm), 64 bins x 50 ps, 100 ADMM iterations"),
+}
+OPTICS = dict(mua=0.01, musp=1.0, n=1.4)
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    except Exception:
+        return 6800.0, "fallback (6.8 TB/s)"
+
+
+class ClockSampler:
+    """Samples nvidia-smi clocks/throttle reasons every 200 ms in the background."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index):
+        self.dev = device_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.dev), f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": float(np.median(sm)), "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def make_inputs(kern, cfg, count, seed0, torch):
+    """Seeded phantoms -> measurements (device forward model + host Poisson noise)."""
+    from paper_2101_11680_gb300 import synth
+    ms, mus = [], []
+    for i in range(count):
+        mu = synth.phantom_shapes(cfg["n"], cfg["nz"], cfg["dx"], cfg["dz"], cfg["z_first"], seed=seed0 + i)
+        mu_d = torch.tensor(mu, dtype=torch.float32, device="cuda")
+        clean = kern.forward(mu_d).double().clamp_(min=0).cpu().numpy()
+        noisy = synth.poisson_noise(clean, cfg["peak"], seed=seed0 + 10_000 + i)
+        ms.append(torch.tensor(noisy, dtype=torch.float32, device="cuda"))
+        mus.append(mu_d)
+    return ms, mus
+
+
+def contract_bytes(info, nz, nt):
+    """Algorithmic DRAM bytes of one ADMM x-update contraction launch.
+
+    Per frequency class: W_hat (nt x nz FP32) and H^-1 (nz x nz FP32) read once.
+    Per half-plane frequency: c_hat (nt complex64) and s_hat (nz) read, x_hat
+    (nz) read and written, K x_hat (nt) written.
+    """
+    per_class = nt * nz * 4 + nz * nz * 4 + 4 + 16
+    per_freq = (2 * nt + 3 * nz) * 8
+    return info.n_class * per_class + info.n_freq * per_freq
+
+
+class OracleSample:
+    """The FP64 oracle's ADMM timed on a bounded lateral sample of the workload.
+
+    Sample: the same depths (nz), bins (nt), pitches and optics on a 32 x 32
+    scan (P = 64 lateral FFT grid, 1/16 of the 256 x 256 grid of the 128 x 128
+    workload).  The oracle's kernel table for the sample is built with a
+    1-point bin rule (construction is a one-time step outside the timed
+    reconstruction; the ADMM arithmetic does not depend on it).  Timed: the
+    beta rule (one adjoint) and individual ADMM iterations, wall clock.  Scaled
+    to one full volume: (beta + iters x iteration) x (P_full / 64)^2, i.e.
+    linear in the number of lateral frequencies, which slightly favours the
+    CPU (the FFT part grows as P^2 log P).
+    """
+
+    NS = 32
+
+    def __init__(self, cfg):
+        from oracle import operators as op
+        from oracle import physics as ph
+        from oracle import solvers as so
+        self.cfg = cfg
+        self.op, self.so = op, so
+        self.g = op.Grid(self.NS, cfg["nz"], cfg["nt"], cfg["dx"], cfg["dz"], cfg["z_first"], cfg["dt"])
+        med = ph.Medium(OPTICS["mua"], OPTICS["musp"], OPTICS["n"], r_min=0.5 * min(cfg["dx"], cfg["dz"]))
+        self.wh = op.kernel_spectrum(op.kernel_offsets(self.g, med, nodes=1, sub=1), self.g)
+        rng = np.random.default_rng(0)
+        shape = (cfg["nz"], self.NS, self.NS)
+        mu = rng.uniform(0, 0.02, shape) * (rng.uniform(size=shape) < 0.1)
+        self.m = op.forward_fft(self.wh, mu, self.g)
+        self.wn = self.wh / so.spectral_norm(self.wh)  # normalised kernel (one-time setup)
+        p_full = 32
+        while p_full < 2 * cfg["n"]:
+            p_full *= 2
+        self.scale = (p_full / self.g.p) ** 2
+
+    def run(self, iters):
+        """Run `iters` oracle ADMM iterations; returns (seconds per full volume per sample, cores)."""
+        stamps = []
+        ru0 = resource.getrusage(resource.RUSAGE_SELF)
+        w0 = time.perf_counter()
+        self.so.admm(self.wh, self.m, self.g, iters, callback=lambda i: stamps.append(time.perf_counter()))
+        t_adj = time.perf_counter()
+        self.op.adjoint_fft(self.wn, self.m, self.g)
+        t_beta = time.perf_counter() - t_adj
+        ru1 = resource.getrusage(resource.RUSAGE_SELF)
+        wall = time.perf_counter() - w0
+        cpu = (ru1.ru_utime + ru1.ru_stime) - (ru0.ru_utime + ru0.ru_stime)
+        cores = max(1, int(round(cpu / max(wall, 1e-9))))
+        per_iter = np.diff(np.array(stamps))
+        vols = [self.scale * (t_beta + self.cfg["iters"] * d) for d in per_iter]
+        return vols, cores, t_beta
+
+    def describe(self, per_iter, t_beta):
+        c = self.cfg
+        return (f"FP64 NumPy oracle ADMM on a {self.NS}x{self.NS} lateral sample (P={self.g.p}) at nz={c['nz']}, "
+                f"nt={c['nt']}: {per_iter:.3f} s/iteration, beta rule {t_beta:.3f} s, scaled by "
+                f"{self.scale:.0f}x lateral frequencies to {c['iters']} iterations of one full volume; "
+                f"host nproc={os.cpu_count()}")
+
+
+def cpu_baseline(cfg):
+    s = OracleSample(cfg)
+    vols, cores, t_beta = s.run(5)
+    sec = float(np.mean(vols))
+    per_iter = (sec / s.scale - t_beta) / cfg["iters"]
+    return {"value": 1.0 / sec, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": s.describe(per_iter, t_beta)}
+
+
+def run_reference(args, cfg, rank):
+    """The oracle arm: each step is one timed oracle ADMM iteration on the sample, scaled to a volume."""
+    if rank != 0:
+        return
+    s = OracleSample(cfg)
+    vols, cores, t_beta = s.run(args.warmup + args.steps + 1)
+    timed = vols[args.warmup:args.warmup + args.steps]
+    sec = float(np.mean(timed))
+    val = 1.0 / sec
+    per_iter = (sec / s.scale - t_beta) / cfg["iters"]
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": cfg["workload"], "n": cfg["n"], "nz": cfg["nz"], "nt": cfg["nt"],
+                       "iters": cfg["iters"]},
+            "cpu_baseline": {"kind": "oracle", "cores": cores, "sample": s.describe(per_iter, t_beta),
+                             "value": val, "unit": UNIT},
+            "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="cfg2", choices=sorted(CONFIGS))
+    ap.add_argument("--iters", type=int, default=None)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--seed", type=int, default=1000)
+    args = ap.parse_args()
+    cfg = dict(CONFIGS[args.config])
+    if args.iters:
+        cfg["iters"] = args.iters
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, cfg, rank)
+        return
+
+    import torch
+    from paper_2101_11680_gb300 import build as B
+    from paper_2101_11680_gb300 import ctof
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+    B.build()
+
+    t0 = time.perf_counter()
+    kern = ctof.Kernel(ctof.make_optics(**OPTICS),
+                       ctof.make_grid(cfg["n"], cfg["nz"], cfg["nt"], cfg["dx"], cfg["dz"], cfg["z_first"],
+                                      cfg["dt"]))
+    build_s = time.perf_counter() - t0
+    info = kern.info
+    count = args.steps + args.warmup
+    ms, mus = make_inputs(kern, cfg, count, args.seed + 1000 * rank, torch)
+    outs = [torch.empty_like(mu) for mu in mus]
+    params = ctof.admm_params(iters=cfg["iters"])
+    kern.set_timing(True)
+    stream = torch.cuda.current_stream()
+
+    for i in range(args.warmup):
+        kern.reconstruct(ms[args.steps + i], params, out=outs[args.steps + i])
+    torch.cuda.synchronize()
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    time.sleep(0.3)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for i in range(args.steps):
+        kern.reconstruct(ms[i], params, out=outs[i])
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    elapsed_ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    timing = kern.get_timing()
+    if dist:
+        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    total_vols = args.steps * world
+    value = total_vols / (elapsed_ms / 1e3)
+
+    # reconstruction quality (vs the phantom) and a NaN scan of the outputs
+    errs = [float((o - mu).norm() / mu.norm()) for o, mu in zip(outs[:args.steps], mus[:args.steps])]
+
+    # end to end through the host-buffer entry point (copies inside the timed region)
+    mh = [m.cpu().pin_memory() for m in ms[:args.steps]]
+    oh = [torch.empty(outs[0].shape, dtype=torch.float32).pin_memory() for _ in range(args.steps)]
+    kern.set_timing(False)
+    kern.reconstruct_host(mh[0], params, oh[0])  # graph re-capture outside the timed region
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        kern.reconstruct_host(mh[i], params, oh[i])
+    e2e_s = time.perf_counter() - t0
+    if dist:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e_val = total_vols / e2e_s
+
+    peak, peak_src = _peaks()
+    avg_contract_ms = timing.contract_ms / max(1, timing.contract_launches)
+    alg_bytes = contract_bytes(info, cfg["nz"], cfg["nt"])
+    achieved = alg_bytes / (avg_contract_ms * 1e-3) / 1e9
+    traffic = None
+    prof = os.path.join(ROOT, "profiles", "contract_admm_cfg2.json")
+    if args.config == "cfg2" and os.path.exists(prof):
+        try:
+            with open(prof) as f:
+                pj = json.load(f)
+            src = open(os.path.join(ROOT, "paper_2101_11680_gb300", "csrc", "contract.cu"), "rb").read()
+            import hashlib
+            if pj.get("contract_cu_sha256") == hashlib.sha256(src).hexdigest():
+                traffic = pj.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    launches_per_step = timing.graph_kernel_nodes
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": cfg["workload"], "n": cfg["n"], "nz": cfg["nz"], "nt": cfg["nt"],
+                   "iters": cfg["iters"], "parallelism": "replicas" if world > 1 else "single",
+                   "l2": "inputs larger than L2 (W_hat %.0f MB streamed per iteration)"
+                         % (info.n_class * cfg["nt"] * cfg["nz"] * 4 / 1e6),
+                   "kernel_build_s": round(build_s, 3)},
+        "roofline": {"bound": "hbm", "kernel": "k_contract_admm", "achieved": achieved, "peak": peak,
+                     "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
+                     "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_contract_ms,
+                     "peak_source": peak_src},
+        "stage_ms_per_step": {"contract": timing.contract_ms, "t_side": timing.t_side_ms,
+                              "z_side": timing.z_side_ms, "iterations": timing.iterations_ms},
+        "e2e": {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(mh[0].numel() * 4),
+                "d2h_bytes_per_step": int(oh[0].numel() * 4)},
+        "gpu_launches": int(launches_per_step * args.steps),
+        "clocks": clk,
+        "quality": {"rel_l2_vs_phantom_mean": float(np.mean(errs))},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(cfg)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    kern.close()
+    if dist:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

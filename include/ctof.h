@@ -166,6 +166,25 @@ ctof_status ctof_reconstruct(ctof_kernel k, const float* d_m, const ctof_solver_
 ctof_status ctof_reconstruct_host(ctof_kernel k, const float* h_m, const ctof_solver_params* params,
                                   float* h_mu, ctof_report* report, void* stream);
 
+/* Device timing of the stages of the last ADMM reconstruction on a handle
+ * (a profiling aid).  With ctof_set_timing(k, 1) the next captured ADMM graph
+ * records CUDA events around each stage of every iteration: the per-class
+ * x-update contraction, the T-side FFT chain and the Z-side FFT/TV chain.
+ * ctof_get_timing waits for the last of those events and sums the stage
+ * durations over the iterations; it returns EUNSUPPORTED (after filling
+ * graph_kernel_nodes) if the current graph was captured without timing. */
+typedef struct {
+  double contract_ms;      /* sum over iterations of the x-update contraction */
+  double t_side_ms;        /* sum of the T-side chains (K x -> v1/u1 -> c_hat) */
+  double z_side_ms;        /* sum of the Z-side chains (x -> TV prox -> s_hat) */
+  double iterations_ms;    /* first contraction start to last stage end */
+  int contract_launches;   /* number of contraction launches summed */
+  int graph_kernel_nodes;  /* kernel launches in one replay of the ADMM graph */
+} ctof_timing;
+
+ctof_status ctof_set_timing(ctof_kernel k, int enable);
+ctof_status ctof_get_timing(ctof_kernel k, ctof_timing* out);
+
 const char* ctof_status_string(ctof_status s);
 
 /* Text of the last CUDA runtime error seen by this thread inside the library

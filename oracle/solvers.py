@@ -91,7 +91,7 @@ def soft(v, thr):
     return np.sign(v) * np.maximum(np.abs(v) - thr, 0.0)
 
 
-def admm(w_hat, m, grid, iters, rho=1.0, beta=None, beta_rel=1e-3, history=False):
+def admm(w_hat, m, grid, iters, rho=1.0, beta=None, beta_rel=1e-3, history=False, callback=None):
     """Scaled-form ADMM for nonnegative, TV-regularised reconstruction.
 
     Splitting: v1 = K x (T planes on the P grid), v2 = D x, v3 = x.
@@ -108,6 +108,8 @@ def admm(w_hat, m, grid, iters, rho=1.0, beta=None, beta_rel=1e-3, history=False
          u1 += K x - v1;  u2 += D x - v2;  u3 += x - v3
       3. return crop(v3).
     Returns (mu, info) with info = dict(scale, beta, iterates (if history)).
+    `callback(i)`, if given, is called after iteration i (a timing hook; it
+    sees no data).
     """
     n, p, nt = grid.n, grid.p, w_hat.shape[0]
     nz = w_hat.shape[1]
@@ -160,6 +162,8 @@ def admm(w_hat, m, grid, iters, rho=1.0, beta=None, beta_rel=1e-3, history=False
         u3 = u3 + x - v3
         if history:
             hist.append(v3[:, :n, :n].copy())
+        if callback is not None:
+            callback(_)
     info = dict(scale=s, beta=beta, x=x)
     if history:
         info["iterates"] = hist

@@ -161,16 +161,20 @@ ctof_status admm_enqueue(ctof_kernel_s* k, const ctof_solver_params* prm, cudaSt
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_u2a, 0, 3 * nz * pp * sizeof(float), st));
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_u3, 0, nz * pp * sizeof(float), st));
   float* u2[2] = {k->d_u2a, k->d_u2b};
+  cudaEvent_t* ev = k->timing ? k->events : nullptr;
   for (int it = 0; it < prm->iters; ++it) {
     const bool last = it == prm->iters - 1;
+    if (ev) CTOF_CUDA_TRY(cudaEventRecord(ev[4 * it + 0], st));
     // x-update (per frequency class) and K x
     CTOF_TRY(contract_admm(k, k->d_spec_t2, k->d_spec_z, k->d_spec_z2, k->d_spec_t, inv_s, st));
+    if (ev) CTOF_CUDA_TRY(cudaEventRecord(ev[4 * it + 1], st));
     if (!last) {
       // T side: K x -> v1/u1 -> c_hat
       CTOF_TRY(fft_cols_inverse(k, k->d_spec_t, k->ldt, nt, n, k->d_inter_t, st));
       CTOF_TRY(fft_rows_admm_t(k, k->d_inter_t, k->d_mstage, k->d_u1, inv_s, rho, st));
       CTOF_TRY(fft_cols_forward(k, k->d_inter_t, nt, n, k->d_spec_t2, k->ldt, st));
     }
+    if (ev) CTOF_CUDA_TRY(cudaEventRecord(ev[4 * it + 2], st));
     // Z side: x -> TV / nonnegativity prox -> s_hat
     CTOF_TRY(fft_cols_inverse(k, k->d_spec_z2, k->ldz, nz, P, k->d_inter_z, st));
     CTOF_TRY(fft_rows_inverse(k, k->d_inter_z, nz, P, P, k->d_xs, P, st));
@@ -180,18 +184,44 @@ ctof_status admm_enqueue(ctof_kernel_s* k, const ctof_solver_params* prm, cudaSt
       CTOF_TRY(fft_rows_forward(k, k->d_s, nz, P, P, P, k->d_inter_z, st));
       CTOF_TRY(fft_cols_forward(k, k->d_inter_z, nz, P, k->d_spec_z, k->ldz, st));
     }
+    if (ev) CTOF_CUDA_TRY(cudaEventRecord(ev[4 * it + 3], st));
   }
+  return CTOF_OK;
+}
+
+void destroy_events(ctof_kernel_s* k) {
+  for (int i = 0; i < k->n_events; ++i) cudaEventDestroy(k->events[i]);
+  delete[] k->events;
+  k->events = nullptr;
+  k->n_events = 0;
+}
+
+ctof_status ensure_events(ctof_kernel_s* k, int count) {
+  if (k->n_events >= count) return CTOF_OK;
+  destroy_events(k);
+  k->events = new (std::nothrow) cudaEvent_t[count];
+  if (!k->events) return CTOF_ENOMEM;
+  for (int i = 0; i < count; ++i) {
+    if (cudaEventCreate(&k->events[i]) != cudaSuccess) {
+      k->n_events = i;
+      destroy_events(k);
+      return CTOF_ECUDA;
+    }
+  }
+  k->n_events = count;
   return CTOF_OK;
 }
 
 ctof_status admm_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st) {
   const bool same = k->graph && k->graph_iters == prm->iters && k->graph_rho == prm->rho &&
-                    k->graph_beta == prm->tv_beta && k->graph_beta_rel == prm->beta_rel;
+                    k->graph_beta == prm->tv_beta && k->graph_beta_rel == prm->beta_rel &&
+                    k->graph_timing == k->timing;
   if (!same) {
     if (k->graph) {
       cudaGraphExecDestroy(k->graph);
       k->graph = nullptr;
     }
+    if (k->timing) CTOF_TRY(ensure_events(k, 4 * prm->iters));
     cudaStream_t cap = nullptr;
     CTOF_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t g = nullptr;
@@ -208,9 +238,23 @@ ctof_status admm_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream
       return s;
     }
     CTOF_CUDA_TRY(e);
+    {
+      size_t nn = 0;
+      int kernels = 0;
+      if (cudaGraphGetNodes(g, nullptr, &nn) == cudaSuccess && nn > 0) {
+        std::vector<cudaGraphNode_t> nodes(nn);
+        if (cudaGraphGetNodes(g, nodes.data(), &nn) == cudaSuccess)
+          for (size_t i = 0; i < nn; ++i) {
+            cudaGraphNodeType t;
+            if (cudaGraphNodeGetType(nodes[i], &t) == cudaSuccess && t == cudaGraphNodeTypeKernel) ++kernels;
+          }
+      }
+      k->graph_kernel_nodes = kernels;
+    }
     e = cudaGraphInstantiate(&k->graph, g, 0);
     cudaGraphDestroy(g);
     CTOF_CUDA_TRY(e);
+    k->graph_timing = k->timing;
     k->graph_iters = prm->iters;
     k->graph_rho = prm->rho;
     k->graph_beta = prm->tv_beta;
@@ -297,6 +341,7 @@ void ctof_kernel_destroy(ctof_kernel k) {
   if (!k) return;
   DeviceGuard guard(k->device);
   if (k->graph) cudaGraphExecDestroy(k->graph);
+  destroy_events(k);
   if (k->d_tik_chol) cudaFree(k->d_tik_chol);
   if (k->d_w) cudaFree(k->d_w);
   if (k->d_base) cudaFree(k->d_base);
@@ -506,6 +551,36 @@ ctof_status ctof_reconstruct_host(ctof_kernel k, const float* h_m, const ctof_so
   CTOF_CUDA_TRY(cudaMemcpyAsync(h_mu, k->d_vstage, vbytes, cudaMemcpyDeviceToHost, st));
   if (report) return fill_report(k, params, lambda, report, st);
   CTOF_CUDA_TRY(cudaStreamSynchronize(st));
+  return CTOF_OK;
+}
+
+ctof_status ctof_set_timing(ctof_kernel k, int enable) {
+  if (!k || (enable != 0 && enable != 1)) return CTOF_EINVAL;
+  k->timing = enable;
+  return CTOF_OK;
+}
+
+ctof_status ctof_get_timing(ctof_kernel k, ctof_timing* out) {
+  if (!k || !out) return CTOF_EINVAL;
+  memset(out, 0, sizeof(*out));
+  out->graph_kernel_nodes = k->graph_kernel_nodes;
+  if (!k->graph || !k->graph_timing) return CTOF_EUNSUPPORTED;
+  DeviceGuard g(k->device);
+  const int iters = k->graph_iters;
+  CTOF_CUDA_TRY(cudaEventSynchronize(k->events[4 * iters - 1]));
+  for (int it = 0; it < iters; ++it) {
+    float a = 0.f, b = 0.f, c = 0.f;
+    CTOF_CUDA_TRY(cudaEventElapsedTime(&a, k->events[4 * it + 0], k->events[4 * it + 1]));
+    CTOF_CUDA_TRY(cudaEventElapsedTime(&b, k->events[4 * it + 1], k->events[4 * it + 2]));
+    CTOF_CUDA_TRY(cudaEventElapsedTime(&c, k->events[4 * it + 2], k->events[4 * it + 3]));
+    out->contract_ms += a;
+    out->t_side_ms += b;
+    out->z_side_ms += c;
+  }
+  float tot = 0.f;
+  CTOF_CUDA_TRY(cudaEventElapsedTime(&tot, k->events[0], k->events[4 * iters - 1]));
+  out->iterations_ms = tot;
+  out->contract_launches = iters;
   return CTOF_OK;
 }
 

@@ -66,7 +66,13 @@ struct ctof_kernel_s {
   cudaGraphExec_t graph;
   int graph_iters;
   double graph_rho, graph_beta, graph_beta_rel;
-  cudaStream_t graph_stream;
+  int graph_timing;
+  int graph_kernel_nodes;
+
+  // optional per-stage timing: 4 events per ADMM iteration, recorded inside the graph
+  int timing;
+  int n_events;
+  cudaEvent_t* events;
 };
 
 // ---- fft.cu -------------------------------------------------------------

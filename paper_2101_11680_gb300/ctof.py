@@ -45,6 +45,12 @@ class Report(ctypes.Structure):
                 ("iters_done", ctypes.c_int)]
 
 
+class Timing(ctypes.Structure):
+    _fields_ = [("contract_ms", ctypes.c_double), ("t_side_ms", ctypes.c_double), ("z_side_ms", ctypes.c_double),
+                ("iterations_ms", ctypes.c_double), ("contract_launches", ctypes.c_int),
+                ("graph_kernel_nodes", ctypes.c_int)]
+
+
 class CtofError(RuntimeError):
     def __init__(self, status, where):
         lib = load()
@@ -70,6 +76,8 @@ _SIGNATURES = {
     "ctof_reconstruct": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolverParams), _P, ctypes.POINTER(Report), _P]),
     "ctof_reconstruct_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolverParams), _P, ctypes.POINTER(Report),
                                              _P]),
+    "ctof_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ctof_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(Timing)]),
     "ctof_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ctof_last_error_message": (ctypes.c_char_p, []),
 }
@@ -158,6 +166,17 @@ class Kernel:
             self.close()
         except Exception:
             pass
+
+    # ---- profiling ----
+    def set_timing(self, enable):
+        _check(self._lib.ctof_set_timing(self._h, 1 if enable else 0), "ctof_set_timing")
+
+    def get_timing(self):
+        t = Timing()
+        st = self._lib.ctof_get_timing(self._h, ctypes.byref(t))
+        if st not in (OK, EUNSUPPORTED):
+            _check(st, "ctof_get_timing")
+        return t
 
     # ---- parity accessors (synchronous) ----
     def get_w(self):
