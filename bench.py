@@ -330,9 +330,9 @@ def main():
         try:
             with open(prof) as f:
                 pj = json.load(f)
-            src = open(os.path.join(ROOT, "paper_2101_11680_gb300", "csrc", "contract.cu"), "rb").read()
+            src = open(os.path.join(ROOT, "paper_2101_11680_gb300", "csrc", "contract_admm.cu"), "rb").read()
             import hashlib
-            if pj.get("contract_cu_sha256") == hashlib.sha256(src).hexdigest():
+            if pj.get("source_sha256") == hashlib.sha256(src).hexdigest():
                 traffic = pj.get("dram_bytes_per_launch")
         except Exception:
             traffic = None

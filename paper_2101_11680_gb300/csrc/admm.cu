@@ -4,9 +4,9 @@
 //   v3 = max(a3, 0) on the scan support S (0 off S),  u3 <- a3 - v3,  w3 = 2 v3 - a3
 //   s  = D^T w2 + w3      (the Z-side part of the next x-update right-hand side)
 // D: forward differences, lateral periodic on the P x P grid, axial Neumann
-// (Z-1 differences).  One CTA owns a 32 x 8 lateral tile and marches along z;
-// the backward differences of D^T need w2 of the left/upper neighbours, which
-// the tile-edge threads recompute from the previous u2 (hence u2 is double
+// (Z-1 differences).  One CTA owns a 32 x 8 lateral tile of one depth plane;
+// the backward differences of D^T need w2 of the left/upper/previous-plane
+// neighbours, which are recomputed from the previous u2 (hence u2 is double
 // buffered: blocks read the old copy, write the new one).
 #include <cuda_runtime.h>
 
@@ -21,6 +21,9 @@ __device__ __forceinline__ float soft(float a, float thr) {
   return m > 0.f ? copysignf(m, a) : 0.f;
 }
 
+// One CTA per (32 x 8 lateral tile, depth plane j).  The axial backward
+// difference needs w2z of plane j-1, which is pointwise in (x[j-1], x[j],
+// u2z[j-1]) and is recomputed here rather than carried across planes.
 __global__ void __launch_bounds__(TX* TY) k_tv_stencil(const float* __restrict__ x, const float* __restrict__ u2o,
                                                        float* __restrict__ u2n, float* __restrict__ u3,
                                                        float* __restrict__ s_out, const double* __restrict__ beta,
@@ -30,68 +33,72 @@ __global__ void __launch_bounds__(TX* TY) k_tv_stencil(const float* __restrict__
   __shared__ float sW2x[TY][TX + 1];
   __shared__ float sW2y[TY + 1][TX];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, j = blockIdx.z;
   const int gx = x0 + tx, gy = y0 + ty;
   const size_t plane = (size_t)P * P;
   const float thr = (float)(beta[0]) * inv_rho;
   const bool in_s = gx < n && gy < n;
   const int tid = ty * TX + tx;
-  float w2z_prev = 0.f;
-  for (int j = 0; j < nz; ++j) {
-    const float* xp = x + (size_t)j * plane;
-    for (int i = tid; i < (TY + 2) * (TX + 2); i += TX * TY) {
-      const int ly = i / (TX + 2), lx = i - ly * (TX + 2);
-      const int yy = (y0 + ly - 1 + P) & (P - 1), xx = (x0 + lx - 1 + P) & (P - 1);
-      sX[ly][lx] = xp[(size_t)yy * P + xx];
-    }
-    __syncthreads();
-    const size_t idx = (size_t)j * plane + (size_t)gy * P + gx;
-    const float c = sX[ty + 1][tx + 1];
-    float w2x, w2y, w2z;
-    {
-      const float a = (sX[ty + 1][tx + 2] - c) + u2o[idx];
-      const float v = soft(a, thr);
-      u2n[idx] = a - v;
-      w2x = 2.f * v - a;
-    }
-    {
-      const float a = (sX[ty + 2][tx + 1] - c) + u2o[plane * nz + idx];
-      const float v = soft(a, thr);
-      u2n[plane * nz + idx] = a - v;
-      w2y = 2.f * v - a;
-    }
-    if (j < nz - 1) {
-      const float a = (x[idx + plane] - c) + u2o[2 * plane * nz + idx];
-      const float v = soft(a, thr);
-      u2n[2 * plane * nz + idx] = a - v;
-      w2z = 2.f * v - a;
-    } else {
-      u2n[2 * plane * nz + idx] = 0.f;
-      w2z = 0.f;
-    }
-    const float a3 = c + u3[idx];
-    const float v3 = in_s ? fmaxf(a3, 0.f) : 0.f;
-    u3[idx] = a3 - v3;
-    const float w3 = 2.f * v3 - a3;
-    sW2x[ty][tx + 1] = w2x;
-    sW2y[ty + 1][tx] = w2y;
-    if (tx == 0) {
-      const int xl = (gx - 1 + P) & (P - 1);
-      const float a = (c - sX[ty + 1][0]) + u2o[(size_t)j * plane + (size_t)gy * P + xl];
-      sW2x[ty][0] = 2.f * soft(a, thr) - a;
-    }
-    if (ty == 0) {
-      const int yu = (gy - 1 + P) & (P - 1);
-      const float a = (c - sX[0][tx + 1]) + u2o[plane * nz + (size_t)j * plane + (size_t)yu * P + gx];
-      sW2y[0][tx] = 2.f * soft(a, thr) - a;
-    }
-    __syncthreads();
-    const float s = (sW2x[ty][tx] - sW2x[ty][tx + 1]) + (sW2y[ty][tx] - sW2y[ty + 1][tx]) + (w2z_prev - w2z) + w3;
-    s_out[idx] = s;
-    if (out_crop && in_s) out_crop[((size_t)j * n + gy) * n + gx] = v3;
-    w2z_prev = w2z;
-    __syncthreads();
+  const float* xp = x + (size_t)j * plane;
+  for (int i = tid; i < (TY + 2) * (TX + 2); i += TX * TY) {
+    const int ly = i / (TX + 2), lx = i - ly * (TX + 2);
+    const int yy = (y0 + ly - 1 + P) & (P - 1), xx = (x0 + lx - 1 + P) & (P - 1);
+    sX[ly][lx] = xp[(size_t)yy * P + xx];
   }
+  const size_t pix = (size_t)gy * P + gx;
+  const size_t idx = (size_t)j * plane + pix;
+  const float* u2oy = u2o + plane * nz;
+  const float* u2oz = u2o + 2 * plane * nz;
+  // w2z of the plane above (j-1), pointwise
+  float w2z_prev = 0.f;
+  if (j > 0) {
+    const float a = (x[idx] - x[idx - plane]) + u2oz[idx - plane];
+    w2z_prev = 2.f * soft(a, thr) - a;
+  }
+  __syncthreads();
+  const float c = sX[ty + 1][tx + 1];
+  float w2x, w2y, w2z;
+  {
+    const float a = (sX[ty + 1][tx + 2] - c) + u2o[idx];
+    const float v = soft(a, thr);
+    u2n[idx] = a - v;
+    w2x = 2.f * v - a;
+  }
+  {
+    const float a = (sX[ty + 2][tx + 1] - c) + u2oy[idx];
+    const float v = soft(a, thr);
+    u2n[plane * nz + idx] = a - v;
+    w2y = 2.f * v - a;
+  }
+  if (j < nz - 1) {
+    const float a = (x[idx + plane] - c) + u2oz[idx];
+    const float v = soft(a, thr);
+    u2n[2 * plane * nz + idx] = a - v;
+    w2z = 2.f * v - a;
+  } else {
+    u2n[2 * plane * nz + idx] = 0.f;
+    w2z = 0.f;
+  }
+  const float a3 = c + u3[idx];
+  const float v3 = in_s ? fmaxf(a3, 0.f) : 0.f;
+  u3[idx] = a3 - v3;
+  const float w3 = 2.f * v3 - a3;
+  sW2x[ty][tx + 1] = w2x;
+  sW2y[ty + 1][tx] = w2y;
+  if (tx == 0) {
+    const int xl = (gx - 1 + P) & (P - 1);
+    const float a = (c - sX[ty + 1][0]) + u2o[(size_t)j * plane + (size_t)gy * P + xl];
+    sW2x[ty][0] = 2.f * soft(a, thr) - a;
+  }
+  if (ty == 0) {
+    const int yu = (gy - 1 + P) & (P - 1);
+    const float a = (c - sX[0][tx + 1]) + u2oy[(size_t)j * plane + (size_t)yu * P + gx];
+    sW2y[0][tx] = 2.f * soft(a, thr) - a;
+  }
+  __syncthreads();
+  const float s = (sW2x[ty][tx] - sW2x[ty][tx + 1]) + (sW2y[ty][tx] - sW2y[ty + 1][tx]) + (w2z_prev - w2z) + w3;
+  s_out[idx] = s;
+  if (out_crop && in_s) out_crop[((size_t)j * n + gy) * n + gx] = v3;
 }
 
 __global__ void k_max_abs(const float* __restrict__ v, size_t count, unsigned int* __restrict__ out) {
@@ -122,7 +129,7 @@ __global__ void k_check_finite(const float* __restrict__ v, size_t count, int* _
 ctof_status admm_tv_stencil(const ctof_kernel_s* k, const float* x, const float* u2_old, float* u2_new, float* u3,
                             float* s, const double* beta_dev, float rho, float* out_crop, cudaStream_t st) {
   dim3 block(TX, TY);
-  dim3 grid(k->p / TX, k->p / TY);
+  dim3 grid(k->p / TX, k->p / TY, k->nz);
   k_tv_stencil<<<grid, block, 0, st>>>(x, u2_old, u2_new, u3, s, beta_dev, 1.0f / rho, k->p, k->nz, k->n, out_crop);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;

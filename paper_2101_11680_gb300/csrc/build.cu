@@ -168,9 +168,15 @@ __global__ void k_gather_classes(const double* __restrict__ out, int nplanes_chu
   }
 }
 
-__global__ void k_to_float(const double* __restrict__ in, float* __restrict__ out, size_t n) {
-  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = (float)in[i];
+// FP32 copy of W_hat with rows padded to z4 floats: out[c][t][z4] (zero padding).
+__global__ void k_to_float_padded(const double* __restrict__ in, float* __restrict__ out, long long rows, int nz,
+                                  int z4) {
+  const long long n = rows * z4;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const long long r = i / z4;
+    const int z = (int)(i - r * z4);
+    out[i] = z < nz ? (float)in[r * nz + z] : 0.f;
+  }
 }
 
 // G[c] = sum_t what64[c][t][:]^T what64[c][t][:]
@@ -323,11 +329,13 @@ __global__ void __launch_bounds__(128) k_factor(const double* __restrict__ gram,
     }
   }
   __syncthreads();
-  for (int idx = threadIdx.x; idx < nz * nz; idx += blockDim.x) {
-    const int i = idx / nz, j = idx - i * nz;
+  const int z4 = (nz + 3) & ~3;
+  for (int idx = threadIdx.x; idx < nz * z4; idx += blockDim.x) {
+    const int i = idx / z4, j = idx - i * z4;
     double acc = 0.0;
-    for (int kk = (i > j ? i : j); kk < nz; ++kk) acc += s_l[kk * ld + i] * s_l[kk * ld + j];
-    out32[(size_t)c * nz * nz + idx] = (float)acc;
+    if (j < nz)
+      for (int kk = (i > j ? i : j); kk < nz; ++kk) acc += s_l[kk * ld + i] * s_l[kk * ld + j];
+    out32[(size_t)c * nz * z4 + idx] = (float)acc;
   }
 }
 
@@ -476,7 +484,8 @@ ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st) {
     }
   }
   // FP32 copy of W_hat (layout [c][t][z] == [c][plane])
-  k_to_float<<<152 * 8, 256, 0, st>>>(d_what64.as<double>(), k->d_what, (size_t)nclass * planes);
+  k_to_float_padded<<<152 * 8, 256, 0, st>>>(d_what64.as<double>(), k->d_what, (long long)nclass * nt, nz,
+                                             k->z4);
   CTOF_CUDA_TRY(cudaGetLastError());
   k_gram<<<nclass, 256, 0, st>>>(d_what64.as<double>(), nt, nz, k->d_gram);
   CTOF_CUDA_TRY(cudaGetLastError());

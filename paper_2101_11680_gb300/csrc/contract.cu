@@ -6,14 +6,7 @@
 // the up-to-four frequencies (a,b), (a,-b), (b,a), (b,-a) of one class; a CTA
 // stages one class's T x Z matrix once in shared memory and applies it to the
 // complex vectors of all members (up to 8 real right-hand sides).
-//
-// The ADMM kernel fuses, per class, the whole x-update of one iteration:
-//   b     = W_hat^T c_hat / s + s_hat - L x_hat_prev
-//   x_hat = x_hat_prev + H^-1 b
-//   Kx    = W_hat x_hat / s
-// where L = (|dx|^2 + |dy|^2 + 1) I + Dz^T Dz and H = W_hat^T W_hat / s^2 + L.
-// This equals x_hat = H^-1 (W_hat^T (K x_hat_prev + c_hat)/s + s_hat): the
-// T-side input K x_prev + c is never materialised.
+// (The fused ADMM x-update lives in contract_admm.cu.)
 #include <cuda_runtime.h>
 
 #include "ctof_internal.h"
@@ -23,17 +16,14 @@ namespace {
 constexpr int CT_THREADS = 256;
 constexpr int CT_WARPS = CT_THREADS / 32;
 
-struct ClassTile {
-  float* w;      // [nt][nz+1]
-  int ldw;
-};
-
+// W_hat is stored [class][nt][z4] (rows padded to a multiple of 4 floats).
 __device__ __forceinline__ void load_what(float* s_w, const float* __restrict__ what, int c, int nt, int nz) {
-  const float* src = what + (size_t)c * nt * nz;
+  const int z4 = (nz + 3) & ~3;
+  const float* src = what + (size_t)c * nt * z4;
   const int total = nt * nz;
   for (int i = threadIdx.x; i < total; i += blockDim.x) {
     const int t = i / nz, z = i - t * nz;
-    s_w[t * (nz + 1) + z] = src[i];
+    s_w[t * (nz + 1) + z] = src[(size_t)t * z4 + z];
   }
 }
 
@@ -147,89 +137,6 @@ __global__ void __launch_bounds__(CT_THREADS) k_contract_adj(const float* __rest
   }
 }
 
-__global__ void __launch_bounds__(CT_THREADS) k_contract_admm(
-    const float* __restrict__ what, const float* __restrict__ hinv, const float* __restrict__ lap,
-    const int* __restrict__ members, int nclass, int nt, int nz, const float2* __restrict__ c_hat, int ldt,
-    const float2* __restrict__ s_hat, float2* __restrict__ x_hat, int ldz, float2* __restrict__ kx_hat,
-    float inv_s) {
-  extern __shared__ float smem_f[];
-  float* s_w = smem_f;
-  float* s_h = s_w + nt * (nz + 1);                                  // [nz][nz+1]
-  float2* s_v = reinterpret_cast<float2*>(s_h + ((nz * (nz + 1) + 1) & ~1) + ((nt * (nz + 1)) & 1));
-  float2* s_part = s_v + 4 * nt;                                     // [warps][4][nz]
-  float2* s_b = s_part + CT_WARPS * 4 * nz;                          // [4][nz]
-  float2* s_xp = s_b + 4 * nz;                                       // [4][nz]
-  float2* s_xn = s_xp + 4 * nz;                                      // [4][nz]
-  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
-    int mem[4];
-    const int nmem = load_members(members, c, mem);
-    load_what(s_w, what, c, nt, nz);
-    {
-      const float* src = hinv + (size_t)c * nz * nz;
-      for (int i = threadIdx.x; i < nz * nz; i += blockDim.x) {
-        const int r = i / nz, q = i - r * nz;
-        s_h[r * (nz + 1) + q] = src[i];
-      }
-    }
-    for (int i = threadIdx.x; i < 4 * nt; i += blockDim.x) {
-      const int m = i / nt, t = i - m * nt;
-      s_v[i] = m < nmem ? c_hat[(size_t)mem[m] * ldt + t] : make_float2(0.f, 0.f);
-    }
-    for (int i = threadIdx.x; i < 4 * nz; i += blockDim.x) {
-      const int m = i / nz, z = i - m * nz;
-      s_xp[i] = m < nmem ? x_hat[(size_t)mem[m] * ldz + z] : make_float2(0.f, 0.f);
-      s_b[i] = m < nmem ? s_hat[(size_t)mem[m] * ldz + z] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    adj_partials(s_w, s_v, nt, nz, nmem, s_part);
-    __syncthreads();
-    const float dl = lap[c] + 1.0f;
-    for (int i = threadIdx.x; i < nmem * nz; i += blockDim.x) {
-      const int m = i / nz, z = i - m * nz;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int w = 0; w < CT_WARPS; ++w) acc = cadd(acc, s_part[(w * 4 + m) * nz + z]);
-      const float2* xp = s_xp + m * nz;
-      float2 lx = cscale(xp[z], dl);
-      if (z > 0) lx = cadd(lx, csub(xp[z], xp[z - 1]));
-      if (z < nz - 1) lx = csub(lx, csub(xp[z + 1], xp[z]));
-      s_b[i] = csub(cadd(cscale(acc, inv_s), s_b[i]), lx);
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nmem * nz; i += blockDim.x) {
-      const int m = i / nz, z = i - m * nz;
-      const float* hr = s_h + z * (nz + 1);
-      const float2* b = s_b + m * nz;
-      float2 acc = s_xp[i];
-      for (int q = 0; q < nz; ++q) {
-        acc.x += hr[q] * b[q].x;
-        acc.y += hr[q] * b[q].y;
-      }
-      s_xn[i] = acc;
-      x_hat[(size_t)mem[m] * ldz + z] = acc;
-    }
-    __syncthreads();
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-      float2 acc[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
-      const float* wr = s_w + t * (nz + 1);
-      for (int z = 0; z < nz; ++z) {
-        const float w = wr[z];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const float2 x = s_xn[m * nz + z];
-          acc[m].x += w * x.x;
-          acc[m].y += w * x.y;
-        }
-      }
-#pragma unroll
-      for (int m = 0; m < 4; ++m)
-        if (m < nmem) kx_hat[(size_t)mem[m] * ldt + t] = cscale(acc[m], inv_s);
-    }
-    __syncthreads();
-  }
-}
-
 // Tikhonov: x_hat = (G + lambda I)^-1 W_hat^T m_hat per member, with the FP64
 // Cholesky factor L (lower, row-major [nz][nz]) of G + lambda I.
 __global__ void __launch_bounds__(CT_THREADS) k_contract_tikhonov(
@@ -314,19 +221,6 @@ ctof_status contract_adjoint(const ctof_kernel_s* k, const float2* in_t, float2*
   CTOF_CUDA_TRY(cudaFuncSetAttribute(k_contract_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   k_contract_adj<<<contract_grid(k->nclass, sm), CT_THREADS, sm, st>>>(k->d_what, k->d_members, k->nclass, k->nt,
                                                                        k->nz, in_t, k->ldt, out_z, k->ldz);
-  CTOF_CUDA_TRY(cudaGetLastError());
-  return CTOF_OK;
-}
-
-ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const float2* s_hat, float2* x_hat,
-                          float2* kx_hat, float inv_scale, cudaStream_t st) {
-  const int nt = k->nt, nz = k->nz;
-  const size_t floats = (size_t)nt * (nz + 1) + (size_t)((nz * (nz + 1) + 1) & ~1) + ((nt * (nz + 1)) & 1);
-  const size_t sm = floats * 4 + ((size_t)4 * nt + (size_t)CT_WARPS * 4 * nz + 3 * 4 * (size_t)nz) * 8;
-  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_contract_admm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_contract_admm<<<contract_grid(k->nclass, sm), CT_THREADS, sm, st>>>(
-      k->d_what, k->d_hinv, k->d_lap, k->d_members, k->nclass, nt, nz, c_hat, k->ldt, s_hat, x_hat, k->ldz, kx_hat,
-      inv_scale);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }

@@ -61,8 +61,9 @@ ctof_status validate(const ctof_optics* o, const ctof_grid* g) {
   {
     const size_t nt = (size_t)g->nt, nz = (size_t)g->nz;
     const size_t w = (nt * (nz + 1) + 1) & ~(size_t)1;
-    const size_t admm = (w + ((nz * (nz + 1) + 1) & ~(size_t)1) + 1) * 4 + (4 * nt + 44 * nz) * 8;
-    const size_t tik = ((w * 4 + 4 * nt * 8 + 32 * nz * 8 + 7) & ~(size_t)7) + (nz * nz + 8 * nz) * 8;
+    const size_t admm = contract_admm_smem_bytes(g->nt, g->nz, 1);
+    const size_t adj = w * 4 + 4 * nt * 8 + 32 * nz * 8;
+    const size_t tik = ((adj + 7) & ~(size_t)7) + (nz * nz + 8 * nz) * 8;
     if (admm > 227 * 1024 || tik > 227 * 1024) return CTOF_EUNSUPPORTED;
   }
   if (g->conv_mode == CTOF_LINEAR) {
@@ -164,17 +165,17 @@ ctof_status admm_enqueue(ctof_kernel_s* k, const ctof_solver_params* prm, cudaSt
   cudaEvent_t* ev = k->timing ? k->events : nullptr;
   for (int it = 0; it < prm->iters; ++it) {
     const bool last = it == prm->iters - 1;
-    if (ev) CTOF_CUDA_TRY(cudaEventRecord(ev[4 * it + 0], st));
+    if (ev) CTOF_CUDA_TRY(cudaEventRecordWithFlags(ev[4 * it + 0], st, cudaEventRecordExternal));
     // x-update (per frequency class) and K x
     CTOF_TRY(contract_admm(k, k->d_spec_t2, k->d_spec_z, k->d_spec_z2, k->d_spec_t, inv_s, st));
-    if (ev) CTOF_CUDA_TRY(cudaEventRecord(ev[4 * it + 1], st));
+    if (ev) CTOF_CUDA_TRY(cudaEventRecordWithFlags(ev[4 * it + 1], st, cudaEventRecordExternal));
     if (!last) {
       // T side: K x -> v1/u1 -> c_hat
       CTOF_TRY(fft_cols_inverse(k, k->d_spec_t, k->ldt, nt, n, k->d_inter_t, st));
       CTOF_TRY(fft_rows_admm_t(k, k->d_inter_t, k->d_mstage, k->d_u1, inv_s, rho, st));
       CTOF_TRY(fft_cols_forward(k, k->d_inter_t, nt, n, k->d_spec_t2, k->ldt, st));
     }
-    if (ev) CTOF_CUDA_TRY(cudaEventRecord(ev[4 * it + 2], st));
+    if (ev) CTOF_CUDA_TRY(cudaEventRecordWithFlags(ev[4 * it + 2], st, cudaEventRecordExternal));
     // Z side: x -> TV / nonnegativity prox -> s_hat
     CTOF_TRY(fft_cols_inverse(k, k->d_spec_z2, k->ldz, nz, P, k->d_inter_z, st));
     CTOF_TRY(fft_rows_inverse(k, k->d_inter_z, nz, P, P, k->d_xs, P, st));
@@ -184,7 +185,7 @@ ctof_status admm_enqueue(ctof_kernel_s* k, const ctof_solver_params* prm, cudaSt
       CTOF_TRY(fft_rows_forward(k, k->d_s, nz, P, P, P, k->d_inter_z, st));
       CTOF_TRY(fft_cols_forward(k, k->d_inter_z, nz, P, k->d_spec_z, k->ldz, st));
     }
-    if (ev) CTOF_CUDA_TRY(cudaEventRecord(ev[4 * it + 3], st));
+    if (ev) CTOF_CUDA_TRY(cudaEventRecordWithFlags(ev[4 * it + 3], st, cudaEventRecordExternal));
   }
   return CTOF_OK;
 }
@@ -275,6 +276,7 @@ ctof_status tikhonov_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaSt
   }
   if (k->tik_lambda != lambda) CTOF_TRY(build_tikhonov_factors(k, lambda, st));
   *lambda_out = lambda;
+  CTOF_CUDA_TRY(cudaMemsetAsync(k->d_scalars, 0, 16 * sizeof(double), st));
   CTOF_TRY(fft_forward_planes(k, k->d_mstage, k->nt, k->n, k->n, k->n, k->d_inter_t, k->d_spec_t, k->ldt, st));
   CTOF_TRY(contract_tikhonov(k, k->d_tik_chol, k->d_spec_t, k->d_spec_z, st));
   return fft_inverse_planes(k, k->d_spec_z, k->ldz, k->nz, k->n, k->n, k->d_inter_z, k->d_vstage, k->n, st);
@@ -306,15 +308,17 @@ ctof_status fill_report(ctof_kernel_s* k, const ctof_solver_params* prm, double 
   int* flag = reinterpret_cast<int*>(k->d_scalars + 8);
   CTOF_CUDA_TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
   CTOF_TRY(check_finite(k->d_vstage, (size_t)k->nz * k->n * k->n, flag, st));
-  double sc[9];
-  CTOF_CUDA_TRY(cudaMemcpyAsync(sc, k->d_scalars, 9 * sizeof(double), cudaMemcpyDeviceToHost, st));
+  double sc[10];
+  CTOF_CUDA_TRY(cudaMemcpyAsync(sc, k->d_scalars, 10 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CTOF_CUDA_TRY(cudaStreamSynchronize(st));
-  int bad = 0;
+  int bad = 0, timeout = 0;
   memcpy(&bad, &sc[8], sizeof(int));
+  memcpy(&timeout, &sc[9], sizeof(int));
   rep->scale = k->scale;
   rep->beta = prm->solver == CTOF_SOLVER_ADMM_TV ? sc[0] : 0.0;
   rep->lambda = lambda;
   rep->iters_done = prm->solver == CTOF_SOLVER_ADMM_TV ? prm->iters : 1;
+  if (timeout) return CTOF_ETIMEOUT;
   return bad ? CTOF_ENONFINITE : CTOF_OK;
 }
 
@@ -370,6 +374,7 @@ ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, 
   k->hp = ctof_round_up(k->h, 4);
   k->nf = k->p * k->h;
   k->q = grid->conv_mode == CTOF_LINEAR ? grid->nx : k->p / 2 + 1;
+  k->z4 = ctof_round_up(k->nz, 4);
   k->ldt = ctof_round_up(k->nt, 8);
   k->ldz = ctof_round_up(k->nz, 8);
   k->symmetric = grid->dx_mm == grid->dy_mm;
@@ -386,9 +391,9 @@ ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, 
   Carver cv;
   const size_t o_members = cv.take<int>((size_t)k->nclass * 4);
   const size_t o_lap = cv.take<float>(k->nclass);
-  const size_t o_what = cv.take<float>((size_t)k->nclass * nt * nz);
+  const size_t o_what = cv.take<float>((size_t)k->nclass * nt * k->z4);
   const size_t o_gram = cv.take<double>((size_t)k->nclass * nz * nz);
-  const size_t o_hinv = cv.take<float>((size_t)k->nclass * nz * nz);
+  const size_t o_hinv = cv.take<float>((size_t)k->nclass * nz * k->z4);
   const size_t o_tw = cv.take<float2>(P);
   const size_t o_st = cv.take<float2>((size_t)k->nf * k->ldt);
   const size_t o_st2 = cv.take<float2>((size_t)k->nf * k->ldt);
@@ -448,7 +453,8 @@ ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, 
   for (int j = 0; j < P; ++j) tw[j] = make_float2((float)cos(two_pi * j / P), (float)-sin(two_pi * j / P));
   ctof_status s = CTOF_OK;
   do {
-    if (cudaMemcpyAsync(k->d_members, members.data(), members.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
+    if (cudaMemsetAsync(k->d_scalars, 0, 16 * sizeof(double), st) != cudaSuccess ||
+        cudaMemcpyAsync(k->d_members, members.data(), members.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
         cudaMemcpyAsync(k->d_lap, lap.data(), lap.size() * sizeof(float), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
@@ -500,8 +506,8 @@ ctof_status ctof_kernel_get_classes(ctof_kernel k, int* h_members) {
 ctof_status ctof_kernel_get_what(ctof_kernel k, float* h_what) {
   if (!k || !h_what) return CTOF_EINVAL;
   DeviceGuard g(k->device);
-  CTOF_CUDA_TRY(cudaMemcpy(h_what, k->d_what, (size_t)k->nclass * k->nt * k->nz * sizeof(float),
-                           cudaMemcpyDeviceToHost));
+  CTOF_CUDA_TRY(cudaMemcpy2D(h_what, (size_t)k->nz * sizeof(float), k->d_what, (size_t)k->z4 * sizeof(float),
+                             (size_t)k->nz * sizeof(float), (size_t)k->nclass * k->nt, cudaMemcpyDeviceToHost));
   return CTOF_OK;
 }
 

@@ -22,6 +22,7 @@ struct ctof_kernel_s {
   int nf;       // P * h half-plane frequencies
   int q;        // kernel-table extent per lateral axis (n linear, P/2+1 circular)
   int nt, nz;
+  int z4;       // nz rounded up to a multiple of 4 (row pitch of W_hat and H^-1)
   int ldt, ldz; // frequency-major leading dims (complex) of T- and Z-side spectra
   int nclass;
   int symmetric;  // dx == dy: 8-fold lateral symmetry, classes hold up to 4 members
@@ -36,9 +37,9 @@ struct ctof_kernel_s {
 
   int* d_members;      // [nclass][4]
   float* d_lap;        // [nclass] 4 sin^2(pi a/P) + 4 sin^2(pi b/P)
-  float* d_what;       // [nclass][nt][nz]
+  float* d_what;       // [nclass][nt][z4] (zero padding)
   double* d_gram;      // [nclass][nz][nz]
-  float* d_hinv;       // [nclass][nz][nz]  (ADMM normal matrix inverse, normalised units)
+  float* d_hinv;       // [nclass][nz][z4]  (ADMM normal matrix inverse, normalised units)
   float2* d_tw;        // [p] forward twiddles exp(-2 pi i j / P)
   double* d_w;         // optional FP64 kernel table [nt][nz][q][q]
 
@@ -108,6 +109,7 @@ ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const flo
                           float2* x_hat, float2* kx_hat, float inv_scale, cudaStream_t st);
 ctof_status contract_tikhonov(const ctof_kernel_s* k, const double* chol, const float2* m_hat,
                               float2* x_hat, cudaStream_t st);
+size_t contract_admm_smem_bytes(int nt, int nz, int nbuf);
 
 // ---- build.cu ----------------------------------------------------------
 ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st);

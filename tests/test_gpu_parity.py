@@ -140,3 +140,21 @@ def test_reconstruct_host_buffers():
     out = torch.empty((g.nz, g.n, g.n), dtype=torch.float32).pin_memory()
     k.reconstruct_host(mh, p, out)
     assert torch.equal(out, dev)
+
+
+def test_stage_timing_api():
+    g, wh, _, m = _measurement("admm16", seed=5, peak=1e5)
+    k = device_kernel("admm16")
+    k.set_timing(True)
+    try:
+        out = k.reconstruct(torch.tensor(m, dtype=torch.float32, device="cuda"), ctof.admm_params(iters=12))
+        torch.cuda.synchronize()
+        t = k.get_timing()
+        assert t.contract_launches == 12
+        assert t.contract_ms > 0 and t.t_side_ms > 0 and t.z_side_ms > 0
+        assert t.iterations_ms >= t.contract_ms
+        assert t.graph_kernel_nodes > 12
+        want, _ = so.admm(wh, m, g, 12)
+        assert rel_l2(out.cpu().numpy(), want) <= 1e-5
+    finally:
+        k.set_timing(False)
