@@ -166,6 +166,21 @@ ctof_status ctof_reconstruct(ctof_kernel k, const float* d_m, const ctof_solver_
 ctof_status ctof_reconstruct_host(ctof_kernel k, const float* h_m, const ctof_solver_params* params,
                                   float* h_mu, ctof_report* report, void* stream);
 
+/* m = A mu like ctof_forward, but allocation-free: every intermediate lives in
+ * one fixed 32 MiB array inside the library image instead of the handle's
+ * workspace, and the call makes no cudaMalloc/cudaFree or other allocating
+ * call.  (The paper has no counterpart; this exists for callers that may not
+ * allocate device memory at the point of the call: code inside a CUDA stream
+ * capture, real-time loops that must not block on an allocator, frameworks
+ * that own every device allocation.)  The handle must already be built.
+ * The first call on a device resolves the array's device address with that
+ * device current; make that first call before any stream capture begins.
+ * All calls share the array: calls that overlap on the GPU race and corrupt
+ * each other; serialise them.  Grids whose intermediates exceed 32 MiB are
+ * rejected with CTOF_EUNSUPPORTED (ctof_last_error_message gives the size).
+ * Asynchronous on `stream`. */
+ctof_status ctof_forward_static(ctof_kernel k, const float* d_mu, float* d_m, void* stream);
+
 /* Device timing of the stages of the last ADMM reconstruction on a handle
  * (a profiling aid).  With ctof_set_timing(k, 1) the next captured ADMM graph
  * records CUDA events around each stage of every iteration: the per-class

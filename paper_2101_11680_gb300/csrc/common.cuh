@@ -23,6 +23,7 @@
   } while (0)
 
 void ctof_set_last_cuda_error(cudaError_t e, const char* what, const char* file, int line);
+void ctof_set_last_error_text(const char* msg);
 
 __host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
 __host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }

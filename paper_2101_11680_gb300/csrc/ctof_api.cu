@@ -19,6 +19,8 @@ void ctof_set_last_cuda_error(cudaError_t e, const char* what, const char* file,
            cudaGetErrorString(e));
 }
 
+void ctof_set_last_error_text(const char* msg) { snprintf(g_last_error, sizeof(g_last_error), "%s", msg); }
+
 namespace {
 
 struct DeviceGuard {

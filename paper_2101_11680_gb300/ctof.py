@@ -76,6 +76,7 @@ _SIGNATURES = {
     "ctof_reconstruct": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolverParams), _P, ctypes.POINTER(Report), _P]),
     "ctof_reconstruct_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolverParams), _P, ctypes.POINTER(Report),
                                              _P]),
+    "ctof_forward_static": (ctypes.c_int, [_P, _P, _P, _P]),
     "ctof_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "ctof_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(Timing)]),
     "ctof_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -214,6 +215,18 @@ class Kernel:
         _check(self._lib.ctof_forward(self._h, _dev_ptr(mu, self._vol_shape(), "mu"),
                                       _dev_ptr(out, self._meas_shape(), "out"), _stream_handle(stream)),
                "ctof_forward")
+        return out
+
+    def forward_static(self, mu, out, stream=None):
+        """Allocation-free forward operator (scratch in the library's fixed device array).
+
+        For callers that may not allocate device memory at the call site (inside a
+        stream capture, real-time loops, frameworks owning all allocations): the
+        caller supplies `out`; nothing is allocated here or in the library.
+        """
+        _check(self._lib.ctof_forward_static(self._h, _dev_ptr(mu, self._vol_shape(), "mu"),
+                                             _dev_ptr(out, self._meas_shape(), "out"), _stream_handle(stream)),
+               "ctof_forward_static")
         return out
 
     def adjoint(self, m, out=None, stream=None):
