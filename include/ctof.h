@@ -51,6 +51,7 @@ typedef enum {
 enum { CTOF_LINEAR = 0, CTOF_CIRCULAR = 1 };
 enum { CTOF_SOLVER_ADMM_TV = 0, CTOF_SOLVER_TIKHONOV = 1 };
 enum { CTOF_KEEP_W = 1 }; /* ctof_build_kernel flag: retain the FP64 kernel table */
+enum { CTOF_FP32 = 0, CTOF_BF16 = 1, CTOF_FP8E4M3 = 2 }; /* contraction precision */
 
 /* Background optics of the homogeneous semi-infinite medium (Section 3,
  * "Analytical approximation"; the diffusion forms are the textbook
@@ -165,6 +166,23 @@ ctof_status ctof_reconstruct(ctof_kernel k, const float* d_m, const ctof_solver_
  * the stream before returning.  Pinned host memory gives the fastest copies. */
 ctof_status ctof_reconstruct_host(ctof_kernel k, const float* h_m, const ctof_solver_params* params,
                                   float* h_mu, ctof_report* report, void* stream);
+
+/* Precision form: Tikhonov reconstruction of `batch` volumes that share the
+ * kernel (the per-frequency regularised inverse of Eq. 7 applied to B
+ * measurements at once).  d_m [batch][nt][ny][nx] -> d_mu [batch][nz][ny][nx].
+ * CTOF_BF16: b = W_hat^T m_hat on BF16 tensor cores with W_hat and m_hat split
+ * into BF16 high and remainder parts (three products, FP32 accumulation);
+ * x0 = C b0 from the high-part product alone, then `refine_steps` steps of
+ * x += C (b - (G + lambda I) x) with C = (G + lambda I)^-1 from the FP64
+ * Cholesky factor (stored FP32).  CTOF_FP32: the plain FP32 per-volume path
+ * (ctof_reconstruct with CTOF_SOLVER_TIKHONOV) for comparison.  CTOF_FP8E4M3:
+ * EUNSUPPORTED (not built).  lambda = lambda_rel * gram_max_diag; *lambda_out
+ * (optional) receives it.  The first BF16 call builds the BF16 tables (2 x 2
+ * bytes per W_hat entry); the batch workspace (spectra of batch x nt planes)
+ * is allocated on first use and kept.  Asynchronous. */
+ctof_status ctof_reconstruct_batch_tikhonov(ctof_kernel k, int batch, const float* d_m, int precision,
+                                            int refine_steps, double lambda_rel, float* d_mu,
+                                            double* lambda_out, void* stream);
 
 /* m = A mu like ctof_forward, but allocation-free: every intermediate lives in
  * one fixed 32 MiB array inside the library image instead of the handle's

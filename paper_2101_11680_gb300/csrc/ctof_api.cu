@@ -348,6 +348,9 @@ void ctof_kernel_destroy(ctof_kernel k) {
   DeviceGuard guard(k->device);
   if (k->graph) cudaGraphExecDestroy(k->graph);
   destroy_events(k);
+  if (k->d_qhi) cudaFree(k->d_qhi);
+  if (k->d_bt_cinv) cudaFree(k->d_bt_cinv);
+  if (k->d_batch) cudaFree(k->d_batch);
   if (k->d_tik_chol) cudaFree(k->d_tik_chol);
   if (k->d_w) cudaFree(k->d_w);
   if (k->d_base) cudaFree(k->d_base);
@@ -560,6 +563,59 @@ ctof_status ctof_reconstruct_host(ctof_kernel k, const float* h_m, const ctof_so
   if (report) return fill_report(k, params, lambda, report, st);
   CTOF_CUDA_TRY(cudaStreamSynchronize(st));
   return CTOF_OK;
+}
+
+ctof_status ctof_reconstruct_batch_tikhonov(ctof_kernel k, int batch, const float* d_m, int precision,
+                                            int refine_steps, double lambda_rel, float* d_mu, double* lambda_out,
+                                            void* stream) {
+  if (!k || !d_m || !d_mu || batch < 1 || batch > 4096) return CTOF_EINVAL;
+  if (refine_steps < 0 || refine_steps > 8 || !finite_pos(lambda_rel)) return CTOF_EINVAL;
+  if (precision != CTOF_FP32 && precision != CTOF_BF16 && precision != CTOF_FP8E4M3) return CTOF_EINVAL;
+  if (precision == CTOF_FP8E4M3) return CTOF_EUNSUPPORTED;
+  if (precision == CTOF_BF16 && batch_tikhonov_smem_bytes(k->nt, k->nz) > 227 * 1024) return CTOF_EUNSUPPORTED;
+  DeviceGuard g(k->device);
+  if (!g.ok) return CTOF_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const double lambda = lambda_rel * k->gram_max;
+  if (lambda_out) *lambda_out = lambda;
+  const size_t mvol = (size_t)k->nt * k->n * k->n, xvol = (size_t)k->nz * k->n * k->n;
+  if (precision == CTOF_FP32) {
+    // the plain FP32 path, one volume at a time (comparison baseline)
+    ctof_solver_params prm{};
+    prm.solver = CTOF_SOLVER_TIKHONOV;
+    prm.tik_lambda_rel = lambda_rel;
+    for (int b = 0; b < batch; ++b) {
+      double lam = 0.0;
+      CTOF_CUDA_TRY(cudaMemcpyAsync(k->d_mstage, d_m + b * mvol, mvol * sizeof(float), cudaMemcpyDeviceToDevice, st));
+      CTOF_TRY(tikhonov_run(k, &prm, st, &lam));
+      CTOF_CUDA_TRY(cudaMemcpyAsync(d_mu + b * xvol, k->d_vstage, xvol * sizeof(float), cudaMemcpyDeviceToDevice, st));
+    }
+    return CTOF_OK;
+  }
+  const int ldm = ctof_round_up(batch * k->nt, 8), ldx = ctof_round_up(batch * k->nz, 8);
+  const size_t b_sm = (size_t)k->nf * ldm * sizeof(float2), b_sx = (size_t)k->nf * ldx * sizeof(float2);
+  const size_t b_in = (size_t)batch * (k->nt > k->nz ? k->nt : k->nz) * k->n * k->hp * sizeof(float2);
+  const size_t need = ((b_sm + 255) & ~(size_t)255) + ((b_sx + 255) & ~(size_t)255) + b_in;
+  if (need > k->batch_bytes) {
+    CTOF_CUDA_TRY(cudaStreamSynchronize(st));
+    if (k->d_batch) cudaFree(k->d_batch);
+    k->d_batch = nullptr;
+    k->batch_bytes = 0;
+    if (cudaMalloc(&k->d_batch, need) != cudaSuccess) {
+      cudaGetLastError();
+      k->d_batch = nullptr;
+      return CTOF_ENOMEM;
+    }
+    k->batch_bytes = need;
+  }
+  char* base = static_cast<char*>(k->d_batch);
+  float2* spec_m = reinterpret_cast<float2*>(base);
+  float2* spec_x = reinterpret_cast<float2*>(base + ((b_sm + 255) & ~(size_t)255));
+  float2* inter = reinterpret_cast<float2*>(base + ((b_sm + 255) & ~(size_t)255) + ((b_sx + 255) & ~(size_t)255));
+  CTOF_TRY(fft_forward_planes(k, d_m, batch * k->nt, k->n, k->n, k->n, inter, spec_m, ldm, st));
+  CTOF_TRY(batch_tikhonov_prepare(k, lambda, st));
+  CTOF_TRY(batch_tikhonov_contract(k, batch, spec_m, ldm, spec_x, ldx, refine_steps, st));
+  return fft_inverse_planes(k, spec_x, ldx, batch * k->nz, k->n, k->n, inter, d_mu, k->n, st);
 }
 
 ctof_status ctof_set_timing(ctof_kernel k, int enable) {

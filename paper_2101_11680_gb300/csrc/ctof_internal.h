@@ -74,6 +74,15 @@ struct ctof_kernel_s {
   int timing;
   int n_events;
   cudaEvent_t* events;
+
+  // precision form (batched Tikhonov): BF16 split tables, FP32 factors, batch workspace
+  void* d_qhi;         // [nclass][nt][zs] bf16 (zs = 16/32/64)
+  void* d_qlo;         // same, the BF16 remainder
+  float* d_bt_cinv;    // [nclass][nz][z4] (G + lambda I)^-1
+  float* d_bt_glam;    // [nclass][nz][z4] G + lambda I
+  double bt_lambda;
+  void* d_batch;       // batch spectra + row intermediates (one allocation)
+  size_t batch_bytes;
 };
 
 // ---- fft.cu -------------------------------------------------------------
@@ -110,6 +119,12 @@ ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const flo
 ctof_status contract_tikhonov(const ctof_kernel_s* k, const double* chol, const float2* m_hat,
                               float2* x_hat, cudaStream_t st);
 size_t contract_admm_smem_bytes(int nt, int nz, int nbuf);
+
+// ---- batch_tikhonov.cu ----------------------------------------------------
+size_t batch_tikhonov_smem_bytes(int nt, int nz);
+ctof_status batch_tikhonov_prepare(ctof_kernel_s* k, double lambda, cudaStream_t st);
+ctof_status batch_tikhonov_contract(const ctof_kernel_s* k, int batch, const float2* m_hat, int ldm,
+                                    float2* x_hat, int ldx, int refine, cudaStream_t st);
 
 // ---- build.cu ----------------------------------------------------------
 ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st);

@@ -16,6 +16,7 @@ OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -
 LINEAR, CIRCULAR = 0, 1
 SOLVER_ADMM_TV, SOLVER_TIKHONOV = 0, 1
 KEEP_W = 1
+FP32, BF16, FP8E4M3 = 0, 1, 2
 
 
 class Optics(ctypes.Structure):
@@ -77,6 +78,8 @@ _SIGNATURES = {
     "ctof_reconstruct_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolverParams), _P, ctypes.POINTER(Report),
                                              _P]),
     "ctof_forward_static": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ctof_reconstruct_batch_tikhonov": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
+                                                       ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double), _P]),
     "ctof_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "ctof_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(Timing)]),
     "ctof_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -248,6 +251,19 @@ class Kernel:
                                           ctypes.byref(rep) if report else None, _stream_handle(stream)),
                "ctof_reconstruct")
         return (out, rep) if report else out
+
+    def reconstruct_batch_tikhonov(self, m, precision=BF16, refine=2, lambda_rel=1e-3, out=None, stream=None):
+        """Tikhonov for a batch m [B][nt][n][n] (device); returns (mu [B][nz][n][n], lambda)."""
+        import torch
+        b = int(m.shape[0])
+        if out is None:
+            out = torch.empty((b,) + self._vol_shape(), device=m.device, dtype=torch.float32)
+        lam = ctypes.c_double()
+        _check(self._lib.ctof_reconstruct_batch_tikhonov(
+            self._h, b, _dev_ptr(m, (b,) + self._meas_shape(), "m"), int(precision), int(refine),
+            float(lambda_rel), _dev_ptr(out, (b,) + self._vol_shape(), "out"), ctypes.byref(lam),
+            _stream_handle(stream)), "ctof_reconstruct_batch_tikhonov")
+        return out, lam.value
 
     def reconstruct_host(self, m_host, params, out_host, report=False, stream=None):
         """Host-buffer variant: m_host / out_host are CPU float32 tensors (pinned for speed)."""
