@@ -69,9 +69,9 @@ typedef struct {
  * [-(n-1), n-1], FFT size P = max(32, smallest power of two >= 2n)) or
  * CTOF_CIRCULAR (periodic, P = n, n a power of two).  Limits:
  * 4 <= nx <= 256 (linear), 32 <= nx <= 512 (circular), 1 <= nz <= 64,
- * 1 <= nt <= 1024, and one frequency class (nt x nz FP32 block plus its
- * vectors) must fit in the 227 KB of shared memory of one CTA: about
- * nt * (nz + 1) <= 40000 (nt <= 600 at nz = 64, nt <= 1024 at nz = 32). */
+ * 1 <= nt <= 1024, and one frequency class (its nt x nz block, H^-1 block
+ * and vectors) must fit in the 227 KB of shared memory of one CTA: e.g.
+ * nt <= 512 at nz = 64, nt <= 896 at nz = 32 (EUNSUPPORTED beyond). */
 typedef struct {
   int nx, ny, nz, nt;
   double dx_mm, dy_mm, dz_mm;

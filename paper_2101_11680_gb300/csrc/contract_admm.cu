@@ -133,7 +133,7 @@ __global__ void __launch_bounds__(AD_THREADS, 1) k_contract_admm(
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, tg = lane & 3;  // MMA fragment coordinates
   const int nt = L.nt, nz = L.nz, zp = L.zp;
-  float* s_part = sm + L.off_part;                               // [AD_WARPS][zm][8]
+  float* s_part = sm + L.off_part;                               // [AD_WARPS][zm][8], aliases s_ch/s_cl
   float* s_b = sm + L.off_b;                                     // [zm][8]
   unsigned* s_ch = reinterpret_cast<unsigned*>(sm + L.off_ch);   // [tm][8] c_hat hi (TF32 bits)
   unsigned* s_cl = reinterpret_cast<unsigned*>(sm + L.off_cl);   // [tm][8] c_hat lo
@@ -204,6 +204,7 @@ __global__ void __launch_bounds__(AD_THREADS, 1) k_contract_admm(
           }
         }
       }
+      __syncthreads();  // the partial sums overwrite the split c_hat operands
 #pragma unroll
       for (int mt = 0; mt < 4; ++mt) {
         if (mt < mtiles_z) {
@@ -300,12 +301,14 @@ AdmmLayout make_layout(int nt, int nz, int nbuf) {
   L.off_s = L.off_c + ((4 * L.ntp * 2 + 3) & ~3);
   L.off_x = L.off_s + 4 * L.z4 * 2;
   L.buf_floats = L.off_x + 4 * L.z4 * 2;
+  // the adjoint's split c_hat operands and its per-warp partial sums share one region
   L.off_ch = nbuf * L.buf_floats;
   L.off_cl = L.off_ch + L.tm * 8;
-  L.off_xh = L.off_cl + L.tm * 8;
+  L.off_part = L.off_ch;
+  const int shared_region = L.tm * 16 > AD_WARPS * L.zm * 8 ? L.tm * 16 : AD_WARPS * L.zm * 8;
+  L.off_xh = L.off_ch + shared_region;
   L.off_xl = L.off_xh + L.zm * 8;
-  L.off_part = L.off_xl + L.zm * 8;
-  L.off_b = L.off_part + AD_WARPS * L.zm * 8;
+  L.off_b = L.off_xl + L.zm * 8;
   L.total_floats = L.off_b + L.zm * 8;
   return L;
 }
