@@ -39,6 +39,10 @@ CONFIGS = {
                  workload="precision form: 256x256 scan @0.5 mm, 256x256x64 voxels (0.5 mm), 512 bins x 25 ps, "
                           "2 spheres (r 1.5 mm, depths 5 and 9 mm), Poisson peak 1e4, batched Tikhonov "
                           "(lambda 1e-3 max diag), BF16 tensor-core contraction + 2 refinement steps"),
+    "cfg4": dict(n=0, nz=0, nt=0, dx=0.5, dz=0.5, z_first=0.5, dt=25.0, iters=50, peak=1e5, count=64,
+                 workload="batching form: 64 ADMM problems (50 iterations, FP32), lateral in {32,64,128,256}^2 at "
+                          "0.5 mm, depth 16-64 x 0.5 mm, bins 64-512 x 25 ps, musp' U[0.5,2], mua U[0.005,0.02] "
+                          "(seed 0), 1-8 ellipsoids/tubes, Poisson peak 1e5"),
     "cfg1": dict(n=32, nz=16, nt=64, dx=1.0, dz=1.0, z_first=1.0, dt=50.0, iters=100, peak=1e4,
                  workload="32x32 scan @1 mm, 32x32x16 voxels (1-16 mm), 64 bins x 50 ps, 100 ADMM iterations"),
 }
@@ -279,6 +283,76 @@ def run_precision(args, cfg):
     kern.close()
 
 
+def run_batching(args, cfg):
+    """Many uneven ADMM problems: one captured multi-stream graph vs one graph per problem in sequence."""
+    import torch
+    from paper_2101_11680_gb300 import build as B
+    from paper_2101_11680_gb300 import ctof, synth
+
+    torch.cuda.set_device(0)
+    B.build()
+    rng = np.random.default_rng(0)
+    count = args.batch or cfg["count"]
+    kernels, ms, outs, shapes = [], [], [], []
+    t0 = time.perf_counter()
+    for i in range(count):
+        n = int(rng.choice([32, 64, 128, 256]))
+        nz = int(rng.integers(16, 65))
+        nt = int(rng.integers(64, 513))
+        musp = float(rng.uniform(0.5, 2.0))
+        mua = float(rng.uniform(0.005, 0.02))
+        k = ctof.Kernel(ctof.make_optics(mua, musp, 1.4),
+                        ctof.make_grid(n, nz, nt, cfg["dx"], cfg["dz"], cfg["z_first"], cfg["dt"]))
+        mu = synth.phantom_shapes(n, nz, cfg["dx"], cfg["dz"], cfg["z_first"], seed=args.seed + i)
+        clean = k.forward(torch.tensor(mu, dtype=torch.float32, device="cuda")).double().clamp_(min=0)
+        m = torch.tensor(synth.poisson_noise(clean.cpu().numpy(), cfg["peak"], seed=args.seed + 9000 + i),
+                         dtype=torch.float32, device="cuda")
+        kernels.append(k)
+        ms.append(m)
+        outs.append(torch.empty((nz, n, n), device="cuda"))
+        shapes.append((n, nz, nt))
+    build_s = time.perf_counter() - t0
+    params = ctof.admm_params(iters=cfg["iters"])
+    res = {}
+    # batched: one graph over all problems
+    for _ in range(max(1, args.warmup)):
+        ctof.reconstruct_batch(kernels, ms, params, outs=outs)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(args.steps):
+        ctof.reconstruct_batch(kernels, ms, params, outs=outs)
+    e1.record()
+    torch.cuda.synchronize()
+    res["batched"] = e0.elapsed_time(e1) / args.steps
+    batched_out = [o.clone() for o in outs]
+    # sequential: one graph per problem, one after another
+    for k, m, o in zip(kernels, ms, outs):
+        k.reconstruct(m, params, out=o)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        for k, m, o in zip(kernels, ms, outs):
+            k.reconstruct(m, params, out=o)
+    e1.record()
+    torch.cuda.synchronize()
+    res["sequential"] = e0.elapsed_time(e1) / args.steps
+    identical = all(torch.equal(a, b) for a, b in zip(batched_out, outs))
+    tiles = [k.tuning() for k in kernels]
+    line = {"metric": "aggregate volumes/sec, 64 uneven ADMM problems (batching form)",
+            "value": count / (res["batched"] / 1e3), "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": res["batched"], "higher_is_better": True, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": cfg["workload"], "count": count, "kernel_build_s": round(build_s, 1),
+                       "sizes_n_nz_nt": shapes},
+            "sequential": {"value": count / (res["sequential"] / 1e3), "ms_per_round": res["sequential"]},
+            "batched_equals_sequential": identical,
+            "autotuned_plane_tiles": {str(pb): sum(1 for t in tiles for v in t if v == pb) for pb in (4, 8, 16)}}
+    print(json.dumps(line), flush=True)
+    for k in kernels:
+        k.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -294,6 +368,9 @@ def main():
     cfg = dict(CONFIGS[args.config])
     if args.config == "cfg3":
         run_precision(args, cfg)
+        return
+    if args.config == "cfg4":
+        run_batching(args, cfg)
         return
     if args.iters:
         cfg["iters"] = args.iters

@@ -167,6 +167,31 @@ ctof_status ctof_reconstruct(ctof_kernel k, const float* d_m, const ctof_solver_
 ctof_status ctof_reconstruct_host(ctof_kernel k, const float* h_m, const ctof_solver_params* params,
                                   float* h_mu, ctof_report* report, void* stream);
 
+/* Batching form: ADMM reconstructions of `count` independent problems of
+ * uneven sizes and optics (one handle each, distinct handles), d_m[i] ->
+ * d_mu[i] with the layouts of ctof_reconstruct, all with `params`.  The
+ * problems' iteration chains are captured into one CUDA graph, each on its
+ * own forked stream so that they run concurrently; the graph is kept and
+ * replayed while the same handles, buffers and parameters come back (one
+ * cached batch graph per process).  Handles not yet tuned are autotuned first
+ * (see ctof_kernel_autotune), so the first call synchronises and must not be
+ * made inside a stream capture.  The batch must not overlap other calls on
+ * its handles.  Asynchronous after the first call.  Errors: EINVAL (bad or
+ * repeated handle, null buffer, handles on different devices), ECUDA. */
+ctof_status ctof_reconstruct_batch(int count, const ctof_kernel* ks, const float* const* d_m,
+                                   const ctof_solver_params* params, float* const* d_mu, void* stream);
+
+/* Autotuner: times the column-FFT plane tile (4, 8 or 16 planes per tile) for
+ * each of the four column-pass shapes of an ADMM iteration on this handle and
+ * keeps the fastest; the results are bit-identical for every tile, only the
+ * speed changes.  Runs automatically before the first ADMM graph capture of a
+ * handle.  Synchronous; not inside a stream capture. */
+ctof_status ctof_kernel_autotune(ctof_kernel k, void* stream);
+
+/* The tuned plane tiles [T-side forward, T-side inverse, Z-side forward,
+ * Z-side inverse]; EUNSUPPORTED (defaults 8 reported) if not tuned yet. */
+ctof_status ctof_kernel_get_tuning(ctof_kernel k, int* h_pb4);
+
 /* Precision form: Tikhonov reconstruction of `batch` volumes that share the
  * kernel (the per-frequency regularised inverse of Eq. 7 applied to B
  * measurements at once).  d_m [batch][nt][ny][nx] -> d_mu [batch][nz][ny][nx].

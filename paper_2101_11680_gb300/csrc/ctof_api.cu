@@ -7,6 +7,8 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -146,7 +148,7 @@ ctof_status adjoint_impl(ctof_kernel_s* k, const float* m, float* vol, cudaStrea
 }
 
 // ADMM on the staged measurement d_mstage; result (crop of v3) in d_vstage.
-ctof_status admm_enqueue(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st) {
+ctof_status admm_enqueue(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st, bool timed) {
   const int nt = k->nt, nz = k->nz, n = k->n, P = k->p;
   const size_t pp = (size_t)P * P;
   const float inv_s = (float)(1.0 / k->scale);
@@ -164,7 +166,7 @@ ctof_status admm_enqueue(ctof_kernel_s* k, const ctof_solver_params* prm, cudaSt
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_u2a, 0, 3 * nz * pp * sizeof(float), st));
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_u3, 0, nz * pp * sizeof(float), st));
   float* u2[2] = {k->d_u2a, k->d_u2b};
-  cudaEvent_t* ev = k->timing ? k->events : nullptr;
+  cudaEvent_t* ev = (timed && k->timing) ? k->events : nullptr;
   for (int it = 0; it < prm->iters; ++it) {
     const bool last = it == prm->iters - 1;
     if (ev) CTOF_CUDA_TRY(cudaEventRecordWithFlags(ev[4 * it + 0], st, cudaEventRecordExternal));
@@ -215,7 +217,64 @@ ctof_status ensure_events(ctof_kernel_s* k, int count) {
   return CTOF_OK;
 }
 
+// Autotuner: times each column-pass plane tile (4, 8, 16 planes) on the
+// handle's own buffers for the four column-pass shapes of an ADMM iteration
+// and keeps the fastest.  Synchronous; must run outside stream capture.
+ctof_status autotune(ctof_kernel_s* k, cudaStream_t st) {
+  if (k->tuned) return CTOF_OK;
+  const int cands[3] = {4, 8, 16};
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  CTOF_CUDA_TRY(cudaEventCreate(&e0));
+  if (cudaEventCreate(&e1) != cudaSuccess) {
+    cudaEventDestroy(e0);
+    return CTOF_ECUDA;
+  }
+  ctof_status s = CTOF_OK;
+  const int n = k->n, P = k->p;
+  if (cudaMemsetAsync(k->d_inter_t, 0, (size_t)k->nt * n * k->hp * sizeof(float2), st) != cudaSuccess ||
+      cudaMemsetAsync(k->d_inter_z, 0, (size_t)k->nz * P * k->hp * sizeof(float2), st) != cudaSuccess ||
+      cudaMemsetAsync(k->d_spec_t, 0, (size_t)k->nf * k->ldt * sizeof(float2), st) != cudaSuccess ||
+      cudaMemsetAsync(k->d_spec_z2, 0, (size_t)k->nf * k->ldz * sizeof(float2), st) != cudaSuccess)
+    s = CTOF_ECUDA;
+  for (int use = 0; use < 4 && s == CTOF_OK; ++use) {
+    float best_ms = 1e30f;
+    int best = 8;
+    for (int ci = 0; ci < 3 && s == CTOF_OK; ++ci) {
+      const int pb = cands[ci];
+      auto launch = [&]() -> ctof_status {
+        switch (use) {
+          case 0: return fft_cols_forward_pb(k, k->d_inter_t, k->nt, n, k->d_spec_t2, k->ldt, pb, st);
+          case 1: return fft_cols_inverse_pb(k, k->d_spec_t, k->ldt, k->nt, n, k->d_inter_t, pb, st);
+          case 2: return fft_cols_forward_pb(k, k->d_inter_z, k->nz, P, k->d_spec_z, k->ldz, pb, st);
+          default: return fft_cols_inverse_pb(k, k->d_spec_z2, k->ldz, k->nz, P, k->d_inter_z, pb, st);
+        }
+      };
+      s = launch();
+      if (s != CTOF_OK) break;
+      if (cudaEventRecord(e0, st) != cudaSuccess) { s = CTOF_ECUDA; break; }
+      for (int r = 0; r < 3 && s == CTOF_OK; ++r) s = launch();
+      if (s != CTOF_OK) break;
+      float ms = 0.f;
+      if (cudaEventRecord(e1, st) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess ||
+          cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess) {
+        s = CTOF_ECUDA;
+        break;
+      }
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = pb;
+      }
+    }
+    k->tune_pb[use] = best;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (s == CTOF_OK) k->tuned = 1;
+  return s;
+}
+
 ctof_status admm_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st) {
+  CTOF_TRY(autotune(k, st));
   const bool same = k->graph && k->graph_iters == prm->iters && k->graph_rho == prm->rho &&
                     k->graph_beta == prm->tv_beta && k->graph_beta_rel == prm->beta_rel &&
                     k->graph_timing == k->timing;
@@ -233,7 +292,7 @@ ctof_status admm_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream
       cudaStreamDestroy(cap);
       CTOF_CUDA_TRY(e);
     }
-    const ctof_status s = admm_enqueue(k, prm, cap);
+    const ctof_status s = admm_enqueue(k, prm, cap, true);
     e = cudaStreamEndCapture(cap, &g);
     cudaStreamDestroy(cap);
     if (s != CTOF_OK) {
@@ -324,6 +383,107 @@ ctof_status fill_report(ctof_kernel_s* k, const ctof_solver_params* prm, double 
   return bad ? CTOF_ENONFINITE : CTOF_OK;
 }
 
+// One graph per distinct batch (handles, buffers, parameters): every problem's
+// ADMM chain is captured on its own forked stream so that the problems run
+// concurrently on the GPU; the graph is replayed while the batch repeats.
+struct BatchGraph {
+  std::vector<unsigned long long> uids;
+  std::vector<const void*> ptrs;
+  int iters = 0;
+  double rho = 0, beta = 0, beta_rel = 0;
+  cudaGraphExec_t exec = nullptr;
+};
+std::mutex g_batch_mutex;
+BatchGraph g_batch;
+std::vector<cudaStream_t> g_side_streams;
+std::vector<cudaEvent_t> g_side_events;
+
+ctof_status batch_graph_run(int count, const ctof_kernel* ks, const float* const* d_m,
+                            const ctof_solver_params* prm, float* const* d_mu, cudaStream_t st) {
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  std::vector<unsigned long long> uids(count);
+  std::vector<const void*> ptrs(2 * count);
+  for (int i = 0; i < count; ++i) {
+    uids[i] = ks[i]->uid;
+    ptrs[2 * i] = d_m[i];
+    ptrs[2 * i + 1] = d_mu[i];
+  }
+  const bool same = g_batch.exec && g_batch.uids == uids && g_batch.ptrs == ptrs && g_batch.iters == prm->iters &&
+                    g_batch.rho == prm->rho && g_batch.beta == prm->tv_beta && g_batch.beta_rel == prm->beta_rel;
+  if (!same) {
+    if (g_batch.exec) {
+      cudaGraphExecDestroy(g_batch.exec);
+      g_batch.exec = nullptr;
+    }
+    const int nside = count < 32 ? count : 32;
+    while ((int)g_side_streams.size() < nside) {
+      cudaStream_t s2 = nullptr;
+      CTOF_CUDA_TRY(cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking));
+      g_side_streams.push_back(s2);
+    }
+    while ((int)g_side_events.size() < nside + 1) {
+      cudaEvent_t e = nullptr;
+      CTOF_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+      g_side_events.push_back(e);
+    }
+    cudaStream_t cap = nullptr;
+    CTOF_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
+    ctof_status s = e == cudaSuccess ? CTOF_OK : CTOF_ECUDA;
+    if (s == CTOF_OK && cudaEventRecord(g_side_events[nside], cap) != cudaSuccess) s = CTOF_ECUDA;
+    for (int j = 0; j < nside && s == CTOF_OK; ++j)
+      if (cudaStreamWaitEvent(g_side_streams[j], g_side_events[nside], 0) != cudaSuccess) s = CTOF_ECUDA;
+    for (int i = 0; i < count && s == CTOF_OK; ++i) {
+      ctof_kernel_s* k = ks[i];
+      cudaStream_t side = g_side_streams[i % nside];
+      const size_t mb = (size_t)k->nt * k->n * k->n * sizeof(float), vb = (size_t)k->nz * k->n * k->n * sizeof(float);
+      if (cudaMemcpyAsync(k->d_mstage, d_m[i], mb, cudaMemcpyDeviceToDevice, side) != cudaSuccess) s = CTOF_ECUDA;
+      if (s == CTOF_OK) s = admm_enqueue(k, prm, side, false);
+      if (s == CTOF_OK && cudaMemcpyAsync(d_mu[i], k->d_vstage, vb, cudaMemcpyDeviceToDevice, side) != cudaSuccess)
+        s = CTOF_ECUDA;
+    }
+    for (int j = 0; j < nside && s == CTOF_OK; ++j) {
+      if (cudaEventRecord(g_side_events[j], g_side_streams[j]) != cudaSuccess ||
+          cudaStreamWaitEvent(cap, g_side_events[j], 0) != cudaSuccess)
+        s = CTOF_ECUDA;
+    }
+    e = cudaStreamEndCapture(cap, &graph);
+    cudaStreamDestroy(cap);
+    if (s == CTOF_OK && e != cudaSuccess) s = CTOF_ECUDA;
+    if (s == CTOF_OK && cudaGraphInstantiate(&g_batch.exec, graph, 0) != cudaSuccess) {
+      g_batch.exec = nullptr;
+      s = CTOF_ECUDA;
+    }
+    if (graph) cudaGraphDestroy(graph);
+    if (s != CTOF_OK) {
+      cudaGetLastError();
+      return s;
+    }
+    g_batch.uids = uids;
+    g_batch.ptrs = ptrs;
+    g_batch.iters = prm->iters;
+    g_batch.rho = prm->rho;
+    g_batch.beta = prm->tv_beta;
+    g_batch.beta_rel = prm->beta_rel;
+    // the handles' own single-problem graphs stay valid: they stage through the
+    // same buffers and are not affected by this graph
+  }
+  CTOF_CUDA_TRY(cudaGraphLaunch(g_batch.exec, st));
+  return CTOF_OK;
+}
+
+void batch_graph_forget(const ctof_kernel_s* k) {
+  std::lock_guard<std::mutex> lock(g_batch_mutex);
+  for (unsigned long long u : g_batch.uids)
+    if (u == k->uid && g_batch.exec) {
+      cudaGraphExecDestroy(g_batch.exec);
+      g_batch.exec = nullptr;
+      g_batch.uids.clear();
+      break;
+    }
+}
+
 }  // namespace
 
 extern "C" {
@@ -346,6 +506,7 @@ const char* ctof_last_error_message(void) { return g_last_error; }
 void ctof_kernel_destroy(ctof_kernel k) {
   if (!k) return;
   DeviceGuard guard(k->device);
+  batch_graph_forget(k);
   if (k->graph) cudaGraphExecDestroy(k->graph);
   destroy_events(k);
   if (k->d_qhi) cudaFree(k->d_qhi);
@@ -385,6 +546,11 @@ ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, 
   k->symmetric = grid->dx_mm == grid->dy_mm;
   k->r_min = optics->clamp_r ? 0.5 * std::min(grid->dx_mm, std::min(grid->dy_mm, grid->dz_mm)) : 0.0;
   k->tik_lambda = -1.0;
+  for (int i = 0; i < 4; ++i) k->tune_pb[i] = 8;
+  {
+    static std::atomic<unsigned long long> next_id{1};
+    k->uid = next_id++;
+  }
 
   std::vector<int> members;
   std::vector<float> lap;
@@ -616,6 +782,37 @@ ctof_status ctof_reconstruct_batch_tikhonov(ctof_kernel k, int batch, const floa
   CTOF_TRY(batch_tikhonov_prepare(k, lambda, st));
   CTOF_TRY(batch_tikhonov_contract(k, batch, spec_m, ldm, spec_x, ldx, refine_steps, st));
   return fft_inverse_planes(k, spec_x, ldx, batch * k->nz, k->n, k->n, inter, d_mu, k->n, st);
+}
+
+ctof_status ctof_kernel_autotune(ctof_kernel k, void* stream) {
+  if (!k) return CTOF_EINVAL;
+  DeviceGuard g(k->device);
+  if (!g.ok) return CTOF_ECUDA;
+  k->tuned = 0;
+  return autotune(k, static_cast<cudaStream_t>(stream));
+}
+
+ctof_status ctof_kernel_get_tuning(ctof_kernel k, int* h_pb4) {
+  if (!k || !h_pb4) return CTOF_EINVAL;
+  for (int i = 0; i < 4; ++i) h_pb4[i] = k->tune_pb[i];
+  return k->tuned ? CTOF_OK : CTOF_EUNSUPPORTED;
+}
+
+ctof_status ctof_reconstruct_batch(int count, const ctof_kernel* ks, const float* const* d_m,
+                                   const ctof_solver_params* params, float* const* d_mu, void* stream) {
+  if (count < 1 || count > 4096 || !ks || !d_m || !d_mu) return CTOF_EINVAL;
+  CTOF_TRY(validate_params(params));
+  if (params->solver != CTOF_SOLVER_ADMM_TV) return CTOF_EINVAL;
+  for (int i = 0; i < count; ++i) {
+    if (!ks[i] || !d_m[i] || !d_mu[i] || ks[i]->device != ks[0]->device) return CTOF_EINVAL;
+    for (int j = 0; j < i; ++j)
+      if (ks[j] == ks[i]) return CTOF_EINVAL;  // a handle's workspace serves one problem at a time
+  }
+  DeviceGuard g(ks[0]->device);
+  if (!g.ok) return CTOF_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  for (int i = 0; i < count; ++i) CTOF_TRY(autotune(ks[i], st));
+  return batch_graph_run(count, ks, d_m, params, d_mu, st);
 }
 
 ctof_status ctof_set_timing(ctof_kernel k, int enable) {

@@ -83,6 +83,11 @@ struct ctof_kernel_s {
   double bt_lambda;
   void* d_batch;       // batch spectra + row intermediates (one allocation)
   size_t batch_bytes;
+
+  // autotuned column-pass plane tiles: [T fwd, T inv, Z fwd, Z inv]
+  int tune_pb[4];
+  int tuned;
+  unsigned long long uid;  // unique per handle (batch graph cache key)
 };
 
 // ---- fft.cu -------------------------------------------------------------
@@ -102,6 +107,10 @@ ctof_status fft_cols_forward(const ctof_kernel_s* k, const float2* inter, int np
                              float2* out, int ldf, cudaStream_t st);
 ctof_status fft_cols_inverse(const ctof_kernel_s* k, const float2* in, int ldf, int nplanes,
                              int rows_out, float2* inter, cudaStream_t st);
+ctof_status fft_cols_forward_pb(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows_in,
+                                float2* out, int ldf, int pb, cudaStream_t st);
+ctof_status fft_cols_inverse_pb(const ctof_kernel_s* k, const float2* in, int ldf, int nplanes,
+                                int rows_out, float2* inter, int pb, cudaStream_t st);
 ctof_status fft_rows_forward(const ctof_kernel_s* k, const float* in, int nplanes, int rows,
                              int cols_in, int ld_in, float2* inter, cudaStream_t st);
 ctof_status fft_rows_inverse(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows,

@@ -8,10 +8,11 @@
 // Two passes per direction:
 //   rows    (x axis, real <-> complex): one warp transforms two real rows packed
 //           as one complex row, then splits them with the Hermitian identities.
-//   columns (y axis, complex): a CTA stages a tile of 4 kx-columns x 8 planes
-//           in shared memory, each warp transforms whole columns, and the tile
-//           is written out transposed so that the frequency-major side moves in
-//           64-byte runs of consecutive planes.
+//   columns (y axis, complex): a CTA stages a tile of 32 columns (32/PB
+//           kx-columns x PB planes) in shared memory, each warp transforms
+//           whole columns, and the tile is written out transposed so that the
+//           frequency-major side moves in runs of PB consecutive planes.  PB is
+//           4, 8 or 16, picked per handle by the autotuner.
 // Each 1-D transform of length P = 32 R lives in one warp: lane l register r
 // holds element l + 32 r; an R-point DIF over registers, a twiddle by
 // w_P^(l k2), and a 32-point DIF across lanes (shuffles) give element
@@ -23,9 +24,9 @@
 
 namespace {
 
-constexpr int KB = 4;          // kx columns per column-pass tile
-constexpr int PB = 8;          // planes per column-pass tile
-constexpr int NC = KB * PB;    // columns per tile
+// Column-pass tiles hold NC = 32 columns: KB kx-columns x PB planes, with
+// PB in {4, 8, 16} chosen per handle and use by the autotuner.
+constexpr int NC = 32;
 constexpr int COL_THREADS = 256;
 constexpr int ROW_WARPS = 8;
 
@@ -271,12 +272,13 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restri
 
 // ------------------------------------------------------------- columns ----
 
-template <int P>
+template <int P, int PB>
 __global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restrict__ inter, int nplanes,
                                                           int rows_in, int h, int hp,
                                                           float2* __restrict__ out, int ldf,
                                                           const float2* __restrict__ tw) {
   constexpr int R = P / 32;
+  constexpr int KB = NC / PB;
   constexpr int LDT = NC + 1;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
@@ -313,12 +315,13 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restri
   }
 }
 
-template <int P>
+template <int P, int PB>
 __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restrict__ in, int ldf, int nplanes,
                                                           int rows_out, int h, int hp,
                                                           float2* __restrict__ inter,
                                                           const float2* __restrict__ tw) {
   constexpr int R = P / 32;
+  constexpr int KB = NC / PB;
   constexpr int LDT = NC + 1;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
@@ -425,30 +428,72 @@ ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* 
   return CTOF_OK;
 }
 
-ctof_status fft_cols_forward(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows_in, float2* out,
-                             int ldf, cudaStream_t st) {
+ctof_status fft_cols_forward_pb(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows_in, float2* out,
+                                int ldf, int pb, cudaStream_t st) {
   if (nplanes <= 0) return CTOF_OK;
   const size_t sm = col_smem(k->p);
-  dim3 grid(ctof_div_up(k->h, KB), ctof_div_up(nplanes, PB));
-  CTOF_P_SWITCH(k->p, {
-    CTOF_CUDA_TRY(allow_smem(k_cols_fwd<P_>, sm));
-    k_cols_fwd<P_><<<grid, COL_THREADS, sm, st>>>(inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
-  });
+  dim3 grid(ctof_div_up(k->h, NC / pb), ctof_div_up(nplanes, pb));
+  switch (pb) {
+    case 4:
+      CTOF_P_SWITCH(k->p, {
+        CTOF_CUDA_TRY(allow_smem(k_cols_fwd<P_, 4>, sm));
+        k_cols_fwd<P_, 4><<<grid, COL_THREADS, sm, st>>>(inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
+      });
+      break;
+    case 16:
+      CTOF_P_SWITCH(k->p, {
+        CTOF_CUDA_TRY(allow_smem(k_cols_fwd<P_, 16>, sm));
+        k_cols_fwd<P_, 16><<<grid, COL_THREADS, sm, st>>>(inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
+      });
+      break;
+    default:
+      CTOF_P_SWITCH(k->p, {
+        CTOF_CUDA_TRY(allow_smem(k_cols_fwd<P_, 8>, sm));
+        k_cols_fwd<P_, 8><<<grid, COL_THREADS, sm, st>>>(inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
+      });
+  }
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status fft_cols_forward(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows_in, float2* out,
+                             int ldf, cudaStream_t st) {
+  const int pb = (nplanes == k->nt) ? k->tune_pb[0] : k->tune_pb[2];
+  return fft_cols_forward_pb(k, inter, nplanes, rows_in, out, ldf, pb, st);
+}
+
+ctof_status fft_cols_inverse_pb(const ctof_kernel_s* k, const float2* in, int ldf, int nplanes, int rows_out,
+                                float2* inter, int pb, cudaStream_t st) {
+  if (nplanes <= 0) return CTOF_OK;
+  const size_t sm = col_smem(k->p);
+  dim3 grid(ctof_div_up(k->h, NC / pb), ctof_div_up(nplanes, pb));
+  switch (pb) {
+    case 4:
+      CTOF_P_SWITCH(k->p, {
+        CTOF_CUDA_TRY(allow_smem(k_cols_inv<P_, 4>, sm));
+        k_cols_inv<P_, 4><<<grid, COL_THREADS, sm, st>>>(in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
+      });
+      break;
+    case 16:
+      CTOF_P_SWITCH(k->p, {
+        CTOF_CUDA_TRY(allow_smem(k_cols_inv<P_, 16>, sm));
+        k_cols_inv<P_, 16><<<grid, COL_THREADS, sm, st>>>(in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
+      });
+      break;
+    default:
+      CTOF_P_SWITCH(k->p, {
+        CTOF_CUDA_TRY(allow_smem(k_cols_inv<P_, 8>, sm));
+        k_cols_inv<P_, 8><<<grid, COL_THREADS, sm, st>>>(in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
+      });
+  }
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
 
 ctof_status fft_cols_inverse(const ctof_kernel_s* k, const float2* in, int ldf, int nplanes, int rows_out,
                              float2* inter, cudaStream_t st) {
-  if (nplanes <= 0) return CTOF_OK;
-  const size_t sm = col_smem(k->p);
-  dim3 grid(ctof_div_up(k->h, KB), ctof_div_up(nplanes, PB));
-  CTOF_P_SWITCH(k->p, {
-    CTOF_CUDA_TRY(allow_smem(k_cols_inv<P_>, sm));
-    k_cols_inv<P_><<<grid, COL_THREADS, sm, st>>>(in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
-  });
-  CTOF_CUDA_TRY(cudaGetLastError());
-  return CTOF_OK;
+  const int pb = (nplanes == k->nt) ? k->tune_pb[1] : k->tune_pb[3];
+  return fft_cols_inverse_pb(k, in, ldf, nplanes, rows_out, inter, pb, st);
 }
 
 ctof_status fft_forward_planes(const ctof_kernel_s* k, const float* in, int nplanes, int rows_in, int cols_in,

@@ -80,6 +80,10 @@ _SIGNATURES = {
     "ctof_forward_static": (ctypes.c_int, [_P, _P, _P, _P]),
     "ctof_reconstruct_batch_tikhonov": (ctypes.c_int, [_P, ctypes.c_int, _P, ctypes.c_int, ctypes.c_int,
                                                        ctypes.c_double, _P, ctypes.POINTER(ctypes.c_double), _P]),
+    "ctof_reconstruct_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
+                                              ctypes.POINTER(SolverParams), ctypes.POINTER(_P), _P]),
+    "ctof_kernel_autotune": (ctypes.c_int, [_P, _P]),
+    "ctof_kernel_get_tuning": (ctypes.c_int, [_P, _P]),
     "ctof_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "ctof_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(Timing)]),
     "ctof_status_string": (ctypes.c_char_p, [ctypes.c_int]),
@@ -140,6 +144,21 @@ def tikhonov_params(lambda_rel=1e-3):
     return SolverParams(SOLVER_TIKHONOV, 1, 1.0, -1.0, 1e-3, float(lambda_rel))
 
 
+def reconstruct_batch(kernels, ms, params, outs=None, stream=None):
+    """ADMM for several problems (one Kernel each) in one captured multi-stream graph."""
+    import torch
+    lib = load()
+    n = len(kernels)
+    if outs is None:
+        outs = [torch.empty(k._vol_shape(), device=m.device, dtype=torch.float32) for k, m in zip(kernels, ms)]
+    hs = (ctypes.c_void_p * n)(*[k._h.value for k in kernels])
+    mp = (ctypes.c_void_p * n)(*[_dev_ptr(m, k._meas_shape(), "m").value for k, m in zip(kernels, ms)])
+    op = (ctypes.c_void_p * n)(*[_dev_ptr(o, k._vol_shape(), "out").value for k, o in zip(kernels, outs)])
+    _check(lib.ctof_reconstruct_batch(n, hs, mp, ctypes.byref(params), op, _stream_handle(stream)),
+           "ctof_reconstruct_batch")
+    return outs
+
+
 class Kernel:
     """A built sensitivity kernel (``ctof_kernel``) bound to the current CUDA device."""
 
@@ -181,6 +200,15 @@ class Kernel:
         if st not in (OK, EUNSUPPORTED):
             _check(st, "ctof_get_timing")
         return t
+
+    def autotune(self, stream=None):
+        _check(self._lib.ctof_kernel_autotune(self._h, _stream_handle(stream)), "ctof_kernel_autotune")
+        return self.tuning()
+
+    def tuning(self):
+        out = (ctypes.c_int * 4)()
+        self._lib.ctof_kernel_get_tuning(self._h, out)
+        return list(out)
 
     # ---- parity accessors (synchronous) ----
     def get_w(self):
