@@ -43,6 +43,11 @@ CONFIGS = {
                  workload="batching form: 64 ADMM problems (50 iterations, FP32), lateral in {32,64,128,256}^2 at "
                           "0.5 mm, depth 16-64 x 0.5 mm, bins 64-512 x 25 ps, musp' U[0.5,2], mua U[0.005,0.02] "
                           "(seed 0), 1-8 ellipsoids/tubes, Poisson peak 1e5"),
+    "cfg5": dict(n=128, nz=48, nt=256, dx=0.5, dz=0.5, z_first=0.5, dt=25.0, iters=100, peak=1e5,
+                 workload="learned form: 10-stage unrolled proximal gradient, 3-D CNN prox (4 conv 3x3x3, 16 ch, "
+                          "BF16, FP32 accumulate) on 128x128x48 voxels (0.5 mm), 256 bins x 25 ps, 1-8 random "
+                          "ellipsoids/tubes (seeds from 10000), Poisson peak 1e5; ADMM fallback when the data "
+                          "residual exceeds 1.5x the ADMM calibration residual"),
     "cfg1": dict(n=32, nz=16, nt=64, dx=1.0, dz=1.0, z_first=1.0, dt=50.0, iters=100, peak=1e4,
                  workload="32x32 scan @1 mm, 32x32x16 voxels (1-16 mm), 64 bins x 50 ps, 100 ADMM iterations"),
 }
@@ -353,6 +358,115 @@ def run_batching(args, cfg):
         k.close()
 
 
+def run_learned(args, cfg):
+    """Learned unrolled solver vs plain FP32 ADMM (100 iterations) on the same seeded volumes.
+
+    The timed step is one volume through the learned solver plus its data-residual
+    check; volumes whose residual exceeds the fallback threshold are then
+    reconstructed by ADMM inside the same timed region.
+    """
+    import torch
+    from paper_2101_11680_gb300 import build as B
+    from paper_2101_11680_gb300 import ctof
+    from paper_2101_11680_gb300 import learned_train as LT
+
+    torch.cuda.set_device(0)
+    B.build()
+    theta, stages, meta = LT.load()
+    g = {k: cfg[k] for k in ("n", "nz", "nt", "dx", "dz", "z_first", "dt")}
+    kern = LT.make_kernel(g)
+    net = LT.make_net(theta, stages, meta)
+    params = ctof.admm_params(iters=cfg["iters"])
+    # fallback threshold from a calibration set (seeds 9000..9007)
+    calib = LT.eval_set(kern, g, range(9000, 9008), cfg["peak"])
+    calib_res = [LT.data_residual(kern, kern.reconstruct(m, params), m) for m, _ in calib]
+    threshold = 1.5 * float(np.median(calib_res))
+    count = args.steps
+    data = LT.eval_set(kern, g, range(10000, 10000 + count + args.warmup), cfg["peak"])
+    ms = torch.stack([m for m, _ in data])
+    outs = torch.empty((len(data), cfg["nz"], cfg["n"], cfg["n"]), device="cuda")
+    res = torch.empty(len(data), device="cuda", dtype=torch.float64)
+    m_norm = torch.stack([m.double().norm() for m, _ in data])
+    pred = torch.empty((cfg["nt"], cfg["n"], cfg["n"]), device="cuda")
+
+    def learned_pass(lo, hi):
+        for i in range(lo, hi):
+            net.reconstruct(kern, ms[i:i + 1], out=outs[i:i + 1])
+            kern.forward(outs[i], out=pred)
+            res[i] = (pred.double() - ms[i].double()).norm() / m_norm[i]
+        r = res[lo:hi].cpu()
+        fb = [lo + j for j in range(hi - lo) if not (float(r[j]) <= threshold)]
+        for i in fb:
+            kern.reconstruct(ms[i], params, out=outs[i])
+        return fb
+
+    learned_pass(count, count + args.warmup)
+    torch.cuda.synchronize()
+    clocks = ClockSampler(0)
+    clocks.start()
+    time.sleep(0.3)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record()
+    torch.cuda.nvtx.range_push("learned_timed")
+    fallback = learned_pass(0, count)
+    torch.cuda.nvtx.range_pop()
+    e1.record()
+    torch.cuda.synchronize()
+    t_learned = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    learned_res = [float(r) for r in res[:count].cpu()]
+    learned_err = [LT.volume_error(outs[i], data[i][1]) for i in range(count)]
+    # plain ADMM on the same volumes
+    adm = torch.empty_like(outs[0])
+    kern.reconstruct(ms[0], params, out=adm)
+    torch.cuda.synchronize()
+    admm_err, admm_res, t_admm = [], [], 0.0
+    for i in range(count):
+        e0.record()
+        kern.reconstruct(ms[i], params, out=adm)
+        e1.record()
+        torch.cuda.synchronize()
+        t_admm += e0.elapsed_time(e1)
+        admm_err.append(LT.volume_error(adm, data[i][1]))
+        admm_res.append(LT.data_residual(kern, adm, ms[i]))
+    # end to end from pinned host measurements (learned path + residual check, results read back)
+    mh = ms[:count].cpu().pin_memory()
+    oh = torch.empty((count, cfg["nz"], cfg["n"], cfg["n"])).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for i in range(count):
+        ms[i].copy_(mh[i], non_blocking=True)
+    learned_pass(0, count)
+    for i in range(count):
+        oh[i].copy_(outs[i], non_blocking=True)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    value = count / (t_learned / 1e3)
+    line = {"metric": "volumes/sec at 128x128x48 (256 bins), learned unrolled solver with ADMM fallback, vs plain "
+                      "FP32 ADMM on the same volumes",
+            "value": value, "unit": UNIT, "n_gpus": 1, "steps": count, "warmup": args.warmup,
+            "ms_per_step": t_learned / count, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": cfg["workload"], "stages": stages, "trained_on": meta.get("grid"),
+                       "x0": "Tikhonov (lambda %g max Gram diag)" % meta.get("x0_lambda_rel", 0.0),
+                       "data_consistency_steps": LT.DC_STEPS, "dc_lambda_rel": LT.DC_LAMBDA,
+                       "training_phantoms": meta.get("phantoms"),
+                       "l2": "inputs larger than L2 (W_hat %.0f MB streamed per operator application)"
+                             % (kern.info.n_class * cfg["nt"] * cfg["nz"] * 4 / 1e6)},
+            "admm": {"value": count / (t_admm / 1e3), "ms_per_volume": t_admm / count,
+                     "volume_error_mean": float(np.mean(admm_err)), "residual_mean": float(np.mean(admm_res))},
+            "learned": {"volume_error_mean": float(np.mean(learned_err)), "residual_mean": float(np.mean(learned_res)),
+                        "fallback_threshold": threshold, "fallback_rate": len(fallback) / count},
+            "speedup_vs_admm": (count / (t_learned / 1e3)) / (count / (t_admm / 1e3)),
+            "e2e": {"value": count / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(ms[0].numel() * 4),
+                    "d2h_bytes_per_step": int(outs[0].numel() * 4)},
+            "clocks": clk}
+    print(json.dumps(line), flush=True)
+    net.close()
+    kern.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,6 +485,9 @@ def main():
         return
     if args.config == "cfg4":
         run_batching(args, cfg)
+        return
+    if args.config == "cfg5":
+        run_learned(args, cfg)
         return
     if args.iters:
         cfg["iters"] = args.iters

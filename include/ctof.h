@@ -167,6 +167,49 @@ ctof_status ctof_reconstruct(ctof_kernel k, const float* d_m, const ctof_solver_
 ctof_status ctof_reconstruct_host(ctof_kernel k, const float* h_m, const ctof_solver_params* params,
                                   float* h_mu, ctof_report* report, void* stream);
 
+/* Learned form (the paper has no learned component; this is an added
+ * reconstruction option): an unrolled proximal-gradient solver with S stages
+ *   g_s = A_n^T (A_n x_s - m_n),  z_s = x_s - eta_s g_s,
+ *   x_{s+1} = z_s + mu0 f(z_s / mu0),
+ * with A_n = A / scale, m_n = m / scale, mu0 = 0.01/mm, and f a 3-D CNN
+ * shared by all stages: conv(1->16)+b, ReLU, conv(16->16)+b, ReLU,
+ * conv(16->16)+b, ReLU, conv(16->1)+b, 3x3x3 taps, zero padding.  BF16
+ * activations and weights, FP32 accumulation, FP32 masters.
+ * x_0 is 0, or the per-frequency Tikhonov solution of m (options).  At
+ * inference only, `dc_steps` data-consistency steps follow the last stage:
+ *   x <- x - T(A x - m),  T = the per-frequency Tikhonov solve,
+ * which remove what the data contradicts from the network's output (training
+ * does not differentiate through them).
+ * Parameters are a flat float array of ctof_learned_param_count(S) values:
+ * w1 [16][1][27], b1 [16], w2 [16][16][27], b2 [16], w3 [16][16][27], b3 [16],
+ * w4 [1][16][27], b4 [1], eta [S]; tap index (dz+1)*9 + (dy+1)*3 + (dx+1).
+ * The kernel handle's lateral size must be a multiple of 16.  Loss (training):
+ * mean over voxels of ((x_S - mu)/mu0)^2.  Batches are [batch][...] stacks of
+ * the usual layouts.  A handle owns its workspace; not re-entrant. */
+typedef struct ctof_learned_s* ctof_learned;
+typedef struct {
+  double x0_lambda_rel; /* > 0: x_0 = Tikhonov solution, lambda = x0_lambda_rel * max Gram diagonal; 0: x_0 = 0 */
+  int dc_steps;         /* data-consistency steps after the last stage at inference (>= 0) */
+  double dc_lambda_rel; /* relative Tikhonov lambda of those steps (> 0 when dc_steps > 0) */
+} ctof_learned_options;
+int ctof_learned_param_count(int stages);
+/* opt may be NULL (x_0 = 0, no data-consistency steps). */
+ctof_status ctof_learned_create(int stages, const float* h_params, const ctof_learned_options* opt,
+                                ctof_learned* out);
+void ctof_learned_destroy(ctof_learned net);
+ctof_status ctof_learned_get_params(ctof_learned net, float* h_params);
+/* Loss and its gradient w.r.t. the flat parameters for a batch (synchronous). */
+ctof_status ctof_learned_loss_grad(ctof_learned net, ctof_kernel k, int batch, const float* d_m,
+                                   const float* d_mu, double* h_loss, float* h_grad, void* stream);
+/* One Adam step (beta 0.9 / 0.999, eps 1e-8) on a batch; *h_loss (optional,
+ * synchronising) receives the batch loss before the step. */
+ctof_status ctof_learned_train_step(ctof_learned net, ctof_kernel k, int batch, const float* d_m,
+                                    const float* d_mu, double lr, double* h_loss, void* stream);
+/* Inference (stages, then the data-consistency steps):
+ * d_m [batch][nt][n][n] -> d_mu [batch][nz][n][n].  Asynchronous. */
+ctof_status ctof_learned_reconstruct(ctof_learned net, ctof_kernel k, int batch, const float* d_m,
+                                     float* d_mu, void* stream);
+
 /* Batching form: ADMM reconstructions of `count` independent problems of
  * uneven sizes and optics (one handle each, distinct handles), d_m[i] ->
  * d_mu[i] with the layouts of ctof_reconstruct, all with `params`.  The

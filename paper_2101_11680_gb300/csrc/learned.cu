@@ -1,0 +1,722 @@
+// Learned form: an unrolled proximal-gradient solver whose proximal step is a
+// small 3-D CNN, trained on the GPU by this file's own forward and backward
+// kernels (no cuDNN/cuBLAS).  Stages s = 0..S-1 from x_0 = 0, or from the
+// per-frequency Tikhonov solution T m of the measurement (the library's
+// Tikhonov solver, lambda = x0_lambda_rel * max Gram diagonal):
+//   g_s     = A_n^T (A_n x_s - m_n)          (the library's forward/adjoint, A_n = A/scale)
+//   z_s     = x_s - eta_s g_s
+//   x_{s+1} = z_s + mu0 f(z_s / mu0)
+// f = conv(1->16)+b, ReLU, conv(16->16)+b, ReLU, conv(16->16)+b, ReLU,
+// conv(16->1)+b; 3x3x3 taps, zero padding on each N x N x Z volume; weights
+// shared across stages; loss mean(((x_S - mu)/mu0)^2); Adam on FP32 masters.
+// Inference may end with data-consistency steps x <- x - T(A x - m).
+//
+// Activations are BF16, channels-last ([voxel][16]); every layer runs as a
+// 16 -> 16 convolution (the single input / output channel of the first and
+// last layers padded with zero weights) on warp-level m16n8k16 BF16 MMAs with
+// FP32 accumulation: one warp computes 16 voxels along x x 16 output channels,
+// K = 27 taps x 16 input channels.  The data gradient is the same kernel with
+// flipped taps and transposed channels; the weight gradient is a K = voxels
+// MMA reduction with per-CTA partial sums.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+
+#include <new>
+#include <vector>
+
+#include "ctof_internal.h"
+
+namespace {
+
+constexpr int CH = 16;
+constexpr float MU0 = 0.01f;
+constexpr int NLAYER = 4;
+const int LAYER_IN[NLAYER] = {1, CH, CH, CH};
+const int LAYER_OUT[NLAYER] = {CH, CH, CH, 1};
+
+__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+__device__ __forceinline__ unsigned relu2(unsigned v) {
+  __nv_bfloat162 h = *reinterpret_cast<__nv_bfloat162*>(&v);
+  h = __hmax2(h, __floats2bfloat162_rn(0.f, 0.f));
+  return *reinterpret_cast<unsigned*>(&h);
+}
+__device__ __forceinline__ unsigned pack2(__nv_bfloat16 lo, __nv_bfloat16 hi) {
+  __nv_bfloat162 h;
+  h.x = lo;
+  h.y = hi;
+  return *reinterpret_cast<unsigned*>(&h);
+}
+
+struct Geo {
+  int b, z, y, x;  // batch, depth, rows, columns (x % 16 == 0)
+};
+
+// Voxel index of (v's row + offsets) or -1 outside the volume.
+__device__ __forceinline__ long long neighbour(const Geo& G, int bb, int zz, int yy, int xx) {
+  if (zz < 0 || zz >= G.z || yy < 0 || yy >= G.y || xx < 0 || xx >= G.x) return -1;
+  return (((long long)bb * G.z + zz) * G.y + yy) * G.x + xx;
+}
+
+// out[v][co] = bias[co] + sum_tap sum_ci W[tap][co][ci] act(in[v + off(tap)][ci]),
+// act = ReLU if relu_in; then out *= (mask[v][co] > 0) if mask.
+__global__ void __launch_bounds__(256) k_conv3d(const __nv_bfloat16* __restrict__ in, int relu_in,
+                                                const __nv_bfloat16* __restrict__ w,
+                                                const float* __restrict__ bias,
+                                                const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ out,
+                                                Geo G) {
+  __shared__ unsigned s_w[27 * CH * CH / 2];
+  for (int i = threadIdx.x; i < 27 * CH * CH / 2; i += blockDim.x) s_w[i] = reinterpret_cast<const unsigned*>(w)[i];
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tg = lane & 3;
+  const long long xchunks = G.x / 16;
+  const long long job = (long long)blockIdx.x * 8 + warp;
+  const long long rows = (long long)G.b * G.z * G.y;
+  if (job >= rows * xchunks) return;
+  const long long row = job / xchunks;
+  const int x0 = (int)(job - row * xchunks) * 16;
+  const int yy = (int)(row % G.y);
+  const int zz = (int)((row / G.y) % G.z);
+  const int bb = (int)(row / ((long long)G.y * G.z));
+  float acc[2][4] = {};
+  const unsigned* inw = reinterpret_cast<const unsigned*>(in);  // [voxel][8] bf16 pairs
+  for (int tap = 0; tap < 27; ++tap) {
+    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+    const long long va = neighbour(G, bb, zz + dz, yy + dy, x0 + g + dx);
+    const long long vb = neighbour(G, bb, zz + dz, yy + dy, x0 + g + 8 + dx);
+    unsigned a[4];
+    a[0] = va >= 0 ? inw[va * 8 + tg] : 0u;
+    a[1] = vb >= 0 ? inw[vb * 8 + tg] : 0u;
+    a[2] = va >= 0 ? inw[va * 8 + tg + 4] : 0u;
+    a[3] = vb >= 0 ? inw[vb * 8 + tg + 4] : 0u;
+    if (relu_in) {
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = relu2(a[i]);
+    }
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int co = nt * 8 + g;
+      const unsigned b0 = s_w[(tap * CH + co) * 8 + tg];
+      const unsigned b1 = s_w[(tap * CH + co) * 8 + tg + 4];
+      mma_bf16(acc[nt], a, b0, b1);
+    }
+  }
+  const long long v0 = neighbour(G, bb, zz, yy, x0 + g), v1 = v0 + 8;
+  unsigned* outw = reinterpret_cast<unsigned*>(out);
+  const unsigned* maskw = reinterpret_cast<const unsigned*>(mask);
+#pragma unroll
+  for (int nt = 0; nt < 2; ++nt) {
+    const int co = nt * 8 + 2 * tg;
+    float r0 = acc[nt][0], r1 = acc[nt][1], r2 = acc[nt][2], r3 = acc[nt][3];
+    if (bias) {
+      r0 += bias[co];
+      r1 += bias[co + 1];
+      r2 += bias[co];
+      r3 += bias[co + 1];
+    }
+    if (mask) {
+      const unsigned m0 = maskw[v0 * 8 + (co >> 1)], m1 = maskw[v1 * 8 + (co >> 1)];
+      const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&m0));
+      const float2 f1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&m1));
+      r0 = f0.x > 0.f ? r0 : 0.f;
+      r1 = f0.y > 0.f ? r1 : 0.f;
+      r2 = f1.x > 0.f ? r2 : 0.f;
+      r3 = f1.y > 0.f ? r3 : 0.f;
+    }
+    outw[v0 * 8 + (co >> 1)] = pack2(__float2bfloat16_rn(r0), __float2bfloat16_rn(r1));
+    outw[v1 * 8 + (co >> 1)] = pack2(__float2bfloat16_rn(r2), __float2bfloat16_rn(r3));
+  }
+}
+
+// Per-CTA partial weight gradients: part[blk][tap][co][ci] = sum over this CTA's
+// voxels of dy[v][co] act(x[v + off(tap)][ci]).  Warp w owns taps w, w+8, w+16, w+24.
+constexpr int WG_ROWS = 16;  // (b, z, y) rows per CTA
+__global__ void __launch_bounds__(256) k_wgrad(const __nv_bfloat16* __restrict__ dy, const __nv_bfloat16* __restrict__ x,
+                                               int relu_in, Geo G, float* __restrict__ part) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tg = lane & 3;
+  const long long rows = (long long)G.b * G.z * G.y;
+  const long long r0 = (long long)blockIdx.x * WG_ROWS;
+  float acc[4][2][4] = {};
+  const __nv_bfloat16* dyb = dy;
+  for (long long row = r0; row < r0 + WG_ROWS && row < rows; ++row) {
+    const int yy = (int)(row % G.y);
+    const int zz = (int)((row / G.y) % G.z);
+    const int bb = (int)(row / ((long long)G.y * G.z));
+    for (int x0 = 0; x0 < G.x; x0 += 16) {
+      const long long vb = neighbour(G, bb, zz, yy, x0);
+      // A = dy^T: rows co, cols the 16 voxels
+      unsigned a[4];
+      a[0] = pack2(dyb[(vb + 2 * tg) * CH + g], dyb[(vb + 2 * tg + 1) * CH + g]);
+      a[1] = pack2(dyb[(vb + 2 * tg) * CH + g + 8], dyb[(vb + 2 * tg + 1) * CH + g + 8]);
+      a[2] = pack2(dyb[(vb + 2 * tg + 8) * CH + g], dyb[(vb + 2 * tg + 9) * CH + g]);
+      a[3] = pack2(dyb[(vb + 2 * tg + 8) * CH + g + 8], dyb[(vb + 2 * tg + 9) * CH + g + 8]);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int tap = warp + 8 * j;
+        if (tap >= 27) break;
+        const int dz = tap / 9 - 1, dy_ = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
+        const long long n0 = neighbour(G, bb, zz + dz, yy + dy_, x0 + 2 * tg + dx);
+        const long long n1 = neighbour(G, bb, zz + dz, yy + dy_, x0 + 2 * tg + 1 + dx);
+        const long long n8 = neighbour(G, bb, zz + dz, yy + dy_, x0 + 2 * tg + 8 + dx);
+        const long long n9 = neighbour(G, bb, zz + dz, yy + dy_, x0 + 2 * tg + 9 + dx);
+#pragma unroll
+        for (int nt = 0; nt < 2; ++nt) {
+          const int ci = nt * 8 + g;
+          const __nv_bfloat16 zb = __float2bfloat16_rn(0.f);
+          __nv_bfloat16 e0 = n0 >= 0 ? x[n0 * CH + ci] : zb, e1 = n1 >= 0 ? x[n1 * CH + ci] : zb;
+          __nv_bfloat16 e8 = n8 >= 0 ? x[n8 * CH + ci] : zb, e9 = n9 >= 0 ? x[n9 * CH + ci] : zb;
+          unsigned b0 = pack2(e0, e1), b1 = pack2(e8, e9);
+          if (relu_in) {
+            b0 = relu2(b0);
+            b1 = relu2(b1);
+          }
+          mma_bf16(acc[j][nt], a, b0, b1);
+        }
+      }
+    }
+  }
+  float* p = part + (size_t)blockIdx.x * 27 * CH * CH;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int tap = warp + 8 * j;
+    if (tap >= 27) break;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int ci = nt * 8 + 2 * tg;
+      p[(tap * CH + g) * CH + ci] = acc[j][nt][0];
+      p[(tap * CH + g) * CH + ci + 1] = acc[j][nt][1];
+      p[(tap * CH + g + 8) * CH + ci] = acc[j][nt][2];
+      p[(tap * CH + g + 8) * CH + ci + 1] = acc[j][nt][3];
+    }
+  }
+}
+
+// acc[i] += sum over blocks of part[blk][i]  (i < 27*16*16)
+__global__ void k_reduce_parts(const float* __restrict__ part, int nblk, float* __restrict__ acc) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= 27 * CH * CH) return;
+  float s = 0.f;
+  for (int b = 0; b < nblk; ++b) s += part[(size_t)b * 27 * CH * CH + i];
+  acc[i] += s;
+}
+
+// db[c] += sum_v dy[v][c]
+__global__ void k_bias_grad(const __nv_bfloat16* __restrict__ dy, long long nvox, float* __restrict__ db) {
+  __shared__ float red[256][CH + 1];
+  float s[CH] = {};
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x)
+#pragma unroll
+    for (int c = 0; c < CH; ++c) s[c] += __bfloat162float(dy[v * CH + c]);
+#pragma unroll
+  for (int c = 0; c < CH; ++c) red[threadIdx.x][c] = s[c];
+  __syncthreads();
+  if (threadIdx.x < CH) {
+    float t = 0.f;
+    for (int i = 0; i < blockDim.x; ++i) t += red[i][threadIdx.x];
+    atomicAdd(&db[threadIdx.x], t);
+  }
+}
+
+// bf16 [v][16] <- (scale * src[v], 0, ..., 0)
+__global__ void k_pack1(const float* __restrict__ src, float scale, long long nvox, __nv_bfloat16* __restrict__ out) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x) {
+    uint4* o = reinterpret_cast<uint4*>(out + v * CH);
+    const unsigned first = pack2(__float2bfloat16_rn(src[v] * scale), __float2bfloat16_rn(0.f));
+    o[0] = make_uint4(first, 0u, 0u, 0u);
+    o[1] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// x[v] = z[v] + mu0 * f[v][0]
+__global__ void k_prox_out(const float* __restrict__ z, const __nv_bfloat16* __restrict__ f, long long nvox,
+                           float* __restrict__ x) {
+  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x)
+    x[v] = z[v] + MU0 * __bfloat162float(f[v * CH]);
+}
+
+// z = x - eta[s] * inv_s2 * g_raw, and g = inv_s2 * g_raw stored for the step-size gradient
+__global__ void k_zstep(const float* __restrict__ x, float* __restrict__ g, const float* __restrict__ eta, int s,
+                        float inv_s2, long long n, float* __restrict__ z) {
+  const float e = eta[s];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float gv = g[i] * inv_s2;
+    g[i] = gv;
+    z[i] = x[i] - e * gv;
+  }
+}
+
+__global__ void k_sub(float* __restrict__ a, const float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    a[i] -= b[i];
+}
+
+// r = (x - mu)/mu0; loss partial sums; gx = 2 r / (mu0 * ntot)
+__global__ void k_loss(const float* __restrict__ x, const float* __restrict__ mu, long long n, float* __restrict__ gx,
+                       double* __restrict__ loss_sum) {
+  double s = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float r = (x[i] - mu[i]) / MU0;
+    s += (double)r * r;
+    gx[i] = 2.f * r / (MU0 * (float)n);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss_sum, s);
+}
+
+// gz = gx + du[v][0] / mu0 ; deta[s] -= sum gz * g
+__global__ void k_gz(const float* __restrict__ gx, const __nv_bfloat16* __restrict__ du, const float* __restrict__ g,
+                     long long n, float* __restrict__ gz, float* __restrict__ deta, int s) {
+  float acc = 0.f;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const float v = gx[i] + __bfloat162float(du[i * CH]) / MU0;
+    gz[i] = v;
+    acc += v * g[i];
+  }
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(&deta[s], -acc);
+}
+
+// gx = gz - eta[s] * inv_s2 * h
+__global__ void k_gx(const float* __restrict__ gz, const float* __restrict__ h, const float* __restrict__ eta, int s,
+                     float inv_s2, long long n, float* __restrict__ gx) {
+  const float e = eta[s];
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    gx[i] = gz[i] - e * inv_s2 * h[i];
+}
+
+struct LayerOff {
+  int w, b, ci, co;
+};
+
+ctof_solver_params tikhonov_params(double lambda_rel);
+
+// Master FP32 parameters -> padded BF16 forward weights [tap][co][ci], data-gradient
+// weights [tap][ci][co] with flipped taps, and padded FP32 biases.
+__global__ void k_prep_weights(const float* __restrict__ theta, LayerOff L, __nv_bfloat16* __restrict__ wf,
+                               __nv_bfloat16* __restrict__ wb, float* __restrict__ bias) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < CH) bias[i] = i < L.co ? theta[L.b + i] : 0.f;
+  if (i >= 27 * CH * CH) return;
+  const int tap = i / (CH * CH), co = (i / CH) % CH, ci = i % CH;
+  const float v = (co < L.co && ci < L.ci) ? theta[L.w + (co * L.ci + ci) * 27 + tap] : 0.f;
+  wf[(tap * CH + co) * CH + ci] = __float2bfloat16_rn(v);
+  wb[((26 - tap) * CH + ci) * CH + co] = __float2bfloat16_rn(v);
+}
+
+// flat gradient += padded layer gradients
+__global__ void k_grad_to_flat(const float* __restrict__ dw, const float* __restrict__ db, LayerOff L,
+                               float* __restrict__ grad) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < L.co) grad[L.b + i] += db[i];
+  if (i >= L.co * L.ci * 27) return;
+  const int co = i / (L.ci * 27), ci = (i / 27) % L.ci, tap = i % 27;
+  grad[L.w + i] += dw[(tap * CH + co) * CH + ci];
+}
+
+__global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, float* __restrict__ m, float* __restrict__ v,
+                       int n, float lr, float b1, float b2, float eps, float c1, float c2) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const float g = gr[i];
+  const float mi = b1 * m[i] + (1.f - b1) * g;
+  const float vi = b2 * v[i] + (1.f - b2) * g * g;
+  m[i] = mi;
+  v[i] = vi;
+  p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+int grid_for(long long n) {
+  long long b = (n + 255) / 256;
+  if (b > 152 * 16) b = 152 * 16;
+  return b < 1 ? 1 : (int)b;
+}
+
+}  // namespace
+
+struct ctof_learned_s {
+  int stages;
+  int nparam;
+  ctof_learned_options opt;
+  int device;
+  LayerOff lo[NLAYER];
+  float* d_theta;   // [nparam] FP32 masters
+  float* d_grad;
+  float* d_m1;
+  float* d_m2;
+  long long adam_step;
+  __nv_bfloat16* d_wf;  // [4][27][16][16]
+  __nv_bfloat16* d_wb;
+  float* d_bias;        // [4][16]
+  float* d_dw;          // [4][27][16][16] FP32 accumulators
+  float* d_db;          // [4][16]
+  double* d_loss;
+  // per-geometry workspace
+  void* d_ws;
+  size_t ws_bytes;
+  long long ws_nvox;
+  int ws_batch, ws_nt;
+};
+
+namespace {
+
+ctof_status learned_prep(ctof_learned_s* L, cudaStream_t st) {
+  for (int l = 0; l < NLAYER; ++l) {
+    k_prep_weights<<<(27 * CH * CH + 255) / 256, 256, 0, st>>>(L->d_theta, L->lo[l], L->d_wf + l * 27 * CH * CH,
+                                                               L->d_wb + l * 27 * CH * CH, L->d_bias + l * CH);
+    CTOF_CUDA_TRY(cudaGetLastError());
+  }
+  return CTOF_OK;
+}
+
+struct Ws {
+  float *x, *tmpT, *gx, *gz, *h;
+  float *z, *g;                 // [S][V]
+  __nv_bfloat16 *u, *y1, *y2, *y3;  // [S][V][16]
+  __nv_bfloat16 *f, *da, *db_;  // [V][16]
+  float* part;
+  int nblk;
+};
+
+ctof_status learned_workspace(ctof_learned_s* L, const ctof_kernel_s* k, int batch, bool train, Ws* w) {
+  const long long V = (long long)batch * k->nz * k->n * k->n;
+  const long long T = (long long)batch * k->nt * k->n * k->n;
+  const int S = train ? L->stages : 1;
+  const long long rows = (long long)batch * k->nz * k->n;
+  const int nblk = (int)((rows + WG_ROWS - 1) / WG_ROWS);
+  size_t need = 0;
+  auto add = [&](size_t b) {
+    const size_t at = need;
+    need += (b + 255) & ~(size_t)255;
+    return at;
+  };
+  const size_t o_x = add(V * 4), o_t = add(T * 4), o_gx = add(V * 4), o_gz = add(V * 4), o_h = add(V * 4);
+  const size_t o_z = add((size_t)S * V * 4), o_g = add((size_t)S * V * 4);
+  const size_t o_u = add((size_t)S * V * CH * 2), o_y1 = add((size_t)S * V * CH * 2), o_y2 = add((size_t)S * V * CH * 2),
+               o_y3 = add((size_t)S * V * CH * 2);
+  const size_t o_f = add(V * CH * 2), o_da = add(V * CH * 2), o_db = add(V * CH * 2);
+  const size_t o_p = add((size_t)nblk * 27 * CH * CH * 4);
+  if (need > L->ws_bytes) {
+    if (L->d_ws) cudaFree(L->d_ws);
+    L->d_ws = nullptr;
+    L->ws_bytes = 0;
+    if (cudaMalloc(&L->d_ws, need) != cudaSuccess) {
+      cudaGetLastError();
+      return CTOF_ENOMEM;
+    }
+    L->ws_bytes = need;
+  }
+  char* b = static_cast<char*>(L->d_ws);
+  w->x = reinterpret_cast<float*>(b + o_x);
+  w->tmpT = reinterpret_cast<float*>(b + o_t);
+  w->gx = reinterpret_cast<float*>(b + o_gx);
+  w->gz = reinterpret_cast<float*>(b + o_gz);
+  w->h = reinterpret_cast<float*>(b + o_h);
+  w->z = reinterpret_cast<float*>(b + o_z);
+  w->g = reinterpret_cast<float*>(b + o_g);
+  w->u = reinterpret_cast<__nv_bfloat16*>(b + o_u);
+  w->y1 = reinterpret_cast<__nv_bfloat16*>(b + o_y1);
+  w->y2 = reinterpret_cast<__nv_bfloat16*>(b + o_y2);
+  w->y3 = reinterpret_cast<__nv_bfloat16*>(b + o_y3);
+  w->f = reinterpret_cast<__nv_bfloat16*>(b + o_f);
+  w->da = reinterpret_cast<__nv_bfloat16*>(b + o_da);
+  w->db_ = reinterpret_cast<__nv_bfloat16*>(b + o_db);
+  w->part = reinterpret_cast<float*>(b + o_p);
+  w->nblk = nblk;
+  return CTOF_OK;
+}
+
+ctof_status conv(const __nv_bfloat16* in, int relu_in, const __nv_bfloat16* wt, const float* bias,
+                 const __nv_bfloat16* mask, __nv_bfloat16* out, Geo G, cudaStream_t st) {
+  const long long jobs = (long long)G.b * G.z * G.y * (G.x / 16);
+  k_conv3d<<<(unsigned)((jobs + 7) / 8), 256, 0, st>>>(in, relu_in, wt, bias, mask, out, G);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status wgrad(const __nv_bfloat16* dy, const __nv_bfloat16* x, int relu_in, Geo G, float* part, int nblk, float* acc,
+                  cudaStream_t st) {
+  k_wgrad<<<nblk, 256, 0, st>>>(dy, x, relu_in, G, part);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  k_reduce_parts<<<(27 * CH * CH + 255) / 256, 256, 0, st>>>(part, nblk, acc);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+// g_raw = A^T (A x - m) for every batch member (unnormalised operator)
+ctof_status normal_residual(ctof_kernel_s* k, int batch, const float* x, const float* m, float* tmpT, float* out,
+                            cudaStream_t st) {
+  const size_t vol = (size_t)k->nz * k->n * k->n, meas = (size_t)k->nt * k->n * k->n;
+  for (int b = 0; b < batch; ++b) CTOF_TRY(ctof_forward(k, x + b * vol, tmpT + b * meas, st));
+  if (m) {
+    k_sub<<<grid_for((long long)batch * meas), 256, 0, st>>>(tmpT, m, (long long)batch * meas);
+    CTOF_CUDA_TRY(cudaGetLastError());
+  }
+  for (int b = 0; b < batch; ++b) CTOF_TRY(ctof_adjoint(k, tmpT + b * meas, out + b * vol, st));
+  return CTOF_OK;
+}
+
+// Forward pass of the unrolled solver; with `train` every stage's activations are kept.
+ctof_status unrolled_forward(ctof_learned_s* L, ctof_kernel_s* k, int batch, const float* m, const Ws& w, bool train,
+                             cudaStream_t st) {
+  const long long V = (long long)batch * k->nz * k->n * k->n;
+  const Geo G{batch, k->nz, k->n, k->n};
+  const float inv_s2 = (float)(1.0 / (k->scale * k->scale));
+  const int nstore = train ? L->stages : 1;
+  const float* eta = L->d_theta + L->nparam - L->stages;
+  const size_t vol = (size_t)k->nz * k->n * k->n, meas = (size_t)k->nt * k->n * k->n;
+  if (L->opt.x0_lambda_rel > 0.0) {
+    const ctof_solver_params tik = tikhonov_params(L->opt.x0_lambda_rel);
+    for (int b = 0; b < batch; ++b) CTOF_TRY(ctof_reconstruct(k, m + b * meas, &tik, w.x + b * vol, nullptr, st));
+  } else {
+    CTOF_CUDA_TRY(cudaMemsetAsync(w.x, 0, V * sizeof(float), st));
+  }
+  for (int s = 0; s < L->stages; ++s) {
+    const int j = train ? s : 0;
+    (void)nstore;
+    float* z = w.z + (size_t)j * V;
+    float* g = w.g + (size_t)j * V;
+    __nv_bfloat16* u = w.u + (size_t)j * V * CH;
+    __nv_bfloat16* y1 = w.y1 + (size_t)j * V * CH;
+    __nv_bfloat16* y2 = w.y2 + (size_t)j * V * CH;
+    __nv_bfloat16* y3 = w.y3 + (size_t)j * V * CH;
+    CTOF_TRY(normal_residual(k, batch, w.x, m, w.tmpT, g, st));
+    k_zstep<<<grid_for(V), 256, 0, st>>>(w.x, g, eta, s, inv_s2, V, z);
+    CTOF_CUDA_TRY(cudaGetLastError());
+    k_pack1<<<grid_for(V), 256, 0, st>>>(z, 1.0f / MU0, V, u);
+    CTOF_CUDA_TRY(cudaGetLastError());
+    CTOF_TRY(conv(u, 0, L->d_wf + 0 * 27 * CH * CH, L->d_bias + 0 * CH, nullptr, y1, G, st));
+    CTOF_TRY(conv(y1, 1, L->d_wf + 1 * 27 * CH * CH, L->d_bias + 1 * CH, nullptr, y2, G, st));
+    CTOF_TRY(conv(y2, 1, L->d_wf + 2 * 27 * CH * CH, L->d_bias + 2 * CH, nullptr, y3, G, st));
+    CTOF_TRY(conv(y3, 1, L->d_wf + 3 * 27 * CH * CH, L->d_bias + 3 * CH, nullptr, w.f, G, st));
+    k_prox_out<<<grid_for(V), 256, 0, st>>>(z, w.f, V, w.x);
+    CTOF_CUDA_TRY(cudaGetLastError());
+  }
+  if (!train && L->opt.dc_steps > 0) {
+    // x <- x - T(A x - m): the residual goes through the Tikhonov solve into w.h
+    const ctof_solver_params tik = tikhonov_params(L->opt.dc_lambda_rel);
+    for (int d = 0; d < L->opt.dc_steps; ++d) {
+      for (int b = 0; b < batch; ++b) CTOF_TRY(ctof_forward(k, w.x + b * vol, w.tmpT + b * meas, st));
+      k_sub<<<grid_for((long long)batch * meas), 256, 0, st>>>(w.tmpT, m, (long long)batch * meas);
+      CTOF_CUDA_TRY(cudaGetLastError());
+      for (int b = 0; b < batch; ++b)
+        CTOF_TRY(ctof_reconstruct(k, w.tmpT + b * meas, &tik, w.h + b * vol, nullptr, st));
+      k_sub<<<grid_for(V), 256, 0, st>>>(w.x, w.h, V);
+      CTOF_CUDA_TRY(cudaGetLastError());
+    }
+  }
+  return CTOF_OK;
+}
+
+// Loss and flat gradient (accumulated into d_grad, which is zeroed first).
+ctof_status unrolled_backward(ctof_learned_s* L, ctof_kernel_s* k, int batch, const float* mu, const Ws& w,
+                              cudaStream_t st) {
+  const long long V = (long long)batch * k->nz * k->n * k->n;
+  const Geo G{batch, k->nz, k->n, k->n};
+  const float inv_s2 = (float)(1.0 / (k->scale * k->scale));
+  const float* eta = L->d_theta + L->nparam - L->stages;
+  float* deta = L->d_grad + L->nparam - L->stages;
+  CTOF_CUDA_TRY(cudaMemsetAsync(L->d_grad, 0, L->nparam * sizeof(float), st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(L->d_dw, 0, (size_t)NLAYER * 27 * CH * CH * sizeof(float), st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(L->d_db, 0, (size_t)NLAYER * CH * sizeof(float), st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(L->d_loss, 0, sizeof(double), st));
+  k_loss<<<grid_for(V), 256, 0, st>>>(w.x, mu, V, w.gx, L->d_loss);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  const int bg_blocks = grid_for(V) < 304 ? grid_for(V) : 304;
+  for (int s = L->stages - 1; s >= 0; --s) {
+    const float* g = w.g + (size_t)s * V;
+    const __nv_bfloat16* u = w.u + (size_t)s * V * CH;
+    const __nv_bfloat16* y1 = w.y1 + (size_t)s * V * CH;
+    const __nv_bfloat16* y2 = w.y2 + (size_t)s * V * CH;
+    const __nv_bfloat16* y3 = w.y3 + (size_t)s * V * CH;
+    // x_{s+1} = z + mu0 f(u): output gradient of f is mu0 * gx
+    k_pack1<<<grid_for(V), 256, 0, st>>>(w.gx, MU0, V, w.da);
+    CTOF_CUDA_TRY(cudaGetLastError());
+    const __nv_bfloat16* acts[NLAYER] = {u, y1, y2, y3};
+    const __nv_bfloat16* pre[NLAYER] = {nullptr, y1, y2, y3};
+    __nv_bfloat16* cur = w.da;
+    __nv_bfloat16* nxt = w.db_;
+    for (int l = NLAYER - 1; l >= 0; --l) {
+      CTOF_TRY(wgrad(cur, acts[l], l > 0 ? 1 : 0, G, w.part, w.nblk, L->d_dw + (size_t)l * 27 * CH * CH, st));
+      k_bias_grad<<<bg_blocks, 256, 0, st>>>(cur, V, L->d_db + l * CH);
+      CTOF_CUDA_TRY(cudaGetLastError());
+      // gradient w.r.t. this layer's input: masked by the ReLU of the previous pre-activation
+      CTOF_TRY(conv(cur, 0, L->d_wb + (size_t)l * 27 * CH * CH, nullptr, pre[l], nxt, G, st));
+      __nv_bfloat16* t = cur;
+      cur = nxt;
+      nxt = t;
+    }
+    // cur holds dL/du (channel 0); z = x - eta g,  g = A_n^T (A_n x - m_n)
+    k_gz<<<grid_for(V) < 304 ? grid_for(V) : 304, 256, 0, st>>>(w.gx, cur, g, V, w.gz, deta, s);
+    CTOF_CUDA_TRY(cudaGetLastError());
+    CTOF_TRY(normal_residual(k, batch, w.gz, nullptr, w.tmpT, w.h, st));
+    k_gx<<<grid_for(V), 256, 0, st>>>(w.gz, w.h, eta, s, inv_s2, V, w.gx);
+    CTOF_CUDA_TRY(cudaGetLastError());
+  }
+  for (int l = 0; l < NLAYER; ++l) {
+    const int n = L->lo[l].co * L->lo[l].ci * 27;
+    k_grad_to_flat<<<(n + 255) / 256, 256, 0, st>>>(L->d_dw + (size_t)l * 27 * CH * CH, L->d_db + l * CH, L->lo[l],
+                                                    L->d_grad);
+    CTOF_CUDA_TRY(cudaGetLastError());
+  }
+  return CTOF_OK;
+}
+
+ctof_solver_params tikhonov_params(double lambda_rel) {
+  ctof_solver_params tik{};
+  tik.solver = CTOF_SOLVER_TIKHONOV;
+  tik.iters = 1;
+  tik.rho = 1.0;
+  tik.tv_beta = -1.0;
+  tik.beta_rel = 1e-3;
+  tik.tik_lambda_rel = lambda_rel;
+  return tik;
+}
+
+ctof_status check_geometry(const ctof_kernel_s* k) {
+  if (k->n % 16 != 0) return CTOF_EUNSUPPORTED;  // convolution tiles are 16 voxels along x
+  return CTOF_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int ctof_learned_param_count(int stages) {
+  int n = 0;
+  for (int l = 0; l < NLAYER; ++l) n += LAYER_OUT[l] * LAYER_IN[l] * 27 + LAYER_OUT[l];
+  return n + stages;
+}
+
+ctof_status ctof_learned_create(int stages, const float* h_params, const ctof_learned_options* opt,
+                                ctof_learned* out) {
+  if (!out || !h_params || stages < 1 || stages > 64) return CTOF_EINVAL;
+  ctof_learned_options o{};
+  if (opt) o = *opt;
+  if (!(o.x0_lambda_rel >= 0.0) || !isfinite(o.x0_lambda_rel) || o.dc_steps < 0 || o.dc_steps > 16 ||
+      (o.dc_steps > 0 && !(o.dc_lambda_rel > 0.0 && isfinite(o.dc_lambda_rel))))
+    return CTOF_EINVAL;
+  *out = nullptr;
+  ctof_learned_s* L = new (std::nothrow) ctof_learned_s();
+  if (!L) return CTOF_ENOMEM;
+  L->stages = stages;
+  L->nparam = ctof_learned_param_count(stages);
+  L->opt = o;
+  CTOF_CUDA_TRY(cudaGetDevice(&L->device));
+  int off = 0;
+  for (int l = 0; l < NLAYER; ++l) {
+    L->lo[l].ci = LAYER_IN[l];
+    L->lo[l].co = LAYER_OUT[l];
+    L->lo[l].w = off;
+    off += LAYER_OUT[l] * LAYER_IN[l] * 27;
+    L->lo[l].b = off;
+    off += LAYER_OUT[l];
+  }
+  const size_t np = L->nparam;
+  const size_t bytes = 4 * np * 4 + 2 * (size_t)NLAYER * 27 * CH * CH * 2 + (size_t)NLAYER * CH * 4 +
+                       (size_t)NLAYER * 27 * CH * CH * 4 + (size_t)NLAYER * CH * 4 + 64;
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    delete L;
+    return CTOF_ENOMEM;
+  }
+  char* b = static_cast<char*>(p);
+  L->d_theta = reinterpret_cast<float*>(b);
+  L->d_grad = L->d_theta + np;
+  L->d_m1 = L->d_grad + np;
+  L->d_m2 = L->d_m1 + np;
+  L->d_wf = reinterpret_cast<__nv_bfloat16*>(L->d_m2 + np);
+  L->d_wb = L->d_wf + (size_t)NLAYER * 27 * CH * CH;
+  L->d_bias = reinterpret_cast<float*>(L->d_wb + (size_t)NLAYER * 27 * CH * CH);
+  L->d_dw = L->d_bias + NLAYER * CH;
+  L->d_db = L->d_dw + (size_t)NLAYER * 27 * CH * CH;
+  L->d_loss = reinterpret_cast<double*>(reinterpret_cast<uintptr_t>(L->d_db + NLAYER * CH + 8) & ~(uintptr_t)7);
+  if (cudaMemcpy(L->d_theta, h_params, np * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+      cudaMemset(L->d_m1, 0, 2 * np * 4) != cudaSuccess || learned_prep(L, nullptr) != CTOF_OK ||
+      cudaDeviceSynchronize() != cudaSuccess) {
+    cudaFree(p);
+    delete L;
+    return CTOF_ECUDA;
+  }
+  *out = L;
+  return CTOF_OK;
+}
+
+void ctof_learned_destroy(ctof_learned L) {
+  if (!L) return;
+  if (L->d_ws) cudaFree(L->d_ws);
+  cudaFree(L->d_theta);
+  delete L;
+}
+
+ctof_status ctof_learned_get_params(ctof_learned L, float* h_params) {
+  if (!L || !h_params) return CTOF_EINVAL;
+  CTOF_CUDA_TRY(cudaMemcpy(h_params, L->d_theta, (size_t)L->nparam * 4, cudaMemcpyDeviceToHost));
+  return CTOF_OK;
+}
+
+ctof_status ctof_learned_loss_grad(ctof_learned L, ctof_kernel k, int batch, const float* d_m, const float* d_mu,
+                                   double* h_loss, float* h_grad, void* stream) {
+  if (!L || !k || !d_m || !d_mu || batch < 1) return CTOF_EINVAL;
+  CTOF_TRY(check_geometry(k));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ws w;
+  CTOF_TRY(learned_workspace(L, k, batch, true, &w));
+  CTOF_TRY(unrolled_forward(L, k, batch, d_m, w, true, st));
+  CTOF_TRY(unrolled_backward(L, k, batch, d_mu, w, st));
+  double loss = 0.0;
+  CTOF_CUDA_TRY(cudaMemcpyAsync(&loss, L->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+  if (h_grad) CTOF_CUDA_TRY(cudaMemcpyAsync(h_grad, L->d_grad, (size_t)L->nparam * 4, cudaMemcpyDeviceToHost, st));
+  CTOF_CUDA_TRY(cudaStreamSynchronize(st));
+  const long long V = (long long)batch * k->nz * k->n * k->n;
+  if (h_loss) *h_loss = loss / (double)V;
+  return CTOF_OK;
+}
+
+ctof_status ctof_learned_train_step(ctof_learned L, ctof_kernel k, int batch, const float* d_m, const float* d_mu,
+                                    double lr, double* h_loss, void* stream) {
+  if (!L || !k || !d_m || !d_mu || batch < 1 || !(lr > 0)) return CTOF_EINVAL;
+  CTOF_TRY(check_geometry(k));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ws w;
+  CTOF_TRY(learned_workspace(L, k, batch, true, &w));
+  CTOF_TRY(unrolled_forward(L, k, batch, d_m, w, true, st));
+  CTOF_TRY(unrolled_backward(L, k, batch, d_mu, w, st));
+  L->adam_step++;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - powf(b1, (float)L->adam_step), c2 = 1.f - powf(b2, (float)L->adam_step);
+  k_adam<<<(L->nparam + 255) / 256, 256, 0, st>>>(L->d_theta, L->d_grad, L->d_m1, L->d_m2, L->nparam, (float)lr, b1, b2,
+                                                  1e-8f, c1, c2);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  CTOF_TRY(learned_prep(L, st));
+  if (h_loss) {
+    double loss = 0.0;
+    CTOF_CUDA_TRY(cudaMemcpyAsync(&loss, L->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CTOF_CUDA_TRY(cudaStreamSynchronize(st));
+    *h_loss = loss / (double)((long long)batch * k->nz * k->n * k->n);
+  }
+  return CTOF_OK;
+}
+
+ctof_status ctof_learned_reconstruct(ctof_learned L, ctof_kernel k, int batch, const float* d_m, float* d_mu,
+                                     void* stream) {
+  if (!L || !k || !d_m || !d_mu || batch < 1) return CTOF_EINVAL;
+  CTOF_TRY(check_geometry(k));
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ws w;
+  CTOF_TRY(learned_workspace(L, k, batch, false, &w));
+  CTOF_TRY(unrolled_forward(L, k, batch, d_m, w, false, st));
+  CTOF_CUDA_TRY(cudaMemcpyAsync(d_mu, w.x, (size_t)batch * k->nz * k->n * k->n * 4, cudaMemcpyDeviceToDevice, st));
+  return CTOF_OK;
+}
+
+}  // extern "C"

@@ -83,6 +83,15 @@ _SIGNATURES = {
     "ctof_reconstruct_batch": (ctypes.c_int, [ctypes.c_int, ctypes.POINTER(_P), ctypes.POINTER(_P),
                                               ctypes.POINTER(SolverParams), ctypes.POINTER(_P), _P]),
     "ctof_kernel_autotune": (ctypes.c_int, [_P, _P]),
+    "ctof_learned_param_count": (ctypes.c_int, [ctypes.c_int]),
+    "ctof_learned_create": (ctypes.c_int, [ctypes.c_int, _P, _P, ctypes.POINTER(_P)]),
+    "ctof_learned_destroy": (None, [_P]),
+    "ctof_learned_get_params": (ctypes.c_int, [_P, _P]),
+    "ctof_learned_loss_grad": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.POINTER(ctypes.c_double), _P,
+                                              _P]),
+    "ctof_learned_train_step": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.c_double,
+                                               ctypes.POINTER(ctypes.c_double), _P]),
+    "ctof_learned_reconstruct": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P]),
     "ctof_kernel_get_tuning": (ctypes.c_int, [_P, _P]),
     "ctof_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "ctof_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(Timing)]),
@@ -142,6 +151,78 @@ def admm_params(iters=100, rho=1.0, tv_beta=-1.0, beta_rel=1e-3):
 
 def tikhonov_params(lambda_rel=1e-3):
     return SolverParams(SOLVER_TIKHONOV, 1, 1.0, -1.0, 1e-3, float(lambda_rel))
+
+
+class LearnedOptions(ctypes.Structure):
+    _fields_ = [("x0_lambda_rel", ctypes.c_double), ("dc_steps", ctypes.c_int), ("dc_lambda_rel", ctypes.c_double)]
+
+
+class Learned:
+    """The unrolled proximal-gradient solver with a 3-D CNN prox (``ctof_learned``)."""
+
+    def __init__(self, stages, params, x0_lambda_rel=0.0, dc_steps=0, dc_lambda_rel=0.0):
+        import numpy as np
+        lib = load()
+        self._lib = lib
+        self.stages = int(stages)
+        self.x0_lambda_rel = float(x0_lambda_rel)
+        self.options = LearnedOptions(float(x0_lambda_rel), int(dc_steps), float(dc_lambda_rel))
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.size != lib.ctof_learned_param_count(self.stages):
+            raise ValueError("parameter count mismatch")
+        h = ctypes.c_void_p()
+        _check(lib.ctof_learned_create(self.stages, p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(self.options),
+                                       ctypes.byref(h)),
+               "ctof_learned_create")
+        self._h = h
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            self._lib.ctof_learned_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def params(self):
+        import numpy as np
+        out = np.empty(self._lib.ctof_learned_param_count(self.stages), dtype=np.float32)
+        _check(self._lib.ctof_learned_get_params(self._h, out.ctypes.data_as(ctypes.c_void_p)),
+               "ctof_learned_get_params")
+        return out
+
+    def loss_grad(self, kernel, m, mu, stream=None):
+        import numpy as np
+        b = int(m.shape[0])
+        grad = np.empty(self._lib.ctof_learned_param_count(self.stages), dtype=np.float32)
+        loss = ctypes.c_double()
+        _check(self._lib.ctof_learned_loss_grad(
+            self._h, kernel._h, b, _dev_ptr(m, (b,) + kernel._meas_shape(), "m"),
+            _dev_ptr(mu, (b,) + kernel._vol_shape(), "mu"), ctypes.byref(loss),
+            grad.ctypes.data_as(ctypes.c_void_p), _stream_handle(stream)), "ctof_learned_loss_grad")
+        return loss.value, grad
+
+    def train_step(self, kernel, m, mu, lr, want_loss=False, stream=None):
+        b = int(m.shape[0])
+        loss = ctypes.c_double()
+        _check(self._lib.ctof_learned_train_step(
+            self._h, kernel._h, b, _dev_ptr(m, (b,) + kernel._meas_shape(), "m"),
+            _dev_ptr(mu, (b,) + kernel._vol_shape(), "mu"), float(lr),
+            ctypes.byref(loss) if want_loss else None, _stream_handle(stream)), "ctof_learned_train_step")
+        return loss.value if want_loss else None
+
+    def reconstruct(self, kernel, m, out=None, stream=None):
+        import torch
+        b = int(m.shape[0])
+        if out is None:
+            out = torch.empty((b,) + kernel._vol_shape(), device=m.device, dtype=torch.float32)
+        _check(self._lib.ctof_learned_reconstruct(
+            self._h, kernel._h, b, _dev_ptr(m, (b,) + kernel._meas_shape(), "m"),
+            _dev_ptr(out, (b,) + kernel._vol_shape(), "out"), _stream_handle(stream)), "ctof_learned_reconstruct")
+        return out
 
 
 def reconstruct_batch(kernels, ms, params, outs=None, stream=None):

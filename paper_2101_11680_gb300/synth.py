@@ -107,3 +107,26 @@ def poisson_noise(m, peak, seed):
     rng = _rng(seed)
     lam = np.clip(m, 0.0, None) * (peak / mx)
     return rng.poisson(lam).astype(np.float64) * (mx / peak)
+
+
+# (input channels, output channels) of the four 3x3x3 layers of the learned prox
+LEARNED_LAYERS = ((1, 16), (16, 16), (16, 16), (16, 1))
+
+
+def learned_init(stages, seed):
+    """Random starting parameters of the learned solver, flat float64.
+
+    He-normal weights std sqrt(2 / (27 ci)) (the last layer's scaled by 0.1, so
+    the untrained prox is close to the identity), zero biases, step sizes 1.
+    Layout: w1 [16][1][27], b1 [16], w2 [16][16][27], b2 [16], w3 [16][16][27],
+    b3 [16], w4 [1][16][27], b4 [1], eta [stages].
+    """
+    rng = _rng(seed)
+    parts = []
+    for li, (ci, co) in enumerate(LEARNED_LAYERS):
+        std = np.sqrt(2.0 / (ci * 27))
+        if li == len(LEARNED_LAYERS) - 1:
+            std *= 0.1
+        parts += [np.ravel(rng.standard_normal((co, ci, 27)) * std), np.zeros(co)]
+    parts.append(np.ones(int(stages)))
+    return np.concatenate(parts)

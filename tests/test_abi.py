@@ -78,3 +78,16 @@ def test_calls_reject_null_handles(lib):
     assert lib.ctof_reconstruct_host(None, None, ctypes.byref(p), None, None, None) == ctof.EINVAL
     assert lib.ctof_kernel_get_info(None, None) == ctof.EINVAL
     lib.ctof_kernel_destroy(None)  # no-op
+
+
+def test_learned_parameter_count_matches_oracle(lib):
+    from oracle import learned as ln
+    for s in (1, 3, 10):
+        assert lib.ctof_learned_param_count(s) == ln.param_count(s)
+    out = ctypes.c_void_p(1)
+    import numpy as np
+    p = np.zeros(ln.param_count(3), dtype=np.float32)
+    assert lib.ctof_learned_create(0, p.ctypes.data_as(ctypes.c_void_p), None, ctypes.byref(out)) != 0
+    assert lib.ctof_learned_loss_grad(None, None, 1, None, None, None, None, None) != 0
+    bad = ctof.LearnedOptions(0.0, 2, 0.0)  # data-consistency steps need a positive lambda
+    assert lib.ctof_learned_create(3, p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(bad), ctypes.byref(out)) != 0
