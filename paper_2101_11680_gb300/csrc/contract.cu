@@ -1,11 +1,21 @@
 // Per-frequency contractions of the convolutional model (Eq. 11 in the
 // lateral Fourier domain): for every half-plane frequency f,
-//   forward  M_hat(f, t) = sum_z W_hat(f, t, z) mu_hat(f, z)       (T x Z . Z)
-//   adjoint  V_hat(f, z) = sum_t W_hat(f, t, z) r_hat(f, t)        (Z x T . T)
+//   forward   M_hat(f, t) = sum_z W_hat(f, t, z) mu_hat(f, z)       (T x Z . Z)
+//   adjoint   V_hat(f, z) = sum_t W_hat(f, t, z) r_hat(f, t)        (Z x T . T)
+//   Tikhonov  x_hat(f)    = (G(f) + lambda I)^-1 V_hat(f)           (Z x Z, FP64)
 // W_hat is real (the kernel is even in x and y) and, for dx == dy, equal on
-// the up-to-four frequencies (a,b), (a,-b), (b,a), (b,-a) of one class; a CTA
-// stages one class's T x Z matrix once in shared memory and applies it to the
-// complex vectors of all members (up to 8 real right-hand sides).
+// the up-to-four frequencies (a,b), (a,-b), (b,a), (b,-a) of one class, so
+// each class's T x Z block is read from HBM once and applied to the complex
+// vectors of all members (up to 8 real right-hand sides).
+//
+// Persistent CTAs walk the classes with a two-stage cp.async pipeline: while
+// one class is computed, the next class's W_hat block (contiguous in HBM,
+// rows of z4 floats), its member vectors and, for Tikhonov, its FP64 inverse
+// stream into the other shared-memory stage.  W_hat rows land with a stride
+// of 4*(z4/4 | 1) floats, so eight consecutive rows read with float4 loads hit
+// eight distinct 16-byte bank groups.  The arithmetic is FP32 FMA (FP64 for
+// the Z x Z solve): these contractions move 1 FLOP per 2 bytes of W_hat and
+// are bound by HBM, not by the FMA pipes.
 // (The fused ADMM x-update lives in contract_admm.cu.)
 #include <cuda_runtime.h>
 
@@ -14,226 +24,275 @@
 namespace {
 
 constexpr int CT_THREADS = 256;
-constexpr int CT_WARPS = CT_THREADS / 32;
 
-// W_hat is stored [class][nt][z4] (rows padded to a multiple of 4 floats).
-__device__ __forceinline__ void load_what(float* s_w, const float* __restrict__ what, int c, int nt, int nz) {
-  const int z4 = (nz + 3) & ~3;
-  const float* src = what + (size_t)c * nt * z4;
-  const int total = nt * nz;
-  for (int i = threadIdx.x; i < total; i += blockDim.x) {
-    const int t = i / nz, z = i - t * nz;
-    s_w[t * (nz + 1) + z] = src[(size_t)t * z4 + z];
+enum { MODE_FWD = 0, MODE_ADJ = 1, MODE_TIK = 2 };
+
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void cp_async16(void* s, const void* g) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* s, const void* g) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(smem_addr(s)), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// Shared-memory plan of one pipeline stage and of the per-CTA scratch.
+struct Plan {
+  int nt, nz, z4, q, sw;   // q = z4/4 float4 chunks per row, sw = smem row stride (floats)
+  int J;                   // adjoint: row groups
+  size_t off_vec, off_h;   // byte offsets inside a stage
+  size_t stage;            // bytes per stage
+  size_t off_part, off_b;  // byte offsets of the scratch after the stages
+  size_t total;            // bytes for nbuf stages + scratch
+};
+
+__host__ __device__ inline size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+__host__ __device__ inline Plan make_plan(int mode, int nt, int nz, int nbuf, int threads) {
+  Plan p;
+  p.nt = nt;
+  p.nz = nz;
+  p.z4 = (nz + 3) & ~3;
+  p.q = p.z4 / 4;
+  p.sw = 4 * (p.q | 1);
+  const int pairs = 2 * p.q;
+  p.J = threads / pairs > 0 ? threads / pairs : 1;
+  size_t b = al16((size_t)nt * p.sw * 4);
+  p.off_vec = b;
+  b += al16(mode == MODE_FWD ? (size_t)p.z4 * 8 * 4 : (size_t)nt * 8 * 4);
+  p.off_h = b;
+  if (mode == MODE_TIK) b += al16((size_t)nz * nz * 8);
+  p.stage = b;
+  size_t s = b * nbuf;
+  p.off_part = s;
+  if (mode != MODE_FWD) s += al16((size_t)p.J * p.z4 * 8 * 4);
+  p.off_b = s;
+  if (mode == MODE_TIK) s += al16((size_t)p.z4 * 8 * 8);
+  p.total = s;
+  return p;
+}
+
+// Issue the copies of class c into stage buffer `st` (members cached in s_mem).
+template <int MODE>
+__device__ __forceinline__ void issue(const Plan& P, char* stg, int* s_mem, const float* __restrict__ what,
+                                      const int* __restrict__ members, const float2* __restrict__ vin, int ld_in,
+                                      const double* __restrict__ hinv, int c) {
+  float* sW = reinterpret_cast<float*>(stg);
+  const float* src = what + (size_t)c * P.nt * P.z4;
+  const int chunks = P.nt * P.q;
+  for (int i = threadIdx.x; i < chunks; i += blockDim.x) {
+    const int t = i / P.q, k = i - t * P.q;
+    cp_async16(sW + t * P.sw + 4 * k, src + (size_t)t * P.z4 + 4 * k);
+  }
+  if (threadIdx.x < 4) s_mem[threadIdx.x] = members[c * 4 + threadIdx.x];
+  float2* sV = reinterpret_cast<float2*>(stg + P.off_vec);  // [row][4] complex = [row][8] floats
+  const int rows = MODE == MODE_FWD ? P.z4 : P.nt;
+  const int valid = MODE == MODE_FWD ? P.nz : P.nt;
+  for (int i = threadIdx.x; i < 4 * rows; i += blockDim.x) {
+    const int m = i / rows, r = i - m * rows;
+    const int f = members[c * 4 + m];
+    if (f >= 0 && r < valid)
+      cp_async8(sV + r * 4 + m, vin + (size_t)f * ld_in + r);
+    else
+      sV[r * 4 + m] = make_float2(0.f, 0.f);
+  }
+  if (MODE == MODE_TIK) {
+    double* sH = reinterpret_cast<double*>(stg + P.off_h);
+    const double* hs = hinv + (size_t)c * P.nz * P.nz;
+    for (int i = threadIdx.x; i < P.nz * P.nz; i += blockDim.x) cp_async8(sH + i, hs + i);
   }
 }
 
-// Partial adjoint sums: warp w covers t in its chunk; lane covers z = lane, lane+32.
-__device__ __forceinline__ void adj_partials(const float* s_w, const float2* s_vin, int nt, int nz, int nmem,
-                                             float2* s_part) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int chunk = (nt + CT_WARPS - 1) / CT_WARPS;
-  const int t0 = warp * chunk, t1 = min(nt, t0 + chunk);
-  float2 acc0[4], acc1[4];
+// out[t][0..7] = sum_z W[t][z] x[z][0..7]  (one thread per row t)
+__device__ __forceinline__ void compute_fwd(const Plan& P, const char* stg, const int* s_mem,
+                                            float2* __restrict__ out_t, int ldt) {
+  const float* sW = reinterpret_cast<const float*>(stg);
+  const float4* sX = reinterpret_cast<const float4*>(stg + P.off_vec);  // [z][2] float4
+  for (int t = threadIdx.x; t < P.nt; t += blockDim.x) {
+    float acc[8];
 #pragma unroll
-  for (int m = 0; m < 4; ++m) acc0[m] = acc1[m] = make_float2(0.f, 0.f);
-  const int z0 = lane, z1 = lane + 32;
-  for (int t = t0; t < t1; ++t) {
-    const float w0 = z0 < nz ? s_w[t * (nz + 1) + z0] : 0.f;
-    const float w1 = z1 < nz ? s_w[t * (nz + 1) + z1] : 0.f;
+    for (int r = 0; r < 8; ++r) acc[r] = 0.f;
+    const float4* wr = reinterpret_cast<const float4*>(sW + t * P.sw);
+    for (int k = 0; k < P.q; ++k) {
+      const float4 w = wr[k];
+      const float wz[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-    for (int m = 0; m < 4; ++m) {
-      if (m < nmem) {
-        const float2 v = s_vin[m * nt + t];
-        acc0[m].x += w0 * v.x;
-        acc0[m].y += w0 * v.y;
-        acc1[m].x += w1 * v.x;
-        acc1[m].y += w1 * v.y;
+      for (int j = 0; j < 4; ++j) {
+        const float4 a = sX[(4 * k + j) * 2], b = sX[(4 * k + j) * 2 + 1];
+        acc[0] = fmaf(wz[j], a.x, acc[0]);
+        acc[1] = fmaf(wz[j], a.y, acc[1]);
+        acc[2] = fmaf(wz[j], a.z, acc[2]);
+        acc[3] = fmaf(wz[j], a.w, acc[3]);
+        acc[4] = fmaf(wz[j], b.x, acc[4]);
+        acc[5] = fmaf(wz[j], b.y, acc[5]);
+        acc[6] = fmaf(wz[j], b.z, acc[6]);
+        acc[7] = fmaf(wz[j], b.w, acc[7]);
       }
     }
-  }
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    if (m < nmem) {
-      if (z0 < nz) s_part[(warp * 4 + m) * nz + z0] = acc0[m];
-      if (z1 < nz) s_part[(warp * 4 + m) * nz + z1] = acc1[m];
+    for (int m = 0; m < 4; ++m)
+      if (s_mem[m] >= 0) out_t[(size_t)s_mem[m] * ldt + t] = make_float2(acc[2 * m], acc[2 * m + 1]);
+  }
+}
+
+// Adjoint partial sums: thread (j, k, h) sums rows t = j (mod J) for z in chunk k
+// and right-hand sides 4h..4h+3; partials land in part[j][z][8].
+__device__ __forceinline__ void compute_adj_partials(const Plan& P, const char* stg, float* part) {
+  const float* sW = reinterpret_cast<const float*>(stg);
+  const float* sC = reinterpret_cast<const float*>(stg + P.off_vec);  // [t][8]
+  const int pairs = 2 * P.q;
+  for (int u = threadIdx.x; u < P.J * pairs; u += blockDim.x) {
+    const int j = u / pairs, pk = u - j * pairs, k = pk >> 1, h = pk & 1;
+    float acc[4][4];
+#pragma unroll
+    for (int a = 0; a < 4; ++a)
+#pragma unroll
+      for (int b = 0; b < 4; ++b) acc[a][b] = 0.f;
+    for (int t = j; t < P.nt; t += P.J) {
+      const float4 w = *reinterpret_cast<const float4*>(sW + t * P.sw + 4 * k);
+      const float4 cv = *reinterpret_cast<const float4*>(sC + t * 8 + 4 * h);
+      const float wz[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+      for (int a = 0; a < 4; ++a) {
+        acc[a][0] = fmaf(wz[a], cv.x, acc[a][0]);
+        acc[a][1] = fmaf(wz[a], cv.y, acc[a][1]);
+        acc[a][2] = fmaf(wz[a], cv.z, acc[a][2]);
+        acc[a][3] = fmaf(wz[a], cv.w, acc[a][3]);
+      }
     }
-  }
-}
-
-__device__ __forceinline__ int load_members(const int* __restrict__ members, int c, int (&mem)[4]) {
-  int nmem = 0;
 #pragma unroll
-  for (int m = 0; m < 4; ++m) {
-    mem[m] = members[c * 4 + m];
-    nmem += mem[m] >= 0;
+    for (int a = 0; a < 4; ++a)
+      *reinterpret_cast<float4*>(part + ((size_t)j * P.z4 + 4 * k + a) * 8 + 4 * h) =
+          make_float4(acc[a][0], acc[a][1], acc[a][2], acc[a][3]);
   }
-  return nmem;  // members are packed first
 }
 
-__global__ void __launch_bounds__(CT_THREADS) k_contract_fwd(const float* __restrict__ what,
-                                                             const int* __restrict__ members, int nclass, int nt,
-                                                             int nz, const float2* __restrict__ in_z, int ldz,
-                                                             float2* __restrict__ out_t, int ldt) {
-  extern __shared__ float smem_f[];
-  float* s_w = smem_f;
-  float2* s_x = reinterpret_cast<float2*>(s_w + ((nt * (nz + 1) + 1) & ~1));
-  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
-    int mem[4];
-    const int nmem = load_members(members, c, mem);
-    load_what(s_w, what, c, nt, nz);
-    for (int i = threadIdx.x; i < 4 * nz; i += blockDim.x) {
-      const int m = i / nz, z = i - m * nz;
-      s_x[i] = m < nmem ? in_z[(size_t)mem[m] * ldz + z] : make_float2(0.f, 0.f);
+template <int MODE>
+__global__ void __launch_bounds__(CT_THREADS) k_contract(const float* __restrict__ what,
+                                                         const int* __restrict__ members, int nclass, int nt, int nz,
+                                                         const float2* __restrict__ vin, int ld_in,
+                                                         float2* __restrict__ vout, int ld_out,
+                                                         const double* __restrict__ hinv, int nbuf) {
+  extern __shared__ __align__(16) char smem[];
+  __shared__ int s_mem[2][4];
+  const Plan P = make_plan(MODE, nt, nz, nbuf, blockDim.x);
+  float* part = reinterpret_cast<float*>(smem + P.off_part);
+  double* sB = reinterpret_cast<double*>(smem + P.off_b);
+  int it = 0;
+  if (blockIdx.x < nclass)
+    issue<MODE>(P, smem, s_mem[0], what, members, vin, ld_in, hinv, blockIdx.x);
+  cp_commit();
+  for (int c = blockIdx.x; c < nclass; c += gridDim.x, ++it) {
+    const int cur = nbuf == 2 ? (it & 1) : 0;
+    const int cn = c + gridDim.x;
+    if (nbuf == 2) {
+      if (cn < nclass) issue<MODE>(P, smem + (cur ^ 1) * P.stage, s_mem[cur ^ 1], what, members, vin, ld_in, hinv, cn);
+      cp_commit();
+      cp_wait<1>();
+    } else {
+      cp_wait<0>();
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < nt; t += blockDim.x) {
-      float2 acc[4];
-#pragma unroll
-      for (int m = 0; m < 4; ++m) acc[m] = make_float2(0.f, 0.f);
-      const float* wr = s_w + t * (nz + 1);
-      for (int z = 0; z < nz; ++z) {
-        const float w = wr[z];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-          const float2 x = s_x[m * nz + z];
-          acc[m].x += w * x.x;
-          acc[m].y += w * x.y;
+    const char* stg = smem + cur * P.stage;
+    const int* mem = s_mem[cur];
+    if (MODE == MODE_FWD) {
+      compute_fwd(P, stg, mem, vout, ld_out);
+    } else {
+      compute_adj_partials(P, stg, part);
+      __syncthreads();
+      if (MODE == MODE_ADJ) {
+        for (int o = threadIdx.x; o < 4 * nz; o += blockDim.x) {
+          const int m = o / nz, z = o - m * nz;
+          if (mem[m] < 0) continue;
+          float re = 0.f, im = 0.f;
+          for (int j = 0; j < P.J; ++j) {
+            re += part[((size_t)j * P.z4 + z) * 8 + 2 * m];
+            im += part[((size_t)j * P.z4 + z) * 8 + 2 * m + 1];
+          }
+          vout[(size_t)mem[m] * ld_out + z] = make_float2(re, im);
+        }
+      } else {
+        for (int o = threadIdx.x; o < nz * 8; o += blockDim.x) {
+          const int z = o >> 3, r = o & 7;
+          double s = 0.0;
+          for (int j = 0; j < P.J; ++j) s += (double)part[((size_t)j * P.z4 + z) * 8 + r];
+          sB[z * 8 + r] = s;
+        }
+        __syncthreads();
+        // x[i] = sum_j Hinv[j][i] b[j]  (Hinv symmetric; consecutive threads read consecutive i)
+        const double* sH = reinterpret_cast<const double*>(stg + P.off_h);
+        for (int o = threadIdx.x; o < 4 * nz; o += blockDim.x) {
+          const int m = o / nz, i = o - m * nz;
+          if (mem[m] < 0) continue;
+          double re = 0.0, im = 0.0;
+          for (int j = 0; j < nz; ++j) {
+            const double h = sH[j * nz + i];
+            re = fma(h, sB[j * 8 + 2 * m], re);
+            im = fma(h, sB[j * 8 + 2 * m + 1], im);
+          }
+          vout[(size_t)mem[m] * ld_out + i] = make_float2((float)re, (float)im);
         }
       }
-#pragma unroll
-      for (int m = 0; m < 4; ++m)
-        if (m < nmem) out_t[(size_t)mem[m] * ldt + t] = acc[m];
     }
     __syncthreads();
+    if (nbuf == 1 && cn < nclass) {
+      issue<MODE>(P, smem, s_mem[0], what, members, vin, ld_in, hinv, cn);
+      cp_commit();
+    }
   }
+  cp_wait<0>();
 }
 
-__global__ void __launch_bounds__(CT_THREADS) k_contract_adj(const float* __restrict__ what,
-                                                             const int* __restrict__ members, int nclass, int nt,
-                                                             int nz, const float2* __restrict__ in_t, int ldt,
-                                                             float2* __restrict__ out_z, int ldz) {
-  extern __shared__ float smem_f[];
-  float* s_w = smem_f;
-  float2* s_v = reinterpret_cast<float2*>(s_w + ((nt * (nz + 1) + 1) & ~1));
-  float2* s_part = s_v + 4 * nt;
-  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
-    int mem[4];
-    const int nmem = load_members(members, c, mem);
-    load_what(s_w, what, c, nt, nz);
-    for (int i = threadIdx.x; i < 4 * nt; i += blockDim.x) {
-      const int m = i / nt, t = i - m * nt;
-      s_v[i] = m < nmem ? in_t[(size_t)mem[m] * ldt + t] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    adj_partials(s_w, s_v, nt, nz, nmem, s_part);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nmem * nz; i += blockDim.x) {
-      const int m = i / nz, z = i - m * nz;
-      float2 acc = make_float2(0.f, 0.f);
-      for (int w = 0; w < CT_WARPS; ++w) acc = cadd(acc, s_part[(w * 4 + m) * nz + z]);
-      out_z[(size_t)mem[m] * ldz + z] = acc;
-    }
-    __syncthreads();
+constexpr size_t SMEM_LIMIT = 227 * 1024;
+
+template <int MODE>
+ctof_status launch(const ctof_kernel_s* k, const float2* vin, int ld_in, float2* vout, int ld_out,
+                   const double* hinv, cudaStream_t st) {
+  int nbuf = 2;
+  Plan p = make_plan(MODE, k->nt, k->nz, 2, CT_THREADS);
+  if (p.total > SMEM_LIMIT) {
+    nbuf = 1;
+    p = make_plan(MODE, k->nt, k->nz, 1, CT_THREADS);
   }
-}
-
-// Tikhonov: x_hat = (G + lambda I)^-1 W_hat^T m_hat per member, with the FP64
-// Cholesky factor L (lower, row-major [nz][nz]) of G + lambda I.
-__global__ void __launch_bounds__(CT_THREADS) k_contract_tikhonov(
-    const float* __restrict__ what, const double* __restrict__ chol, const int* __restrict__ members, int nclass,
-    int nt, int nz, const float2* __restrict__ m_hat, int ldt, float2* __restrict__ x_hat, int ldz) {
-  extern __shared__ float smem_f[];
-  float* s_w = smem_f;
-  float2* s_v = reinterpret_cast<float2*>(s_w + ((nt * (nz + 1) + 1) & ~1));
-  float2* s_part = s_v + 4 * nt;
-  double* s_l = reinterpret_cast<double*>(s_part + CT_WARPS * 4 * nz);  // [nz][nz]
-  double* s_b = s_l + nz * nz;                                         // [4][2][nz]
-  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
-    int mem[4];
-    const int nmem = load_members(members, c, mem);
-    load_what(s_w, what, c, nt, nz);
-    for (int i = threadIdx.x; i < nz * nz; i += blockDim.x) s_l[i] = chol[(size_t)c * nz * nz + i];
-    for (int i = threadIdx.x; i < 4 * nt; i += blockDim.x) {
-      const int m = i / nt, t = i - m * nt;
-      s_v[i] = m < nmem ? m_hat[(size_t)mem[m] * ldt + t] : make_float2(0.f, 0.f);
-    }
-    __syncthreads();
-    adj_partials(s_w, s_v, nt, nz, nmem, s_part);
-    __syncthreads();
-    for (int i = threadIdx.x; i < nmem * nz; i += blockDim.x) {
-      const int m = i / nz, z = i - m * nz;
-      double ax = 0.0, ay = 0.0;
-      for (int w = 0; w < CT_WARPS; ++w) {
-        ax += (double)s_part[(w * 4 + m) * nz + z].x;
-        ay += (double)s_part[(w * 4 + m) * nz + z].y;
-      }
-      s_b[(m * 2 + 0) * nz + z] = ax;
-      s_b[(m * 2 + 1) * nz + z] = ay;
-    }
-    __syncthreads();
-    // one thread per real right-hand side: L y = b, then L^T x = y
-    if (threadIdx.x < 2 * nmem) {
-      double* b = s_b + threadIdx.x * nz;
-      for (int i = 0; i < nz; ++i) {
-        double acc = b[i];
-        for (int j = 0; j < i; ++j) acc -= s_l[i * nz + j] * b[j];
-        b[i] = acc / s_l[i * nz + i];
-      }
-      for (int i = nz - 1; i >= 0; --i) {
-        double acc = b[i];
-        for (int j = i + 1; j < nz; ++j) acc -= s_l[j * nz + i] * b[j];
-        b[i] = acc / s_l[i * nz + i];
-      }
-    }
-    __syncthreads();
-    for (int i = threadIdx.x; i < nmem * nz; i += blockDim.x) {
-      const int m = i / nz, z = i - m * nz;
-      x_hat[(size_t)mem[m] * ldz + z] =
-          make_float2((float)s_b[(m * 2 + 0) * nz + z], (float)s_b[(m * 2 + 1) * nz + z]);
-    }
-    __syncthreads();
-  }
-}
-
-size_t what_floats(int nt, int nz) { return (size_t)((nt * (nz + 1) + 1) & ~1); }
-
-int contract_grid(int nclass, size_t smem) {
-  int per_sm = (int)(200 * 1024 / (smem + 1024));
+  if (p.total > SMEM_LIMIT) return CTOF_EUNSUPPORTED;
+  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_contract<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.total));
+  int per_sm = (int)((228 * 1024) / (p.total + 1024 + 64));
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > 8) per_sm = 8;
-  int g = 152 * per_sm;
-  return nclass < g ? nclass : g;
+  if (per_sm > 4) per_sm = 4;
+  int grid = 152 * per_sm;
+  if (grid > k->nclass) grid = k->nclass;
+  k_contract<MODE><<<grid, CT_THREADS, p.total, st>>>(k->d_what, k->d_members, k->nclass, k->nt, k->nz, vin, ld_in,
+                                                      vout, ld_out, hinv, nbuf);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
 }
 
 }  // namespace
 
+size_t contract_smem_bytes(int nt, int nz) {
+  size_t worst = 0;
+  for (int mode = MODE_FWD; mode <= MODE_TIK; ++mode) {
+    const size_t b = make_plan(mode, nt, nz, 1, CT_THREADS).total;
+    worst = b > worst ? b : worst;
+  }
+  return worst;
+}
+
 ctof_status contract_forward(const ctof_kernel_s* k, const float2* in_z, float2* out_t, cudaStream_t st) {
-  const size_t sm = what_floats(k->nt, k->nz) * 4 + (size_t)4 * k->nz * 8;
-  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_contract_fwd, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_contract_fwd<<<contract_grid(k->nclass, sm), CT_THREADS, sm, st>>>(k->d_what, k->d_members, k->nclass, k->nt,
-                                                                       k->nz, in_z, k->ldz, out_t, k->ldt);
-  CTOF_CUDA_TRY(cudaGetLastError());
-  return CTOF_OK;
+  return launch<MODE_FWD>(k, in_z, k->ldz, out_t, k->ldt, nullptr, st);
 }
 
 ctof_status contract_adjoint(const ctof_kernel_s* k, const float2* in_t, float2* out_z, cudaStream_t st) {
-  const size_t sm = what_floats(k->nt, k->nz) * 4 + (size_t)4 * k->nt * 8 + (size_t)CT_WARPS * 4 * k->nz * 8;
-  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_contract_adj, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_contract_adj<<<contract_grid(k->nclass, sm), CT_THREADS, sm, st>>>(k->d_what, k->d_members, k->nclass, k->nt,
-                                                                       k->nz, in_t, k->ldt, out_z, k->ldz);
-  CTOF_CUDA_TRY(cudaGetLastError());
-  return CTOF_OK;
+  return launch<MODE_ADJ>(k, in_t, k->ldt, out_z, k->ldz, nullptr, st);
 }
 
-ctof_status contract_tikhonov(const ctof_kernel_s* k, const double* chol, const float2* m_hat, float2* x_hat,
+ctof_status contract_tikhonov(const ctof_kernel_s* k, const double* hinv, const float2* m_hat, float2* x_hat,
                               cudaStream_t st) {
-  const int nt = k->nt, nz = k->nz;
-  size_t sm = what_floats(nt, nz) * 4 + (size_t)4 * nt * 8 + (size_t)CT_WARPS * 4 * nz * 8;
-  sm = (sm + 7) & ~(size_t)7;
-  sm += ((size_t)nz * nz + 8 * (size_t)nz) * 8;
-  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_contract_tikhonov, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-  k_contract_tikhonov<<<contract_grid(k->nclass, sm), CT_THREADS, sm, st>>>(
-      k->d_what, chol, k->d_members, k->nclass, nt, nz, m_hat, k->ldt, x_hat, k->ldz);
-  CTOF_CUDA_TRY(cudaGetLastError());
-  return CTOF_OK;
+  return launch<MODE_TIK>(k, m_hat, k->ldt, x_hat, k->ldz, hinv, st);
 }

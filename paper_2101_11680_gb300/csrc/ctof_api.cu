@@ -63,12 +63,9 @@ ctof_status validate(const ctof_optics* o, const ctof_grid* g) {
   if (g->nz > 64 || g->nt > 1024) return CTOF_EUNSUPPORTED;
   // one frequency class (W_hat block, vectors, partial sums) must fit in shared memory
   {
-    const size_t nt = (size_t)g->nt, nz = (size_t)g->nz;
-    const size_t w = (nt * (nz + 1) + 1) & ~(size_t)1;
     const size_t admm = contract_admm_smem_bytes(g->nt, g->nz, 1);
-    const size_t adj = w * 4 + 4 * nt * 8 + 32 * nz * 8;
-    const size_t tik = ((adj + 7) & ~(size_t)7) + (nz * nz + 8 * nz) * 8;
-    if (admm > 227 * 1024 || tik > 227 * 1024) return CTOF_EUNSUPPORTED;
+    const size_t other = contract_smem_bytes(g->nt, g->nz);
+    if (admm > 227 * 1024 || other > 227 * 1024) return CTOF_EUNSUPPORTED;
   }
   if (g->conv_mode == CTOF_LINEAR) {
     if (g->nx < 4 || g->nx > 256) return CTOF_EUNSUPPORTED;
@@ -329,17 +326,17 @@ ctof_status admm_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream
 ctof_status tikhonov_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st, double* lambda_out) {
   const double lambda = prm->tik_lambda_rel * k->gram_max;
   if (!(lambda > 0.0) || !isfinite(lambda)) return CTOF_EINVAL;
-  if (!k->d_tik_chol) {
+  if (!k->d_tik_hinv) {
     void* p = nullptr;
     if (cudaMalloc(&p, (size_t)k->nclass * k->nz * k->nz * sizeof(double)) != cudaSuccess) return CTOF_ENOMEM;
-    k->d_tik_chol = static_cast<double*>(p);
+    k->d_tik_hinv = static_cast<double*>(p);
     k->tik_lambda = -1.0;
   }
   if (k->tik_lambda != lambda) CTOF_TRY(build_tikhonov_factors(k, lambda, st));
   *lambda_out = lambda;
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_scalars, 0, 16 * sizeof(double), st));
   CTOF_TRY(fft_forward_planes(k, k->d_mstage, k->nt, k->n, k->n, k->n, k->d_inter_t, k->d_spec_t, k->ldt, st));
-  CTOF_TRY(contract_tikhonov(k, k->d_tik_chol, k->d_spec_t, k->d_spec_z, st));
+  CTOF_TRY(contract_tikhonov(k, k->d_tik_hinv, k->d_spec_t, k->d_spec_z, st));
   return fft_inverse_planes(k, k->d_spec_z, k->ldz, k->nz, k->n, k->n, k->d_inter_z, k->d_vstage, k->n, st);
 }
 
@@ -512,7 +509,7 @@ void ctof_kernel_destroy(ctof_kernel k) {
   if (k->d_qhi) cudaFree(k->d_qhi);
   if (k->d_bt_cinv) cudaFree(k->d_bt_cinv);
   if (k->d_batch) cudaFree(k->d_batch);
-  if (k->d_tik_chol) cudaFree(k->d_tik_chol);
+  if (k->d_tik_hinv) cudaFree(k->d_tik_hinv);
   if (k->d_w) cudaFree(k->d_w);
   if (k->d_base) cudaFree(k->d_base);
   delete k;
@@ -655,7 +652,7 @@ ctof_status ctof_kernel_get_info(ctof_kernel k, ctof_kernel_info* info) {
   info->scale = k->scale;
   info->gram_max_diag = k->gram_max;
   info->device_bytes = k->bytes + (k->d_w ? (size_t)k->nt * k->nz * k->q * k->q * sizeof(double) : 0) +
-                       (k->d_tik_chol ? (size_t)k->nclass * k->nz * k->nz * sizeof(double) : 0);
+                       (k->d_tik_hinv ? (size_t)k->nclass * k->nz * k->nz * sizeof(double) : 0);
   return CTOF_OK;
 }
 

@@ -61,7 +61,7 @@ struct ctof_kernel_s {
 
   // Tikhonov cache: FP64 Cholesky factors of G + lambda I
   double tik_lambda;
-  double* d_tik_chol;  // [nclass][nz][nz] (separate allocation, lazily made)
+  double* d_tik_hinv;  // [nclass][nz][nz] FP64 (G + lambda I)^-1 (separate allocation, lazily made)
 
   // ADMM graph cache
   cudaGraphExec_t graph;
@@ -121,11 +121,13 @@ ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* 
                             float inv_scale, float rho, cudaStream_t st);
 
 // ---- contract.cu --------------------------------------------------------
+// shared memory the contraction kernels need at this size (single-buffered worst case)
+size_t contract_smem_bytes(int nt, int nz);
 ctof_status contract_forward(const ctof_kernel_s* k, const float2* in_z, float2* out_t, cudaStream_t st);
 ctof_status contract_adjoint(const ctof_kernel_s* k, const float2* in_t, float2* out_z, cudaStream_t st);
 ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const float2* s_hat,
                           float2* x_hat, float2* kx_hat, float inv_scale, cudaStream_t st);
-ctof_status contract_tikhonov(const ctof_kernel_s* k, const double* chol, const float2* m_hat,
+ctof_status contract_tikhonov(const ctof_kernel_s* k, const double* hinv, const float2* m_hat,
                               float2* x_hat, cudaStream_t st);
 size_t contract_admm_smem_bytes(int nt, int nz, int nbuf);
 

@@ -42,7 +42,7 @@ PEAK = 1e5
 X0_LAMBDA = 1e-3
 # Inference-time data-consistency steps after the last stage and their relative Tikhonov lambda.
 DC_STEPS = 2
-DC_LAMBDA = 1e-4
+DC_LAMBDA = 1e-3
 
 
 def _render(args):
