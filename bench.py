@@ -382,16 +382,20 @@ def run_learned(args, cfg):
     calib_res = [LT.data_residual(kern, kern.reconstruct(m, params), m) for m, _ in calib]
     threshold = 1.5 * float(np.median(calib_res))
     count = args.steps
-    data = LT.eval_set(kern, g, range(10000, 10000 + count + args.warmup), cfg["peak"])
+    data = LT.eval_set(kern, g, range(10000, 10000 + count), cfg["peak"])
     ms = torch.stack([m for m, _ in data])
     outs = torch.empty((len(data), cfg["nz"], cfg["n"], cfg["n"]), device="cuda")
     res = torch.empty(len(data), device="cuda", dtype=torch.float64)
     m_norm = torch.stack([m.double().norm() for m, _ in data])
     pred = torch.empty((cfg["nt"], cfg["n"], cfg["n"]), device="cuda")
 
+    lb = args.batch or count  # volumes per learned call (W_hat read once per class for all of them)
+
     def learned_pass(lo, hi):
+        for c in range(lo, hi, lb):
+            e = min(hi, c + lb)
+            net.reconstruct(kern, ms[c:e], out=outs[c:e])
         for i in range(lo, hi):
-            net.reconstruct(kern, ms[i:i + 1], out=outs[i:i + 1])
             kern.forward(outs[i], out=pred)
             res[i] = (pred.double() - ms[i].double()).norm() / m_norm[i]
         r = res[lo:hi].cpu()
@@ -400,7 +404,8 @@ def run_learned(args, cfg):
             kern.reconstruct(ms[i], params, out=outs[i])
         return fb
 
-    learned_pass(count, count + args.warmup)
+    for _ in range(max(1, args.warmup)):
+        learned_pass(0, count)
     torch.cuda.synchronize()
     clocks = ClockSampler(0)
     clocks.start()
@@ -451,6 +456,7 @@ def run_learned(args, cfg):
             "config": {"workload": cfg["workload"], "stages": stages, "trained_on": meta.get("grid"),
                        "x0": "Tikhonov (lambda %g max Gram diag)" % meta.get("x0_lambda_rel", 0.0),
                        "data_consistency_steps": LT.DC_STEPS, "dc_lambda_rel": LT.DC_LAMBDA,
+                       "volumes_per_call": lb,
                        "training_phantoms": meta.get("phantoms"),
                        "l2": "inputs larger than L2 (W_hat %.0f MB streamed per operator application)"
                              % (kern.info.n_class * cfg["nt"] * cfg["nz"] * 4 / 1e6)},

@@ -512,12 +512,12 @@ ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st) {
   return CTOF_OK;
 }
 
-ctof_status build_tikhonov_factors(ctof_kernel_s* k, double lambda, cudaStream_t st) {
+ctof_status build_tikhonov_factors(ctof_kernel_s* k, int slot, double lambda, cudaStream_t st) {
   const int nz = k->nz;
   const size_t fsm = (size_t)2 * nz * (nz + 1) * sizeof(double);
   CTOF_CUDA_TRY(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
-  k_factor<<<k->nclass, 128, fsm, st>>>(k->d_gram, k->d_lap, nz, 0.0, lambda, 1, nullptr, k->d_tik_hinv);
+  k_factor<<<k->nclass, 128, fsm, st>>>(k->d_gram, k->d_lap, nz, 0.0, lambda, 1, nullptr, k->d_tik_hinv[slot]);
   CTOF_CUDA_TRY(cudaGetLastError());
-  k->tik_lambda = lambda;
+  k->tik_lambda[slot] = lambda;
   return CTOF_OK;
 }

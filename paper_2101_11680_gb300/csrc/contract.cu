@@ -10,8 +10,11 @@
 //
 // Persistent CTAs walk the classes with a two-stage cp.async pipeline: while
 // one class is computed, the next class's W_hat block (contiguous in HBM,
-// rows of z4 floats), its member vectors and, for Tikhonov, its FP64 inverse
-// stream into the other shared-memory stage.  W_hat rows land with a stride
+// rows of z4 floats) and, for Tikhonov, its FP64 inverse stream into the other
+// shared-memory stage.  A launch may carry several volumes that share the
+// kernel (`nvol`, spectra `vstride` apart): the class block then stays in
+// shared memory while the volumes' member vectors stream through their own
+// double buffer, so W_hat is read once for all of them.  W_hat rows land with a stride
 // of 4*(z4/4 | 1) floats, so eight consecutive rows read with float4 loads hit
 // eight distinct 16-byte bank groups.  The arithmetic is FP32 FMA (FP64 for
 // the Z x Z solve): these contractions move 1 FLOP per 2 bytes of W_hat and
@@ -42,14 +45,16 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Shared-memory plan of one pipeline stage and of the per-CTA scratch.
+// Shared-memory plan: nbuf W stages (W_hat block, Tikhonov inverse), nbuf
+// vector stages, then the per-CTA scratch.
 struct Plan {
   int nt, nz, z4, q, sw;   // q = z4/4 float4 chunks per row, sw = smem row stride (floats)
   int J;                   // adjoint: row groups
-  size_t off_vec, off_h;   // byte offsets inside a stage
-  size_t stage;            // bytes per stage
-  size_t off_part, off_b;  // byte offsets of the scratch after the stages
-  size_t total;            // bytes for nbuf stages + scratch
+  size_t off_h;            // Tikhonov inverse inside a W stage
+  size_t wst, vst;         // bytes per W stage / vector stage
+  size_t off_v;            // first vector stage
+  size_t off_part, off_b;  // scratch
+  size_t total;
 };
 
 __host__ __device__ inline size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
@@ -63,13 +68,11 @@ __host__ __device__ inline Plan make_plan(int mode, int nt, int nz, int nbuf, in
   p.sw = 4 * (p.q | 1);
   const int pairs = 2 * p.q;
   p.J = threads / pairs > 0 ? threads / pairs : 1;
-  size_t b = al16((size_t)nt * p.sw * 4);
-  p.off_vec = b;
-  b += al16(mode == MODE_FWD ? (size_t)p.z4 * 8 * 4 : (size_t)nt * 8 * 4);
-  p.off_h = b;
-  if (mode == MODE_TIK) b += al16((size_t)nz * nz * 8);
-  p.stage = b;
-  size_t s = b * nbuf;
+  p.off_h = al16((size_t)nt * p.sw * 4);
+  p.wst = p.off_h + (mode == MODE_TIK ? al16((size_t)nz * nz * 8) : 0);
+  p.vst = al16(mode == MODE_FWD ? (size_t)p.z4 * 8 * 4 : (size_t)nt * 8 * 4);
+  p.off_v = p.wst * nbuf;
+  size_t s = p.off_v + p.vst * nbuf;
   p.off_part = s;
   if (mode != MODE_FWD) s += al16((size_t)p.J * p.z4 * 8 * 4);
   p.off_b = s;
@@ -78,11 +81,10 @@ __host__ __device__ inline Plan make_plan(int mode, int nt, int nz, int nbuf, in
   return p;
 }
 
-// Issue the copies of class c into stage buffer `st` (members cached in s_mem).
+// Copies of class c's W_hat block (and Tikhonov inverse) into a W stage.
 template <int MODE>
-__device__ __forceinline__ void issue(const Plan& P, char* stg, int* s_mem, const float* __restrict__ what,
-                                      const int* __restrict__ members, const float2* __restrict__ vin, int ld_in,
-                                      const double* __restrict__ hinv, int c) {
+__device__ __forceinline__ void issue_w(const Plan& P, char* stg, int* s_mem, const float* __restrict__ what,
+                                        const int* __restrict__ members, const double* __restrict__ hinv, int c) {
   float* sW = reinterpret_cast<float*>(stg);
   const float* src = what + (size_t)c * P.nt * P.z4;
   const int chunks = P.nt * P.q;
@@ -91,7 +93,18 @@ __device__ __forceinline__ void issue(const Plan& P, char* stg, int* s_mem, cons
     cp_async16(sW + t * P.sw + 4 * k, src + (size_t)t * P.z4 + 4 * k);
   }
   if (threadIdx.x < 4) s_mem[threadIdx.x] = members[c * 4 + threadIdx.x];
-  float2* sV = reinterpret_cast<float2*>(stg + P.off_vec);  // [row][4] complex = [row][8] floats
+  if (MODE == MODE_TIK) {
+    double* sH = reinterpret_cast<double*>(stg + P.off_h);
+    const double* hs = hinv + (size_t)c * P.nz * P.nz;
+    for (int i = threadIdx.x; i < P.nz * P.nz; i += blockDim.x) cp_async8(sH + i, hs + i);
+  }
+}
+
+// Copies of class c's member vectors of one volume into a vector stage: [row][4] complex.
+template <int MODE>
+__device__ __forceinline__ void issue_v(const Plan& P, char* vst, const int* __restrict__ members,
+                                        const float2* __restrict__ vin, int ld_in, int c) {
+  float2* sV = reinterpret_cast<float2*>(vst);
   const int rows = MODE == MODE_FWD ? P.z4 : P.nt;
   const int valid = MODE == MODE_FWD ? P.nz : P.nt;
   for (int i = threadIdx.x; i < 4 * rows; i += blockDim.x) {
@@ -102,18 +115,12 @@ __device__ __forceinline__ void issue(const Plan& P, char* stg, int* s_mem, cons
     else
       sV[r * 4 + m] = make_float2(0.f, 0.f);
   }
-  if (MODE == MODE_TIK) {
-    double* sH = reinterpret_cast<double*>(stg + P.off_h);
-    const double* hs = hinv + (size_t)c * P.nz * P.nz;
-    for (int i = threadIdx.x; i < P.nz * P.nz; i += blockDim.x) cp_async8(sH + i, hs + i);
-  }
 }
 
 // out[t][0..7] = sum_z W[t][z] x[z][0..7]  (one thread per row t)
-__device__ __forceinline__ void compute_fwd(const Plan& P, const char* stg, const int* s_mem,
+__device__ __forceinline__ void compute_fwd(const Plan& P, const float* sW, const char* sv, const int* s_mem,
                                             float2* __restrict__ out_t, int ldt) {
-  const float* sW = reinterpret_cast<const float*>(stg);
-  const float4* sX = reinterpret_cast<const float4*>(stg + P.off_vec);  // [z][2] float4
+  const float4* sX = reinterpret_cast<const float4*>(sv);  // [z][2] float4
   for (int t = threadIdx.x; t < P.nt; t += blockDim.x) {
     float acc[8];
 #pragma unroll
@@ -143,9 +150,8 @@ __device__ __forceinline__ void compute_fwd(const Plan& P, const char* stg, cons
 
 // Adjoint partial sums: thread (j, k, h) sums rows t = j (mod J) for z in chunk k
 // and right-hand sides 4h..4h+3; partials land in part[j][z][8].
-__device__ __forceinline__ void compute_adj_partials(const Plan& P, const char* stg, float* part) {
-  const float* sW = reinterpret_cast<const float*>(stg);
-  const float* sC = reinterpret_cast<const float*>(stg + P.off_vec);  // [t][8]
+__device__ __forceinline__ void compute_adj_partials(const Plan& P, const float* sW, const char* sv, float* part) {
+  const float* sC = reinterpret_cast<const float*>(sv);  // [t][8]
   const int pairs = 2 * P.q;
   for (int u = threadIdx.x; u < P.J * pairs; u += blockDim.x) {
     const int j = u / pairs, pk = u - j * pairs, k = pk >> 1, h = pk & 1;
@@ -176,74 +182,91 @@ __device__ __forceinline__ void compute_adj_partials(const Plan& P, const char* 
 template <int MODE>
 __global__ void __launch_bounds__(CT_THREADS) k_contract(const float* __restrict__ what,
                                                          const int* __restrict__ members, int nclass, int nt, int nz,
-                                                         const float2* __restrict__ vin, int ld_in,
-                                                         float2* __restrict__ vout, int ld_out,
-                                                         const double* __restrict__ hinv, int nbuf) {
+                                                         const float2* __restrict__ vin, int ld_in, size_t in_vstride,
+                                                         float2* __restrict__ vout, int ld_out, size_t out_vstride,
+                                                         int nvol, const double* __restrict__ hinv, int nbuf) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int s_mem[2][4];
   const Plan P = make_plan(MODE, nt, nz, nbuf, blockDim.x);
   float* part = reinterpret_cast<float*>(smem + P.off_part);
   double* sB = reinterpret_cast<double*>(smem + P.off_b);
-  int it = 0;
-  if (blockIdx.x < nclass)
-    issue<MODE>(P, smem, s_mem[0], what, members, vin, ld_in, hinv, blockIdx.x);
+  const int G = gridDim.x;
+  if (blockIdx.x < nclass) {
+    issue_w<MODE>(P, smem, s_mem[0], what, members, hinv, blockIdx.x);
+    issue_v<MODE>(P, smem + P.off_v, members, vin, ld_in, blockIdx.x);
+  }
   cp_commit();
-  for (int c = blockIdx.x; c < nclass; c += gridDim.x, ++it) {
-    const int cur = nbuf == 2 ? (it & 1) : 0;
-    const int cn = c + gridDim.x;
-    if (nbuf == 2) {
-      if (cn < nclass) issue<MODE>(P, smem + (cur ^ 1) * P.stage, s_mem[cur ^ 1], what, members, vin, ld_in, hinv, cn);
-      cp_commit();
-      cp_wait<1>();
-    } else {
-      cp_wait<0>();
-    }
-    __syncthreads();
-    const char* stg = smem + cur * P.stage;
-    const int* mem = s_mem[cur];
-    if (MODE == MODE_FWD) {
-      compute_fwd(P, stg, mem, vout, ld_out);
-    } else {
-      compute_adj_partials(P, stg, part);
-      __syncthreads();
-      if (MODE == MODE_ADJ) {
-        for (int o = threadIdx.x; o < 4 * nz; o += blockDim.x) {
-          const int m = o / nz, z = o - m * nz;
-          if (mem[m] < 0) continue;
-          float re = 0.f, im = 0.f;
-          for (int j = 0; j < P.J; ++j) {
-            re += part[((size_t)j * P.z4 + z) * 8 + 2 * m];
-            im += part[((size_t)j * P.z4 + z) * 8 + 2 * m + 1];
-          }
-          vout[(size_t)mem[m] * ld_out + z] = make_float2(re, im);
-        }
+  int step = 0, ci = 0;
+  for (int c = blockIdx.x; c < nclass; c += G, ++ci) {
+    const int wcur = nbuf == 2 ? (ci & 1) : 0;
+    for (int b = 0; b < nvol; ++b, ++step) {
+      const int vcur = nbuf == 2 ? (step & 1) : 0;
+      int nc = c, nb = b + 1;
+      if (nb == nvol) {
+        nc = c + G;
+        nb = 0;
+      }
+      if (nbuf == 2) {
+        if (b == 0 && c + G < nclass)
+          issue_w<MODE>(P, smem + (wcur ^ 1) * P.wst, s_mem[wcur ^ 1], what, members, hinv, c + G);
+        if (nc < nclass)
+          issue_v<MODE>(P, smem + P.off_v + (vcur ^ 1) * P.vst, members, vin + (size_t)nb * in_vstride, ld_in, nc);
+        cp_commit();
+        cp_wait<1>();
       } else {
-        for (int o = threadIdx.x; o < nz * 8; o += blockDim.x) {
-          const int z = o >> 3, r = o & 7;
-          double s = 0.0;
-          for (int j = 0; j < P.J; ++j) s += (double)part[((size_t)j * P.z4 + z) * 8 + r];
-          sB[z * 8 + r] = s;
-        }
+        cp_wait<0>();
+      }
+      __syncthreads();
+      const char* wst = smem + wcur * P.wst;
+      const float* sW = reinterpret_cast<const float*>(wst);
+      const char* sv = smem + P.off_v + vcur * P.vst;
+      const int* mem = s_mem[wcur];
+      float2* out = vout + (size_t)b * out_vstride;
+      if (MODE == MODE_FWD) {
+        compute_fwd(P, sW, sv, mem, out, ld_out);
+      } else {
+        compute_adj_partials(P, sW, sv, part);
         __syncthreads();
-        // x[i] = sum_j Hinv[j][i] b[j]  (Hinv symmetric; consecutive threads read consecutive i)
-        const double* sH = reinterpret_cast<const double*>(stg + P.off_h);
-        for (int o = threadIdx.x; o < 4 * nz; o += blockDim.x) {
-          const int m = o / nz, i = o - m * nz;
-          if (mem[m] < 0) continue;
-          double re = 0.0, im = 0.0;
-          for (int j = 0; j < nz; ++j) {
-            const double h = sH[j * nz + i];
-            re = fma(h, sB[j * 8 + 2 * m], re);
-            im = fma(h, sB[j * 8 + 2 * m + 1], im);
+        if (MODE == MODE_ADJ) {
+          for (int o = threadIdx.x; o < 4 * nz; o += blockDim.x) {
+            const int m = o / nz, z = o - m * nz;
+            if (mem[m] < 0) continue;
+            float re = 0.f, im = 0.f;
+            for (int j = 0; j < P.J; ++j) {
+              re += part[((size_t)j * P.z4 + z) * 8 + 2 * m];
+              im += part[((size_t)j * P.z4 + z) * 8 + 2 * m + 1];
+            }
+            out[(size_t)mem[m] * ld_out + z] = make_float2(re, im);
           }
-          vout[(size_t)mem[m] * ld_out + i] = make_float2((float)re, (float)im);
+        } else {
+          for (int o = threadIdx.x; o < nz * 8; o += blockDim.x) {
+            const int z = o >> 3, r = o & 7;
+            double s = 0.0;
+            for (int j = 0; j < P.J; ++j) s += (double)part[((size_t)j * P.z4 + z) * 8 + r];
+            sB[z * 8 + r] = s;
+          }
+          __syncthreads();
+          // x[i] = sum_j Hinv[j][i] b[j]  (Hinv symmetric; consecutive threads read consecutive i)
+          const double* sH = reinterpret_cast<const double*>(wst + P.off_h);
+          for (int o = threadIdx.x; o < 4 * nz; o += blockDim.x) {
+            const int m = o / nz, i = o - m * nz;
+            if (mem[m] < 0) continue;
+            double re = 0.0, im = 0.0;
+            for (int j = 0; j < nz; ++j) {
+              const double h = sH[j * nz + i];
+              re = fma(h, sB[j * 8 + 2 * m], re);
+              im = fma(h, sB[j * 8 + 2 * m + 1], im);
+            }
+            out[(size_t)mem[m] * ld_out + i] = make_float2((float)re, (float)im);
+          }
         }
       }
-    }
-    __syncthreads();
-    if (nbuf == 1 && cn < nclass) {
-      issue<MODE>(P, smem, s_mem[0], what, members, vin, ld_in, hinv, cn);
-      cp_commit();
+      __syncthreads();
+      if (nbuf == 1 && nc < nclass) {
+        if (nb == 0) issue_w<MODE>(P, smem, s_mem[0], what, members, hinv, nc);
+        issue_v<MODE>(P, smem + P.off_v, members, vin + (size_t)nb * in_vstride, ld_in, nc);
+        cp_commit();
+      }
     }
   }
   cp_wait<0>();
@@ -252,8 +275,9 @@ __global__ void __launch_bounds__(CT_THREADS) k_contract(const float* __restrict
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 template <int MODE>
-ctof_status launch(const ctof_kernel_s* k, const float2* vin, int ld_in, float2* vout, int ld_out,
-                   const double* hinv, cudaStream_t st) {
+ctof_status launch(const ctof_kernel_s* k, int nvol, const float2* vin, int ld_in, size_t in_vstride, float2* vout,
+                   int ld_out, size_t out_vstride, const double* hinv, cudaStream_t st) {
+  if (nvol < 1) return CTOF_EINVAL;
   int nbuf = 2;
   Plan p = make_plan(MODE, k->nt, k->nz, 2, CT_THREADS);
   if (p.total > SMEM_LIMIT) {
@@ -268,7 +292,7 @@ ctof_status launch(const ctof_kernel_s* k, const float2* vin, int ld_in, float2*
   int grid = 152 * per_sm;
   if (grid > k->nclass) grid = k->nclass;
   k_contract<MODE><<<grid, CT_THREADS, p.total, st>>>(k->d_what, k->d_members, k->nclass, k->nt, k->nz, vin, ld_in,
-                                                      vout, ld_out, hinv, nbuf);
+                                                      in_vstride, vout, ld_out, out_vstride, nvol, hinv, nbuf);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
@@ -285,14 +309,32 @@ size_t contract_smem_bytes(int nt, int nz) {
 }
 
 ctof_status contract_forward(const ctof_kernel_s* k, const float2* in_z, float2* out_t, cudaStream_t st) {
-  return launch<MODE_FWD>(k, in_z, k->ldz, out_t, k->ldt, nullptr, st);
+  return contract_forward_batch(k, 1, in_z, out_t, st);
 }
 
 ctof_status contract_adjoint(const ctof_kernel_s* k, const float2* in_t, float2* out_z, cudaStream_t st) {
-  return launch<MODE_ADJ>(k, in_t, k->ldt, out_z, k->ldz, nullptr, st);
+  return contract_adjoint_batch(k, 1, in_t, out_z, st);
 }
 
 ctof_status contract_tikhonov(const ctof_kernel_s* k, const double* hinv, const float2* m_hat, float2* x_hat,
                               cudaStream_t st) {
-  return launch<MODE_TIK>(k, m_hat, k->ldt, x_hat, k->ldz, hinv, st);
+  return contract_tikhonov_batch(k, 1, hinv, m_hat, x_hat, st);
+}
+
+ctof_status contract_forward_batch(const ctof_kernel_s* k, int nvol, const float2* in_z, float2* out_t,
+                                   cudaStream_t st) {
+  return launch<MODE_FWD>(k, nvol, in_z, k->ldz, (size_t)k->nf * k->ldz, out_t, k->ldt, (size_t)k->nf * k->ldt,
+                          nullptr, st);
+}
+
+ctof_status contract_adjoint_batch(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z,
+                                   cudaStream_t st) {
+  return launch<MODE_ADJ>(k, nvol, in_t, k->ldt, (size_t)k->nf * k->ldt, out_z, k->ldz, (size_t)k->nf * k->ldz,
+                          nullptr, st);
+}
+
+ctof_status contract_tikhonov_batch(const ctof_kernel_s* k, int nvol, const double* hinv, const float2* m_hat,
+                                    float2* x_hat, cudaStream_t st) {
+  return launch<MODE_TIK>(k, nvol, m_hat, k->ldt, (size_t)k->nf * k->ldt, x_hat, k->ldz, (size_t)k->nf * k->ldz, hinv,
+                          st);
 }

@@ -25,21 +25,6 @@ void ctof_set_last_error_text(const char* msg) { snprintf(g_last_error, sizeof(g
 
 namespace {
 
-struct DeviceGuard {
-  int prev = -1;
-  bool ok = true;
-  explicit DeviceGuard(int dev) {
-    if (cudaGetDevice(&prev) != cudaSuccess) {
-      ok = false;
-      return;
-    }
-    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 bool finite_pos(double v) { return isfinite(v) && v > 0.0; }
 
@@ -323,20 +308,39 @@ ctof_status admm_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream
   return CTOF_OK;
 }
 
+}  // namespace
+
+ctof_status tikhonov_inverse(ctof_kernel_s* k, double lambda, const double** hinv, cudaStream_t st) {
+  if (!(lambda > 0.0) || !isfinite(lambda)) return CTOF_EINVAL;
+  int slot = k->tik_lambda[0] == lambda ? 0 : (k->tik_lambda[1] == lambda ? 1 : -1);
+  if (slot < 0) {
+    slot = 1 - k->tik_last;  // replace the slot not used last
+    if (!k->d_tik_hinv[slot]) {
+      void* p = nullptr;
+      if (cudaMalloc(&p, (size_t)k->nclass * k->nz * k->nz * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return CTOF_ENOMEM;
+      }
+      k->d_tik_hinv[slot] = static_cast<double*>(p);
+    }
+    k->tik_lambda[slot] = -1.0;
+    CTOF_TRY(build_tikhonov_factors(k, slot, lambda, st));
+  }
+  k->tik_last = slot;
+  *hinv = k->d_tik_hinv[slot];
+  return CTOF_OK;
+}
+
+namespace {
+
 ctof_status tikhonov_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st, double* lambda_out) {
   const double lambda = prm->tik_lambda_rel * k->gram_max;
-  if (!(lambda > 0.0) || !isfinite(lambda)) return CTOF_EINVAL;
-  if (!k->d_tik_hinv) {
-    void* p = nullptr;
-    if (cudaMalloc(&p, (size_t)k->nclass * k->nz * k->nz * sizeof(double)) != cudaSuccess) return CTOF_ENOMEM;
-    k->d_tik_hinv = static_cast<double*>(p);
-    k->tik_lambda = -1.0;
-  }
-  if (k->tik_lambda != lambda) CTOF_TRY(build_tikhonov_factors(k, lambda, st));
+  const double* hinv = nullptr;
+  CTOF_TRY(tikhonov_inverse(k, lambda, &hinv, st));
   *lambda_out = lambda;
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_scalars, 0, 16 * sizeof(double), st));
   CTOF_TRY(fft_forward_planes(k, k->d_mstage, k->nt, k->n, k->n, k->n, k->d_inter_t, k->d_spec_t, k->ldt, st));
-  CTOF_TRY(contract_tikhonov(k, k->d_tik_hinv, k->d_spec_t, k->d_spec_z, st));
+  CTOF_TRY(contract_tikhonov(k, hinv, k->d_spec_t, k->d_spec_z, st));
   return fft_inverse_planes(k, k->d_spec_z, k->ldz, k->nz, k->n, k->n, k->d_inter_z, k->d_vstage, k->n, st);
 }
 
@@ -509,7 +513,8 @@ void ctof_kernel_destroy(ctof_kernel k) {
   if (k->d_qhi) cudaFree(k->d_qhi);
   if (k->d_bt_cinv) cudaFree(k->d_bt_cinv);
   if (k->d_batch) cudaFree(k->d_batch);
-  if (k->d_tik_hinv) cudaFree(k->d_tik_hinv);
+  for (int i = 0; i < 2; ++i)
+    if (k->d_tik_hinv[i]) cudaFree(k->d_tik_hinv[i]);
   if (k->d_w) cudaFree(k->d_w);
   if (k->d_base) cudaFree(k->d_base);
   delete k;
@@ -542,7 +547,8 @@ ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, 
   k->ldz = ctof_round_up(k->nz, 8);
   k->symmetric = grid->dx_mm == grid->dy_mm;
   k->r_min = optics->clamp_r ? 0.5 * std::min(grid->dx_mm, std::min(grid->dy_mm, grid->dz_mm)) : 0.0;
-  k->tik_lambda = -1.0;
+  k->tik_lambda[0] = k->tik_lambda[1] = -1.0;
+  k->tik_last = 1;
   for (int i = 0; i < 4; ++i) k->tune_pb[i] = 8;
   {
     static std::atomic<unsigned long long> next_id{1};
@@ -651,8 +657,9 @@ ctof_status ctof_kernel_get_info(ctof_kernel k, ctof_kernel_info* info) {
   info->nz = k->nz;
   info->scale = k->scale;
   info->gram_max_diag = k->gram_max;
+  const size_t tik_bytes = (size_t)k->nclass * k->nz * k->nz * sizeof(double);
   info->device_bytes = k->bytes + (k->d_w ? (size_t)k->nt * k->nz * k->q * k->q * sizeof(double) : 0) +
-                       (k->d_tik_hinv ? (size_t)k->nclass * k->nz * k->nz * sizeof(double) : 0);
+                       ((k->d_tik_hinv[0] ? 1 : 0) + (k->d_tik_hinv[1] ? 1 : 0)) * tik_bytes;
   return CTOF_OK;
 }
 

@@ -60,8 +60,11 @@ struct ctof_kernel_s {
   double* d_scalars;   // [16] device scalars (beta, max reductions, flags)
 
   // Tikhonov cache: FP64 Cholesky factors of G + lambda I
-  double tik_lambda;
-  double* d_tik_hinv;  // [nclass][nz][nz] FP64 (G + lambda I)^-1 (separate allocation, lazily made)
+  // Tikhonov inverses (G + lambda I)^-1, FP64 [nclass][nz][nz], for the two
+  // most recently used lambdas (separate allocations, made on first use)
+  double tik_lambda[2];
+  double* d_tik_hinv[2];
+  int tik_last;  // slot used last
 
   // ADMM graph cache
   cudaGraphExec_t graph;
@@ -88,6 +91,23 @@ struct ctof_kernel_s {
   int tune_pb[4];
   int tuned;
   unsigned long long uid;  // unique per handle (batch graph cache key)
+};
+
+// Makes `dev` current for a scope and restores the previous device after it.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = true;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) {
+      ok = false;
+      return;
+    }
+    if (prev != dev && cudaSetDevice(dev) != cudaSuccess) ok = false;
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
 };
 
 // ---- fft.cu -------------------------------------------------------------
@@ -124,6 +144,13 @@ ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* 
 // shared memory the contraction kernels need at this size (single-buffered worst case)
 size_t contract_smem_bytes(int nt, int nz);
 ctof_status contract_forward(const ctof_kernel_s* k, const float2* in_z, float2* out_t, cudaStream_t st);
+// nvol volumes sharing the kernel; spectra [nvol][nf][ld] (W_hat read once per class for all)
+ctof_status contract_forward_batch(const ctof_kernel_s* k, int nvol, const float2* in_z, float2* out_t,
+                                   cudaStream_t st);
+ctof_status contract_adjoint_batch(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z,
+                                   cudaStream_t st);
+ctof_status contract_tikhonov_batch(const ctof_kernel_s* k, int nvol, const double* hinv, const float2* m_hat,
+                                    float2* x_hat, cudaStream_t st);
 ctof_status contract_adjoint(const ctof_kernel_s* k, const float2* in_t, float2* out_z, cudaStream_t st);
 ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const float2* s_hat,
                           float2* x_hat, float2* kx_hat, float inv_scale, cudaStream_t st);
@@ -139,7 +166,9 @@ ctof_status batch_tikhonov_contract(const ctof_kernel_s* k, int batch, const flo
 
 // ---- build.cu ----------------------------------------------------------
 ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st);
-ctof_status build_tikhonov_factors(ctof_kernel_s* k, double lambda, cudaStream_t st);
+ctof_status build_tikhonov_factors(ctof_kernel_s* k, int slot, double lambda, cudaStream_t st);
+// FP64 (G + lambda I)^-1 for an absolute lambda, made on first use (two cached lambdas).
+ctof_status tikhonov_inverse(ctof_kernel_s* k, double lambda, const double** hinv, cudaStream_t st);
 
 // ---- admm.cu ------------------------------------------------------------
 ctof_status admm_tv_stencil(const ctof_kernel_s* k, const float* x, const float* u2_old,

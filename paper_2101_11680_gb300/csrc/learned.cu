@@ -65,74 +65,146 @@ __device__ __forceinline__ long long neighbour(const Geo& G, int bb, int zz, int
   return (((long long)bb * G.z + zz) * G.y + yy) * G.x + xx;
 }
 
-// out[v][co] = bias[co] + sum_tap sum_ci W[tap][co][ci] act(in[v + off(tap)][ci]),
-// act = ReLU if relu_in; then out *= (mask[v][co] > 0) if mask.
-__global__ void __launch_bounds__(256) k_conv3d(const __nv_bfloat16* __restrict__ in, int relu_in,
-                                                const __nv_bfloat16* __restrict__ w,
-                                                const float* __restrict__ bias,
-                                                const __nv_bfloat16* __restrict__ mask, __nv_bfloat16* __restrict__ out,
-                                                Geo G) {
-  __shared__ unsigned s_w[27 * CH * CH / 2];
-  for (int i = threadIdx.x; i < 27 * CH * CH / 2; i += blockDim.x) s_w[i] = reinterpret_cast<const unsigned*>(w)[i];
+// One CTA computes an 8-row x TX-voxel patch of one (batch, depth) plane for
+// all 16 output channels: the 3 x 10 x (TX+2) input block (halo included,
+// zero outside the volume) and the 27 x 16 x 16 weights are staged in shared
+// memory with 16-byte cp.async copies; each warp owns one output row and
+// runs, per tap, one ldmatrix for the weights and one per 16-voxel job for
+// the inputs, then two m16n8k16 MMAs per job.  The two 16-byte halves of a
+// voxel's 32-byte channel vector swap places on bit 2 of the voxel index, so
+// the eight rows of every ldmatrix land in distinct bank groups.
+//   out[v][co] = bias[co] + sum_tap sum_ci W[tap][co][ci] act(in[v + off(tap)][ci])
+// act = ReLU if relu_in; out *= (mask[v][co] > 0) if mask.  IN_F32: the input
+// is one FP32 channel `in_f` scaled by in_scale (channel 0; the rest zero).
+// OUT_PROX: instead of `out`, x[v] = z[v] + mu0 * bf16(out[v][0]).
+constexpr int CV_TY = 8;
+constexpr int CV_THREADS = 256;
+
+__device__ __forceinline__ unsigned su32(const void* p) { return static_cast<unsigned>(__cvta_generic_to_shared(p)); }
+__device__ __forceinline__ void cp16_zfill(void* s, const void* g, bool valid) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(su32(s)), "l"(g), "r"(valid ? 16 : 0)
+               : "memory");
+}
+__device__ __forceinline__ void ldm_x4(unsigned (&r)[4], const void* p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(su32(p)));
+}
+// byte offset of 16-byte half h of staged row v
+__device__ __forceinline__ int tile_off(int v, int h) { return v * 32 + ((h ^ ((v >> 2) & 1)) << 4); }
+
+size_t conv_smem_bytes(int txc) { return (size_t)3 * (CV_TY + 2) * (16 * txc + 2) * 32 + 27 * CH * 32; }
+
+template <int TXC, bool IN_F32, bool OUT_PROX>
+__global__ void __launch_bounds__(CV_THREADS) k_conv3d(const __nv_bfloat16* __restrict__ in,
+                                                       const float* __restrict__ in_f, float in_scale, int relu_in,
+                                                       const __nv_bfloat16* __restrict__ w,
+                                                       const float* __restrict__ bias,
+                                                       const __nv_bfloat16* __restrict__ mask,
+                                                       __nv_bfloat16* __restrict__ out, const float* __restrict__ z,
+                                                       float* __restrict__ x_out, Geo G) {
+  constexpr int TX = 16 * TXC, SX = TX + 2, SY = CV_TY + 2;
+  extern __shared__ __align__(128) char sm[];
+  char* s_in = sm;                      // [3][SY][SX] staged voxels, 32 B each
+  char* s_w = sm + 3 * SY * SX * 32;    // [27 * 16] rows (tap, co) of 16 ci, 32 B each
+  const int bb = blockIdx.z / G.z, zz = blockIdx.z - bb * G.z;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * CV_TY;
+  for (int i = threadIdx.x; i < 27 * CH * 2; i += CV_THREADS)
+    cp16_zfill(s_w + tile_off(i >> 1, i & 1), w + (i >> 1) * CH + (i & 1) * 8, true);
+  const int nvox = 3 * SY * SX;
+  if (IN_F32) {
+    for (int v = threadIdx.x; v < nvox; v += CV_THREADS) {
+      const int tx = v % SX, r = v / SX, ty = r % SY, tz = r / SY;
+      const int gx = x0 + tx - 1, gy = y0 + ty - 1, gz = zz + tz - 1;
+      float val = 0.f;
+      if (gx >= 0 && gx < G.x && gy >= 0 && gy < G.y && gz >= 0 && gz < G.z)
+        val = in_f[(((long long)bb * G.z + gz) * G.y + gy) * G.x + gx] * in_scale;
+      *reinterpret_cast<uint4*>(s_in + tile_off(v, 0)) =
+          make_uint4(pack2(__float2bfloat16_rn(val), __float2bfloat16_rn(0.f)), 0u, 0u, 0u);
+      *reinterpret_cast<uint4*>(s_in + tile_off(v, 1)) = make_uint4(0u, 0u, 0u, 0u);
+    }
+  } else {
+    for (int i = threadIdx.x; i < nvox * 2; i += CV_THREADS) {
+      const int v = i >> 1, h = i & 1;
+      const int tx = v % SX, r = v / SX, ty = r % SY, tz = r / SY;
+      const int gx = x0 + tx - 1, gy = y0 + ty - 1, gz = zz + tz - 1;
+      const bool ok = gx >= 0 && gx < G.x && gy >= 0 && gy < G.y && gz >= 0 && gz < G.z;
+      const long long gv = ok ? (((long long)bb * G.z + gz) * G.y + gy) * G.x + gx : 0;
+      cp16_zfill(s_in + tile_off(v, h), in + gv * CH + h * 8, ok);
+    }
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tg = lane & 3;
-  const long long xchunks = G.x / 16;
-  const long long job = (long long)blockIdx.x * 8 + warp;
-  const long long rows = (long long)G.b * G.z * G.y;
-  if (job >= rows * xchunks) return;
-  const long long row = job / xchunks;
-  const int x0 = (int)(job - row * xchunks) * 16;
-  const int yy = (int)(row % G.y);
-  const int zz = (int)((row / G.y) % G.z);
-  const int bb = (int)(row / ((long long)G.y * G.z));
-  float acc[2][4] = {};
-  const unsigned* inw = reinterpret_cast<const unsigned*>(in);  // [voxel][8] bf16 pairs
+  const int mi = lane >> 3, lr = lane & 7;
+  const int a_vox = lr + ((mi & 1) << 3), a_half = mi >> 1;   // A: (voxels 0-7 | 8-15) x (ci 0-7 | 8-15)
+  const int b_row = lr + ((mi >> 1) << 3), b_half = mi & 1;   // B: (co 0-7 | 8-15) x (ci 0-7 | 8-15)
+  float acc[TXC][2][4];
+#pragma unroll
+  for (int j = 0; j < TXC; ++j)
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[j][n][e] = 0.f;
+#pragma unroll 3
   for (int tap = 0; tap < 27; ++tap) {
-    const int dz = tap / 9 - 1, dy = (tap / 3) % 3 - 1, dx = tap % 3 - 1;
-    const long long va = neighbour(G, bb, zz + dz, yy + dy, x0 + g + dx);
-    const long long vb = neighbour(G, bb, zz + dz, yy + dy, x0 + g + 8 + dx);
-    unsigned a[4];
-    a[0] = va >= 0 ? inw[va * 8 + tg] : 0u;
-    a[1] = vb >= 0 ? inw[vb * 8 + tg] : 0u;
-    a[2] = va >= 0 ? inw[va * 8 + tg + 4] : 0u;
-    a[3] = vb >= 0 ? inw[vb * 8 + tg + 4] : 0u;
-    if (relu_in) {
+    const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+    unsigned b[4];
+    ldm_x4(b, s_w + tile_off(tap * CH + b_row, b_half));
+    const int vrow = (dz * SY + warp + dy) * SX + dx;
 #pragma unroll
-      for (int i = 0; i < 4; ++i) a[i] = relu2(a[i]);
-    }
+    for (int j = 0; j < TXC; ++j) {
+      unsigned a[4];
+      ldm_x4(a, s_in + tile_off(vrow + j * 16 + a_vox, a_half));
+      if (relu_in) {
 #pragma unroll
-    for (int nt = 0; nt < 2; ++nt) {
-      const int co = nt * 8 + g;
-      const unsigned b0 = s_w[(tap * CH + co) * 8 + tg];
-      const unsigned b1 = s_w[(tap * CH + co) * 8 + tg + 4];
-      mma_bf16(acc[nt], a, b0, b1);
+        for (int e = 0; e < 4; ++e) a[e] = relu2(a[e]);
+      }
+      mma_bf16(acc[j][0], a, b[0], b[1]);
+      mma_bf16(acc[j][1], a, b[2], b[3]);
     }
   }
-  const long long v0 = neighbour(G, bb, zz, yy, x0 + g), v1 = v0 + 8;
-  unsigned* outw = reinterpret_cast<unsigned*>(out);
-  const unsigned* maskw = reinterpret_cast<const unsigned*>(mask);
+  const int yy = y0 + warp;
+  const long long row = (((long long)bb * G.z + zz) * G.y + yy) * G.x;
 #pragma unroll
-  for (int nt = 0; nt < 2; ++nt) {
-    const int co = nt * 8 + 2 * tg;
-    float r0 = acc[nt][0], r1 = acc[nt][1], r2 = acc[nt][2], r3 = acc[nt][3];
-    if (bias) {
-      r0 += bias[co];
-      r1 += bias[co + 1];
-      r2 += bias[co];
-      r3 += bias[co + 1];
+  for (int j = 0; j < TXC; ++j) {
+    const long long v0 = row + x0 + j * 16 + g, v1 = v0 + 8;
+    if (OUT_PROX) {
+      if (tg == 0) {
+        const float b0 = bias ? bias[0] : 0.f;
+        const float f0 = __bfloat162float(__float2bfloat16_rn(acc[j][0][0] + b0));
+        const float f1 = __bfloat162float(__float2bfloat16_rn(acc[j][0][2] + b0));
+        x_out[v0] = z[v0] + MU0 * f0;
+        x_out[v1] = z[v1] + MU0 * f1;
+      }
+      continue;
     }
-    if (mask) {
-      const unsigned m0 = maskw[v0 * 8 + (co >> 1)], m1 = maskw[v1 * 8 + (co >> 1)];
-      const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&m0));
-      const float2 f1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&m1));
-      r0 = f0.x > 0.f ? r0 : 0.f;
-      r1 = f0.y > 0.f ? r1 : 0.f;
-      r2 = f1.x > 0.f ? r2 : 0.f;
-      r3 = f1.y > 0.f ? r3 : 0.f;
+    unsigned* outw = reinterpret_cast<unsigned*>(out);
+    const unsigned* maskw = reinterpret_cast<const unsigned*>(mask);
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int co = nt * 8 + 2 * tg;
+      float r0 = acc[j][nt][0], r1 = acc[j][nt][1], r2 = acc[j][nt][2], r3 = acc[j][nt][3];
+      if (bias) {
+        r0 += bias[co];
+        r1 += bias[co + 1];
+        r2 += bias[co];
+        r3 += bias[co + 1];
+      }
+      if (mask) {
+        const unsigned m0 = maskw[v0 * 8 + (co >> 1)], m1 = maskw[v1 * 8 + (co >> 1)];
+        const float2 f0 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&m0));
+        const float2 f1 = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&m1));
+        r0 = f0.x > 0.f ? r0 : 0.f;
+        r1 = f0.y > 0.f ? r1 : 0.f;
+        r2 = f1.x > 0.f ? r2 : 0.f;
+        r3 = f1.y > 0.f ? r3 : 0.f;
+      }
+      outw[v0 * 8 + (co >> 1)] = pack2(__float2bfloat16_rn(r0), __float2bfloat16_rn(r1));
+      outw[v1 * 8 + (co >> 1)] = pack2(__float2bfloat16_rn(r2), __float2bfloat16_rn(r3));
     }
-    outw[v0 * 8 + (co >> 1)] = pack2(__float2bfloat16_rn(r0), __float2bfloat16_rn(r1));
-    outw[v1 * 8 + (co >> 1)] = pack2(__float2bfloat16_rn(r2), __float2bfloat16_rn(r3));
   }
 }
 
@@ -236,13 +308,6 @@ __global__ void k_pack1(const float* __restrict__ src, float scale, long long nv
   }
 }
 
-// x[v] = z[v] + mu0 * f[v][0]
-__global__ void k_prox_out(const float* __restrict__ z, const __nv_bfloat16* __restrict__ f, long long nvox,
-                           float* __restrict__ x) {
-  for (long long v = blockIdx.x * (long long)blockDim.x + threadIdx.x; v < nvox; v += (long long)gridDim.x * blockDim.x)
-    x[v] = z[v] + MU0 * __bfloat162float(f[v * CH]);
-}
-
 // z = x - eta[s] * inv_s2 * g_raw, and g = inv_s2 * g_raw stored for the step-size gradient
 __global__ void k_zstep(const float* __restrict__ x, float* __restrict__ g, const float* __restrict__ eta, int s,
                         float inv_s2, long long n, float* __restrict__ z) {
@@ -297,7 +362,6 @@ struct LayerOff {
   int w, b, ci, co;
 };
 
-ctof_solver_params tikhonov_params(double lambda_rel);
 
 // Master FP32 parameters -> padded BF16 forward weights [tap][co][ci], data-gradient
 // weights [tap][ci][co] with flipped taps, and padded FP32 biases.
@@ -381,9 +445,10 @@ struct Ws {
   float *x, *tmpT, *gx, *gz, *h;
   float *z, *g;                 // [S][V]
   __nv_bfloat16 *u, *y1, *y2, *y3;  // [S][V][16]
-  __nv_bfloat16 *f, *da, *db_;  // [V][16]
+  __nv_bfloat16 *da, *db_;  // [V][16]
   float* part;
   int nblk;
+  float2 *spec_t, *spec_z;  // [batch][nf][ldt], [batch][nf][ldz]
 };
 
 ctof_status learned_workspace(ctof_learned_s* L, const ctof_kernel_s* k, int batch, bool train, Ws* w) {
@@ -402,8 +467,9 @@ ctof_status learned_workspace(ctof_learned_s* L, const ctof_kernel_s* k, int bat
   const size_t o_z = add((size_t)S * V * 4), o_g = add((size_t)S * V * 4);
   const size_t o_u = add((size_t)S * V * CH * 2), o_y1 = add((size_t)S * V * CH * 2), o_y2 = add((size_t)S * V * CH * 2),
                o_y3 = add((size_t)S * V * CH * 2);
-  const size_t o_f = add(V * CH * 2), o_da = add(V * CH * 2), o_db = add(V * CH * 2);
+  const size_t o_da = add(V * CH * 2), o_db = add(V * CH * 2);
   const size_t o_p = add((size_t)nblk * 27 * CH * CH * 4);
+  const size_t o_st = add((size_t)batch * k->nf * k->ldt * 8), o_sz = add((size_t)batch * k->nf * k->ldz * 8);
   if (need > L->ws_bytes) {
     if (L->d_ws) cudaFree(L->d_ws);
     L->d_ws = nullptr;
@@ -426,20 +492,42 @@ ctof_status learned_workspace(ctof_learned_s* L, const ctof_kernel_s* k, int bat
   w->y1 = reinterpret_cast<__nv_bfloat16*>(b + o_y1);
   w->y2 = reinterpret_cast<__nv_bfloat16*>(b + o_y2);
   w->y3 = reinterpret_cast<__nv_bfloat16*>(b + o_y3);
-  w->f = reinterpret_cast<__nv_bfloat16*>(b + o_f);
   w->da = reinterpret_cast<__nv_bfloat16*>(b + o_da);
   w->db_ = reinterpret_cast<__nv_bfloat16*>(b + o_db);
   w->part = reinterpret_cast<float*>(b + o_p);
+  w->spec_t = reinterpret_cast<float2*>(b + o_st);
+  w->spec_z = reinterpret_cast<float2*>(b + o_sz);
   w->nblk = nblk;
+  return CTOF_OK;
+}
+
+template <bool IN_F32, bool OUT_PROX>
+ctof_status conv_launch(const __nv_bfloat16* in, const float* in_f, float in_scale, int relu_in,
+                        const __nv_bfloat16* wt, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out,
+                        const float* z, float* x_out, Geo G, cudaStream_t st) {
+  const int txc = G.x % 64 == 0 ? 4 : (G.x % 32 == 0 ? 2 : 1);
+  const dim3 grid(G.x / (16 * txc), G.y / CV_TY, G.b * G.z);
+  const size_t smem = conv_smem_bytes(txc);
+  switch (txc) {
+#define CTOF_CONV_CASE(T)                                                                                       \
+  case T:                                                                                                       \
+    CTOF_CUDA_TRY(cudaFuncSetAttribute(k_conv3d<T, IN_F32, OUT_PROX>,                                          \
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));               \
+    k_conv3d<T, IN_F32, OUT_PROX><<<grid, CV_THREADS, smem, st>>>(in, in_f, in_scale, relu_in, wt, bias, mask, \
+                                                                  out, z, x_out, G);                           \
+    break;
+    CTOF_CONV_CASE(4)
+    CTOF_CONV_CASE(2)
+    CTOF_CONV_CASE(1)
+#undef CTOF_CONV_CASE
+  }
+  CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
 
 ctof_status conv(const __nv_bfloat16* in, int relu_in, const __nv_bfloat16* wt, const float* bias,
                  const __nv_bfloat16* mask, __nv_bfloat16* out, Geo G, cudaStream_t st) {
-  const long long jobs = (long long)G.b * G.z * G.y * (G.x / 16);
-  k_conv3d<<<(unsigned)((jobs + 7) / 8), 256, 0, st>>>(in, relu_in, wt, bias, mask, out, G);
-  CTOF_CUDA_TRY(cudaGetLastError());
-  return CTOF_OK;
+  return conv_launch<false, false>(in, nullptr, 0.f, relu_in, wt, bias, mask, out, nullptr, nullptr, G, st);
 }
 
 ctof_status wgrad(const __nv_bfloat16* dy, const __nv_bfloat16* x, int relu_in, Geo G, float* part, int nblk, float* acc,
@@ -451,17 +539,47 @@ ctof_status wgrad(const __nv_bfloat16* dy, const __nv_bfloat16* x, int relu_in, 
   return CTOF_OK;
 }
 
-// g_raw = A^T (A x - m) for every batch member (unnormalised operator)
-ctof_status normal_residual(ctof_kernel_s* k, int batch, const float* x, const float* m, float* tmpT, float* out,
+// Operator applications for the whole batch: per-volume lateral FFTs, one
+// contraction launch per direction that reads W_hat once for all volumes.
+ctof_status op_forward(ctof_kernel_s* k, int batch, const float* x, float* meas, const Ws& w, cudaStream_t st) {
+  const size_t vol = (size_t)k->nz * k->n * k->n, mt = (size_t)k->nt * k->n * k->n;
+  const size_t sz = (size_t)k->nf * k->ldz, stt = (size_t)k->nf * k->ldt;
+  for (int b = 0; b < batch; ++b)
+    CTOF_TRY(fft_forward_planes(k, x + b * vol, k->nz, k->n, k->n, k->n, k->d_inter_z, w.spec_z + b * sz, k->ldz, st));
+  CTOF_TRY(contract_forward_batch(k, batch, w.spec_z, w.spec_t, st));
+  for (int b = 0; b < batch; ++b)
+    CTOF_TRY(fft_inverse_planes(k, w.spec_t + b * stt, k->ldt, k->nt, k->n, k->n, k->d_inter_t, meas + b * mt, k->n,
+                                st));
+  return CTOF_OK;
+}
+
+// out = A^T r (tik_hinv null) or the Tikhonov solve T r = (G + lambda I)^-1 W^T r (per frequency)
+ctof_status op_adjoint(ctof_kernel_s* k, int batch, const float* r, float* out, const double* tik_hinv, const Ws& w,
+                       cudaStream_t st) {
+  const size_t vol = (size_t)k->nz * k->n * k->n, mt = (size_t)k->nt * k->n * k->n;
+  const size_t sz = (size_t)k->nf * k->ldz, stt = (size_t)k->nf * k->ldt;
+  for (int b = 0; b < batch; ++b)
+    CTOF_TRY(fft_forward_planes(k, r + b * mt, k->nt, k->n, k->n, k->n, k->d_inter_t, w.spec_t + b * stt, k->ldt, st));
+  if (tik_hinv)
+    CTOF_TRY(contract_tikhonov_batch(k, batch, tik_hinv, w.spec_t, w.spec_z, st));
+  else
+    CTOF_TRY(contract_adjoint_batch(k, batch, w.spec_t, w.spec_z, st));
+  for (int b = 0; b < batch; ++b)
+    CTOF_TRY(fft_inverse_planes(k, w.spec_z + b * sz, k->ldz, k->nz, k->n, k->n, k->d_inter_z, out + b * vol, k->n,
+                                st));
+  return CTOF_OK;
+}
+
+// g_raw = A^T (A x - m) for every batch member (unnormalised operator; m may be null)
+ctof_status normal_residual(ctof_kernel_s* k, int batch, const float* x, const float* m, float* out, const Ws& w,
                             cudaStream_t st) {
-  const size_t vol = (size_t)k->nz * k->n * k->n, meas = (size_t)k->nt * k->n * k->n;
-  for (int b = 0; b < batch; ++b) CTOF_TRY(ctof_forward(k, x + b * vol, tmpT + b * meas, st));
+  CTOF_TRY(op_forward(k, batch, x, w.tmpT, w, st));
   if (m) {
-    k_sub<<<grid_for((long long)batch * meas), 256, 0, st>>>(tmpT, m, (long long)batch * meas);
+    const long long mt = (long long)batch * k->nt * k->n * k->n;
+    k_sub<<<grid_for(mt), 256, 0, st>>>(w.tmpT, m, mt);
     CTOF_CUDA_TRY(cudaGetLastError());
   }
-  for (int b = 0; b < batch; ++b) CTOF_TRY(ctof_adjoint(k, tmpT + b * meas, out + b * vol, st));
-  return CTOF_OK;
+  return op_adjoint(k, batch, w.tmpT, out, nullptr, w, st);
 }
 
 // Forward pass of the unrolled solver; with `train` every stage's activations are kept.
@@ -472,10 +590,10 @@ ctof_status unrolled_forward(ctof_learned_s* L, ctof_kernel_s* k, int batch, con
   const float inv_s2 = (float)(1.0 / (k->scale * k->scale));
   const int nstore = train ? L->stages : 1;
   const float* eta = L->d_theta + L->nparam - L->stages;
-  const size_t vol = (size_t)k->nz * k->n * k->n, meas = (size_t)k->nt * k->n * k->n;
   if (L->opt.x0_lambda_rel > 0.0) {
-    const ctof_solver_params tik = tikhonov_params(L->opt.x0_lambda_rel);
-    for (int b = 0; b < batch; ++b) CTOF_TRY(ctof_reconstruct(k, m + b * meas, &tik, w.x + b * vol, nullptr, st));
+    const double* hinv = nullptr;
+    CTOF_TRY(tikhonov_inverse(k, L->opt.x0_lambda_rel * k->gram_max, &hinv, st));
+    CTOF_TRY(op_adjoint(k, batch, m, w.x, hinv, w, st));
   } else {
     CTOF_CUDA_TRY(cudaMemsetAsync(w.x, 0, V * sizeof(float), st));
   }
@@ -488,27 +606,33 @@ ctof_status unrolled_forward(ctof_learned_s* L, ctof_kernel_s* k, int batch, con
     __nv_bfloat16* y1 = w.y1 + (size_t)j * V * CH;
     __nv_bfloat16* y2 = w.y2 + (size_t)j * V * CH;
     __nv_bfloat16* y3 = w.y3 + (size_t)j * V * CH;
-    CTOF_TRY(normal_residual(k, batch, w.x, m, w.tmpT, g, st));
+    CTOF_TRY(normal_residual(k, batch, w.x, m, g, w, st));
     k_zstep<<<grid_for(V), 256, 0, st>>>(w.x, g, eta, s, inv_s2, V, z);
     CTOF_CUDA_TRY(cudaGetLastError());
-    k_pack1<<<grid_for(V), 256, 0, st>>>(z, 1.0f / MU0, V, u);
-    CTOF_CUDA_TRY(cudaGetLastError());
-    CTOF_TRY(conv(u, 0, L->d_wf + 0 * 27 * CH * CH, L->d_bias + 0 * CH, nullptr, y1, G, st));
+    if (train) {  // the backward pass needs the network input u
+      k_pack1<<<grid_for(V), 256, 0, st>>>(z, 1.0f / MU0, V, u);
+      CTOF_CUDA_TRY(cudaGetLastError());
+      CTOF_TRY(conv(u, 0, L->d_wf + 0 * 27 * CH * CH, L->d_bias + 0 * CH, nullptr, y1, G, st));
+    } else {
+      CTOF_TRY((conv_launch<true, false>(nullptr, z, 1.0f / MU0, 0, L->d_wf, L->d_bias, nullptr, y1, nullptr,
+                                         nullptr, G, st)));
+    }
     CTOF_TRY(conv(y1, 1, L->d_wf + 1 * 27 * CH * CH, L->d_bias + 1 * CH, nullptr, y2, G, st));
     CTOF_TRY(conv(y2, 1, L->d_wf + 2 * 27 * CH * CH, L->d_bias + 2 * CH, nullptr, y3, G, st));
-    CTOF_TRY(conv(y3, 1, L->d_wf + 3 * 27 * CH * CH, L->d_bias + 3 * CH, nullptr, w.f, G, st));
-    k_prox_out<<<grid_for(V), 256, 0, st>>>(z, w.f, V, w.x);
-    CTOF_CUDA_TRY(cudaGetLastError());
+    // last layer with the residual step fused: x = z + mu0 f(u)
+    CTOF_TRY((conv_launch<false, true>(y3, nullptr, 0.f, 1, L->d_wf + 3 * 27 * CH * CH, L->d_bias + 3 * CH,
+                                       nullptr, nullptr, z, w.x, G, st)));
   }
   if (!train && L->opt.dc_steps > 0) {
     // x <- x - T(A x - m): the residual goes through the Tikhonov solve into w.h
-    const ctof_solver_params tik = tikhonov_params(L->opt.dc_lambda_rel);
+    const double* hinv = nullptr;
+    CTOF_TRY(tikhonov_inverse(k, L->opt.dc_lambda_rel * k->gram_max, &hinv, st));
+    const long long mt = (long long)batch * k->nt * k->n * k->n;
     for (int d = 0; d < L->opt.dc_steps; ++d) {
-      for (int b = 0; b < batch; ++b) CTOF_TRY(ctof_forward(k, w.x + b * vol, w.tmpT + b * meas, st));
-      k_sub<<<grid_for((long long)batch * meas), 256, 0, st>>>(w.tmpT, m, (long long)batch * meas);
+      CTOF_TRY(op_forward(k, batch, w.x, w.tmpT, w, st));
+      k_sub<<<grid_for(mt), 256, 0, st>>>(w.tmpT, m, mt);
       CTOF_CUDA_TRY(cudaGetLastError());
-      for (int b = 0; b < batch; ++b)
-        CTOF_TRY(ctof_reconstruct(k, w.tmpT + b * meas, &tik, w.h + b * vol, nullptr, st));
+      CTOF_TRY(op_adjoint(k, batch, w.tmpT, w.h, hinv, w, st));
       k_sub<<<grid_for(V), 256, 0, st>>>(w.x, w.h, V);
       CTOF_CUDA_TRY(cudaGetLastError());
     }
@@ -557,7 +681,7 @@ ctof_status unrolled_backward(ctof_learned_s* L, ctof_kernel_s* k, int batch, co
     // cur holds dL/du (channel 0); z = x - eta g,  g = A_n^T (A_n x - m_n)
     k_gz<<<grid_for(V) < 304 ? grid_for(V) : 304, 256, 0, st>>>(w.gx, cur, g, V, w.gz, deta, s);
     CTOF_CUDA_TRY(cudaGetLastError());
-    CTOF_TRY(normal_residual(k, batch, w.gz, nullptr, w.tmpT, w.h, st));
+    CTOF_TRY(normal_residual(k, batch, w.gz, nullptr, w.h, w, st));
     k_gx<<<grid_for(V), 256, 0, st>>>(w.gz, w.h, eta, s, inv_s2, V, w.gx);
     CTOF_CUDA_TRY(cudaGetLastError());
   }
@@ -568,17 +692,6 @@ ctof_status unrolled_backward(ctof_learned_s* L, ctof_kernel_s* k, int batch, co
     CTOF_CUDA_TRY(cudaGetLastError());
   }
   return CTOF_OK;
-}
-
-ctof_solver_params tikhonov_params(double lambda_rel) {
-  ctof_solver_params tik{};
-  tik.solver = CTOF_SOLVER_TIKHONOV;
-  tik.iters = 1;
-  tik.rho = 1.0;
-  tik.tv_beta = -1.0;
-  tik.beta_rel = 1e-3;
-  tik.tik_lambda_rel = lambda_rel;
-  return tik;
 }
 
 ctof_status check_geometry(const ctof_kernel_s* k) {
@@ -668,6 +781,9 @@ ctof_status ctof_learned_loss_grad(ctof_learned L, ctof_kernel k, int batch, con
                                    double* h_loss, float* h_grad, void* stream) {
   if (!L || !k || !d_m || !d_mu || batch < 1) return CTOF_EINVAL;
   CTOF_TRY(check_geometry(k));
+  if (L->device != k->device) return CTOF_EINVAL;
+  DeviceGuard dg(k->device);
+  if (!dg.ok) return CTOF_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Ws w;
   CTOF_TRY(learned_workspace(L, k, batch, true, &w));
@@ -686,6 +802,9 @@ ctof_status ctof_learned_train_step(ctof_learned L, ctof_kernel k, int batch, co
                                     double lr, double* h_loss, void* stream) {
   if (!L || !k || !d_m || !d_mu || batch < 1 || !(lr > 0)) return CTOF_EINVAL;
   CTOF_TRY(check_geometry(k));
+  if (L->device != k->device) return CTOF_EINVAL;
+  DeviceGuard dg(k->device);
+  if (!dg.ok) return CTOF_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Ws w;
   CTOF_TRY(learned_workspace(L, k, batch, true, &w));
@@ -711,6 +830,9 @@ ctof_status ctof_learned_reconstruct(ctof_learned L, ctof_kernel k, int batch, c
                                      void* stream) {
   if (!L || !k || !d_m || !d_mu || batch < 1) return CTOF_EINVAL;
   CTOF_TRY(check_geometry(k));
+  if (L->device != k->device) return CTOF_EINVAL;
+  DeviceGuard dg(k->device);
+  if (!dg.ok) return CTOF_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   Ws w;
   CTOF_TRY(learned_workspace(L, k, batch, false, &w));

@@ -41,8 +41,8 @@ PEAK = 1e5
 # Start of the unrolled stages: the per-frequency Tikhonov solution at this relative lambda.
 X0_LAMBDA = 1e-3
 # Inference-time data-consistency steps after the last stage and their relative Tikhonov lambda.
-DC_STEPS = 2
-DC_LAMBDA = 1e-3
+DC_STEPS = 3
+DC_LAMBDA = 1e-5
 
 
 def _render(args):
