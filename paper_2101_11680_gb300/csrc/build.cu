@@ -287,9 +287,10 @@ __device__ void block_cholesky(double* s_a, int nz) {
   }
 }
 
-// mode 0: ADMM  H = G/s^2 + (lap+1) I + Dz^T Dz  -> FP32 inverse into out32 [nz][z4]
-// mode 1: Tikhonov  G + lambda I -> FP64 inverse into out64 [nz][nz]
-// Both invert through the FP64 Cholesky factor: H^-1 = L^-T L^-1 (exactly symmetric).
+// mode 0: ADMM  H = G/s^2 + (lap+1) I + Dz^T Dz
+// mode 1: Tikhonov  H = G + lambda I
+// H^-1 = L^-T L^-1 through the FP64 Cholesky factor (exactly symmetric), stored
+// FP32 into out32 [nz][z4].
 __global__ void __launch_bounds__(128) k_factor(const double* __restrict__ gram, const float* __restrict__ lap,
                                                 int nz, double inv_s2, double lambda, int mode,
                                                 float* __restrict__ out32, double* __restrict__ out64) {
@@ -323,15 +324,6 @@ __global__ void __launch_bounds__(128) k_factor(const double* __restrict__ gram,
     }
   }
   __syncthreads();
-  if (mode == 1) {
-    for (int idx = threadIdx.x; idx < nz * nz; idx += blockDim.x) {
-      const int i = idx / nz, j = idx - i * nz;
-      double acc = 0.0;
-      for (int kk = (i > j ? i : j); kk < nz; ++kk) acc += s_l[kk * ld + i] * s_l[kk * ld + j];
-      out64[(size_t)c * nz * nz + idx] = acc;
-    }
-    return;
-  }
   const int z4 = (nz + 3) & ~3;
   for (int idx = threadIdx.x; idx < nz * z4; idx += blockDim.x) {
     const int i = idx / z4, j = idx - i * z4;
@@ -516,7 +508,7 @@ ctof_status build_tikhonov_factors(ctof_kernel_s* k, int slot, double lambda, cu
   const int nz = k->nz;
   const size_t fsm = (size_t)2 * nz * (nz + 1) * sizeof(double);
   CTOF_CUDA_TRY(cudaFuncSetAttribute(k_factor, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
-  k_factor<<<k->nclass, 128, fsm, st>>>(k->d_gram, k->d_lap, nz, 0.0, lambda, 1, nullptr, k->d_tik_hinv[slot]);
+  k_factor<<<k->nclass, 128, fsm, st>>>(k->d_gram, k->d_lap, nz, 0.0, lambda, 1, k->d_tik_hinv[slot], nullptr);
   CTOF_CUDA_TRY(cudaGetLastError());
   k->tik_lambda[slot] = lambda;
   return CTOF_OK;

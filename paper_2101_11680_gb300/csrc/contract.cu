@@ -2,7 +2,7 @@
 // lateral Fourier domain): for every half-plane frequency f,
 //   forward   M_hat(f, t) = sum_z W_hat(f, t, z) mu_hat(f, z)       (T x Z . Z)
 //   adjoint   V_hat(f, z) = sum_t W_hat(f, t, z) r_hat(f, t)        (Z x T . T)
-//   Tikhonov  x_hat(f)    = (G(f) + lambda I)^-1 V_hat(f)           (Z x Z, FP64)
+//   Tikhonov  x_hat(f)    = (G(f) + lambda I)^-1 V_hat(f)           (Z x Z)
 // W_hat is real (the kernel is even in x and y) and, for dx == dy, equal on
 // the up-to-four frequencies (a,b), (a,-b), (b,a), (b,-a) of one class, so
 // each class's T x Z block is read from HBM once and applied to the complex
@@ -16,9 +16,10 @@
 // shared memory while the volumes' member vectors stream through their own
 // double buffer, so W_hat is read once for all of them.  W_hat rows land with a stride
 // of 4*(z4/4 | 1) floats, so eight consecutive rows read with float4 loads hit
-// eight distinct 16-byte bank groups.  The arithmetic is FP32 FMA (FP64 for
-// the Z x Z solve): these contractions move 1 FLOP per 2 bytes of W_hat and
-// are bound by HBM, not by the FMA pipes.
+// eight distinct 16-byte bank groups.  The arithmetic is FP32 FMA: these
+// contractions move 1 FLOP per 2 bytes of W_hat.  The Tikhonov inverse is
+// formed in FP64 and applied in FP32: its rounding error, eps |H^-1| |b|, is
+// of the same size as the one b already carries from its FP32 sums.
 // (The fused ADMM x-update lives in contract_admm.cu.)
 #include <cuda_runtime.h>
 
@@ -69,14 +70,14 @@ __host__ __device__ inline Plan make_plan(int mode, int nt, int nz, int nbuf, in
   const int pairs = 2 * p.q;
   p.J = threads / pairs > 0 ? threads / pairs : 1;
   p.off_h = al16((size_t)nt * p.sw * 4);
-  p.wst = p.off_h + (mode == MODE_TIK ? al16((size_t)nz * nz * 8) : 0);
+  p.wst = p.off_h + (mode == MODE_TIK ? al16((size_t)nz * p.z4 * 4) : 0);
   p.vst = al16(mode == MODE_FWD ? (size_t)p.z4 * 8 * 4 : (size_t)nt * 8 * 4);
   p.off_v = p.wst * nbuf;
   size_t s = p.off_v + p.vst * nbuf;
   p.off_part = s;
   if (mode != MODE_FWD) s += al16((size_t)p.J * p.z4 * 8 * 4);
   p.off_b = s;
-  if (mode == MODE_TIK) s += al16((size_t)p.z4 * 8 * 8);
+  if (mode == MODE_TIK) s += al16((size_t)p.z4 * 8 * 4);
   p.total = s;
   return p;
 }
@@ -84,7 +85,7 @@ __host__ __device__ inline Plan make_plan(int mode, int nt, int nz, int nbuf, in
 // Copies of class c's W_hat block (and Tikhonov inverse) into a W stage.
 template <int MODE>
 __device__ __forceinline__ void issue_w(const Plan& P, char* stg, int* s_mem, const float* __restrict__ what,
-                                        const int* __restrict__ members, const double* __restrict__ hinv, int c) {
+                                        const int* __restrict__ members, const float* __restrict__ hinv, int c) {
   float* sW = reinterpret_cast<float*>(stg);
   const float* src = what + (size_t)c * P.nt * P.z4;
   const int chunks = P.nt * P.q;
@@ -94,9 +95,9 @@ __device__ __forceinline__ void issue_w(const Plan& P, char* stg, int* s_mem, co
   }
   if (threadIdx.x < 4) s_mem[threadIdx.x] = members[c * 4 + threadIdx.x];
   if (MODE == MODE_TIK) {
-    double* sH = reinterpret_cast<double*>(stg + P.off_h);
-    const double* hs = hinv + (size_t)c * P.nz * P.nz;
-    for (int i = threadIdx.x; i < P.nz * P.nz; i += blockDim.x) cp_async8(sH + i, hs + i);
+    float* sH = reinterpret_cast<float*>(stg + P.off_h);
+    const float* hs = hinv + (size_t)c * P.nz * P.z4;
+    for (int i = threadIdx.x; i < P.nz * P.q; i += blockDim.x) cp_async16(sH + 4 * i, hs + 4 * i);
   }
 }
 
@@ -184,12 +185,12 @@ __global__ void __launch_bounds__(CT_THREADS) k_contract(const float* __restrict
                                                          const int* __restrict__ members, int nclass, int nt, int nz,
                                                          const float2* __restrict__ vin, int ld_in, size_t in_vstride,
                                                          float2* __restrict__ vout, int ld_out, size_t out_vstride,
-                                                         int nvol, const double* __restrict__ hinv, int nbuf) {
+                                                         int nvol, const float* __restrict__ hinv, int nbuf) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int s_mem[2][4];
   const Plan P = make_plan(MODE, nt, nz, nbuf, blockDim.x);
   float* part = reinterpret_cast<float*>(smem + P.off_part);
-  double* sB = reinterpret_cast<double*>(smem + P.off_b);
+  float* sB = reinterpret_cast<float*>(smem + P.off_b);
   const int G = gridDim.x;
   if (blockIdx.x < nclass) {
     issue_w<MODE>(P, smem, s_mem[0], what, members, hinv, blockIdx.x);
@@ -241,23 +242,23 @@ __global__ void __launch_bounds__(CT_THREADS) k_contract(const float* __restrict
         } else {
           for (int o = threadIdx.x; o < nz * 8; o += blockDim.x) {
             const int z = o >> 3, r = o & 7;
-            double s = 0.0;
-            for (int j = 0; j < P.J; ++j) s += (double)part[((size_t)j * P.z4 + z) * 8 + r];
+            float s = 0.f;
+            for (int j = 0; j < P.J; ++j) s += part[((size_t)j * P.z4 + z) * 8 + r];
             sB[z * 8 + r] = s;
           }
           __syncthreads();
           // x[i] = sum_j Hinv[j][i] b[j]  (Hinv symmetric; consecutive threads read consecutive i)
-          const double* sH = reinterpret_cast<const double*>(wst + P.off_h);
+          const float* sH = reinterpret_cast<const float*>(wst + P.off_h);
           for (int o = threadIdx.x; o < 4 * nz; o += blockDim.x) {
             const int m = o / nz, i = o - m * nz;
             if (mem[m] < 0) continue;
-            double re = 0.0, im = 0.0;
+            float re = 0.f, im = 0.f;
             for (int j = 0; j < nz; ++j) {
-              const double h = sH[j * nz + i];
-              re = fma(h, sB[j * 8 + 2 * m], re);
-              im = fma(h, sB[j * 8 + 2 * m + 1], im);
+              const float h = sH[j * P.z4 + i];
+              re = fmaf(h, sB[j * 8 + 2 * m], re);
+              im = fmaf(h, sB[j * 8 + 2 * m + 1], im);
             }
-            out[(size_t)mem[m] * ld_out + i] = make_float2((float)re, (float)im);
+            out[(size_t)mem[m] * ld_out + i] = make_float2(re, im);
           }
         }
       }
@@ -276,7 +277,7 @@ constexpr size_t SMEM_LIMIT = 227 * 1024;
 
 template <int MODE>
 ctof_status launch(const ctof_kernel_s* k, int nvol, const float2* vin, int ld_in, size_t in_vstride, float2* vout,
-                   int ld_out, size_t out_vstride, const double* hinv, cudaStream_t st) {
+                   int ld_out, size_t out_vstride, const float* hinv, cudaStream_t st) {
   if (nvol < 1) return CTOF_EINVAL;
   int nbuf = 2;
   Plan p = make_plan(MODE, k->nt, k->nz, 2, CT_THREADS);
@@ -316,7 +317,7 @@ ctof_status contract_adjoint(const ctof_kernel_s* k, const float2* in_t, float2*
   return contract_adjoint_batch(k, 1, in_t, out_z, st);
 }
 
-ctof_status contract_tikhonov(const ctof_kernel_s* k, const double* hinv, const float2* m_hat, float2* x_hat,
+ctof_status contract_tikhonov(const ctof_kernel_s* k, const float* hinv, const float2* m_hat, float2* x_hat,
                               cudaStream_t st) {
   return contract_tikhonov_batch(k, 1, hinv, m_hat, x_hat, st);
 }
@@ -333,7 +334,7 @@ ctof_status contract_adjoint_batch(const ctof_kernel_s* k, int nvol, const float
                           nullptr, st);
 }
 
-ctof_status contract_tikhonov_batch(const ctof_kernel_s* k, int nvol, const double* hinv, const float2* m_hat,
+ctof_status contract_tikhonov_batch(const ctof_kernel_s* k, int nvol, const float* hinv, const float2* m_hat,
                                     float2* x_hat, cudaStream_t st) {
   return launch<MODE_TIK>(k, nvol, m_hat, k->ldt, (size_t)k->nf * k->ldt, x_hat, k->ldz, (size_t)k->nf * k->ldz, hinv,
                           st);

@@ -310,18 +310,18 @@ ctof_status admm_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream
 
 }  // namespace
 
-ctof_status tikhonov_inverse(ctof_kernel_s* k, double lambda, const double** hinv, cudaStream_t st) {
+ctof_status tikhonov_inverse(ctof_kernel_s* k, double lambda, const float** hinv, cudaStream_t st) {
   if (!(lambda > 0.0) || !isfinite(lambda)) return CTOF_EINVAL;
   int slot = k->tik_lambda[0] == lambda ? 0 : (k->tik_lambda[1] == lambda ? 1 : -1);
   if (slot < 0) {
     slot = 1 - k->tik_last;  // replace the slot not used last
     if (!k->d_tik_hinv[slot]) {
       void* p = nullptr;
-      if (cudaMalloc(&p, (size_t)k->nclass * k->nz * k->nz * sizeof(double)) != cudaSuccess) {
+      if (cudaMalloc(&p, (size_t)k->nclass * k->nz * k->z4 * sizeof(float)) != cudaSuccess) {
         cudaGetLastError();
         return CTOF_ENOMEM;
       }
-      k->d_tik_hinv[slot] = static_cast<double*>(p);
+      k->d_tik_hinv[slot] = static_cast<float*>(p);
     }
     k->tik_lambda[slot] = -1.0;
     CTOF_TRY(build_tikhonov_factors(k, slot, lambda, st));
@@ -335,7 +335,7 @@ namespace {
 
 ctof_status tikhonov_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st, double* lambda_out) {
   const double lambda = prm->tik_lambda_rel * k->gram_max;
-  const double* hinv = nullptr;
+  const float* hinv = nullptr;
   CTOF_TRY(tikhonov_inverse(k, lambda, &hinv, st));
   *lambda_out = lambda;
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_scalars, 0, 16 * sizeof(double), st));
@@ -657,7 +657,7 @@ ctof_status ctof_kernel_get_info(ctof_kernel k, ctof_kernel_info* info) {
   info->nz = k->nz;
   info->scale = k->scale;
   info->gram_max_diag = k->gram_max;
-  const size_t tik_bytes = (size_t)k->nclass * k->nz * k->nz * sizeof(double);
+  const size_t tik_bytes = (size_t)k->nclass * k->nz * k->z4 * sizeof(float);
   info->device_bytes = k->bytes + (k->d_w ? (size_t)k->nt * k->nz * k->q * k->q * sizeof(double) : 0) +
                        ((k->d_tik_hinv[0] ? 1 : 0) + (k->d_tik_hinv[1] ? 1 : 0)) * tik_bytes;
   return CTOF_OK;

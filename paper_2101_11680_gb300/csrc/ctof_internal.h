@@ -60,10 +60,10 @@ struct ctof_kernel_s {
   double* d_scalars;   // [16] device scalars (beta, max reductions, flags)
 
   // Tikhonov cache: FP64 Cholesky factors of G + lambda I
-  // Tikhonov inverses (G + lambda I)^-1, FP64 [nclass][nz][nz], for the two
-  // most recently used lambdas (separate allocations, made on first use)
+  // Tikhonov inverses (G + lambda I)^-1 (FP64 Cholesky, stored FP32 [nclass][nz][z4])
+  // for the two most recently used lambdas (separate allocations, made on first use)
   double tik_lambda[2];
-  double* d_tik_hinv[2];
+  float* d_tik_hinv[2];
   int tik_last;  // slot used last
 
   // ADMM graph cache
@@ -149,12 +149,12 @@ ctof_status contract_forward_batch(const ctof_kernel_s* k, int nvol, const float
                                    cudaStream_t st);
 ctof_status contract_adjoint_batch(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z,
                                    cudaStream_t st);
-ctof_status contract_tikhonov_batch(const ctof_kernel_s* k, int nvol, const double* hinv, const float2* m_hat,
+ctof_status contract_tikhonov_batch(const ctof_kernel_s* k, int nvol, const float* hinv, const float2* m_hat,
                                     float2* x_hat, cudaStream_t st);
 ctof_status contract_adjoint(const ctof_kernel_s* k, const float2* in_t, float2* out_z, cudaStream_t st);
 ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const float2* s_hat,
                           float2* x_hat, float2* kx_hat, float inv_scale, cudaStream_t st);
-ctof_status contract_tikhonov(const ctof_kernel_s* k, const double* hinv, const float2* m_hat,
+ctof_status contract_tikhonov(const ctof_kernel_s* k, const float* hinv, const float2* m_hat,
                               float2* x_hat, cudaStream_t st);
 size_t contract_admm_smem_bytes(int nt, int nz, int nbuf);
 
@@ -167,8 +167,8 @@ ctof_status batch_tikhonov_contract(const ctof_kernel_s* k, int batch, const flo
 // ---- build.cu ----------------------------------------------------------
 ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st);
 ctof_status build_tikhonov_factors(ctof_kernel_s* k, int slot, double lambda, cudaStream_t st);
-// FP64 (G + lambda I)^-1 for an absolute lambda, made on first use (two cached lambdas).
-ctof_status tikhonov_inverse(ctof_kernel_s* k, double lambda, const double** hinv, cudaStream_t st);
+// (G + lambda I)^-1 for an absolute lambda, made on first use (two cached lambdas).
+ctof_status tikhonov_inverse(ctof_kernel_s* k, double lambda, const float** hinv, cudaStream_t st);
 
 // ---- admm.cu ------------------------------------------------------------
 ctof_status admm_tv_stencil(const ctof_kernel_s* k, const float* x, const float* u2_old,

@@ -554,7 +554,7 @@ ctof_status op_forward(ctof_kernel_s* k, int batch, const float* x, float* meas,
 }
 
 // out = A^T r (tik_hinv null) or the Tikhonov solve T r = (G + lambda I)^-1 W^T r (per frequency)
-ctof_status op_adjoint(ctof_kernel_s* k, int batch, const float* r, float* out, const double* tik_hinv, const Ws& w,
+ctof_status op_adjoint(ctof_kernel_s* k, int batch, const float* r, float* out, const float* tik_hinv, const Ws& w,
                        cudaStream_t st) {
   const size_t vol = (size_t)k->nz * k->n * k->n, mt = (size_t)k->nt * k->n * k->n;
   const size_t sz = (size_t)k->nf * k->ldz, stt = (size_t)k->nf * k->ldt;
@@ -591,7 +591,7 @@ ctof_status unrolled_forward(ctof_learned_s* L, ctof_kernel_s* k, int batch, con
   const int nstore = train ? L->stages : 1;
   const float* eta = L->d_theta + L->nparam - L->stages;
   if (L->opt.x0_lambda_rel > 0.0) {
-    const double* hinv = nullptr;
+    const float* hinv = nullptr;
     CTOF_TRY(tikhonov_inverse(k, L->opt.x0_lambda_rel * k->gram_max, &hinv, st));
     CTOF_TRY(op_adjoint(k, batch, m, w.x, hinv, w, st));
   } else {
@@ -625,7 +625,7 @@ ctof_status unrolled_forward(ctof_learned_s* L, ctof_kernel_s* k, int batch, con
   }
   if (!train && L->opt.dc_steps > 0) {
     // x <- x - T(A x - m): the residual goes through the Tikhonov solve into w.h
-    const double* hinv = nullptr;
+    const float* hinv = nullptr;
     CTOF_TRY(tikhonov_inverse(k, L->opt.dc_lambda_rel * k->gram_max, &hinv, st));
     const long long mt = (long long)batch * k->nt * k->n * k->n;
     for (int d = 0; d < L->opt.dc_steps; ++d) {
