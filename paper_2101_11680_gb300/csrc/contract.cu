@@ -46,7 +46,7 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
 }
 
-// Shared-memory plan: nbuf W stages (W_hat block, Tikhonov inverse), nbuf
+// Shared-memory plan: nbuf W stages (W_hat block, Tikhonov inverse), nvs
 // vector stages, then the per-CTA scratch.
 struct Plan {
   int nt, nz, z4, q, sw;   // q = z4/4 float4 chunks per row, sw = smem row stride (floats)
@@ -60,7 +60,7 @@ struct Plan {
 
 __host__ __device__ inline size_t al16(size_t b) { return (b + 15) & ~(size_t)15; }
 
-__host__ __device__ inline Plan make_plan(int mode, int nt, int nz, int nbuf, int threads) {
+__host__ __device__ inline Plan make_plan(int mode, int nt, int nz, int nbuf, int nvs, int threads) {
   Plan p;
   p.nt = nt;
   p.nz = nz;
@@ -73,7 +73,7 @@ __host__ __device__ inline Plan make_plan(int mode, int nt, int nz, int nbuf, in
   p.wst = p.off_h + (mode == MODE_TIK ? al16((size_t)nz * p.z4 * 4) : 0);
   p.vst = al16(mode == MODE_FWD ? (size_t)p.z4 * 8 * 4 : (size_t)nt * 8 * 4);
   p.off_v = p.wst * nbuf;
-  size_t s = p.off_v + p.vst * nbuf;
+  size_t s = p.off_v + p.vst * nvs;
   p.off_part = s;
   if (mode != MODE_FWD) s += al16((size_t)p.J * p.z4 * 8 * 4);
   p.off_b = s;
@@ -180,94 +180,111 @@ __device__ __forceinline__ void compute_adj_partials(const Plan& P, const float*
   }
 }
 
+// Steps s = 0, 1, ... of a CTA are (class blockIdx.x + (s / nvol) * gridDim.x,
+// volume s % nvol).  With nbuf == 2 the copies of step s + nvs - 1 are issued
+// while step s computes (one commit group per step; a class's W_hat block goes
+// with the vectors of its first volume, at most one class ahead since
+// nvs <= nvol + 1).  With nbuf == 1 nothing overlaps.
+template <int MODE>
+__device__ __forceinline__ void issue_step(const Plan& P, char* smem, int (*s_mem)[4], const float* __restrict__ what,
+                                           const int* __restrict__ members, const float2* __restrict__ vin,
+                                           int ld_in, size_t in_vstride, const float* __restrict__ hinv,
+                                           int nclass, int nvol, int nbuf, int nvs, int s) {
+  const int ci = s / nvol, b = s - ci * nvol;
+  const int c = blockIdx.x + ci * gridDim.x;
+  if (c >= nclass) return;
+  const int wb = nbuf == 2 ? (ci & 1) : 0;
+  if (b == 0) issue_w<MODE>(P, smem + wb * P.wst, s_mem[wb], what, members, hinv, c);
+  issue_v<MODE>(P, smem + P.off_v + (s % nvs) * P.vst, members, vin + (size_t)b * in_vstride, ld_in, c);
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(CT_THREADS) k_contract(const float* __restrict__ what,
                                                          const int* __restrict__ members, int nclass, int nt, int nz,
                                                          const float2* __restrict__ vin, int ld_in, size_t in_vstride,
                                                          float2* __restrict__ vout, int ld_out, size_t out_vstride,
-                                                         int nvol, const float* __restrict__ hinv, int nbuf) {
+                                                         int nvol, const float* __restrict__ hinv, int nbuf, int nvs) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int s_mem[2][4];
-  const Plan P = make_plan(MODE, nt, nz, nbuf, blockDim.x);
+  const Plan P = make_plan(MODE, nt, nz, nbuf, nvs, blockDim.x);
   float* part = reinterpret_cast<float*>(smem + P.off_part);
   float* sB = reinterpret_cast<float*>(smem + P.off_b);
   const int G = gridDim.x;
-  if (blockIdx.x < nclass) {
-    issue_w<MODE>(P, smem, s_mem[0], what, members, hinv, blockIdx.x);
-    issue_v<MODE>(P, smem + P.off_v, members, vin, ld_in, blockIdx.x);
+  const int my_classes = blockIdx.x < nclass ? (nclass - 1 - blockIdx.x) / G + 1 : 0;
+  const int nsteps = my_classes * nvol;
+  const int ahead = nbuf == 2 ? nvs - 1 : 0;
+  for (int s = 0; s < (ahead > 0 ? ahead : 1); ++s) {
+    if (s < nsteps)
+      issue_step<MODE>(P, smem, s_mem, what, members, vin, ld_in, in_vstride, hinv, nclass, nvol, nbuf, nvs, s);
+    cp_commit();
   }
-  cp_commit();
-  int step = 0, ci = 0;
-  for (int c = blockIdx.x; c < nclass; c += G, ++ci) {
+  for (int s = 0; s < nsteps; ++s) {
+    const int ci = s / nvol, b = s - ci * nvol;
     const int wcur = nbuf == 2 ? (ci & 1) : 0;
-    for (int b = 0; b < nvol; ++b, ++step) {
-      const int vcur = nbuf == 2 ? (step & 1) : 0;
-      int nc = c, nb = b + 1;
-      if (nb == nvol) {
-        nc = c + G;
-        nb = 0;
+    const int vcur = s % nvs;
+    if (nbuf == 2) {
+      if (s + ahead < nsteps)
+        issue_step<MODE>(P, smem, s_mem, what, members, vin, ld_in, in_vstride, hinv, nclass, nvol, nbuf, nvs,
+                         s + ahead);
+      cp_commit();
+      // all groups but the newest `ahead` are complete: those hold steps s+1 .. s+ahead
+      switch (ahead) {
+        case 1: cp_wait<1>(); break;
+        case 2: cp_wait<2>(); break;
+        default: cp_wait<3>(); break;
       }
-      if (nbuf == 2) {
-        if (b == 0 && c + G < nclass)
-          issue_w<MODE>(P, smem + (wcur ^ 1) * P.wst, s_mem[wcur ^ 1], what, members, hinv, c + G);
-        if (nc < nclass)
-          issue_v<MODE>(P, smem + P.off_v + (vcur ^ 1) * P.vst, members, vin + (size_t)nb * in_vstride, ld_in, nc);
-        cp_commit();
-        cp_wait<1>();
-      } else {
-        cp_wait<0>();
-      }
+    } else {
+      cp_wait<0>();
+    }
+    __syncthreads();
+    const char* wst = smem + wcur * P.wst;
+    const float* sW = reinterpret_cast<const float*>(wst);
+    const char* sv = smem + P.off_v + vcur * P.vst;
+    const int* mem = s_mem[wcur];
+    float2* out = vout + (size_t)b * out_vstride;
+    if (MODE == MODE_FWD) {
+      compute_fwd(P, sW, sv, mem, out, ld_out);
+    } else {
+      compute_adj_partials(P, sW, sv, part);
       __syncthreads();
-      const char* wst = smem + wcur * P.wst;
-      const float* sW = reinterpret_cast<const float*>(wst);
-      const char* sv = smem + P.off_v + vcur * P.vst;
-      const int* mem = s_mem[wcur];
-      float2* out = vout + (size_t)b * out_vstride;
-      if (MODE == MODE_FWD) {
-        compute_fwd(P, sW, sv, mem, out, ld_out);
+      if (MODE == MODE_ADJ) {
+        for (int o = threadIdx.x; o < 4 * nz; o += blockDim.x) {
+          const int m = o / nz, z = o - m * nz;
+          if (mem[m] < 0) continue;
+          float re = 0.f, im = 0.f;
+          for (int j = 0; j < P.J; ++j) {
+            re += part[((size_t)j * P.z4 + z) * 8 + 2 * m];
+            im += part[((size_t)j * P.z4 + z) * 8 + 2 * m + 1];
+          }
+          out[(size_t)mem[m] * ld_out + z] = make_float2(re, im);
+        }
       } else {
-        compute_adj_partials(P, sW, sv, part);
+        for (int o = threadIdx.x; o < nz * 8; o += blockDim.x) {
+          const int z = o >> 3, r = o & 7;
+          float s = 0.f;
+          for (int j = 0; j < P.J; ++j) s += part[((size_t)j * P.z4 + z) * 8 + r];
+          sB[z * 8 + r] = s;
+        }
         __syncthreads();
-        if (MODE == MODE_ADJ) {
-          for (int o = threadIdx.x; o < 4 * nz; o += blockDim.x) {
-            const int m = o / nz, z = o - m * nz;
-            if (mem[m] < 0) continue;
-            float re = 0.f, im = 0.f;
-            for (int j = 0; j < P.J; ++j) {
-              re += part[((size_t)j * P.z4 + z) * 8 + 2 * m];
-              im += part[((size_t)j * P.z4 + z) * 8 + 2 * m + 1];
-            }
-            out[(size_t)mem[m] * ld_out + z] = make_float2(re, im);
+        // x[i] = sum_j Hinv[j][i] b[j]  (Hinv symmetric; consecutive threads read consecutive i)
+        const float* sH = reinterpret_cast<const float*>(wst + P.off_h);
+        for (int o = threadIdx.x; o < 4 * nz; o += blockDim.x) {
+          const int m = o / nz, i = o - m * nz;
+          if (mem[m] < 0) continue;
+          float re = 0.f, im = 0.f;
+          for (int j = 0; j < nz; ++j) {
+            const float h = sH[j * P.z4 + i];
+            re = fmaf(h, sB[j * 8 + 2 * m], re);
+            im = fmaf(h, sB[j * 8 + 2 * m + 1], im);
           }
-        } else {
-          for (int o = threadIdx.x; o < nz * 8; o += blockDim.x) {
-            const int z = o >> 3, r = o & 7;
-            float s = 0.f;
-            for (int j = 0; j < P.J; ++j) s += part[((size_t)j * P.z4 + z) * 8 + r];
-            sB[z * 8 + r] = s;
-          }
-          __syncthreads();
-          // x[i] = sum_j Hinv[j][i] b[j]  (Hinv symmetric; consecutive threads read consecutive i)
-          const float* sH = reinterpret_cast<const float*>(wst + P.off_h);
-          for (int o = threadIdx.x; o < 4 * nz; o += blockDim.x) {
-            const int m = o / nz, i = o - m * nz;
-            if (mem[m] < 0) continue;
-            float re = 0.f, im = 0.f;
-            for (int j = 0; j < nz; ++j) {
-              const float h = sH[j * P.z4 + i];
-              re = fmaf(h, sB[j * 8 + 2 * m], re);
-              im = fmaf(h, sB[j * 8 + 2 * m + 1], im);
-            }
-            out[(size_t)mem[m] * ld_out + i] = make_float2(re, im);
-          }
+          out[(size_t)mem[m] * ld_out + i] = make_float2(re, im);
         }
       }
-      __syncthreads();
-      if (nbuf == 1 && nc < nclass) {
-        if (nb == 0) issue_w<MODE>(P, smem, s_mem[0], what, members, hinv, nc);
-        issue_v<MODE>(P, smem + P.off_v, members, vin + (size_t)nb * in_vstride, ld_in, nc);
-        cp_commit();
-      }
+    }
+    __syncthreads();
+    if (nbuf == 1 && s + 1 < nsteps) {
+      issue_step<MODE>(P, smem, s_mem, what, members, vin, ld_in, in_vstride, hinv, nclass, nvol, nbuf, nvs, s + 1);
+      cp_commit();
     }
   }
   cp_wait<0>();
@@ -279,12 +296,16 @@ template <int MODE>
 ctof_status launch(const ctof_kernel_s* k, int nvol, const float2* vin, int ld_in, size_t in_vstride, float2* vout,
                    int ld_out, size_t out_vstride, const float* hinv, cudaStream_t st) {
   if (nvol < 1) return CTOF_EINVAL;
-  int nbuf = 2;
-  Plan p = make_plan(MODE, k->nt, k->nz, 2, CT_THREADS);
-  if (p.total > SMEM_LIMIT) {
-    nbuf = 1;
-    p = make_plan(MODE, k->nt, k->nz, 1, CT_THREADS);
+  // deepest vector pipeline that fits (at most one class ahead: nvs <= nvol + 1), else no overlap
+  int nbuf = 1, nvs = 1;
+  for (int v = (nvol + 1 < 4 ? nvol + 1 : 4); v >= 2; --v) {
+    if (make_plan(MODE, k->nt, k->nz, 2, v, CT_THREADS).total <= SMEM_LIMIT) {
+      nbuf = 2;
+      nvs = v;
+      break;
+    }
   }
+  const Plan p = make_plan(MODE, k->nt, k->nz, nbuf, nvs, CT_THREADS);
   if (p.total > SMEM_LIMIT) return CTOF_EUNSUPPORTED;
   CTOF_CUDA_TRY(cudaFuncSetAttribute(k_contract<MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)p.total));
   int per_sm = (int)((228 * 1024) / (p.total + 1024 + 64));
@@ -293,7 +314,7 @@ ctof_status launch(const ctof_kernel_s* k, int nvol, const float2* vin, int ld_i
   int grid = 152 * per_sm;
   if (grid > k->nclass) grid = k->nclass;
   k_contract<MODE><<<grid, CT_THREADS, p.total, st>>>(k->d_what, k->d_members, k->nclass, k->nt, k->nz, vin, ld_in,
-                                                      in_vstride, vout, ld_out, out_vstride, nvol, hinv, nbuf);
+                                                      in_vstride, vout, ld_out, out_vstride, nvol, hinv, nbuf, nvs);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
@@ -303,7 +324,7 @@ ctof_status launch(const ctof_kernel_s* k, int nvol, const float2* vin, int ld_i
 size_t contract_smem_bytes(int nt, int nz) {
   size_t worst = 0;
   for (int mode = MODE_FWD; mode <= MODE_TIK; ++mode) {
-    const size_t b = make_plan(mode, nt, nz, 1, CT_THREADS).total;
+    const size_t b = make_plan(mode, nt, nz, 1, 1, CT_THREADS).total;
     worst = b > worst ? b : worst;
   }
   return worst;
