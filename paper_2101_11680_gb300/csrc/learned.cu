@@ -163,7 +163,7 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d(const __nv_bfloat16* __re
         for (int e = 0; e < 4; ++e) a[e] = relu2(a[e]);
       }
       mma_bf16(acc[j][0], a, b[0], b[1]);
-      mma_bf16(acc[j][1], a, b[2], b[3]);
+      if (!OUT_PROX) mma_bf16(acc[j][1], a, b[2], b[3]);  // the last layer has one output channel
     }
   }
   const int yy = y0 + warp;
@@ -204,6 +204,92 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d(const __nv_bfloat16* __re
       }
       outw[v0 * 8 + (co >> 1)] = pack2(__float2bfloat16_rn(r0), __float2bfloat16_rn(r1));
       outw[v1 * 8 + (co >> 1)] = pack2(__float2bfloat16_rn(r2), __float2bfloat16_rn(r3));
+    }
+  }
+}
+
+// First layer at inference: one input channel (z / mu0), so the 27 taps (padded
+// to 32) form the MMA's K dimension instead of 27 K = 16 channel blocks with
+// 15 zero channels: 2 x 2 MMAs per 16-voxel job instead of 27 x 2.  The input
+// tile holds one BF16 value per voxel; A fragments are gathered from it tap by
+// tap, B fragments (W1[co][tap]) sit in registers for the whole CTA.
+template <int TXC>
+__global__ void __launch_bounds__(CV_THREADS) k_conv_first(const float* __restrict__ zin, float in_scale,
+                                                           const __nv_bfloat16* __restrict__ w,
+                                                           const float* __restrict__ bias,
+                                                           __nv_bfloat16* __restrict__ out, Geo G) {
+  constexpr int TX = 16 * TXC, SX = TX + 2, SY = CV_TY + 2;
+  __shared__ __nv_bfloat16 s_in[3 * SY * SX];
+  const int bb = blockIdx.z / G.z, zz = blockIdx.z - bb * G.z;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * CV_TY;
+  for (int v = threadIdx.x; v < 3 * SY * SX; v += CV_THREADS) {
+    const int tx = v % SX, r = v / SX, ty = r % SY, tz = r / SY;
+    const int gx = x0 + tx - 1, gy = y0 + ty - 1, gz = zz + tz - 1;
+    float val = 0.f;
+    if (gx >= 0 && gx < G.x && gy >= 0 && gy < G.y && gz >= 0 && gz < G.z)
+      val = zin[(((long long)bb * G.z + gz) * G.y + gy) * G.x + gx] * in_scale;
+    s_in[v] = __float2bfloat16_rn(val);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int g = lane >> 2, tg = lane & 3;
+  const __nv_bfloat16 zb = __float2bfloat16_rn(0.f);
+  // B[k = tap][n = co] = W1[co][tap] (tap >= 27: 0); [k chunk][n tile][b0 / b1]
+  unsigned bf[2][2][2];
+  // this lane's taps: k chunk kc, half h, element e -> tap 16 kc + 8 h + 2 tg + e; offset in the tile or -1
+  int toff[2][2][2];
+#pragma unroll
+  for (int kc = 0; kc < 2; ++kc)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int t = 16 * kc + 8 * h + 2 * tg + e;
+        toff[kc][h][e] = t < 27 ? ((t / 9) * SY + (t / 3) % 3) * SX + t % 3 : -1;
+      }
+#pragma unroll
+      for (int nt = 0; nt < 2; ++nt) {
+        const int co = nt * 8 + g, t = 16 * kc + 8 * h + 2 * tg;
+        const __nv_bfloat16 lo = t < 27 ? w[(t * CH + co) * CH] : zb;
+        const __nv_bfloat16 hi = t + 1 < 27 ? w[((t + 1) * CH + co) * CH] : zb;
+        bf[kc][nt][h] = pack2(lo, hi);
+      }
+    }
+  __syncthreads();
+  float acc[TXC][2][4];
+#pragma unroll
+  for (int j = 0; j < TXC; ++j)
+#pragma unroll
+    for (int n = 0; n < 2; ++n)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) acc[j][n][e] = 0.f;
+#pragma unroll
+  for (int j = 0; j < TXC; ++j) {
+    const int base0 = warp * SX + j * 16 + g, base1 = base0 + 8;
+#pragma unroll
+    for (int kc = 0; kc < 2; ++kc) {
+      unsigned a[4];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int o0 = toff[kc][h][0], o1 = toff[kc][h][1];
+        a[2 * h] = pack2(o0 >= 0 ? s_in[base0 + o0] : zb, o1 >= 0 ? s_in[base0 + o1] : zb);
+        a[2 * h + 1] = pack2(o0 >= 0 ? s_in[base1 + o0] : zb, o1 >= 0 ? s_in[base1 + o1] : zb);
+      }
+      mma_bf16(acc[j][0], a, bf[kc][0][0], bf[kc][0][1]);
+      mma_bf16(acc[j][1], a, bf[kc][1][0], bf[kc][1][1]);
+    }
+  }
+  const long long row = (((long long)bb * G.z + zz) * G.y + y0 + warp) * G.x;
+  unsigned* outw = reinterpret_cast<unsigned*>(out);
+#pragma unroll
+  for (int j = 0; j < TXC; ++j) {
+    const long long v0 = row + x0 + j * 16 + g, v1 = v0 + 8;
+#pragma unroll
+    for (int nt = 0; nt < 2; ++nt) {
+      const int co = nt * 8 + 2 * tg;
+      outw[v0 * 8 + (co >> 1)] =
+          pack2(__float2bfloat16_rn(acc[j][nt][0] + bias[co]), __float2bfloat16_rn(acc[j][nt][1] + bias[co + 1]));
+      outw[v1 * 8 + (co >> 1)] =
+          pack2(__float2bfloat16_rn(acc[j][nt][2] + bias[co]), __float2bfloat16_rn(acc[j][nt][3] + bias[co + 1]));
     }
   }
 }
@@ -525,6 +611,20 @@ ctof_status conv_launch(const __nv_bfloat16* in, const float* in_f, float in_sca
   return CTOF_OK;
 }
 
+ctof_status conv_first(const float* z, float in_scale, const __nv_bfloat16* wt, const float* bias,
+                       __nv_bfloat16* out, Geo G, cudaStream_t st) {
+  const int txc = G.x % 64 == 0 ? 4 : (G.x % 32 == 0 ? 2 : 1);
+  const dim3 grid(G.x / (16 * txc), G.y / CV_TY, G.b * G.z);
+  if (txc == 4)
+    k_conv_first<4><<<grid, CV_THREADS, 0, st>>>(z, in_scale, wt, bias, out, G);
+  else if (txc == 2)
+    k_conv_first<2><<<grid, CV_THREADS, 0, st>>>(z, in_scale, wt, bias, out, G);
+  else
+    k_conv_first<1><<<grid, CV_THREADS, 0, st>>>(z, in_scale, wt, bias, out, G);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
 ctof_status conv(const __nv_bfloat16* in, int relu_in, const __nv_bfloat16* wt, const float* bias,
                  const __nv_bfloat16* mask, __nv_bfloat16* out, Geo G, cudaStream_t st) {
   return conv_launch<false, false>(in, nullptr, 0.f, relu_in, wt, bias, mask, out, nullptr, nullptr, G, st);
@@ -614,8 +714,7 @@ ctof_status unrolled_forward(ctof_learned_s* L, ctof_kernel_s* k, int batch, con
       CTOF_CUDA_TRY(cudaGetLastError());
       CTOF_TRY(conv(u, 0, L->d_wf + 0 * 27 * CH * CH, L->d_bias + 0 * CH, nullptr, y1, G, st));
     } else {
-      CTOF_TRY((conv_launch<true, false>(nullptr, z, 1.0f / MU0, 0, L->d_wf, L->d_bias, nullptr, y1, nullptr,
-                                         nullptr, G, st)));
+      CTOF_TRY(conv_first(z, 1.0f / MU0, L->d_wf, L->d_bias, y1, G, st));
     }
     CTOF_TRY(conv(y1, 1, L->d_wf + 1 * 27 * CH * CH, L->d_bias + 1 * CH, nullptr, y2, G, st));
     CTOF_TRY(conv(y2, 1, L->d_wf + 2 * 27 * CH * CH, L->d_bias + 2 * CH, nullptr, y3, G, st));
