@@ -86,6 +86,16 @@ __device__ __forceinline__ int out_pos(int lane, int i) {
   return R * brev5(lane) + bitrevc(i, ilog2c(R));
 }
 
+// Shared-memory slot of transform element e.  A warp writes its R registers
+// to elements R*bitrev5(lane) + i', i.e. 32 elements R apart, which would all
+// fall in two banks; XOR-ing the low log2(R) bits with the next ones spreads
+// them over all banks.  A permutation within each aligned block of R elements.
+template <int P>
+__device__ __forceinline__ int sw_pos(int e) {
+  constexpr int R = P / 32;
+  return e ^ ((e / R) & (R - 1));
+}
+
 template <int P>
 __device__ __forceinline__ void stage_twiddles(float2* s_tw, const float2* tw) {
   for (int i = threadIdx.x; i < P; i += blockDim.x) s_tw[i] = tw[i];
@@ -95,8 +105,8 @@ __device__ __forceinline__ void stage_twiddles(float2* s_tw, const float2* tw) {
 template <int P>
 __device__ __forceinline__ void split_write(const float2* buf, int lane, float2* rowA, float2* rowB) {
   for (int kk = lane; kk <= P / 2; kk += 32) {
-    const float2 zk = buf[kk];
-    const float2 zm = buf[(P - kk) & (P - 1)];
+    const float2 zk = buf[sw_pos<P>(kk)];
+    const float2 zm = buf[sw_pos<P>((P - kk) & (P - 1))];
     rowA[kk] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
     if (rowB) rowB[kk] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
   }
@@ -152,7 +162,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_fwd(const float* __rest
     }
     warp_fft<P, false>(v, lane, s_tw);
 #pragma unroll
-    for (int i = 0; i < R; ++i) buf[out_pos<P>(lane, i)] = v[i];
+    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
     __syncwarp();
     split_write<P>(buf, lane, inter + (size_t)g0 * hp, has1 ? inter + (size_t)g1 * hp : nullptr);
     __syncwarp();
@@ -187,10 +197,10 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const float2* __res
     __syncwarp();
     warp_fft<P, true>(v, lane, s_tw);
 #pragma unroll
-    for (int i = 0; i < R; ++i) buf[out_pos<P>(lane, i)] = v[i];
+    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
     __syncwarp();
     for (int c = lane; c < cols_out; c += 32) {
-      const float2 z = buf[c];
+      const float2 z = buf[sw_pos<P>(c)];
       out[(size_t)g0 * ld_out + c] = z.x * scale;
       if (has1) out[(size_t)g1 * ld_out + c] = z.y * scale;
     }
@@ -235,14 +245,14 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restri
     __syncwarp();
     warp_fft<P, true>(v, lane, s_tw);
 #pragma unroll
-    for (int i = 0; i < R; ++i) buf[out_pos<P>(lane, i)] = v[i];
+    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int c = lane + 32 * i;
       float2 cc = make_float2(0.f, 0.f);
       if (c < n) {
-        const float2 kx = cscale(buf[c], scale);
+        const float2 kx = cscale(buf[sw_pos<P>(c)], scale);
         {
           const size_t idx = (size_t)g0 * n + c;
           const float a1 = kx.x + u1[idx];
@@ -263,7 +273,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restri
     __syncwarp();
     warp_fft<P, false>(v, lane, s_tw);
 #pragma unroll
-    for (int i = 0; i < R; ++i) buf[out_pos<P>(lane, i)] = v[i];
+    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
     __syncwarp();
     split_write<P>(buf, lane, inter + (size_t)g0 * hp, has1 ? inter + (size_t)g1 * hp : nullptr);
     __syncwarp();
@@ -304,14 +314,14 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restri
     }
     warp_fft<P, false>(v, lane, s_tw);
 #pragma unroll
-    for (int i = 0; i < R; ++i) tile[out_pos<P>(lane, i) * LDT + c] = v[i];
+    for (int i = 0; i < R; ++i) tile[sw_pos<P>(out_pos<P>(lane, i)) * LDT + c] = v[i];
   }
   __syncthreads();
   for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
     const int ky = idx / NC, cc = idx % NC;
     const int pll = cc % PB, kxl = cc / PB;
     const int kx = kx0 + kxl, pl = pl0 + pll;
-    if (kx < h && pl < nplanes) out[((size_t)ky * h + kx) * ldf + pl] = tile[ky * LDT + cc];
+    if (kx < h && pl < nplanes) out[((size_t)ky * h + kx) * ldf + pl] = tile[sw_pos<P>(ky) * LDT + cc];
   }
 }
 
@@ -346,7 +356,7 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restri
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int y = out_pos<P>(lane, i);
-      if (y < rows_out) tile[y * LDT + c] = v[i];
+      if (y < rows_out) tile[sw_pos<P>(y) * LDT + c] = v[i];
     }
   }
   __syncthreads();
@@ -354,7 +364,8 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restri
     const int row = idx / NC, cc = idx % NC;
     const int kxl = cc % KB, pll = cc / KB;
     const int kx = kx0 + kxl, pl = pl0 + pll;
-    if (kx < h && pl < nplanes) inter[((size_t)pl * rows_out + row) * hp + kx] = tile[row * LDT + kxl * PB + pll];
+    if (kx < h && pl < nplanes)
+      inter[((size_t)pl * rows_out + row) * hp + kx] = tile[sw_pos<P>(row) * LDT + kxl * PB + pll];
   }
 }
 
