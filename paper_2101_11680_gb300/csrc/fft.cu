@@ -45,6 +45,17 @@ __device__ __forceinline__ float2 tw_get(const float2* tw, int j) {
   return INV ? make_float2(w.x, -w.y) : w;
 }
 
+// Shared twiddle table: the P roots w^j, then per-lane copies of the values
+// the lanes need at the same time, so that those reads hit distinct banks:
+// [P + s - 1 + l] = w^(l P / 2s) for the cross-lane stage s (l < s), and
+// [P + 31 + 32 (k2 - 1) + lane] = w^(lane k2) for the register twiddles.
+__host__ __device__ constexpr int tw_count(int P) { return P + 31 + 32 * (P / 32 - 1); }
+
+template <bool INV>
+__device__ __forceinline__ float2 tw_conj(float2 w) {
+  return INV ? make_float2(w.x, -w.y) : w;
+}
+
 // Length-P DFT held by one warp (see file comment).  INV selects exp(+...).
 template <int P, bool INV>
 __device__ __forceinline__ void warp_fft(float2 (&v)[P / 32], int lane, const float2* tw) {
@@ -63,12 +74,12 @@ __device__ __forceinline__ void warp_fft(float2 (&v)[P / 32], int lane, const fl
 #pragma unroll
   for (int i = 1; i < R; ++i) {
     const int k2 = bitrevc(i, ilog2c(R));
-    v[i] = cmul(v[i], tw_get<P, INV>(tw, lane * k2));
+    v[i] = cmul(v[i], tw_conj<INV>(tw[P + 31 + 32 * (k2 - 1) + lane]));
   }
 #pragma unroll
   for (int s = 16; s >= 1; s >>= 1) {
     const bool upper = (lane & s) != 0;
-    const float2 w = tw_get<P, INV>(tw, (lane & (s - 1)) * (P / (2 * s)));
+    const float2 w = tw_conj<INV>(tw[P + s - 1 + (lane & (s - 1))]);
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       float2 o;
@@ -98,7 +109,21 @@ __device__ __forceinline__ int sw_pos(int e) {
 
 template <int P>
 __device__ __forceinline__ void stage_twiddles(float2* s_tw, const float2* tw) {
-  for (int i = threadIdx.x; i < P; i += blockDim.x) s_tw[i] = tw[i];
+  for (int i = threadIdx.x; i < tw_count(P); i += blockDim.x) {
+    int j;
+    if (i < P) {
+      j = i;
+    } else if (i < P + 31) {
+      const int e = i - P;
+      int s = 1;
+      while (2 * s - 1 <= e) s *= 2;  // stage s holds entries s-1 .. 2s-2
+      j = (e - (s - 1)) * (P / (2 * s));
+    } else {
+      const int e = i - P - 31;
+      j = ((e & 31) * (e / 32 + 1)) & (P - 1);
+    }
+    s_tw[i] = tw[j];
+  }
 }
 
 // Split Z = FFT(a + i b) of two real rows into A = FFT(a), B = FFT(b), k <= P/2.
@@ -143,7 +168,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_fwd(const float* __rest
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* buf = smem + P + warp * (P + 2);
+  float2* buf = smem + tw_count(P) + warp * (P + 2);
   stage_twiddles<P>(s_tw, tw);
   __syncthreads();
   const int npairs = (total_rows + 1) >> 1;
@@ -178,7 +203,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const float2* __res
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* buf = smem + P + warp * (P + 2);
+  float2* buf = smem + tw_count(P) + warp * (P + 2);
   stage_twiddles<P>(s_tw, tw);
   __syncthreads();
   const int npairs = (total_rows + 1) >> 1;
@@ -225,7 +250,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restri
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* buf = smem + P + warp * (P + 2);
+  float2* buf = smem + tw_count(P) + warp * (P + 2);
   stage_twiddles<P>(s_tw, tw);
   __syncthreads();
   const float inv1r = 1.0f / (1.0f + rho);
@@ -292,7 +317,7 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restri
   constexpr int LDT = NC + 1;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
-  float2* tile = smem + P;
+  float2* tile = smem + tw_count(P);
   const int kx0 = blockIdx.x * KB, pl0 = blockIdx.y * PB;
   stage_twiddles<P>(s_tw, tw);
   for (int idx = threadIdx.x; idx < rows_in * NC; idx += COL_THREADS) {
@@ -335,7 +360,7 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restri
   constexpr int LDT = NC + 1;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
-  float2* tile = smem + P;
+  float2* tile = smem + tw_count(P);
   const int kx0 = blockIdx.x * KB, pl0 = blockIdx.y * PB;
   stage_twiddles<P>(s_tw, tw);
   for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
@@ -371,8 +396,8 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restri
 
 // ------------------------------------------------------------ launchers ----
 
-size_t row_smem(int p) { return (size_t)(p + ROW_WARPS * (p + 2)) * sizeof(float2); }
-size_t col_smem(int p) { return (size_t)(p + p * (NC + 1)) * sizeof(float2); }
+size_t row_smem(int p) { return (size_t)(tw_count(p) + ROW_WARPS * (p + 2)) * sizeof(float2); }
+size_t col_smem(int p) { return (size_t)(tw_count(p) + p * (NC + 1)) * sizeof(float2); }
 
 template <typename F>
 cudaError_t allow_smem(F* fn, size_t bytes) {
