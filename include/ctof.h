@@ -224,7 +224,7 @@ ctof_status ctof_learned_reconstruct(ctof_learned net, ctof_kernel k, int batch,
 ctof_status ctof_reconstruct_batch(int count, const ctof_kernel* ks, const float* const* d_m,
                                    const ctof_solver_params* params, float* const* d_mu, void* stream);
 
-/* Autotuner: times the column-FFT plane tile (4, 8 or 16 planes per tile) for
+/* Autotuner: times the column-FFT plane tile (8, 16 or 32 planes per tile) for
  * each of the four column-pass shapes of an ADMM iteration on this handle and
  * keeps the fastest; the results are bit-identical for every tile, only the
  * speed changes.  Runs automatically before the first ADMM graph capture of a

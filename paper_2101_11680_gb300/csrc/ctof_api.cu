@@ -199,12 +199,12 @@ ctof_status ensure_events(ctof_kernel_s* k, int count) {
   return CTOF_OK;
 }
 
-// Autotuner: times each column-pass plane tile (4, 8, 16 planes) on the
+// Autotuner: times each column-pass plane tile (8, 16, 32 planes) on the
 // handle's own buffers for the four column-pass shapes of an ADMM iteration
 // and keeps the fastest.  Synchronous; must run outside stream capture.
 ctof_status autotune(ctof_kernel_s* k, cudaStream_t st) {
   if (k->tuned) return CTOF_OK;
-  const int cands[3] = {4, 8, 16};
+  const int cands[3] = {8, 16, 32};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CTOF_CUDA_TRY(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -213,14 +213,14 @@ ctof_status autotune(ctof_kernel_s* k, cudaStream_t st) {
   }
   ctof_status s = CTOF_OK;
   const int n = k->n, P = k->p;
-  if (cudaMemsetAsync(k->d_inter_t, 0, (size_t)k->nt * n * k->hp * sizeof(float2), st) != cudaSuccess ||
-      cudaMemsetAsync(k->d_inter_z, 0, (size_t)k->nz * P * k->hp * sizeof(float2), st) != cudaSuccess ||
+  if (cudaMemsetAsync(k->d_inter_t, 0, fft_inter_elems(k, k->nt, n) * sizeof(float2), st) != cudaSuccess ||
+      cudaMemsetAsync(k->d_inter_z, 0, fft_inter_elems(k, k->nz, P) * sizeof(float2), st) != cudaSuccess ||
       cudaMemsetAsync(k->d_spec_t, 0, (size_t)k->nf * k->ldt * sizeof(float2), st) != cudaSuccess ||
       cudaMemsetAsync(k->d_spec_z2, 0, (size_t)k->nf * k->ldz * sizeof(float2), st) != cudaSuccess)
     s = CTOF_ECUDA;
   for (int use = 0; use < 4 && s == CTOF_OK; ++use) {
     float best_ms = 1e30f;
-    int best = 8;
+    int best = 16;
     for (int ci = 0; ci < 3 && s == CTOF_OK; ++ci) {
       const int pb = cands[ci];
       auto launch = [&]() -> ctof_status {
@@ -549,7 +549,7 @@ ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, 
   k->r_min = optics->clamp_r ? 0.5 * std::min(grid->dx_mm, std::min(grid->dy_mm, grid->dz_mm)) : 0.0;
   k->tik_lambda[0] = k->tik_lambda[1] = -1.0;
   k->tik_last = 1;
-  for (int i = 0; i < 4; ++i) k->tune_pb[i] = 8;
+  for (int i = 0; i < 4; ++i) k->tune_pb[i] = 16;
   {
     static std::atomic<unsigned long long> next_id{1};
     k->uid = next_id++;
@@ -573,8 +573,8 @@ ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, 
   const size_t o_st2 = cv.take<float2>((size_t)k->nf * k->ldt);
   const size_t o_sz = cv.take<float2>((size_t)k->nf * k->ldz);
   const size_t o_sz2 = cv.take<float2>((size_t)k->nf * k->ldz);
-  const size_t o_it = cv.take<float2>((size_t)nt * n * k->hp);
-  const size_t o_iz = cv.take<float2>((size_t)nz * P * k->hp);
+  const size_t o_it = cv.take<float2>(fft_inter_elems(k, nt, n));
+  const size_t o_iz = cv.take<float2>(fft_inter_elems(k, nz, P));
   const size_t o_u1 = cv.take<float>((size_t)nt * n * n);
   const size_t o_ms = cv.take<float>((size_t)nt * n * n);
   const size_t o_u2a = cv.take<float>(3 * nz * pp);

@@ -18,7 +18,7 @@ struct ctof_kernel_s {
   int n;        // lateral scan size (nx == ny)
   int p;        // lateral FFT size
   int h;        // P/2 + 1 (half-plane width)
-  int hp;       // row pitch (complex) of row-pass intermediates
+  int hp;       // kx pitch of the row-pass intermediates [row][hp][plane pitch]
   int nf;       // P * h half-plane frequencies
   int q;        // kernel-table extent per lateral axis (n linear, P/2+1 circular)
   int nt, nz;
@@ -47,8 +47,8 @@ struct ctof_kernel_s {
   float2* d_spec_t2;   // [nf][ldt]
   float2* d_spec_z;    // [nf][ldz]
   float2* d_spec_z2;   // [nf][ldz]
-  float2* d_inter_t;   // [nt][n][hp]
-  float2* d_inter_z;   // [nz][p][hp]
+  float2* d_inter_t;   // [n][hp][round_up(nt, 16)]
+  float2* d_inter_z;   // [p][hp][round_up(nz, 16)]
   float* d_u1;         // [nt][n][n]
   float* d_mstage;     // [nt][n][n]
   float* d_u2a;        // [3][nz][p][p]
@@ -111,6 +111,8 @@ struct DeviceGuard {
 };
 
 // ---- fft.cu -------------------------------------------------------------
+// Complex elements of a row-pass intermediate for `rows` rows of `nplanes` planes.
+size_t fft_inter_elems(const ctof_kernel_s* k, int nplanes, int rows);
 // Forward R2C of planes of real rows [nplanes][rows_in][ld_in] (first cols_in
 // columns used, the rest of the P-wide row is zero) into frequency-major
 // spectra out[f][ldf] (plane index fastest).  Zero rows beyond rows_in.

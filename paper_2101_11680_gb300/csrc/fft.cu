@@ -5,14 +5,20 @@
 // the plane index (time bin or depth) fastest, because the per-frequency
 // contraction reads whole T- or Z-vectors of one frequency.
 //
-// Two passes per direction:
-//   rows    (x axis, real <-> complex): one warp transforms two real rows packed
-//           as one complex row, then splits them with the Hermitian identities.
-//   columns (y axis, complex): a CTA stages a tile of 32 columns (32/PB
-//           kx-columns x PB planes) in shared memory, each warp transforms
-//           whole columns, and the tile is written out transposed so that the
-//           frequency-major side moves in runs of PB consecutive planes.  PB is
-//           4, 8 or 16, picked per handle by the autotuner.
+// Two passes per direction, through an intermediate inter[row][kx][plane]
+// (plane fastest, plane pitch LP = nplanes rounded up to 16):
+//   rows    (x axis, real <-> complex): a CTA takes one row index for 16
+//           planes; each warp transforms the rows of two planes packed as one
+//           complex row and splits them with the Hermitian identities; the 16
+//           planes' half spectra leave through shared memory as 128-byte runs
+//           of consecutive planes.
+//   columns (y axis, complex): a CTA stages 32 columns (32/PB kx x PB
+//           consecutive planes) of all rows in shared memory, each warp
+//           transforms whole columns; both the intermediate and the
+//           frequency-major spectra are read and written in runs of PB planes
+//           (PB = 8, 16 or 32, picked per handle by the autotuner).  The
+//           transpose between plane-major input planes and frequency-major
+//           spectra happens in the row pass's shared-memory tile.
 // Each 1-D transform of length P = 32 R lives in one warp: lane l register r
 // holds element l + 32 r; an R-point DIF over registers, a twiddle by
 // w_P^(l k2), and a 32-point DIF across lanes (shuffles) give element
@@ -25,7 +31,7 @@
 namespace {
 
 // Column-pass tiles hold NC = 32 columns: KB kx-columns x PB planes, with
-// PB in {4, 8, 16} chosen per handle and use by the autotuner.
+// PB in {8, 16, 32} chosen per handle and use by the autotuner.
 constexpr int NC = 32;
 constexpr int COL_THREADS = 256;
 constexpr int ROW_WARPS = 8;
@@ -126,148 +132,165 @@ __device__ __forceinline__ void stage_twiddles(float2* s_tw, const float2* tw) {
   }
 }
 
-// Split Z = FFT(a + i b) of two real rows into A = FFT(a), B = FFT(b), k <= P/2.
+// ---------------------------------------------------------------- rows ----
+
+constexpr int RP = 2 * ROW_WARPS;  // planes per row-pass CTA
+
+__host__ __device__ inline int plane_ld(int nplanes) { return (nplanes + RP - 1) / RP * RP; }
+
+// Half spectra of the CTA's planes for one row: s_h[kx][plane] (pitch RP + 1).
+constexpr int SH_LD = RP + 1;
+
 template <int P>
-__device__ __forceinline__ void split_write(const float2* buf, int lane, float2* rowA, float2* rowB) {
+__device__ __forceinline__ void split_to_tile(const float2* buf, int lane, float2* s_h, int c0) {
   for (int kk = lane; kk <= P / 2; kk += 32) {
     const float2 zk = buf[sw_pos<P>(kk)];
     const float2 zm = buf[sw_pos<P>((P - kk) & (P - 1))];
-    rowA[kk] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-    if (rowB) rowB[kk] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+    s_h[kk * SH_LD + c0] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
+    s_h[kk * SH_LD + c0 + 1] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
   }
 }
 
-// Build Z[n] = A[n] + i B[n] from the half spectra of two real rows (Hermitian
-// extension for n > P/2) for the registers of this lane.
+// Z[n] = A[n] + i B[n] from the half spectra in tile columns c0, c0 + 1.
 template <int P>
-__device__ __forceinline__ void load_pair_spectrum(float2 (&v)[P / 32], const float2* a, const float2* b,
-                                                   int lane) {
+__device__ __forceinline__ void load_pair_from_tile(float2 (&v)[P / 32], const float2* s_h, int c0, int lane) {
   constexpr int R = P / 32;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int n = lane + 32 * i;
     float2 A, B;
     if (n <= P / 2) {
-      A = a[n];
-      B = b[n];
+      A = s_h[n * SH_LD + c0];
+      B = s_h[n * SH_LD + c0 + 1];
     } else {
-      A = cconj(a[P - n]);
-      B = cconj(b[P - n]);
+      A = cconj(s_h[(P - n) * SH_LD + c0]);
+      B = cconj(s_h[(P - n) * SH_LD + c0 + 1]);
     }
     v[i] = make_float2(A.x - B.y, A.y + B.x);
   }
 }
 
-// ---------------------------------------------------------------- rows ----
+template <int P>
+__device__ __forceinline__ void store_tile(const float2* s_h, float2* __restrict__ inter, int r, int hp, int LP,
+                                           int pl0, int nplanes) {
+  for (int idx = threadIdx.x; idx < (P / 2 + 1) * RP; idx += blockDim.x) {
+    const int kk = idx / RP, pl = idx - kk * RP;
+    if (pl0 + pl < nplanes) inter[((size_t)r * hp + kk) * LP + pl0 + pl] = s_h[kk * SH_LD + pl];
+  }
+}
 
 template <int P>
-__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_fwd(const float* __restrict__ in, int total_rows,
+__device__ __forceinline__ void load_tile(float2* s_h, const float2* __restrict__ inter, int r, int hp, int LP,
+                                          int pl0, int nplanes) {
+  for (int idx = threadIdx.x; idx < (P / 2 + 1) * RP; idx += blockDim.x) {
+    const int kk = idx / RP, pl = idx - kk * RP;
+    s_h[kk * SH_LD + pl] =
+        pl0 + pl < nplanes ? inter[((size_t)r * hp + kk) * LP + pl0 + pl] : make_float2(0.f, 0.f);
+  }
+}
+
+// Forward R2C of rows: in[plane][row][ld_in] (first cols_in columns, zero beyond)
+// -> inter[row][kx][LP].
+template <int P>
+__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_fwd(const float* __restrict__ in, int nplanes, int rows,
                                                              int cols_in, int ld_in, float2* __restrict__ inter,
                                                              int hp, const float2* __restrict__ tw) {
   constexpr int R = P / 32;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
+  float2* s_h = smem + tw_count(P);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* buf = smem + tw_count(P) + warp * (P + 2);
+  float2* buf = s_h + (P / 2 + 1) * SH_LD + warp * (P + 2);
   stage_twiddles<P>(s_tw, tw);
   __syncthreads();
-  const int npairs = (total_rows + 1) >> 1;
-  for (int pair = blockIdx.x * ROW_WARPS + warp; pair < npairs; pair += gridDim.x * ROW_WARPS) {
-    const int g0 = 2 * pair, g1 = g0 + 1;
-    const bool has1 = g1 < total_rows;
-    const float* r0 = in + (size_t)g0 * ld_in;
-    const float* r1 = in + (size_t)g1 * ld_in;
+  const int LP = plane_ld(nplanes), nblk = LP / RP;
+  for (int job = blockIdx.x; job < rows * nblk; job += gridDim.x) {
+    const int r = job / nblk, pl0 = (job - r * nblk) * RP;
+    const int p0 = pl0 + 2 * warp, p1 = p0 + 1;
+    const float* r0 = in + ((size_t)p0 * rows + r) * ld_in;
+    const float* r1 = in + ((size_t)p1 * rows + r) * ld_in;
     float2 v[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int n = lane + 32 * i;
-      const float a = n < cols_in ? r0[n] : 0.f;
-      const float b = (has1 && n < cols_in) ? r1[n] : 0.f;
+      const float a = (p0 < nplanes && n < cols_in) ? r0[n] : 0.f;
+      const float b = (p1 < nplanes && n < cols_in) ? r1[n] : 0.f;
       v[i] = make_float2(a, b);
     }
     warp_fft<P, false>(v, lane, s_tw);
 #pragma unroll
     for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
     __syncwarp();
-    split_write<P>(buf, lane, inter + (size_t)g0 * hp, has1 ? inter + (size_t)g1 * hp : nullptr);
-    __syncwarp();
+    split_to_tile<P>(buf, lane, s_h, 2 * warp);
+    __syncthreads();
+    store_tile<P>(s_h, inter, r, hp, LP, pl0, nplanes);
+    __syncthreads();
   }
 }
 
+// Inverse C2R of rows: inter[row][kx][LP] -> out[plane][row][ld_out] (first cols_out columns), x scale.
 template <int P>
-__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const float2* __restrict__ inter, int total_rows,
-                                                             int hp, int cols_out, float* __restrict__ out,
+__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const float2* __restrict__ inter, int nplanes,
+                                                             int rows, int hp, int cols_out, float* __restrict__ out,
                                                              int ld_out, float scale,
                                                              const float2* __restrict__ tw) {
   constexpr int R = P / 32;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
+  float2* s_h = smem + tw_count(P);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* buf = smem + tw_count(P) + warp * (P + 2);
+  float2* buf = s_h + (P / 2 + 1) * SH_LD + warp * (P + 2);
   stage_twiddles<P>(s_tw, tw);
-  __syncthreads();
-  const int npairs = (total_rows + 1) >> 1;
-  for (int pair = blockIdx.x * ROW_WARPS + warp; pair < npairs; pair += gridDim.x * ROW_WARPS) {
-    const int g0 = 2 * pair, g1 = g0 + 1;
-    const bool has1 = g1 < total_rows;
-    float2* ba = buf;
-    float2* bb = buf + (P / 2 + 1);
-    for (int kk = lane; kk <= P / 2; kk += 32) {
-      ba[kk] = inter[(size_t)g0 * hp + kk];
-      bb[kk] = has1 ? inter[(size_t)g1 * hp + kk] : make_float2(0.f, 0.f);
-    }
-    __syncwarp();
+  const int LP = plane_ld(nplanes), nblk = LP / RP;
+  for (int job = blockIdx.x; job < rows * nblk; job += gridDim.x) {
+    const int r = job / nblk, pl0 = (job - r * nblk) * RP;
+    const int p0 = pl0 + 2 * warp, p1 = p0 + 1;
+    load_tile<P>(s_h, inter, r, hp, LP, pl0, nplanes);
+    __syncthreads();
     float2 v[R];
-    load_pair_spectrum<P>(v, ba, bb, lane);
-    __syncwarp();
+    load_pair_from_tile<P>(v, s_h, 2 * warp, lane);
     warp_fft<P, true>(v, lane, s_tw);
 #pragma unroll
     for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
     __syncwarp();
     for (int c = lane; c < cols_out; c += 32) {
       const float2 z = buf[sw_pos<P>(c)];
-      out[(size_t)g0 * ld_out + c] = z.x * scale;
-      if (has1) out[(size_t)g1 * ld_out + c] = z.y * scale;
+      if (p0 < nplanes) out[((size_t)p0 * rows + r) * ld_out + c] = z.x * scale;
+      if (p1 < nplanes) out[((size_t)p1 * rows + r) * ld_out + c] = z.y * scale;
     }
-    __syncwarp();
+    __syncthreads();
   }
 }
 
-// ADMM T side, per pair of measurement rows (time bin t, scan row y):
+// ADMM T side, per measurement row y and pair of time bins t:
 //   Kx   = C2R(row spectra) on the N scan columns
 //   a1   = Kx + u1;  v1 = (m/scale + rho a1) / (1 + rho);  u1 <- a1 - v1
 //   c    = (v1 - u1) - Kx = 2 v1 - a1 - Kx      (zero off the scan)
 //   row spectra <- R2C(c zero-padded to P)
 // so that FFT(v1 - u1) = K x_hat + c_hat without a transform of the full
-// P x P plane.
+// P x P plane.  m, u1: [nt][n][n]; inter: [n][kx][LP] in place.
 template <int P>
-__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restrict__ inter, int total_rows,
-                                                                int hp, int n, const float* __restrict__ m,
-                                                                float* __restrict__ u1, float scale,
-                                                                float inv_s, float rho,
-                                                                const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restrict__ inter, int nplanes, int n,
+                                                                int hp, const float* __restrict__ m,
+                                                                float* __restrict__ u1, float scale, float inv_s,
+                                                                float rho, const float2* __restrict__ tw) {
   constexpr int R = P / 32;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
+  float2* s_h = smem + tw_count(P);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* buf = smem + tw_count(P) + warp * (P + 2);
+  float2* buf = s_h + (P / 2 + 1) * SH_LD + warp * (P + 2);
   stage_twiddles<P>(s_tw, tw);
-  __syncthreads();
   const float inv1r = 1.0f / (1.0f + rho);
-  const int npairs = (total_rows + 1) >> 1;
-  for (int pair = blockIdx.x * ROW_WARPS + warp; pair < npairs; pair += gridDim.x * ROW_WARPS) {
-    const int g0 = 2 * pair, g1 = g0 + 1;
-    const bool has1 = g1 < total_rows;
-    float2* ba = buf;
-    float2* bb = buf + (P / 2 + 1);
-    for (int kk = lane; kk <= P / 2; kk += 32) {
-      ba[kk] = inter[(size_t)g0 * hp + kk];
-      bb[kk] = has1 ? inter[(size_t)g1 * hp + kk] : make_float2(0.f, 0.f);
-    }
-    __syncwarp();
+  const int LP = plane_ld(nplanes), nblk = LP / RP;
+  for (int job = blockIdx.x; job < n * nblk; job += gridDim.x) {
+    const int r = job / nblk, pl0 = (job - r * nblk) * RP;
+    const int p0 = pl0 + 2 * warp, p1 = p0 + 1;
+    const bool has0 = p0 < nplanes, has1 = p1 < nplanes;
+    load_tile<P>(s_h, inter, r, hp, LP, pl0, nplanes);
+    __syncthreads();
     float2 v[R];
-    load_pair_spectrum<P>(v, ba, bb, lane);
-    __syncwarp();
+    load_pair_from_tile<P>(v, s_h, 2 * warp, lane);
     warp_fft<P, true>(v, lane, s_tw);
 #pragma unroll
     for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
@@ -278,15 +301,15 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restri
       float2 cc = make_float2(0.f, 0.f);
       if (c < n) {
         const float2 kx = cscale(buf[sw_pos<P>(c)], scale);
-        {
-          const size_t idx = (size_t)g0 * n + c;
+        if (has0) {
+          const size_t idx = ((size_t)p0 * n + r) * n + c;
           const float a1 = kx.x + u1[idx];
           const float v1 = (m[idx] * inv_s + rho * a1) * inv1r;
           u1[idx] = a1 - v1;
           cc.x = 2.f * v1 - a1 - kx.x;
         }
         if (has1) {
-          const size_t idx = (size_t)g1 * n + c;
+          const size_t idx = ((size_t)p1 * n + r) * n + c;
           const float a1 = kx.y + u1[idx];
           const float v1 = (m[idx] * inv_s + rho * a1) * inv1r;
           u1[idx] = a1 - v1;
@@ -300,13 +323,17 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restri
 #pragma unroll
     for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
     __syncwarp();
-    split_write<P>(buf, lane, inter + (size_t)g0 * hp, has1 ? inter + (size_t)g1 * hp : nullptr);
-    __syncwarp();
+    __syncthreads();  // every warp is done reading s_h
+    split_to_tile<P>(buf, lane, s_h, 2 * warp);
+    __syncthreads();
+    store_tile<P>(s_h, inter, r, hp, LP, pl0, nplanes);
+    __syncthreads();
   }
 }
 
 // ------------------------------------------------------------- columns ----
 
+// Forward C2C along y: inter[row][kx][LP] (rows_in rows, zero beyond) -> out[ky h + kx][ldf].
 template <int P, int PB>
 __global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restrict__ inter, int nplanes,
                                                           int rows_in, int h, int hp,
@@ -319,14 +346,14 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restri
   float2* s_tw = smem;
   float2* tile = smem + tw_count(P);
   const int kx0 = blockIdx.x * KB, pl0 = blockIdx.y * PB;
+  const int LP = plane_ld(nplanes);
   stage_twiddles<P>(s_tw, tw);
   for (int idx = threadIdx.x; idx < rows_in * NC; idx += COL_THREADS) {
     const int row = idx / NC, cc = idx % NC;
-    const int kxl = cc % KB, pll = cc / KB;
-    const int kx = kx0 + kxl, pl = pl0 + pll;
+    const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
     float2 val = make_float2(0.f, 0.f);
-    if (kx < h && pl < nplanes) val = inter[((size_t)pl * rows_in + row) * hp + kx];
-    tile[row * LDT + kxl * PB + pll] = val;
+    if (kx < h && pl < nplanes) val = inter[((size_t)row * hp + kx) * LP + pl];
+    tile[row * LDT + cc] = val;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -344,12 +371,12 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restri
   __syncthreads();
   for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
     const int ky = idx / NC, cc = idx % NC;
-    const int pll = cc % PB, kxl = cc / PB;
-    const int kx = kx0 + kxl, pl = pl0 + pll;
+    const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
     if (kx < h && pl < nplanes) out[((size_t)ky * h + kx) * ldf + pl] = tile[sw_pos<P>(ky) * LDT + cc];
   }
 }
 
+// Inverse C2C along y: in[ky h + kx][ldf] -> inter[row][kx][LP] for the first rows_out rows.
 template <int P, int PB>
 __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restrict__ in, int ldf, int nplanes,
                                                           int rows_out, int h, int hp,
@@ -362,11 +389,11 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restri
   float2* s_tw = smem;
   float2* tile = smem + tw_count(P);
   const int kx0 = blockIdx.x * KB, pl0 = blockIdx.y * PB;
+  const int LP = plane_ld(nplanes);
   stage_twiddles<P>(s_tw, tw);
   for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
     const int ky = idx / NC, cc = idx % NC;
-    const int pll = cc % PB, kxl = cc / PB;
-    const int kx = kx0 + kxl, pl = pl0 + pll;
+    const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
     float2 val = make_float2(0.f, 0.f);
     if (kx < h && pl < nplanes) val = in[((size_t)ky * h + kx) * ldf + pl];
     tile[ky * LDT + cc] = val;
@@ -387,16 +414,16 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restri
   __syncthreads();
   for (int idx = threadIdx.x; idx < rows_out * NC; idx += COL_THREADS) {
     const int row = idx / NC, cc = idx % NC;
-    const int kxl = cc % KB, pll = cc / KB;
-    const int kx = kx0 + kxl, pl = pl0 + pll;
-    if (kx < h && pl < nplanes)
-      inter[((size_t)pl * rows_out + row) * hp + kx] = tile[sw_pos<P>(row) * LDT + kxl * PB + pll];
+    const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
+    if (kx < h && pl < nplanes) inter[((size_t)row * hp + kx) * LP + pl] = tile[sw_pos<P>(row) * LDT + cc];
   }
 }
 
 // ------------------------------------------------------------ launchers ----
 
-size_t row_smem(int p) { return (size_t)(tw_count(p) + ROW_WARPS * (p + 2)) * sizeof(float2); }
+size_t row_smem(int p) {
+  return (size_t)(tw_count(p) + (p / 2 + 1) * SH_LD + ROW_WARPS * (p + 2)) * sizeof(float2);
+}
 size_t col_smem(int p) { return (size_t)(tw_count(p) + p * (NC + 1)) * sizeof(float2); }
 
 template <typename F>
@@ -404,11 +431,10 @@ cudaError_t allow_smem(F* fn, size_t bytes) {
   return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-int row_grid(int total_rows) {
-  const int npairs = (total_rows + 1) / 2;
-  int g = (npairs + ROW_WARPS - 1) / ROW_WARPS;
+int row_grid(int rows, int nplanes) {
+  const int jobs = rows * (plane_ld(nplanes) / RP);
   const int cap = 152 * 8;
-  return g < 1 ? 1 : (g > cap ? cap : g);
+  return jobs < 1 ? 1 : (jobs > cap ? cap : jobs);
 }
 
 #define CTOF_P_SWITCH(p, ...)                                    \
@@ -424,12 +450,12 @@ int row_grid(int total_rows) {
 
 ctof_status fft_rows_forward(const ctof_kernel_s* k, const float* in, int nplanes, int rows, int cols_in,
                              int ld_in, float2* inter, cudaStream_t st) {
-  const int total = nplanes * rows;
-  if (total <= 0) return CTOF_OK;
+  if (nplanes <= 0 || rows <= 0) return CTOF_OK;
   const size_t sm = row_smem(k->p);
   CTOF_P_SWITCH(k->p, {
     CTOF_CUDA_TRY(allow_smem(k_rows_fwd<P_>, sm));
-    k_rows_fwd<P_><<<row_grid(total), ROW_WARPS * 32, sm, st>>>(in, total, cols_in, ld_in, inter, k->hp, k->d_tw);
+    k_rows_fwd<P_><<<row_grid(rows, nplanes), ROW_WARPS * 32, sm, st>>>(in, nplanes, rows, cols_in, ld_in, inter,
+                                                                         k->hp, k->d_tw);
   });
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
@@ -437,14 +463,13 @@ ctof_status fft_rows_forward(const ctof_kernel_s* k, const float* in, int nplane
 
 ctof_status fft_rows_inverse(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows, int cols_out,
                              float* out, int ld_out, cudaStream_t st) {
-  const int total = nplanes * rows;
-  if (total <= 0) return CTOF_OK;
+  if (nplanes <= 0 || rows <= 0) return CTOF_OK;
   const size_t sm = row_smem(k->p);
   const float scale = 1.0f / ((float)k->p * (float)k->p);
   CTOF_P_SWITCH(k->p, {
     CTOF_CUDA_TRY(allow_smem(k_rows_inv<P_>, sm));
-    k_rows_inv<P_><<<row_grid(total), ROW_WARPS * 32, sm, st>>>(inter, total, k->hp, cols_out, out, ld_out, scale,
-                                                                 k->d_tw);
+    k_rows_inv<P_><<<row_grid(rows, nplanes), ROW_WARPS * 32, sm, st>>>(inter, nplanes, rows, k->hp, cols_out, out,
+                                                                         ld_out, scale, k->d_tw);
   });
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
@@ -452,13 +477,12 @@ ctof_status fft_rows_inverse(const ctof_kernel_s* k, const float2* inter, int np
 
 ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* m, float* u1, float inv_scale,
                             float rho, cudaStream_t st) {
-  const int total = k->nt * k->n;
   const size_t sm = row_smem(k->p);
   const float scale = 1.0f / ((float)k->p * (float)k->p);
   CTOF_P_SWITCH(k->p, {
     CTOF_CUDA_TRY(allow_smem(k_rows_admm_t<P_>, sm));
-    k_rows_admm_t<P_><<<row_grid(total), ROW_WARPS * 32, sm, st>>>(inter, total, k->hp, k->n, m, u1, scale,
-                                                                    inv_scale, rho, k->d_tw);
+    k_rows_admm_t<P_><<<row_grid(k->n, k->nt), ROW_WARPS * 32, sm, st>>>(inter, k->nt, k->n, k->hp, m, u1, scale,
+                                                                          inv_scale, rho, k->d_tw);
   });
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
@@ -470,10 +494,10 @@ ctof_status fft_cols_forward_pb(const ctof_kernel_s* k, const float2* inter, int
   const size_t sm = col_smem(k->p);
   dim3 grid(ctof_div_up(k->h, NC / pb), ctof_div_up(nplanes, pb));
   switch (pb) {
-    case 4:
+    case 32:
       CTOF_P_SWITCH(k->p, {
-        CTOF_CUDA_TRY(allow_smem(k_cols_fwd<P_, 4>, sm));
-        k_cols_fwd<P_, 4><<<grid, COL_THREADS, sm, st>>>(inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
+        CTOF_CUDA_TRY(allow_smem(k_cols_fwd<P_, 32>, sm));
+        k_cols_fwd<P_, 32><<<grid, COL_THREADS, sm, st>>>(inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
       });
       break;
     case 16:
@@ -504,10 +528,10 @@ ctof_status fft_cols_inverse_pb(const ctof_kernel_s* k, const float2* in, int ld
   const size_t sm = col_smem(k->p);
   dim3 grid(ctof_div_up(k->h, NC / pb), ctof_div_up(nplanes, pb));
   switch (pb) {
-    case 4:
+    case 32:
       CTOF_P_SWITCH(k->p, {
-        CTOF_CUDA_TRY(allow_smem(k_cols_inv<P_, 4>, sm));
-        k_cols_inv<P_, 4><<<grid, COL_THREADS, sm, st>>>(in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
+        CTOF_CUDA_TRY(allow_smem(k_cols_inv<P_, 32>, sm));
+        k_cols_inv<P_, 32><<<grid, COL_THREADS, sm, st>>>(in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
       });
       break;
     case 16:
@@ -530,6 +554,10 @@ ctof_status fft_cols_inverse(const ctof_kernel_s* k, const float2* in, int ldf, 
                              float2* inter, cudaStream_t st) {
   const int pb = (nplanes == k->nt) ? k->tune_pb[1] : k->tune_pb[3];
   return fft_cols_inverse_pb(k, in, ldf, nplanes, rows_out, inter, pb, st);
+}
+
+size_t fft_inter_elems(const ctof_kernel_s* k, int nplanes, int rows) {
+  return (size_t)rows * k->hp * plane_ld(nplanes);
 }
 
 ctof_status fft_forward_planes(const ctof_kernel_s* k, const float* in, int nplanes, int rows_in, int cols_in,

@@ -55,10 +55,10 @@ size_t align256(size_t b) { return (b + 255) & ~(size_t)255; }
 extern "C" ctof_status ctof_forward_static(ctof_kernel k, const float* d_mu, float* d_m, void* stream) {
   if (!k || !d_mu || !d_m) return CTOF_EINVAL;
   // scratch: Z-side row spectra, Z-side spectrum, T-side spectrum, T-side row spectra
-  const size_t b_iz = align256((size_t)k->nz * k->n * k->hp * sizeof(float2));
+  const size_t b_iz = align256(fft_inter_elems(k, k->nz, k->n) * sizeof(float2));
   const size_t b_sz = align256((size_t)k->nf * k->ldz * sizeof(float2));
   const size_t b_st = align256((size_t)k->nf * k->ldt * sizeof(float2));
-  const size_t b_it = align256((size_t)k->nt * k->n * k->hp * sizeof(float2));
+  const size_t b_it = align256(fft_inter_elems(k, k->nt, k->n) * sizeof(float2));
   const size_t need = b_iz + b_sz + b_st + b_it;
   if (need > CTOF_STATIC_SCRATCH_BYTES) {
     char msg[256];
