@@ -58,6 +58,7 @@ __device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], 
 
 struct BtLayout {
   int nt, nz, z4, zs, tk;  // tk = nt rounded up to 16 (K extent)
+  int cs;                  // shared row pitch of C and G + lambda I: 4 (z4/4 | 1) floats
   int batch;
   // byte offsets in shared memory
   int off_qh, off_ql, off_mh, off_ml, off_c, off_g, off_b0, off_bf, off_x;
@@ -79,6 +80,21 @@ __device__ __forceinline__ int m_off(const BtLayout& L, int n, int chunk) {
   return (n * L.tk + (cc << 3)) * 2;
 }
 
+// sum_w row[w] v[w][nq .. nq+3] for v [.][NB] (FP32)
+__device__ __forceinline__ float4 small_mv(const float* __restrict__ row, const float* __restrict__ v, int nz, int nq) {
+  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll 4
+  for (int w = 0; w < nz; ++w) {
+    const float c = row[w];
+    const float4 b = *reinterpret_cast<const float4*>(v + w * NB + nq);
+    a.x = fmaf(c, b.x, a.x);
+    a.y = fmaf(c, b.y, a.y);
+    a.z = fmaf(c, b.z, a.z);
+    a.w = fmaf(c, b.w, a.w);
+  }
+  return a;
+}
+
 __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_tikhonov_bf16(
     BtLayout L, const __nv_bfloat16* __restrict__ qhi, const __nv_bfloat16* __restrict__ qlo,
     const float* __restrict__ cinv, const float* __restrict__ glam, const int* __restrict__ members, int nclass,
@@ -87,8 +103,8 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_tikhonov_bf16(
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int g = lane >> 2, tg = lane & 3;
   const int nt = L.nt, nz = L.nz, zs = L.zs, tk = L.tk;
-  float* s_c = reinterpret_cast<float*>(smb + L.off_c);    // [nz][z4]
-  float* s_g = reinterpret_cast<float*>(smb + L.off_g);    // [nz][z4]
+  float* s_c = reinterpret_cast<float*>(smb + L.off_c);    // [nz][cs]
+  float* s_g = reinterpret_cast<float*>(smb + L.off_g);    // [nz][cs]
   float* s_b0 = reinterpret_cast<float*>(smb + L.off_b0);  // [zs][NB]
   float* s_bf = reinterpret_cast<float*>(smb + L.off_bf);  // [zs][NB]
   float* s_x = reinterpret_cast<float*>(smb + L.off_x);    // [zs][NB]
@@ -114,8 +130,8 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_tikhonov_bf16(
       const int cq = L.z4 >> 2;
       for (int i = tid; i < nz * cq; i += BT_THREADS) {
         const int r = i / cq, ch = i - r * cq;
-        cp_async16(s_c + r * L.z4 + ch * 4, cinv + ((size_t)c * nz + r) * L.z4 + ch * 4);
-        cp_async16(s_g + r * L.z4 + ch * 4, glam + ((size_t)c * nz + r) * L.z4 + ch * 4);
+        cp_async16(s_c + r * L.cs + ch * 4, cinv + ((size_t)c * nz + r) * L.z4 + ch * 4);
+        cp_async16(s_g + r * L.cs + ch * 4, glam + ((size_t)c * nz + r) * L.z4 + ch * 4);
       }
       cp_async_commit();
       cp_async_wait_all();
@@ -198,36 +214,30 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_tikhonov_bf16(
       }
       __syncthreads();
       // ---- x0 = C b0, then x += C (b - (G + lambda I) x) ----
-      for (int i = tid; i < nz * NB; i += BT_THREADS) {
-        const int z = i / NB, n = i - z * NB;
-        float acc = 0.f;
-        for (int w = 0; w < nz; ++w) acc += s_c[z * L.z4 + w] * s_b0[w * NB + n];
-        s_x[z * NB + n] = acc;
+      // Each thread owns one depth z and four right-hand sides: four independent
+      // accumulators per row walk, rows of C and G at a pitch that puts the
+      // eight depths of a warp on distinct banks.
+      const int zq = tid >> 2, nq = (tid & 3) * 4;
+      const bool own = zq < nz && tid < 4 * nz;
+      if (own) {
+        const float4 y = small_mv(s_c + zq * L.cs, s_b0, nz, nq);
+        *reinterpret_cast<float4*>(s_x + zq * NB + nq) = y;
       }
       __syncthreads();
       for (int it = 0; it < refine; ++it) {
-        float rr[(64 * NB + BT_THREADS - 1) / BT_THREADS];
-        int cnt = 0;
-        for (int i = tid; i < nz * NB; i += BT_THREADS, ++cnt) {
-          const int z = i / NB, n = i - z * NB;
-          float acc = s_bf[z * NB + n];
-          for (int w = 0; w < nz; ++w) acc -= s_g[z * L.z4 + w] * s_x[w * NB + n];
-          rr[cnt] = acc;
+        if (own) {  // residual r = b - (G + lambda I) x into s_b0
+          const float4 gx = small_mv(s_g + zq * L.cs, s_x, nz, nq);
+          const float4 bf = *reinterpret_cast<const float4*>(s_bf + zq * NB + nq);
+          *reinterpret_cast<float4*>(s_b0 + zq * NB + nq) =
+              make_float4(bf.x - gx.x, bf.y - gx.y, bf.z - gx.z, bf.w - gx.w);
         }
         __syncthreads();
-        cnt = 0;
-        for (int i = tid; i < nz * NB; i += BT_THREADS, ++cnt) s_b0[i] = rr[cnt];  // reuse b0 as residual
-        __syncthreads();
-        cnt = 0;
-        for (int i = tid; i < nz * NB; i += BT_THREADS, ++cnt) {
-          const int z = i / NB, n = i - z * NB;
-          float acc = 0.f;
-          for (int w = 0; w < nz; ++w) acc += s_c[z * L.z4 + w] * s_b0[w * NB + n];
-          rr[cnt] = s_x[z * NB + n] + acc;
+        if (own) {  // x += C r (each thread updates only its own entries)
+          const float4 cr = small_mv(s_c + zq * L.cs, s_b0, nz, nq);
+          float4* xp = reinterpret_cast<float4*>(s_x + zq * NB + nq);
+          const float4 x = *xp;
+          *xp = make_float4(x.x + cr.x, x.y + cr.y, x.z + cr.z, x.w + cr.w);
         }
-        __syncthreads();
-        cnt = 0;
-        for (int i = tid; i < nz * NB; i += BT_THREADS, ++cnt) s_x[i] = rr[cnt];
         __syncthreads();
       }
       // ---- x_hat[f][b*nz + z] ----
@@ -316,6 +326,7 @@ BtLayout make_layout(int nt, int nz, int batch) {
   L.z4 = (nz + 3) & ~3;
   L.zs = nz <= 16 ? 16 : (nz <= 32 ? 32 : 64);
   L.tk = (nt + 15) & ~15;
+  L.cs = 4 * ((L.z4 / 4) | 1);
   L.batch = batch;
   int off = 0;
   auto take = [&](int bytes) {
@@ -327,8 +338,8 @@ BtLayout make_layout(int nt, int nz, int batch) {
   L.off_ql = take(L.tk * L.zs * 2);
   L.off_mh = take(NB * L.tk * 2);
   L.off_ml = take(NB * L.tk * 2);
-  L.off_c = take(nz * L.z4 * 4);
-  L.off_g = take(nz * L.z4 * 4);
+  L.off_c = take(nz * L.cs * 4);
+  L.off_g = take(nz * L.cs * 4);
   L.off_b0 = take(L.zs * NB * 4);
   L.off_bf = take(L.zs * NB * 4);
   L.off_x = take(L.zs * NB * 4);
