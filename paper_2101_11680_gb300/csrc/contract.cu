@@ -108,13 +108,16 @@ __device__ __forceinline__ void issue_v(const Plan& P, char* vst, const int* __r
   float2* sV = reinterpret_cast<float2*>(vst);
   const int rows = MODE == MODE_FWD ? P.z4 : P.nt;
   const int valid = MODE == MODE_FWD ? P.nz : P.nt;
-  for (int i = threadIdx.x; i < 4 * rows; i += blockDim.x) {
-    const int m = i / rows, r = i - m * rows;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
     const int f = members[c * 4 + m];
-    if (f >= 0 && r < valid)
-      cp_async8(sV + r * 4 + m, vin + (size_t)f * ld_in + r);
-    else
-      sV[r * 4 + m] = make_float2(0.f, 0.f);
+    const float2* src = vin + (size_t)(f < 0 ? 0 : f) * ld_in;
+    for (int r = threadIdx.x; r < rows; r += blockDim.x) {
+      if (f >= 0 && r < valid)
+        cp_async8(sV + r * 4 + m, src + r);
+      else
+        sV[r * 4 + m] = make_float2(0.f, 0.f);
+    }
   }
 }
 
@@ -181,20 +184,22 @@ __device__ __forceinline__ void compute_adj_partials(const Plan& P, const float*
 }
 
 // Steps s = 0, 1, ... of a CTA are (class blockIdx.x + (s / nvol) * gridDim.x,
-// volume s % nvol).  With nbuf == 2 the copies of step s + nvs - 1 are issued
-// while step s computes (one commit group per step; a class's W_hat block goes
-// with the vectors of its first volume, at most one class ahead since
-// nvs <= nvol + 1).  With nbuf == 1 nothing overlaps.
+// volume s % nvol).  The member vectors of step s + nvs - 1 are issued while
+// step s computes (one commit group per step).  With two W stages (nbw == 2)
+// a class's W_hat block goes with the vectors of its first volume, at most one
+// class ahead since nvs <= nvol + 1.  With one W stage (nbw == 1; used when
+// many volumes share a class, so that two CTAs fit on an SM) the block is
+// loaded when its class starts.  With nvs == 1 nothing overlaps.
 template <int MODE>
 __device__ __forceinline__ void issue_step(const Plan& P, char* smem, int (*s_mem)[4], const float* __restrict__ what,
                                            const int* __restrict__ members, const float2* __restrict__ vin,
                                            int ld_in, size_t in_vstride, const float* __restrict__ hinv,
-                                           int nclass, int nvol, int nbuf, int nvs, int s) {
+                                           int nclass, int nvol, int nbw, int nvs, int s, bool with_w) {
   const int ci = s / nvol, b = s - ci * nvol;
   const int c = blockIdx.x + ci * gridDim.x;
   if (c >= nclass) return;
-  const int wb = nbuf == 2 ? (ci & 1) : 0;
-  if (b == 0) issue_w<MODE>(P, smem + wb * P.wst, s_mem[wb], what, members, hinv, c);
+  const int wb = nbw == 2 ? (ci & 1) : 0;
+  if (b == 0 && with_w) issue_w<MODE>(P, smem + wb * P.wst, s_mem[wb], what, members, hinv, c);
   issue_v<MODE>(P, smem + P.off_v + (s % nvs) * P.vst, members, vin + (size_t)b * in_vstride, ld_in, c);
 }
 
@@ -203,37 +208,45 @@ __global__ void __launch_bounds__(CT_THREADS) k_contract(const float* __restrict
                                                          const int* __restrict__ members, int nclass, int nt, int nz,
                                                          const float2* __restrict__ vin, int ld_in, size_t in_vstride,
                                                          float2* __restrict__ vout, int ld_out, size_t out_vstride,
-                                                         int nvol, const float* __restrict__ hinv, int nbuf, int nvs) {
+                                                         int nvol, const float* __restrict__ hinv, int nbw, int nvs) {
   extern __shared__ __align__(16) char smem[];
   __shared__ int s_mem[2][4];
-  const Plan P = make_plan(MODE, nt, nz, nbuf, nvs, blockDim.x);
+  const Plan P = make_plan(MODE, nt, nz, nbw, nvs, blockDim.x);
   float* part = reinterpret_cast<float*>(smem + P.off_part);
   float* sB = reinterpret_cast<float*>(smem + P.off_b);
   const int G = gridDim.x;
   const int my_classes = blockIdx.x < nclass ? (nclass - 1 - blockIdx.x) / G + 1 : 0;
   const int nsteps = my_classes * nvol;
-  const int ahead = nbuf == 2 ? nvs - 1 : 0;
+  const int ahead = nvs - 1;
   for (int s = 0; s < (ahead > 0 ? ahead : 1); ++s) {
     if (s < nsteps)
-      issue_step<MODE>(P, smem, s_mem, what, members, vin, ld_in, in_vstride, hinv, nclass, nvol, nbuf, nvs, s);
+      issue_step<MODE>(P, smem, s_mem, what, members, vin, ld_in, in_vstride, hinv, nclass, nvol, nbw, nvs, s,
+                       nbw == 2 || s == 0);
     cp_commit();
   }
   for (int s = 0; s < nsteps; ++s) {
     const int ci = s / nvol, b = s - ci * nvol;
-    const int wcur = nbuf == 2 ? (ci & 1) : 0;
+    const int wcur = nbw == 2 ? (ci & 1) : 0;
     const int vcur = s % nvs;
-    if (nbuf == 2) {
+    const bool w_now = nbw == 1 && ahead > 0 && b == 0 && s > 0;  // one W stage: load this class now
+    if (w_now) issue_w<MODE>(P, smem, s_mem[0], what, members, hinv, blockIdx.x + ci * G);
+    if (ahead > 0) {
       if (s + ahead < nsteps)
-        issue_step<MODE>(P, smem, s_mem, what, members, vin, ld_in, in_vstride, hinv, nclass, nvol, nbuf, nvs,
-                         s + ahead);
+        issue_step<MODE>(P, smem, s_mem, what, members, vin, ld_in, in_vstride, hinv, nclass, nvol, nbw, nvs,
+                         s + ahead, nbw == 2);
       cp_commit();
       // all groups but the newest `ahead` are complete: those hold steps s+1 .. s+ahead
-      switch (ahead) {
-        case 1: cp_wait<1>(); break;
-        case 2: cp_wait<2>(); break;
-        default: cp_wait<3>(); break;
+      if (w_now) {
+        cp_wait<0>();
+      } else {
+        switch (ahead) {
+          case 1: cp_wait<1>(); break;
+          case 2: cp_wait<2>(); break;
+          default: cp_wait<3>(); break;
+        }
       }
     } else {
+      cp_commit();
       cp_wait<0>();
     }
     __syncthreads();
@@ -282,10 +295,9 @@ __global__ void __launch_bounds__(CT_THREADS) k_contract(const float* __restrict
       }
     }
     __syncthreads();
-    if (nbuf == 1 && s + 1 < nsteps) {
-      issue_step<MODE>(P, smem, s_mem, what, members, vin, ld_in, in_vstride, hinv, nclass, nvol, nbuf, nvs, s + 1);
-      cp_commit();
-    }
+    if (ahead == 0 && s + 1 < nsteps)
+      issue_step<MODE>(P, smem, s_mem, what, members, vin, ld_in, in_vstride, hinv, nclass, nvol, nbw, nvs, s + 1,
+                       true);
   }
   cp_wait<0>();
 }
@@ -296,13 +308,20 @@ template <int MODE>
 ctof_status launch(const ctof_kernel_s* k, int nvol, const float2* vin, int ld_in, size_t in_vstride, float2* vout,
                    int ld_out, size_t out_vstride, const float* hinv, cudaStream_t st) {
   if (nvol < 1) return CTOF_EINVAL;
-  // deepest vector pipeline that fits (at most one class ahead: nvs <= nvol + 1), else no overlap
+  // Many volumes per class: one W stage and a deep vector ring (the block is
+  // reused nvol times, and the smaller footprint lets two CTAs share an SM).
+  // Few volumes: the deepest vector pipeline with two W stages that fits.
+  // Otherwise no overlap.
   int nbuf = 1, nvs = 1;
-  for (int v = (nvol + 1 < 4 ? nvol + 1 : 4); v >= 2; --v) {
-    if (make_plan(MODE, k->nt, k->nz, 2, v, CT_THREADS).total <= SMEM_LIMIT) {
-      nbuf = 2;
-      nvs = v;
-      break;
+  if (nvol >= 4 && make_plan(MODE, k->nt, k->nz, 1, 4, CT_THREADS).total <= SMEM_LIMIT) {
+    nvs = 4;
+  } else {
+    for (int v = (nvol + 1 < 4 ? nvol + 1 : 4); v >= 2; --v) {
+      if (make_plan(MODE, k->nt, k->nz, 2, v, CT_THREADS).total <= SMEM_LIMIT) {
+        nbuf = 2;
+        nvs = v;
+        break;
+      }
     }
   }
   const Plan p = make_plan(MODE, k->nt, k->nz, nbuf, nvs, CT_THREADS);
