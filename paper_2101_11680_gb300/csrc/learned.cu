@@ -74,7 +74,7 @@ __device__ __forceinline__ long long neighbour(const Geo& G, int bb, int zz, int
 // voxel's 32-byte channel vector swap places on bit 2 of the voxel index, so
 // the eight rows of every ldmatrix land in distinct bank groups.
 //   out[v][co] = bias[co] + sum_tap sum_ci W[tap][co][ci] act(in[v + off(tap)][ci])
-// act = ReLU if relu_in; out *= (mask[v][co] > 0) if mask.  IN_F32: the input
+// act = ReLU if relu_in (applied once to the staged tile); out *= (mask[v][co] > 0) if mask.  IN_F32: the input
 // is one FP32 channel `in_f` scaled by in_scale (channel 0; the rest zero).
 // OUT_PROX: instead of `out`, x[v] = z[v] + mu0 * bf16(out[v][0]).
 constexpr int CV_TY = 8;
@@ -136,6 +136,18 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d(const __nv_bfloat16* __re
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   __syncthreads();
+  if (!IN_F32 && relu_in) {  // ReLU once per staged value instead of once per tap
+    for (int i = threadIdx.x; i < nvox * 2; i += CV_THREADS) {
+      uint4* p = reinterpret_cast<uint4*>(s_in + i * 16);
+      uint4 v = *p;
+      v.x = relu2(v.x);
+      v.y = relu2(v.y);
+      v.z = relu2(v.z);
+      v.w = relu2(v.w);
+      *p = v;
+    }
+    __syncthreads();
+  }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int g = lane >> 2, tg = lane & 3;
   const int mi = lane >> 3, lr = lane & 7;
@@ -154,14 +166,12 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d(const __nv_bfloat16* __re
     unsigned b[4];
     ldm_x4(b, s_w + tile_off(tap * CH + b_row, b_half));
     const int vrow = (dz * SY + warp + dy) * SX + dx;
+    // +16 voxels keeps bit 2 of the voxel index, so job j is 512 bytes further on
+    const char* a_base = s_in + tile_off(vrow + a_vox, a_half);
 #pragma unroll
     for (int j = 0; j < TXC; ++j) {
       unsigned a[4];
-      ldm_x4(a, s_in + tile_off(vrow + j * 16 + a_vox, a_half));
-      if (relu_in) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e) a[e] = relu2(a[e]);
-      }
+      ldm_x4(a, a_base + j * 512);
       mma_bf16(acc[j][0], a, b[0], b[1]);
       if (!OUT_PROX) mma_bf16(acc[j][1], a, b[2], b[3]);  // the last layer has one output channel
     }
