@@ -8,10 +8,12 @@
 // right-hand sides are the real/imaginary parts of the up-to-4 frequencies
 // of one class (they share the real matrix W_hat).
 //
-// The kernel streams W_hat once per iteration, so it is bound by HBM.  One
-// persistent CTA per SM (16 warps) walks the classes; while it computes class
-// i it prefetches class i+1 (W_hat block, H^-1 block and the member vectors)
-// with 16-byte cp.async copies into the second of two shared-memory buffers.
+// The kernel streams W_hat once per iteration.  Persistent CTAs of 8 warps walk
+// the classes, two per SM where their shared memory fits (one buffer each: the
+// phases of one class run between block-wide barriers, and the other CTA's
+// class fills the SM meanwhile); otherwise one CTA per SM prefetches class
+// i+1 (W_hat block, H^-1 block and the member vectors) with 16-byte cp.async
+// copies into the second of two shared-memory buffers.
 // (Per-row TMA bulk copies were measured slower here: 300+ requests of 192
 // bytes per class are limited by the TMA request rate, not by bandwidth.)
 // The two T x Z contractions run on the warp-level tensor-core MMA
@@ -30,7 +32,7 @@
 
 namespace {
 
-constexpr int AD_THREADS = 512;
+constexpr int AD_THREADS = 256;
 constexpr int AD_WARPS = AD_THREADS / 32;
 
 __device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
@@ -124,7 +126,7 @@ __device__ __forceinline__ void issue_class(const AdmmLayout& L, float* buf, int
   }
 }
 
-__global__ void __launch_bounds__(AD_THREADS, 1) k_contract_admm(
+__global__ void __launch_bounds__(AD_THREADS, 2) k_contract_admm(
     AdmmLayout L, const float* __restrict__ what, const float* __restrict__ hinv, const float* __restrict__ lap,
     const int* __restrict__ members, int nclass, const float2* __restrict__ c_hat, int ldt,
     const float2* __restrict__ s_hat, float2* __restrict__ x_hat, int ldz, float2* __restrict__ kx_hat,
@@ -320,14 +322,21 @@ size_t contract_admm_smem_bytes(int nt, int nz, int nbuf) { return (size_t)make_
 ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const float2* s_hat, float2* x_hat,
                           float2* kx_hat, float inv_scale, cudaStream_t st) {
   const size_t limit = 227 * 1024;
-  AdmmLayout L = make_layout(k->nt, k->nz, 2);
-  if ((size_t)L.total_floats * 4 > limit) L = make_layout(k->nt, k->nz, 1);
+  // Two single-buffered CTAs per SM when they fit (one computes while the
+  // other loads), else one double-buffered CTA.
+  int per_sm = 2;
+  AdmmLayout L = make_layout(k->nt, k->nz, 1);
+  if (2 * ((size_t)L.total_floats * 4 + 1024) > 228 * 1024) {
+    per_sm = 1;
+    L = make_layout(k->nt, k->nz, 2);
+    if ((size_t)L.total_floats * 4 > limit) L = make_layout(k->nt, k->nz, 1);
+  }
   if ((size_t)L.total_floats * 4 > limit) return CTOF_EUNSUPPORTED;
   const size_t sm = (size_t)L.total_floats * 4;
   CTOF_CUDA_TRY(cudaFuncSetAttribute(k_contract_admm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
-  const int grid = k->nclass < nsm ? k->nclass : nsm;
+  const int grid = k->nclass < per_sm * nsm ? k->nclass : per_sm * nsm;
   k_contract_admm<<<grid, AD_THREADS, sm, st>>>(L, k->d_what, k->d_hinv, k->d_lap, k->d_members, k->nclass, c_hat,
                                                 k->ldt, s_hat, x_hat, k->ldz, kx_hat, inv_scale);
   CTOF_CUDA_TRY(cudaGetLastError());
