@@ -310,8 +310,11 @@ ctof_status launch(const ctof_kernel_s* k, int nvol, const float2* vin, int ld_i
   if (nvol < 1) return CTOF_EINVAL;
   // Many volumes per class: one W stage and a deep vector ring (the block is
   // reused nvol times, and the smaller footprint lets two CTAs share an SM).
-  // Few volumes: the deepest vector pipeline with two W stages that fits.
-  // Otherwise no overlap.
+  // Few volumes: whichever of (two W stages, deepest vector pipeline that fits)
+  // and (one W stage, vectors one step ahead) puts more CTAs on an SM: the
+  // phases of a class run between block-wide barriers, so another CTA's class
+  // hides them better than a prefetch inside one CTA does.
+  auto per_sm_of = [](size_t bytes) { return (int)((228 * 1024) / (bytes + 1024)); };
   int nbuf = 1, nvs = 1;
   if (nvol >= 4 && make_plan(MODE, k->nt, k->nz, 1, 4, CT_THREADS).total <= SMEM_LIMIT) {
     nvs = 4;
@@ -322,6 +325,12 @@ ctof_status launch(const ctof_kernel_s* k, int nvol, const float2* vin, int ld_i
         nvs = v;
         break;
       }
+    }
+    const size_t one = make_plan(MODE, k->nt, k->nz, 1, 2, CT_THREADS).total;
+    const size_t cur = make_plan(MODE, k->nt, k->nz, nbuf, nvs, CT_THREADS).total;
+    if (one <= SMEM_LIMIT && per_sm_of(one) > per_sm_of(cur)) {
+      nbuf = 1;
+      nvs = 2;
     }
   }
   const Plan p = make_plan(MODE, k->nt, k->nz, nbuf, nvs, CT_THREADS);

@@ -420,6 +420,19 @@ __global__ void k_sub(float* __restrict__ a, const float* __restrict__ b, long l
     a[i] -= b[i];
 }
 
+// a -= b over n4 float4 (both 16-byte aligned)
+__global__ void k_sub4(float4* __restrict__ a, const float4* __restrict__ b, long long n4) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n4; i += (long long)gridDim.x * blockDim.x) {
+    float4 x = a[i];
+    const float4 y = b[i];
+    x.x -= y.x;
+    x.y -= y.y;
+    x.z -= y.z;
+    x.w -= y.w;
+    a[i] = x;
+  }
+}
+
 // r = (x - mu)/mu0; loss partial sums; gx = 2 r / (mu0 * ntot)
 __global__ void k_loss(const float* __restrict__ x, const float* __restrict__ mu, long long n, float* __restrict__ gx,
                        double* __restrict__ loss_sum) {
@@ -492,6 +505,17 @@ __global__ void k_adam(float* __restrict__ p, const float* __restrict__ gr, floa
   m[i] = mi;
   v[i] = vi;
   p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+}
+
+int grid_for(long long n);
+
+// a -= b (n floats); float4 when both pointers are 16-byte aligned and n % 4 == 0
+cudaError_t sub_inplace(float* a, const float* b, long long n, cudaStream_t st) {
+  if (((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b)) & 15) == 0 && (n & 3) == 0)
+    k_sub4<<<grid_for(n / 4), 256, 0, st>>>(reinterpret_cast<float4*>(a), reinterpret_cast<const float4*>(b), n / 4);
+  else
+    k_sub<<<grid_for(n), 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
 }
 
 int grid_for(long long n) {
@@ -686,8 +710,7 @@ ctof_status normal_residual(ctof_kernel_s* k, int batch, const float* x, const f
   CTOF_TRY(op_forward(k, batch, x, w.tmpT, w, st));
   if (m) {
     const long long mt = (long long)batch * k->nt * k->n * k->n;
-    k_sub<<<grid_for(mt), 256, 0, st>>>(w.tmpT, m, mt);
-    CTOF_CUDA_TRY(cudaGetLastError());
+    CTOF_CUDA_TRY(sub_inplace(w.tmpT, m, mt, st));
   }
   return op_adjoint(k, batch, w.tmpT, out, nullptr, w, st);
 }
@@ -739,11 +762,9 @@ ctof_status unrolled_forward(ctof_learned_s* L, ctof_kernel_s* k, int batch, con
     const long long mt = (long long)batch * k->nt * k->n * k->n;
     for (int d = 0; d < L->opt.dc_steps; ++d) {
       CTOF_TRY(op_forward(k, batch, w.x, w.tmpT, w, st));
-      k_sub<<<grid_for(mt), 256, 0, st>>>(w.tmpT, m, mt);
-      CTOF_CUDA_TRY(cudaGetLastError());
+      CTOF_CUDA_TRY(sub_inplace(w.tmpT, m, mt, st));
       CTOF_TRY(op_adjoint(k, batch, w.tmpT, w.h, hinv, w, st));
-      k_sub<<<grid_for(V), 256, 0, st>>>(w.x, w.h, V);
-      CTOF_CUDA_TRY(cudaGetLastError());
+      CTOF_CUDA_TRY(sub_inplace(w.x, w.h, V, st));
     }
   }
   return CTOF_OK;
