@@ -3,14 +3,17 @@
 TEST INFRASTRUCTURE ONLY (see the package docstring).
 
 The paper poses reconstruction as the regularised inverse of Eq. 7 (and the
-L1 problem of Eq. 8, solved there by FISTA).  The solvers here are
+L1 problem of Eq. 8, solved there by FISTA, with one weight per depth in
+Eq. 10).  The solvers here are
 (a) per-frequency Tikhonov, the closed-form minimiser of
     ||K x - pad(m)||^2 + lam ||x||^2 on the P x P periodic grid, and
 (b) scaled-form ADMM for
     min_x 1/2 ||C K x - m||^2 + beta ||D x||_1 + indicator{x >= 0, x = 0 off S}
 with C the crop to the measured N x N scan, D forward differences (lateral
-periodic on the P grid, axial Neumann), S = [0,N)^2 x all depths.
-Both are written step by step in the order the algorithm states them.
+periodic on the P grid, axial Neumann), S = [0,N)^2 x all depths, and
+(c) FISTA for the layer-weighted L1 problem of Eq. 10,
+    min_x 1/2 ||A x - m||^2 + sum_z lam(z) ||x_z||_1,   A = C K.
+All are written step by step in the order the algorithm states them.
 
 Conventions: numpy FFT (X[k] = sum x[n] exp(-2 pi i k n / P)), so the
 periodic forward difference x[n+1] - x[n] has symbol exp(2 pi i k/P) - 1.
@@ -18,7 +21,7 @@ periodic forward difference x[n+1] - x[n] has symbol exp(2 pi i k/P) - 1.
 
 import numpy as np
 
-from .operators import _pad, adjoint_fft
+from .operators import _pad, adjoint_fft, forward_fft
 
 
 def gram(w_hat):
@@ -168,3 +171,52 @@ def admm(w_hat, m, grid, iters, rho=1.0, beta=None, beta_rel=1e-3, history=False
     if history:
         info["iterates"] = hist
     return v3[:, :n, :n].copy(), info
+
+
+def depth_sensitivity(w_hat):
+    """sigma(z) = sqrt(G(0)_zz): the norm of depth z's kernel summed over the
+    lateral plane (the DC Gram diagonal), which falls with depth."""
+    g0 = gram(w_hat[:, :, :1, :1])[0, 0]
+    return np.sqrt(np.real(np.diag(g0)))
+
+
+def fista_l1(w_hat, m, grid, iters, lam=None, lam_rel=1e-2, layerwise=True, history=False):
+    """FISTA (Beck and Teboulle) for Eq. 10 with the layer-wise weight lam(z).
+
+    Readings: the data term is 1/2 ||A x - m||^2 (the smooth part FISTA needs);
+    units are normalised by s = max_f sigma_max(W_hat(f)) (A <- A/s, m <- m/s,
+    so the gradient's Lipschitz constant is 1 and the step is 1); the weight
+    follows the depth sensitivity, lam(z) = lam0 sigma(z) / max_z sigma(z)
+    (layerwise=False: lam(z) = lam0), which lowers the threshold where the
+    measurements see less and so counteracts the fading with depth that
+    Eq. 10 is introduced for; lam0 (if lam is None) = lam_rel max |A^T m|.
+      1. x_0 = y_1 = 0, t_1 = 1.
+      2. for k = 1 .. iters:
+           x_k     = soft(y_k - A^T (A y_k - m), lam(z))
+           t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
+           y_{k+1} = x_k + ((t_k - 1) / t_{k+1}) (x_k - x_{k-1})
+      3. return x_iters.
+    Returns (mu, info) with info = dict(scale, lam (per depth), iterates).
+    """
+    s = spectral_norm(w_hat)
+    wn = w_hat / s
+    mn = m / s
+    nz = w_hat.shape[1]
+    if lam is None:
+        lam = lam_rel * float(np.max(np.abs(adjoint_fft(wn, mn, grid))))
+    sig = depth_sensitivity(wn)
+    lam_z = lam * (sig / sig.max() if layerwise else np.ones(nz))
+    thr = lam_z[:, None, None]
+    x_prev = np.zeros((nz, grid.n, grid.n))
+    y = x_prev.copy()
+    t = 1.0
+    its = []
+    for _ in range(iters):
+        g = adjoint_fft(wn, forward_fft(wn, y, grid) - mn, grid)
+        x = soft(y - g, thr)
+        t_next = (1.0 + np.sqrt(1.0 + 4.0 * t * t)) / 2.0
+        y = x + ((t - 1.0) / t_next) * (x - x_prev)
+        x_prev, t = x, t_next
+        if history:
+            its.append(x.copy())
+    return x_prev, dict(scale=s, lam=lam_z, iterates=its)

@@ -225,3 +225,60 @@ def test_poisson_noise_statistics():
     # counts at 2500 expected: mean 0.25, variance 0.25 * (max/peak)
     assert y[1:].mean() == pytest.approx(0.25, rel=2e-3)
     assert y[1:].var() == pytest.approx(0.25 * 1e-4, rel=2e-2)
+
+
+def test_depth_sensitivity_is_response_to_a_constant_plane():
+    """Periodic grid: K applied to a constant plane of ones at depth z is the DC
+    term alone, so ||K 1_z|| = P sigma(z); sigma falls with depth (Eq. 10's
+    motive)."""
+    g = op.Grid(8, 4, 16, 1.0, 1.0, 1.0, 50.0, mode="circular")
+    wh = op.kernel_spectrum(op.kernel_offsets(g, medium()), g)
+    sig = so.depth_sensitivity(wh)
+    for z in range(g.nz):
+        plane = np.zeros((g.nz, g.n, g.n))
+        plane[z] = 1.0
+        resp = op.forward_fft(wh, plane, g)
+        assert np.linalg.norm(resp) == pytest.approx(g.p * sig[z], rel=1e-12)
+    assert np.all(np.diff(sig) < 0)
+
+
+def test_fista_lam0_converges_to_least_squares():
+    """lam = 0: FISTA minimises 1/2 ||A x - m||^2; its limit is the least-squares
+    solution (one depth: condition number 13, so it gets there quickly)."""
+    g, wh, J, meas = _tiny(nz=1, nt=16)
+    x, info = so.fista_l1(wh, meas, g, 6000, lam=0.0)
+    s = info["scale"]
+    want, *_ = np.linalg.lstsq(J / s, meas.ravel() / s, rcond=None)
+    assert np.abs(x.ravel() - want).max() <= 1e-8 * np.abs(want).max()
+
+
+def test_fista_matches_weighted_lasso_of_sklearn():
+    """lam > 0, layer-wise: the FISTA limit equals scikit-learn's coordinate-descent
+    Lasso on the dense Jacobian with columns scaled by 1/lam(z)."""
+    linear_model = pytest.importorskip("sklearn.linear_model")
+    g, wh, J, meas = _tiny(nz=2, nt=16, seed=7)
+    x, info = so.fista_l1(wh, meas, g, 6000, lam_rel=0.2)
+    s, lam_z = info["scale"], info["lam"]
+    assert lam_z[1] < lam_z[0]  # deeper layer, smaller weight
+    a = J / s
+    y = meas.ravel() / s
+    w = np.repeat(lam_z, g.n * g.n)
+    model = linear_model.Lasso(alpha=1.0 / len(y), fit_intercept=False, tol=1e-14, max_iter=200000)
+    model.fit(a / w[None, :], y)
+    want = model.coef_ / w
+    assert np.abs(x.ravel() - want).max() <= 1e-9 * np.abs(want).max()
+    # optimality (KKT) of the weighted L1 problem
+    r = a.T @ (y - a @ x.ravel())
+    nzr = np.abs(x.ravel()) > 0
+    assert np.all(np.abs(r[~nzr]) <= w[~nzr] * (1 + 1e-6))
+    assert np.allclose(r[nzr], w[nzr] * np.sign(x.ravel()[nzr]), rtol=1e-5, atol=1e-9 * w.max())
+
+
+def test_fista_first_iterate_is_a_thresholded_gradient_step():
+    g, wh, J, meas = _tiny(nz=2, nt=16)
+    x, info = so.fista_l1(wh, meas, g, 1, lam_rel=0.1)
+    s, lam_z = info["scale"], info["lam"]
+    step = (J / s).T @ (meas.ravel() / s)  # y_1 = 0: y - grad = A^T m
+    thr = np.repeat(lam_z, g.n * g.n)
+    want = np.sign(step) * np.maximum(np.abs(step) - thr, 0.0)
+    assert np.allclose(x.ravel(), want, rtol=1e-12, atol=1e-15)
