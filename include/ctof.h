@@ -49,7 +49,7 @@ typedef enum {
 } ctof_status;
 
 enum { CTOF_LINEAR = 0, CTOF_CIRCULAR = 1 };
-enum { CTOF_SOLVER_ADMM_TV = 0, CTOF_SOLVER_TIKHONOV = 1 };
+enum { CTOF_SOLVER_ADMM_TV = 0, CTOF_SOLVER_TIKHONOV = 1, CTOF_SOLVER_FISTA_L1 = 2 };
 enum { CTOF_KEEP_W = 1 }; /* ctof_build_kernel flag: retain the FP64 kernel table */
 enum { CTOF_FP32 = 0, CTOF_BF16 = 1, CTOF_FP8E4M3 = 2 }; /* contraction precision */
 
@@ -96,12 +96,20 @@ typedef struct {
 /* Solver choice and parameters.  ADMM_TV solves
  *   min_x 1/2 ||C K x - m||^2 + beta ||D x||_1,  x >= 0,  x = 0 off the scan
  * in units normalised by `scale` (K/scale has unit norm); Tikhonov solves
- * per lateral frequency (G + lambda I) x_hat = W_hat^T m_hat. */
+ * per lateral frequency (G + lambda I) x_hat = W_hat^T m_hat.  FISTA_L1 is the
+ * paper's own solver (FISTA for the L1 problem of Eq. 8 with one weight per
+ * depth, Eq. 10):
+ *   min_x 1/2 ||A x - m||^2 + sum_z lam(z) ||x_z||_1,   A = C K / scale,
+ * step 1, x_0 = 0, lam(z) = lam0 sigma(z) / max sigma with sigma(z) the DC
+ * sensitivity of depth z (sqrt of the Gram diagonal at frequency 0), so that
+ * deeper, fainter layers are thresholded less; lam0 = tv_beta (normalised
+ * units) or, if tv_beta < 0, beta_rel * max|A^T m| / scale^2.  The report's
+ * `beta` is lam0. */
 typedef struct {
-  int solver;             /* CTOF_SOLVER_ADMM_TV or CTOF_SOLVER_TIKHONOV */
-  int iters;              /* ADMM iterations (>= 1) */
+  int solver;             /* CTOF_SOLVER_ADMM_TV, CTOF_SOLVER_TIKHONOV or CTOF_SOLVER_FISTA_L1 */
+  int iters;              /* ADMM / FISTA iterations (>= 1) */
   double rho;             /* ADMM penalty (> 0), e.g. 1 */
-  double tv_beta;         /* TV weight in normalised units; < 0 selects
+  double tv_beta;         /* TV weight (FISTA: lam0) in normalised units; < 0 selects
                              beta_rel * max|A^T m| / scale^2 */
   double beta_rel;        /* e.g. 1e-3 */
   double tik_lambda_rel;  /* lambda = tik_lambda_rel * gram_max_diag, e.g. 1e-3 */
@@ -109,7 +117,7 @@ typedef struct {
 
 typedef struct {
   double scale;      /* normalisation used */
-  double beta;       /* TV weight used (normalised units) */
+  double beta;       /* TV weight (FISTA: lam0) used, normalised units */
   double lambda;     /* Tikhonov lambda used */
   int iters_done;
 } ctof_report;

@@ -124,6 +124,58 @@ __global__ void k_check_finite(const float* __restrict__ v, size_t count, int* _
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(flag, 1);
 }
 
+// ---- FISTA for the layer-weighted L1 problem (Eq. 8, Eq. 10) ----
+
+// lam[z] = lam0 * sigma(z) / max_z sigma(z), sigma(z) = sqrt(G_zz) of the class
+// holding the DC frequency (f = 0), lam0 = scalars[0].  One block.
+__global__ void k_fista_lambda(const double* __restrict__ scalars, const double* __restrict__ gram,
+                               const int* __restrict__ members, int nclass, int nz, float* __restrict__ lam) {
+  __shared__ int s_c;
+  __shared__ double s_max;
+  if (threadIdx.x == 0) s_c = -1;
+  __syncthreads();
+  for (int i = threadIdx.x; i < nclass * 4; i += blockDim.x)
+    if (members[i] == 0) s_c = i / 4;  // exactly one entry holds frequency 0
+  __syncthreads();
+  const int c = s_c;
+  if (threadIdx.x == 0) {
+    double mx = 0.0;
+    if (c >= 0)
+      for (int z = 0; z < nz; ++z) mx = fmax(mx, sqrt(gram[((size_t)c * nz + z) * nz + z]));
+    s_max = mx;
+  }
+  __syncthreads();
+  const double lam0 = scalars[0];
+  for (int z = threadIdx.x; z < nz; z += blockDim.x)
+    lam[z] = (c >= 0 && s_max > 0.0) ? (float)(lam0 * sqrt(gram[((size_t)c * nz + z) * nz + z]) / s_max)
+                                     : (float)lam0;
+}
+
+// r -= m
+__global__ void k_sub_meas(float* __restrict__ r, const float* __restrict__ m, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x)
+    r[i] -= m[i];
+}
+
+// One FISTA step per voxel (g = A^T (A y - m) unnormalised; x holds x_{k-1} on entry):
+//   x_k = soft(y - g / s^2, lam[z]);  y <- x_k + beta (x_k - x_{k-1});  x <- x_k
+__global__ void k_fista_step(float* __restrict__ y, const float* __restrict__ g, float* __restrict__ x,
+                             const float* __restrict__ lam, float beta, float inv_s2, int plane, size_t count) {
+  for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < count; i += (size_t)gridDim.x * blockDim.x) {
+    const float v = y[i] - inv_s2 * g[i];
+    const float xn = soft(v, lam[i / plane]);
+    const float xo = x[i];
+    x[i] = xn;
+    y[i] = xn + beta * (xn - xo);
+  }
+}
+
+int grid_elem(size_t count) {
+  size_t b = (count + 255) / 256;
+  if (b > 152 * 8) b = 152 * 8;
+  return b < 1 ? 1 : (int)b;
+}
+
 }  // namespace
 
 ctof_status admm_tv_stencil(const ctof_kernel_s* k, const float* x, const float* u2_old, float* u2_new, float* u3,
@@ -157,6 +209,25 @@ ctof_status check_finite(const float* v, size_t count, int* flag_dev, cudaStream
   if (blocks > 152 * 8) blocks = 152 * 8;
   if (blocks < 1) blocks = 1;
   k_check_finite<<<blocks, 256, 0, st>>>(v, count, flag_dev);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status fista_lambda(const ctof_kernel_s* k, const double* scalars, float* lam, cudaStream_t st) {
+  k_fista_lambda<<<1, 128, 0, st>>>(scalars, k->d_gram, k->d_members, k->nclass, k->nz, lam);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status fista_sub_meas(float* r, const float* m, size_t count, cudaStream_t st) {
+  k_sub_meas<<<grid_elem(count), 256, 0, st>>>(r, m, count);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status fista_step(float* y, const float* g, float* x, const float* lam, float beta, float inv_s2, int plane,
+                       size_t count, cudaStream_t st) {
+  k_fista_step<<<grid_elem(count), 256, 0, st>>>(y, g, x, lam, beta, inv_s2, plane, count);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }

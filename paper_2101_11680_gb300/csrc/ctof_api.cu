@@ -344,8 +344,47 @@ ctof_status tikhonov_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaSt
   return fft_inverse_planes(k, k->d_spec_z, k->ldz, k->nz, k->n, k->n, k->d_inter_z, k->d_vstage, k->n, st);
 }
 
+// FISTA for Eq. 10 on the staged measurement (result in d_vstage).  Normalised
+// units (A_n = A / s, step 1); lam0 by the same rule as the ADMM TV weight;
+// lam(z) follows the DC depth sensitivity.  Workspace: ADMM state buffers.
+ctof_status fista_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st) {
+  const size_t vol = (size_t)k->nz * k->n * k->n, meas = (size_t)k->nt * k->n * k->n;
+  float* y = k->d_u3;
+  float* x = k->d_xs;
+  float* g = k->d_s;
+  float* r = k->d_u1;
+  float* lam = k->d_u2a;
+  const float inv_s2 = (float)(1.0 / (k->scale * k->scale));
+  CTOF_CUDA_TRY(cudaMemsetAsync(k->d_scalars, 0, 16 * sizeof(double), st));
+  if (prm->tv_beta < 0) {
+    CTOF_TRY(adjoint_impl(k, k->d_mstage, k->d_vstage, st));
+    CTOF_TRY(reduce_max_abs(k->d_vstage, vol, k->d_scalars + 1, st));
+  }
+  CTOF_TRY(admm_set_beta(k->d_scalars, prm->tv_beta, prm->beta_rel, 1.0 / (k->scale * k->scale), st));
+  CTOF_TRY(fista_lambda(k, k->d_scalars, lam, st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(y, 0, vol * sizeof(float), st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(x, 0, vol * sizeof(float), st));
+  double t = 1.0;
+  for (int it = 0; it < prm->iters; ++it) {
+    CTOF_TRY(forward_impl(k, y, r, st));
+    CTOF_TRY(fista_sub_meas(r, k->d_mstage, meas, st));
+    CTOF_TRY(adjoint_impl(k, r, g, st));
+    const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
+    CTOF_TRY(fista_step(y, g, x, lam, (float)((t - 1.0) / t_next), inv_s2, k->n * k->n, vol, st));
+    t = t_next;
+  }
+  CTOF_CUDA_TRY(cudaMemcpyAsync(k->d_vstage, x, vol * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  return CTOF_OK;
+}
+
 ctof_status validate_params(const ctof_solver_params* p) {
   if (!p) return CTOF_EINVAL;
+  if (p->solver == CTOF_SOLVER_FISTA_L1) {
+    if (p->iters < 1 || p->iters > 100000) return CTOF_EINVAL;
+    if (!isfinite(p->tv_beta)) return CTOF_EINVAL;
+    if (p->tv_beta < 0 && !(isfinite(p->beta_rel) && p->beta_rel >= 0)) return CTOF_EINVAL;
+    return CTOF_OK;
+  }
   if (p->solver == CTOF_SOLVER_ADMM_TV) {
     if (p->iters < 1 || p->iters > 100000) return CTOF_EINVAL;
     if (!finite_pos(p->rho)) return CTOF_EINVAL;
@@ -361,6 +400,7 @@ ctof_status validate_params(const ctof_solver_params* p) {
 ctof_status solve_staged(ctof_kernel_s* k, const ctof_solver_params* prm, double* lambda, cudaStream_t st) {
   *lambda = 0.0;
   if (prm->solver == CTOF_SOLVER_ADMM_TV) return admm_run(k, prm, st);
+  if (prm->solver == CTOF_SOLVER_FISTA_L1) return fista_run(k, prm, st);
   return tikhonov_run(k, prm, st, lambda);
 }
 
@@ -377,9 +417,9 @@ ctof_status fill_report(ctof_kernel_s* k, const ctof_solver_params* prm, double 
   memcpy(&bad, &sc[8], sizeof(int));
   memcpy(&timeout, &sc[9], sizeof(int));
   rep->scale = k->scale;
-  rep->beta = prm->solver == CTOF_SOLVER_ADMM_TV ? sc[0] : 0.0;
+  rep->beta = prm->solver == CTOF_SOLVER_TIKHONOV ? 0.0 : sc[0];
   rep->lambda = lambda;
-  rep->iters_done = prm->solver == CTOF_SOLVER_ADMM_TV ? prm->iters : 1;
+  rep->iters_done = prm->solver == CTOF_SOLVER_TIKHONOV ? 1 : prm->iters;
   if (timeout) return CTOF_ETIMEOUT;
   return bad ? CTOF_ENONFINITE : CTOF_OK;
 }

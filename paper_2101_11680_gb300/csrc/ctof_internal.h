@@ -180,3 +180,9 @@ ctof_status reduce_max_abs(const float* v, size_t count, double* out_dev, cudaSt
 ctof_status admm_set_beta(double* scalars, double beta_fixed, double beta_rel, double inv_scale2,
                           cudaStream_t st);
 ctof_status check_finite(const float* v, size_t count, int* flag_dev, cudaStream_t st);
+// FISTA (Eq. 8, Eq. 10): per-depth weights from lam0 = scalars[0], r -= m, and one step
+// (x holds x_{k-1} on entry and x_k on exit; y becomes the next extrapolated point).
+ctof_status fista_lambda(const ctof_kernel_s* k, const double* scalars, float* lam, cudaStream_t st);
+ctof_status fista_sub_meas(float* r, const float* m, size_t count, cudaStream_t st);
+ctof_status fista_step(float* y, const float* g, float* x, const float* lam, float beta, float inv_s2, int plane,
+                       size_t count, cudaStream_t st);

@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libctof.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 LINEAR, CIRCULAR = 0, 1
-SOLVER_ADMM_TV, SOLVER_TIKHONOV = 0, 1
+SOLVER_ADMM_TV, SOLVER_TIKHONOV, SOLVER_FISTA_L1 = 0, 1, 2
 KEEP_W = 1
 FP32, BF16, FP8E4M3 = 0, 1, 2
 
@@ -151,6 +151,11 @@ def admm_params(iters=100, rho=1.0, tv_beta=-1.0, beta_rel=1e-3):
 
 def tikhonov_params(lambda_rel=1e-3):
     return SolverParams(SOLVER_TIKHONOV, 1, 1.0, -1.0, 1e-3, float(lambda_rel))
+
+
+def fista_params(iters=100, lam_rel=1e-2, lam=-1.0):
+    """FISTA for the layer-weighted L1 problem (Eq. 10); lam < 0 selects lam_rel * max|A^T m| (normalised)."""
+    return SolverParams(SOLVER_FISTA_L1, int(iters), 1.0, float(lam), float(lam_rel), 1e-3)
 
 
 class LearnedOptions(ctypes.Structure):

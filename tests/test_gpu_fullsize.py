@@ -118,3 +118,21 @@ def test_admm_full_size_properties(kern):
     r0 = float(m.double().norm())
     r1 = float((kern.forward(rec) - m).double().norm())
     assert r1 < r0
+
+
+def test_fista_full_size_properties(kern):
+    """The paper's FISTA (Eq. 10) at the benchmark size: finite, with exact zeros,
+    reproducible, and it lowers the data residual."""
+    mu = synth.phantom_shapes(N, NZ, DX, DZ, ZF, seed=1002)
+    mu_d = torch.tensor(mu, dtype=torch.float32, device="cuda")
+    clean = kern.forward(mu_d).double().clamp_(min=0).cpu().numpy()
+    m = torch.tensor(synth.poisson_noise(clean, 1e5, seed=11002), dtype=torch.float32, device="cuda")
+    p = ctof.fista_params(iters=100)
+    rec, rep = kern.reconstruct(m, p, report=True)
+    assert torch.isfinite(rec).all()
+    assert rep.iters_done == 100 and rep.beta > 0
+    assert bool((rec == 0).any())  # the L1 weight zeroes voxels exactly
+    assert torch.equal(rec, kern.reconstruct(m, p))
+    r0 = float(m.double().norm())
+    r1 = float((kern.forward(rec) - m).double().norm())
+    assert r1 < r0
