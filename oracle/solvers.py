@@ -180,7 +180,7 @@ def depth_sensitivity(w_hat):
     return np.sqrt(np.real(np.diag(g0)))
 
 
-def fista_l1(w_hat, m, grid, iters, lam=None, lam_rel=1e-2, layerwise=True, history=False):
+def fista_l1(w_hat, m, grid, iters, lam=None, lam_rel=1e-2, layerwise=True, history=False, multiplexed=False):
     """FISTA (Beck and Teboulle) for Eq. 10 with the layer-wise weight lam(z).
 
     Readings: the data term is 1/2 ||A x - m||^2 (the smooth part FISTA needs);
@@ -196,14 +196,20 @@ def fista_l1(w_hat, m, grid, iters, lam=None, lam_rel=1e-2, layerwise=True, hist
            t_{k+1} = (1 + sqrt(1 + 4 t_k^2)) / 2
            y_{k+1} = x_k + ((t_k - 1) / t_{k+1}) (x_k - x_{k-1})
       3. return x_iters.
+    multiplexed=True solves the composite problem of Eq. 12 with the same
+    scheme: A is replaced by S A (``multiplex.composite_forward``), `m` is the
+    multiplexed measurement y, and s by the composite norm 8 s (||S|| = 8).
     Returns (mu, info) with info = dict(scale, lam (per depth), iterates).
     """
-    s = spectral_norm(w_hat)
+    from . import multiplex as mx
+    s = spectral_norm(w_hat) * (8.0 if multiplexed else 1.0)
     wn = w_hat / s
     mn = m / s
     nz = w_hat.shape[1]
+    fwd = (lambda v: mx.composite_forward(wn, v, grid)) if multiplexed else (lambda v: forward_fft(wn, v, grid))
+    adj = (lambda r: mx.composite_adjoint(wn, r, grid)) if multiplexed else (lambda r: adjoint_fft(wn, r, grid))
     if lam is None:
-        lam = lam_rel * float(np.max(np.abs(adjoint_fft(wn, mn, grid))))
+        lam = lam_rel * float(np.max(np.abs(adj(mn))))
     sig = depth_sensitivity(wn)
     lam_z = lam * (sig / sig.max() if layerwise else np.ones(nz))
     thr = lam_z[:, None, None]
@@ -212,7 +218,7 @@ def fista_l1(w_hat, m, grid, iters, lam=None, lam_rel=1e-2, layerwise=True, hist
     t = 1.0
     its = []
     for _ in range(iters):
-        g = adjoint_fft(wn, forward_fft(wn, y, grid) - mn, grid)
+        g = adj(fwd(y) - mn)
         x = soft(y - g, thr)
         t_next = (1.0 + np.sqrt(1.0 + 4.0 * t * t)) / 2.0
         y = x + ((t - 1.0) / t_next) * (x - x_prev)
