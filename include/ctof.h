@@ -49,7 +49,7 @@ typedef enum {
 } ctof_status;
 
 enum { CTOF_LINEAR = 0, CTOF_CIRCULAR = 1 };
-enum { CTOF_SOLVER_ADMM_TV = 0, CTOF_SOLVER_TIKHONOV = 1, CTOF_SOLVER_FISTA_L1 = 2 };
+enum { CTOF_SOLVER_ADMM_TV = 0, CTOF_SOLVER_TIKHONOV = 1, CTOF_SOLVER_FISTA_L1 = 2, CTOF_SOLVER_FISTA_L1_MUX = 3 };
 enum { CTOF_KEEP_W = 1 }; /* ctof_build_kernel flag: retain the FP64 kernel table */
 enum { CTOF_FP32 = 0, CTOF_BF16 = 1, CTOF_FP8E4M3 = 2 }; /* contraction precision */
 
@@ -104,9 +104,12 @@ typedef struct {
  * sensitivity of depth z (sqrt of the Gram diagonal at frequency 0), so that
  * deeper, fainter layers are thresholded less; lam0 = tv_beta (normalised
  * units) or, if tv_beta < 0, beta_rel * max|A^T m| / scale^2.  The report's
- * `beta` is lam0. */
+ * `beta` is lam0.  FISTA_L1_MUX solves the same problem for the multiplexed
+ * composite operator of Eq. 12 (see ctof_forward_multiplexed): the measurement
+ * passed is y = S m and A becomes S A with normalisation 8 scale; it needs a
+ * lateral size that is a multiple of 8 (else EUNSUPPORTED). */
 typedef struct {
-  int solver;             /* CTOF_SOLVER_ADMM_TV, CTOF_SOLVER_TIKHONOV or CTOF_SOLVER_FISTA_L1 */
+  int solver;             /* CTOF_SOLVER_ADMM_TV, _TIKHONOV, _FISTA_L1 or _FISTA_L1_MUX */
   int iters;              /* ADMM / FISTA iterations (>= 1) */
   double rho;             /* ADMM penalty (> 0), e.g. 1 */
   double tv_beta;         /* TV weight (FISTA: lam0) in normalised units; < 0 selects
@@ -160,6 +163,16 @@ ctof_status ctof_forward(ctof_kernel k, const float* d_mu, float* d_m, void* str
 
 /* vol = A^T m: d_m [nt][ny][nx] -> d_vol [nz][ny][nx].  Asynchronous. */
 ctof_status ctof_adjoint(ctof_kernel k, const float* d_m, float* d_vol, void* stream);
+
+/* Source multiplexing (Section 5, "Composite reconstruction algorithm",
+ * Eq. 12): y = S A mu with S the 64 x 64 Sylvester Hadamard matrix (entries
+ * +-1; the paper's 8 x 8 source array) acting, for every time bin, on each
+ * 8 x 8 block of scan points taken row-major inside the block.  Layouts as
+ * ctof_forward / ctof_adjoint; the lateral size must be a multiple of 8
+ * (else EUNSUPPORTED).  The adjoint A^T S^T y (S^T = S) uses a workspace of
+ * the handle.  Asynchronous. */
+ctof_status ctof_forward_multiplexed(ctof_kernel k, const float* d_mu, float* d_y, void* stream);
+ctof_status ctof_adjoint_multiplexed(ctof_kernel k, const float* d_y, float* d_vol, void* stream);
 
 /* Reconstruct mu from m with the chosen solver: d_m [nt][ny][nx] ->
  * d_mu [nz][ny][nx].  If `report` is non-NULL the call synchronises the

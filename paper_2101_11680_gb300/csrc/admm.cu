@@ -170,6 +170,38 @@ __global__ void k_fista_step(float* __restrict__ y, const float* __restrict__ g,
   }
 }
 
+// ---- source multiplexing (Section 5, Eq. 12) ----
+
+// In place: every 8 x 8 block of scan points of every plane ([plane][n][n])
+// <- H_64 (Sylvester Hadamard) times its 64 values taken row-major.  One warp
+// per block, lane l holding entries l and l + 32; the fast Walsh-Hadamard
+// butterflies (a + b, a - b) run over strides 1..16 across lanes and 32 in
+// registers, which is H_64 in its natural (Sylvester) order.
+__global__ void k_block_hadamard(float* __restrict__ v, int planes, int n) {
+  const int warp = (int)((blockIdx.x * (size_t)blockDim.x + threadIdx.x) >> 5), lane = threadIdx.x & 31;
+  const int nb = n >> 3;
+  const long long nblk = (long long)planes * nb * nb;
+  if (warp >= nblk) return;
+  const int plane = (int)(warp / ((long long)nb * nb));
+  const int rem = (int)(warp - (long long)plane * nb * nb);
+  const int by = rem / nb, bx = rem - by * nb;
+  float* base = v + (size_t)plane * n * n + (size_t)(by * 8) * n + bx * 8;
+  // entry i -> row i / 8, column i % 8 of the block
+  float a = base[(lane >> 3) * n + (lane & 7)];
+  float b = base[((lane + 32) >> 3) * n + (lane & 7)];
+#pragma unroll
+  for (int h = 1; h < 32; h <<= 1) {
+    const float pa = __shfl_xor_sync(0xffffffffu, a, h);
+    const float pb = __shfl_xor_sync(0xffffffffu, b, h);
+    const bool hi = (lane & h) != 0;
+    a = hi ? pa - a : a + pa;
+    b = hi ? pb - b : b + pb;
+  }
+  const float s = a + b, d = a - b;
+  base[(lane >> 3) * n + (lane & 7)] = s;
+  base[((lane + 32) >> 3) * n + (lane & 7)] = d;
+}
+
 int grid_elem(size_t count) {
   size_t b = (count + 255) / 256;
   if (b > 152 * 8) b = 152 * 8;
@@ -228,6 +260,15 @@ ctof_status fista_sub_meas(float* r, const float* m, size_t count, cudaStream_t 
 ctof_status fista_step(float* y, const float* g, float* x, const float* lam, float beta, float inv_s2, int plane,
                        size_t count, cudaStream_t st) {
   k_fista_step<<<grid_elem(count), 256, 0, st>>>(y, g, x, lam, beta, inv_s2, plane, count);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status block_hadamard(float* v, int planes, int n, cudaStream_t st) {
+  if (n % 8 != 0) return CTOF_EUNSUPPORTED;
+  const long long warps = (long long)planes * (n / 8) * (n / 8);
+  const long long blocks = (warps * 32 + 255) / 256;
+  k_block_hadamard<<<(unsigned)blocks, 256, 0, st>>>(v, planes, n);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }

@@ -346,28 +346,40 @@ ctof_status tikhonov_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaSt
 
 // FISTA for Eq. 10 on the staged measurement (result in d_vstage).  Normalised
 // units (A_n = A / s, step 1); lam0 by the same rule as the ADMM TV weight;
-// lam(z) follows the DC depth sensitivity.  Workspace: ADMM state buffers.
-ctof_status fista_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st) {
+// lam(z) follows the DC depth sensitivity.  With `mux` the operator is the
+// composite S A of Eq. 12 (S = H_64 on every 8 x 8 block of scan points, so
+// the normalisation is 8 s) and the staged measurement is the multiplexed y.
+// Workspace: ADMM state buffers.
+ctof_status fista_run(ctof_kernel_s* k, const ctof_solver_params* prm, bool mux, cudaStream_t st) {
   const size_t vol = (size_t)k->nz * k->n * k->n, meas = (size_t)k->nt * k->n * k->n;
   float* y = k->d_u3;
   float* x = k->d_xs;
   float* g = k->d_s;
   float* r = k->d_u1;
   float* lam = k->d_u2a;
-  const float inv_s2 = (float)(1.0 / (k->scale * k->scale));
+  const double sc = k->scale * (mux ? 8.0 : 1.0);
+  const float inv_s2 = (float)(1.0 / (sc * sc));
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_scalars, 0, 16 * sizeof(double), st));
   if (prm->tv_beta < 0) {
-    CTOF_TRY(adjoint_impl(k, k->d_mstage, k->d_vstage, st));
+    if (mux) {
+      CTOF_CUDA_TRY(cudaMemcpyAsync(r, k->d_mstage, meas * sizeof(float), cudaMemcpyDeviceToDevice, st));
+      CTOF_TRY(block_hadamard(r, k->nt, k->n, st));
+      CTOF_TRY(adjoint_impl(k, r, k->d_vstage, st));
+    } else {
+      CTOF_TRY(adjoint_impl(k, k->d_mstage, k->d_vstage, st));
+    }
     CTOF_TRY(reduce_max_abs(k->d_vstage, vol, k->d_scalars + 1, st));
   }
-  CTOF_TRY(admm_set_beta(k->d_scalars, prm->tv_beta, prm->beta_rel, 1.0 / (k->scale * k->scale), st));
+  CTOF_TRY(admm_set_beta(k->d_scalars, prm->tv_beta, prm->beta_rel, 1.0 / (sc * sc), st));
   CTOF_TRY(fista_lambda(k, k->d_scalars, lam, st));
   CTOF_CUDA_TRY(cudaMemsetAsync(y, 0, vol * sizeof(float), st));
   CTOF_CUDA_TRY(cudaMemsetAsync(x, 0, vol * sizeof(float), st));
   double t = 1.0;
   for (int it = 0; it < prm->iters; ++it) {
     CTOF_TRY(forward_impl(k, y, r, st));
+    if (mux) CTOF_TRY(block_hadamard(r, k->nt, k->n, st));
     CTOF_TRY(fista_sub_meas(r, k->d_mstage, meas, st));
+    if (mux) CTOF_TRY(block_hadamard(r, k->nt, k->n, st));  // S^T = S
     CTOF_TRY(adjoint_impl(k, r, g, st));
     const double t_next = 0.5 * (1.0 + sqrt(1.0 + 4.0 * t * t));
     CTOF_TRY(fista_step(y, g, x, lam, (float)((t - 1.0) / t_next), inv_s2, k->n * k->n, vol, st));
@@ -379,7 +391,7 @@ ctof_status fista_run(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStrea
 
 ctof_status validate_params(const ctof_solver_params* p) {
   if (!p) return CTOF_EINVAL;
-  if (p->solver == CTOF_SOLVER_FISTA_L1) {
+  if (p->solver == CTOF_SOLVER_FISTA_L1 || p->solver == CTOF_SOLVER_FISTA_L1_MUX) {
     if (p->iters < 1 || p->iters > 100000) return CTOF_EINVAL;
     if (!isfinite(p->tv_beta)) return CTOF_EINVAL;
     if (p->tv_beta < 0 && !(isfinite(p->beta_rel) && p->beta_rel >= 0)) return CTOF_EINVAL;
@@ -400,7 +412,11 @@ ctof_status validate_params(const ctof_solver_params* p) {
 ctof_status solve_staged(ctof_kernel_s* k, const ctof_solver_params* prm, double* lambda, cudaStream_t st) {
   *lambda = 0.0;
   if (prm->solver == CTOF_SOLVER_ADMM_TV) return admm_run(k, prm, st);
-  if (prm->solver == CTOF_SOLVER_FISTA_L1) return fista_run(k, prm, st);
+  if (prm->solver == CTOF_SOLVER_FISTA_L1) return fista_run(k, prm, false, st);
+  if (prm->solver == CTOF_SOLVER_FISTA_L1_MUX) {
+    if (k->n % 8 != 0) return CTOF_EUNSUPPORTED;
+    return fista_run(k, prm, true, st);
+  }
   return tikhonov_run(k, prm, st, lambda);
 }
 
@@ -738,6 +754,28 @@ ctof_status ctof_adjoint(ctof_kernel k, const float* d_m, float* d_vol, void* st
   DeviceGuard g(k->device);
   if (!g.ok) return CTOF_ECUDA;
   return adjoint_impl(k, d_m, d_vol, static_cast<cudaStream_t>(stream));
+}
+
+ctof_status ctof_forward_multiplexed(ctof_kernel k, const float* d_mu, float* d_y, void* stream) {
+  if (!k || !d_mu || !d_y) return CTOF_EINVAL;
+  if (k->n % 8 != 0) return CTOF_EUNSUPPORTED;
+  DeviceGuard g(k->device);
+  if (!g.ok) return CTOF_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  CTOF_TRY(forward_impl(k, d_mu, d_y, st));
+  return block_hadamard(d_y, k->nt, k->n, st);
+}
+
+ctof_status ctof_adjoint_multiplexed(ctof_kernel k, const float* d_y, float* d_vol, void* stream) {
+  if (!k || !d_y || !d_vol) return CTOF_EINVAL;
+  if (k->n % 8 != 0) return CTOF_EUNSUPPORTED;
+  DeviceGuard g(k->device);
+  if (!g.ok) return CTOF_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const size_t meas = (size_t)k->nt * k->n * k->n;
+  CTOF_CUDA_TRY(cudaMemcpyAsync(k->d_u1, d_y, meas * sizeof(float), cudaMemcpyDeviceToDevice, st));
+  CTOF_TRY(block_hadamard(k->d_u1, k->nt, k->n, st));
+  return adjoint_impl(k, k->d_u1, d_vol, st);
 }
 
 ctof_status ctof_reconstruct(ctof_kernel k, const float* d_m, const ctof_solver_params* params, float* d_mu,

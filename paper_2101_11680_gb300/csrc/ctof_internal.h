@@ -183,6 +183,8 @@ ctof_status check_finite(const float* v, size_t count, int* flag_dev, cudaStream
 // FISTA (Eq. 8, Eq. 10): per-depth weights from lam0 = scalars[0], r -= m, and one step
 // (x holds x_{k-1} on entry and x_k on exit; y becomes the next extrapolated point).
 ctof_status fista_lambda(const ctof_kernel_s* k, const double* scalars, float* lam, cudaStream_t st);
+// In place, [planes][n][n]: every 8 x 8 block of scan points <- H_64 times it (n % 8 == 0).
+ctof_status block_hadamard(float* v, int planes, int n, cudaStream_t st);
 ctof_status fista_sub_meas(float* r, const float* m, size_t count, cudaStream_t st);
 ctof_status fista_step(float* y, const float* g, float* x, const float* lam, float beta, float inv_s2, int plane,
                        size_t count, cudaStream_t st);

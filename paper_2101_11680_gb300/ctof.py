@@ -14,7 +14,7 @@ LIB_PATH = os.path.join(HERE, "libctof.so")
 
 OK, EINVAL, ENOMEM, ECUDA, ENONFINITE, ETIMEOUT, EUNSUPPORTED = 0, -1, -2, -3, -4, -5, -6
 LINEAR, CIRCULAR = 0, 1
-SOLVER_ADMM_TV, SOLVER_TIKHONOV, SOLVER_FISTA_L1 = 0, 1, 2
+SOLVER_ADMM_TV, SOLVER_TIKHONOV, SOLVER_FISTA_L1, SOLVER_FISTA_L1_MUX = 0, 1, 2, 3
 KEEP_W = 1
 FP32, BF16, FP8E4M3 = 0, 1, 2
 
@@ -74,6 +74,8 @@ _SIGNATURES = {
     "ctof_kernel_get_what": (ctypes.c_int, [_P, _P]),
     "ctof_forward": (ctypes.c_int, [_P, _P, _P, _P]),
     "ctof_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ctof_forward_multiplexed": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ctof_adjoint_multiplexed": (ctypes.c_int, [_P, _P, _P, _P]),
     "ctof_reconstruct": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolverParams), _P, ctypes.POINTER(Report), _P]),
     "ctof_reconstruct_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolverParams), _P, ctypes.POINTER(Report),
                                              _P]),
@@ -153,9 +155,12 @@ def tikhonov_params(lambda_rel=1e-3):
     return SolverParams(SOLVER_TIKHONOV, 1, 1.0, -1.0, 1e-3, float(lambda_rel))
 
 
-def fista_params(iters=100, lam_rel=1e-2, lam=-1.0):
-    """FISTA for the layer-weighted L1 problem (Eq. 10); lam < 0 selects lam_rel * max|A^T m| (normalised)."""
-    return SolverParams(SOLVER_FISTA_L1, int(iters), 1.0, float(lam), float(lam_rel), 1e-3)
+def fista_params(iters=100, lam_rel=1e-2, lam=-1.0, multiplexed=False):
+    """FISTA for the layer-weighted L1 problem (Eq. 10); lam < 0 selects lam_rel * max|A^T m| (normalised).
+
+    multiplexed=True: the composite problem of Eq. 12 (measurement y = S m)."""
+    return SolverParams(SOLVER_FISTA_L1_MUX if multiplexed else SOLVER_FISTA_L1, int(iters), 1.0, float(lam),
+                        float(lam_rel), 1e-3)
 
 
 class LearnedOptions(ctypes.Structure):
@@ -353,6 +358,26 @@ class Kernel:
         _check(self._lib.ctof_adjoint(self._h, _dev_ptr(m, self._meas_shape(), "m"),
                                       _dev_ptr(out, self._vol_shape(), "out"), _stream_handle(stream)),
                "ctof_adjoint")
+        return out
+
+    def forward_multiplexed(self, mu, out=None, stream=None):
+        """y = S A mu (Eq. 12: Hadamard multiplexing over 8 x 8 scan blocks)."""
+        import torch
+        if out is None:
+            out = torch.empty(self._meas_shape(), device=mu.device, dtype=torch.float32)
+        _check(self._lib.ctof_forward_multiplexed(self._h, _dev_ptr(mu, self._vol_shape(), "mu"),
+                                                  _dev_ptr(out, self._meas_shape(), "out"), _stream_handle(stream)),
+               "ctof_forward_multiplexed")
+        return out
+
+    def adjoint_multiplexed(self, y, out=None, stream=None):
+        """A^T S^T y."""
+        import torch
+        if out is None:
+            out = torch.empty(self._vol_shape(), device=y.device, dtype=torch.float32)
+        _check(self._lib.ctof_adjoint_multiplexed(self._h, _dev_ptr(y, self._meas_shape(), "y"),
+                                                  _dev_ptr(out, self._vol_shape(), "out"), _stream_handle(stream)),
+               "ctof_adjoint_multiplexed")
         return out
 
     def reconstruct(self, m, params, out=None, report=False, stream=None):

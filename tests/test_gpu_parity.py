@@ -183,3 +183,42 @@ def test_fista_l1(name, iters):
     # the solver is deterministic
     got2 = k.reconstruct(torch.tensor(m, dtype=torch.float32, device="cuda"), ctof.fista_params(iters=iters))
     assert torch.equal(got, got2)
+
+
+@pytest.mark.parametrize("name", ["admm16", "cfg1"])
+def test_multiplexed_operator(name):
+    """Composite operator of Eq. 12 (Hadamard over 8 x 8 scan blocks) and its adjoint."""
+    from oracle import multiplex as mx
+    g, _, wh = oracle_kernel(name)
+    k = device_kernel(name)
+    mu = _rand_vol(g, 11)
+    want = mx.composite_forward(wh, mu, g)
+    got = k.forward_multiplexed(torch.tensor(mu, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert rel_l2(got, want) <= 1e-5
+    rng = np.random.default_rng(12)
+    y = rng.standard_normal((g.nt, g.n, g.n)) * np.abs(want).max()
+    want_a = mx.composite_adjoint(wh, y, g)
+    got_a = k.adjoint_multiplexed(torch.tensor(y, dtype=torch.float32, device="cuda")).cpu().numpy()
+    assert rel_l2(got_a, want_a) <= 1e-5
+
+
+def test_multiplexed_fista():
+    """FISTA on the composite problem of Eq. 12 against the oracle (tolerance as test_fista_l1)."""
+    from oracle import multiplex as mx
+    g, wh, mu, _ = _measurement("admm16", seed=6, peak=1e5)
+    y = mx.composite_forward(wh, mu, g)
+    y = y + 1e-3 * np.abs(y).max() * np.random.default_rng(13).standard_normal(y.shape)
+    iters = 100
+    want, info = so.fista_l1(wh, y, g, iters, lam_rel=1e-2, multiplexed=True)
+    k = device_kernel("admm16")
+    got, rep = k.reconstruct(torch.tensor(y, dtype=torch.float32, device="cuda"),
+                             ctof.fista_params(iters=iters, lam_rel=1e-2, multiplexed=True), report=True)
+    assert rep.beta == pytest.approx(float(info["lam"].max()), rel=1e-5)
+    assert rel_l2(got.cpu().numpy(), want) <= max(1e-5, 5e-7 * iters)
+
+
+def test_multiplexed_needs_blocks_of_8():
+    k = device_kernel("ragged")  # 20 x 20 scan
+    with pytest.raises(ctof.CtofError) as e:
+        k.forward_multiplexed(torch.zeros((5, 20, 20), device="cuda"))
+    assert e.value.status == ctof.EUNSUPPORTED
