@@ -625,7 +625,8 @@ template <bool IN_F32, bool OUT_PROX>
 ctof_status conv_launch(const __nv_bfloat16* in, const float* in_f, float in_scale, int relu_in,
                         const __nv_bfloat16* wt, const float* bias, const __nv_bfloat16* mask, __nv_bfloat16* out,
                         const float* z, float* x_out, Geo G, cudaStream_t st) {
-  const int txc = G.x % 64 == 0 ? 4 : (G.x % 32 == 0 ? 2 : 1);
+  // 32-voxel-wide tiles (47 KB of shared memory) let four CTAs share an SM
+  const int txc = G.x % 32 == 0 ? 2 : 1;
   const dim3 grid(G.x / (16 * txc), G.y / CV_TY, G.b * G.z);
   const size_t smem = conv_smem_bytes(txc);
   switch (txc) {
