@@ -54,6 +54,26 @@ CONFIGS = {
 OPTICS = dict(mua=0.01, musp=1.0, n=1.4)
 
 
+def replica_seed(seed, rank):
+    """Input seed of a replica: every rank reconstructs its own phantoms."""
+    return seed + 1000 * rank
+
+
+def max_over_ranks(x, dist, device):
+    """The slowest rank's value of x (x itself without a process group)."""
+    if dist is None:
+        return x
+    import torch
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(units_per_rank, world, seconds):
+    """Whole-job throughput: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / seconds
+
+
 def _peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     try:
@@ -573,7 +593,7 @@ def main():
     build_s = time.perf_counter() - t0
     info = kern.info
     count = args.steps + args.warmup
-    ms, mus = make_inputs(kern, cfg, count, args.seed + 1000 * rank, torch)
+    ms, mus = make_inputs(kern, cfg, count, replica_seed(args.seed, rank), torch)
     outs = [torch.empty_like(mu) for mu in mus]
     params = ctof.admm_params(iters=cfg["iters"])
     kern.set_timing(True)
@@ -601,12 +621,8 @@ def main():
     elapsed_ms = ev0.elapsed_time(ev1)
     clk = clocks.stop()
     timing = kern.get_timing()
-    if dist:
-        t = torch.tensor([elapsed_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
-    total_vols = args.steps * world
-    value = total_vols / (elapsed_ms / 1e3)
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, "cuda")
+    value = aggregate_rate(args.steps, world, elapsed_ms / 1e3)
 
     # reconstruction quality (vs the phantom) and a NaN scan of the outputs
     errs = [float((o - mu).norm() / mu.norm()) for o, mu in zip(outs[:args.steps], mus[:args.steps])]
@@ -621,12 +637,8 @@ def main():
     t0 = time.perf_counter()
     for i in range(args.steps):
         kern.reconstruct_host(mh[i], params, oh[i])
-    e2e_s = time.perf_counter() - t0
-    if dist:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e_val = total_vols / e2e_s
+    e2e_s = max_over_ranks(time.perf_counter() - t0, dist, "cuda")
+    e2e_val = aggregate_rate(args.steps, world, e2e_s)
 
     peak, peak_src = _peaks()
     avg_contract_ms = timing.contract_ms / max(1, timing.contract_launches)
