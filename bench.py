@@ -548,10 +548,15 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--seed", type=int, default=1000)
     ap.add_argument("--batch", type=int, default=None)
+    ap.add_argument("--lateral", type=int, default=None,
+                    help="override the lateral size (a smaller case of the same per-class kernels, for profiling)")
     ap.add_argument("--solver", default="admm", choices=["admm", "fista"],
                     help="default-config solver: ADMM-TV (the benchmark) or the paper's FISTA-L1")
     args = ap.parse_args()
     cfg = dict(CONFIGS[args.config])
+    if args.lateral:
+        cfg["n"] = args.lateral
+        cfg["workload"] = cfg["workload"] + " [lateral size overridden to %d]" % args.lateral
     if args.config == "cfg3":
         run_precision(args, cfg)
         return
