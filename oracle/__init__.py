@@ -11,7 +11,9 @@ Layout
 ------
 physics    diffusion Green's functions (Eq. 4, Eq. 5), the source->voxel->
            detector time convolution in closed form and numerically, and the
-           time-bin quadrature.
+           time-bin quadrature; the fluorescence-mode response (excitation
+           and emission optics, lifetime convolution) by the convolution
+           theorem and a fixed-Talbot Laplace inversion.
 operators  the sensitivity kernel W on the lateral offset grid, the dense
            confocal Jacobian (Eq. 2, Eq. 6), and the convolutional forward /
            adjoint operators of the 3D convolutional approximation

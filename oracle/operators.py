@@ -23,7 +23,7 @@ which depends only on the lateral offset: the convolutional approximation
 
 import numpy as np
 
-from .physics import binned_conv
+from .physics import binned_conv, binned_fluorescence
 
 
 class Grid:
@@ -73,9 +73,28 @@ def kernel_offsets(grid, med, nodes=8, sub=4):
     rho = np.sqrt((a[None, :] * grid.dx) ** 2 + (a[:, None] * grid.dy) ** 2)  # [qy][qx]
     z = grid.depths[:, None, None]
     quad = binned_conv(rho[None, :, :], z, grid.nt, grid.dt, med, nodes, sub) * grid.voxel_volume
-    # quad: [T][Z][|oy|][|ox|] -> full offsets
+    return _mirror(quad, n)
+
+
+def _mirror(quad, n):
+    """[T][Z][|oy|][|ox|] quadrant -> [T][Z][2N-1][2N-1] full offsets."""
     idx = np.abs(np.arange(-(n - 1), n))
     return quad[:, :, idx][:, :, :, idx]
+
+
+def kernel_offsets_fluorescence(grid, med_ex, med_em, tau):
+    """Fluorescence-mode kernel on the offset grid (same layout as ``kernel_offsets``).
+
+    W[k][j][oy][ox] = dx dy dz * int_bin_k (Phi0_ex (*) L_tau (*) R_em)(rho, z_j, t) dt
+    (Section 5: excitation and emission optics, lifetime tau in ps), the bin
+    integral taken exactly as differences of the cumulative response.
+    """
+    n = grid.n
+    a = np.arange(n)
+    rho = np.sqrt((a[None, :] * grid.dx) ** 2 + (a[:, None] * grid.dy) ** 2)
+    z = grid.depths[:, None, None]
+    quad = binned_fluorescence(rho[None, :, :], z, grid.nt, grid.dt, med_ex, med_em, tau) * grid.voxel_volume
+    return _mirror(quad, n)
 
 
 def periodic_kernel(w_off, grid):

@@ -6,7 +6,10 @@
 //     (Eq. 5), the time convolution in closed form from the Laplace
 //     transforms of the semi-infinite extrapolated-boundary Green's
 //     functions, the bin integral by an 8-node Gauss-Legendre rule on each of
-//     4 equal pieces of the bin.
+//     4 equal pieces of the bin.  Fluorescence mode (Section 5): Phi0 of the
+//     excitation optics, R of the emission optics and a lifetime
+//     convolution, through the product of Laplace transforms and a
+//     fixed-Talbot inversion at the bin edges (k_w_quadrant_fl).
 //  2. W_hat = the 2-D DFT of the periodic kernel.  The kernel is even in x
 //     and y, so W_hat is real and is a separable cosine sum over the
 //     non-negative offsets: W_hat(a,b) = sum_{q,p} c_q c_p W[q][p]
@@ -100,6 +103,165 @@ __global__ void k_w_quadrant(double* __restrict__ w, int t0, int tcount, int nz,
       w[(((size_t)tk * nz + j) * q + qy) * q + qx] = acc;
       if (symmetric && qx != qy) w[(((size_t)tk * nz + j) * q + qx) * q + qy] = acc;
     }
+  }
+}
+
+// ---- fluorescence mode ----
+// f = Phi0_ex (*)_t L_tau (*)_t R_em.  Its Laplace transform is the product of
+// the three factors' closed-form transforms (q = sqrt((s + mua c)/(D c)) of
+// each medium):
+//   F(s) = [e^{-r1 q_ex}/r1 - e^{-r2 q_ex}/r2] / (4 pi D_ex)
+//        * [z (1 + r3 q_em) e^{-r3 q_em}/r3^3 + (z + 2 zb_em)(1 + r4 q_em) e^{-r4 q_em}/r4^3] / (4 pi)
+//        / (1 + s tau).
+// The cumulative response C(t) = int_0^t f is the inverse transform of F(s)/s,
+// taken with the fixed-Talbot rule (Abate and Valko 2004): on the contour
+// s(theta) = r theta (cot theta + i), r = 2M/(5t), the trapezoidal rule in
+// theta gives C(t) = (r/M) sum_j Re(gamma_j G(r u_j)) with u_j = theta_j
+// cot theta_j + i theta_j (u_0 = 1) and weights gamma_j = e^{(2M/5) u_j}
+// (1 + i sigma_j), sigma = theta + (theta cot theta - 1) cot theta,
+// gamma_0 = e^{2M/5}/2; since t r = 2M/5 the weights do not depend on t.
+// The bin integral is C at the upper edge minus C at the lower edge.
+constexpr int TALBOT_M = 24;
+
+struct FluoParams {
+  double a_ex, k_ex, D_ex, zb_ex, z0;  // a = mua c, k = D c
+  double a_em, k_em, zb_em;
+  double tau, rmin, dx, dy, dz, zfirst, dt, vol;
+  double u_re[TALBOT_M], u_im[TALBOT_M];
+  double g_re[TALBOT_M], g_im[TALBOT_M];
+};
+
+struct cd {
+  double re, im;
+};
+__device__ __forceinline__ cd c_mul(cd a, cd b) { return {a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re}; }
+__device__ __forceinline__ cd c_div(cd a, cd b) {
+  // Smith's algorithm
+  if (fabs(b.re) >= fabs(b.im)) {
+    const double r = b.im / b.re, d = b.re + b.im * r;
+    return {(a.re + a.im * r) / d, (a.im - a.re * r) / d};
+  }
+  const double r = b.re / b.im, d = b.re * r + b.im;
+  return {(a.re * r + a.im) / d, (a.im * r - a.re) / d};
+}
+// principal square root, written to avoid cancellation in either half-plane
+__device__ __forceinline__ cd c_sqrt(cd a) {
+  const double m = hypot(a.re, a.im);
+  if (m == 0.0) return {0.0, 0.0};
+  if (a.re >= 0.0) {
+    const double t = sqrt(0.5 * (m + a.re));
+    return {t, a.im / (2.0 * t)};
+  }
+  const double t = sqrt(0.5 * (m - a.re));
+  return {fabs(a.im) / (2.0 * t), copysign(t, a.im)};
+}
+// e^{-x a}, x >= 0 and Re a >= 0 (no overflow)
+__device__ __forceinline__ cd c_exp_neg(double x, cd a) {
+  const double e = exp(-x * a.re);
+  double sn, cs;
+  sincos(x * a.im, &sn, &cs);
+  return {e * cs, -e * sn};
+}
+
+__device__ double fl_cumulative(double t, double r1, double r2, double r3, double r4, double z, const FluoParams& p) {
+  const double pi = 3.14159265358979323846;
+  const double r = 2.0 * TALBOT_M / (5.0 * t);
+  const double z4 = z + 2.0 * p.zb_em;
+  double acc = 0.0;
+  for (int j = 0; j < TALBOT_M; ++j) {
+    const cd s = {r * p.u_re[j], r * p.u_im[j]};
+    const cd qx = c_sqrt({(s.re + p.a_ex) / p.k_ex, s.im / p.k_ex});
+    const cd qm = c_sqrt({(s.re + p.a_em) / p.k_em, s.im / p.k_em});
+    const cd e1 = c_exp_neg(r1, qx), e2 = c_exp_neg(r2, qx);
+    const cd src = {(e1.re / r1 - e2.re / r2) / (4.0 * pi * p.D_ex), (e1.im / r1 - e2.im / r2) / (4.0 * pi * p.D_ex)};
+    const cd e3 = c_exp_neg(r3, qm), e4 = c_exp_neg(r4, qm);
+    const cd f3 = c_mul({1.0 + r3 * qm.re, r3 * qm.im}, e3);
+    const cd f4 = c_mul({1.0 + r4 * qm.re, r4 * qm.im}, e4);
+    const double w3 = z / (4.0 * pi * r3 * r3 * r3), w4 = z4 / (4.0 * pi * r4 * r4 * r4);
+    const cd det = {w3 * f3.re + w4 * f4.re, w3 * f3.im + w4 * f4.im};
+    // G(s) = src det / ((1 + s tau) s)
+    const cd den = c_mul({1.0 + s.re * p.tau, s.im * p.tau}, s);
+    const cd g = c_div(c_mul(src, det), den);
+    acc += p.g_re[j] * g.re - p.g_im[j] * g.im;
+  }
+  return r / TALBOT_M * acc;
+}
+
+__global__ void k_w_quadrant_fl(double* __restrict__ w, int t0, int tcount, int nz, int q, int symmetric,
+                                FluoParams prm) {
+  const long long npairs = symmetric ? (long long)q * (q + 1) / 2 : (long long)q * q;
+  const long long total = npairs * nz;
+  for (long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x; gid < total;
+       gid += (long long)gridDim.x * blockDim.x) {
+    const int j = (int)(gid / npairs);
+    const long long pr = gid - (long long)j * npairs;
+    int qy, qx;
+    if (symmetric) {
+      qy = (int)((sqrt(8.0 * (double)pr + 1.0) - 1.0) * 0.5);
+      while ((long long)(qy + 1) * (qy + 2) / 2 <= pr) ++qy;
+      while ((long long)qy * (qy + 1) / 2 > pr) --qy;
+      qx = (int)(pr - (long long)qy * (qy + 1) / 2);
+    } else {
+      qy = (int)(pr / q);
+      qx = (int)(pr - (long long)qy * q);
+    }
+    const double rho2 = (qx * prm.dx) * (qx * prm.dx) + (qy * prm.dy) * (qy * prm.dy);
+    const double z = prm.zfirst + j * prm.dz;
+    const double r1 = fmax(sqrt(rho2 + (z - prm.z0) * (z - prm.z0)), prm.rmin);
+    const double r2 = fmax(sqrt(rho2 + (z + prm.z0 + 2.0 * prm.zb_ex) * (z + prm.z0 + 2.0 * prm.zb_ex)), prm.rmin);
+    const double r3 = fmax(sqrt(rho2 + z * z), prm.rmin);
+    const double r4 = fmax(sqrt(rho2 + (z + 2.0 * prm.zb_em) * (z + 2.0 * prm.zb_em)), prm.rmin);
+    double prev = t0 > 0 ? fl_cumulative(t0 * prm.dt, r1, r2, r3, r4, z, prm) : 0.0;
+    for (int tk = 0; tk < tcount; ++tk) {
+      const double cur = fl_cumulative((t0 + tk + 1) * prm.dt, r1, r2, r3, r4, z, prm);
+      const double acc = (cur - prev) * prm.vol;
+      prev = cur;
+      w[(((size_t)tk * nz + j) * q + qy) * q + qx] = acc;
+      if (symmetric && qx != qy) w[(((size_t)tk * nz + j) * q + qx) * q + qy] = acc;
+    }
+  }
+}
+
+void make_fluo_params(const ctof_kernel_s* k, FluoParams& p) {
+  const double n = k->optics.n;
+  const double c = 0.299792458 / n;
+  const double reff = -1.440 / (n * n) + 0.710 / n + 0.668 + 0.0636 * n;
+  const double Acoef = (1.0 + reff) / (1.0 - reff);
+  const double mx = k->optics.mua_mm, sx = k->optics.musp_mm;
+  const double mm = k->emission.mua_mm, sm = k->emission.musp_mm;
+  p.D_ex = 1.0 / (3.0 * (mx + sx));
+  p.a_ex = mx * c;
+  p.k_ex = p.D_ex * c;
+  p.zb_ex = 2.0 * Acoef * p.D_ex;
+  p.z0 = k->optics.z0_mm > 0 ? k->optics.z0_mm : 1.0 / (mx + sx);
+  const double D_em = 1.0 / (3.0 * (mm + sm));
+  p.a_em = mm * c;
+  p.k_em = D_em * c;
+  p.zb_em = 2.0 * Acoef * D_em;
+  p.tau = k->emission.tau_ps;
+  p.rmin = k->r_min;
+  p.dx = k->grid.dx_mm;
+  p.dy = k->grid.dy_mm;
+  p.dz = k->grid.dz_mm;
+  p.zfirst = k->grid.z_first_mm;
+  p.dt = k->grid.dt_ps;
+  p.vol = p.dx * p.dy * p.dz;
+  const double pi = 3.14159265358979323846;
+  const double cm = 2.0 * TALBOT_M / 5.0;
+  p.u_re[0] = 1.0;
+  p.u_im[0] = 0.0;
+  p.g_re[0] = 0.5 * exp(cm);
+  p.g_im[0] = 0.0;
+  for (int j = 1; j < TALBOT_M; ++j) {
+    const double th = j * pi / TALBOT_M;
+    const double cot = cos(th) / sin(th);
+    const double sigma = th + (th * cot - 1.0) * cot;
+    p.u_re[j] = th * cot;
+    p.u_im[j] = th;
+    const double e = exp(cm * th * cot);
+    const double er = e * cos(cm * th), ei = e * sin(cm * th);
+    p.g_re[j] = er - ei * sigma;  // e^{cm u} (1 + i sigma)
+    p.g_im[j] = ei + er * sigma;
   }
 }
 
@@ -422,6 +584,8 @@ ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st) {
     prm.vol = prm.dx * prm.dy * prm.dz;
     gauss_legendre(8, prm.gl_x, prm.gl_w);
   }
+  FluoParams fprm;
+  if (k->fluorescence) make_fluo_params(k, fprm);
 
   // ---- device temporaries, processed in chunks of time bins ----
   const long long planes = (long long)nt * nz;
@@ -451,7 +615,11 @@ ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st) {
       const long long work = npairs * nz;
       int blocks = (int)((work + 127) / 128);
       if (blocks > 152 * 64) blocks = 152 * 64;
-      k_w_quadrant<<<blocks, 128, 0, st>>>(d_wq.as<double>(), t0, tc, nz, q, k->symmetric, prm);
+      if (k->fluorescence) {
+        k_w_quadrant_fl<<<blocks, 128, 0, st>>>(d_wq.as<double>(), t0, tc, nz, q, k->symmetric, fprm);
+      } else {
+        k_w_quadrant<<<blocks, 128, 0, st>>>(d_wq.as<double>(), t0, tc, nz, q, k->symmetric, prm);
+      }
       CTOF_CUDA_TRY(cudaGetLastError());
     }
     if (k->d_w) {

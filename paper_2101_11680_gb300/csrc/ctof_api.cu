@@ -576,11 +576,16 @@ void ctof_kernel_destroy(ctof_kernel k) {
   delete k;
 }
 
-ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, int flags, void* stream,
-                              ctof_kernel* out) {
+namespace {
+
+ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, const ctof_grid* grid, int flags,
+                      void* stream, ctof_kernel* out) {
   if (!out) return CTOF_EINVAL;
   *out = nullptr;
   CTOF_TRY(validate(optics, grid));
+  if (emission && !(isfinite(emission->mua_mm) && emission->mua_mm >= 0.0 && finite_pos(emission->musp_mm) &&
+                    isfinite(emission->tau_ps) && emission->tau_ps >= 0.0))
+    return CTOF_EINVAL;
   if (flags & ~CTOF_KEEP_W) return CTOF_EINVAL;
   int dev = 0;
   CTOF_CUDA_TRY(cudaGetDevice(&dev));
@@ -589,6 +594,8 @@ ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, 
   k->optics = *optics;
   k->grid = *grid;
   k->flags = flags;
+  k->fluorescence = emission ? 1 : 0;
+  if (emission) k->emission = *emission;
   k->device = dev;
   k->n = grid->nx;
   k->nt = grid->nt;
@@ -702,6 +709,22 @@ ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, 
   }
   *out = k;
   return CTOF_OK;
+}
+
+}  // namespace
+
+ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, int flags, void* stream,
+                              ctof_kernel* out) {
+  return build_any(optics, nullptr, grid, flags, stream, out);
+}
+
+ctof_status ctof_build_kernel_fluorescence(const ctof_optics* excitation, const ctof_emission* emission,
+                                           const ctof_grid* grid, int flags, void* stream, ctof_kernel* out) {
+  if (!emission) {
+    if (out) *out = nullptr;
+    return CTOF_EINVAL;
+  }
+  return build_any(excitation, emission, grid, flags, stream, out);
 }
 
 ctof_status ctof_kernel_get_info(ctof_kernel k, ctof_kernel_info* info) {

@@ -12,6 +12,8 @@ struct ctof_kernel_s {
   ctof_optics optics;
   ctof_grid grid;
   int flags;
+  int fluorescence;        // 1: W is the fluorescence-mode kernel with `emission`
+  ctof_emission emission;
   int device;
 
   // geometry

@@ -24,6 +24,10 @@ class Optics(ctypes.Structure):
                 ("z0_mm", ctypes.c_double), ("clamp_r", ctypes.c_int)]
 
 
+class Emission(ctypes.Structure):
+    _fields_ = [("mua_mm", ctypes.c_double), ("musp_mm", ctypes.c_double), ("tau_ps", ctypes.c_double)]
+
+
 class GridSpec(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("nt", ctypes.c_int),
                 ("dx_mm", ctypes.c_double), ("dy_mm", ctypes.c_double), ("dz_mm", ctypes.c_double),
@@ -67,6 +71,9 @@ _P = ctypes.c_void_p
 _SIGNATURES = {
     "ctof_build_kernel": (ctypes.c_int, [ctypes.POINTER(Optics), ctypes.POINTER(GridSpec), ctypes.c_int, _P,
                                          ctypes.POINTER(_P)]),
+    "ctof_build_kernel_fluorescence": (ctypes.c_int, [ctypes.POINTER(Optics), ctypes.POINTER(Emission),
+                                                      ctypes.POINTER(GridSpec), ctypes.c_int, _P,
+                                                      ctypes.POINTER(_P)]),
     "ctof_kernel_destroy": (None, [_P]),
     "ctof_kernel_get_info": (ctypes.c_int, [_P, ctypes.POINTER(KernelInfo)]),
     "ctof_kernel_get_w": (ctypes.c_int, [_P, _P]),
@@ -140,6 +147,11 @@ def _dev_ptr(t, shape, name):
 
 def make_optics(mua=0.01, musp=1.0, n=1.4, z0=0.0, clamp_r=True):
     return Optics(float(mua), float(musp), float(n), float(z0), int(bool(clamp_r)))
+
+
+def make_emission(mua=0.005, musp=0.8, tau=0.0):
+    """Emission-wavelength optics [1/mm] and fluorescence lifetime [ps] of the fluorescence mode."""
+    return Emission(float(mua), float(musp), float(tau))
 
 
 def make_grid(n, nz, nt, dx, dz, z_first, dt, dy=None, mode="linear"):
@@ -253,14 +265,23 @@ def reconstruct_batch(kernels, ms, params, outs=None, stream=None):
 class Kernel:
     """A built sensitivity kernel (``ctof_kernel``) bound to the current CUDA device."""
 
-    def __init__(self, optics, grid, keep_w=False, stream=None):
+    def __init__(self, optics, grid, keep_w=False, stream=None, emission=None):
+        """emission: None for the absorption kernel, or an ``Emission`` (``make_emission``) for the
+        fluorescence-mode kernel (``optics`` then holds the excitation-wavelength optics)."""
         lib = load()
         self._lib = lib
         self.optics = optics
         self.grid = grid
+        self.emission = emission
         h = ctypes.c_void_p()
-        _check(lib.ctof_build_kernel(ctypes.byref(optics), ctypes.byref(grid), KEEP_W if keep_w else 0,
-                                     _stream_handle(stream), ctypes.byref(h)), "ctof_build_kernel")
+        flags = KEEP_W if keep_w else 0
+        if emission is None:
+            _check(lib.ctof_build_kernel(ctypes.byref(optics), ctypes.byref(grid), flags, _stream_handle(stream),
+                                         ctypes.byref(h)), "ctof_build_kernel")
+        else:
+            _check(lib.ctof_build_kernel_fluorescence(ctypes.byref(optics), ctypes.byref(emission),
+                                                      ctypes.byref(grid), flags, _stream_handle(stream),
+                                                      ctypes.byref(h)), "ctof_build_kernel_fluorescence")
         self._h = h
         info = KernelInfo()
         _check(lib.ctof_kernel_get_info(h, ctypes.byref(info)), "ctof_kernel_get_info")

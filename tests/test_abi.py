@@ -91,3 +91,18 @@ def test_learned_parameter_count_matches_oracle(lib):
     assert lib.ctof_learned_loss_grad(None, None, 1, None, None, None, None, None) != 0
     bad = ctof.LearnedOptions(0.0, 2, 0.0)  # data-consistency steps need a positive lambda
     assert lib.ctof_learned_create(3, p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(bad), ctypes.byref(out)) != 0
+
+
+def test_fluorescence_build_rejects_bad_emission(lib):
+    """Argument checks of ctof_build_kernel_fluorescence run before any device call."""
+    o = ctof.make_optics()
+    g = ctof.make_grid(32, 16, 64, 1.0, 1.0, 1.0, 50.0)
+    h = ctypes.c_void_p(1)
+    assert lib.ctof_build_kernel_fluorescence(ctypes.byref(o), None, ctypes.byref(g), 0, None,
+                                              ctypes.byref(h)) == ctof.EINVAL
+    assert h.value is None
+    for bad in (dict(mua=-0.1), dict(musp=0.0), dict(tau=-1.0), dict(tau=float("inf")), dict(mua=float("nan"))):
+        h = ctypes.c_void_p()
+        st = lib.ctof_build_kernel_fluorescence(ctypes.byref(o), ctypes.byref(ctof.make_emission(**bad)),
+                                                ctypes.byref(g), 0, None, ctypes.byref(h))
+        assert st == ctof.EINVAL, bad
