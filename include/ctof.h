@@ -166,6 +166,31 @@ typedef struct {
 ctof_status ctof_build_kernel_fluorescence(const ctof_optics* excitation, const ctof_emission* emission,
                                            const ctof_grid* grid, int flags, void* stream, ctof_kernel* out);
 
+/* Voxel-averaged kernel near the surface.  The time-domain forward model
+ * integrates J mu over the volume (Section 3, Eq. of m(r_d, r_s, t)); with mu
+ * constant on each voxel the exact weight of a voxel is the integral of J
+ * over it, of which the centre value times the volume is the midpoint rule.
+ * Near the surface and the source J varies strongly inside one voxel (the
+ * paper notes the diffusion form is least reliable there, Section 3), so
+ * the first `layers` depth layers take the voxel average, a tensor
+ * Gauss-Legendre rule of `nodes` points per axis over the voxel
+ * (centre +- dx/2, +- dy/2, +- dz/2; z_j is the layer centre). */
+typedef struct {
+  int layers;  /* 0..nz: depth layers, from the first, that are averaged (0 = none) */
+  int nodes;   /* 1..8 Gauss-Legendre nodes per axis (1 = the centre value) */
+} ctof_voxel_average;
+
+/* General kernel build: absorption (emission == NULL) or fluorescence mode,
+ * with (average != NULL) or without voxel averaging; otherwise as
+ * ctof_build_kernel / ctof_build_kernel_fluorescence.  Cost of the table
+ * build grows by nodes^3 on the averaged layers.  Errors: as those two,
+ * plus EINVAL for layers outside [0, nz], nodes outside [1, 8], or
+ * averaged layers reaching above the surface (z_first < dz/2 with
+ * layers > 0). */
+ctof_status ctof_build_kernel_ex(const ctof_optics* optics, const ctof_emission* emission,
+                                 const ctof_voxel_average* average, const ctof_grid* grid, int flags,
+                                 void* stream, ctof_kernel* out);
+
 void ctof_kernel_destroy(ctof_kernel k);
 
 ctof_status ctof_kernel_get_info(ctof_kernel k, ctof_kernel_info* info);

@@ -82,6 +82,54 @@ def _mirror(quad, n):
     return quad[:, :, idx][:, :, :, idx]
 
 
+def voxel_average(point, qx, qy, z, grid, nodes):
+    """(1/V) int over the voxel of point(rho(x, y), z') dV, tensor Gauss-Legendre rule.
+
+    The voxel at lateral offset (qx dx, qy dy) from the scan point and centre
+    depth z spans +-dx/2, +-dy/2, +-dz/2 around that centre; ``nodes``
+    Gauss-Legendre nodes per axis (weights sum to 2 on [-1, 1], so the
+    average divides by 8).  point(rho, z) may return extra leading axes.
+    """
+    x, w = np.polynomial.legendre.leggauss(nodes)
+    acc = 0.0
+    for a in range(nodes):
+        for b in range(nodes):
+            for c in range(nodes):
+                px = qx * grid.dx + 0.5 * grid.dx * x[a]
+                py = qy * grid.dy + 0.5 * grid.dy * x[b]
+                pz = z + 0.5 * grid.dz * x[c]
+                acc = acc + w[a] * w[b] * w[c] / 8.0 * point(np.sqrt(px * px + py * py), pz)
+    return acc
+
+
+def kernel_offsets_averaged(grid, med, layers, nodes, emission=None):
+    """Kernel with the first ``layers`` depth layers averaged over the voxel volume.
+
+    Reading of the time-domain forward model m = int_v J mu dr_v with mu
+    constant on each voxel: the exact voxel weight is the integral of J over
+    the voxel, of which the centre value times the volume is the midpoint
+    rule.  Near the surface (and the source) J varies strongly inside one
+    voxel, so those layers take the voxel average with ``nodes`` Gauss-Legendre
+    nodes per axis; deeper layers keep the centre value.  ``emission`` = None
+    for the absorption kernel (``binned_conv``), else (med_em, tau) for the
+    fluorescence kernel (``binned_fluorescence``).
+    """
+    n = grid.n
+    if emission is None:
+        point = lambda rho, z: binned_conv(rho, z, grid.nt, grid.dt, med)
+    else:
+        med_em, tau = emission
+        point = lambda rho, z: binned_fluorescence(rho, z, grid.nt, grid.dt, med, med_em, tau)
+    a = np.arange(n)
+    qx, qy = a[None, :], a[:, None]
+    rho = np.sqrt((qx * grid.dx) ** 2 + (qy * grid.dy) ** 2)
+    z = grid.depths[:, None, None]
+    quad = point(rho[None, :, :], z)  # [T][Z][qy][qx]
+    for j in range(min(layers, grid.nz)):
+        quad[:, j] = voxel_average(point, qx, qy, grid.depths[j], grid, nodes)
+    return _mirror(quad * grid.voxel_volume, n)
+
+
 def kernel_offsets_fluorescence(grid, med_ex, med_em, tau):
     """Fluorescence-mode kernel on the offset grid (same layout as ``kernel_offsets``).
 

@@ -35,69 +35,101 @@ struct PhysParams {
   double gl_x[8], gl_w[8];
 };
 
+// Voxel averaging of the first `layers` depth layers: the voxel's weight is the
+// integral of the kernel over the voxel (the time-domain forward model
+// integrates J mu over the volume, mu constant per voxel), taken with a tensor
+// Gauss-Legendre rule of `nodes` points per axis around the voxel centre; the
+// other layers keep the centre value (the midpoint rule).
+struct AvgParams {
+  int layers, nodes;
+  double x[8], w[8];  // nodes and weights on [-1, 1]
+};
+
+// Bin integral of (Phi0 (*) R)(rho, z, t) over bin kbin (32-node composite rule).
+__device__ double abs_point_bin(double rho2, double z, int kbin, const PhysParams& prm) {
+  double r[4];
+  r[0] = sqrt(rho2 + (z - prm.z0) * (z - prm.z0));
+  r[1] = sqrt(rho2 + (z + prm.z0 + 2.0 * prm.zb) * (z + prm.z0 + 2.0 * prm.zb));
+  r[2] = sqrt(rho2 + z * z);
+  r[3] = sqrt(rho2 + (z + 2.0 * prm.zb) * (z + 2.0 * prm.zb));
+#pragma unroll
+  for (int i = 0; i < 4; ++i) r[i] = fmax(r[i], prm.rmin);
+  // four source/detector image pairs (i in {1,2}, j in {3,4})
+  double pre[4], a[4], a2[4], rj[4];
+  const double zz[2] = {z, z + 2.0 * prm.zb};
+  const double pi = 3.14159265358979323846;
+#pragma unroll
+  for (int ii = 0; ii < 2; ++ii) {
+#pragma unroll
+    for (int jj = 0; jj < 2; ++jj) {
+      const int e = ii * 2 + jj;
+      const double ri = r[ii], rjj = r[2 + jj];
+      pre[e] = (ii == 0 ? 1.0 : -1.0) * zz[jj] / (16.0 * pi * pi * prm.D * ri * rjj * rjj * rjj);
+      a[e] = ri + rjj;
+      a2[e] = a[e] * a[e];
+      rj[e] = rjj;
+    }
+  }
+  const double base_c = 1.0 / (2.0 * sqrt(pi * prm.kappa));
+  const double hsub = prm.dt * 0.25;
+  const double muac = prm.mua * prm.c;
+  double acc = 0.0;
+  for (int s = 0; s < 4; ++s) {
+    const double ta = kbin * prm.dt + s * hsub;
+#pragma unroll
+    for (int gi = 0; gi < 8; ++gi) {
+      const double t = ta + 0.5 * hsub * (prm.gl_x[gi] + 1.0);
+      const double inv4 = 1.0 / (4.0 * prm.kappa * t);
+      double val = 0.0;
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const double arg = -a2[e] * inv4 - muac * t;
+        if (arg > -745.0) val += pre[e] * exp(arg) * (a[e] + rj[e] * (2.0 * a2[e] * inv4 - 1.0));
+      }
+      acc += 0.5 * hsub * prm.gl_w[gi] * base_c * val / (t * sqrt(t));
+    }
+  }
+  return acc;
+}
+
+// (qy, qx) of quadrant pair index pr (lower triangle when symmetric, else row-major)
+__device__ __forceinline__ void pair_of(long long pr, int q, int symmetric, int& qy, int& qx) {
+  if (symmetric) {
+    qy = (int)((sqrt(8.0 * (double)pr + 1.0) - 1.0) * 0.5);
+    while ((long long)(qy + 1) * (qy + 2) / 2 <= pr) ++qy;
+    while ((long long)qy * (qy + 1) / 2 > pr) --qy;
+    qx = (int)(pr - (long long)qy * (qy + 1) / 2);
+  } else {
+    qy = (int)(pr / q);
+    qx = (int)(pr - (long long)qy * q);
+  }
+}
+
 __global__ void k_w_quadrant(double* __restrict__ w, int t0, int tcount, int nz, int q, int symmetric,
-                             PhysParams prm) {
+                             PhysParams prm, AvgParams av) {
   const long long npairs = symmetric ? (long long)q * (q + 1) / 2 : (long long)q * q;
   const long long total = npairs * nz;
   for (long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x; gid < total;
        gid += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(gid / npairs);
-    const long long pr = gid - (long long)j * npairs;
     int qy, qx;
-    if (symmetric) {
-      qy = (int)((sqrt(8.0 * (double)pr + 1.0) - 1.0) * 0.5);
-      while ((long long)(qy + 1) * (qy + 2) / 2 <= pr) ++qy;
-      while ((long long)qy * (qy + 1) / 2 > pr) --qy;
-      qx = (int)(pr - (long long)qy * (qy + 1) / 2);
-    } else {
-      qy = (int)(pr / q);
-      qx = (int)(pr - (long long)qy * q);
-    }
-    const double rho2 = (qx * prm.dx) * (qx * prm.dx) + (qy * prm.dy) * (qy * prm.dy);
+    pair_of(gid - (long long)j * npairs, q, symmetric, qy, qx);
     const double z = prm.zfirst + j * prm.dz;
-    double r[4];
-    r[0] = sqrt(rho2 + (z - prm.z0) * (z - prm.z0));
-    r[1] = sqrt(rho2 + (z + prm.z0 + 2.0 * prm.zb) * (z + prm.z0 + 2.0 * prm.zb));
-    r[2] = sqrt(rho2 + z * z);
-    r[3] = sqrt(rho2 + (z + 2.0 * prm.zb) * (z + 2.0 * prm.zb));
-#pragma unroll
-    for (int i = 0; i < 4; ++i) r[i] = fmax(r[i], prm.rmin);
-    // four source/detector image pairs (i in {1,2}, j in {3,4})
-    double pre[4], a[4], a2[4], rj[4];
-    const double zz[2] = {z, z + 2.0 * prm.zb};
-    const double pi = 3.14159265358979323846;
-#pragma unroll
-    for (int ii = 0; ii < 2; ++ii) {
-#pragma unroll
-      for (int jj = 0; jj < 2; ++jj) {
-        const int e = ii * 2 + jj;
-        const double ri = r[ii], rjj = r[2 + jj];
-        pre[e] = (ii == 0 ? 1.0 : -1.0) * zz[jj] / (16.0 * pi * pi * prm.D * ri * rjj * rjj * rjj);
-        a[e] = ri + rjj;
-        a2[e] = a[e] * a[e];
-        rj[e] = rjj;
-      }
-    }
-    const double base_c = 1.0 / (2.0 * sqrt(pi * prm.kappa));
-    const double hsub = prm.dt * 0.25;
-    const double muac = prm.mua * prm.c;
+    const int ns = j < av.layers ? av.nodes : 1;
     for (int tk = 0; tk < tcount; ++tk) {
       const int kbin = t0 + tk;
       double acc = 0.0;
-      for (int s = 0; s < 4; ++s) {
-        const double ta = kbin * prm.dt + s * hsub;
-#pragma unroll
-        for (int gi = 0; gi < 8; ++gi) {
-          const double t = ta + 0.5 * hsub * (prm.gl_x[gi] + 1.0);
-          const double inv4 = 1.0 / (4.0 * prm.kappa * t);
-          double val = 0.0;
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const double arg = -a2[e] * inv4 - muac * t;
-            if (arg > -745.0) val += pre[e] * exp(arg) * (a[e] + rj[e] * (2.0 * a2[e] * inv4 - 1.0));
-          }
-          acc += 0.5 * hsub * prm.gl_w[gi] * base_c * val / (t * sqrt(t));
-        }
+      if (ns == 1) {
+        acc = abs_point_bin((qx * prm.dx) * (qx * prm.dx) + (qy * prm.dy) * (qy * prm.dy), z, kbin, prm);
+      } else {
+        for (int c = 0; c < ns; ++c)
+          for (int b = 0; b < ns; ++b)
+            for (int a = 0; a < ns; ++a) {
+              const double px = qx * prm.dx + 0.5 * prm.dx * av.x[a];
+              const double py = qy * prm.dy + 0.5 * prm.dy * av.x[b];
+              const double pz = z + 0.5 * prm.dz * av.x[c];
+              acc += av.w[a] * av.w[b] * av.w[c] * 0.125 * abs_point_bin(px * px + py * py, pz, kbin, prm);
+            }
       }
       acc *= prm.vol;
       w[(((size_t)tk * nz + j) * q + qy) * q + qx] = acc;
@@ -163,8 +195,12 @@ __device__ __forceinline__ cd c_exp_neg(double x, cd a) {
   return {e * cs, -e * sn};
 }
 
-__device__ double fl_cumulative(double t, double r1, double r2, double r3, double r4, double z, const FluoParams& p) {
+__device__ double fl_cumulative_at(double t, double rho2, double z, const FluoParams& p) {
   const double pi = 3.14159265358979323846;
+  const double r1 = fmax(sqrt(rho2 + (z - p.z0) * (z - p.z0)), p.rmin);
+  const double r2 = fmax(sqrt(rho2 + (z + p.z0 + 2.0 * p.zb_ex) * (z + p.z0 + 2.0 * p.zb_ex)), p.rmin);
+  const double r3 = fmax(sqrt(rho2 + z * z), p.rmin);
+  const double r4 = fmax(sqrt(rho2 + (z + 2.0 * p.zb_em) * (z + 2.0 * p.zb_em)), p.rmin);
   const double r = 2.0 * TALBOT_M / (5.0 * t);
   const double z4 = z + 2.0 * p.zb_em;
   double acc = 0.0;
@@ -187,33 +223,36 @@ __device__ double fl_cumulative(double t, double r1, double r2, double r3, doubl
   return r / TALBOT_M * acc;
 }
 
+// Cumulative response at time t, voxel-averaged when ns > 1 (the average of
+// the cumulative is the cumulative of the average).
+__device__ double fl_cumulative(double t, int qx, int qy, double z, int ns, const FluoParams& p, const AvgParams& av) {
+  if (ns == 1) return fl_cumulative_at(t, (qx * p.dx) * (qx * p.dx) + (qy * p.dy) * (qy * p.dy), z, p);
+  double acc = 0.0;
+  for (int c = 0; c < ns; ++c)
+    for (int b = 0; b < ns; ++b)
+      for (int a = 0; a < ns; ++a) {
+        const double px = qx * p.dx + 0.5 * p.dx * av.x[a];
+        const double py = qy * p.dy + 0.5 * p.dy * av.x[b];
+        const double pz = z + 0.5 * p.dz * av.x[c];
+        acc += av.w[a] * av.w[b] * av.w[c] * 0.125 * fl_cumulative_at(t, px * px + py * py, pz, p);
+      }
+  return acc;
+}
+
 __global__ void k_w_quadrant_fl(double* __restrict__ w, int t0, int tcount, int nz, int q, int symmetric,
-                                FluoParams prm) {
+                                FluoParams prm, AvgParams av) {
   const long long npairs = symmetric ? (long long)q * (q + 1) / 2 : (long long)q * q;
   const long long total = npairs * nz;
   for (long long gid = blockIdx.x * (long long)blockDim.x + threadIdx.x; gid < total;
        gid += (long long)gridDim.x * blockDim.x) {
     const int j = (int)(gid / npairs);
-    const long long pr = gid - (long long)j * npairs;
     int qy, qx;
-    if (symmetric) {
-      qy = (int)((sqrt(8.0 * (double)pr + 1.0) - 1.0) * 0.5);
-      while ((long long)(qy + 1) * (qy + 2) / 2 <= pr) ++qy;
-      while ((long long)qy * (qy + 1) / 2 > pr) --qy;
-      qx = (int)(pr - (long long)qy * (qy + 1) / 2);
-    } else {
-      qy = (int)(pr / q);
-      qx = (int)(pr - (long long)qy * q);
-    }
-    const double rho2 = (qx * prm.dx) * (qx * prm.dx) + (qy * prm.dy) * (qy * prm.dy);
+    pair_of(gid - (long long)j * npairs, q, symmetric, qy, qx);
     const double z = prm.zfirst + j * prm.dz;
-    const double r1 = fmax(sqrt(rho2 + (z - prm.z0) * (z - prm.z0)), prm.rmin);
-    const double r2 = fmax(sqrt(rho2 + (z + prm.z0 + 2.0 * prm.zb_ex) * (z + prm.z0 + 2.0 * prm.zb_ex)), prm.rmin);
-    const double r3 = fmax(sqrt(rho2 + z * z), prm.rmin);
-    const double r4 = fmax(sqrt(rho2 + (z + 2.0 * prm.zb_em) * (z + 2.0 * prm.zb_em)), prm.rmin);
-    double prev = t0 > 0 ? fl_cumulative(t0 * prm.dt, r1, r2, r3, r4, z, prm) : 0.0;
+    const int ns = j < av.layers ? av.nodes : 1;
+    double prev = t0 > 0 ? fl_cumulative(t0 * prm.dt, qx, qy, z, ns, prm, av) : 0.0;
     for (int tk = 0; tk < tcount; ++tk) {
-      const double cur = fl_cumulative((t0 + tk + 1) * prm.dt, r1, r2, r3, r4, z, prm);
+      const double cur = fl_cumulative((t0 + tk + 1) * prm.dt, qx, qy, z, ns, prm, av);
       const double acc = (cur - prev) * prm.vol;
       prev = cur;
       w[(((size_t)tk * nz + j) * q + qy) * q + qx] = acc;
@@ -586,6 +625,11 @@ ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st) {
   }
   FluoParams fprm;
   if (k->fluorescence) make_fluo_params(k, fprm);
+  AvgParams av;
+  av.layers = k->avg.layers;
+  av.nodes = k->avg.layers > 0 ? k->avg.nodes : 1;
+  for (int i = 0; i < 8; ++i) av.x[i] = av.w[i] = 0.0;
+  if (av.nodes > 1) gauss_legendre(av.nodes, av.x, av.w);
 
   // ---- device temporaries, processed in chunks of time bins ----
   const long long planes = (long long)nt * nz;
@@ -616,9 +660,9 @@ ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st) {
       int blocks = (int)((work + 127) / 128);
       if (blocks > 152 * 64) blocks = 152 * 64;
       if (k->fluorescence) {
-        k_w_quadrant_fl<<<blocks, 128, 0, st>>>(d_wq.as<double>(), t0, tc, nz, q, k->symmetric, fprm);
+        k_w_quadrant_fl<<<blocks, 128, 0, st>>>(d_wq.as<double>(), t0, tc, nz, q, k->symmetric, fprm, av);
       } else {
-        k_w_quadrant<<<blocks, 128, 0, st>>>(d_wq.as<double>(), t0, tc, nz, q, k->symmetric, prm);
+        k_w_quadrant<<<blocks, 128, 0, st>>>(d_wq.as<double>(), t0, tc, nz, q, k->symmetric, prm, av);
       }
       CTOF_CUDA_TRY(cudaGetLastError());
     }

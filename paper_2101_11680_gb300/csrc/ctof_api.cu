@@ -578,14 +578,19 @@ void ctof_kernel_destroy(ctof_kernel k) {
 
 namespace {
 
-ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, const ctof_grid* grid, int flags,
-                      void* stream, ctof_kernel* out) {
+ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, const ctof_voxel_average* average,
+                      const ctof_grid* grid, int flags, void* stream, ctof_kernel* out) {
   if (!out) return CTOF_EINVAL;
   *out = nullptr;
   CTOF_TRY(validate(optics, grid));
   if (emission && !(isfinite(emission->mua_mm) && emission->mua_mm >= 0.0 && finite_pos(emission->musp_mm) &&
                     isfinite(emission->tau_ps) && emission->tau_ps >= 0.0))
     return CTOF_EINVAL;
+  if (average) {
+    if (average->layers < 0 || average->layers > grid->nz || average->nodes < 1 || average->nodes > 8)
+      return CTOF_EINVAL;
+    if (average->layers > 0 && grid->z_first_mm < 0.5 * grid->dz_mm) return CTOF_EINVAL;
+  }
   if (flags & ~CTOF_KEEP_W) return CTOF_EINVAL;
   int dev = 0;
   CTOF_CUDA_TRY(cudaGetDevice(&dev));
@@ -596,6 +601,8 @@ ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, 
   k->flags = flags;
   k->fluorescence = emission ? 1 : 0;
   if (emission) k->emission = *emission;
+  k->avg.layers = average ? average->layers : 0;
+  k->avg.nodes = average ? average->nodes : 1;
   k->device = dev;
   k->n = grid->nx;
   k->nt = grid->nt;
@@ -715,7 +722,13 @@ ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, 
 
 ctof_status ctof_build_kernel(const ctof_optics* optics, const ctof_grid* grid, int flags, void* stream,
                               ctof_kernel* out) {
-  return build_any(optics, nullptr, grid, flags, stream, out);
+  return build_any(optics, nullptr, nullptr, grid, flags, stream, out);
+}
+
+ctof_status ctof_build_kernel_ex(const ctof_optics* optics, const ctof_emission* emission,
+                                 const ctof_voxel_average* average, const ctof_grid* grid, int flags, void* stream,
+                                 ctof_kernel* out) {
+  return build_any(optics, emission, average, grid, flags, stream, out);
 }
 
 ctof_status ctof_build_kernel_fluorescence(const ctof_optics* excitation, const ctof_emission* emission,
@@ -724,7 +737,7 @@ ctof_status ctof_build_kernel_fluorescence(const ctof_optics* excitation, const 
     if (out) *out = nullptr;
     return CTOF_EINVAL;
   }
-  return build_any(excitation, emission, grid, flags, stream, out);
+  return build_any(excitation, emission, nullptr, grid, flags, stream, out);
 }
 
 ctof_status ctof_kernel_get_info(ctof_kernel k, ctof_kernel_info* info) {

@@ -14,6 +14,7 @@ struct ctof_kernel_s {
   int flags;
   int fluorescence;        // 1: W is the fluorescence-mode kernel with `emission`
   ctof_emission emission;
+  ctof_voxel_average avg;  // layers = 0: centre values everywhere
   int device;
 
   // geometry

@@ -28,6 +28,10 @@ class Emission(ctypes.Structure):
     _fields_ = [("mua_mm", ctypes.c_double), ("musp_mm", ctypes.c_double), ("tau_ps", ctypes.c_double)]
 
 
+class VoxelAverage(ctypes.Structure):
+    _fields_ = [("layers", ctypes.c_int), ("nodes", ctypes.c_int)]
+
+
 class GridSpec(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int), ("nt", ctypes.c_int),
                 ("dx_mm", ctypes.c_double), ("dy_mm", ctypes.c_double), ("dz_mm", ctypes.c_double),
@@ -74,6 +78,9 @@ _SIGNATURES = {
     "ctof_build_kernel_fluorescence": (ctypes.c_int, [ctypes.POINTER(Optics), ctypes.POINTER(Emission),
                                                       ctypes.POINTER(GridSpec), ctypes.c_int, _P,
                                                       ctypes.POINTER(_P)]),
+    "ctof_build_kernel_ex": (ctypes.c_int, [ctypes.POINTER(Optics), ctypes.POINTER(Emission),
+                                            ctypes.POINTER(VoxelAverage), ctypes.POINTER(GridSpec), ctypes.c_int,
+                                            _P, ctypes.POINTER(_P)]),
     "ctof_kernel_destroy": (None, [_P]),
     "ctof_kernel_get_info": (ctypes.c_int, [_P, ctypes.POINTER(KernelInfo)]),
     "ctof_kernel_get_w": (ctypes.c_int, [_P, _P]),
@@ -265,9 +272,11 @@ def reconstruct_batch(kernels, ms, params, outs=None, stream=None):
 class Kernel:
     """A built sensitivity kernel (``ctof_kernel``) bound to the current CUDA device."""
 
-    def __init__(self, optics, grid, keep_w=False, stream=None, emission=None):
+    def __init__(self, optics, grid, keep_w=False, stream=None, emission=None, average=None):
         """emission: None for the absorption kernel, or an ``Emission`` (``make_emission``) for the
-        fluorescence-mode kernel (``optics`` then holds the excitation-wavelength optics)."""
+        fluorescence-mode kernel (``optics`` then holds the excitation-wavelength optics).
+        average: None, or (layers, nodes) to average the first ``layers`` depth layers over the voxel
+        with ``nodes`` Gauss-Legendre points per axis."""
         lib = load()
         self._lib = lib
         self.optics = optics
@@ -275,7 +284,13 @@ class Kernel:
         self.emission = emission
         h = ctypes.c_void_p()
         flags = KEEP_W if keep_w else 0
-        if emission is None:
+        self.average = average
+        if average is not None:
+            av = VoxelAverage(int(average[0]), int(average[1]))
+            _check(lib.ctof_build_kernel_ex(ctypes.byref(optics), ctypes.byref(emission) if emission is not None else None,
+                                            ctypes.byref(av), ctypes.byref(grid), flags, _stream_handle(stream),
+                                            ctypes.byref(h)), "ctof_build_kernel_ex")
+        elif emission is None:
             _check(lib.ctof_build_kernel(ctypes.byref(optics), ctypes.byref(grid), flags, _stream_handle(stream),
                                          ctypes.byref(h)), "ctof_build_kernel")
         else:

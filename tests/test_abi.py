@@ -106,3 +106,16 @@ def test_fluorescence_build_rejects_bad_emission(lib):
         st = lib.ctof_build_kernel_fluorescence(ctypes.byref(o), ctypes.byref(ctof.make_emission(**bad)),
                                                 ctypes.byref(g), 0, None, ctypes.byref(h))
         assert st == ctof.EINVAL, bad
+
+
+def test_build_ex_rejects_bad_average(lib):
+    """Voxel-averaging options are checked before any device call."""
+    o = ctof.make_optics()
+    g = ctof.make_grid(32, 16, 64, 1.0, 1.0, 1.0, 50.0)
+    shallow = ctof.make_grid(32, 16, 64, 1.0, 1.0, 0.4, 50.0)  # top layer reaches above the surface
+    for grid, layers, nodes in ((g, -1, 4), (g, 17, 4), (g, 2, 0), (g, 2, 9), (shallow, 1, 4)):
+        h = ctypes.c_void_p()
+        av = ctof.VoxelAverage(layers, nodes)
+        st = lib.ctof_build_kernel_ex(ctypes.byref(o), None, ctypes.byref(av), ctypes.byref(grid), 0, None,
+                                      ctypes.byref(h))
+        assert st == ctof.EINVAL, (layers, nodes)
