@@ -106,7 +106,9 @@ def test_fluorescence_tikhonov_cfg1():
 
 def test_lifetime_delays_the_response():
     """Same optics as the absorption kernel and tau > 0: every column keeps its total over a
-    long window but moves to later bins."""
+    long window and its mean arrival time grows by tau.  Means are taken at the bin centres,
+    which misplaces a response that sits inside one bin by up to half a bin (the tau = 0
+    response of the shallow voxels is a few ps wide), hence the bound dt/2."""
     kw = dict(n=8, nz=3, nt=300, dx=1.0, dz=1.0, z_first=1.0, dt=50.0)
     grid = ctof.make_grid(kw["n"], kw["nz"], kw["nt"], kw["dx"], kw["dz"], kw["z_first"], kw["dt"])
     opt = ctof.make_optics(**CFG1_OPTICS)
@@ -119,4 +121,5 @@ def test_lifetime_delays_the_response():
     assert np.allclose(s1, s0, rtol=1e-6)
     m0 = np.tensordot(t, w0, axes=1) / s0
     m1 = np.tensordot(t, w1, axes=1) / s1
-    assert np.allclose(m1 - m0, 800.0, rtol=2e-3)
+    assert np.abs(m1 - m0 - 800.0).max() <= 0.5 * kw["dt"]
+    assert np.all(m1 > m0 + 700.0)
