@@ -52,6 +52,7 @@ CONFIGS = {
                  workload="32x32 scan @1 mm, 32x32x16 voxels (1-16 mm), 64 bins x 50 ps, 100 ADMM iterations"),
 }
 OPTICS = dict(mua=0.01, musp=1.0, n=1.4)
+FLUORESCENCE = dict(mua=0.005, musp=0.8, tau=500.0)  # emission optics [1/mm] and lifetime [ps]
 
 
 def replica_seed(seed, rank):
@@ -550,6 +551,12 @@ def main():
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--lateral", type=int, default=None,
                     help="override the lateral size (a smaller case of the same per-class kernels, for profiling)")
+    ap.add_argument("--kernel", default="absorption", choices=["absorption", "fluorescence"],
+                    help="default-config kernel: absorption, or the fluorescence mode (emission mua 0.005/mm, "
+                         "musp' 0.8/mm, lifetime 500 ps); the reconstruction step is the same code")
+    ap.add_argument("--average", default=None,
+                    help="LAYERS,NODES: average the first LAYERS depth layers over the voxel with NODES "
+                         "Gauss-Legendre points per axis (kernel build only)")
     ap.add_argument("--solver", default="admm", choices=["admm", "fista"],
                     help="default-config solver: ADMM-TV (the benchmark) or the paper's FISTA-L1")
     args = ap.parse_args()
@@ -591,10 +598,22 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
     B.build()
 
+    emission = None
+    average = None
+    kernel_desc = "absorption"
+    if args.kernel == "fluorescence":
+        emission = ctof.make_emission(**FLUORESCENCE)
+        kernel_desc = "fluorescence (emission mua %g/mm, musp' %g/mm, lifetime %g ps)" % (
+            FLUORESCENCE["mua"], FLUORESCENCE["musp"], FLUORESCENCE["tau"])
+    if args.average:
+        layers, nodes = (int(v) for v in args.average.split(","))
+        average = (layers, nodes)
+        kernel_desc += ", voxel-averaged first %d layers (%d^3 nodes)" % (layers, nodes)
     t0 = time.perf_counter()
     kern = ctof.Kernel(ctof.make_optics(**OPTICS),
                        ctof.make_grid(cfg["n"], cfg["nz"], cfg["nt"], cfg["dx"], cfg["dz"], cfg["z_first"],
-                                      cfg["dt"]))
+                                      cfg["dt"]), emission=emission, average=average)
+    torch.cuda.synchronize()
     build_s = time.perf_counter() - t0
     info = kern.info
     count = args.steps + args.warmup
@@ -671,7 +690,7 @@ def main():
                    "iters": cfg["iters"], "parallelism": "replicas" if world > 1 else "single",
                    "l2": "inputs larger than L2 (W_hat %.0f MB streamed per iteration)"
                          % (info.n_class * cfg["nt"] * cfg["nz"] * 4 / 1e6),
-                   "kernel_build_s": round(build_s, 3)},
+                   "kernel": kernel_desc, "kernel_build_s": round(build_s, 3)},
         "roofline": {"bound": "hbm", "kernel": "k_contract_admm", "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_contract_ms,
@@ -684,7 +703,7 @@ def main():
         "clocks": clk,
         "quality": {"rel_l2_vs_phantom_mean": float(np.mean(errs))},
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline and emission is None and average is None:
         line["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0:
         print(json.dumps(line), flush=True)
