@@ -224,6 +224,22 @@ ctof_status ctof_adjoint(ctof_kernel k, const float* d_m, float* d_vol, void* st
  * (else EUNSUPPORTED).  The adjoint A^T S^T y (S^T = S) uses a workspace of
  * the handle.  Asynchronous. */
 ctof_status ctof_forward_multiplexed(ctof_kernel k, const float* d_mu, float* d_y, void* stream);
+
+/* Per-frequency contractions of Eq. 11 in the lateral Fourier domain for
+ * nvol volumes at once, on frequency-major half-plane spectra (device
+ * buffers, complex as interleaved float pairs, f = ky * (P/2+1) + kx):
+ *   forward  d_out[v][f][t] = sum_z W_hat(f, t, z) d_in[v][f][z],
+ *            d_in [nvol][n_freq][ldz], d_out [nvol][n_freq][ldt];
+ *   adjoint  d_out[v][f][z] = sum_t W_hat(f, t, z) d_in[v][f][t],
+ *            d_in [nvol][n_freq][ldt], d_out [nvol][n_freq][ldz];
+ * ldz = nz rounded up to 8, ldt = nt rounded up to 8 (complex entries).
+ * Input entries beyond nz / nt are ignored, output entries beyond them are
+ * not written.  From 4 volumes on, 16 volumes and one frequency class form
+ * one 128-wide tcgen05 GEMM (3xTF32, FP32-level accuracy); fewer volumes take
+ * the FP32 CUDA-core path.  Asynchronous on `stream`.  Errors: EINVAL (null
+ * pointer, nvol < 1), ECUDA. */
+ctof_status ctof_contract_forward_batch(ctof_kernel k, int nvol, const float* d_in, float* d_out, void* stream);
+ctof_status ctof_contract_adjoint_batch(ctof_kernel k, int nvol, const float* d_in, float* d_out, void* stream);
 ctof_status ctof_adjoint_multiplexed(ctof_kernel k, const float* d_y, float* d_vol, void* stream);
 
 /* Reconstruct mu from m with the chosen solver: d_m [nt][ny][nx] ->

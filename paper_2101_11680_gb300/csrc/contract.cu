@@ -371,14 +371,21 @@ ctof_status contract_tikhonov(const ctof_kernel_s* k, const float* hinv, const f
   return contract_tikhonov_batch(k, 1, hinv, m_hat, x_hat, st);
 }
 
+// From this many volumes on, the batched forward and adjoint run as one
+// 128-wide tensor-core GEMM per frequency class (contract_tc.cu); below it the
+// per-volume FP32 path above streams the class block once for all volumes.
+constexpr int TC_MIN_VOLUMES = 4;
+
 ctof_status contract_forward_batch(const ctof_kernel_s* k, int nvol, const float2* in_z, float2* out_t,
                                    cudaStream_t st) {
+  if (nvol >= TC_MIN_VOLUMES) return contract_tc_forward(k, nvol, in_z, out_t, st);
   return launch<MODE_FWD>(k, nvol, in_z, k->ldz, (size_t)k->nf * k->ldz, out_t, k->ldt, (size_t)k->nf * k->ldt,
                           nullptr, st);
 }
 
 ctof_status contract_adjoint_batch(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z,
                                    cudaStream_t st) {
+  if (nvol >= TC_MIN_VOLUMES) return contract_tc_adjoint(k, nvol, in_t, out_z, st);
   return launch<MODE_ADJ>(k, nvol, in_t, k->ldt, (size_t)k->nf * k->ldt, out_z, k->ldz, (size_t)k->nf * k->ldz,
                           nullptr, st);
 }

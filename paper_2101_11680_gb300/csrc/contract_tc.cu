@@ -1,0 +1,358 @@
+// Batched per-frequency contractions on the 5th-generation tensor cores
+// (tcgen05, TMEM accumulators): the forward M_hat(f, t) = sum_z W_hat(f, t, z)
+// mu_hat(f, z) and the adjoint V_hat(f, z) = sum_t W_hat(f, t, z) r_hat(f, t)
+// of Eq. 11 in the lateral Fourier domain, for many volumes that share one
+// kernel.  A frequency class (up to 4 frequencies with the same real T x Z
+// block) and 16 volumes give 16 x 4 x 2 = 128 real right-hand sides, so each
+// class is one GEMM with a 128-wide side:
+//   forward  D[t][n] = sum_z W[t][z] X[n][z]   M = 128 rows of t, N = 128, K = z
+//   adjoint  D[n][z] = sum_t C[n][t] W[t][z]   M = 128,  N = Z (to 16), K = t
+// (n = 8 v + 2 m + c: volume v of the chunk, member m, real/imaginary c).
+// Operands are staged in shared memory in the no-swizzle K-major layout of
+// umma.cuh, each split into a TF32 high part and an FP32 remainder; three
+// MMAs per K step (lo*hi + hi*lo + hi*hi) keep FP32-level accuracy.  The
+// adjoint's W^T is formed by the staging itself (4 x 4 register transposes),
+// so W_hat is read from its one [class][t][z] table.  One elected thread issues
+// the MMAs and commits them to an mbarrier; the CTA waits on it with a
+// bounded poll (a timeout sets the handle's timeout flag), then every warp
+// reads its 32-lane quarter of TMEM for the epilogue.  Persistent CTAs walk
+// the classes; two fit on an SM when their shared memory allows, so one
+// CTA's staging overlaps the other's MMAs and stores.
+#include <cuda_runtime.h>
+
+#include "ctof_internal.h"
+#include "umma.cuh"
+
+namespace {
+
+constexpr int TC_THREADS = 256;
+constexpr int VB = 16;         // volumes per chunk
+constexpr int NR = 8 * VB;     // right-hand sides per chunk (the 128-wide GEMM side)
+constexpr int TCH = 64;        // adjoint: t values per staged K chunk
+constexpr long long MAX_POLLS = 1ll << 24;
+
+struct TcPlan {
+  int nt, nz, z4, zK, zN, tK, tc;
+  int off_ahi, off_alo, off_bhi, off_blo, off_bar, total;
+  uint32_t ncols;  // TMEM columns
+};
+
+inline int rup(int x, int m) { return (x + m - 1) / m * m; }
+
+// Forward: A = W rows (128 per M tile) x zK, B = X rows (128) x zK.
+TcPlan plan_fwd(int nt, int nz) {
+  TcPlan p{};
+  p.nt = nt;
+  p.nz = nz;
+  p.z4 = rup(nz, 4);
+  p.zK = rup(nz, 8);
+  const int tile = 128 * p.zK * 4;
+  p.off_ahi = 0;
+  p.off_alo = tile;
+  p.off_bhi = 2 * tile;
+  p.off_blo = 3 * tile;
+  p.off_bar = 4 * tile;
+  p.total = p.off_bar + 64;
+  p.ncols = 128;
+  return p;
+}
+
+// Adjoint: A = C rows (128) x tc, B = W^T rows (zN) x tc, per K chunk of tc t values.
+TcPlan plan_adj(int nt, int nz) {
+  TcPlan p{};
+  p.nt = nt;
+  p.nz = nz;
+  p.z4 = rup(nz, 4);
+  p.zN = rup(nz, 16);
+  p.tK = rup(nt, 8);
+  p.tc = p.tK < TCH ? p.tK : TCH;
+  const int ta = 128 * p.tc * 4, tb = p.zN * p.tc * 4;
+  p.off_ahi = 0;
+  p.off_alo = ta;
+  p.off_bhi = 2 * ta;
+  p.off_blo = 2 * ta + tb;
+  p.off_bar = 2 * ta + 2 * tb;
+  p.total = p.off_bar + 64;
+  p.ncols = p.zN <= 32 ? 32 : 64;
+  return p;
+}
+
+__device__ __forceinline__ void st_split4(unsigned char* sm, const TcPlan& P, uint32_t off, float4 v) {
+  float4 h, l;
+  umma::split_tf32(v.x, h.x, l.x);
+  umma::split_tf32(v.y, h.y, l.y);
+  umma::split_tf32(v.z, h.z, l.z);
+  umma::split_tf32(v.w, h.w, l.w);
+  *reinterpret_cast<float4*>(sm + P.off_ahi + off) = h;
+  *reinterpret_cast<float4*>(sm + P.off_alo + off) = l;
+}
+
+__device__ __forceinline__ void st_split1(unsigned char* hi, unsigned char* lo, uint32_t off, float v) {
+  float h, l;
+  umma::split_tf32(v, h, l);
+  *reinterpret_cast<float*>(hi + off) = h;
+  *reinterpret_cast<float*>(lo + off) = l;
+}
+
+// Setup shared by both kernels: zero shared memory (padding rows and columns
+// of the operand tiles stay zero), allocate TMEM, initialise the mbarrier.
+__device__ __forceinline__ uint32_t tc_setup(unsigned char* sm, const TcPlan& P) {
+  for (int i = threadIdx.x; i < P.total / 16; i += blockDim.x)
+    reinterpret_cast<float4*>(sm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.off_bar);
+  uint32_t* slot = reinterpret_cast<uint32_t*>(sm + P.off_bar + 16);
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) umma::tmem_alloc(slot, P.ncols);
+  if (threadIdx.x == 0) umma::mbar_init(bar, 1);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  return *slot;
+}
+
+__device__ __forceinline__ void tc_teardown(uint32_t taddr, const TcPlan& P) {
+  umma::fence_before_sync();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) umma::tmem_dealloc(taddr, P.ncols);
+}
+
+// Staged operands -> visible to the tensor core; all threads.
+__device__ __forceinline__ void publish() {
+  umma::fence_proxy_async();
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+}
+
+// Wait for the committed MMAs (phase parity), flag a timeout.
+__device__ __forceinline__ void wait_mma(uint64_t* bar, uint32_t& phase, int* timeout_flag) {
+  if (!umma::mbar_wait(bar, phase, MAX_POLLS)) {
+    if ((threadIdx.x & 31) == 0) atomicExch(timeout_flag, 1);
+    umma::mbar_wait(bar, phase, MAX_POLLS);
+  }
+  phase ^= 1u;
+  umma::fence_after_sync();
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_fwd(TcPlan P, const float* __restrict__ what,
+                                                               const int* __restrict__ members, int nclass, int nvol,
+                                                               const float2* __restrict__ vin, int ld_in,
+                                                               size_t in_vstride, float2* __restrict__ vout,
+                                                               int ld_out, size_t out_vstride, int* timeout_flag) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const uint32_t taddr = tc_setup(sm, P);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.off_bar);
+  uint32_t phase = 0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nt = P.nt, nz = P.nz, q4 = P.z4 >> 2;
+  const uint32_t idesc = umma::idesc_tf32(128, NR);
+  const uint32_t sbase = umma::smem_u32(sm);
+  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
+    int mem[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
+    const float* wc = what + (size_t)c * nt * P.z4;
+    for (int v0 = 0; v0 < nvol; v0 += VB) {
+      const int nv = nvol - v0 < VB ? nvol - v0 : VB;
+      // B: X[n][z] for the chunk's volumes (rows of absent members are zero)
+      for (int i = tid; i < nv * 4 * nz; i += TC_THREADS) {
+        const int v = i / (4 * nz), r = i - v * 4 * nz, m = r / nz, z = r - m * nz;
+        const float2 x = mem[m] >= 0 ? vin[(v0 + v) * in_vstride + (size_t)mem[m] * ld_in + z] : make_float2(0.f, 0.f);
+        const int n = 8 * v + 2 * m;
+        st_split1(sm + P.off_bhi, sm + P.off_blo, umma::kmajor_off(NR, n, z), x.x);
+        st_split1(sm + P.off_bhi, sm + P.off_blo, umma::kmajor_off(NR, n + 1, z), x.y);
+      }
+      for (int t0 = 0; t0 < nt; t0 += 128) {
+        const int rows = nt - t0 < 128 ? nt - t0 : 128;
+        // A: W rows t0 .. t0 + rows, consecutive threads on consecutive rows
+        for (int i = tid; i < rows * q4; i += TC_THREADS) {
+          const int k4 = i / rows, tl = i - k4 * rows;
+          const float4 w = __ldg(reinterpret_cast<const float4*>(wc + (size_t)(t0 + tl) * P.z4) + k4);
+          st_split4(sm, P, umma::kmajor_off(128, tl, 4 * k4), w);
+        }
+        publish();
+        if (tid == 0) {
+          for (int s = 0; s < P.zK / 8; ++s) {
+            const uint32_t o = s * 2 * 128 * 16;
+            const uint64_t ah = umma::desc(sbase + P.off_ahi + o, 128 * 16, 128);
+            const uint64_t al = umma::desc(sbase + P.off_alo + o, 128 * 16, 128);
+            const uint64_t bh = umma::desc(sbase + P.off_bhi + o, NR * 16, 128);
+            const uint64_t bl = umma::desc(sbase + P.off_blo + o, NR * 16, 128);
+            umma::mma_tf32(taddr, al, bh, idesc, s > 0);
+            umma::mma_tf32(taddr, ah, bl, idesc, 1);
+            umma::mma_tf32(taddr, ah, bh, idesc, 1);
+          }
+          umma::commit(bar);
+        }
+        wait_mma(bar, phase, timeout_flag);
+        // epilogue: TMEM lane = t row of the tile; warps w and w + 4 split the 8 column groups
+        const int tl = 32 * (warp & 3) + lane, t = t0 + tl;
+        for (int j = warp >> 2; j < NR / 16; j += 2) {
+          float d[16];
+          umma::tmem_ld16(taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * j, d);
+#pragma unroll
+          for (int vv = 0; vv < 2; ++vv) {
+            const int v = 2 * j + vv;
+            if (v < nv && t < nt) {
+#pragma unroll
+              for (int m = 0; m < 4; ++m)
+                if (mem[m] >= 0)
+                  vout[(v0 + v) * out_vstride + (size_t)mem[m] * ld_out + t] =
+                      make_float2(d[8 * vv + 2 * m], d[8 * vv + 2 * m + 1]);
+            }
+          }
+        }
+        umma::fence_before_sync();
+        __syncthreads();
+      }
+    }
+  }
+  tc_teardown(taddr, P);
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_adj(TcPlan P, const float* __restrict__ what,
+                                                               const int* __restrict__ members, int nclass, int nvol,
+                                                               const float2* __restrict__ vin, int ld_in,
+                                                               size_t in_vstride, float2* __restrict__ vout,
+                                                               int ld_out, size_t out_vstride, int* timeout_flag) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const uint32_t taddr = tc_setup(sm, P);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.off_bar);
+  uint32_t phase = 0;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nt = P.nt, nz = P.nz, q4 = P.z4 >> 2;
+  const uint32_t idesc = umma::idesc_tf32(128, P.zN);
+  const uint32_t sbase = umma::smem_u32(sm);
+  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
+    int mem[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
+    const float* wc = what + (size_t)c * nt * P.z4;
+    for (int v0 = 0; v0 < nvol; v0 += VB) {
+      const int nv = nvol - v0 < VB ? nvol - v0 : VB;
+      for (int t0 = 0; t0 < P.tK; t0 += P.tc) {
+        const int tcc = P.tK - t0 < P.tc ? P.tK - t0 : P.tc;  // a multiple of 8
+        // A: C[n][t], four consecutive t per thread (one 16-byte row piece per component);
+        // consecutive threads take consecutive (volume, member) rows
+        for (int i = tid; i < (tcc >> 2) * nv * 4; i += TC_THREADS) {
+          const int t4 = i / (nv * 4), vm = i - t4 * nv * 4, v = vm >> 2, m = vm & 3;
+          const int tb = t0 + 4 * t4;
+          float re[4], im[4];
+          const float2* src = vin + (v0 + v) * in_vstride + (size_t)(mem[m] >= 0 ? mem[m] : 0) * ld_in;
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float2 x = (mem[m] >= 0 && tb + e < nt) ? src[tb + e] : make_float2(0.f, 0.f);
+            re[e] = x.x;
+            im[e] = x.y;
+          }
+          const int n = 8 * v + 2 * m;
+          const uint32_t o0 = umma::kmajor_off(NR, n, 4 * t4), o1 = umma::kmajor_off(NR, n + 1, 4 * t4);
+          float4 h, l;
+          umma::split_tf32(re[0], h.x, l.x);
+          umma::split_tf32(re[1], h.y, l.y);
+          umma::split_tf32(re[2], h.z, l.z);
+          umma::split_tf32(re[3], h.w, l.w);
+          *reinterpret_cast<float4*>(sm + P.off_ahi + o0) = h;
+          *reinterpret_cast<float4*>(sm + P.off_alo + o0) = l;
+          umma::split_tf32(im[0], h.x, l.x);
+          umma::split_tf32(im[1], h.y, l.y);
+          umma::split_tf32(im[2], h.z, l.z);
+          umma::split_tf32(im[3], h.w, l.w);
+          *reinterpret_cast<float4*>(sm + P.off_ahi + o1) = h;
+          *reinterpret_cast<float4*>(sm + P.off_alo + o1) = l;
+        }
+        // B: W^T[z][t] from 4 x 4 blocks of W (4 rows t x 4 z), transposed in registers
+        for (int i = tid; i < (tcc >> 2) * q4; i += TC_THREADS) {
+          const int t4 = i / q4, k4 = i - t4 * q4;
+          const int tb = t0 + 4 * t4;
+          float4 w[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            w[e] = tb + e < nt ? __ldg(reinterpret_cast<const float4*>(wc + (size_t)(tb + e) * P.z4) + k4)
+                               : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float col[4][4] = {{w[0].x, w[1].x, w[2].x, w[3].x},
+                                   {w[0].y, w[1].y, w[2].y, w[3].y},
+                                   {w[0].z, w[1].z, w[2].z, w[3].z},
+                                   {w[0].w, w[1].w, w[2].w, w[3].w}};
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            float4 h, l;
+            umma::split_tf32(col[a][0], h.x, l.x);
+            umma::split_tf32(col[a][1], h.y, l.y);
+            umma::split_tf32(col[a][2], h.z, l.z);
+            umma::split_tf32(col[a][3], h.w, l.w);
+            const uint32_t o = umma::kmajor_off(P.zN, 4 * k4 + a, 4 * t4);
+            *reinterpret_cast<float4*>(sm + P.off_bhi + o) = h;
+            *reinterpret_cast<float4*>(sm + P.off_blo + o) = l;
+          }
+        }
+        publish();
+        if (tid == 0) {
+          for (int s = 0; s < tcc / 8; ++s) {
+            const uint64_t ah = umma::desc(sbase + P.off_ahi + s * 2 * NR * 16, NR * 16, 128);
+            const uint64_t al = umma::desc(sbase + P.off_alo + s * 2 * NR * 16, NR * 16, 128);
+            const uint64_t bh = umma::desc(sbase + P.off_bhi + s * 2 * P.zN * 16, P.zN * 16, 128);
+            const uint64_t bl = umma::desc(sbase + P.off_blo + s * 2 * P.zN * 16, P.zN * 16, 128);
+            umma::mma_tf32(taddr, al, bh, idesc, (t0 > 0 || s > 0) ? 1u : 0u);
+            umma::mma_tf32(taddr, ah, bl, idesc, 1);
+            umma::mma_tf32(taddr, ah, bh, idesc, 1);
+          }
+          umma::commit(bar);
+        }
+        wait_mma(bar, phase, timeout_flag);
+      }
+      // epilogue: TMEM lane n = 8 v + 2 m + c; column z.  Even lanes hold the
+      // real parts, odd lanes the imaginary parts of the same output.
+      const int n = 32 * (warp & 3) + lane, v = n >> 3, m = (n >> 1) & 3;
+      const bool writer = (lane & 1) == 0 && v < nv && mem[m] >= 0;
+      float2* dst = vout + (v0 + (v < nv ? v : 0)) * out_vstride + (size_t)(mem[m] >= 0 ? mem[m] : 0) * ld_out;
+      for (int j = warp >> 2; j < P.zN / 16; j += 2) {
+        float d[16];
+        umma::tmem_ld16(taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * j, d);
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          const float im = __shfl_down_sync(0xffffffffu, d[e], 1);
+          const int z = 16 * j + e;
+          if (writer && z < nz) dst[z] = make_float2(d[e], im);
+        }
+      }
+      umma::fence_before_sync();
+      __syncthreads();
+    }
+  }
+  tc_teardown(taddr, P);
+}
+
+template <typename K>
+ctof_status launch_tc(K kern, const TcPlan& P, const ctof_kernel_s* k, int nvol, const float2* vin, int ld_in,
+                      size_t in_vstride, float2* vout, int ld_out, size_t out_vstride, cudaStream_t st) {
+  if (P.total > 227 * 1024) return CTOF_EUNSUPPORTED;
+  CTOF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P.total));
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
+  int per_sm = (228 * 1024) / (P.total + 1024);
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 2) per_sm = 2;
+  const int grid = k->nclass < per_sm * nsm ? k->nclass : per_sm * nsm;
+  int* flag = reinterpret_cast<int*>(k->d_scalars + 9);
+  kern<<<grid, TC_THREADS, P.total, st>>>(P, k->d_what, k->d_members, k->nclass, nvol, vin, ld_in, in_vstride, vout,
+                                          ld_out, out_vstride, flag);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+}  // namespace
+
+ctof_status contract_tc_forward(const ctof_kernel_s* k, int nvol, const float2* in_z, float2* out_t,
+                                cudaStream_t st) {
+  if (nvol < 1) return CTOF_EINVAL;
+  return launch_tc(k_contract_tc_fwd, plan_fwd(k->nt, k->nz), k, nvol, in_z, k->ldz, (size_t)k->nf * k->ldz, out_t,
+                   k->ldt, (size_t)k->nf * k->ldt, st);
+}
+
+ctof_status contract_tc_adjoint(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z,
+                                cudaStream_t st) {
+  if (nvol < 1) return CTOF_EINVAL;
+  return launch_tc(k_contract_tc_adj, plan_adj(k->nt, k->nz), k, nvol, in_t, k->ldt, (size_t)k->nf * k->ldt, out_z,
+                   k->ldz, (size_t)k->nf * k->ldz, st);
+}

@@ -792,6 +792,22 @@ ctof_status ctof_adjoint(ctof_kernel k, const float* d_m, float* d_vol, void* st
   return adjoint_impl(k, d_m, d_vol, static_cast<cudaStream_t>(stream));
 }
 
+ctof_status ctof_contract_forward_batch(ctof_kernel k, int nvol, const float* d_in, float* d_out, void* stream) {
+  if (!k || !d_in || !d_out || nvol < 1) return CTOF_EINVAL;
+  DeviceGuard g(k->device);
+  if (!g.ok) return CTOF_ECUDA;
+  return contract_forward_batch(k, nvol, reinterpret_cast<const float2*>(d_in), reinterpret_cast<float2*>(d_out),
+                                static_cast<cudaStream_t>(stream));
+}
+
+ctof_status ctof_contract_adjoint_batch(ctof_kernel k, int nvol, const float* d_in, float* d_out, void* stream) {
+  if (!k || !d_in || !d_out || nvol < 1) return CTOF_EINVAL;
+  DeviceGuard g(k->device);
+  if (!g.ok) return CTOF_ECUDA;
+  return contract_adjoint_batch(k, nvol, reinterpret_cast<const float2*>(d_in), reinterpret_cast<float2*>(d_out),
+                                static_cast<cudaStream_t>(stream));
+}
+
 ctof_status ctof_forward_multiplexed(ctof_kernel k, const float* d_mu, float* d_y, void* stream) {
   if (!k || !d_mu || !d_y) return CTOF_EINVAL;
   if (k->n % 8 != 0) return CTOF_EUNSUPPORTED;

@@ -150,6 +150,12 @@ ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* 
 size_t contract_smem_bytes(int nt, int nz);
 ctof_status contract_forward(const ctof_kernel_s* k, const float2* in_z, float2* out_t, cudaStream_t st);
 // nvol volumes sharing the kernel; spectra [nvol][nf][ld] (W_hat read once per class for all)
+// Batched forward / adjoint on the tcgen05 tensor cores (contract_tc.cu):
+// 16 volumes x one frequency class = one 128-wide GEMM, 3xTF32.
+ctof_status contract_tc_forward(const ctof_kernel_s* k, int nvol, const float2* in_z, float2* out_t,
+                                cudaStream_t st);
+ctof_status contract_tc_adjoint(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z,
+                                cudaStream_t st);
 ctof_status contract_forward_batch(const ctof_kernel_s* k, int nvol, const float2* in_z, float2* out_t,
                                    cudaStream_t st);
 ctof_status contract_adjoint_batch(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z,

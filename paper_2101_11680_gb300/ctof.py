@@ -89,6 +89,8 @@ _SIGNATURES = {
     "ctof_forward": (ctypes.c_int, [_P, _P, _P, _P]),
     "ctof_adjoint": (ctypes.c_int, [_P, _P, _P, _P]),
     "ctof_forward_multiplexed": (ctypes.c_int, [_P, _P, _P, _P]),
+    "ctof_contract_forward_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
+    "ctof_contract_adjoint_batch": (ctypes.c_int, [_P, ctypes.c_int, _P, _P, _P]),
     "ctof_adjoint_multiplexed": (ctypes.c_int, [_P, _P, _P, _P]),
     "ctof_reconstruct": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolverParams), _P, ctypes.POINTER(Report), _P]),
     "ctof_reconstruct_host": (ctypes.c_int, [_P, _P, ctypes.POINTER(SolverParams), _P, ctypes.POINTER(Report),
@@ -414,6 +416,39 @@ class Kernel:
         _check(self._lib.ctof_adjoint_multiplexed(self._h, _dev_ptr(y, self._meas_shape(), "y"),
                                                   _dev_ptr(out, self._vol_shape(), "out"), _stream_handle(stream)),
                "ctof_adjoint_multiplexed")
+        return out
+
+    # ---- per-frequency contractions on spectra (batched) ----
+    @property
+    def ldt(self):
+        return (self.info.nt + 7) // 8 * 8
+
+    @property
+    def ldz(self):
+        return (self.info.nz + 7) // 8 * 8
+
+    def contract_forward_batch(self, spec_z, out=None, stream=None):
+        """[nvol][n_freq][ldz][2] float32 spectra -> [nvol][n_freq][ldt][2] (ctof_contract_forward_batch)."""
+        import torch
+        nvol = spec_z.shape[0]
+        if out is None:
+            out = torch.zeros((nvol, self.info.n_freq, self.ldt, 2), device=spec_z.device, dtype=torch.float32)
+        _check(self._lib.ctof_contract_forward_batch(
+            self._h, nvol, _dev_ptr(spec_z, (nvol, self.info.n_freq, self.ldz, 2), "spec_z"),
+            _dev_ptr(out, (nvol, self.info.n_freq, self.ldt, 2), "out"), _stream_handle(stream)),
+            "ctof_contract_forward_batch")
+        return out
+
+    def contract_adjoint_batch(self, spec_t, out=None, stream=None):
+        """[nvol][n_freq][ldt][2] float32 spectra -> [nvol][n_freq][ldz][2] (ctof_contract_adjoint_batch)."""
+        import torch
+        nvol = spec_t.shape[0]
+        if out is None:
+            out = torch.zeros((nvol, self.info.n_freq, self.ldz, 2), device=spec_t.device, dtype=torch.float32)
+        _check(self._lib.ctof_contract_adjoint_batch(
+            self._h, nvol, _dev_ptr(spec_t, (nvol, self.info.n_freq, self.ldt, 2), "spec_t"),
+            _dev_ptr(out, (nvol, self.info.n_freq, self.ldz, 2), "out"), _stream_handle(stream)),
+            "ctof_contract_adjoint_batch")
         return out
 
     def reconstruct(self, m, params, out=None, report=False, stream=None):
