@@ -28,7 +28,12 @@ namespace {
 constexpr int TC_THREADS = 256;
 constexpr int VB = 16;         // volumes per chunk
 constexpr int NR = 8 * VB;     // right-hand sides per chunk (the 128-wide GEMM side)
-constexpr int TCH = 64;        // adjoint: t values per staged K chunk
+constexpr int TCH = 32;        // adjoint: t values per staged K chunk
+// adjoint staging per thread and chunk: (TCH / 4) * NR / 2 row pieces over the
+// CTA's threads, and at most one 4 x 4 block of W (TCH / 4 * 16 <= TC_THREADS)
+constexpr int AD_ITEMS = (TCH / 4) * (NR / 2) / TC_THREADS;
+static_assert((TCH / 4) * (NR / 2) % TC_THREADS == 0, "adjoint staging items");
+static_assert((TCH / 4) * 16 <= TC_THREADS, "one W block per thread");
 constexpr long long MAX_POLLS = 1ll << 24;
 
 struct TcPlan {
@@ -85,6 +90,11 @@ __device__ __forceinline__ void st_split4(unsigned char* sm, const TcPlan& P, ui
   umma::split_tf32(v.w, h.w, l.w);
   *reinterpret_cast<float4*>(sm + P.off_ahi + off) = h;
   *reinterpret_cast<float4*>(sm + P.off_alo + off) = l;
+}
+
+// mem[m] for a runtime m without spilling the array to local memory
+__device__ __forceinline__ int pick(const int (&mem)[4], int m) {
+  return m == 0 ? mem[0] : (m == 1 ? mem[1] : (m == 2 ? mem[2] : mem[3]));
 }
 
 __device__ __forceinline__ void st_split1(unsigned char* hi, unsigned char* lo, uint32_t off, float v) {
@@ -154,21 +164,53 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_fwd(TcPlan P, con
     const float* wc = what + (size_t)c * nt * P.z4;
     for (int v0 = 0; v0 < nvol; v0 += VB) {
       const int nv = nvol - v0 < VB ? nvol - v0 : VB;
-      // B: X[n][z] for the chunk's volumes (rows of absent members are zero)
-      for (int i = tid; i < nv * 4 * nz; i += TC_THREADS) {
-        const int v = i / (4 * nz), r = i - v * 4 * nz, m = r / nz, z = r - m * nz;
-        const float2 x = mem[m] >= 0 ? vin[(v0 + v) * in_vstride + (size_t)mem[m] * ld_in + z] : make_float2(0.f, 0.f);
-        const int n = 8 * v + 2 * m;
-        st_split1(sm + P.off_bhi, sm + P.off_blo, umma::kmajor_off(NR, n, z), x.x);
-        st_split1(sm + P.off_bhi, sm + P.off_blo, umma::kmajor_off(NR, n + 1, z), x.y);
+      // B: X[n][z] for the chunk's volumes (rows of absent members are zero);
+      // each batch issues all of its loads before the first store
+      const int nb = nv * 4 * nz;
+      for (int base = 0; base < nb; base += 8 * TC_THREADS) {
+        float2 x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = base + u * TC_THREADS + tid;
+          x[u] = make_float2(0.f, 0.f);
+          if (i < nb) {
+            const int v = i / (4 * nz), r = i - v * 4 * nz, m = r / nz, z = r - m * nz;
+            const int f = pick(mem, m);
+            if (f >= 0) x[u] = vin[(v0 + v) * in_vstride + (size_t)f * ld_in + z];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = base + u * TC_THREADS + tid;
+          if (i < nb) {
+            const int v = i / (4 * nz), r = i - v * 4 * nz, m = r / nz, z = r - m * nz;
+            const int n = 8 * v + 2 * m;
+            st_split1(sm + P.off_bhi, sm + P.off_blo, umma::kmajor_off(NR, n, z), x[u].x);
+            st_split1(sm + P.off_bhi, sm + P.off_blo, umma::kmajor_off(NR, n + 1, z), x[u].y);
+          }
+        }
       }
       for (int t0 = 0; t0 < nt; t0 += 128) {
         const int rows = nt - t0 < 128 ? nt - t0 : 128;
         // A: W rows t0 .. t0 + rows, consecutive threads on consecutive rows
-        for (int i = tid; i < rows * q4; i += TC_THREADS) {
-          const int k4 = i / rows, tl = i - k4 * rows;
-          const float4 w = __ldg(reinterpret_cast<const float4*>(wc + (size_t)(t0 + tl) * P.z4) + k4);
-          st_split4(sm, P, umma::kmajor_off(128, tl, 4 * k4), w);
+        // (at most 128 x 16 float4, 8 per thread: all loads first)
+        const int na = rows * q4;
+        float4 w[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = u * TC_THREADS + tid;
+          if (i < na) {
+            const int k4 = i / rows, tl = i - k4 * rows;
+            w[u] = __ldg(reinterpret_cast<const float4*>(wc + (size_t)(t0 + tl) * P.z4) + k4);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int i = u * TC_THREADS + tid;
+          if (i < na) {
+            const int k4 = i / rows, tl = i - k4 * rows;
+            st_split4(sm, P, umma::kmajor_off(128, tl, 4 * k4), w[u]);
+          }
         }
         publish();
         if (tid == 0) {
@@ -210,7 +252,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_fwd(TcPlan P, con
   tc_teardown(taddr, P);
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_adj(TcPlan P, const float* __restrict__ what,
+__global__ void __launch_bounds__(TC_THREADS, 4) k_contract_tc_adj(TcPlan P, const float* __restrict__ what,
                                                                const int* __restrict__ members, int nclass, int nvol,
                                                                const float2* __restrict__ vin, int ld_in,
                                                                size_t in_vstride, float2* __restrict__ vout,
@@ -232,48 +274,65 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_adj(TcPlan P, con
       const int nv = nvol - v0 < VB ? nvol - v0 : VB;
       for (int t0 = 0; t0 < P.tK; t0 += P.tc) {
         const int tcc = P.tK - t0 < P.tc ? P.tK - t0 : P.tc;  // a multiple of 8
-        // A: C[n][t], four consecutive t per thread (one 16-byte row piece per component);
-        // consecutive threads take consecutive (volume, member) rows
-        for (int i = tid; i < (tcc >> 2) * nv * 4; i += TC_THREADS) {
-          const int t4 = i / (nv * 4), vm = i - t4 * nv * 4, v = vm >> 2, m = vm & 3;
-          const int tb = t0 + 4 * t4;
-          float re[4], im[4];
-          const float2* src = vin + (v0 + v) * in_vstride + (size_t)(mem[m] >= 0 ? mem[m] : 0) * ld_in;
+        // Loads of the whole chunk first (A: at most 2 row pieces per thread,
+        // B: at most one 4 x 4 block), then the splits and stores.
+        // A: C[n][t], four consecutive t per item (one 16-byte row piece per
+        // component); consecutive threads take consecutive (volume, member) rows.
+        const int na = (tcc >> 2) * nv * 4, nbk = (tcc >> 2) * q4;
+        float4 ca[AD_ITEMS][2];
 #pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float2 x = (mem[m] >= 0 && tb + e < nt) ? src[tb + e] : make_float2(0.f, 0.f);
-            re[e] = x.x;
-            im[e] = x.y;
+        for (int u = 0; u < AD_ITEMS; ++u) {
+          const int i = u * TC_THREADS + tid;
+          ca[u][0] = ca[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (i < na) {
+            const int t4 = i / (nv * 4), vm = i - t4 * nv * 4, v = vm >> 2, f = pick(mem, vm & 3);
+            const int tb = t0 + 4 * t4;
+            if (f >= 0) {
+              const float2* src = vin + (v0 + v) * in_vstride + (size_t)f * ld_in + tb;
+              if (tb + 4 <= nt) {
+                ca[u][0] = __ldg(reinterpret_cast<const float4*>(src));
+                ca[u][1] = __ldg(reinterpret_cast<const float4*>(src) + 1);
+              } else {
+                float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int q = 0; q < 4 && tb + q < nt; ++q) {
+                  const float2 x = src[q];
+                  e[2 * q] = x.x;
+                  e[2 * q + 1] = x.y;
+                }
+                ca[u][0] = make_float4(e[0], e[1], e[2], e[3]);
+                ca[u][1] = make_float4(e[4], e[5], e[6], e[7]);
+              }
+            }
           }
-          const int n = 8 * v + 2 * m;
-          const uint32_t o0 = umma::kmajor_off(NR, n, 4 * t4), o1 = umma::kmajor_off(NR, n + 1, 4 * t4);
-          float4 h, l;
-          umma::split_tf32(re[0], h.x, l.x);
-          umma::split_tf32(re[1], h.y, l.y);
-          umma::split_tf32(re[2], h.z, l.z);
-          umma::split_tf32(re[3], h.w, l.w);
-          *reinterpret_cast<float4*>(sm + P.off_ahi + o0) = h;
-          *reinterpret_cast<float4*>(sm + P.off_alo + o0) = l;
-          umma::split_tf32(im[0], h.x, l.x);
-          umma::split_tf32(im[1], h.y, l.y);
-          umma::split_tf32(im[2], h.z, l.z);
-          umma::split_tf32(im[3], h.w, l.w);
-          *reinterpret_cast<float4*>(sm + P.off_ahi + o1) = h;
-          *reinterpret_cast<float4*>(sm + P.off_alo + o1) = l;
         }
         // B: W^T[z][t] from 4 x 4 blocks of W (4 rows t x 4 z), transposed in registers
-        for (int i = tid; i < (tcc >> 2) * q4; i += TC_THREADS) {
-          const int t4 = i / q4, k4 = i - t4 * q4;
-          const int tb = t0 + 4 * t4;
-          float4 w[4];
+        float4 wb[4];
+        const int ib = tid;
+        if (ib < nbk) {
+          const int t4 = ib / q4, k4 = ib - t4 * q4, tb = t0 + 4 * t4;
 #pragma unroll
           for (int e = 0; e < 4; ++e)
-            w[e] = tb + e < nt ? __ldg(reinterpret_cast<const float4*>(wc + (size_t)(tb + e) * P.z4) + k4)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float col[4][4] = {{w[0].x, w[1].x, w[2].x, w[3].x},
-                                   {w[0].y, w[1].y, w[2].y, w[3].y},
-                                   {w[0].z, w[1].z, w[2].z, w[3].z},
-                                   {w[0].w, w[1].w, w[2].w, w[3].w}};
+            wb[e] = tb + e < nt ? __ldg(reinterpret_cast<const float4*>(wc + (size_t)(tb + e) * P.z4) + k4)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < AD_ITEMS; ++u) {
+          const int i = u * TC_THREADS + tid;
+          if (i < na) {
+            const int t4 = i / (nv * 4), vm = i - t4 * nv * 4, v = vm >> 2, m = vm & 3;
+            const int n = 8 * v + 2 * m;
+            const float4 re = make_float4(ca[u][0].x, ca[u][0].z, ca[u][1].x, ca[u][1].z);
+            const float4 im = make_float4(ca[u][0].y, ca[u][0].w, ca[u][1].y, ca[u][1].w);
+            st_split4(sm, P, umma::kmajor_off(NR, n, 4 * t4), re);
+            st_split4(sm, P, umma::kmajor_off(NR, n + 1, 4 * t4), im);
+          }
+        }
+        if (ib < nbk) {
+          const int t4 = ib / q4, k4 = ib - t4 * q4;
+          const float col[4][4] = {{wb[0].x, wb[1].x, wb[2].x, wb[3].x},
+                                   {wb[0].y, wb[1].y, wb[2].y, wb[3].y},
+                                   {wb[0].z, wb[1].z, wb[2].z, wb[3].z},
+                                   {wb[0].w, wb[1].w, wb[2].w, wb[3].w}};
 #pragma unroll
           for (int a = 0; a < 4; ++a) {
             float4 h, l;
@@ -303,9 +362,9 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_adj(TcPlan P, con
       }
       // epilogue: TMEM lane n = 8 v + 2 m + c; column z.  Even lanes hold the
       // real parts, odd lanes the imaginary parts of the same output.
-      const int n = 32 * (warp & 3) + lane, v = n >> 3, m = (n >> 1) & 3;
-      const bool writer = (lane & 1) == 0 && v < nv && mem[m] >= 0;
-      float2* dst = vout + (v0 + (v < nv ? v : 0)) * out_vstride + (size_t)(mem[m] >= 0 ? mem[m] : 0) * ld_out;
+      const int n = 32 * (warp & 3) + lane, v = n >> 3, fm = pick(mem, (n >> 1) & 3);
+      const bool writer = (lane & 1) == 0 && v < nv && fm >= 0;
+      float2* dst = vout + (v0 + (v < nv ? v : 0)) * out_vstride + (size_t)(fm >= 0 ? fm : 0) * ld_out;
       for (int j = warp >> 2; j < P.zN / 16; j += 2) {
         float d[16];
         umma::tmem_ld16(taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * j, d);
@@ -332,7 +391,10 @@ ctof_status launch_tc(K kern, const TcPlan& P, const ctof_kernel_s* k, int nvol,
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
   int per_sm = (228 * 1024) / (P.total + 1024);
   if (per_sm < 1) per_sm = 1;
-  if (per_sm > 2) per_sm = 2;
+  // TMEM: per_sm x ncols <= 512 columns
+  const int tmem_cap = (int)(512 / P.ncols);
+  if (per_sm > 4) per_sm = 4;
+  if (per_sm > tmem_cap) per_sm = tmem_cap;
   const int grid = k->nclass < per_sm * nsm ? k->nclass : per_sm * nsm;
   int* flag = reinterpret_cast<int*>(k->d_scalars + 9);
   kern<<<grid, TC_THREADS, P.total, st>>>(P, k->d_what, k->d_members, k->nclass, nvol, vin, ld_in, in_vstride, vout,
