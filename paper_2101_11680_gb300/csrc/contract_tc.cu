@@ -252,111 +252,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_fwd(TcPlan P, con
   tc_teardown(taddr, P);
 }
 
-// Adjoint, software-pipelined over the CTA's steps s = (class, volume chunk,
-// t chunk): the global loads of step s + 1 go to registers while the MMAs of
-// step s run, so each step pays the load latency once, overlapped.
-struct AdjRegs {
-  float4 ca[AD_ITEMS][2];  // C row pieces: 4 complex t values
-  float4 wb[4];            // one 4 x 4 block of W (4 rows t x 4 z)
-};
-
-struct AdjStep {
-  int c, v0, nv, t0, tcc, last;
-};
-
-__device__ __forceinline__ AdjStep adj_step(const TcPlan& P, int s, int nvol, int nvc, int ntc) {
-  AdjStep a;
-  const int per = nvc * ntc, j = s / per, r = s - j * per, vc = r / ntc, tci = r - vc * ntc;
-  a.c = blockIdx.x + j * gridDim.x;
-  a.v0 = vc * VB;
-  a.nv = nvol - a.v0 < VB ? nvol - a.v0 : VB;
-  a.t0 = tci * P.tc;
-  a.tcc = P.tK - a.t0 < P.tc ? P.tK - a.t0 : P.tc;
-  a.last = tci == ntc - 1;
-  return a;
-}
-
-__device__ __forceinline__ void adj_load(const TcPlan& P, const AdjStep& a, const int (&mem)[4],
-                                         const float* __restrict__ what, const float2* __restrict__ vin, int ld_in,
-                                         size_t in_vstride, AdjRegs& R) {
-  const int tid = threadIdx.x, nt = P.nt, q4 = P.z4 >> 2;
-  const int nvm = a.nv * 4, na = (a.tcc >> 2) * nvm, nbk = (a.tcc >> 2) * q4;
-#pragma unroll
-  for (int u = 0; u < AD_ITEMS; ++u) {
-    const int i = u * TC_THREADS + tid;
-    R.ca[u][0] = R.ca[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-    if (i < na) {
-      const int t4 = i / nvm, vm = i - t4 * nvm, f = pick(mem, vm & 3);
-      const int tb = a.t0 + 4 * t4;
-      if (f >= 0) {
-        const float2* src = vin + (a.v0 + (vm >> 2)) * in_vstride + (size_t)f * ld_in + tb;
-        if (tb + 4 <= nt) {
-          R.ca[u][0] = __ldg(reinterpret_cast<const float4*>(src));
-          R.ca[u][1] = __ldg(reinterpret_cast<const float4*>(src) + 1);
-        } else {
-          float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-          for (int q = 0; q < 4 && tb + q < nt; ++q) {
-            const float2 x = src[q];
-            e[2 * q] = x.x;
-            e[2 * q + 1] = x.y;
-          }
-          R.ca[u][0] = make_float4(e[0], e[1], e[2], e[3]);
-          R.ca[u][1] = make_float4(e[4], e[5], e[6], e[7]);
-        }
-      }
-    }
-  }
-  if (tid < nbk) {
-    const int t4 = tid / q4, k4 = tid - t4 * q4, tb = a.t0 + 4 * t4;
-    const float* wc = what + (size_t)a.c * nt * P.z4;
-#pragma unroll
-    for (int e = 0; e < 4; ++e)
-      R.wb[e] = tb + e < nt ? __ldg(reinterpret_cast<const float4*>(wc + (size_t)(tb + e) * P.z4) + k4)
-                            : make_float4(0.f, 0.f, 0.f, 0.f);
-  }
-}
-
-__device__ __forceinline__ void adj_store(const TcPlan& P, unsigned char* sm, const AdjStep& a, const AdjRegs& R) {
-  const int tid = threadIdx.x, q4 = P.z4 >> 2;
-  const int nvm = a.nv * 4, na = (a.tcc >> 2) * nvm, nbk = (a.tcc >> 2) * q4;
-#pragma unroll
-  for (int u = 0; u < AD_ITEMS; ++u) {
-    const int i = u * TC_THREADS + tid;
-    if (i < na) {
-      const int t4 = i / nvm, vm = i - t4 * nvm;
-      const int n = 8 * (vm >> 2) + 2 * (vm & 3);
-      st_split4(sm, P, umma::kmajor_off(NR, n, 4 * t4),
-                make_float4(R.ca[u][0].x, R.ca[u][0].z, R.ca[u][1].x, R.ca[u][1].z));
-      st_split4(sm, P, umma::kmajor_off(NR, n + 1, 4 * t4),
-                make_float4(R.ca[u][0].y, R.ca[u][0].w, R.ca[u][1].y, R.ca[u][1].w));
-    }
-  }
-  if (tid < nbk) {
-    const int t4 = tid / q4, k4 = tid - t4 * q4;
-    const float col[4][4] = {{R.wb[0].x, R.wb[1].x, R.wb[2].x, R.wb[3].x},
-                             {R.wb[0].y, R.wb[1].y, R.wb[2].y, R.wb[3].y},
-                             {R.wb[0].z, R.wb[1].z, R.wb[2].z, R.wb[3].z},
-                             {R.wb[0].w, R.wb[1].w, R.wb[2].w, R.wb[3].w}};
-#pragma unroll
-    for (int r = 0; r < 4; ++r) {
-      float4 h, l;
-      umma::split_tf32(col[r][0], h.x, l.x);
-      umma::split_tf32(col[r][1], h.y, l.y);
-      umma::split_tf32(col[r][2], h.z, l.z);
-      umma::split_tf32(col[r][3], h.w, l.w);
-      const uint32_t o = umma::kmajor_off(P.zN, 4 * k4 + r, 4 * t4);
-      *reinterpret_cast<float4*>(sm + P.off_bhi + o) = h;
-      *reinterpret_cast<float4*>(sm + P.off_blo + o) = l;
-    }
-  }
-}
-
-__device__ __forceinline__ void load_members(const int* __restrict__ members, int c, int (&mem)[4]) {
-#pragma unroll
-  for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
-}
-
-__global__ void __launch_bounds__(TC_THREADS, 3) k_contract_tc_adj(TcPlan P, const float* __restrict__ what,
+__global__ void __launch_bounds__(TC_THREADS, 4) k_contract_tc_adj(TcPlan P, const float* __restrict__ what,
                                                                const int* __restrict__ members, int nclass, int nvol,
                                                                const float2* __restrict__ vin, int ld_in,
                                                                size_t in_vstride, float2* __restrict__ vout,
@@ -366,48 +262,109 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_contract_tc_adj(TcPlan P, con
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.off_bar);
   uint32_t phase = 0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nt = P.nt, nz = P.nz, q4 = P.z4 >> 2;
   const uint32_t idesc = umma::idesc_tf32(128, P.zN);
   const uint32_t sbase = umma::smem_u32(sm);
-  const int nvc = (nvol + VB - 1) / VB, ntc = (P.tK + P.tc - 1) / P.tc;
-  const int mine = blockIdx.x < nclass ? (nclass - 1 - blockIdx.x) / gridDim.x + 1 : 0;
-  const int steps = mine * nvc * ntc;
-  AdjRegs R;
-  int mem[4], mem_next[4];
-  if (steps > 0) {
-    const AdjStep a0 = adj_step(P, 0, nvol, nvc, ntc);
-    load_members(members, a0.c, mem_next);
-    adj_load(P, a0, mem_next, what, vin, ld_in, in_vstride, R);
-  }
-  for (int s = 0; s < steps; ++s) {
-    const AdjStep a = adj_step(P, s, nvol, nvc, ntc);
+  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
+    int mem[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) mem[m] = mem_next[m];
-    adj_store(P, sm, a, R);
-    publish();
-    if (tid == 0) {
-      for (int k = 0; k < a.tcc / 8; ++k) {
-        const uint64_t ah = umma::desc(sbase + P.off_ahi + k * 2 * NR * 16, NR * 16, 128);
-        const uint64_t al = umma::desc(sbase + P.off_alo + k * 2 * NR * 16, NR * 16, 128);
-        const uint64_t bh = umma::desc(sbase + P.off_bhi + k * 2 * P.zN * 16, P.zN * 16, 128);
-        const uint64_t bl = umma::desc(sbase + P.off_blo + k * 2 * P.zN * 16, P.zN * 16, 128);
-        umma::mma_tf32(taddr, al, bh, idesc, (a.t0 > 0 || k > 0) ? 1u : 0u);
-        umma::mma_tf32(taddr, ah, bl, idesc, 1);
-        umma::mma_tf32(taddr, ah, bh, idesc, 1);
+    for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
+    const float* wc = what + (size_t)c * nt * P.z4;
+    for (int v0 = 0; v0 < nvol; v0 += VB) {
+      const int nv = nvol - v0 < VB ? nvol - v0 : VB;
+      for (int t0 = 0; t0 < P.tK; t0 += P.tc) {
+        const int tcc = P.tK - t0 < P.tc ? P.tK - t0 : P.tc;  // a multiple of 8
+        // Loads of the whole chunk first (A: at most 2 row pieces per thread,
+        // B: at most one 4 x 4 block), then the splits and stores.
+        // A: C[n][t], four consecutive t per item (one 16-byte row piece per
+        // component); consecutive threads take consecutive (volume, member) rows.
+        const int na = (tcc >> 2) * nv * 4, nbk = (tcc >> 2) * q4;
+        float4 ca[AD_ITEMS][2];
+#pragma unroll
+        for (int u = 0; u < AD_ITEMS; ++u) {
+          const int i = u * TC_THREADS + tid;
+          ca[u][0] = ca[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (i < na) {
+            const int t4 = i / (nv * 4), vm = i - t4 * nv * 4, v = vm >> 2, f = pick(mem, vm & 3);
+            const int tb = t0 + 4 * t4;
+            if (f >= 0) {
+              const float2* src = vin + (v0 + v) * in_vstride + (size_t)f * ld_in + tb;
+              if (tb + 4 <= nt) {
+                ca[u][0] = __ldg(reinterpret_cast<const float4*>(src));
+                ca[u][1] = __ldg(reinterpret_cast<const float4*>(src) + 1);
+              } else {
+                float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+                for (int q = 0; q < 4 && tb + q < nt; ++q) {
+                  const float2 x = src[q];
+                  e[2 * q] = x.x;
+                  e[2 * q + 1] = x.y;
+                }
+                ca[u][0] = make_float4(e[0], e[1], e[2], e[3]);
+                ca[u][1] = make_float4(e[4], e[5], e[6], e[7]);
+              }
+            }
+          }
+        }
+        // B: W^T[z][t] from 4 x 4 blocks of W (4 rows t x 4 z), transposed in registers
+        float4 wb[4];
+        const int ib = tid;
+        if (ib < nbk) {
+          const int t4 = ib / q4, k4 = ib - t4 * q4, tb = t0 + 4 * t4;
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            wb[e] = tb + e < nt ? __ldg(reinterpret_cast<const float4*>(wc + (size_t)(tb + e) * P.z4) + k4)
+                                : make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+#pragma unroll
+        for (int u = 0; u < AD_ITEMS; ++u) {
+          const int i = u * TC_THREADS + tid;
+          if (i < na) {
+            const int t4 = i / (nv * 4), vm = i - t4 * nv * 4, v = vm >> 2, m = vm & 3;
+            const int n = 8 * v + 2 * m;
+            const float4 re = make_float4(ca[u][0].x, ca[u][0].z, ca[u][1].x, ca[u][1].z);
+            const float4 im = make_float4(ca[u][0].y, ca[u][0].w, ca[u][1].y, ca[u][1].w);
+            st_split4(sm, P, umma::kmajor_off(NR, n, 4 * t4), re);
+            st_split4(sm, P, umma::kmajor_off(NR, n + 1, 4 * t4), im);
+          }
+        }
+        if (ib < nbk) {
+          const int t4 = ib / q4, k4 = ib - t4 * q4;
+          const float col[4][4] = {{wb[0].x, wb[1].x, wb[2].x, wb[3].x},
+                                   {wb[0].y, wb[1].y, wb[2].y, wb[3].y},
+                                   {wb[0].z, wb[1].z, wb[2].z, wb[3].z},
+                                   {wb[0].w, wb[1].w, wb[2].w, wb[3].w}};
+#pragma unroll
+          for (int a = 0; a < 4; ++a) {
+            float4 h, l;
+            umma::split_tf32(col[a][0], h.x, l.x);
+            umma::split_tf32(col[a][1], h.y, l.y);
+            umma::split_tf32(col[a][2], h.z, l.z);
+            umma::split_tf32(col[a][3], h.w, l.w);
+            const uint32_t o = umma::kmajor_off(P.zN, 4 * k4 + a, 4 * t4);
+            *reinterpret_cast<float4*>(sm + P.off_bhi + o) = h;
+            *reinterpret_cast<float4*>(sm + P.off_blo + o) = l;
+          }
+        }
+        publish();
+        if (tid == 0) {
+          for (int s = 0; s < tcc / 8; ++s) {
+            const uint64_t ah = umma::desc(sbase + P.off_ahi + s * 2 * NR * 16, NR * 16, 128);
+            const uint64_t al = umma::desc(sbase + P.off_alo + s * 2 * NR * 16, NR * 16, 128);
+            const uint64_t bh = umma::desc(sbase + P.off_bhi + s * 2 * P.zN * 16, P.zN * 16, 128);
+            const uint64_t bl = umma::desc(sbase + P.off_blo + s * 2 * P.zN * 16, P.zN * 16, 128);
+            umma::mma_tf32(taddr, al, bh, idesc, (t0 > 0 || s > 0) ? 1u : 0u);
+            umma::mma_tf32(taddr, ah, bl, idesc, 1);
+            umma::mma_tf32(taddr, ah, bh, idesc, 1);
+          }
+          umma::commit(bar);
+        }
+        wait_mma(bar, phase, timeout_flag);
       }
-      umma::commit(bar);
-    }
-    if (s + 1 < steps) {  // next step's loads overlap this step's MMAs
-      const AdjStep b = adj_step(P, s + 1, nvol, nvc, ntc);
-      if (b.c != a.c) load_members(members, b.c, mem_next);
-      adj_load(P, b, mem_next, what, vin, ld_in, in_vstride, R);
-    }
-    wait_mma(bar, phase, timeout_flag);
-    if (a.last) {
       // epilogue: TMEM lane n = 8 v + 2 m + c; column z.  Even lanes hold the
       // real parts, odd lanes the imaginary parts of the same output.
       const int n = 32 * (warp & 3) + lane, v = n >> 3, fm = pick(mem, (n >> 1) & 3);
-      const bool writer = (lane & 1) == 0 && v < a.nv && fm >= 0;
-      float2* dst = vout + (a.v0 + (v < a.nv ? v : 0)) * out_vstride + (size_t)(fm >= 0 ? fm : 0) * ld_out;
+      const bool writer = (lane & 1) == 0 && v < nv && fm >= 0;
+      float2* dst = vout + (v0 + (v < nv ? v : 0)) * out_vstride + (size_t)(fm >= 0 ? fm : 0) * ld_out;
       for (int j = warp >> 2; j < P.zN / 16; j += 2) {
         float d[16];
         umma::tmem_ld16(taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * j, d);
@@ -415,11 +372,12 @@ __global__ void __launch_bounds__(TC_THREADS, 3) k_contract_tc_adj(TcPlan P, con
         for (int e = 0; e < 16; ++e) {
           const float im = __shfl_down_sync(0xffffffffu, d[e], 1);
           const int z = 16 * j + e;
-          if (writer && z < P.nz) dst[z] = make_float2(d[e], im);
+          if (writer && z < nz) dst[z] = make_float2(d[e], im);
         }
       }
+      umma::fence_before_sync();
+      __syncthreads();
     }
-    // the next step's publish() orders these TMEM reads before its MMAs
   }
   tc_teardown(taddr, P);
 }
@@ -431,13 +389,12 @@ ctof_status launch_tc(K kern, const TcPlan& P, const ctof_kernel_s* k, int nvol,
   CTOF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P.total));
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
-  // resident CTAs per SM (registers, shared memory), within the TMEM budget of
-  // 512 columns per SM; the grid is exactly that many persistent CTAs per SM
-  int per_sm = 1;
-  CTOF_CUDA_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, TC_THREADS, P.total));
-  const int tmem_cap = (int)(512 / P.ncols);
-  if (per_sm > tmem_cap) per_sm = tmem_cap;
+  int per_sm = (228 * 1024) / (P.total + 1024);
   if (per_sm < 1) per_sm = 1;
+  // TMEM: per_sm x ncols <= 512 columns
+  const int tmem_cap = (int)(512 / P.ncols);
+  if (per_sm > 4) per_sm = 4;
+  if (per_sm > tmem_cap) per_sm = tmem_cap;
   const int grid = k->nclass < per_sm * nsm ? k->nclass : per_sm * nsm;
   int* flag = reinterpret_cast<int*>(k->d_scalars + 9);
   kern<<<grid, TC_THREADS, P.total, st>>>(P, k->d_what, k->d_members, k->nclass, nvol, vin, ld_in, in_vstride, vout,
