@@ -29,16 +29,13 @@ constexpr int TC_THREADS = 256;
 constexpr int VB = 16;         // volumes per chunk
 constexpr int NR = 8 * VB;     // right-hand sides per chunk (the 128-wide GEMM side)
 constexpr int TCH = 32;        // adjoint: t values per staged K chunk
-// adjoint staging per thread and chunk: (TCH / 4) * NR / 2 row pieces over the
-// CTA's threads, and at most one 4 x 4 block of W (TCH / 4 * 16 <= TC_THREADS)
-constexpr int AD_ITEMS = (TCH / 4) * (NR / 2) / TC_THREADS;
-static_assert((TCH / 4) * (NR / 2) % TC_THREADS == 0, "adjoint staging items");
-static_assert((TCH / 4) * 16 <= TC_THREADS, "one W block per thread");
+constexpr int RCS = TCH * 8 + 16;  // adjoint raw stage: bytes per (volume, member) row, padded
 constexpr long long MAX_POLLS = 1ll << 24;
 
 struct TcPlan {
   int nt, nz, z4, zK, zN, tK, tc;
   int off_ahi, off_alo, off_bhi, off_blo, off_bar, total;
+  int off_raw, raw_c, raw_stage;  // adjoint: two raw stages of [64 rows][RCS] C and [tc][z4] W
   uint32_t ncols;  // TMEM columns
 };
 
@@ -76,7 +73,10 @@ TcPlan plan_adj(int nt, int nz) {
   p.off_alo = ta;
   p.off_bhi = 2 * ta;
   p.off_blo = 2 * ta + tb;
-  p.off_bar = 2 * ta + 2 * tb;
+  p.raw_c = 4 * VB * RCS;
+  p.raw_stage = p.raw_c + p.tc * p.z4 * 4;
+  p.off_raw = 2 * ta + 2 * tb;
+  p.off_bar = p.off_raw + 2 * p.raw_stage;
   p.total = p.off_bar + 64;
   p.ncols = p.zN <= 32 ? 32 : 64;
   return p;
@@ -252,7 +252,98 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_fwd(TcPlan P, con
   tc_teardown(taddr, P);
 }
 
-__global__ void __launch_bounds__(TC_THREADS, 4) k_contract_tc_adj(TcPlan P, const float* __restrict__ what,
+// Adjoint.  The CTA's steps are s = (class, volume chunk, t chunk).  Step
+// s + 1's input rows (64 (volume, member) rows of TCH complex t values, and
+// TCH rows of W) stream into the other of two raw shared-memory stages with
+// coalesced 16-byte cp.async copies while step s is converted (raw -> split
+// K-major tiles, W transposed through 4 x 4 register blocks) and multiplied.
+struct AdjStep {
+  int c, v0, nv, t0, tcc, last;
+};
+
+__device__ __forceinline__ AdjStep adj_step(const TcPlan& P, int s, int nvol, int nvc, int ntc) {
+  AdjStep a;
+  const int per = nvc * ntc, j = s / per, r = s - j * per, vc = r / ntc, tci = r - vc * ntc;
+  a.c = blockIdx.x + j * gridDim.x;
+  a.v0 = vc * VB;
+  a.nv = nvol - a.v0 < VB ? nvol - a.v0 : VB;
+  a.t0 = tci * P.tc;
+  a.tcc = P.tK - a.t0 < P.tc ? P.tK - a.t0 : P.tc;
+  a.last = tci == ntc - 1;
+  return a;
+}
+
+__device__ __forceinline__ void load_members(const int* __restrict__ members, int c, int (&mem)[4]) {
+#pragma unroll
+  for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
+}
+
+// 16-byte asynchronous copy; bytes < 16 zero-fills the rest (0: no read)
+__device__ __forceinline__ void cp_async16z(void* smem, const void* gmem, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(umma::smem_u32(smem)), "l"(gmem),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+
+__device__ __forceinline__ void adj_issue(const TcPlan& P, unsigned char* sm, int stage, const AdjStep& a,
+                                          const int (&mem)[4], const float* __restrict__ what,
+                                          const float2* __restrict__ vin, int ld_in, size_t in_vstride) {
+  unsigned char* rc = sm + P.off_raw + stage * P.raw_stage;
+  unsigned char* rw = rc + P.raw_c;
+  const int nt = P.nt, q4 = P.z4 >> 2, pieces = a.tcc >> 1, nvm = a.nv * 4;
+  for (int i = threadIdx.x; i < nvm * pieces; i += TC_THREADS) {
+    const int vm = i / pieces, p = i - vm * pieces, f = pick(mem, vm & 3), t = a.t0 + 2 * p;
+    const int bytes = f < 0 ? 0 : (t + 2 <= nt ? 16 : (t < nt ? 8 : 0));
+    const float2* src = bytes ? vin + (a.v0 + (vm >> 2)) * in_vstride + (size_t)f * ld_in + t : vin;
+    cp_async16z(rc + vm * RCS + p * 16, src, bytes);
+  }
+  const float* wc = what + (size_t)a.c * nt * P.z4;
+  for (int i = threadIdx.x; i < a.tcc * q4; i += TC_THREADS) {
+    const int tl = i / q4, k4 = i - tl * q4, t = a.t0 + tl;
+    const int bytes = t < nt ? 16 : 0;
+    cp_async16z(rw + i * 16, bytes ? wc + (size_t)t * P.z4 + 4 * k4 : what, bytes);
+  }
+}
+
+__device__ __forceinline__ void adj_convert(const TcPlan& P, unsigned char* sm, int stage, const AdjStep& a) {
+  const unsigned char* rc = sm + P.off_raw + stage * P.raw_stage;
+  const unsigned char* rw = rc + P.raw_c;
+  const int q4 = P.z4 >> 2, nvm = a.nv * 4, t4n = a.tcc >> 2;
+  // A: C[n][t] from the raw rows; consecutive threads on consecutive rows
+  for (int i = threadIdx.x; i < nvm * t4n; i += TC_THREADS) {
+    const int t4 = i / nvm, vm = i - t4 * nvm;
+    const float4* r = reinterpret_cast<const float4*>(rc + vm * RCS + t4 * 32);
+    const float4 x0 = r[0], x1 = r[1];
+    st_split4(sm, P, umma::kmajor_off(NR, 2 * vm, 4 * t4), make_float4(x0.x, x0.z, x1.x, x1.z));
+    st_split4(sm, P, umma::kmajor_off(NR, 2 * vm + 1, 4 * t4), make_float4(x0.y, x0.w, x1.y, x1.w));
+  }
+  // B: W^T[z][t] from 4 x 4 blocks of the raw W rows, transposed in registers
+  for (int i = threadIdx.x; i < t4n * q4; i += TC_THREADS) {
+    const int t4 = i / q4, k4 = i - t4 * q4;
+    float4 w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) w[e] = *reinterpret_cast<const float4*>(rw + ((4 * t4 + e) * q4 + k4) * 16);
+    const float col[4][4] = {{w[0].x, w[1].x, w[2].x, w[3].x},
+                             {w[0].y, w[1].y, w[2].y, w[3].y},
+                             {w[0].z, w[1].z, w[2].z, w[3].z},
+                             {w[0].w, w[1].w, w[2].w, w[3].w}};
+#pragma unroll
+    for (int r = 0; r < 4; ++r) {
+      float4 h, l;
+      umma::split_tf32(col[r][0], h.x, l.x);
+      umma::split_tf32(col[r][1], h.y, l.y);
+      umma::split_tf32(col[r][2], h.z, l.z);
+      umma::split_tf32(col[r][3], h.w, l.w);
+      const uint32_t o = umma::kmajor_off(P.zN, 4 * k4 + r, 4 * t4);
+      *reinterpret_cast<float4*>(sm + P.off_bhi + o) = h;
+      *reinterpret_cast<float4*>(sm + P.off_blo + o) = l;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_adj(TcPlan P, const float* __restrict__ what,
                                                                const int* __restrict__ members, int nclass, int nvol,
                                                                const float2* __restrict__ vin, int ld_in,
                                                                size_t in_vstride, float2* __restrict__ vout,
@@ -262,109 +353,51 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_contract_tc_adj(TcPlan P, con
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.off_bar);
   uint32_t phase = 0;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nt = P.nt, nz = P.nz, q4 = P.z4 >> 2;
   const uint32_t idesc = umma::idesc_tf32(128, P.zN);
   const uint32_t sbase = umma::smem_u32(sm);
-  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
-    int mem[4];
+  const int nvc = (nvol + VB - 1) / VB, ntc = (P.tK + P.tc - 1) / P.tc;
+  const int mine = blockIdx.x < nclass ? (nclass - 1 - blockIdx.x) / gridDim.x + 1 : 0;
+  const int steps = mine * nvc * ntc;
+  int mem[4], mem_next[4];
+  if (steps > 0) {
+    const AdjStep a0 = adj_step(P, 0, nvol, nvc, ntc);
+    load_members(members, a0.c, mem_next);
+    adj_issue(P, sm, 0, a0, mem_next, what, vin, ld_in, in_vstride);
+  }
+  cp_commit();
+  for (int s = 0; s < steps; ++s) {
+    const AdjStep a = adj_step(P, s, nvol, nvc, ntc);
 #pragma unroll
-    for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
-    const float* wc = what + (size_t)c * nt * P.z4;
-    for (int v0 = 0; v0 < nvol; v0 += VB) {
-      const int nv = nvol - v0 < VB ? nvol - v0 : VB;
-      for (int t0 = 0; t0 < P.tK; t0 += P.tc) {
-        const int tcc = P.tK - t0 < P.tc ? P.tK - t0 : P.tc;  // a multiple of 8
-        // Loads of the whole chunk first (A: at most 2 row pieces per thread,
-        // B: at most one 4 x 4 block), then the splits and stores.
-        // A: C[n][t], four consecutive t per item (one 16-byte row piece per
-        // component); consecutive threads take consecutive (volume, member) rows.
-        const int na = (tcc >> 2) * nv * 4, nbk = (tcc >> 2) * q4;
-        float4 ca[AD_ITEMS][2];
-#pragma unroll
-        for (int u = 0; u < AD_ITEMS; ++u) {
-          const int i = u * TC_THREADS + tid;
-          ca[u][0] = ca[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
-          if (i < na) {
-            const int t4 = i / (nv * 4), vm = i - t4 * nv * 4, v = vm >> 2, f = pick(mem, vm & 3);
-            const int tb = t0 + 4 * t4;
-            if (f >= 0) {
-              const float2* src = vin + (v0 + v) * in_vstride + (size_t)f * ld_in + tb;
-              if (tb + 4 <= nt) {
-                ca[u][0] = __ldg(reinterpret_cast<const float4*>(src));
-                ca[u][1] = __ldg(reinterpret_cast<const float4*>(src) + 1);
-              } else {
-                float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-                for (int q = 0; q < 4 && tb + q < nt; ++q) {
-                  const float2 x = src[q];
-                  e[2 * q] = x.x;
-                  e[2 * q + 1] = x.y;
-                }
-                ca[u][0] = make_float4(e[0], e[1], e[2], e[3]);
-                ca[u][1] = make_float4(e[4], e[5], e[6], e[7]);
-              }
-            }
-          }
-        }
-        // B: W^T[z][t] from 4 x 4 blocks of W (4 rows t x 4 z), transposed in registers
-        float4 wb[4];
-        const int ib = tid;
-        if (ib < nbk) {
-          const int t4 = ib / q4, k4 = ib - t4 * q4, tb = t0 + 4 * t4;
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            wb[e] = tb + e < nt ? __ldg(reinterpret_cast<const float4*>(wc + (size_t)(tb + e) * P.z4) + k4)
-                                : make_float4(0.f, 0.f, 0.f, 0.f);
-        }
-#pragma unroll
-        for (int u = 0; u < AD_ITEMS; ++u) {
-          const int i = u * TC_THREADS + tid;
-          if (i < na) {
-            const int t4 = i / (nv * 4), vm = i - t4 * nv * 4, v = vm >> 2, m = vm & 3;
-            const int n = 8 * v + 2 * m;
-            const float4 re = make_float4(ca[u][0].x, ca[u][0].z, ca[u][1].x, ca[u][1].z);
-            const float4 im = make_float4(ca[u][0].y, ca[u][0].w, ca[u][1].y, ca[u][1].w);
-            st_split4(sm, P, umma::kmajor_off(NR, n, 4 * t4), re);
-            st_split4(sm, P, umma::kmajor_off(NR, n + 1, 4 * t4), im);
-          }
-        }
-        if (ib < nbk) {
-          const int t4 = ib / q4, k4 = ib - t4 * q4;
-          const float col[4][4] = {{wb[0].x, wb[1].x, wb[2].x, wb[3].x},
-                                   {wb[0].y, wb[1].y, wb[2].y, wb[3].y},
-                                   {wb[0].z, wb[1].z, wb[2].z, wb[3].z},
-                                   {wb[0].w, wb[1].w, wb[2].w, wb[3].w}};
-#pragma unroll
-          for (int a = 0; a < 4; ++a) {
-            float4 h, l;
-            umma::split_tf32(col[a][0], h.x, l.x);
-            umma::split_tf32(col[a][1], h.y, l.y);
-            umma::split_tf32(col[a][2], h.z, l.z);
-            umma::split_tf32(col[a][3], h.w, l.w);
-            const uint32_t o = umma::kmajor_off(P.zN, 4 * k4 + a, 4 * t4);
-            *reinterpret_cast<float4*>(sm + P.off_bhi + o) = h;
-            *reinterpret_cast<float4*>(sm + P.off_blo + o) = l;
-          }
-        }
-        publish();
-        if (tid == 0) {
-          for (int s = 0; s < tcc / 8; ++s) {
-            const uint64_t ah = umma::desc(sbase + P.off_ahi + s * 2 * NR * 16, NR * 16, 128);
-            const uint64_t al = umma::desc(sbase + P.off_alo + s * 2 * NR * 16, NR * 16, 128);
-            const uint64_t bh = umma::desc(sbase + P.off_bhi + s * 2 * P.zN * 16, P.zN * 16, 128);
-            const uint64_t bl = umma::desc(sbase + P.off_blo + s * 2 * P.zN * 16, P.zN * 16, 128);
-            umma::mma_tf32(taddr, al, bh, idesc, (t0 > 0 || s > 0) ? 1u : 0u);
-            umma::mma_tf32(taddr, ah, bl, idesc, 1);
-            umma::mma_tf32(taddr, ah, bh, idesc, 1);
-          }
-          umma::commit(bar);
-        }
-        wait_mma(bar, phase, timeout_flag);
+    for (int m = 0; m < 4; ++m) mem[m] = mem_next[m];
+    if (s + 1 < steps) {  // the other raw stage was last read by step s - 1's conversion
+      const AdjStep b = adj_step(P, s + 1, nvol, nvc, ntc);
+      if (b.c != a.c) load_members(members, b.c, mem_next);
+      adj_issue(P, sm, (s + 1) & 1, b, mem_next, what, vin, ld_in, in_vstride);
+    }
+    cp_commit();
+    cp_wait1();  // every group but the newest: step s's copies have landed
+    __syncthreads();
+    adj_convert(P, sm, s & 1, a);
+    publish();
+    if (tid == 0) {
+      for (int k = 0; k < a.tcc / 8; ++k) {
+        const uint64_t ah = umma::desc(sbase + P.off_ahi + k * 2 * NR * 16, NR * 16, 128);
+        const uint64_t al = umma::desc(sbase + P.off_alo + k * 2 * NR * 16, NR * 16, 128);
+        const uint64_t bh = umma::desc(sbase + P.off_bhi + k * 2 * P.zN * 16, P.zN * 16, 128);
+        const uint64_t bl = umma::desc(sbase + P.off_blo + k * 2 * P.zN * 16, P.zN * 16, 128);
+        umma::mma_tf32(taddr, al, bh, idesc, (a.t0 > 0 || k > 0) ? 1u : 0u);
+        umma::mma_tf32(taddr, ah, bl, idesc, 1);
+        umma::mma_tf32(taddr, ah, bh, idesc, 1);
       }
+      umma::commit(bar);
+    }
+    wait_mma(bar, phase, timeout_flag);
+    if (a.last) {
       // epilogue: TMEM lane n = 8 v + 2 m + c; column z.  Even lanes hold the
       // real parts, odd lanes the imaginary parts of the same output.
       const int n = 32 * (warp & 3) + lane, v = n >> 3, fm = pick(mem, (n >> 1) & 3);
-      const bool writer = (lane & 1) == 0 && v < nv && fm >= 0;
-      float2* dst = vout + (v0 + (v < nv ? v : 0)) * out_vstride + (size_t)(fm >= 0 ? fm : 0) * ld_out;
+      const bool writer = (lane & 1) == 0 && v < a.nv && fm >= 0;
+      float2* dst = vout + (a.v0 + (v < a.nv ? v : 0)) * out_vstride + (size_t)(fm >= 0 ? fm : 0) * ld_out;
       for (int j = warp >> 2; j < P.zN / 16; j += 2) {
         float d[16];
         umma::tmem_ld16(taddr + ((uint32_t)(32 * (warp & 3)) << 16) + 16 * j, d);
@@ -372,13 +405,13 @@ __global__ void __launch_bounds__(TC_THREADS, 4) k_contract_tc_adj(TcPlan P, con
         for (int e = 0; e < 16; ++e) {
           const float im = __shfl_down_sync(0xffffffffu, d[e], 1);
           const int z = 16 * j + e;
-          if (writer && z < nz) dst[z] = make_float2(d[e], im);
+          if (writer && z < P.nz) dst[z] = make_float2(d[e], im);
         }
       }
-      umma::fence_before_sync();
-      __syncthreads();
     }
+    // the next step's publish() orders these TMEM reads before its MMAs
   }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
   tc_teardown(taddr, P);
 }
 
