@@ -164,53 +164,78 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_fwd(TcPlan P, con
     const float* wc = what + (size_t)c * nt * P.z4;
     for (int v0 = 0; v0 < nvol; v0 += VB) {
       const int nv = nvol - v0 < VB ? nvol - v0 : VB;
-      // B: X[n][z] for the chunk's volumes (rows of absent members are zero);
-      // each batch issues all of its loads before the first store
-      const int nb = nv * 4 * nz;
-      for (int base = 0; base < nb; base += 8 * TC_THREADS) {
-        float2 x[8];
+      // B: X[n][z] for the chunk's volumes (rows of absent members are zero).
+      // A warp takes 8 (volume, member) rows x 4 chunks of 4 complex z: 128
+      // contiguous bytes per row on the load side, consecutive rows on the
+      // store side.  All loads are issued before the first store.
+      const int nvm = nv * 4, zq = (nz + 3) >> 2, kgb = (zq + 3) >> 2, nbb = ((nvm + 7) >> 3) * kgb;
+      {
+        float4 x[4][2];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int i = base + u * TC_THREADS + tid;
-          x[u] = make_float2(0.f, 0.f);
-          if (i < nb) {
-            const int v = i / (4 * nz), r = i - v * 4 * nz, m = r / nz, z = r - m * nz;
-            const int f = pick(mem, m);
-            if (f >= 0) x[u] = vin[(v0 + v) * in_vstride + (size_t)f * ld_in + z];
+        for (int u = 0; u < 4; ++u) {
+          const int blk = u * (TC_THREADS / 32) + warp, rg = blk / kgb, kg = blk - rg * kgb;
+          const int vm = 8 * rg + (lane & 7), zc = 4 * kg + (lane >> 3);
+          x[u][0] = x[u][1] = make_float4(0.f, 0.f, 0.f, 0.f);
+          const int f = vm < nvm ? pick(mem, vm & 3) : -1;
+          if (blk < nbb && vm < nvm && zc < zq && f >= 0) {
+            const float2* src = vin + (v0 + (vm >> 2)) * in_vstride + (size_t)f * ld_in + 4 * zc;
+            if (4 * zc + 4 <= nz) {
+              x[u][0] = __ldg(reinterpret_cast<const float4*>(src));
+              x[u][1] = __ldg(reinterpret_cast<const float4*>(src) + 1);
+            } else {
+              float e[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+              for (int q = 0; q < 4 && 4 * zc + q < nz; ++q) {
+                const float2 y = src[q];
+                e[2 * q] = y.x;
+                e[2 * q + 1] = y.y;
+              }
+              x[u][0] = make_float4(e[0], e[1], e[2], e[3]);
+              x[u][1] = make_float4(e[4], e[5], e[6], e[7]);
+            }
           }
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int i = base + u * TC_THREADS + tid;
-          if (i < nb) {
-            const int v = i / (4 * nz), r = i - v * 4 * nz, m = r / nz, z = r - m * nz;
-            const int n = 8 * v + 2 * m;
-            st_split1(sm + P.off_bhi, sm + P.off_blo, umma::kmajor_off(NR, n, z), x[u].x);
-            st_split1(sm + P.off_bhi, sm + P.off_blo, umma::kmajor_off(NR, n + 1, z), x[u].y);
+        for (int u = 0; u < 4; ++u) {
+          const int blk = u * (TC_THREADS / 32) + warp, rg = blk / kgb, kg = blk - rg * kgb;
+          const int vm = 8 * rg + (lane & 7), zc = 4 * kg + (lane >> 3);
+          if (blk < nbb && vm < nvm && zc < zq) {
+            const float4 re = make_float4(x[u][0].x, x[u][0].z, x[u][1].x, x[u][1].z);
+            const float4 im = make_float4(x[u][0].y, x[u][0].w, x[u][1].y, x[u][1].w);
+            float4 h, l;
+            umma::split_tf32(re.x, h.x, l.x);
+            umma::split_tf32(re.y, h.y, l.y);
+            umma::split_tf32(re.z, h.z, l.z);
+            umma::split_tf32(re.w, h.w, l.w);
+            *reinterpret_cast<float4*>(sm + P.off_bhi + umma::kmajor_off(NR, 2 * vm, 4 * zc)) = h;
+            *reinterpret_cast<float4*>(sm + P.off_blo + umma::kmajor_off(NR, 2 * vm, 4 * zc)) = l;
+            umma::split_tf32(im.x, h.x, l.x);
+            umma::split_tf32(im.y, h.y, l.y);
+            umma::split_tf32(im.z, h.z, l.z);
+            umma::split_tf32(im.w, h.w, l.w);
+            *reinterpret_cast<float4*>(sm + P.off_bhi + umma::kmajor_off(NR, 2 * vm + 1, 4 * zc)) = h;
+            *reinterpret_cast<float4*>(sm + P.off_blo + umma::kmajor_off(NR, 2 * vm + 1, 4 * zc)) = l;
           }
         }
       }
       for (int t0 = 0; t0 < nt; t0 += 128) {
         const int rows = nt - t0 < 128 ? nt - t0 : 128;
-        // A: W rows t0 .. t0 + rows, consecutive threads on consecutive rows
-        // (at most 128 x 16 float4, 8 per thread: all loads first)
-        const int na = rows * q4;
+        // A: W rows t0 .. t0 + rows.  A warp takes 8 rows x 4 float4 chunks
+        // (64 contiguous bytes per row to load, 8 consecutive 16-byte tile rows
+        // per store phase); at most 16 x 4 blocks, 8 per warp; loads first.
+        const int kga = (q4 + 3) >> 2, nba = ((rows + 7) >> 3) * kga;
         float4 w[8];
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const int i = u * TC_THREADS + tid;
-          if (i < na) {
-            const int k4 = i / rows, tl = i - k4 * rows;
+          const int blk = u * (TC_THREADS / 32) + warp, rg = blk / kga, kg = blk - rg * kga;
+          const int tl = 8 * rg + (lane & 7), k4 = 4 * kg + (lane >> 3);
+          if (blk < nba && tl < rows && k4 < q4)
             w[u] = __ldg(reinterpret_cast<const float4*>(wc + (size_t)(t0 + tl) * P.z4) + k4);
-          }
         }
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
-          const int i = u * TC_THREADS + tid;
-          if (i < na) {
-            const int k4 = i / rows, tl = i - k4 * rows;
-            st_split4(sm, P, umma::kmajor_off(128, tl, 4 * k4), w[u]);
-          }
+          const int blk = u * (TC_THREADS / 32) + warp, rg = blk / kga, kg = blk - rg * kga;
+          const int tl = 8 * rg + (lane & 7), k4 = 4 * kg + (lane >> 3);
+          if (blk < nba && tl < rows && k4 < q4) st_split4(sm, P, umma::kmajor_off(128, tl, 4 * k4), w[u]);
         }
         publish();
         if (tid == 0) {
