@@ -379,6 +379,69 @@ def run_batching(args, cfg):
         k.close()
 
 
+def run_contract_batch(args, cfg):
+    """Batched per-frequency contractions alone (ctof_contract_forward_batch / _adjoint_batch)
+    on random spectra of `--contract-batch` volumes at the config's size; one step = one
+    forward plus one adjoint launch over all volumes."""
+    import torch
+    from paper_2101_11680_gb300 import build as B
+    from paper_2101_11680_gb300 import ctof
+    B.build()
+    nvol = args.contract_batch
+    k = ctof.Kernel(ctof.make_optics(**OPTICS),
+                    ctof.make_grid(cfg["n"], cfg["nz"], cfg["nt"], cfg["dx"], cfg["dz"], cfg["z_first"], cfg["dt"]))
+    nf, nc = k.info.n_freq, k.info.n_class
+    gen = torch.Generator(device="cuda").manual_seed(args.seed)
+    xz = torch.randn((nvol, nf, k.ldz, 2), device="cuda", generator=gen)
+    xt = torch.randn((nvol, nf, k.ldt, 2), device="cuda", generator=gen)
+    ot = torch.zeros((nvol, nf, k.ldt, 2), device="cuda")
+    oz = torch.zeros((nvol, nf, k.ldz, 2), device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn):
+        for _ in range(args.warmup):
+            fn()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        return e0.elapsed_time(e1) / args.steps
+
+    clocks = ClockSampler(torch.cuda.current_device())
+    clocks.start()
+    fwd_ms = timed(lambda: k.contract_forward_batch(xz, out=ot))
+    adj_ms = timed(lambda: k.contract_adjoint_batch(xt, out=oz))
+    clk = clocks.stop()
+    w_bytes = nc * cfg["nt"] * ((cfg["nz"] + 3) // 4 * 4) * 4
+    vz, vt = nvol * nf * cfg["nz"] * 8, nvol * nf * cfg["nt"] * 8
+    alg = w_bytes + vz + vt  # each direction reads W_hat and one side, writes the other
+    peak, peak_src = _peaks()
+    path = "tcgen05 (3xTF32)" if nvol >= 4 else "FP32 CUDA cores"
+    line = {
+        "metric": "volumes/s through one batched forward + adjoint contraction pair", "value":
+        nvol / ((fwd_ms + adj_ms) * 1e-3), "unit": "volumes/s", "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": fwd_ms + adj_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32 (%s)" % path, "data": "synthetic",
+        "config": {"workload": cfg["workload"] + " [spectra-level contractions of %d volumes]" % nvol,
+                   "volumes": nvol, "n_class": nc, "n_freq": nf,
+                   "l2": "inputs larger than L2 (W_hat %.0f MB + spectra)" % (w_bytes / 1e6)},
+        "forward": {"ms": fwd_ms, "algorithmic_bytes": alg, "achieved_gbs": alg / (fwd_ms * 1e-3) / 1e9,
+                    "frac": alg / (fwd_ms * 1e-3) / 1e9 / peak},
+        "adjoint": {"ms": adj_ms, "algorithmic_bytes": alg, "achieved_gbs": alg / (adj_ms * 1e-3) / 1e9,
+                    "frac": alg / (adj_ms * 1e-3) / 1e9 / peak},
+        "roofline": {"bound": "hbm", "kernel": "k_contract_tc_adj" if nvol >= 4 else "k_contract<1>",
+                     "achieved": alg / (adj_ms * 1e-3) / 1e9, "peak": peak, "unit": "GB/s",
+                     "frac": alg / (adj_ms * 1e-3) / 1e9 / peak, "traffic": None, "peak_source": peak_src},
+        "gpu_launches": 2 * args.steps,
+        "clocks": clk,
+    }
+    print(json.dumps(line), flush=True)
+    k.close()
+
+
 def run_fista(args, cfg):
     """The paper's own solver (FISTA, layer-weighted L1, Eq. 8 and Eq. 10) on the config-2 workload."""
     import torch
@@ -557,6 +620,9 @@ def main():
     ap.add_argument("--average", default=None,
                     help="LAYERS,NODES: average the first LAYERS depth layers over the voxel with NODES "
                          "Gauss-Legendre points per axis (kernel build only)")
+    ap.add_argument("--contract-batch", type=int, default=0,
+                    help="time the batched spectra-level forward/adjoint contractions of this many volumes "
+                         "(4 or more: the tcgen05 kernels) instead of a reconstruction")
     ap.add_argument("--solver", default="admm", choices=["admm", "fista"],
                     help="default-config solver: ADMM-TV (the benchmark) or the paper's FISTA-L1")
     args = ap.parse_args()
@@ -577,6 +643,9 @@ def main():
         cfg["iters"] = args.iters
     if args.solver == "fista" and args.impl == "ours":
         run_fista(args, cfg)
+        return
+    if args.contract_batch and args.impl == "ours":
+        run_contract_batch(args, cfg)
         return
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
