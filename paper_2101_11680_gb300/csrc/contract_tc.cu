@@ -318,17 +318,37 @@ __device__ __forceinline__ void adj_issue(const TcPlan& P, unsigned char* sm, in
   unsigned char* rc = sm + P.off_raw + stage * P.raw_stage;
   unsigned char* rw = rc + P.raw_c;
   const int nt = P.nt, q4 = P.z4 >> 2, pieces = a.tcc >> 1, nvm = a.nv * 4;
-  for (int i = threadIdx.x; i < nvm * pieces; i += TC_THREADS) {
-    const int vm = i / pieces, p = i - vm * pieces, f = pick(mem, vm & 3), t = a.t0 + 2 * p;
-    const int bytes = f < 0 ? 0 : (t + 2 <= nt ? 16 : (t < nt ? 8 : 0));
-    const float2* src = bytes ? vin + (a.v0 + (vm >> 2)) * in_vstride + (size_t)f * ld_in + t : vin;
-    cp_async16z(rc + vm * RCS + p * 16, src, bytes);
+  // (row, piece) of copy i = tid + k * TC_THREADS, advanced without divisions
+  {
+    int vm = threadIdx.x / pieces, p = threadIdx.x - vm * pieces;
+    const int dvm = TC_THREADS / pieces, dp = TC_THREADS - dvm * pieces;
+    while (vm < nvm) {
+      const int f = pick(mem, vm & 3), t = a.t0 + 2 * p;
+      const int bytes = f < 0 ? 0 : (t + 2 <= nt ? 16 : (t < nt ? 8 : 0));
+      const float2* src = bytes ? vin + (a.v0 + (vm >> 2)) * in_vstride + (size_t)f * ld_in + t : vin;
+      cp_async16z(rc + vm * RCS + p * 16, src, bytes);
+      vm += dvm;
+      p += dp;
+      if (p >= pieces) {
+        p -= pieces;
+        ++vm;
+      }
+    }
   }
   const float* wc = what + (size_t)a.c * nt * P.z4;
-  for (int i = threadIdx.x; i < a.tcc * q4; i += TC_THREADS) {
-    const int tl = i / q4, k4 = i - tl * q4, t = a.t0 + tl;
-    const int bytes = t < nt ? 16 : 0;
-    cp_async16z(rw + i * 16, bytes ? wc + (size_t)t * P.z4 + 4 * k4 : what, bytes);
+  {
+    int tl = threadIdx.x / q4, k4 = threadIdx.x - tl * q4;
+    const int dtl = TC_THREADS / q4, dk = TC_THREADS - dtl * q4;
+    while (tl < a.tcc) {
+      const int t = a.t0 + tl, bytes = t < nt ? 16 : 0;
+      cp_async16z(rw + (tl * q4 + k4) * 16, bytes ? wc + (size_t)t * P.z4 + 4 * k4 : what, bytes);
+      tl += dtl;
+      k4 += dk;
+      if (k4 >= q4) {
+        k4 -= q4;
+        ++tl;
+      }
+    }
   }
 }
 
@@ -337,12 +357,21 @@ __device__ __forceinline__ void adj_convert(const TcPlan& P, unsigned char* sm, 
   const unsigned char* rw = rc + P.raw_c;
   const int q4 = P.z4 >> 2, nvm = a.nv * 4, t4n = a.tcc >> 2;
   // A: C[n][t] from the raw rows; consecutive threads on consecutive rows
-  for (int i = threadIdx.x; i < nvm * t4n; i += TC_THREADS) {
-    const int t4 = i / nvm, vm = i - t4 * nvm;
-    const float4* r = reinterpret_cast<const float4*>(rc + vm * RCS + t4 * 32);
-    const float4 x0 = r[0], x1 = r[1];
-    st_split4(sm, P, umma::kmajor_off(NR, 2 * vm, 4 * t4), make_float4(x0.x, x0.z, x1.x, x1.z));
-    st_split4(sm, P, umma::kmajor_off(NR, 2 * vm + 1, 4 * t4), make_float4(x0.y, x0.w, x1.y, x1.w));
+  {
+    int t4 = threadIdx.x / nvm, vm = threadIdx.x - t4 * nvm;
+    const int dt = TC_THREADS / nvm, dv = TC_THREADS - dt * nvm;
+    while (t4 < t4n) {
+      const float4* r = reinterpret_cast<const float4*>(rc + vm * RCS + t4 * 32);
+      const float4 x0 = r[0], x1 = r[1];
+      st_split4(sm, P, umma::kmajor_off(NR, 2 * vm, 4 * t4), make_float4(x0.x, x0.z, x1.x, x1.z));
+      st_split4(sm, P, umma::kmajor_off(NR, 2 * vm + 1, 4 * t4), make_float4(x0.y, x0.w, x1.y, x1.w));
+      t4 += dt;
+      vm += dv;
+      if (vm >= nvm) {
+        vm -= nvm;
+        ++t4;
+      }
+    }
   }
   // B: W^T[z][t] from 4 x 4 blocks of the raw W rows, transposed in registers
   for (int i = threadIdx.x; i < t4n * q4; i += TC_THREADS) {
