@@ -304,6 +304,50 @@ __global__ void __launch_bounds__(CT_THREADS) k_contract(const float* __restrict
 
 constexpr size_t SMEM_LIMIT = 227 * 1024;
 
+// In-place application of the per-class Tikhonov inverse to batched adjoint
+// results: x[v][f][i] = sum_j Hinv_c[j][i] x[v][f][j] for every member f of
+// class c and volume v (Hinv symmetric, FP32, formed in FP64).  A CTA stages
+// the class's inverse and up to 16 volumes' member vectors in shared memory;
+// consecutive threads take consecutive i, so the inverse is read along its
+// rows without bank conflicts and each vector entry is a broadcast.
+constexpr int HV = 16;  // volumes per staged chunk
+
+__global__ void __launch_bounds__(256) k_apply_hinv(const float* __restrict__ hinv, const int* __restrict__ members,
+                                                    int nclass, int nz, int z4, int nvol, float2* __restrict__ x,
+                                                    int ldz, size_t vstride) {
+  extern __shared__ __align__(16) float hsm[];
+  float* sH = hsm;                                          // [nz][z4]
+  float2* sV = reinterpret_cast<float2*>(hsm + nz * z4);    // [HV * 4][nz]
+  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
+    int mem[4];
+#pragma unroll
+    for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
+    __syncthreads();  // the previous class's reads of sH / sV are done
+    for (int i = threadIdx.x; i < nz * z4; i += blockDim.x) sH[i] = __ldg(hinv + (size_t)c * nz * z4 + i);
+    for (int v0 = 0; v0 < nvol; v0 += HV) {
+      const int nv = nvol - v0 < HV ? nvol - v0 : HV;
+      for (int o = threadIdx.x; o < nv * 4 * nz; o += blockDim.x) {
+        const int r = o / nz, j = o - r * nz, f = mem[r & 3];
+        sV[r * nz + j] = f >= 0 ? x[(v0 + (r >> 2)) * vstride + (size_t)f * ldz + j] : make_float2(0.f, 0.f);
+      }
+      __syncthreads();
+      for (int o = threadIdx.x; o < nv * 4 * nz; o += blockDim.x) {
+        const int r = o / nz, i = o - r * nz, f = mem[r & 3];
+        if (f < 0) continue;
+        const float2* vr = sV + r * nz;
+        float re = 0.f, im = 0.f;
+        for (int j = 0; j < nz; ++j) {
+          const float h = sH[j * z4 + i];
+          re = fmaf(h, vr[j].x, re);
+          im = fmaf(h, vr[j].y, im);
+        }
+        x[(v0 + (r >> 2)) * vstride + (size_t)f * ldz + i] = make_float2(re, im);
+      }
+      __syncthreads();
+    }
+  }
+}
+
 template <int MODE>
 ctof_status launch(const ctof_kernel_s* k, int nvol, const float2* vin, int ld_in, size_t in_vstride, float2* vout,
                    int ld_out, size_t out_vstride, const float* hinv, cudaStream_t st) {
@@ -392,6 +436,21 @@ ctof_status contract_adjoint_batch(const ctof_kernel_s* k, int nvol, const float
 
 ctof_status contract_tikhonov_batch(const ctof_kernel_s* k, int nvol, const float* hinv, const float2* m_hat,
                                     float2* x_hat, cudaStream_t st) {
+  if (nvol >= TC_MIN_VOLUMES) {
+    // W_hat^T m_hat on the tensor cores, then the per-class inverse in place
+    CTOF_TRY(contract_tc_adjoint(k, nvol, m_hat, x_hat, st));
+    const int z4 = (k->nz + 3) & ~3;
+    const size_t sm = (size_t)k->nz * z4 * 4 + (size_t)HV * 4 * k->nz * 8;
+    CTOF_CUDA_TRY(cudaFuncSetAttribute(k_apply_hinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
+    const int per_sm = (int)((228 * 1024) / (sm + 1024)) < 4 ? (int)((228 * 1024) / (sm + 1024)) : 4;
+    const int grid = k->nclass < per_sm * nsm ? k->nclass : per_sm * nsm;
+    k_apply_hinv<<<grid, 256, sm, st>>>(hinv, k->d_members, k->nclass, k->nz, z4, nvol, x_hat, k->ldz,
+                                        (size_t)k->nf * k->ldz);
+    CTOF_CUDA_TRY(cudaGetLastError());
+    return CTOF_OK;
+  }
   return launch<MODE_TIK>(k, nvol, m_hat, k->ldt, (size_t)k->nf * k->ldt, x_hat, k->ldz, (size_t)k->nf * k->ldz, hinv,
                           st);
 }

@@ -163,6 +163,27 @@ def test_learned_data_consistency_steps_match_oracle():
     net.close()
 
 
+def test_learned_batch_of_five_matches_oracle():
+    """A batch of five volumes takes the batched tensor-core contractions (forward,
+    adjoint, and the Tikhonov start / data-consistency solves: adjoint on tcgen05
+    plus the per-class inverse); every member still matches the FP64 oracle run
+    on it alone, at the bound of the single-volume Tikhonov-start test."""
+    k = device_kernel(CASE)
+    fwd, adj, s = _oracle_ops()
+    g, _, wh = oracle_kernel(CASE)
+    theta = _on_bf16_grid(_params(27))
+    net = ctof.Learned(STAGES, theta, x0_lambda_rel=1e-3, dc_steps=2, dc_lambda_rel=1e-4)
+    probs = [_problem(800 + i) for i in range(5)]
+    d_m = torch.tensor(np.stack([m for _, m in probs]), dtype=torch.float32, device="cuda")
+    got = net.reconstruct(k, d_m).cpu().numpy()
+    tik = lambda r: so.tikhonov(wh / s, r, g, 1e-4)[0]
+    for b, (mu, m) in enumerate(probs):
+        x0 = so.tikhonov(wh, m, g, 1e-3)[0]
+        want = ln.unrolled(theta, STAGES, fwd, adj, m / s, rnd=ln.bf16, x0=x0, dc_steps=2, dc_solve=tik)
+        assert rel_l2(got[b], want) <= 2e-3, b
+    net.close()
+
+
 def test_trained_network_gains_over_untrained_and_admm():
     """The shipped parameters, on held-out seeded phantoms at the training geometry
     (64 x 64 scan at 0.5 mm, 48 depths, 256 bins of 25 ps, Poisson peak 1e5): the
