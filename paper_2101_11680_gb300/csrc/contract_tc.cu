@@ -476,12 +476,18 @@ ctof_status launch_tc(K kern, const TcPlan& P, const ctof_kernel_s* k, int nvol,
   CTOF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, P.total));
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
+  // resident CTAs per SM: shared memory, registers (65,536 per SM, allocated
+  // in units of 8 per thread) and TMEM (512 columns per SM), at most 4; the
+  // persistent grid is exactly that many CTAs per SM
   int per_sm = (228 * 1024) / (P.total + 1024);
-  if (per_sm < 1) per_sm = 1;
-  // TMEM: per_sm x ncols <= 512 columns
+  cudaFuncAttributes fa;
+  CTOF_CUDA_TRY(cudaFuncGetAttributes(&fa, kern));
+  const int regs = (fa.numRegs + 7) / 8 * 8 * TC_THREADS;
+  if (regs > 0 && 65536 / regs < per_sm) per_sm = 65536 / regs;
   const int tmem_cap = (int)(512 / P.ncols);
   if (per_sm > 4) per_sm = 4;
   if (per_sm > tmem_cap) per_sm = tmem_cap;
+  if (per_sm < 1) per_sm = 1;
   const int grid = k->nclass < per_sm * nsm ? k->nclass : per_sm * nsm;
   int* flag = reinterpret_cast<int*>(k->d_scalars + 9);
   kern<<<grid, TC_THREADS, P.total, st>>>(P, k->d_what, k->d_members, k->nclass, nvol, vin, ld_in, in_vstride, vout,
