@@ -434,22 +434,38 @@ ctof_status contract_adjoint_batch(const ctof_kernel_s* k, int nvol, const float
                           nullptr, st);
 }
 
+namespace {
+
+// x[v][f][:] <- Hinv_c x[v][f][:] for every class member f and volume v; volume v
+// of frequency f at x + v * vstride + f * ld.
+ctof_status apply_hinv(const ctof_kernel_s* k, int nvol, const float* hinv, float2* x, int ld, size_t vstride,
+                       cudaStream_t st) {
+  const int z4 = (k->nz + 3) & ~3;
+  const size_t sm = (size_t)k->nz * z4 * 4 + (size_t)HV * 4 * k->nz * 8;
+  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_apply_hinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
+  const int per_sm = (int)((228 * 1024) / (sm + 1024)) < 4 ? (int)((228 * 1024) / (sm + 1024)) : 4;
+  const int grid = k->nclass < per_sm * nsm ? k->nclass : per_sm * nsm;
+  k_apply_hinv<<<grid, 256, sm, st>>>(hinv, k->d_members, k->nclass, k->nz, z4, nvol, x, ld, vstride);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+}  // namespace
+
+ctof_status contract_tikhonov_zb(const ctof_kernel_s* k, int nvol, const float* hinv, const float2* m_hat,
+                                 float2* x_hat, int ldzb, cudaStream_t st) {
+  CTOF_TRY(contract_tc_adjoint_zb(k, nvol, m_hat, x_hat, ldzb, st));
+  return apply_hinv(k, nvol, hinv, x_hat, ldzb, (size_t)k->nz, st);
+}
+
 ctof_status contract_tikhonov_batch(const ctof_kernel_s* k, int nvol, const float* hinv, const float2* m_hat,
                                     float2* x_hat, cudaStream_t st) {
   if (nvol >= TC_MIN_VOLUMES) {
     // W_hat^T m_hat on the tensor cores, then the per-class inverse in place
     CTOF_TRY(contract_tc_adjoint(k, nvol, m_hat, x_hat, st));
-    const int z4 = (k->nz + 3) & ~3;
-    const size_t sm = (size_t)k->nz * z4 * 4 + (size_t)HV * 4 * k->nz * 8;
-    CTOF_CUDA_TRY(cudaFuncSetAttribute(k_apply_hinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
-    int nsm = 152;
-    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
-    const int per_sm = (int)((228 * 1024) / (sm + 1024)) < 4 ? (int)((228 * 1024) / (sm + 1024)) : 4;
-    const int grid = k->nclass < per_sm * nsm ? k->nclass : per_sm * nsm;
-    k_apply_hinv<<<grid, 256, sm, st>>>(hinv, k->d_members, k->nclass, k->nz, z4, nvol, x_hat, k->ldz,
-                                        (size_t)k->nf * k->ldz);
-    CTOF_CUDA_TRY(cudaGetLastError());
-    return CTOF_OK;
+    return apply_hinv(k, nvol, hinv, x_hat, k->ldz, (size_t)k->nf * k->ldz, st);
   }
   return launch<MODE_TIK>(k, nvol, m_hat, k->ldt, (size_t)k->nf * k->ldt, x_hat, k->ldz, (size_t)k->nf * k->ldz, hinv,
                           st);

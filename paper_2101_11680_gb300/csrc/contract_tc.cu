@@ -511,3 +511,17 @@ ctof_status contract_tc_adjoint(const ctof_kernel_s* k, int nvol, const float2* 
   return launch_tc(k_contract_tc_adj, plan_adj(k->nt, k->nz), k, nvol, in_t, k->ldt, (size_t)k->nf * k->ldt, out_z,
                    k->ldz, (size_t)k->nf * k->ldz, st);
 }
+
+ctof_status contract_tc_forward_zb(const ctof_kernel_s* k, int nvol, const float2* in_z, int ldzb, float2* out_t,
+                                   cudaStream_t st) {
+  if (nvol < 1 || (k->nz & 1) || (ldzb & 7) || ldzb < nvol * k->nz) return CTOF_EINVAL;
+  return launch_tc(k_contract_tc_fwd, plan_fwd(k->nt, k->nz), k, nvol, in_z, ldzb, (size_t)k->nz, out_t, k->ldt,
+                   (size_t)k->nf * k->ldt, st);
+}
+
+ctof_status contract_tc_adjoint_zb(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z, int ldzb,
+                                   cudaStream_t st) {
+  if (nvol < 1 || (k->nz & 1) || (ldzb & 7) || ldzb < nvol * k->nz) return CTOF_EINVAL;
+  return launch_tc(k_contract_tc_adj, plan_adj(k->nt, k->nz), k, nvol, in_t, k->ldt, (size_t)k->nf * k->ldt, out_z,
+                   ldzb, (size_t)k->nz, st);
+}

@@ -156,6 +156,17 @@ ctof_status contract_tc_forward(const ctof_kernel_s* k, int nvol, const float2* 
                                 cudaStream_t st);
 ctof_status contract_tc_adjoint(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z,
                                 cudaStream_t st);
+// The same with the Z-side spectra of all volumes interleaved per frequency
+// (the output layout of one plane-batched FFT over nvol * nz planes): volume
+// v's plane z at column v * nz + z of row f, row pitch ldzb (a multiple of 8,
+// >= nvol * nz).  nz must be even (16-byte aligned volume rows); T-side
+// spectra stay [v][f][ldt].  EINVAL otherwise.
+ctof_status contract_tc_forward_zb(const ctof_kernel_s* k, int nvol, const float2* in_z, int ldzb, float2* out_t,
+                                   cudaStream_t st);
+ctof_status contract_tc_adjoint_zb(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z, int ldzb,
+                                   cudaStream_t st);
+ctof_status contract_tikhonov_zb(const ctof_kernel_s* k, int nvol, const float* hinv, const float2* m_hat,
+                                 float2* x_hat, int ldzb, cudaStream_t st);
 ctof_status contract_forward_batch(const ctof_kernel_s* k, int nvol, const float2* in_z, float2* out_t,
                                    cudaStream_t st);
 ctof_status contract_adjoint_batch(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z,

@@ -568,7 +568,11 @@ struct Ws {
   __nv_bfloat16 *da, *db_;  // [V][16]
   float* part;
   int nblk;
-  float2 *spec_t, *spec_z;  // [batch][nf][ldt], [batch][nf][ldz]
+  float2 *spec_t, *spec_z;  // [batch][nf][ldt], [batch][nf][ldz] (or [nf][ldzb], see zb)
+  // Z side as one plane-batched FFT over batch * nz planes (batch >= 4, nz even):
+  // spectra interleaved per frequency, row pitch ldzb, own FFT intermediate
+  float2* inter_zb;
+  int ldzb;
 };
 
 ctof_status learned_workspace(ctof_learned_s* L, const ctof_kernel_s* k, int batch, bool train, Ws* w) {
@@ -590,6 +594,8 @@ ctof_status learned_workspace(ctof_learned_s* L, const ctof_kernel_s* k, int bat
   const size_t o_da = add(V * CH * 2), o_db = add(V * CH * 2);
   const size_t o_p = add((size_t)nblk * 27 * CH * CH * 4);
   const size_t o_st = add((size_t)batch * k->nf * k->ldt * 8), o_sz = add((size_t)batch * k->nf * k->ldz * 8);
+  const bool zb = batch >= 4 && (k->nz % 2) == 0;
+  const size_t o_izb = add(zb ? fft_inter_elems(k, batch * k->nz, k->n) * 8 : 0);
   if (need > L->ws_bytes) {
     if (L->d_ws) cudaFree(L->d_ws);
     L->d_ws = nullptr;
@@ -617,6 +623,8 @@ ctof_status learned_workspace(ctof_learned_s* L, const ctof_kernel_s* k, int bat
   w->part = reinterpret_cast<float*>(b + o_p);
   w->spec_t = reinterpret_cast<float2*>(b + o_st);
   w->spec_z = reinterpret_cast<float2*>(b + o_sz);
+  w->inter_zb = zb ? reinterpret_cast<float2*>(b + o_izb) : nullptr;
+  w->ldzb = zb ? ctof_round_up(batch * k->nz, 8) : 0;
   w->nblk = nblk;
   return CTOF_OK;
 }
@@ -679,9 +687,15 @@ ctof_status wgrad(const __nv_bfloat16* dy, const __nv_bfloat16* x, int relu_in, 
 ctof_status op_forward(ctof_kernel_s* k, int batch, const float* x, float* meas, const Ws& w, cudaStream_t st) {
   const size_t vol = (size_t)k->nz * k->n * k->n, mt = (size_t)k->nt * k->n * k->n;
   const size_t sz = (size_t)k->nf * k->ldz, stt = (size_t)k->nf * k->ldt;
-  for (int b = 0; b < batch; ++b)
-    CTOF_TRY(fft_forward_planes(k, x + b * vol, k->nz, k->n, k->n, k->n, k->d_inter_z, w.spec_z + b * sz, k->ldz, st));
-  CTOF_TRY(contract_forward_batch(k, batch, w.spec_z, w.spec_t, st));
+  if (w.inter_zb) {  // all volumes' depth planes as one transform
+    CTOF_TRY(fft_forward_planes(k, x, batch * k->nz, k->n, k->n, k->n, w.inter_zb, w.spec_z, w.ldzb, st));
+    CTOF_TRY(contract_tc_forward_zb(k, batch, w.spec_z, w.ldzb, w.spec_t, st));
+  } else {
+    for (int b = 0; b < batch; ++b)
+      CTOF_TRY(fft_forward_planes(k, x + b * vol, k->nz, k->n, k->n, k->n, k->d_inter_z, w.spec_z + b * sz, k->ldz,
+                                  st));
+    CTOF_TRY(contract_forward_batch(k, batch, w.spec_z, w.spec_t, st));
+  }
   for (int b = 0; b < batch; ++b)
     CTOF_TRY(fft_inverse_planes(k, w.spec_t + b * stt, k->ldt, k->nt, k->n, k->n, k->d_inter_t, meas + b * mt, k->n,
                                 st));
@@ -695,6 +709,13 @@ ctof_status op_adjoint(ctof_kernel_s* k, int batch, const float* r, float* out, 
   const size_t sz = (size_t)k->nf * k->ldz, stt = (size_t)k->nf * k->ldt;
   for (int b = 0; b < batch; ++b)
     CTOF_TRY(fft_forward_planes(k, r + b * mt, k->nt, k->n, k->n, k->n, k->d_inter_t, w.spec_t + b * stt, k->ldt, st));
+  if (w.inter_zb) {  // all volumes' depth planes as one transform
+    if (tik_hinv)
+      CTOF_TRY(contract_tikhonov_zb(k, batch, tik_hinv, w.spec_t, w.spec_z, w.ldzb, st));
+    else
+      CTOF_TRY(contract_tc_adjoint_zb(k, batch, w.spec_t, w.spec_z, w.ldzb, st));
+    return fft_inverse_planes(k, w.spec_z, w.ldzb, batch * k->nz, k->n, k->n, w.inter_zb, out, k->n, st);
+  }
   if (tik_hinv)
     CTOF_TRY(contract_tikhonov_batch(k, batch, tik_hinv, w.spec_t, w.spec_z, st));
   else
