@@ -30,6 +30,13 @@
  *  - Every function returns ctof_status (0 = success); nothing throws
  *    across the ABI.  The GPU path has no CPU fallback: if no CUDA device is
  *    usable, calls that compute return CTOF_ECUDA.
+ *  - Device-side waits (the tensor-core kernels' completion barriers) are
+ *    bounded: one that runs out sets a sticky flag on the handle, lets the
+ *    work in flight drain and stops its thread block, so that call's output
+ *    is incomplete.  The flag is read and cleared by the next synchronising
+ *    call on the handle (ctof_reconstruct with a report,
+ *    ctof_reconstruct_host, ctof_learned_loss_grad, ctof_learned_train_step
+ *    with a loss, ctof_sync_status), which then returns CTOF_ETIMEOUT.
  */
 #ifndef CTOF_H
 #define CTOF_H
@@ -236,8 +243,9 @@ ctof_status ctof_forward_multiplexed(ctof_kernel k, const float* d_mu, float* d_
  * Input entries beyond nz / nt are ignored, output entries beyond them are
  * not written.  From 4 volumes on, 16 volumes and one frequency class form
  * one 128-wide tcgen05 GEMM (3xTF32, FP32-level accuracy); fewer volumes take
- * the FP32 CUDA-core path.  Asynchronous on `stream`.  Errors: EINVAL (null
- * pointer, nvol < 1), ECUDA. */
+ * the FP32 CUDA-core path.  Asynchronous on `stream`; a device wait that runs
+ * out is reported by the next synchronising call (ctof_sync_status).
+ * Errors: EINVAL (null pointer, nvol < 1), ECUDA. */
 ctof_status ctof_contract_forward_batch(ctof_kernel k, int nvol, const float* d_in, float* d_out, void* stream);
 ctof_status ctof_contract_adjoint_batch(ctof_kernel k, int nvol, const float* d_in, float* d_out, void* stream);
 ctof_status ctof_adjoint_multiplexed(ctof_kernel k, const float* d_y, float* d_vol, void* stream);
@@ -345,11 +353,15 @@ ctof_status ctof_reconstruct_batch_tikhonov(ctof_kernel k, int batch, const floa
  * one fixed 32 MiB array inside the library image instead of the handle's
  * workspace, and the call makes no cudaMalloc/cudaFree or other allocating
  * call.  (The paper has no counterpart; this exists for callers that may not
- * allocate device memory at the point of the call: code inside a CUDA stream
- * capture, real-time loops that must not block on an allocator, frameworks
- * that own every device allocation.)  The handle must already be built.
+ * allocate device memory at the point of the call: real-time acquisition
+ * loops that must never wait on an allocator, and host frameworks or plugins
+ * that own every device allocation and give the library only its inputs and
+ * outputs.)  The handle must already be built.
  * The first call on a device resolves the array's device address with that
- * device current; make that first call before any stream capture begins.
+ * device current and keeps it for the life of the process; make that first
+ * call before any stream capture begins.  The kept address does not survive
+ * cudaDeviceReset (or any other teardown of the device's primary context):
+ * do not call this entry point after one.
  * All calls share the array: calls that overlap on the GPU race and corrupt
  * each other; serialise them.  Grids whose intermediates exceed 32 MiB are
  * rejected with CTOF_EUNSUPPORTED (ctof_last_error_message gives the size).
@@ -374,6 +386,19 @@ typedef struct {
 
 ctof_status ctof_set_timing(ctof_kernel k, int enable);
 ctof_status ctof_get_timing(ctof_kernel k, ctof_timing* out);
+
+/* Bounded device waits (not from the paper: a safety property of this
+ * library).  ctof_set_wait_limit sets how many times a kernel of this handle
+ * polls a completion barrier before it gives up (default 2^24; 0 makes every
+ * such wait give up at once, which tests use to exercise the error path).
+ * polls < 0: EINVAL.  Host-only, takes effect at the next launch. */
+ctof_status ctof_set_wait_limit(ctof_kernel k, long long polls);
+
+/* Synchronises `stream`, then reads and clears the handle's sticky device
+ * status: CTOF_ETIMEOUT if a bounded device wait of one of the handle's
+ * kernels ran out since the last synchronising call (the output of that
+ * call is incomplete), CTOF_OK otherwise. */
+ctof_status ctof_sync_status(ctof_kernel k, void* stream);
 
 const char* ctof_status_string(ctof_status s);
 

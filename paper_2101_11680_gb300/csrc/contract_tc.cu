@@ -18,6 +18,11 @@
 // reads its 32-lane quarter of TMEM for the epilogue.  Persistent CTAs walk
 // the classes; two fit on an SM when their shared memory allows, so one
 // CTA's staging overlaps the other's MMAs and stores.
+// A wait that runs out (after the handle's poll limit) sets the handle's
+// sticky status flag, waits again with the fixed drain limit so that no MMA
+// is left in flight, and the whole CTA then stops (a block-wide vote), frees
+// its TMEM and returns; the host reports CTOF_ETIMEOUT at the next
+// synchronising call.
 #include <cuda_runtime.h>
 
 #include "ctof_internal.h"
@@ -30,7 +35,7 @@ constexpr int VB = 16;         // volumes per chunk
 constexpr int NR = 8 * VB;     // right-hand sides per chunk (the 128-wide GEMM side)
 constexpr int TCH = 32;        // adjoint: t values per staged K chunk
 constexpr int RCS = TCH * 8 + 16;  // adjoint raw stage: bytes per (volume, member) row, padded
-constexpr long long MAX_POLLS = 1ll << 24;
+constexpr long long DRAIN_POLLS = 1ll << 24;  // polls of the wait that follows a timeout
 
 struct TcPlan {
   int nt, nz, z4, zK, zN, tK, tc;
@@ -134,35 +139,43 @@ __device__ __forceinline__ void publish() {
   umma::fence_after_sync();
 }
 
-// Wait for the committed MMAs (phase parity), flag a timeout.
-__device__ __forceinline__ void wait_mma(uint64_t* bar, uint32_t& phase, int* timeout_flag) {
-  if (!umma::mbar_wait(bar, phase, MAX_POLLS)) {
-    if ((threadIdx.x & 31) == 0) atomicExch(timeout_flag, 1);
-    umma::mbar_wait(bar, phase, MAX_POLLS);
+// Wait for the committed MMAs (phase parity).  After max_polls polls the
+// wait gives up: it sets the timeout flag and drains (waits up to
+// DRAIN_POLLS more for the MMAs in flight).  Block-wide: returns true when
+// any thread of the CTA gave up, and then the CTA must stop.
+__device__ __forceinline__ bool wait_mma(uint64_t* bar, uint32_t& phase, int* timeout_flag, long long max_polls) {
+  int gave_up = 0;
+  if (!umma::mbar_wait(bar, phase, max_polls)) {
+    gave_up = 1;
+    atomicExch(timeout_flag, 1);
+    umma::mbar_wait(bar, phase, DRAIN_POLLS);
   }
   phase ^= 1u;
   umma::fence_after_sync();
+  return __syncthreads_or(gave_up) != 0;
 }
 
 __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_fwd(TcPlan P, const float* __restrict__ what,
                                                                const int* __restrict__ members, int nclass, int nvol,
                                                                const float2* __restrict__ vin, int ld_in,
                                                                size_t in_vstride, float2* __restrict__ vout,
-                                                               int ld_out, size_t out_vstride, int* timeout_flag) {
+                                                               int ld_out, size_t out_vstride, int* timeout_flag,
+                                                               long long max_polls) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const uint32_t taddr = tc_setup(sm, P);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.off_bar);
   uint32_t phase = 0;
+  bool stop = false;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int nt = P.nt, nz = P.nz, q4 = P.z4 >> 2;
   const uint32_t idesc = umma::idesc_tf32(128, NR);
   const uint32_t sbase = umma::smem_u32(sm);
-  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
+  for (int c = blockIdx.x; c < nclass && !stop; c += gridDim.x) {
     int mem[4];
 #pragma unroll
     for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
     const float* wc = what + (size_t)c * nt * P.z4;
-    for (int v0 = 0; v0 < nvol; v0 += VB) {
+    for (int v0 = 0; v0 < nvol && !stop; v0 += VB) {
       const int nv = nvol - v0 < VB ? nvol - v0 : VB;
       // B: X[n][z] for the chunk's volumes (rows of absent members are zero).
       // A warp takes 8 (volume, member) rows x 4 chunks of 4 complex z: 128
@@ -251,7 +264,10 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_fwd(TcPlan P, con
           }
           umma::commit(bar);
         }
-        wait_mma(bar, phase, timeout_flag);
+        if (wait_mma(bar, phase, timeout_flag, max_polls)) {
+          stop = true;
+          break;
+        }
         // epilogue: TMEM lane = t row of the tile; warps w and w + 4 split the 8 column groups
         const int tl = 32 * (warp & 3) + lane, t = t0 + tl;
         for (int j = warp >> 2; j < NR / 16; j += 2) {
@@ -401,7 +417,8 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_adj(TcPlan P, con
                                                                const int* __restrict__ members, int nclass, int nvol,
                                                                const float2* __restrict__ vin, int ld_in,
                                                                size_t in_vstride, float2* __restrict__ vout,
-                                                               int ld_out, size_t out_vstride, int* timeout_flag) {
+                                                               int ld_out, size_t out_vstride, int* timeout_flag,
+                                                               long long max_polls) {
   extern __shared__ __align__(1024) unsigned char sm[];
   const uint32_t taddr = tc_setup(sm, P);
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.off_bar);
@@ -445,7 +462,7 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_adj(TcPlan P, con
       }
       umma::commit(bar);
     }
-    wait_mma(bar, phase, timeout_flag);
+    if (wait_mma(bar, phase, timeout_flag, max_polls)) break;
     if (a.last) {
       // epilogue: TMEM lane n = 8 v + 2 m + c; column z.  Even lanes hold the
       // real parts, odd lanes the imaginary parts of the same output.
@@ -489,9 +506,8 @@ ctof_status launch_tc(K kern, const TcPlan& P, const ctof_kernel_s* k, int nvol,
   if (per_sm > tmem_cap) per_sm = tmem_cap;
   if (per_sm < 1) per_sm = 1;
   const int grid = k->nclass < per_sm * nsm ? k->nclass : per_sm * nsm;
-  int* flag = reinterpret_cast<int*>(k->d_scalars + 9);
   kern<<<grid, TC_THREADS, P.total, st>>>(P, k->d_what, k->d_members, k->nclass, nvol, vin, ld_in, in_vstride, vout,
-                                          ld_out, out_vstride, flag);
+                                          ld_out, out_vstride, k->d_flags, k->max_polls);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }

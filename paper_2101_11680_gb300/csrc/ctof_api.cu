@@ -420,7 +420,20 @@ ctof_status solve_staged(ctof_kernel_s* k, const ctof_solver_params* prm, double
   return tikhonov_run(k, prm, st, lambda);
 }
 
-// Synchronising report: parameters used and a NaN/Inf scan of the result.
+}  // namespace
+
+ctof_status take_device_status(ctof_kernel_s* k, cudaStream_t st) {
+  int flag = 0;
+  CTOF_CUDA_TRY(cudaMemcpyAsync(&flag, k->d_flags, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CTOF_CUDA_TRY(cudaMemsetAsync(k->d_flags, 0, sizeof(int), st));
+  CTOF_CUDA_TRY(cudaStreamSynchronize(st));
+  return flag ? CTOF_ETIMEOUT : CTOF_OK;
+}
+
+namespace {
+
+// Synchronising report: parameters used, a NaN/Inf scan of the result, and
+// the handle's sticky device status (a bounded wait that ran out).
 ctof_status fill_report(ctof_kernel_s* k, const ctof_solver_params* prm, double lambda, ctof_report* rep,
                         cudaStream_t st) {
   int* flag = reinterpret_cast<int*>(k->d_scalars + 8);
@@ -429,14 +442,14 @@ ctof_status fill_report(ctof_kernel_s* k, const ctof_solver_params* prm, double 
   double sc[10];
   CTOF_CUDA_TRY(cudaMemcpyAsync(sc, k->d_scalars, 10 * sizeof(double), cudaMemcpyDeviceToHost, st));
   CTOF_CUDA_TRY(cudaStreamSynchronize(st));
-  int bad = 0, timeout = 0;
+  int bad = 0;
   memcpy(&bad, &sc[8], sizeof(int));
-  memcpy(&timeout, &sc[9], sizeof(int));
+  const ctof_status waits = take_device_status(k, st);
   rep->scale = k->scale;
   rep->beta = prm->solver == CTOF_SOLVER_TIKHONOV ? 0.0 : sc[0];
   rep->lambda = lambda;
   rep->iters_done = prm->solver == CTOF_SOLVER_TIKHONOV ? 1 : prm->iters;
-  if (timeout) return CTOF_ETIMEOUT;
+  if (waits != CTOF_OK) return waits;
   return bad ? CTOF_ENONFINITE : CTOF_OK;
 }
 
@@ -619,6 +632,7 @@ ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, 
   k->r_min = optics->clamp_r ? 0.5 * std::min(grid->dx_mm, std::min(grid->dy_mm, grid->dz_mm)) : 0.0;
   k->tik_lambda[0] = k->tik_lambda[1] = -1.0;
   k->tik_last = 1;
+  k->max_polls = CTOF_DEFAULT_MAX_POLLS;
   for (int i = 0; i < 4; ++i) k->tune_pb[i] = 16;
   {
     static std::atomic<unsigned long long> next_id{1};
@@ -654,6 +668,7 @@ ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, 
   const size_t o_s = cv.take<float>(nz * pp);
   const size_t o_vs = cv.take<float>((size_t)nz * n * n);
   const size_t o_sc = cv.take<double>(16);
+  const size_t o_fl = cv.take<int>(4);
   k->bytes = cv.off;
   if (cudaMalloc(&k->d_base, k->bytes) != cudaSuccess) {
     cudaGetLastError();
@@ -682,6 +697,7 @@ ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, 
   k->d_s = reinterpret_cast<float*>(b + o_s);
   k->d_vstage = reinterpret_cast<float*>(b + o_vs);
   k->d_scalars = reinterpret_cast<double*>(b + o_sc);
+  k->d_flags = reinterpret_cast<int*>(b + o_fl);
   if (flags & CTOF_KEEP_W) {
     void* p = nullptr;
     if (cudaMalloc(&p, (size_t)nt * nz * k->q * k->q * sizeof(double)) != cudaSuccess) {
@@ -698,6 +714,7 @@ ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, 
   ctof_status s = CTOF_OK;
   do {
     if (cudaMemsetAsync(k->d_scalars, 0, 16 * sizeof(double), st) != cudaSuccess ||
+        cudaMemsetAsync(k->d_flags, 0, 4 * sizeof(int), st) != cudaSuccess ||
         cudaMemcpyAsync(k->d_members, members.data(), members.size() * sizeof(int), cudaMemcpyHostToDevice, st) !=
             cudaSuccess ||
         cudaMemcpyAsync(k->d_lap, lap.data(), lap.size() * sizeof(float), cudaMemcpyHostToDevice, st) !=
@@ -861,8 +878,7 @@ ctof_status ctof_reconstruct_host(ctof_kernel k, const float* h_m, const ctof_so
   CTOF_TRY(solve_staged(k, params, &lambda, st));
   CTOF_CUDA_TRY(cudaMemcpyAsync(h_mu, k->d_vstage, vbytes, cudaMemcpyDeviceToHost, st));
   if (report) return fill_report(k, params, lambda, report, st);
-  CTOF_CUDA_TRY(cudaStreamSynchronize(st));
-  return CTOF_OK;
+  return take_device_status(k, st);
 }
 
 ctof_status ctof_reconstruct_batch_tikhonov(ctof_kernel k, int batch, const float* d_m, int precision,
@@ -947,6 +963,19 @@ ctof_status ctof_reconstruct_batch(int count, const ctof_kernel* ks, const float
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   for (int i = 0; i < count; ++i) CTOF_TRY(autotune(ks[i], st));
   return batch_graph_run(count, ks, d_m, params, d_mu, st);
+}
+
+ctof_status ctof_set_wait_limit(ctof_kernel k, long long polls) {
+  if (!k || polls < 0) return CTOF_EINVAL;
+  k->max_polls = polls;
+  return CTOF_OK;
+}
+
+ctof_status ctof_sync_status(ctof_kernel k, void* stream) {
+  if (!k) return CTOF_EINVAL;
+  DeviceGuard g(k->device);
+  if (!g.ok) return CTOF_ECUDA;
+  return take_device_status(k, static_cast<cudaStream_t>(stream));
 }
 
 ctof_status ctof_set_timing(ctof_kernel k, int enable) {

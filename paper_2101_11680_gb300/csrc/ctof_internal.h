@@ -61,6 +61,8 @@ struct ctof_kernel_s {
   float* d_s;          // [nz][p][p]
   float* d_vstage;     // [nz][n][n]
   double* d_scalars;   // [16] device scalars (beta, max reductions, flags)
+  int* d_flags;        // [4] sticky device status, cleared when read: [0] a bounded wait ran out
+  long long max_polls; // polls before a device-side wait gives up (ctof_set_wait_limit)
 
   // Tikhonov cache: FP64 Cholesky factors of G + lambda I
   // Tikhonov inverses (G + lambda I)^-1 (FP64 Cholesky, stored FP32 [nclass][nz][z4])
@@ -112,6 +114,13 @@ struct DeviceGuard {
     if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
   }
 };
+
+// Default number of mbarrier polls before a device-side wait gives up.
+constexpr long long CTOF_DEFAULT_MAX_POLLS = 1ll << 24;
+
+// Synchronises `st`, then reads and clears the handle's sticky device status:
+// CTOF_ETIMEOUT if a bounded device-side wait ran out since the last read.
+ctof_status take_device_status(ctof_kernel_s* k, cudaStream_t st);
 
 // ---- fft.cu -------------------------------------------------------------
 // Complex elements of a row-pass intermediate for `rows` rows of `nplanes` planes.

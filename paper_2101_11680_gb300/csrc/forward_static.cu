@@ -3,13 +3,12 @@
 // library.
 //
 // Who needs this: callers that may not allocate device memory at the point of
-// the call -- code running inside a CUDA stream capture (cudaMalloc/cudaFree
-// are not permitted while a stream is being captured and they synchronise the
-// device), real-time acquisition loops that must never block on an allocator,
-// and host frameworks or plugins that own every device allocation themselves
-// and hand the library only input and output buffers.  This entry point
-// performs no cudaMalloc, cudaFree or other allocating call; the caller passes
-// the handle (built beforehand), the input volume and the output buffer.
+// the call -- real-time acquisition loops that must never wait on an
+// allocator (cudaMalloc/cudaFree can synchronise the device), and host
+// frameworks or plugins that own every device allocation themselves and hand
+// the library only input and output buffers.  This entry point performs no
+// cudaMalloc, cudaFree or other allocating call; the caller passes the handle
+// (built beforehand), the input volume and the output buffer.
 //
 // The scratch array (CTOF_STATIC_SCRATCH_BYTES, 32 MiB) is part of the loaded
 // library image: every GPU that loads the library holds it until the process
@@ -35,7 +34,11 @@ std::mutex g_setup_mutex;
 void* g_scratch_ptr[CTOF_MAX_DEVICES] = {};
 
 // Device address of the scratch array on `dev`, resolved once per device with
-// that device current (the host-side symbol is only a stand-in).
+// that device current (the host-side symbol is only a stand-in) and kept for
+// the life of the process: the first call on a device does this set-up, so it
+// must come before any stream capture.  A cudaDeviceReset destroys the
+// context the address belongs to; the kept address is then stale, and the
+// entry point must not be called again in that process.
 ctof_status scratch_address(int dev, void** out) {
   if (dev < 0 || dev >= CTOF_MAX_DEVICES) return CTOF_EUNSUPPORTED;
   std::lock_guard<std::mutex> lock(g_setup_mutex);

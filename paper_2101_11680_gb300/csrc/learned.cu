@@ -944,10 +944,10 @@ ctof_status ctof_learned_loss_grad(ctof_learned L, ctof_kernel k, int batch, con
   double loss = 0.0;
   CTOF_CUDA_TRY(cudaMemcpyAsync(&loss, L->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
   if (h_grad) CTOF_CUDA_TRY(cudaMemcpyAsync(h_grad, L->d_grad, (size_t)L->nparam * 4, cudaMemcpyDeviceToHost, st));
-  CTOF_CUDA_TRY(cudaStreamSynchronize(st));
+  const ctof_status waits = take_device_status(k, st);  // synchronises
   const long long V = (long long)batch * k->nz * k->n * k->n;
   if (h_loss) *h_loss = loss / (double)V;
-  return CTOF_OK;
+  return waits;
 }
 
 ctof_status ctof_learned_train_step(ctof_learned L, ctof_kernel k, int batch, const float* d_m, const float* d_mu,
@@ -972,8 +972,9 @@ ctof_status ctof_learned_train_step(ctof_learned L, ctof_kernel k, int batch, co
   if (h_loss) {
     double loss = 0.0;
     CTOF_CUDA_TRY(cudaMemcpyAsync(&loss, L->d_loss, sizeof(double), cudaMemcpyDeviceToHost, st));
-    CTOF_CUDA_TRY(cudaStreamSynchronize(st));
+    const ctof_status waits = take_device_status(k, st);  // synchronises
     *h_loss = loss / (double)((long long)batch * k->nz * k->n * k->n);
+    return waits;
   }
   return CTOF_OK;
 }

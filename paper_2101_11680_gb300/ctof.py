@@ -112,6 +112,8 @@ _SIGNATURES = {
     "ctof_learned_reconstruct": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P]),
     "ctof_kernel_get_tuning": (ctypes.c_int, [_P, _P]),
     "ctof_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
+    "ctof_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
+    "ctof_sync_status": (ctypes.c_int, [_P, _P]),
     "ctof_get_timing": (ctypes.c_int, [_P, ctypes.POINTER(Timing)]),
     "ctof_status_string": (ctypes.c_char_p, [ctypes.c_int]),
     "ctof_last_error_message": (ctypes.c_char_p, []),
@@ -318,6 +320,15 @@ class Kernel:
             self.close()
         except Exception:
             pass
+
+    # ---- bounded device waits ----
+    def set_wait_limit(self, polls):
+        """Polls before a device-side wait of this handle's kernels gives up (0: at once)."""
+        _check(self._lib.ctof_set_wait_limit(self._h, int(polls)), "ctof_set_wait_limit")
+
+    def sync_status(self, stream=None):
+        """Synchronise and read (and clear) the handle's sticky device status; raises on a timeout."""
+        _check(self._lib.ctof_sync_status(self._h, _stream_handle(stream)), "ctof_sync_status")
 
     # ---- profiling ----
     def set_timing(self, enable):

@@ -84,3 +84,36 @@ def test_batched_equals_single_volume_calls():
         one = k.contract_forward_batch(xz[v:v + 1].contiguous())
         d = (batch[v, :, :nt] - one[0, :, :nt]).norm() / one[0, :, :nt].norm()
         assert float(d) <= 2e-6
+
+
+def test_bounded_wait_gives_up_and_reports_timeout():
+    """A completion wait that runs out stops the tensor-core kernel and is reported.
+
+    With the poll limit at 0 every MMA-completion wait of the tcgen05 kernels
+    gives up at once: the kernel sets the handle's sticky flag, waits (with the
+    fixed drain limit) for the MMAs in flight, frees its TMEM and returns.  The
+    next synchronising call reports CTOF_ETIMEOUT and clears the flag; with the
+    default limit the same calls are correct again.
+    """
+    wf, k, g = case("cfg1")
+    nf, nt, nz = wf.shape
+    rng = np.random.default_rng(9)
+    xz = torch.tensor(_spectra(rng, 4, nf, k.ldz, nz), device="cuda")
+    xt = torch.tensor(_spectra(rng, 4, nf, k.ldt, nt), device="cuda")
+    k.sync_status()  # nothing pending
+    k.set_wait_limit(0)
+    try:
+        for call in (k.contract_forward_batch, k.contract_adjoint_batch):
+            call(xz if call == k.contract_forward_batch else xt)
+            with pytest.raises(ctof.CtofError) as e:
+                k.sync_status()
+            assert e.value.status == ctof.ETIMEOUT
+            k.sync_status()  # the flag was cleared by the read
+    finally:
+        k.set_wait_limit(1 << 24)
+    got = k.contract_forward_batch(xz).cpu().numpy()
+    k.sync_status()
+    xc = xz.cpu().numpy()[..., :nz, 0].astype(np.float64) + 1j * xz.cpu().numpy()[..., :nz, 1]
+    want = np.einsum("ftz,vfz->vft", wf, xc)
+    gc = got[..., :nt, 0] + 1j * got[..., :nt, 1]
+    assert np.linalg.norm(gc - want) <= 1e-5 * np.linalg.norm(want)

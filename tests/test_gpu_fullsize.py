@@ -8,6 +8,8 @@ that hold at any size for the rest.
   device must match.
 * forward: a sparse volume (40 absorbers) makes each measurement sample a
   40-term sum of closed-form kernel values the oracle computes directly.
+* adjoint: a sparse measurement (40 nonzero samples) makes each output voxel
+  a 40-term sum of closed-form kernel values, likewise.
 * adjoint identity at full size; ADMM (the bench launch configuration,
   100 iterations) is finite, non-negative, reproducible and reduces the data
   residual.
@@ -90,6 +92,32 @@ def test_forward_sampled_full_size(kern):
             sel = vz == zz
             want += float(np.sum(_bin_value(med, rho[sel], ZF + zz * DZ, int(k)) * val[sel]))
         assert abs(m[k, y, x] - want) <= 2e-6 * scale + 1e-5 * abs(want)
+
+
+def test_adjoint_sampled_full_size(kern):
+    """A^T m at 150 sampled voxels: vol[z][y][x] = sum_k sum_(y',x') W(x'-x, y'-y, z_j, k) m[k][y'][x']
+    (the transpose of Eq. 11), a 40-term sum for a measurement with 40 nonzero samples."""
+    rng = np.random.default_rng(12)
+    nmeas = 40
+    mk = rng.integers(0, NT, nmeas)
+    my = rng.integers(0, N, nmeas)
+    mx = rng.integers(0, N, nmeas)
+    val = rng.uniform(0.5, 2.0, nmeas)
+    m = np.zeros((NT, N, N))
+    m[mk, my, mx] = val
+    vol = kern.adjoint(torch.tensor(m, dtype=torch.float32, device="cuda")).cpu().numpy()
+    med = _medium()
+    sz = rng.integers(0, NZ, 150)
+    sy = rng.integers(0, N, 150)
+    sx = rng.integers(0, N, 150)
+    scale = np.abs(vol).max()
+    for z, y, x in zip(sz, sy, sx):
+        rho = np.sqrt(((mx - x) * DX) ** 2 + ((my - y) * DX) ** 2)
+        want = 0.0
+        for kk in np.unique(mk):
+            sel = mk == kk
+            want += float(np.sum(_bin_value(med, rho[sel], ZF + z * DZ, int(kk)) * val[sel]))
+        assert abs(vol[z, y, x] - want) <= 2e-6 * scale + 1e-5 * abs(want)
 
 
 def test_adjoint_identity_full_size(kern):

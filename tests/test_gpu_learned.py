@@ -12,12 +12,17 @@ at most 2^-9 each).  Two comparisons:
   FP64 accumulation, and the odd element whose FP32 sum falls on the other
   side of a BF16 rounding boundary);
 * against the exact FP64 oracle, which measures the roundings themselves: the
-  loss to 1e-3 and the whole gradient to 3e-2.  No per-tensor bound is
-  written for this one: a layer's bias or weight gradient can be a sum over
-  all voxels whose terms cancel to a small fraction of their absolute sum,
-  and pre-activations within a rounding error of zero switch their ReLU, so a
-  single small tensor can be off by 10-20 % in BF16 while the device matches
-  the BF16 computation itself to 1e-4.
+  loss to 1e-3, the whole gradient to 3e-2 and each parameter tensor to
+  1.5e-2 where BF16 storage allows it.  The rounding oracle run on the CPU
+  (same problems, same weights) fixes what BF16 storage alone does to each
+  tensor against the exact oracle: on one problem every tensor is within
+  1.14e-2 (b2 the largest); on the two-problem batch the layer-3/4 and step
+  size tensors stay within 1.13e-2, while the layer-1/2 tensors are 1-21 %
+  off: their gradient is a sum over all voxels (and over the two problems)
+  whose terms cancel to a small fraction of their absolute sum, and
+  pre-activations within a rounding error of zero switch their ReLU.  Those
+  four tensors are held there by the whole-gradient bound and, per tensor,
+  by the rounding oracle.
 """
 
 import numpy as np
@@ -35,6 +40,9 @@ pytestmark = pytest.mark.gpu
 
 CASE = "admm16"  # 16 x 16 scan, 6 depths, 32 bins
 STAGES = 3
+TENSORS = ["w1", "b1", "w2", "b2", "w3", "b3", "w4", "b4", "eta"]
+# tensors held per tensor against the exact FP64 oracle, by batch size (see the module docstring)
+EXACT_PER_TENSOR = {1: set(TENSORS), 2: {"w3", "b3", "w4", "b4", "eta"}}
 
 
 def _problem(seed):
@@ -100,12 +108,15 @@ def test_learned_loss_and_gradient_match_oracle():
                 want_g += gr / batch
             if rnd is not None:
                 assert got_l == pytest.approx(want_l, rel=2e-4)
-                for name, gt, wt in zip(["w1", "b1", "w2", "b2", "w3", "b3", "w4", "b4", "eta"], _tensors(got_g),
-                                        _tensors(want_g)):
+                for name, gt, wt in zip(TENSORS, _tensors(got_g), _tensors(want_g)):
                     assert rel_l2(gt, wt) <= 2e-3, (batch, name, rel_l2(gt, wt))
             else:
                 assert got_l == pytest.approx(want_l, rel=1e-3)
                 assert rel_l2(got_g, want_g) <= 3e-2
+                exact_ok = EXACT_PER_TENSOR[batch]
+                for name, gt, wt in zip(TENSORS, _tensors(got_g), _tensors(want_g)):
+                    if name in exact_ok:
+                        assert rel_l2(gt, wt) <= 1.5e-2, (batch, name, rel_l2(gt, wt))
     net.close()
 
 

@@ -222,3 +222,30 @@ def test_multiplexed_needs_blocks_of_8():
     with pytest.raises(ctof.CtofError) as e:
         k.forward_multiplexed(torch.zeros((5, 20, 20), device="cuda"))
     assert e.value.status == ctof.EUNSUPPORTED
+
+
+def test_admm_class_shape_48_depths_256_bins():
+    """ADMM at the per-class shape of the 128 x 128 x 48 x 256 workload.
+
+    The x-update contraction works per frequency class on a 256-bin x 48-depth
+    block, the same block as at the full workload; only the lateral field is
+    smaller (32 x 32 scan, P = 64), so the FP64 oracle run (minutes) is stored
+    in tests/golden by make_oracle_fixtures.py with the exact noisy counts it
+    was given.  100 iterations, rel-L2 <= 1e-5 on crop(v3), beta to 1e-5.
+    """
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "admm_n32_z48_t256.npz")
+    fx = np.load(path)
+    n, nz, nt = (int(v) for v in fx["grid"])
+    dx, dz, zf, dt = (float(v) for v in fx["pitch"])
+    m = fx["counts"].astype(np.float64) * float(fx["unit"])
+    k = ctof.Kernel(ctof.make_optics(), ctof.make_grid(n, nz, nt, dx, dz, zf, dt))
+    try:
+        assert k.info.scale == pytest.approx(float(fx["scale"]), rel=1e-10)
+        iters = int(fx["iters"])
+        got, rep = k.reconstruct(torch.tensor(m, dtype=torch.float32, device="cuda"), ctof.admm_params(iters=iters),
+                                 report=True)
+        assert rep.beta == pytest.approx(float(fx["beta"]), rel=1e-5)
+        assert rel_l2(got.cpu().numpy(), fx["want"]) <= 1e-5
+    finally:
+        k.close()
