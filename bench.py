@@ -750,6 +750,7 @@ def main():
         except Exception:
             traffic = None
 
+    admm_kernel = "k_contract_admm_pipe" if info.admm_stages else "k_contract_admm"
     launches_per_step = timing.graph_kernel_nodes
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
@@ -760,7 +761,7 @@ def main():
                    "l2": "inputs larger than L2 (W_hat %.0f MB streamed per iteration)"
                          % (info.n_class * cfg["nt"] * cfg["nz"] * 4 / 1e6),
                    "kernel": kernel_desc, "kernel_build_s": round(build_s, 3)},
-        "roofline": {"bound": "hbm", "kernel": "k_contract_admm", "achieved": achieved, "peak": peak,
+        "roofline": {"bound": "hbm", "kernel": admm_kernel, "achieved": achieved, "peak": peak,
                      "unit": "GB/s", "frac": achieved / peak, "traffic": traffic,
                      "algorithmic_bytes_per_launch": alg_bytes, "avg_launch_ms": avg_contract_ms,
                      "peak_source": peak_src},

@@ -98,6 +98,8 @@ typedef struct {
   double scale;     /* max_f sigma_max(W_hat(f)) (the ADMM normalisation) */
   double gram_max_diag; /* max over f, j of (W_hat^T W_hat)_jj */
   size_t device_bytes;  /* device memory held by the handle */
+  int admm_stages;      /* shared-memory stages of the pipelined ADMM x-update
+                           kernel at this size (0: the fallback kernel runs) */
 } ctof_kernel_info;
 
 /* Solver choice and parameters.  ADMM_TV solves

@@ -712,6 +712,7 @@ ctof_status build_kernel_tables(ctof_kernel_s* k, cudaStream_t st) {
   k_factor<<<nclass, 128, fsm, st>>>(k->d_gram, k->d_lap, nz, 1.0 / (k->scale * k->scale), 0.0, 0, k->d_hinv,
                                      nullptr);
   CTOF_CUDA_TRY(cudaGetLastError());
+  CTOF_TRY(contract_admm_prepare(k, st));
   CTOF_CUDA_TRY(cudaStreamSynchronize(st));
   return CTOF_OK;
 }

@@ -6,22 +6,45 @@
 // with L = (|dx|^2 + |dy|^2 + 1) I + Dz^T Dz and H = W_hat^T W_hat / s^2 + L,
 // i.e. x_hat = H^-1 (W_hat^T (K x_hat_prev + c_hat)/s + s_hat).  The 8 real
 // right-hand sides are the real/imaginary parts of the up-to-4 frequencies
-// of one class (they share the real matrix W_hat).
-//
-// The kernel streams W_hat once per iteration.  Persistent CTAs of 8 warps walk
-// the classes, two per SM where their shared memory fits (one buffer each: the
-// phases of one class run between block-wide barriers, and the other CTA's
-// class fills the SM meanwhile); otherwise one CTA per SM prefetches class
-// i+1 (W_hat block, H^-1 block and the member vectors) with 16-byte cp.async
-// copies into the second of two shared-memory buffers.
-// (Per-row TMA bulk copies were measured slower here: 300+ requests of 192
-// bytes per class are limited by the TMA request rate, not by bandwidth.)
-// The two T x Z contractions run on the warp-level tensor-core MMA
+// of one class (they share the real matrix W_hat).  W_hat is streamed once
+// per iteration; every contraction runs on the warp-level tensor-core MMA
 // (m16n8k8, TF32 inputs, FP32 accumulation) with each operand split into a
 // TF32 high part and a TF32 remainder (three MMAs per tile: lo*hi + hi*lo +
 // hi*hi), which keeps FP32-level accuracy; N = 8 is exactly the 8 real
-// right-hand sides of a class.  Shared W_hat rows are padded to a stride zp
-// with zp/4 odd so that the MMA fragment loads hit distinct banks.
+// right-hand sides of a class.
+//
+// Two kernels:
+//
+// k_contract_admm_pipe (used whenever two or more stages fit in shared
+// memory; 128 x 128 x 48 x 256 takes three): one CTA per SM, a producer warp
+// and eight consumer warps.  The producer streams each class into a ring of
+// shared-memory stages with bulk asynchronous copies (cp.async.bulk, one per
+// contiguous block: the class's W_hat and H^-1 blocks and each member's
+// c_hat, s_hat and x_hat rows, 14 requests of up to 48 KB for a class of four
+// members), completing on the stage's mbarrier; consumers release a stage
+// through a second mbarrier once its class is done.  W_hat and H^-1 are read
+// from ADMM copies laid out in 8 x 8 blocks whose 64 words are permuted so
+// that both the forward fragments (row <-> lane group, column <-> lane in
+// group) and the adjoint's transposed fragments load without shared-memory
+// bank conflicts from the flat bulk copy:
+//   word(i, j) = 32 (j / 4) + 4 ((i + 4 (j / 4)) mod 8) + j mod 4,
+//   i = row mod 8, j = column mod 8.
+// Per class the consumers run four phases between named barriers:
+//   A  adjoint partial sums, the eight warps splitting the t (K) steps;
+//   B  b = sum of the partials / s + s_hat - L x_prev, split for the MMA;
+//   C  x_new = x_prev + H^-1 b (one warp per 16-row z tile), stored;
+//   D  Kx = W x_new / s (warps over 16-row t tiles), stored.
+// Every wait is bounded: a wait that runs out sets the handle's sticky flag
+// and the CTA stops (the consumers vote at their next barrier, the producer
+// stops issuing and waits, with a fixed drain limit, for the copies it has
+// in flight).
+//
+// k_contract_admm (fallback for class blocks too large for two stages):
+// persistent CTAs of 8 warps walk the classes, two per SM where their shared
+// memory fits (one buffer each), otherwise one CTA per SM prefetching class
+// i+1 with 16-byte cp.async copies into a second buffer; shared W_hat rows
+// are padded to a stride zp with zp/4 odd so that the MMA fragment loads hit
+// distinct banks.
 //   adjoint part: warps split the t (K) steps over all z tiles; partial
 //                 results meet in shared memory.
 //   H^-1 part:    FP32 FMA, thread per (z, member).
@@ -315,12 +338,417 @@ AdmmLayout make_layout(int nt, int nz, int nbuf) {
   return L;
 }
 
+
+// ======================= pipelined kernel (bulk-copy stage ring) =======================
+
+constexpr int PIPE_CONS_WARPS = 8;
+constexpr int PIPE_CONS_THREADS = 32 * PIPE_CONS_WARPS;
+constexpr int PIPE_THREADS = PIPE_CONS_THREADS + 32;  // + one producer warp
+constexpr long long PIPE_DRAIN_POLLS = 1ll << 24;     // polls of the waits that follow a timeout
+constexpr int PIPE_SMEM_LIMIT = 227 * 1024;
+
+inline int rup(int x, int m) { return (x + m - 1) / m * m; }
+
+struct PipePlan {
+  int nt, nz, z4, zm, tm, ntp;
+  int cs, sz;                     // words per member row: c stage (2 tm + 8), s / x stages (2 z4 + 8)
+  int stages;
+  int o_w, o_h, o_c, o_s, o_x;    // byte offsets within a stage
+  int stage_bytes;
+  int o_part, o_bh, o_bl, o_xh, o_xl, o_bar;  // byte offsets after the stages
+  int total;
+  unsigned w_bytes, h_bytes, c_bytes, v_bytes;  // bulk copy sizes
+};
+
+PipePlan make_pipe_plan(int nt, int nz, int stages) {
+  PipePlan P{};
+  P.nt = nt;
+  P.nz = nz;
+  P.z4 = rup(nz, 4);
+  P.zm = rup(nz, 16);
+  P.tm = rup(nt, 16);
+  P.ntp = rup(nt, 2);
+  P.cs = 2 * P.tm + 8;  // = 8 mod 32 words: the adjoint's B fragments are conflict-free
+  P.sz = 2 * P.z4 + 8;  // member rows 8 banks apart
+  P.stages = stages;
+  P.o_w = 0;
+  P.o_h = P.o_w + P.tm * P.zm * 4;
+  P.o_c = P.o_h + P.zm * P.zm * 4;
+  P.o_s = P.o_c + 4 * P.cs * 4;
+  P.o_x = P.o_s + 4 * P.sz * 4;
+  P.stage_bytes = rup(P.o_x + 4 * P.sz * 4, 128);
+  P.o_part = stages * P.stage_bytes;
+  P.o_bh = P.o_part + PIPE_CONS_WARPS * P.zm * 8 * 4;
+  P.o_bl = P.o_bh + P.zm * 8 * 4;
+  P.o_xh = P.o_bl + P.zm * 8 * 4;
+  P.o_xl = P.o_xh + P.zm * 8 * 4;
+  P.o_bar = P.o_xl + P.zm * 8 * 4;
+  P.total = P.o_bar + 2 * stages * 8 + 16;  // full[S], empty[S], abort word
+  P.w_bytes = (unsigned)(P.tm * P.zm * 4);
+  P.h_bytes = (unsigned)(P.zm * P.zm * 4);
+  P.c_bytes = (unsigned)(P.ntp * 8);
+  P.v_bytes = (unsigned)(P.z4 * 8);
+  return P;
+}
+
+// Most stages (up to 4) that fit, or 0 when fewer than two do.
+int pipe_stages(int nt, int nz) {
+  if (nz > 64) return 0;
+  for (int s = 4; s >= 2; --s)
+    if (make_pipe_plan(nt, nz, s).total <= PIPE_SMEM_LIMIT) return s;
+  return 0;
+}
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint64_t* bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+      "selp.u32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(done)
+      : "r"(smem_addr(bar)), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// Bounded wait for the phase of the given parity (false: gave up).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, long long max_polls) {
+  for (long long i = 0; i < max_polls; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_addr(bar)) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_addr(bar)), "r"(bytes)
+               : "memory");
+}
+
+// Bulk global -> shared copy completing `bytes` of transaction count on `bar`
+// (16-byte aligned addresses, size a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+          smem_addr(dst)),
+      "l"(src), "r"(bytes), "r"(smem_addr(bar))
+      : "memory");
+}
+
+// Barrier 1 over the 256 consumer threads (the producer warp never joins it).
+__device__ __forceinline__ void cons_sync() { asm volatile("bar.sync 1, 256;\n" ::: "memory"); }
+__device__ __forceinline__ int cons_sync_or(int v) {
+  int out;
+  asm volatile(
+      "{\n"
+      ".reg .pred q, p;\n"
+      "setp.ne.s32 q, %1, 0;\n"
+      "bar.red.or.pred p, 1, 256, q;\n"
+      "selp.s32 %0, 1, 0, p;\n"
+      "}\n"
+      : "=r"(out)
+      : "r"(v)
+      : "memory");
+  return out;
+}
+
+// d += A B with separate accumulators for the large (hi*hi) and the small
+// (lo*hi + hi*lo) terms: two short dependency chains instead of one long one.
+__device__ __forceinline__ void mma_3xtf32_2acc(float (&dh)[4], float (&dl)[4], const float (&a)[4], unsigned bh0,
+                                                unsigned bh1, unsigned bl0, unsigned bl1) {
+  unsigned ah[4], al[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split_tf32(a[i], ah[i], al[i]);
+  mma_tf32(dl, al, bh0, bh1);
+  mma_tf32(dl, ah, bl0, bl1);
+  mma_tf32(dh, ah, bh0, bh1);
+}
+
+// W_hat -> [class][tm/8][zm/8][64] and H^-1 -> [class][zm/8][zm/8][64] in the
+// permuted 8 x 8 block layout described at the top of this file (zero padding).
+__global__ void k_admm_reorder(const float* __restrict__ src, int rows, int cols, int ld, int rm, int cm,
+                               float* __restrict__ dst, int nclass) {
+  const size_t per = (size_t)rm * cm, total = per * nclass;
+  const int cb_n = cm >> 3;
+  for (size_t d = (size_t)blockIdx.x * blockDim.x + threadIdx.x; d < total; d += (size_t)gridDim.x * blockDim.x) {
+    const size_t c = d / per;
+    const int rem = (int)(d - c * per), blk = rem >> 6, w = rem & 63;
+    const int rb = blk / cb_n, cb = blk - rb * cb_n;
+    const int half = w >> 5, q = w & 31;
+    const int i = ((q >> 2) - 4 * half) & 7, j = 4 * half + (q & 3);
+    const int r = 8 * rb + i, col = 8 * cb + j;
+    dst[d] = (r < rows && col < cols) ? src[c * (size_t)rows * ld + (size_t)r * ld + col] : 0.f;
+  }
+}
+
+template <int MZ>
+__global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
+    PipePlan P, const float* __restrict__ what_o, const float* __restrict__ hinv_o, const float* __restrict__ lap,
+    const int* __restrict__ members, int nclass, const float2* c_hat, int ldt, const float2* s_hat, float2* x_hat,
+    int ldz, float2* __restrict__ kx_hat, float inv_s, int* status_flag, long long max_polls) {
+  extern __shared__ __align__(128) float4 sm_pipe[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(sm_pipe);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int S = P.stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + P.o_bar);
+  uint64_t* empty = full + S;
+  volatile int* s_abort = reinterpret_cast<volatile int*>(empty + S);
+  // zero everything below the barriers: padding rows/columns of the operand
+  // blocks and absent members' rows then read as finite zeros
+  for (int i = tid; i < P.o_bar / 16; i += PIPE_THREADS)
+    reinterpret_cast<float4*>(sm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (tid == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, PIPE_CONS_WARPS);
+    }
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // zeroes before the bulk copies
+  __syncthreads();
+  const int mine = (int)blockIdx.x < nclass ? (nclass - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  if (warp == PIPE_CONS_WARPS) {
+    // ---------------- producer ----------------
+    if (lane != 0) return;
+    int issued = 0;
+    for (; issued < mine; ++issued) {
+      const int s = issued % S;
+      const uint32_t par = ((issued / S) & 1) ^ 1;  // a fresh barrier counts its parity-1 phase as done
+      bool ok = false;
+      for (long long i = 0; i < max_polls; ++i) {
+        if (mbar_try(empty + s, par)) {
+          ok = true;
+          break;
+        }
+        if (*s_abort) break;
+      }
+      if (!ok) {
+        if (!*s_abort) {
+          atomicExch(status_flag, 1);
+          *s_abort = 1;
+        }
+        break;
+      }
+      const int c = (int)blockIdx.x + issued * (int)gridDim.x;
+      unsigned char* st = sm + s * P.stage_bytes;
+      int f[4];
+      unsigned bytes = P.w_bytes + P.h_bytes;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        f[m] = __ldg(members + 4 * c + m);
+        if (f[m] >= 0) bytes += P.c_bytes + 2 * P.v_bytes;
+      }
+      mbar_expect_tx(full + s, bytes);
+      bulk_g2s(st + P.o_w, what_o + (size_t)c * P.tm * P.zm, P.w_bytes, full + s);
+      bulk_g2s(st + P.o_h, hinv_o + (size_t)c * P.zm * P.zm, P.h_bytes, full + s);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        if (f[m] < 0) continue;
+        bulk_g2s(st + P.o_c + m * P.cs * 4, c_hat + (size_t)f[m] * ldt, P.c_bytes, full + s);
+        bulk_g2s(st + P.o_s + m * P.sz * 4, s_hat + (size_t)f[m] * ldz, P.v_bytes, full + s);
+        bulk_g2s(st + P.o_x + m * P.sz * 4, x_hat + (size_t)f[m] * ldz, P.v_bytes, full + s);
+      }
+    }
+    // no copy may be in flight when the CTA exits: wait for each stage's last fill
+    for (int s = 0; s < S; ++s) {
+      if (issued > s) {
+        const int last = s + ((issued - 1 - s) / S) * S;
+        mbar_wait_bounded(full + s, (uint32_t)((last / S) & 1), PIPE_DRAIN_POLLS);
+      }
+    }
+    return;
+  }
+
+  // ---------------- consumers ----------------
+  const int g = lane >> 2, tg = lane & 3;
+  const int hg = g >> 2;
+  // word offsets of this lane's fragment elements inside an 8 x 8 block
+  const int offF0 = 4 * g + tg;                                // (row g, column tg)
+  const int offF2 = 32 + 4 * ((g + 4) & 7) + tg;               // (row g, column tg + 4)
+  const int offA0 = 32 * hg + 4 * ((tg + 4 * hg) & 7) + (g & 3);      // (row tg, column g)
+  const int offA2 = 32 * hg + 4 * ((tg + 4 + 4 * hg) & 7) + (g & 3);  // (row tg + 4, column g)
+  const int nt = P.nt, nz = P.nz, zm = P.zm, zb = zm >> 3;
+  const int kt = (nt + 7) >> 3, kz = (nz + 7) >> 3, mtt = P.tm >> 4;
+  float* part = reinterpret_cast<float*>(sm + P.o_part);  // [warp][zm][8]
+  unsigned* s_bh = reinterpret_cast<unsigned*>(sm + P.o_bh);  // [zm][8] b, TF32 hi / lo
+  unsigned* s_bl = reinterpret_cast<unsigned*>(sm + P.o_bl);
+  unsigned* s_xh = reinterpret_cast<unsigned*>(sm + P.o_xh);  // [zm][8] x_new, TF32 hi / lo
+  unsigned* s_xl = reinterpret_cast<unsigned*>(sm + P.o_xl);
+  for (int k = 0; k < mine; ++k) {
+    const int c = (int)blockIdx.x + k * (int)gridDim.x, s = k % S;
+    int gave_up = 0;
+    if (!mbar_wait_bounded(full + s, (uint32_t)((k / S) & 1), max_polls)) {
+      gave_up = 1;
+      atomicExch(status_flag, 1);
+    }
+    const unsigned char* st = sm + s * P.stage_bytes;
+    const float* W = reinterpret_cast<const float*>(st + P.o_w);
+    const float* H = reinterpret_cast<const float*>(st + P.o_h);
+    const float* C = reinterpret_cast<const float*>(st + P.o_c);
+    const float* SV = reinterpret_cast<const float*>(st + P.o_s);
+    const float* XV = reinterpret_cast<const float*>(st + P.o_x);
+
+    // ---- A: adjoint partial sums y_w[z][r] = sum over this warp's t of W[t][z] c[t][r] ----
+    {
+      float acc[MZ][4];
+#pragma unroll
+      for (int mt = 0; mt < MZ; ++mt)
+#pragma unroll
+        for (int i = 0; i < 4; ++i) acc[mt][i] = 0.f;
+      const float* cb = C + (g >> 1) * P.cs + 2 * tg + (g & 1);
+      for (int ks = warp; ks < kt; ks += PIPE_CONS_WARPS) {
+        const float* cr = cb + 16 * ks;  // t = 8 ks + tg (b0) and 8 ks + 4 + tg (b1)
+        unsigned bh0, bl0, bh1, bl1;
+        split_tf32(cr[0], bh0, bl0);
+        split_tf32(cr[8], bh1, bl1);
+        const float* wb = W + ks * zb * 64;  // block (t / 8 = ks, z / 8 = 0)
+#pragma unroll
+        for (int mt = 0; mt < MZ; ++mt) {
+          const float* w0 = wb + 2 * mt * 64;
+          const float a[4] = {w0[offA0], w0[64 + offA0], w0[offA2], w0[64 + offA2]};
+          mma_3xtf32(acc[mt], a, bh0, bh1, bl0, bl1);
+        }
+      }
+#pragma unroll
+      for (int mt = 0; mt < MZ; ++mt) {
+        float* p = part + (warp * zm + 16 * mt + g) * 8 + 2 * tg;
+        *reinterpret_cast<float2*>(p) = make_float2(acc[mt][0], acc[mt][1]);
+        *reinterpret_cast<float2*>(p + 64) = make_float2(acc[mt][2], acc[mt][3]);
+      }
+    }
+    if (cons_sync_or(gave_up)) {
+      if (tid == 0) *s_abort = 1;
+      break;
+    }
+    // ---- B: b = y / s + s_hat - L x_prev, split for the H^-1 MMA ----
+    {
+      const float dl = __ldg(lap + c) + 1.0f;
+      for (int i = tid; i < nz * 8; i += PIPE_CONS_THREADS) {
+        const int z = i >> 3, r = i & 7, m = r >> 1, cp = r & 1;
+        float y = 0.f;
+#pragma unroll
+        for (int w = 0; w < PIPE_CONS_WARPS; ++w) y += part[(w * zm + z) * 8 + r];
+        const float* xm = XV + m * P.sz + cp;
+        const float xz = xm[2 * z];
+        float lx = dl * xz;
+        if (z > 0) lx += xz - xm[2 * (z - 1)];
+        if (z < nz - 1) lx -= xm[2 * (z + 1)] - xz;
+        unsigned h, l;
+        split_tf32(y * inv_s + SV[m * P.sz + 2 * z + cp] - lx, h, l);
+        s_bh[i] = h;
+        s_bl[i] = l;
+      }
+    }
+    cons_sync();
+    const int mem_tg = __ldg(members + 4 * c + tg);  // this lane's output member (D columns 2 tg, 2 tg + 1)
+    // ---- C: x_new = x_prev + H^-1 b; one warp per 16-row z tile ----
+    if (warp < MZ) {
+      float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+      const float* h0 = H + 2 * warp * zb * 64;  // block (z / 8 = 2 warp, w / 8 = 0)
+      for (int ks = 0; ks < zb; ++ks) {
+        const float* hb = h0 + ks * 64;
+        const float a[4] = {hb[offF0], hb[zb * 64 + offF0], hb[offF2], hb[zb * 64 + offF2]};
+        const int b0 = (8 * ks + tg) * 8 + g, b1 = b0 + 32;
+        mma_3xtf32_2acc(ah, al, a, s_bh[b0], s_bh[b1], s_bl[b0], s_bl[b1]);
+      }
+#pragma unroll
+      for (int hf = 0; hf < 2; ++hf) {
+        const int z = 16 * warp + g + 8 * hf;
+        const float2 xp = z < nz ? *reinterpret_cast<const float2*>(XV + tg * P.sz + 2 * z) : make_float2(0.f, 0.f);
+        const float2 xn = make_float2(xp.x + (ah[2 * hf] + al[2 * hf]), xp.y + (ah[2 * hf + 1] + al[2 * hf + 1]));
+        if (z < nz && mem_tg >= 0) x_hat[(size_t)mem_tg * ldz + z] = xn;
+        unsigned h0b, l0b, h1b, l1b;
+        split_tf32(xn.x, h0b, l0b);
+        split_tf32(xn.y, h1b, l1b);
+        *reinterpret_cast<uint2*>(s_xh + z * 8 + 2 * tg) = make_uint2(h0b, h1b);
+        *reinterpret_cast<uint2*>(s_xl + z * 8 + 2 * tg) = make_uint2(l0b, l1b);
+      }
+    }
+    cons_sync();
+    // ---- D: Kx[t][r] = sum_z W[t][z] x_new[z][r] / s; warps over 16-row t tiles ----
+    for (int mt = warp; mt < mtt; mt += PIPE_CONS_WARPS) {
+      float dh[4] = {0.f, 0.f, 0.f, 0.f}, dlo[4] = {0.f, 0.f, 0.f, 0.f};
+      const float* w0 = W + 2 * mt * zb * 64;  // block (t / 8 = 2 mt, z / 8 = 0)
+      for (int ks = 0; ks < kz; ++ks) {
+        const float* wb = w0 + ks * 64;
+        const float a[4] = {wb[offF0], wb[zb * 64 + offF0], wb[offF2], wb[zb * 64 + offF2]};
+        const int b0 = (8 * ks + tg) * 8 + g, b1 = b0 + 32;
+        mma_3xtf32_2acc(dh, dlo, a, s_xh[b0], s_xh[b1], s_xl[b0], s_xl[b1]);
+      }
+      if (mem_tg >= 0) {
+        float2* dst = kx_hat + (size_t)mem_tg * ldt;
+        const int t = 16 * mt + g;
+        if (t < nt) dst[t] = make_float2((dh[0] + dlo[0]) * inv_s, (dh[1] + dlo[1]) * inv_s);
+        if (t + 8 < nt) dst[t + 8] = make_float2((dh[2] + dlo[2]) * inv_s, (dh[3] + dlo[3]) * inv_s);
+      }
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty + s);
+  }
+}
+
+template <int MZ>
+ctof_status launch_pipe(const ctof_kernel_s* k, const PipePlan& P, int grid, const float2* c_hat, const float2* s_hat,
+                        float2* x_hat, float2* kx_hat, float inv_scale, cudaStream_t st) {
+  CTOF_CUDA_TRY(
+      cudaFuncSetAttribute(k_contract_admm_pipe<MZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, P.total));
+  k_contract_admm_pipe<MZ><<<grid, PIPE_THREADS, P.total, st>>>(P, k->d_what_admm, k->d_hinv_admm, k->d_lap,
+                                                                 k->d_members, k->nclass, c_hat, k->ldt, s_hat,
+                                                                 x_hat, k->ldz, kx_hat, inv_scale, k->d_flags,
+                                                                 k->max_polls);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
 }  // namespace
 
 size_t contract_admm_smem_bytes(int nt, int nz, int nbuf) { return (size_t)make_layout(nt, nz, nbuf).total_floats * 4; }
 
+int contract_admm_pipe_stages(int nt, int nz) { return pipe_stages(nt, nz); }
+
+size_t contract_admm_pipe_floats(int nt, int nz, int which) {
+  if (!pipe_stages(nt, nz)) return 0;
+  const size_t tm = (size_t)rup(nt, 16), zm = (size_t)rup(nz, 16);
+  return which == 0 ? tm * zm : zm * zm;
+}
+
+ctof_status contract_admm_prepare(ctof_kernel_s* k, cudaStream_t st) {
+  if (!k->d_what_admm || !k->d_hinv_admm) return CTOF_OK;
+  const int tm = rup(k->nt, 16), zm = rup(k->nz, 16);
+  k_admm_reorder<<<152 * 8, 256, 0, st>>>(k->d_what, k->nt, k->nz, k->z4, tm, zm, k->d_what_admm, k->nclass);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  k_admm_reorder<<<152 * 8, 256, 0, st>>>(k->d_hinv, k->nz, k->nz, k->z4, zm, zm, k->d_hinv_admm, k->nclass);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
 ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const float2* s_hat, float2* x_hat,
                           float2* kx_hat, float inv_scale, cudaStream_t st) {
+  const int stages = k->d_what_admm ? pipe_stages(k->nt, k->nz) : 0;
+  if (stages) {
+    const PipePlan P = make_pipe_plan(k->nt, k->nz, stages);
+    int nsm = 152;
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
+    const int grid = k->nclass < nsm ? k->nclass : nsm;
+    switch (P.zm >> 4) {
+      case 1: return launch_pipe<1>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
+      case 2: return launch_pipe<2>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
+      case 3: return launch_pipe<3>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
+      default: return launch_pipe<4>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
+    }
+  }
   const size_t limit = 227 * 1024;
   // Two single-buffered CTAs per SM when they fit (one computes while the
   // other loads), else one double-buffered CTA.

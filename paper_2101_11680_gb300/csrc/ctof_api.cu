@@ -652,6 +652,9 @@ ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, 
   const size_t o_what = cv.take<float>((size_t)k->nclass * nt * k->z4);
   const size_t o_gram = cv.take<double>((size_t)k->nclass * nz * nz);
   const size_t o_hinv = cv.take<float>((size_t)k->nclass * nz * k->z4);
+  const size_t wa_per = contract_admm_pipe_floats(nt, nz, 0), ha_per = contract_admm_pipe_floats(nt, nz, 1);
+  const size_t o_wa = wa_per ? cv.take<float>((size_t)k->nclass * wa_per) : 0;
+  const size_t o_ha = wa_per ? cv.take<float>((size_t)k->nclass * ha_per) : 0;
   const size_t o_tw = cv.take<float2>(P);
   const size_t o_st = cv.take<float2>((size_t)k->nf * k->ldt);
   const size_t o_st2 = cv.take<float2>((size_t)k->nf * k->ldt);
@@ -681,6 +684,8 @@ ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, 
   k->d_what = reinterpret_cast<float*>(b + o_what);
   k->d_gram = reinterpret_cast<double*>(b + o_gram);
   k->d_hinv = reinterpret_cast<float*>(b + o_hinv);
+  k->d_what_admm = wa_per ? reinterpret_cast<float*>(b + o_wa) : nullptr;
+  k->d_hinv_admm = wa_per ? reinterpret_cast<float*>(b + o_ha) : nullptr;
   k->d_tw = reinterpret_cast<float2*>(b + o_tw);
   k->d_spec_t = reinterpret_cast<float2*>(b + o_st);
   k->d_spec_t2 = reinterpret_cast<float2*>(b + o_st2);
@@ -766,6 +771,7 @@ ctof_status ctof_kernel_get_info(ctof_kernel k, ctof_kernel_info* info) {
   info->nz = k->nz;
   info->scale = k->scale;
   info->gram_max_diag = k->gram_max;
+  info->admm_stages = k->d_what_admm ? contract_admm_pipe_stages(k->nt, k->nz) : 0;
   const size_t tik_bytes = (size_t)k->nclass * k->nz * k->z4 * sizeof(float);
   info->device_bytes = k->bytes + (k->d_w ? (size_t)k->nt * k->nz * k->q * k->q * sizeof(double) : 0) +
                        ((k->d_tik_hinv[0] ? 1 : 0) + (k->d_tik_hinv[1] ? 1 : 0)) * tik_bytes;

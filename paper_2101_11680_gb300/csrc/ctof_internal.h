@@ -43,6 +43,8 @@ struct ctof_kernel_s {
   float* d_what;       // [nclass][nt][z4] (zero padding)
   double* d_gram;      // [nclass][nz][nz]
   float* d_hinv;       // [nclass][nz][z4]  (ADMM normal matrix inverse, normalised units)
+  float* d_what_admm;  // W_hat in the ADMM kernel's block layout [nclass][tm/8][zm/8][64] (or null)
+  float* d_hinv_admm;  // H^-1 in the same layout [nclass][zm/8][zm/8][64] (or null)
   float2* d_tw;        // [p] forward twiddles exp(-2 pi i j / P)
   double* d_w;         // optional FP64 kernel table [nt][nz][q][q]
 
@@ -188,6 +190,13 @@ ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const flo
 ctof_status contract_tikhonov(const ctof_kernel_s* k, const float* hinv, const float2* m_hat,
                               float2* x_hat, cudaStream_t st);
 size_t contract_admm_smem_bytes(int nt, int nz, int nbuf);
+// Floats per class of the pipelined ADMM kernel's W_hat (which = 0) or H^-1
+// (which = 1) copy; 0 when that kernel does not apply at this size.
+size_t contract_admm_pipe_floats(int nt, int nz, int which);
+// Stages of the pipelined ADMM kernel at this size (0: the fallback kernel).
+int contract_admm_pipe_stages(int nt, int nz);
+// Fill the pipelined kernel's copies from d_what / d_hinv (after the build).
+ctof_status contract_admm_prepare(ctof_kernel_s* k, cudaStream_t st);
 
 // ---- batch_tikhonov.cu ----------------------------------------------------
 size_t batch_tikhonov_smem_bytes(int nt, int nz);

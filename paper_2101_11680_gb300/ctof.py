@@ -41,7 +41,7 @@ class GridSpec(ctypes.Structure):
 class KernelInfo(ctypes.Structure):
     _fields_ = [("p", ctypes.c_int), ("n_freq", ctypes.c_int), ("n_class", ctypes.c_int), ("nt", ctypes.c_int),
                 ("nz", ctypes.c_int), ("scale", ctypes.c_double), ("gram_max_diag", ctypes.c_double),
-                ("device_bytes", ctypes.c_size_t)]
+                ("device_bytes", ctypes.c_size_t), ("admm_stages", ctypes.c_int)]
 
 
 class SolverParams(ctypes.Structure):
