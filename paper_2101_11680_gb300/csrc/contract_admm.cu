@@ -353,7 +353,7 @@ struct PipePlan {
   int nt, nz, z4, zm, tm, ntp;
   int cs, sz;                     // words per member row: c stage (2 tm + 8), s / x stages (2 z4 + 8)
   int stages;
-  int o_w, o_h, o_c, o_s, o_x;    // byte offsets within a stage
+  int o_w, o_h, o_c, o_s, o_x, o_hdr;  // byte offsets within a stage
   int stage_bytes;
   int o_part, o_bh, o_bl, o_xh, o_xl, o_bar;  // byte offsets after the stages
   int total;
@@ -376,7 +376,8 @@ PipePlan make_pipe_plan(int nt, int nz, int stages) {
   P.o_c = P.o_h + P.zm * P.zm * 4;
   P.o_s = P.o_c + 4 * P.cs * 4;
   P.o_x = P.o_s + 4 * P.sz * 4;
-  P.stage_bytes = rup(P.o_x + 4 * P.sz * 4, 128);
+  P.o_hdr = P.o_x + 4 * P.sz * 4;  // 4 member indices + the diagonal of L (written by the producer)
+  P.stage_bytes = rup(P.o_hdr + 32, 128);
   P.o_part = stages * P.stage_bytes;
   P.o_bh = P.o_part + PIPE_CONS_WARPS * P.zm * 8 * 4;
   P.o_bl = P.o_bh + P.zm * 8 * 4;
@@ -462,18 +463,6 @@ __device__ __forceinline__ int cons_sync_or(int v) {
   return out;
 }
 
-// d += A B with separate accumulators for the large (hi*hi) and the small
-// (lo*hi + hi*lo) terms: two short dependency chains instead of one long one.
-__device__ __forceinline__ void mma_3xtf32_2acc(float (&dh)[4], float (&dl)[4], const float (&a)[4], unsigned bh0,
-                                                unsigned bh1, unsigned bl0, unsigned bl1) {
-  unsigned ah[4], al[4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) split_tf32(a[i], ah[i], al[i]);
-  mma_tf32(dl, al, bh0, bh1);
-  mma_tf32(dl, ah, bl0, bl1);
-  mma_tf32(dh, ah, bh0, bh1);
-}
-
 // W_hat -> [class][tm/8][zm/8][64] and H^-1 -> [class][zm/8][zm/8][64] in the
 // permuted 8 x 8 block layout described at the top of this file (zero padding).
 __global__ void k_admm_reorder(const float* __restrict__ src, int rows, int cols, int ld, int rm, int cm,
@@ -491,11 +480,42 @@ __global__ void k_admm_reorder(const float* __restrict__ src, int rows, int cols
   }
 }
 
-template <int MZ>
+// TF32 split for the pipelined kernel: hi = x rounded to the TF32 grid (to
+// nearest, ties away from zero: the same value as cvt.rna), lo = x - hi
+// exactly, passed to the MMA as raw FP32 bits, of which the tensor core reads
+// the TF32 part (|lo| <= 2^-11 |x|, so what is dropped is below 2^-21 |x|).
+__device__ __forceinline__ void split_fast(float x, unsigned& hi, unsigned& lo) {
+  hi = (__float_as_uint(x) + 0x1000u) & 0xffffe000u;
+  lo = __float_as_uint(x - __uint_as_float(hi));
+}
+
+__device__ __forceinline__ void mma_split_a(float (&d)[4], const float (&a)[4], unsigned bh0, unsigned bh1,
+                                            unsigned bl0, unsigned bl1) {
+  unsigned ah[4], al[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split_fast(a[i], ah[i], al[i]);
+  mma_tf32(d, al, bh0, bh1);
+  mma_tf32(d, ah, bl0, bl1);
+  mma_tf32(d, ah, bh0, bh1);
+}
+
+__device__ __forceinline__ void mma_split_a_2acc(float (&dh)[4], float (&dl)[4], const float (&a)[4], unsigned bh0,
+                                                 unsigned bh1, unsigned bl0, unsigned bl1) {
+  unsigned ah[4], al[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) split_fast(a[i], ah[i], al[i]);
+  mma_tf32(dl, al, bh0, bh1);
+  mma_tf32(dl, ah, bl0, bl1);
+  mma_tf32(dh, ah, bh0, bh1);
+}
+
+// KZ = forward K steps = ceil(nz / 8); MZ = 16-row z tiles = ceil(nz / 16).
+template <int KZ>
 __global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
     PipePlan P, const float* __restrict__ what_o, const float* __restrict__ hinv_o, const float* __restrict__ lap,
     const int* __restrict__ members, int nclass, const float2* c_hat, int ldt, const float2* s_hat, float2* x_hat,
     int ldz, float2* __restrict__ kx_hat, float inv_s, int* status_flag, long long max_polls) {
+  constexpr int MZ = (KZ + 1) / 2;
   extern __shared__ __align__(128) float4 sm_pipe[];
   unsigned char* sm = reinterpret_cast<unsigned char*>(sm_pipe);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -550,6 +570,12 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
         f[m] = __ldg(members + 4 * c + m);
         if (f[m] >= 0) bytes += P.c_bytes + 2 * P.v_bytes;
       }
+      // the class header (members, diagonal of L) for the consumers; the
+      // arrive below releases these stores to them
+      int* hdr = reinterpret_cast<int*>(st + P.o_hdr);
+#pragma unroll
+      for (int m = 0; m < 4; ++m) hdr[m] = f[m];
+      reinterpret_cast<float*>(hdr)[4] = __ldg(lap + c) + 1.0f;
       mbar_expect_tx(full + s, bytes);
       bulk_g2s(st + P.o_w, what_o + (size_t)c * P.tm * P.zm, P.w_bytes, full + s);
       bulk_g2s(st + P.o_h, hinv_o + (size_t)c * P.zm * P.zm, P.h_bytes, full + s);
@@ -575,19 +601,20 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
   const int g = lane >> 2, tg = lane & 3;
   const int hg = g >> 2;
   // word offsets of this lane's fragment elements inside an 8 x 8 block
-  const int offF0 = 4 * g + tg;                                // (row g, column tg)
-  const int offF2 = 32 + 4 * ((g + 4) & 7) + tg;               // (row g, column tg + 4)
+  const int offF0 = 4 * g + tg;                                       // (row g, column tg)
+  const int offF2 = 32 + 4 * ((g + 4) & 7) + tg;                      // (row g, column tg + 4)
   const int offA0 = 32 * hg + 4 * ((tg + 4 * hg) & 7) + (g & 3);      // (row tg, column g)
   const int offA2 = 32 * hg + 4 * ((tg + 4 + 4 * hg) & 7) + (g & 3);  // (row tg + 4, column g)
-  const int nt = P.nt, nz = P.nz, zm = P.zm, zb = zm >> 3;
-  const int kt = (nt + 7) >> 3, kz = (nz + 7) >> 3, mtt = P.tm >> 4;
-  float* part = reinterpret_cast<float*>(sm + P.o_part);  // [warp][zm][8]
-  unsigned* s_bh = reinterpret_cast<unsigned*>(sm + P.o_bh);  // [zm][8] b, TF32 hi / lo
+  const int nt = P.nt, nz = P.nz;
+  constexpr int ZB = 2 * MZ, ZM = 16 * MZ;  // z blocks of 8, padded depth
+  const int kt = (nt + 7) >> 3, mtt = P.tm >> 4;
+  float* part = reinterpret_cast<float*>(sm + P.o_part);      // [warp][ZM][8]
+  unsigned* s_bh = reinterpret_cast<unsigned*>(sm + P.o_bh);  // [ZM][8] b, TF32 hi / raw lo
   unsigned* s_bl = reinterpret_cast<unsigned*>(sm + P.o_bl);
-  unsigned* s_xh = reinterpret_cast<unsigned*>(sm + P.o_xh);  // [zm][8] x_new, TF32 hi / lo
+  unsigned* s_xh = reinterpret_cast<unsigned*>(sm + P.o_xh);  // [ZM][8] x_new, TF32 hi / raw lo
   unsigned* s_xl = reinterpret_cast<unsigned*>(sm + P.o_xl);
   for (int k = 0; k < mine; ++k) {
-    const int c = (int)blockIdx.x + k * (int)gridDim.x, s = k % S;
+    const int s = k % S;
     int gave_up = 0;
     if (!mbar_wait_bounded(full + s, (uint32_t)((k / S) & 1), max_polls)) {
       gave_up = 1;
@@ -599,6 +626,7 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
     const float* C = reinterpret_cast<const float*>(st + P.o_c);
     const float* SV = reinterpret_cast<const float*>(st + P.o_s);
     const float* XV = reinterpret_cast<const float*>(st + P.o_x);
+    const int* hdr = reinterpret_cast<const int*>(st + P.o_hdr);
 
     // ---- A: adjoint partial sums y_w[z][r] = sum over this warp's t of W[t][z] c[t][r] ----
     {
@@ -607,23 +635,26 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
       for (int mt = 0; mt < MZ; ++mt)
 #pragma unroll
         for (int i = 0; i < 4; ++i) acc[mt][i] = 0.f;
-      const float* cb = C + (g >> 1) * P.cs + 2 * tg + (g & 1);
+      const float* cr = C + (g >> 1) * P.cs + 2 * tg + (g & 1) + 16 * warp;  // t = 8 ks + tg
+      const float* wa0 = W + warp * ZB * 64 + offA0;
+      const float* wa2 = W + warp * ZB * 64 + offA2;
+#pragma unroll 2
       for (int ks = warp; ks < kt; ks += PIPE_CONS_WARPS) {
-        const float* cr = cb + 16 * ks;  // t = 8 ks + tg (b0) and 8 ks + 4 + tg (b1)
         unsigned bh0, bl0, bh1, bl1;
-        split_tf32(cr[0], bh0, bl0);
-        split_tf32(cr[8], bh1, bl1);
-        const float* wb = W + ks * zb * 64;  // block (t / 8 = ks, z / 8 = 0)
+        split_fast(cr[0], bh0, bl0);
+        split_fast(cr[8], bh1, bl1);
 #pragma unroll
         for (int mt = 0; mt < MZ; ++mt) {
-          const float* w0 = wb + 2 * mt * 64;
-          const float a[4] = {w0[offA0], w0[64 + offA0], w0[offA2], w0[64 + offA2]};
-          mma_3xtf32(acc[mt], a, bh0, bh1, bl0, bl1);
+          const float a[4] = {wa0[128 * mt], wa0[128 * mt + 64], wa2[128 * mt], wa2[128 * mt + 64]};
+          mma_split_a(acc[mt], a, bh0, bh1, bl0, bl1);
         }
+        cr += 16 * PIPE_CONS_WARPS;
+        wa0 += PIPE_CONS_WARPS * ZB * 64;
+        wa2 += PIPE_CONS_WARPS * ZB * 64;
       }
 #pragma unroll
       for (int mt = 0; mt < MZ; ++mt) {
-        float* p = part + (warp * zm + 16 * mt + g) * 8 + 2 * tg;
+        float* p = part + (warp * ZM + 16 * mt + g) * 8 + 2 * tg;
         *reinterpret_cast<float2*>(p) = make_float2(acc[mt][0], acc[mt][1]);
         *reinterpret_cast<float2*>(p + 64) = make_float2(acc[mt][2], acc[mt][3]);
       }
@@ -634,34 +665,35 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
     }
     // ---- B: b = y / s + s_hat - L x_prev, split for the H^-1 MMA ----
     {
-      const float dl = __ldg(lap + c) + 1.0f;
+      const float dl = reinterpret_cast<const float*>(hdr)[4];
       for (int i = tid; i < nz * 8; i += PIPE_CONS_THREADS) {
         const int z = i >> 3, r = i & 7, m = r >> 1, cp = r & 1;
         float y = 0.f;
 #pragma unroll
-        for (int w = 0; w < PIPE_CONS_WARPS; ++w) y += part[(w * zm + z) * 8 + r];
-        const float* xm = XV + m * P.sz + cp;
-        const float xz = xm[2 * z];
+        for (int w = 0; w < PIPE_CONS_WARPS; ++w) y += part[w * ZM * 8 + i];
+        const float* xm = XV + m * P.sz + cp + 2 * z;
+        const float xz = xm[0];
         float lx = dl * xz;
-        if (z > 0) lx += xz - xm[2 * (z - 1)];
-        if (z < nz - 1) lx -= xm[2 * (z + 1)] - xz;
+        if (z > 0) lx += xz - xm[-2];
+        if (z < nz - 1) lx -= xm[2] - xz;
         unsigned h, l;
-        split_tf32(y * inv_s + SV[m * P.sz + 2 * z + cp] - lx, h, l);
+        split_fast(y * inv_s + SV[m * P.sz + 2 * z + cp] - lx, h, l);
         s_bh[i] = h;
         s_bl[i] = l;
       }
     }
     cons_sync();
-    const int mem_tg = __ldg(members + 4 * c + tg);  // this lane's output member (D columns 2 tg, 2 tg + 1)
+    const int mem_tg = hdr[tg];  // this lane's output member (D columns 2 tg, 2 tg + 1)
     // ---- C: x_new = x_prev + H^-1 b; one warp per 16-row z tile ----
     if (warp < MZ) {
       float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
-      const float* h0 = H + 2 * warp * zb * 64;  // block (z / 8 = 2 warp, w / 8 = 0)
-      for (int ks = 0; ks < zb; ++ks) {
+      const float* h0 = H + 2 * warp * ZB * 64;  // block (z / 8 = 2 warp, w / 8 = 0)
+#pragma unroll
+      for (int ks = 0; ks < ZB; ++ks) {
         const float* hb = h0 + ks * 64;
-        const float a[4] = {hb[offF0], hb[zb * 64 + offF0], hb[offF2], hb[zb * 64 + offF2]};
+        const float a[4] = {hb[offF0], hb[ZB * 64 + offF0], hb[offF2], hb[ZB * 64 + offF2]};
         const int b0 = (8 * ks + tg) * 8 + g, b1 = b0 + 32;
-        mma_3xtf32_2acc(ah, al, a, s_bh[b0], s_bh[b1], s_bl[b0], s_bl[b1]);
+        mma_split_a_2acc(ah, al, a, s_bh[b0], s_bh[b1], s_bl[b0], s_bl[b1]);
       }
 #pragma unroll
       for (int hf = 0; hf < 2; ++hf) {
@@ -670,28 +702,51 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
         const float2 xn = make_float2(xp.x + (ah[2 * hf] + al[2 * hf]), xp.y + (ah[2 * hf + 1] + al[2 * hf + 1]));
         if (z < nz && mem_tg >= 0) x_hat[(size_t)mem_tg * ldz + z] = xn;
         unsigned h0b, l0b, h1b, l1b;
-        split_tf32(xn.x, h0b, l0b);
-        split_tf32(xn.y, h1b, l1b);
+        split_fast(xn.x, h0b, l0b);
+        split_fast(xn.y, h1b, l1b);
         *reinterpret_cast<uint2*>(s_xh + z * 8 + 2 * tg) = make_uint2(h0b, h1b);
         *reinterpret_cast<uint2*>(s_xl + z * 8 + 2 * tg) = make_uint2(l0b, l1b);
       }
     }
     cons_sync();
-    // ---- D: Kx[t][r] = sum_z W[t][z] x_new[z][r] / s; warps over 16-row t tiles ----
-    for (int mt = warp; mt < mtt; mt += PIPE_CONS_WARPS) {
-      float dh[4] = {0.f, 0.f, 0.f, 0.f}, dlo[4] = {0.f, 0.f, 0.f, 0.f};
-      const float* w0 = W + 2 * mt * zb * 64;  // block (t / 8 = 2 mt, z / 8 = 0)
-      for (int ks = 0; ks < kz; ++ks) {
-        const float* wb = w0 + ks * 64;
-        const float a[4] = {wb[offF0], wb[zb * 64 + offF0], wb[offF2], wb[zb * 64 + offF2]};
-        const int b0 = (8 * ks + tg) * 8 + g, b1 = b0 + 32;
-        mma_3xtf32_2acc(dh, dlo, a, s_xh[b0], s_xh[b1], s_xl[b0], s_xl[b1]);
+    // ---- D: Kx[t][r] = sum_z W[t][z] x_new[z][r] / s; each warp two 16-row t tiles at a time ----
+    {
+      unsigned xb[KZ][4];  // B fragments (hi0, hi1, lo0, lo1) of every K step, shared by the tiles
+#pragma unroll
+      for (int ks = 0; ks < KZ; ++ks) {
+        const int b0 = (8 * ks + tg) * 8 + g;
+        xb[ks][0] = s_xh[b0];
+        xb[ks][1] = s_xh[b0 + 32];
+        xb[ks][2] = s_xl[b0];
+        xb[ks][3] = s_xl[b0 + 32];
       }
-      if (mem_tg >= 0) {
-        float2* dst = kx_hat + (size_t)mem_tg * ldt;
-        const int t = 16 * mt + g;
-        if (t < nt) dst[t] = make_float2((dh[0] + dlo[0]) * inv_s, (dh[1] + dlo[1]) * inv_s);
-        if (t + 8 < nt) dst[t + 8] = make_float2((dh[2] + dlo[2]) * inv_s, (dh[3] + dlo[3]) * inv_s);
+      float2* dst = mem_tg >= 0 ? kx_hat + (size_t)mem_tg * ldt : nullptr;
+      for (int mt = warp; mt < mtt; mt += 2 * PIPE_CONS_WARPS) {
+        const int mt2 = mt + PIPE_CONS_WARPS;
+        const bool two = mt2 < mtt;
+        float dh[2][4] = {}, dlo[2][4] = {};
+        const float* w0 = W + 2 * mt * ZB * 64;   // block (t / 8 = 2 mt, z / 8 = 0)
+        const float* w1 = W + 2 * mt2 * ZB * 64;
+#pragma unroll
+        for (int ks = 0; ks < KZ; ++ks) {
+          const float a0[4] = {w0[ks * 64 + offF0], w0[(ZB + ks) * 64 + offF0], w0[ks * 64 + offF2],
+                               w0[(ZB + ks) * 64 + offF2]};
+          mma_split_a_2acc(dh[0], dlo[0], a0, xb[ks][0], xb[ks][1], xb[ks][2], xb[ks][3]);
+          if (two) {
+            const float a1[4] = {w1[ks * 64 + offF0], w1[(ZB + ks) * 64 + offF0], w1[ks * 64 + offF2],
+                                 w1[(ZB + ks) * 64 + offF2]};
+            mma_split_a_2acc(dh[1], dlo[1], a1, xb[ks][0], xb[ks][1], xb[ks][2], xb[ks][3]);
+          }
+        }
+        if (dst) {
+#pragma unroll
+          for (int u = 0; u < 2; ++u) {
+            if (u == 1 && !two) break;
+            const int t = 16 * (u ? mt2 : mt) + g;
+            if (t < nt) dst[t] = make_float2((dh[u][0] + dlo[u][0]) * inv_s, (dh[u][1] + dlo[u][1]) * inv_s);
+            if (t + 8 < nt) dst[t + 8] = make_float2((dh[u][2] + dlo[u][2]) * inv_s, (dh[u][3] + dlo[u][3]) * inv_s);
+          }
+        }
       }
     }
     __syncwarp();
@@ -699,12 +754,12 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
   }
 }
 
-template <int MZ>
+template <int KZ>
 ctof_status launch_pipe(const ctof_kernel_s* k, const PipePlan& P, int grid, const float2* c_hat, const float2* s_hat,
                         float2* x_hat, float2* kx_hat, float inv_scale, cudaStream_t st) {
   CTOF_CUDA_TRY(
-      cudaFuncSetAttribute(k_contract_admm_pipe<MZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, P.total));
-  k_contract_admm_pipe<MZ><<<grid, PIPE_THREADS, P.total, st>>>(P, k->d_what_admm, k->d_hinv_admm, k->d_lap,
+      cudaFuncSetAttribute(k_contract_admm_pipe<KZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, P.total));
+  k_contract_admm_pipe<KZ><<<grid, PIPE_THREADS, P.total, st>>>(P, k->d_what_admm, k->d_hinv_admm, k->d_lap,
                                                                  k->d_members, k->nclass, c_hat, k->ldt, s_hat,
                                                                  x_hat, k->ldz, kx_hat, inv_scale, k->d_flags,
                                                                  k->max_polls);
@@ -742,11 +797,15 @@ ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const flo
     int nsm = 152;
     cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
     const int grid = k->nclass < nsm ? k->nclass : nsm;
-    switch (P.zm >> 4) {
+    switch ((k->nz + 7) >> 3) {
       case 1: return launch_pipe<1>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
       case 2: return launch_pipe<2>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
       case 3: return launch_pipe<3>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
-      default: return launch_pipe<4>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
+      case 4: return launch_pipe<4>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
+      case 5: return launch_pipe<5>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
+      case 6: return launch_pipe<6>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
+      case 7: return launch_pipe<7>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
+      default: return launch_pipe<8>(k, P, grid, c_hat, s_hat, x_hat, kx_hat, inv_scale, st);
     }
   }
   const size_t limit = 227 * 1024;
