@@ -109,6 +109,30 @@ def poisson_noise(m, peak, seed):
     return rng.poisson(lam).astype(np.float64) * (mx / peak)
 
 
+def dark_count_noise(m, rate_cps, integration_s, dark_cps, seed):
+    """Photon counting with detector dark counts (the noise of the paper's
+    multiplexing simulations, Section 5: Poisson photon noise at a detected
+    count rate, plus dark counts at a fixed rate, 200 counts/s for its SPAD).
+
+    m [T][...]: clean non-negative measurement, time bins on the first axis.
+    Reading: the brightest measurement (largest sum over its T bins) collects
+    rate_cps * integration_s photons; every measurement collects
+    dark_cps * integration_s dark counts, spread evenly over its T bins.
+    Returns (counts, unit, dark_per_bin): counts ~ Poisson(m / unit +
+    dark_per_bin) (int64), with unit = max_x sum_t m / (rate_cps *
+    integration_s); (counts - dark_per_bin) * unit is an unbiased estimate of m.
+    """
+    m = np.asarray(m, dtype=np.float64)
+    nt = m.shape[0]
+    total = m.reshape(nt, -1).sum(axis=0).max()
+    photons = float(rate_cps) * float(integration_s)
+    unit = float(total) / photons if total > 0 and photons > 0 else 1.0
+    dark_per_bin = float(dark_cps) * float(integration_s) / nt
+    rng = _rng(seed)
+    lam = np.clip(m, 0.0, None) / unit + dark_per_bin
+    return rng.poisson(lam), unit, dark_per_bin
+
+
 # (input channels, output channels) of the four 3x3x3 layers of the learned prox
 LEARNED_LAYERS = ((1, 16), (16, 16), (16, 16), (16, 1))
 

@@ -227,6 +227,37 @@ def test_poisson_noise_statistics():
     assert y[1:].var() == pytest.approx(0.25 * 1e-4, rel=2e-2)
 
 
+def test_dark_count_noise_statistics():
+    """Dark-count noise of the multiplexing simulations (Section 5: 200 counts/s dark rate).
+
+    With no light every measurement holds only dark counts: dark_cps x
+    integration time per measurement, spread over its bins, Poisson (mean =
+    variance).  With light, the brightest measurement collects rate x time
+    photons, and the dark-subtracted counts are an unbiased estimate of m.
+    """
+    nt, n = 64, 24
+    dark = synth.dark_count_noise(np.zeros((nt, n, n)), 5e6, 0.5, 200.0, seed=1)
+    counts, unit, per_bin = dark
+    assert per_bin == pytest.approx(200.0 * 0.5 / nt)
+    tot = counts.reshape(nt, -1).sum(axis=0)  # dark counts per measurement: Poisson(100)
+    assert tot.mean() == pytest.approx(100.0, rel=0.02)
+    assert tot.var() == pytest.approx(100.0, rel=0.1)
+    t = np.arange(nt)[:, None, None]
+    m = np.exp(-((t - 20.0) / 6.0) ** 2) * np.ones((1, n, n)) * np.linspace(0.2, 1.0, n)[None, None, :]
+    est = []
+    for seed in range(40):
+        c, unit, per_bin = synth.dark_count_noise(m, 5e6, 1e-3, 200.0, seed=100 + seed)
+        assert c.dtype.kind == "i"
+        assert unit * 5e6 * 1e-3 == pytest.approx(m.sum(axis=0).max())
+        est.append((c - per_bin) * unit)
+    est = np.array(est)
+    assert np.abs(est.mean(axis=0) - m).max() <= 6 * np.sqrt(m.max() * unit / 40 + 1e-30)
+    # Poisson: the variance of the counts equals their mean
+    lam = m / unit + per_bin
+    var = (est / unit).var(axis=0)
+    assert float(np.mean(var[lam > 50] / lam[lam > 50])) == pytest.approx(1.0, rel=0.05)
+
+
 def test_depth_sensitivity_is_response_to_a_constant_plane():
     """Periodic grid: K applied to a constant plane of ones at depth z is the DC
     term alone, so ||K 1_z|| = P sigma(z); sigma falls with depth (Eq. 10's
