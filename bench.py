@@ -536,38 +536,38 @@ def run_fista(args, cfg):
     kern.close()
 
 
-def run_learned(args, cfg):
-    """Learned unrolled solver vs plain FP32 ADMM (100 iterations) on the same seeded volumes.
+def learned_comparison(cfg, count, warmup, batch=None, kern=None):
+    """Learned unrolled solver vs plain FP32 ADMM on the same `count` held-out volumes.
 
-    The timed step is one volume through the learned solver plus its data-residual
-    check; volumes whose residual exceeds the fallback threshold are then
-    reconstructed by ADMM inside the same timed region.
+    Timed step: the learned solver (volumes in batches of `batch`, W_hat read
+    once per class for all of them) plus its data-residual check; volumes whose
+    residual exceeds the fallback threshold (1.5 x the median ADMM residual of a
+    calibration set, seeds 9000..9007) are reconstructed by ADMM inside the same
+    timed region.  ADMM (the handle's `iters` iterations) is then timed on the
+    same volumes.  Returns a dict with both rates, errors, residuals, the
+    fallback rate and the learned path's end-to-end rate from pinned host memory.
     """
     import torch
-    from paper_2101_11680_gb300 import build as B
     from paper_2101_11680_gb300 import ctof
     from paper_2101_11680_gb300 import learned_train as LT
 
-    torch.cuda.set_device(0)
-    B.build()
     theta, stages, meta = LT.load()
     g = {k: cfg[k] for k in ("n", "nz", "nt", "dx", "dz", "z_first", "dt")}
-    kern = LT.make_kernel(g)
+    own = kern is None
+    if own:
+        kern = LT.make_kernel(g)
     net = LT.make_net(theta, stages, meta)
     params = ctof.admm_params(iters=cfg["iters"])
-    # fallback threshold from a calibration set (seeds 9000..9007)
     calib = LT.eval_set(kern, g, range(9000, 9008), cfg["peak"])
     calib_res = [LT.data_residual(kern, kern.reconstruct(m, params), m) for m, _ in calib]
     threshold = 1.5 * float(np.median(calib_res))
-    count = args.steps
     data = LT.eval_set(kern, g, range(10000, 10000 + count), cfg["peak"])
     ms = torch.stack([m for m, _ in data])
     outs = torch.empty((len(data), cfg["nz"], cfg["n"], cfg["n"]), device="cuda")
     res = torch.empty(len(data), device="cuda", dtype=torch.float64)
     m_norm = torch.stack([m.double().norm() for m, _ in data])
     pred = torch.empty((cfg["nt"], cfg["n"], cfg["n"]), device="cuda")
-
-    lb = args.batch or count  # volumes per learned call (W_hat read once per class for all of them)
+    lb = batch or count
 
     def learned_pass(lo, hi):
         for c in range(lo, hi, lb):
@@ -582,25 +582,22 @@ def run_learned(args, cfg):
             kern.reconstruct(ms[i], params, out=outs[i])
         return fb
 
-    for _ in range(max(1, args.warmup)):
+    for _ in range(max(1, warmup)):
         learned_pass(0, count)
     torch.cuda.synchronize()
-    clocks = ClockSampler(0)
+    clocks = ClockSampler(torch.cuda.current_device())
     clocks.start()
     time.sleep(0.3)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
-    torch.cuda.nvtx.range_push("learned_timed")
     fallback = learned_pass(0, count)
-    torch.cuda.nvtx.range_pop()
     e1.record()
     torch.cuda.synchronize()
     t_learned = e0.elapsed_time(e1)
     clk = clocks.stop()
     learned_res = [float(r) for r in res[:count].cpu()]
     learned_err = [LT.volume_error(outs[i], data[i][1]) for i in range(count)]
-    # plain ADMM on the same volumes
     adm = torch.empty_like(outs[0])
     kern.reconstruct(ms[0], params, out=adm)
     torch.cuda.synchronize()
@@ -613,7 +610,6 @@ def run_learned(args, cfg):
         t_admm += e0.elapsed_time(e1)
         admm_err.append(LT.volume_error(adm, data[i][1]))
         admm_res.append(LT.data_residual(kern, adm, ms[i]))
-    # end to end from pinned host measurements (learned path + residual check, results read back)
     mh = ms[:count].cpu().pin_memory()
     oh = torch.empty((count, cfg["nz"], cfg["n"], cfg["n"])).pin_memory()
     torch.cuda.synchronize()
@@ -625,30 +621,48 @@ def run_learned(args, cfg):
         oh[i].copy_(outs[i], non_blocking=True)
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    value = count / (t_learned / 1e3)
+    out = {"volumes": count, "volumes_per_call": lb, "stages": stages,
+           "learned": {"value": count / (t_learned / 1e3), "ms_per_volume": t_learned / count,
+                       "volume_error_mean": float(np.mean(learned_err)),
+                       "residual_mean": float(np.mean(learned_res)),
+                       "fallback_threshold": threshold, "fallback_rate": len(fallback) / count},
+           "admm": {"value": count / (t_admm / 1e3), "ms_per_volume": t_admm / count, "iters": cfg["iters"],
+                    "volume_error_mean": float(np.mean(admm_err)), "residual_mean": float(np.mean(admm_res))},
+           "speedup_vs_admm": t_admm / t_learned,
+           "e2e": {"value": count / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(ms[0].numel() * 4),
+                   "d2h_bytes_per_step": int(outs[0].numel() * 4)},
+           "meta": meta, "clocks": clk,
+           "l2": "inputs larger than L2 (W_hat %.0f MB streamed per operator application)"
+                 % (kern.info.n_class * cfg["nt"] * cfg["nz"] * 4 / 1e6)}
+    net.close()
+    if own:
+        kern.close()
+    return out
+
+
+def run_learned(args, cfg):
+    """Learned unrolled solver vs plain FP32 ADMM (100 iterations) on the same seeded volumes."""
+    import torch
+    from paper_2101_11680_gb300 import build as B
+    from paper_2101_11680_gb300 import learned_train as LT
+
+    torch.cuda.set_device(0)
+    B.build()
+    r = learned_comparison(cfg, args.steps, args.warmup, args.batch)
+    meta = r["meta"]
     line = {"metric": "volumes/sec at 128x128x48 (256 bins), learned unrolled solver with ADMM fallback, vs plain "
                       "FP32 ADMM on the same volumes",
-            "value": value, "unit": UNIT, "n_gpus": 1, "steps": count, "warmup": args.warmup,
-            "ms_per_step": t_learned / count, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "bf16", "data": "synthetic",
-            "config": {"workload": cfg["workload"], "stages": stages, "trained_on": meta.get("grid"),
+            "value": r["learned"]["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": r["learned"]["ms_per_volume"], "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+            "config": {"workload": cfg["workload"], "stages": r["stages"], "trained_on": meta.get("grid"),
                        "x0": "Tikhonov (lambda %g max Gram diag)" % meta.get("x0_lambda_rel", 0.0),
                        "data_consistency_steps": LT.DC_STEPS, "dc_lambda_rel": LT.DC_LAMBDA,
-                       "volumes_per_call": lb,
-                       "training_phantoms": meta.get("phantoms"),
-                       "l2": "inputs larger than L2 (W_hat %.0f MB streamed per operator application)"
-                             % (kern.info.n_class * cfg["nt"] * cfg["nz"] * 4 / 1e6)},
-            "admm": {"value": count / (t_admm / 1e3), "ms_per_volume": t_admm / count,
-                     "volume_error_mean": float(np.mean(admm_err)), "residual_mean": float(np.mean(admm_res))},
-            "learned": {"volume_error_mean": float(np.mean(learned_err)), "residual_mean": float(np.mean(learned_res)),
-                        "fallback_threshold": threshold, "fallback_rate": len(fallback) / count},
-            "speedup_vs_admm": (count / (t_learned / 1e3)) / (count / (t_admm / 1e3)),
-            "e2e": {"value": count / e2e_s, "unit": UNIT, "h2d_bytes_per_step": int(ms[0].numel() * 4),
-                    "d2h_bytes_per_step": int(outs[0].numel() * 4)},
-            "clocks": clk}
+                       "volumes_per_call": r["volumes_per_call"], "training_phantoms": meta.get("phantoms"),
+                       "l2": r["l2"]},
+            "admm": r["admm"], "learned": r["learned"], "speedup_vs_admm": r["speedup_vs_admm"],
+            "e2e": r["e2e"], "clocks": r["clocks"]}
     print(json.dumps(line), flush=True)
-    net.close()
-    kern.close()
 
 
 def main():
@@ -660,6 +674,8 @@ def main():
     ap.add_argument("--config", default="cfg2", choices=sorted(CONFIGS))
     ap.add_argument("--iters", type=int, default=None)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-learned", action="store_true",
+                    help="skip the learned-solver-vs-ADMM comparison attached to the default line")
     ap.add_argument("--seed", type=int, default=1000)
     ap.add_argument("--batch", type=int, default=None)
     ap.add_argument("--lateral", type=int, default=None,
@@ -823,6 +839,12 @@ def main():
         "clocks": clk,
         "quality": {"rel_l2_vs_phantom_mean": float(np.mean(errs))},
     }
+    if rank == 0 and not args.no_learned and emission is None and average is None and args.config == "cfg2":
+        # the metric's comparison: the learned solver (with ADMM fallback) against this plain FP32 ADMM on
+        # the same held-out volumes (16 volumes, one batched call)
+        r = learned_comparison(cfg, 16, 1, kern=kern)
+        line["learned_vs_admm"] = {k: r[k] for k in ("volumes", "volumes_per_call", "stages", "learned", "admm",
+                                                     "speedup_vs_admm", "e2e")}
     if rank == 0 and world == 1 and not args.no_cpu_baseline and emission is None and average is None:
         line["cpu_baseline"] = cpu_baseline(cfg)
     if rank == 0:
