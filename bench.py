@@ -328,11 +328,12 @@ def run_precision(args, cfg):
         clean = kern.forward(torch.tensor(mu, dtype=torch.float32, device="cuda")).double().clamp_(min=0)
         ms[i] = torch.tensor(synth.poisson_noise(clean.cpu().numpy(), cfg["peak"], seed=args.seed + 5000 + i),
                              dtype=torch.float32, device="cuda")
-    out = torch.empty((bsz, cfg["nz"], cfg["n"], cfg["n"]), device="cuda")
-    ref = torch.empty_like(out)
+    outs = {p: torch.empty((bsz, cfg["nz"], cfg["n"], cfg["n"]), device="cuda") for p in ("bf16", "fp8", "fp32")}
+    precs = {"bf16": ctof.BF16, "fp8": ctof.FP8E4M3, "fp32": ctof.FP32}
     times = {}
-    for name, prec, steps in (("bf16", ctof.BF16, args.steps), ("fp32", ctof.FP32, max(1, args.steps // 4))):
-        dst = out if prec == ctof.BF16 else ref
+    for name in ("bf16", "fp8", "fp32"):
+        prec, dst = precs[name], outs[name]
+        steps = args.steps if name != "fp32" else max(1, args.steps // 4)
         for _ in range(args.warmup):
             kern.reconstruct_batch_tikhonov(ms, precision=prec, refine=2, out=dst)
         torch.cuda.synchronize()
@@ -344,17 +345,33 @@ def run_precision(args, cfg):
         e1.record()
         torch.cuda.synchronize()
         times[name] = e0.elapsed_time(e1) / steps
-    err = max(float((out[i] - ref[i]).double().norm() / ref[i].double().norm()) for i in range(bsz))
-    kern.reconstruct_batch_tikhonov(ms, precision=ctof.BF16, refine=0, out=out)
-    torch.cuda.synchronize()
-    err0 = max(float((out[i] - ref[i]).double().norm() / ref[i].double().norm()) for i in range(bsz))
+    ref = outs["fp32"]
+
+    def max_err(o):
+        return max(float((o[i] - ref[i]).double().norm() / ref[i].double().norm()) for i in range(bsz))
+
+    errs = {n: max_err(outs[n]) for n in ("bf16", "fp8")}
+    errs0 = {}
+    for name in ("bf16", "fp8"):
+        kern.reconstruct_batch_tikhonov(ms, precision=precs[name], refine=0, out=outs[name])
+        torch.cuda.synchronize()
+        errs0[name] = max_err(outs[name])
+    info = kern.info
+    # algorithmic bytes of one contraction launch: m_hat read, x_hat written, W_hat and the solve tables read
+    zn = (cfg["nz"] + 15) // 16 * 16
+    alg = (info.n_freq * bsz * (cfg["nt"] + cfg["nz"]) * 8 + info.n_class * cfg["nt"] * ((cfg["nz"] + 3) // 4 * 4) * 4
+           + info.n_class * 4 * zn * zn * 2)
     line = {"metric": "volumes/sec, batched Tikhonov (precision form)", "value": bsz / (times["bf16"] / 1e3),
             "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": times["bf16"], "higher_is_better": True, "dtype": "bf16 (fp32 accumulate)",
             "data": "synthetic",
             "config": {"workload": cfg["workload"], "batch": bsz, "kernel_build_s": round(build_s, 2)},
+            "fp8": {"value": bsz / (times["fp8"] / 1e3), "ms_per_batch": times["fp8"],
+                    "rel_l2_refined_vs_fp32_path_max": errs["fp8"],
+                    "rel_l2_unrefined_vs_fp32_path_max": errs0["fp8"]},
             "fp32_path": {"value": bsz / (times["fp32"] / 1e3), "ms_per_batch": times["fp32"]},
-            "rel_l2_bf16_refined_vs_fp32_path_max": err, "rel_l2_bf16_unrefined_vs_fp32_path_max": err0}
+            "rel_l2_bf16_refined_vs_fp32_path_max": errs["bf16"], "rel_l2_bf16_unrefined_vs_fp32_path_max": errs0["bf16"],
+            "contraction_algorithmic_bytes": alg}
     print(json.dumps(line), flush=True)
     kern.close()
 

@@ -1,279 +1,660 @@
 // Precision form: Tikhonov reconstruction of a batch of B measurement volumes
-// that share one kernel, with the per-frequency contraction b = W_hat^T m_hat
-// on BF16 tensor cores and mixed-precision iterative refinement of the
-// Z x Z solve (the regularised inverse of Eq. 7 per lateral frequency).
+// that share one kernel (the per-frequency regularised inverse of Eq. 7 for
+// B measurements at once), with the per-frequency contraction
+// b = W_hat^T m_hat on the 5th-generation tensor cores in BF16 or FP8 (e4m3)
+// and the Z x Z solve refined iteratively:
 //
-//   W_hat = Q_hi + Q_lo,  m_hat = M_hi + M_lo        (BF16 pairs, exact split)
-//   b0    = Q_hi^T M_hi                              (one BF16 GEMM term)
-//   b     = Q_hi^T M_hi + Q_hi^T M_lo + Q_lo^T M_hi  (three terms, FP32 accumulation)
-//   x0    = C b0,   x_{i+1} = x_i + C (b - (G + lambda I) x_i)
-// with C = (G + lambda I)^-1 (FP64 Cholesky, stored FP32) and G the FP64 Gram
-// (stored FP32 for the residual).  x0 carries the BF16 error; each refinement
-// step replaces it by the error of the three-term product (about 2^-16).
+//   b0 = first product term only,  b = all product terms (FP32 accumulation)
+//   x0 = C b0,   x_{i+1} = x_i + C (b - (G + lambda I) x_i)
 //
-// One CTA (8 warps) per frequency class at a time: Q_hi / Q_lo (T x Zs, Zs the
-// depth count rounded to 16/32/64) and C, G stay in shared memory while the
-// batch streams through in chunks of two volumes (8 members x 2 volumes = 16
-// real right-hand sides).  Fragments come from swizzled shared rows via
-// ldmatrix (Q^T through .trans); products use mma.sync m16n8k16 BF16.
+// with C = (G + lambda I)^-1 (FP64 Cholesky) and G the FP64 Gram.  Operands
+// are split into narrow-format terms whose sum reproduces the FP32 value:
+//
+//   BF16: v = v_hi + v_lo (both BF16); b0 = hi.hi, b = hi.hi + (hi.lo + lo.hi)
+//   FP8:  v = s (q0 + q1/16 + q2/256), each q an e4m3 value, s a scale that
+//         maps the block's largest magnitude to 448 (per frequency class for
+//         W_hat, per right-hand side for m_hat); products grouped by level:
+//         D0 = q0.p0, D1 = q0.p1 + q1.p0, D2 = q0.p2 + q1.p1 + q2.p0,
+//         b0 = s_w s_m D0,  b = s_w s_m (D0 + D1/16 + D2/256)
+//
+// (a 2-term e4m3 split leaves the refined solution ~1e-2 from the exact one
+// on small grids; three terms bring it to ~1e-4).  The solve's products
+// (C b0, (G + lambda I) x, C r) run on the same tensor cores in TF32 with
+// hi/lo splits of both operands (three products each: FP32-level results):
+// the residual b - (G + lambda I) x is a small difference of nearly equal
+// terms, and BF16-level products there left the refined result at ~2e-4.
+//
+// One CTA of 8 warps per SM walks the frequency classes.  Per class, the
+// tables C and G + lambda I (BF16 hi/lo, canonical K-major layout, made once
+// per lambda, TF32 hi/lo) come in with 16-byte cp.async copies; the batch is taken 16 volumes at a
+// time: 16 volumes x 4 members x re/im = 128 right-hand sides = the M side of
+// the GEMM D[n][z] = sum_t m[n][t] W[t][z] (M = 128, N = Z rounded up to 16,
+// K = t in chunks of 32).  Each t chunk of m_hat rows and W_hat rows streams
+// into one of two raw shared-memory stages with 16-byte cp.async copies while
+// the previous chunk is split into its terms (W^T through 4 x 4 register
+// transposes) and multiplied; the term buffers are double-buffered as well,
+// each set guarded by its own MMA-completion mbarrier.  After the last chunk
+// the refinement runs on the TMEM accumulators: each thread owns one
+// right-hand side (a TMEM lane) and half of its Z columns.  Every wait is
+// bounded; a wait that runs out sets the handle's sticky flag, drains the
+// MMAs in flight and stops the CTA.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
-#include <vector>
-
 #include "ctof_internal.h"
+#include "umma.cuh"
 
 namespace {
 
 constexpr int BT_THREADS = 256;
-constexpr int BT_WARPS = BT_THREADS / 32;
-constexpr int BC = 2;            // volumes per chunk
-constexpr int NB = 8 * BC;       // real right-hand sides per chunk
+constexpr int VB = 16;             // volumes per chunk
+constexpr int NR = 8 * VB;         // right-hand sides per chunk (the GEMM's M = 128)
+constexpr int TCH = 32;            // t values per K chunk
+constexpr int RCS = TCH * 8 + 16;  // raw stage bytes per (volume, member) row
+constexpr long long DRAIN_POLLS = 1ll << 24;
+constexpr float E4M3_MAX = 448.f;
 
-__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+inline int rup(int x, int m) { return (x + m - 1) / m * m; }
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(smem_u32(smem)), "l"(gmem) : "memory");
-}
-__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
-
-__device__ __forceinline__ void ldsm_x4_trans(unsigned (&r)[4], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void ldsm_x2(unsigned (&r)[2], const void* p) {
-  asm volatile("ldmatrix.sync.aligned.m8n8.x2.shared.b16 {%0,%1}, [%2];\n"
-               : "=r"(r[0]), "=r"(r[1])
-               : "r"(smem_u32(p)));
-}
-__device__ __forceinline__ void mma_bf16(float (&d)[4], const unsigned (&a)[4], const unsigned (&b)[2]) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b[0]), "r"(b[1]));
-}
-
-struct BtLayout {
-  int nt, nz, z4, zs, tk;  // tk = nt rounded up to 16 (K extent)
-  int cs;                  // shared row pitch of C and G + lambda I: 4 (z4/4 | 1) floats
+struct BtPlan {
+  int nt, nz, z4, zn;  // zn = nz rounded up to 16 (N of the GEMMs, K of the solve)
+  int fp8, nterm, esize, epc;  // epc = elements per 16-byte core-matrix row
+  int a_term, b_term;          // bytes of one term of the A (m) and B (W^T) chunk tiles
+  int set_bytes;               // A terms + B terms
+  int raw_c, raw_stage;
+  int tab_bytes;               // C hi, C lo, G' hi, G' lo (TF32, zn x zn each)
+  int x_tile;                  // one TF32 [128][zn] A operand of the solve
+  int off_set, off_raw, off_tab, off_xh, off_xl, off_sn, off_bar, total;
   int batch;
-  // byte offsets in shared memory
-  int off_qh, off_ql, off_mh, off_ml, off_c, off_g, off_b0, off_bf, off_x;
-  int total;
 };
 
-// Q rows: zs bf16 = zs/8 chunks, chunk index XOR (t & (zs/8 - 1)).
-__device__ __forceinline__ int q_off(const BtLayout& L, int t, int chunk) {
-  const int mask = (L.zs >> 3) - 1;
-  return (t * L.zs + ((chunk ^ (t & mask)) << 3)) * 2;
-}
-// M rows (one per right-hand side n): tk bf16 = tk/8 chunks, chunk index rotated
-// by (n & 7) modulo the chunk count (stays inside the row for any tk).
-__device__ __forceinline__ int m_off(const BtLayout& L, int n, int chunk) {
-  const int nch = L.tk >> 3;
-  int cc = chunk + (n & 7);
-  cc = cc >= nch ? cc - nch : cc;
-  cc = cc >= nch ? cc % nch : cc;
-  return (n * L.tk + (cc << 3)) * 2;
+BtPlan make_plan(int nt, int nz, int fp8, int batch) {
+  BtPlan P{};
+  P.nt = nt;
+  P.nz = nz;
+  P.z4 = rup(nz, 4);
+  P.zn = rup(nz, 16);
+  P.fp8 = fp8;
+  P.nterm = fp8 ? 3 : 2;
+  P.esize = fp8 ? 1 : 2;
+  P.epc = 16 / P.esize;
+  P.a_term = NR * TCH * P.esize;
+  P.b_term = P.zn * TCH * P.esize;
+  P.set_bytes = P.nterm * (P.a_term + P.b_term);
+  P.raw_c = 4 * VB * RCS;
+  P.raw_stage = P.raw_c + TCH * P.z4 * 4;
+  P.tab_bytes = 4 * P.zn * P.zn * 4;
+  P.x_tile = NR * P.zn * 4;
+  P.batch = batch;
+  int off = 0;
+  auto take = [&](int bytes) {
+    const int at = off;
+    off += rup(bytes, 128);
+    return at;
+  };
+  P.off_set = take(2 * P.set_bytes);
+  P.off_raw = take(2 * P.raw_stage);
+  P.off_tab = take(P.tab_bytes);
+  P.off_xh = take(P.x_tile);
+  P.off_xl = take(P.x_tile);
+  P.off_sn = take(NR * 4);
+  P.off_bar = take(64);
+  P.total = off;
+  return P;
 }
 
-// sum_w row[w] v[w][nq .. nq+3] for v [.][NB] (FP32)
-__device__ __forceinline__ float4 small_mv(const float* __restrict__ row, const float* __restrict__ v, int nz, int nq) {
-  float4 a = make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll 4
-  for (int w = 0; w < nz; ++w) {
-    const float c = row[w];
-    const float4 b = *reinterpret_cast<const float4*>(v + w * NB + nq);
-    a.x = fmaf(c, b.x, a.x);
-    a.y = fmaf(c, b.y, a.y);
-    a.z = fmaf(c, b.z, a.z);
-    a.w = fmaf(c, b.w, a.w);
+// Instruction descriptors (FP32 accumulation, both operands K-major): D format
+// F32 in bits 4-5, A / B formats in bits 7-9 / 10-12 (kind::f16: BF16 = 1;
+// kind::f8f6f4: E4M3 = 0), N >> 3 in bits 17-22, M >> 4 in bits 24-28.
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+__host__ __device__ constexpr uint32_t idesc_e4m3(int m, int n) {
+  return (1u << 4) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_e4m3(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// Byte offset of the 16-byte core-matrix row holding elements (r, k .. k + epc - 1)
+// of a K-major no-swizzle tile of `rows` rows (k a multiple of epc).
+__device__ __forceinline__ uint32_t kchunk(int rows, int r, int k, int epc) {
+  return (uint32_t)(((k / epc) * rows + r) << 4);
+}
+
+__device__ __forceinline__ unsigned pack_bf16x2(float a, float b) {
+  __nv_bfloat162 h = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<unsigned*>(&h);
+}
+
+// BF16 split of 8 values into hi / lo 16-byte rows.
+__device__ __forceinline__ void split8_bf16(const float (&v)[8], uint4& hi, uint4& lo) {
+  unsigned h[4], l[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const __nv_bfloat162 p = __floats2bfloat162_rn(v[2 * i], v[2 * i + 1]);
+    const float2 back = __bfloat1622float2(p);
+    h[i] = *reinterpret_cast<const unsigned*>(&p);
+    l[i] = pack_bf16x2(v[2 * i] - back.x, v[2 * i + 1] - back.y);
   }
-  return a;
+  hi = make_uint4(h[0], h[1], h[2], h[3]);
+  lo = make_uint4(l[0], l[1], l[2], l[3]);
 }
 
-__global__ void __launch_bounds__(BT_THREADS, 1) k_batch_tikhonov_bf16(
-    BtLayout L, const __nv_bfloat16* __restrict__ qhi, const __nv_bfloat16* __restrict__ qlo,
-    const float* __restrict__ cinv, const float* __restrict__ glam, const int* __restrict__ members, int nclass,
-    const float2* __restrict__ m_hat, int ldm, float2* __restrict__ x_hat, int ldx, int refine) {
-  extern __shared__ __align__(128) unsigned char smb[];
-  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int g = lane >> 2, tg = lane & 3;
-  const int nt = L.nt, nz = L.nz, zs = L.zs, tk = L.tk;
-  float* s_c = reinterpret_cast<float*>(smb + L.off_c);    // [nz][cs]
-  float* s_g = reinterpret_cast<float*>(smb + L.off_g);    // [nz][cs]
-  float* s_b0 = reinterpret_cast<float*>(smb + L.off_b0);  // [zs][NB]
-  float* s_bf = reinterpret_cast<float*>(smb + L.off_bf);  // [zs][NB]
-  float* s_x = reinterpret_cast<float*>(smb + L.off_x);    // [zs][NB]
-  // zero everything once: Q rows beyond nt, M rows beyond nt / absent members stay 0
-  for (int i = tid * 16; i < L.total; i += BT_THREADS * 16)
-    *reinterpret_cast<uint4*>(smb + i) = make_uint4(0u, 0u, 0u, 0u);
+// e4m3 pair (round to nearest, saturating) and its value.
+__device__ __forceinline__ unsigned short e4m3x2(float a, float b, float2& back) {
+  const __nv_fp8x2_storage_t q = __nv_cvt_float2_to_fp8x2(make_float2(a, b), __NV_SATFINITE, __NV_E4M3);
+  const __half2_raw hr = __nv_cvt_fp8x2_to_halfraw2(q, __NV_E4M3);
+  back = __half22float2(*reinterpret_cast<const __half2*>(&hr));
+  return (unsigned short)q;
+}
+
+// FP8 three-term split of 16 values already divided by their scale
+// (|v| <= 448): v ~ q0 + q1/16 + q2/256.
+__device__ __forceinline__ void split16_e4m3(const float (&v)[16], uint4& t0, uint4& t1, uint4& t2) {
+  unsigned w0[4], w1[4], w2[4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    unsigned a0 = 0, a1 = 0, a2 = 0;
+#pragma unroll
+    for (int j = 0; j < 2; ++j) {
+      const float x = v[4 * i + 2 * j], y = v[4 * i + 2 * j + 1];
+      float2 b0, b1, b2;
+      const unsigned short q0 = e4m3x2(x, y, b0);
+      const float rx = x - b0.x, ry = y - b0.y;
+      const unsigned short q1 = e4m3x2(16.f * rx, 16.f * ry, b1);
+      const unsigned short q2 = e4m3x2(256.f * (rx - b1.x * 0.0625f), 256.f * (ry - b1.y * 0.0625f), b2);
+      a0 |= (unsigned)q0 << (16 * j);
+      a1 |= (unsigned)q1 << (16 * j);
+      a2 |= (unsigned)q2 << (16 * j);
+    }
+    w0[i] = a0;
+    w1[i] = a1;
+    w2[i] = a2;
+  }
+  t0 = make_uint4(w0[0], w0[1], w0[2], w0[3]);
+  t1 = make_uint4(w1[0], w1[1], w1[2], w1[3]);
+  t2 = make_uint4(w2[0], w2[1], w2[2], w2[3]);
+}
+
+__device__ __forceinline__ void cp_async16z(void* smem, const void* gmem, int bytes) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(umma::smem_u32(smem)), "l"(gmem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8z(void* smem, const void* gmem, int bytes) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8, %2;\n" ::"r"(umma::smem_u32(smem)), "l"(gmem), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+__device__ __forceinline__ int pick(const int (&mem)[4], int m) {
+  return m == 0 ? mem[0] : (m == 1 ? mem[1] : (m == 2 ? mem[2] : mem[3]));
+}
+
+// Raw copies of one t chunk: 64 (volume, member) rows of TCH complex m_hat
+// values and TCH rows of W_hat (zero fill beyond nt, absent members, v >= nv).
+__device__ __forceinline__ void issue_raw(const BtPlan& P, unsigned char* raw, const int (&mem)[4], int v0, int nv,
+                                          int t0, const float* __restrict__ wc, const float2* __restrict__ m_hat,
+                                          int ldm) {
+  const int nt = P.nt;
+  if ((nt & 1) == 0) {  // volume rows start on 16-byte boundaries: two complex values per copy
+    for (int i = threadIdx.x; i < 4 * VB * (TCH / 2); i += BT_THREADS) {
+      const int vm = i / (TCH / 2), p = i - vm * (TCH / 2);
+      const int v = vm >> 2, f = pick(mem, vm & 3), t = t0 + 2 * p;
+      const int bytes = (f < 0 || v >= nv) ? 0 : (t + 2 <= nt ? 16 : (t < nt ? 8 : 0));
+      const float2* src = bytes ? m_hat + (size_t)f * ldm + (size_t)(v0 + v) * nt + t : m_hat;
+      cp_async16z(raw + vm * RCS + p * 16, src, bytes);
+    }
+  } else {  // odd nt: rows of odd volumes start 8 bytes off, one complex value per copy
+    for (int i = threadIdx.x; i < 4 * VB * TCH; i += BT_THREADS) {
+      const int vm = i / TCH, p = i - vm * TCH;
+      const int v = vm >> 2, f = pick(mem, vm & 3), t = t0 + p;
+      const int bytes = (f < 0 || v >= nv || t >= nt) ? 0 : 8;
+      const float2* src = bytes ? m_hat + (size_t)f * ldm + (size_t)(v0 + v) * nt + t : m_hat;
+      cp_async8z(raw + vm * RCS + p * 8, src, bytes);
+    }
+  }
+  unsigned char* rw = raw + P.raw_c;
+  const int q4 = P.z4 >> 2;
+  for (int i = threadIdx.x; i < TCH * q4; i += BT_THREADS) {
+    const int tl = i / q4, k4 = i - tl * q4, t = t0 + tl;
+    const int bytes = t < nt ? 16 : 0;
+    cp_async16z(rw + i * 16, bytes ? wc + (size_t)t * P.z4 + 4 * k4 : wc, bytes);
+  }
+}
+
+// Split the raw chunk into its terms: A = m rows (n = 8 v + 2 member + re/im,
+// K = t), B = W^T rows (z, K = t).  s_n: per right-hand-side scales (FP8).
+__device__ __forceinline__ void convert_chunk(const BtPlan& P, const unsigned char* raw, unsigned char* set,
+                                              const float* s_n, float inv_sw) {
+  const int epc = P.epc;
+  unsigned char* a = set;                       // nterm A terms
+  unsigned char* b = set + P.nterm * P.a_term;  // nterm B terms
+  // A: item = (row n, group g of epc t values); consecutive threads on consecutive rows
+  const int groups = TCH / epc;
+  for (int i = threadIdx.x; i < NR * groups; i += BT_THREADS) {
+    const int n = i & (NR - 1), gI = i >> 7;
+    const float* row = reinterpret_cast<const float*>(raw + (n >> 1) * RCS) + 2 * gI * epc + (n & 1);
+    const uint32_t o = kchunk(NR, n, gI * epc, epc);
+    if (P.fp8) {
+      const float sc = 1.f / s_n[n];
+      float v[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) v[e] = row[2 * e] * sc;
+      uint4 t0, t1, t2;
+      split16_e4m3(v, t0, t1, t2);
+      *reinterpret_cast<uint4*>(a + o) = t0;
+      *reinterpret_cast<uint4*>(a + P.a_term + o) = t1;
+      *reinterpret_cast<uint4*>(a + 2 * P.a_term + o) = t2;
+    } else {
+      float v[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) v[e] = row[2 * e];
+      uint4 hi, lo;
+      split8_bf16(v, hi, lo);
+      *reinterpret_cast<uint4*>(a + o) = hi;
+      *reinterpret_cast<uint4*>(a + P.a_term + o) = lo;
+    }
+  }
+  // B: item = (4 z, group of epc t), read as epc float4 rows and transposed in registers
+  const unsigned char* rw = raw + P.raw_c;
+  const int q4 = P.z4 >> 2;
+  for (int i = threadIdx.x; i < q4 * groups; i += BT_THREADS) {
+    const int k4 = i % q4, gI = i / q4;
+    if (P.fp8) {
+      float w[4][16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const float4 x = *reinterpret_cast<const float4*>(rw + ((gI * 16 + e) * q4 + k4) * 16);
+        w[0][e] = x.x * inv_sw;
+        w[1][e] = x.y * inv_sw;
+        w[2][e] = x.z * inv_sw;
+        w[3][e] = x.w * inv_sw;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        uint4 t0, t1, t2;
+        split16_e4m3(w[r], t0, t1, t2);
+        const uint32_t o = kchunk(P.zn, 4 * k4 + r, gI * 16, 16);
+        *reinterpret_cast<uint4*>(b + o) = t0;
+        *reinterpret_cast<uint4*>(b + P.b_term + o) = t1;
+        *reinterpret_cast<uint4*>(b + 2 * P.b_term + o) = t2;
+      }
+    } else {
+      float w[4][8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const float4 x = *reinterpret_cast<const float4*>(rw + ((gI * 8 + e) * q4 + k4) * 16);
+        w[0][e] = x.x;
+        w[1][e] = x.y;
+        w[2][e] = x.z;
+        w[3][e] = x.w;
+      }
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        uint4 hi, lo;
+        split8_bf16(w[r], hi, lo);
+        const uint32_t o = kchunk(P.zn, 4 * k4 + r, gI * 8, 8);
+        *reinterpret_cast<uint4*>(b + o) = hi;
+        *reinterpret_cast<uint4*>(b + P.b_term + o) = lo;
+      }
+    }
+  }
+}
+
+// Bounded wait on an MMA-completion mbarrier (block-wide: true = some thread
+// gave up; then every thread has drained and the CTA must stop).
+__device__ __forceinline__ bool wait_bar(uint64_t* bar, uint32_t& phase, int* flag, long long max_polls) {
+  int gave_up = 0;
+  if (!umma::mbar_wait(bar, phase, max_polls)) {
+    gave_up = 1;
+    atomicExch(flag, 1);
+    umma::mbar_wait(bar, phase, DRAIN_POLLS);
+  }
+  phase ^= 1u;
+  umma::fence_after_sync();
+  return __syncthreads_or(gave_up) != 0;
+}
+
+__device__ __forceinline__ void publish() {
+  umma::fence_proxy_async();
+  umma::fence_before_sync();
   __syncthreads();
-  const int mtiles = zs >> 4, ksteps = tk >> 4;
-  const int chunks_q = zs >> 3;
-  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
+  umma::fence_after_sync();
+}
+
+// Three TF32 products D (+)= X_lo T_hi + X_hi T_lo + X_hi T_hi of the solve:
+// X = [128][zn] (A, K = w), T = table rows z (B, K = w).
+__device__ __forceinline__ void issue_solve3(uint32_t d, uint32_t xh, uint32_t xl, uint32_t th, uint32_t tl, int zn) {
+  const uint32_t idesc = umma::idesc_tf32(NR, zn);
+  for (int s = 0; s < zn / 8; ++s) {
+    const uint32_t oa = s * 2 * NR * 16, ob = s * 2 * zn * 16;
+    const uint64_t ah = umma::desc(xh + oa, NR * 16, 128), al = umma::desc(xl + oa, NR * 16, 128);
+    const uint64_t bh = umma::desc(th + ob, zn * 16, 128), bl = umma::desc(tl + ob, zn * 16, 128);
+    umma::mma_tf32(d, al, bh, idesc, s > 0);
+    umma::mma_tf32(d, ah, bl, idesc, 1);
+    umma::mma_tf32(d, ah, bh, idesc, 1);
+  }
+}
+
+// Row n of the solve operand X (K = w): TF32 hi / lo of 16 values at w = 16 j.
+__device__ __forceinline__ void put_x16(unsigned char* xh, unsigned char* xl, int n, int j, const float (&v)[16]) {
+#pragma unroll
+  for (int qd = 0; qd < 4; ++qd) {
+    float4 h, l;
+    umma::split_tf32(v[4 * qd + 0], h.x, l.x);
+    umma::split_tf32(v[4 * qd + 1], h.y, l.y);
+    umma::split_tf32(v[4 * qd + 2], h.z, l.z);
+    umma::split_tf32(v[4 * qd + 3], h.w, l.w);
+    const uint32_t o = kchunk(NR, n, 16 * j + 4 * qd, 4);
+    *reinterpret_cast<float4*>(xh + o) = h;
+    *reinterpret_cast<float4*>(xl + o) = l;
+  }
+}
+
+__global__ void __launch_bounds__(BT_THREADS, 1) k_batch_tikhonov_tc(
+    BtPlan P, const float* __restrict__ what, const unsigned char* __restrict__ tabs,
+    const float* __restrict__ class_scale, const int* __restrict__ members, int nclass,
+    const float2* __restrict__ m_hat, int ldm, float2* __restrict__ x_hat, int ldx, int refine, int* flag,
+    long long max_polls) {
+  extern __shared__ __align__(1024) unsigned char sm[];
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nt = P.nt, nz = P.nz, zn = P.zn;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(sm + P.off_bar);  // [0], [1]: term sets; [2]: solve
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(sm + P.off_bar + 32);
+  float* s_n = reinterpret_cast<float*>(sm + P.off_sn);
+  for (int i = tid; i < P.off_bar / 16; i += BT_THREADS)
+    reinterpret_cast<uint4*>(sm)[i] = make_uint4(0u, 0u, 0u, 0u);
+  for (int i = tid; i < NR; i += BT_THREADS) s_n[i] = 1.f;
+  __syncthreads();
+  if (warp == 0) umma::tmem_alloc(tslot, 256);
+  if (tid == 0) {
+    umma::mbar_init(bars + 0, 1);
+    umma::mbar_init(bars + 1, 1);
+    umma::mbar_init(bars + 2, 1);
+  }
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t taddr = *tslot;
+  uint32_t ph[3] = {0u, 0u, 0u};
+  int pend[2] = {0, 0};  // commits on the term-set barriers not yet waited for
+  const uint32_t sbase = umma::smem_u32(sm);
+  const uint32_t col_acc0 = 0, col_acc1 = zn, col_acc2 = 2 * zn, col_work = 3 * zn;
+  const uint32_t idesc_main = P.fp8 ? idesc_e4m3(NR, zn) : idesc_bf16(NR, zn);
+  const int nchunks = (nt + TCH - 1) / TCH;
+  const int nvc = (P.batch + VB - 1) / VB;
+  // epilogue mapping: TMEM lane = right-hand side n, warps w and w + 4 take alternate 16-column groups
+  const int q = warp & 3, half = warp >> 2, n = 32 * q + lane;
+  const uint32_t trow = taddr + ((uint32_t)(32 * q) << 16);
+  unsigned char* xh = sm + P.off_xh;
+  unsigned char* xl = sm + P.off_xl;
+  // solve tables in shared memory: C hi, C lo, G' hi, G' lo
+  const uint32_t t_ch = sbase + P.off_tab, t_cl = t_ch + zn * zn * 4, t_gh = t_cl + zn * zn * 4,
+                 t_gl = t_gh + zn * zn * 4;
+  bool stop = false;
+  for (int c = blockIdx.x; c < nclass && !stop; c += gridDim.x) {
     int mem[4];
 #pragma unroll
-    for (int m = 0; m < 4; ++m) mem[m] = members[c * 4 + m];
-    // ---- class tables: Q_hi, Q_lo (swizzled rows), C, G + lambda I ----
+    for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
+    const float* wc = what + (size_t)c * nt * P.z4;
+    const float sw = P.fp8 ? __ldg(class_scale + c) : 1.f;
+    const float inv_sw = 1.f / sw;
+    // the class's solve tables (previous readers, the solve MMAs, have completed)
     {
-      const __nv_bfloat16* qh = qhi + (size_t)c * nt * zs;
-      const __nv_bfloat16* ql = qlo + (size_t)c * nt * zs;
-      for (int i = tid; i < nt * chunks_q; i += BT_THREADS) {
-        const int t = i / chunks_q, ch = i - t * chunks_q;
-        cp_async16(smb + L.off_qh + q_off(L, t, ch), qh + (size_t)t * zs + ch * 8);
-        cp_async16(smb + L.off_ql + q_off(L, t, ch), ql + (size_t)t * zs + ch * 8);
-      }
-      const int cq = L.z4 >> 2;
-      for (int i = tid; i < nz * cq; i += BT_THREADS) {
-        const int r = i / cq, ch = i - r * cq;
-        cp_async16(s_c + r * L.cs + ch * 4, cinv + ((size_t)c * nz + r) * L.z4 + ch * 4);
-        cp_async16(s_g + r * L.cs + ch * 4, glam + ((size_t)c * nz + r) * L.z4 + ch * 4);
-      }
-      cp_async_commit();
-      cp_async_wait_all();
+      const uint4* src = reinterpret_cast<const uint4*>(tabs + (size_t)c * P.tab_bytes);
+      for (int i = tid; i < P.tab_bytes / 16; i += BT_THREADS) cp_async16z(sm + P.off_tab + 16 * i, src + i, 16);
+      cp_commit();
     }
-    __syncthreads();
-    for (int b0 = 0; b0 < L.batch; b0 += BC) {
-      // ---- right-hand sides of this chunk, split into BF16 hi/lo, rows n = (m*BC + bl)*2 + comp ----
-      {
-        const int tch = tk >> 3;  // 8-sample chunks along t
-        for (int i = tid; i < 4 * BC * tch; i += BT_THREADS) {
-          const int ch = i % tch, mb = i / tch, bl = mb % BC, m = mb / BC;
-          const int b = b0 + bl;
-          const int n = (m * BC + bl) * 2;
-          uint4 rh, rl, ih, il;
-          unsigned* prh = reinterpret_cast<unsigned*>(&rh);
-          unsigned* prl = reinterpret_cast<unsigned*>(&rl);
-          unsigned* pih = reinterpret_cast<unsigned*>(&ih);
-          unsigned* pil = reinterpret_cast<unsigned*>(&il);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            float2 v0 = make_float2(0.f, 0.f), v1 = make_float2(0.f, 0.f);
-            const int t = ch * 8 + 2 * j;
-            if (mem[m] >= 0 && b < L.batch) {
-              const float2* src = m_hat + (size_t)mem[m] * ldm + (size_t)b * nt;
-              if (t < nt) v0 = src[t];
-              if (t + 1 < nt) v1 = src[t + 1];
-            }
-            const __nv_bfloat16 h0 = __float2bfloat16_rn(v0.x), h1 = __float2bfloat16_rn(v1.x);
-            const __nv_bfloat16 l0 = __float2bfloat16_rn(v0.x - __bfloat162float(h0));
-            const __nv_bfloat16 l1 = __float2bfloat16_rn(v1.x - __bfloat162float(h1));
-            const __nv_bfloat16 g0 = __float2bfloat16_rn(v0.y), g1 = __float2bfloat16_rn(v1.y);
-            const __nv_bfloat16 k0 = __float2bfloat16_rn(v0.y - __bfloat162float(g0));
-            const __nv_bfloat16 k1 = __float2bfloat16_rn(v1.y - __bfloat162float(g1));
-            __nv_bfloat162 p;
-            p.x = h0; p.y = h1; prh[j] = *reinterpret_cast<unsigned*>(&p);
-            p.x = l0; p.y = l1; prl[j] = *reinterpret_cast<unsigned*>(&p);
-            p.x = g0; p.y = g1; pih[j] = *reinterpret_cast<unsigned*>(&p);
-            p.x = k0; p.y = k1; pil[j] = *reinterpret_cast<unsigned*>(&p);
+    for (int vc = 0; vc < nvc && !stop; ++vc) {
+      const int v0 = vc * VB, nv = P.batch - v0 < VB ? P.batch - v0 : VB;
+      if (P.fp8) {
+        // per right-hand-side scale: the largest magnitude over t maps to 448
+        const int vm = tid >> 2, part = tid & 3, v = vm >> 2, f = pick(mem, vm & 3);
+        float mr = 0.f, mi = 0.f;
+        if (f >= 0 && v < nv) {
+          const float2* src = m_hat + (size_t)f * ldm + (size_t)(v0 + v) * nt;
+          for (int t = part; t < nt; t += 4) {
+            const float2 x = __ldg(src + t);
+            mr = fmaxf(mr, fabsf(x.x));
+            mi = fmaxf(mi, fabsf(x.y));
           }
-          *reinterpret_cast<uint4*>(smb + L.off_mh + m_off(L, n, ch)) = rh;
-          *reinterpret_cast<uint4*>(smb + L.off_ml + m_off(L, n, ch)) = rl;
-          *reinterpret_cast<uint4*>(smb + L.off_mh + m_off(L, n + 1, ch)) = ih;
-          *reinterpret_cast<uint4*>(smb + L.off_ml + m_off(L, n + 1, ch)) = il;
         }
-      }
-      __syncthreads();
-      // ---- b0 = Q_hi^T M_hi,  b = b0 + Q_hi^T M_lo + Q_lo^T M_hi ----
-      for (int pair = warp; pair < mtiles * (NB / 8); pair += BT_WARPS) {
-        const int mt = pair % mtiles, ntile = pair / mtiles;
-        const int z0 = mt * 16, n0 = ntile * 8;
-        float acc_h[4] = {0.f, 0.f, 0.f, 0.f}, acc_x[4] = {0.f, 0.f, 0.f, 0.f};
-        const int jm = lane >> 3, r8 = lane & 7;
-        for (int ks = 0; ks < ksteps; ++ks) {
-          const int k0 = ks * 16;
-          // A = Q^T tile (z0.., k0..): matrix jm = (t block jm>>1, z block jm&1)
-          const int tq = k0 + ((jm >> 1) << 3) + r8;
-          const int zc = (z0 >> 3) + (jm & 1);
-          unsigned ah[4], al[4];
-          ldsm_x4_trans(ah, smb + L.off_qh + q_off(L, tq, zc));
-          ldsm_x4_trans(al, smb + L.off_ql + q_off(L, tq, zc));
-          // B = M tile (k0.., n0..): matrix (lane>>3)&1 = t block, row = n
-          const int nr = n0 + r8;
-          const int tcn = (k0 >> 3) + ((lane >> 3) & 1);
-          unsigned bh[2], bl[2];
-          ldsm_x2(bh, smb + L.off_mh + m_off(L, nr, tcn));
-          ldsm_x2(bl, smb + L.off_ml + m_off(L, nr, tcn));
-          mma_bf16(acc_h, ah, bh);
-          mma_bf16(acc_x, ah, bl);
-          mma_bf16(acc_x, al, bh);
-        }
-        const int zr = z0 + g, nc = n0 + 2 * tg;
-        s_b0[zr * NB + nc] = acc_h[0];
-        s_b0[zr * NB + nc + 1] = acc_h[1];
-        s_b0[(zr + 8) * NB + nc] = acc_h[2];
-        s_b0[(zr + 8) * NB + nc + 1] = acc_h[3];
-        s_bf[zr * NB + nc] = acc_h[0] + acc_x[0];
-        s_bf[zr * NB + nc + 1] = acc_h[1] + acc_x[1];
-        s_bf[(zr + 8) * NB + nc] = acc_h[2] + acc_x[2];
-        s_bf[(zr + 8) * NB + nc + 1] = acc_h[3] + acc_x[3];
-      }
-      __syncthreads();
-      // ---- x0 = C b0, then x += C (b - (G + lambda I) x) ----
-      // Each thread owns one depth z and four right-hand sides: four independent
-      // accumulators per row walk, rows of C and G at a pitch that puts the
-      // eight depths of a warp on distinct banks.
-      const int zq = tid >> 2, nq = (tid & 3) * 4;
-      const bool own = zq < nz && tid < 4 * nz;
-      if (own) {
-        const float4 y = small_mv(s_c + zq * L.cs, s_b0, nz, nq);
-        *reinterpret_cast<float4*>(s_x + zq * NB + nq) = y;
-      }
-      __syncthreads();
-      for (int it = 0; it < refine; ++it) {
-        if (own) {  // residual r = b - (G + lambda I) x into s_b0
-          const float4 gx = small_mv(s_g + zq * L.cs, s_x, nz, nq);
-          const float4 bf = *reinterpret_cast<const float4*>(s_bf + zq * NB + nq);
-          *reinterpret_cast<float4*>(s_b0 + zq * NB + nq) =
-              make_float4(bf.x - gx.x, bf.y - gx.y, bf.z - gx.z, bf.w - gx.w);
-        }
-        __syncthreads();
-        if (own) {  // x += C r (each thread updates only its own entries)
-          const float4 cr = small_mv(s_c + zq * L.cs, s_b0, nz, nq);
-          float4* xp = reinterpret_cast<float4*>(s_x + zq * NB + nq);
-          const float4 x = *xp;
-          *xp = make_float4(x.x + cr.x, x.y + cr.y, x.z + cr.z, x.w + cr.w);
+        mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, 1));
+        mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, 2));
+        mi = fmaxf(mi, __shfl_xor_sync(0xffffffffu, mi, 1));
+        mi = fmaxf(mi, __shfl_xor_sync(0xffffffffu, mi, 2));
+        if (part == 0) {
+          s_n[2 * vm] = mr > 0.f ? mr / E4M3_MAX : 1.f;
+          s_n[2 * vm + 1] = mi > 0.f ? mi / E4M3_MAX : 1.f;
         }
         __syncthreads();
       }
-      // ---- x_hat[f][b*nz + z] ----
-      for (int i = tid; i < 4 * BC * nz; i += BT_THREADS) {
-        const int z = i % nz, mb = i / nz, bl = mb % BC, m = mb / BC;
-        const int b = b0 + bl;
-        if (mem[m] < 0 || b >= L.batch) continue;
-        const int n = (m * BC + bl) * 2;
-        x_hat[(size_t)mem[m] * ldx + (size_t)b * nz + z] = make_float2(s_x[z * NB + n], s_x[z * NB + n + 1]);
+      issue_raw(P, sm + P.off_raw, mem, v0, nv, 0, wc, m_hat, ldm);
+      cp_commit();
+      for (int kc = 0; kc < nchunks; ++kc) {
+        if (kc + 1 < nchunks)
+          issue_raw(P, sm + P.off_raw + ((kc + 1) & 1) * P.raw_stage, mem, v0, nv, (kc + 1) * TCH, wc, m_hat, ldm);
+        cp_commit();
+        cp_wait1();
+        __syncthreads();
+        const int set = kc & 1;
+        if (pend[set]) {  // the MMAs that last read this term set
+          if (wait_bar(bars + set, ph[set], flag, max_polls)) {
+            stop = true;
+            break;
+          }
+          pend[set] = 0;
+        }
+        unsigned char* sb = sm + P.off_set + set * P.set_bytes;
+        convert_chunk(P, sm + P.off_raw + (kc & 1) * P.raw_stage, sb, s_n, inv_sw);
+        publish();
+        if (tid == 0) {
+          const uint32_t a0 = sbase + P.off_set + set * P.set_bytes;
+          const uint32_t b0 = a0 + P.nterm * P.a_term;
+          const int ksteps = TCH * P.esize / 32;  // K steps of 32 bytes per row
+          for (int s = 0; s < ksteps; ++s) {
+            const uint32_t oa = s * 2 * NR * 16, ob = s * 2 * zn * 16;
+            uint64_t A[3], B[3];
+            for (int i = 0; i < P.nterm; ++i) {
+              A[i] = umma::desc(a0 + i * P.a_term + oa, NR * 16, 128);
+              B[i] = umma::desc(b0 + i * P.b_term + ob, zn * 16, 128);
+            }
+            const uint32_t first = (kc > 0 || s > 0) ? 1u : 0u;
+            if (P.fp8) {
+              mma_e4m3(taddr + col_acc0, A[0], B[0], idesc_main, first);
+              mma_e4m3(taddr + col_acc1, A[0], B[1], idesc_main, first);
+              mma_e4m3(taddr + col_acc1, A[1], B[0], idesc_main, 1);
+              mma_e4m3(taddr + col_acc2, A[0], B[2], idesc_main, first);
+              mma_e4m3(taddr + col_acc2, A[1], B[1], idesc_main, 1);
+              mma_e4m3(taddr + col_acc2, A[2], B[0], idesc_main, 1);
+            } else {
+              mma_bf16(taddr + col_acc0, A[0], B[0], idesc_main, first);
+              mma_bf16(taddr + col_acc1, A[0], B[1], idesc_main, first);
+              mma_bf16(taddr + col_acc1, A[1], B[0], idesc_main, 1);
+            }
+          }
+          umma::commit(bars + set);
+        }
+        pend[set] = 1;
       }
+      if (stop) break;
+      // all products of this chunk of volumes: wait for both term sets' last commits
+      for (int s = 0; s < 2 && !stop; ++s) {
+        if (pend[s]) {
+          if (wait_bar(bars + s, ph[s], flag, max_polls)) stop = true;
+          pend[s] = 0;
+        }
+      }
+      if (stop) break;
+      cp_wait0();  // the class tables
+      __syncthreads();
+      // ---- solve: x0 = C b0, then `refine` steps x += C (b - G' x) ----
+      const float sn = s_n[n] * sw;
+      float x[2][16];
+      // b0 -> X
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        const int j = half + 2 * jj;
+        if (16 * j < zn) {
+          float v[16];
+          umma::tmem_ld16(trow + col_acc0 + 16 * j, v);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) v[e] *= P.fp8 ? sn : 1.f;
+          put_x16(xh, xl, n, j, v);
+        }
+      }
+      publish();
+      if (tid == 0) {
+        issue_solve3(taddr + col_work, sbase + P.off_xh, sbase + P.off_xl, t_ch, t_cl, zn);
+        umma::commit(bars + 2);
+      }
+      if (wait_bar(bars + 2, ph[2], flag, max_polls)) {
+        stop = true;
+        break;
+      }
+#pragma unroll
+      for (int jj = 0; jj < 2; ++jj) {
+        const int j = half + 2 * jj;
+        if (16 * j < zn) umma::tmem_ld16(trow + col_work + 16 * j, x[jj]);
+      }
+      for (int it = 0; it < refine && !stop; ++it) {
+        // r = b - G' x
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int j = half + 2 * jj;
+          if (16 * j < zn) put_x16(xh, xl, n, j, x[jj]);
+        }
+        publish();
+        if (tid == 0) {
+          issue_solve3(taddr + col_work, sbase + P.off_xh, sbase + P.off_xl, t_gh, t_gl, zn);
+          umma::commit(bars + 2);
+        }
+        if (wait_bar(bars + 2, ph[2], flag, max_polls)) {
+          stop = true;
+          break;
+        }
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int j = half + 2 * jj;
+          if (16 * j < zn) {
+            float gx[16], d0[16], d1[16], d2[16];
+            umma::tmem_ld16(trow + col_work + 16 * j, gx);
+            umma::tmem_ld16(trow + col_acc0 + 16 * j, d0);
+            umma::tmem_ld16(trow + col_acc1 + 16 * j, d1);
+            if (P.fp8) umma::tmem_ld16(trow + col_acc2 + 16 * j, d2);
+            float r[16];
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const float b = P.fp8 ? sn * (d0[e] + 0.0625f * d1[e] + 0.00390625f * d2[e]) : d0[e] + d1[e];
+              r[e] = b - gx[e];
+            }
+            put_x16(xh, xl, n, j, r);
+          }
+        }
+        // x += C r
+        publish();
+        if (tid == 0) {
+          issue_solve3(taddr + col_work, sbase + P.off_xh, sbase + P.off_xl, t_ch, t_cl, zn);
+          umma::commit(bars + 2);
+        }
+        if (wait_bar(bars + 2, ph[2], flag, max_polls)) {
+          stop = true;
+          break;
+        }
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int j = half + 2 * jj;
+          if (16 * j < zn) {
+            float cr[16];
+            umma::tmem_ld16(trow + col_work + 16 * j, cr);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) x[jj][e] += cr[e];
+          }
+        }
+      }
+      if (stop) break;
+      // x_hat[f][v * nz + z]: right-hand side n = 8 v + 2 member + re/im; even lanes write (re, im)
+      {
+        const int v = n >> 3, fm = pick(mem, (n >> 1) & 3);
+        const bool writer = (lane & 1) == 0 && v < nv && fm >= 0;
+        float2* dst = x_hat + (size_t)(fm >= 0 ? fm : 0) * ldx + (size_t)(v0 + (v < nv ? v : 0)) * nz;
+#pragma unroll
+        for (int jj = 0; jj < 2; ++jj) {
+          const int j = half + 2 * jj;
+          if (16 * j < zn) {
+#pragma unroll
+            for (int e = 0; e < 16; ++e) {
+              const float im = __shfl_down_sync(0xffffffffu, x[jj][e], 1);
+              const int z = 16 * j + e;
+              if (writer && z < nz) dst[z] = make_float2(x[jj][e], im);
+            }
+          }
+        }
+      }
+      // TMEM reads of this epilogue before the next chunk's MMAs overwrite the accumulators
+      umma::fence_before_sync();
       __syncthreads();
     }
   }
+  if (stop) {  // no MMA may still write TMEM when it is freed
+    if (tid == 0) umma::commit(bars + 2);
+    umma::mbar_wait(bars + 2, ph[2], DRAIN_POLLS);
+  }
+  cp_wait0();
+  umma::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) umma::tmem_dealloc(taddr, 256);
 }
 
-// Q_hi / Q_lo tables from the FP32 W_hat ([c][t][z4] -> [c][t][zs], zero padded).
-__global__ void k_split_bf16(const float* __restrict__ what, long long rows, int nz, int z4, int zs,
-                             __nv_bfloat16* __restrict__ qhi, __nv_bfloat16* __restrict__ qlo) {
-  const long long n = rows * zs;
-  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const long long r = i / zs;
-    const int z = (int)(i - r * zs);
-    const float v = z < nz ? what[r * z4 + z] : 0.f;
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    qhi[i] = h;
-    qlo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+// Per-class FP8 scale of W_hat: max |W| / 448.
+__global__ void k_class_absmax(const float* __restrict__ what, int per_class, int nclass, float* __restrict__ out) {
+  __shared__ float red[32];
+  for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
+    float m = 0.f;
+    const float* w = what + (size_t)c * per_class;
+    for (int i = threadIdx.x; i < per_class; i += blockDim.x) m = fmaxf(m, fabsf(w[i]));
+    for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      m = threadIdx.x < (int)(blockDim.x >> 5) ? red[threadIdx.x] : 0.f;
+      for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (threadIdx.x == 0) out[c] = m > 0.f ? m / E4M3_MAX : 1.f;
+    }
+    __syncthreads();
   }
 }
 
 // C = (G + lambda I)^-1 (FP64 Cholesky -> FP32) and G + lambda I (FP32), rows padded to z4.
 __global__ void __launch_bounds__(128) k_factor_tik(const double* __restrict__ gram, int nz, double lambda,
                                                     float* __restrict__ cinv, float* __restrict__ glam) {
-  extern __shared__ double sm[];
+  extern __shared__ double smd[];
   const int ld = nz + 1;
-  double* s_a = sm;
-  double* s_l = sm + nz * ld;
+  double* s_a = smd;
+  double* s_l = smd + nz * ld;
   const int c = blockIdx.x;
   const int z4 = (nz + 3) & ~3;
   const double* g = gram + (size_t)c * nz * nz;
@@ -319,86 +700,87 @@ __global__ void __launch_bounds__(128) k_factor_tik(const double* __restrict__ g
   }
 }
 
-BtLayout make_layout(int nt, int nz, int batch) {
-  BtLayout L;
-  L.nt = nt;
-  L.nz = nz;
-  L.z4 = (nz + 3) & ~3;
-  L.zs = nz <= 16 ? 16 : (nz <= 32 ? 32 : 64);
-  L.tk = (nt + 15) & ~15;
-  L.cs = 4 * ((L.z4 / 4) | 1);
-  L.batch = batch;
-  int off = 0;
-  auto take = [&](int bytes) {
-    const int at = off;
-    off += (bytes + 127) & ~127;
-    return at;
-  };
-  L.off_qh = take(L.tk * L.zs * 2);
-  L.off_ql = take(L.tk * L.zs * 2);
-  L.off_mh = take(NB * L.tk * 2);
-  L.off_ml = take(NB * L.tk * 2);
-  L.off_c = take(nz * L.cs * 4);
-  L.off_g = take(nz * L.cs * 4);
-  L.off_b0 = take(L.zs * NB * 4);
-  L.off_bf = take(L.zs * NB * 4);
-  L.off_x = take(L.zs * NB * 4);
-  L.total = off;
-  return L;
+// Solve tables per class: C and G + lambda I as TF32 hi / lo in the canonical
+// K-major layout of a B operand with zn rows (z) and K = w (both symmetric).
+__global__ void k_solve_tables(const float* __restrict__ cinv, const float* __restrict__ glam, int nz, int z4, int zn,
+                               int nclass, unsigned char* __restrict__ tabs) {
+  const int per = zn * zn;
+  const size_t total = (size_t)nclass * per;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total; i += (size_t)gridDim.x * blockDim.x) {
+    const size_t c = i / per;
+    const int rem = (int)(i - c * per), z = rem / zn, w = rem - z * zn;
+    float vc = 0.f, vg = 0.f;
+    if (z < nz && w < nz) {
+      vc = cinv[(c * nz + z) * z4 + w];
+      vg = glam[(c * nz + z) * z4 + w];
+    }
+    float ch, cl, gh, gl;
+    umma::split_tf32(vc, ch, cl);
+    umma::split_tf32(vg, gh, gl);
+    const size_t o = (size_t)(((w >> 2) * zn + z) * 16 + (w & 3) * 4);
+    unsigned char* t = tabs + c * (size_t)(4 * per * 4);
+    *reinterpret_cast<float*>(t + o) = ch;
+    *reinterpret_cast<float*>(t + per * 4 + o) = cl;
+    *reinterpret_cast<float*>(t + 2 * per * 4 + o) = gh;
+    *reinterpret_cast<float*>(t + 3 * per * 4 + o) = gl;
+  }
 }
 
 }  // namespace
 
-size_t batch_tikhonov_smem_bytes(int nt, int nz) { return (size_t)make_layout(nt, nz, 1).total; }
+size_t batch_tikhonov_smem_bytes(int nt, int nz) {
+  const BtPlan a = make_plan(nt, nz, 0, 1), b = make_plan(nt, nz, 1, 1);
+  return (size_t)(a.total > b.total ? a.total : b.total);
+}
 
-// Build (once per handle) the BF16 tables and (per lambda) C and G + lambda I.
+// Build (once per handle) the per-class FP8 scales and (per lambda) C, G + lambda I
+// and their BF16 solve tables.
 ctof_status batch_tikhonov_prepare(ctof_kernel_s* k, double lambda, cudaStream_t st) {
-  const int zs = k->nz <= 16 ? 16 : (k->nz <= 32 ? 32 : 64);
-  if (!k->d_qhi) {
-    const size_t n = (size_t)k->nclass * k->nt * zs;
-    void* p = nullptr;
-    if (cudaMalloc(&p, 2 * n * sizeof(__nv_bfloat16)) != cudaSuccess) {
-      cudaGetLastError();
-      return CTOF_ENOMEM;
-    }
-    k->d_qhi = p;
-    k->d_qlo = static_cast<__nv_bfloat16*>(p) + n;
-    k_split_bf16<<<152 * 8, 256, 0, st>>>(k->d_what, (long long)k->nclass * k->nt, k->nz, k->z4, zs,
-                                          static_cast<__nv_bfloat16*>(k->d_qhi),
-                                          static_cast<__nv_bfloat16*>(k->d_qlo));
-    CTOF_CUDA_TRY(cudaGetLastError());
-  }
+  const int zn = rup(k->nz, 16);
   if (!k->d_bt_cinv) {
+    // one allocation, each part starting on a 256-byte boundary (the tables are
+    // read with 16-byte asynchronous copies)
+    auto al = [](size_t b) { return (b + 255) & ~(size_t)255; };
+    const size_t fl = al((size_t)k->nclass * k->nz * k->z4 * sizeof(float));
+    const size_t sw = al((size_t)k->nclass * sizeof(float));
+    const size_t tab = (size_t)k->nclass * 4 * zn * zn * 4;
     void* p = nullptr;
-    if (cudaMalloc(&p, 2 * (size_t)k->nclass * k->nz * k->z4 * sizeof(float)) != cudaSuccess) {
+    if (cudaMalloc(&p, 2 * fl + sw + tab) != cudaSuccess) {
       cudaGetLastError();
       return CTOF_ENOMEM;
     }
-    k->d_bt_cinv = static_cast<float*>(p);
-    k->d_bt_glam = k->d_bt_cinv + (size_t)k->nclass * k->nz * k->z4;
+    unsigned char* b = static_cast<unsigned char*>(p);
+    k->d_bt_cinv = reinterpret_cast<float*>(b);
+    k->d_bt_glam = reinterpret_cast<float*>(b + fl);
+    k->d_bt_sw = reinterpret_cast<float*>(b + 2 * fl);
+    k->d_bt_tab = b + 2 * fl + sw;
     k->bt_lambda = -1.0;
+    k_class_absmax<<<152 * 4, 256, 0, st>>>(k->d_what, k->nt * k->z4, k->nclass, k->d_bt_sw);
+    CTOF_CUDA_TRY(cudaGetLastError());
   }
   if (k->bt_lambda != lambda) {
     const size_t fsm = (size_t)2 * k->nz * (k->nz + 1) * sizeof(double);
     CTOF_CUDA_TRY(cudaFuncSetAttribute(k_factor_tik, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)fsm));
     k_factor_tik<<<k->nclass, 128, fsm, st>>>(k->d_gram, k->nz, lambda, k->d_bt_cinv, k->d_bt_glam);
     CTOF_CUDA_TRY(cudaGetLastError());
+    k_solve_tables<<<152 * 8, 256, 0, st>>>(k->d_bt_cinv, k->d_bt_glam, k->nz, k->z4, zn, k->nclass, k->d_bt_tab);
+    CTOF_CUDA_TRY(cudaGetLastError());
     k->bt_lambda = lambda;
   }
   return CTOF_OK;
 }
 
-ctof_status batch_tikhonov_contract(const ctof_kernel_s* k, int batch, const float2* m_hat, int ldm, float2* x_hat,
-                                    int ldx, int refine, cudaStream_t st) {
-  const BtLayout L = make_layout(k->nt, k->nz, batch);
-  if ((size_t)L.total > 227 * 1024) return CTOF_EUNSUPPORTED;
-  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_batch_tikhonov_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, L.total));
+ctof_status batch_tikhonov_contract(const ctof_kernel_s* k, int precision, int batch, const float2* m_hat, int ldm,
+                                    float2* x_hat, int ldx, int refine, cudaStream_t st) {
+  const BtPlan P = make_plan(k->nt, k->nz, precision == CTOF_FP8E4M3 ? 1 : 0, batch);
+  if (P.total > 227 * 1024) return CTOF_EUNSUPPORTED;
+  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_batch_tikhonov_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, P.total));
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
   const int grid = k->nclass < nsm ? k->nclass : nsm;
-  k_batch_tikhonov_bf16<<<grid, BT_THREADS, L.total, st>>>(
-      L, static_cast<const __nv_bfloat16*>(k->d_qhi), static_cast<const __nv_bfloat16*>(k->d_qlo), k->d_bt_cinv,
-      k->d_bt_glam, k->d_members, k->nclass, m_hat, ldm, x_hat, ldx, refine);
+  k_batch_tikhonov_tc<<<grid, BT_THREADS, P.total, st>>>(P, k->d_what, k->d_bt_tab, k->d_bt_sw, k->d_members,
+                                                          k->nclass, m_hat, ldm, x_hat, ldx, refine, k->d_flags,
+                                                          k->max_polls);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }

@@ -579,7 +579,6 @@ void ctof_kernel_destroy(ctof_kernel k) {
   batch_graph_forget(k);
   if (k->graph) cudaGraphExecDestroy(k->graph);
   destroy_events(k);
-  if (k->d_qhi) cudaFree(k->d_qhi);
   if (k->d_bt_cinv) cudaFree(k->d_bt_cinv);
   if (k->d_batch) cudaFree(k->d_batch);
   for (int i = 0; i < 2; ++i)
@@ -893,8 +892,7 @@ ctof_status ctof_reconstruct_batch_tikhonov(ctof_kernel k, int batch, const floa
   if (!k || !d_m || !d_mu || batch < 1 || batch > 4096) return CTOF_EINVAL;
   if (refine_steps < 0 || refine_steps > 8 || !finite_pos(lambda_rel)) return CTOF_EINVAL;
   if (precision != CTOF_FP32 && precision != CTOF_BF16 && precision != CTOF_FP8E4M3) return CTOF_EINVAL;
-  if (precision == CTOF_FP8E4M3) return CTOF_EUNSUPPORTED;
-  if (precision == CTOF_BF16 && batch_tikhonov_smem_bytes(k->nt, k->nz) > 227 * 1024) return CTOF_EUNSUPPORTED;
+  if (precision != CTOF_FP32 && batch_tikhonov_smem_bytes(k->nt, k->nz) > 227 * 1024) return CTOF_EUNSUPPORTED;
   DeviceGuard g(k->device);
   if (!g.ok) return CTOF_ECUDA;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -936,7 +934,7 @@ ctof_status ctof_reconstruct_batch_tikhonov(ctof_kernel k, int batch, const floa
   float2* inter = reinterpret_cast<float2*>(base + ((b_sm + 255) & ~(size_t)255) + ((b_sx + 255) & ~(size_t)255));
   CTOF_TRY(fft_forward_planes(k, d_m, batch * k->nt, k->n, k->n, k->n, inter, spec_m, ldm, st));
   CTOF_TRY(batch_tikhonov_prepare(k, lambda, st));
-  CTOF_TRY(batch_tikhonov_contract(k, batch, spec_m, ldm, spec_x, ldx, refine_steps, st));
+  CTOF_TRY(batch_tikhonov_contract(k, precision, batch, spec_m, ldm, spec_x, ldx, refine_steps, st));
   return fft_inverse_planes(k, spec_x, ldx, batch * k->nz, k->n, k->n, inter, d_mu, k->n, st);
 }
 

@@ -86,10 +86,10 @@ struct ctof_kernel_s {
   cudaEvent_t* events;
 
   // precision form (batched Tikhonov): BF16 split tables, FP32 factors, batch workspace
-  void* d_qhi;         // [nclass][nt][zs] bf16 (zs = 16/32/64)
-  void* d_qlo;         // same, the BF16 remainder
-  float* d_bt_cinv;    // [nclass][nz][z4] (G + lambda I)^-1
+  float* d_bt_cinv;    // [nclass][nz][z4] (G + lambda I)^-1 (one allocation holds the four below)
   float* d_bt_glam;    // [nclass][nz][z4] G + lambda I
+  float* d_bt_sw;      // [nclass] FP8 scale of W_hat (max |W_hat| / 448)
+  unsigned char* d_bt_tab;  // [nclass] C hi, C lo, G + lambda I hi, lo: BF16 [zn x zn] K-major tiles
   double bt_lambda;
   void* d_batch;       // batch spectra + row intermediates (one allocation)
   size_t batch_bytes;
@@ -201,7 +201,7 @@ ctof_status contract_admm_prepare(ctof_kernel_s* k, cudaStream_t st);
 // ---- batch_tikhonov.cu ----------------------------------------------------
 size_t batch_tikhonov_smem_bytes(int nt, int nz);
 ctof_status batch_tikhonov_prepare(ctof_kernel_s* k, double lambda, cudaStream_t st);
-ctof_status batch_tikhonov_contract(const ctof_kernel_s* k, int batch, const float2* m_hat, int ldm,
+ctof_status batch_tikhonov_contract(const ctof_kernel_s* k, int precision, int batch, const float2* m_hat, int ldm,
                                     float2* x_hat, int ldx, int refine, cudaStream_t st);
 
 // ---- build.cu ----------------------------------------------------------

@@ -16,6 +16,10 @@ Fixtures:
   the frequency-class block of the 128 x 128 x 48 x 256 workload (48
   depths x 256 bins per class) on a smaller lateral field.  Phantom: 1-8
   ellipsoids/tubes (seed 3), Poisson noise at peak 1e5 (seed 103).
+* ``tikhonov_n32_z64_t512.npz``: per-frequency Tikhonov (lambda 1e-3 max Gram
+  diagonal) at 64 depths x 512 bins on a 32 x 32 scan (P = 64, all 2112
+  frequencies), the class block of the 256 x 256 x 64 x 512 precision-form
+  workload; two sphere phantoms, Poisson peak 1e4.
 """
 
 import os
@@ -67,7 +71,32 @@ def admm_n32_z48_t256():
                         want=want, beta=info["beta"], scale=info["scale"])
 
 
-FIXTURES = {"admm_n32_z48_t256": admm_n32_z48_t256}
+def tikhonov_n32_z64_t512():
+    """Precision-form class shape: 64 depths x 512 bins (the 256 x 256 x 64 x 512
+    workload's frequency-class block) on a 32 x 32 scan at 0.5 mm (P = 64: all
+    2112 half-plane frequencies solved exactly by the FP64 oracle).  Two
+    measurement volumes (2 spheres each, seeds 0 and 1; Poisson peak 1e4, seeds
+    100 and 101); lambda = 1e-3 max Gram diagonal.  Counts stored as int16."""
+    kw = dict(n=32, nz=64, nt=512, dx=0.5, dz=0.5, z_first=0.5, dt=25.0)
+    g = _grid(kw)
+    wh = op.kernel_spectrum(op.kernel_offsets(g, _medium(kw)), g)
+    counts, units, wants = [], [], []
+    lam = None
+    for i in range(2):
+        mu = synth.phantom_spheres(g.n, g.nz, g.dx, g.dz, g.z_first, seed=i)
+        c, unit = _noisy_counts(wh, g, mu, 1e4, 100 + i)
+        assert c.max() < 32767
+        want, lam, _ = so.tikhonov(wh, c.astype(np.float64) * unit, g)
+        counts.append(c.astype(np.int16))
+        units.append(unit)
+        wants.append(want.astype(np.float32))
+    np.savez_compressed(os.path.join(HERE, "tikhonov_n32_z64_t512.npz"), counts=np.stack(counts),
+                        unit=np.array(units), grid=np.array([kw["n"], kw["nz"], kw["nt"]]),
+                        pitch=np.array([kw["dx"], kw["dz"], kw["z_first"], kw["dt"]]), lam=lam,
+                        want=np.stack(wants))
+
+
+FIXTURES = {"admm_n32_z48_t256": admm_n32_z48_t256, "tikhonov_n32_z64_t512": tikhonov_n32_z64_t512}
 
 if __name__ == "__main__":
     for name in sys.argv[1:] or list(FIXTURES):
