@@ -62,9 +62,62 @@ __device__ __forceinline__ float2 tw_conj(float2 w) {
   return INV ? make_float2(w.x, -w.y) : w;
 }
 
+// 4- and 8-point DFTs in registers, natural order in and out (w = exp(-2 pi i / n),
+// conjugated when INV).
+template <bool INV>
+__device__ __forceinline__ float2 mul_mi(float2 a) {  // a * (-i), or a * (+i) when INV
+  return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
+  const float2 s02 = cadd(x0, x2), d02 = csub(x0, x2), s13 = cadd(x1, x3), d13 = mul_mi<INV>(csub(x1, x3));
+  x0 = cadd(s02, s13);
+  x2 = csub(s02, s13);
+  x1 = cadd(d02, d13);
+  x3 = csub(d02, d13);
+}
+
+template <bool INV>
+__device__ __forceinline__ void dft8(float2 (&x)[8]) {
+  float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6], o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+  dft4<INV>(e0, e1, e2, e3);
+  dft4<INV>(o0, o1, o2, o3);
+  const float h = 0.70710678118654752f;
+  // w8 o1, w8^2 o2, w8^3 o3 with w8 = (1 - i)/sqrt(2) (conjugated when INV)
+  const float2 t1 = INV ? make_float2(h * (o1.x - o1.y), h * (o1.x + o1.y))
+                        : make_float2(h * (o1.x + o1.y), h * (o1.y - o1.x));
+  const float2 t2 = mul_mi<INV>(o2);
+  const float2 t3 = INV ? make_float2(-h * (o3.x + o3.y), h * (o3.x - o3.y))
+                        : make_float2(h * (o3.y - o3.x), -h * (o3.x + o3.y));
+  x[0] = cadd(e0, o0);
+  x[4] = csub(e0, o0);
+  x[1] = cadd(e1, t1);
+  x[5] = csub(e1, t1);
+  x[2] = cadd(e2, t2);
+  x[6] = csub(e2, t2);
+  x[3] = cadd(e3, t3);
+  x[7] = csub(e3, t3);
+}
+
+// Scratch slots of the 32-point step for P >= 256 (each a permutation of
+// [0, P)): S[i][l] (register i, lane l) and S2[i][m1][b]; the rotations keep a
+// half-warp's 8-byte accesses on distinct banks (at most 2-way conflicts).
+__device__ __forceinline__ int slot_a(int i, int l) { return i * 32 + ((l + 8 * (i & 1)) & 31); }
+__device__ __forceinline__ int slot_c(int i, int m1, int b) {
+  const int t = 4 * i + m1;
+  return t * 8 + (b ^ (t & 7));
+}
+
 // Length-P DFT held by one warp (see file comment).  INV selects exp(+...).
-template <int P, bool INV>
-__device__ __forceinline__ void warp_fft(float2 (&v)[P / 32], int lane, const float2* tw) {
+// With SCRATCH and P >= 256 (the column passes, whose warps own a tile column
+// to use as scratch) the 32-point DFT across the lanes runs as 4 x 8 points in
+// registers, with two passes through the scratch (P slots `stride` float2
+// apart), instead of five shuffle stages (measured ~10 % faster there; the
+// row passes keep the shuffles, which measured faster for them):
+//   Z[m1 + 4 m2] = sum_b w8^(b m2) w32^(b m1) sum_a y[b + 8 a] w4^(a m1).
+template <int P, bool INV, bool SCRATCH = true>
+__device__ __forceinline__ void warp_fft(float2 (&v)[P / 32], int lane, const float2* tw, float2* scr, int stride) {
   constexpr int R = P / 32;
 #pragma unroll
   for (int s = R / 2; s >= 1; s >>= 1) {
@@ -82,25 +135,68 @@ __device__ __forceinline__ void warp_fft(float2 (&v)[P / 32], int lane, const fl
     const int k2 = bitrevc(i, ilog2c(R));
     v[i] = cmul(v[i], tw_conj<INV>(tw[P + 31 + 32 * (k2 - 1) + lane]));
   }
+  if constexpr (SCRATCH && R >= 8) {
+    __syncwarp();  // every lane has read its inputs (callers may pass their input column as scratch)
 #pragma unroll
-  for (int s = 16; s >= 1; s >>= 1) {
-    const bool upper = (lane & s) != 0;
-    const float2 w = tw_conj<INV>(tw[P + s - 1 + (lane & (s - 1))]);
+    for (int i = 0; i < R; ++i) scr[slot_a(i, lane) * stride] = v[i];
+    __syncwarp();
+    const int b = lane & 7;
+    float2 t[R / 4][4];
 #pragma unroll
-    for (int i = 0; i < R; ++i) {
-      float2 o;
-      o.x = __shfl_xor_sync(0xffffffffu, v[i].x, s);
-      o.y = __shfl_xor_sync(0xffffffffu, v[i].y, s);
-      v[i] = upper ? cmul(csub(o, v[i]), w) : cadd(v[i], o);
+    for (int q = 0; q < R / 4; ++q) {
+      const int i = (lane >> 3) + 4 * q;
+#pragma unroll
+      for (int a = 0; a < 4; ++a) t[q][a] = scr[slot_a(i, b + 8 * a) * stride];
+    }
+    __syncwarp();
+#pragma unroll
+    for (int q = 0; q < R / 4; ++q) {
+      const int i = (lane >> 3) + 4 * q;
+      dft4<INV>(t[q][0], t[q][1], t[q][2], t[q][3]);
+#pragma unroll
+      for (int m1 = 1; m1 < 4; ++m1) t[q][m1] = cmul(t[q][m1], tw_get<P, INV>(tw, R * b * m1));
+#pragma unroll
+      for (int m1 = 0; m1 < 4; ++m1) scr[slot_c(i, m1, b) * stride] = t[q][m1];
+    }
+    __syncwarp();
+    const int m1 = lane & 3;
+#pragma unroll
+    for (int q = 0; q < R / 8; ++q) {
+      const int i = (lane >> 2) + 8 * q;
+      float2 u[8];
+#pragma unroll
+      for (int bb = 0; bb < 8; ++bb) u[bb] = scr[slot_c(i, m1, bb) * stride];
+      dft8<INV>(u);
+#pragma unroll
+      for (int m2 = 0; m2 < 8; ++m2) v[8 * q + m2] = u[m2];
+    }
+    __syncwarp();
+  } else {
+#pragma unroll
+    for (int s = 16; s >= 1; s >>= 1) {
+      const bool upper = (lane & s) != 0;
+      const float2 w = tw_conj<INV>(tw[P + s - 1 + (lane & (s - 1))]);
+#pragma unroll
+      for (int i = 0; i < R; ++i) {
+        float2 o;
+        o.x = __shfl_xor_sync(0xffffffffu, v[i].x, s);
+        o.y = __shfl_xor_sync(0xffffffffu, v[i].y, s);
+        v[i] = upper ? cmul(csub(o, v[i]), w) : cadd(v[i], o);
+      }
     }
   }
 }
 
-// Output position of register i of lane `lane` after warp_fft.
-template <int P>
+// Output position of register i of lane `lane` after warp_fft<P, INV, SCRATCH>.
+template <int P, bool SCRATCH = true>
 __device__ __forceinline__ int out_pos(int lane, int i) {
   constexpr int R = P / 32;
-  return R * brev5(lane) + bitrevc(i, ilog2c(R));
+  if constexpr (SCRATCH && R >= 8) {
+    // register 8 q + m2 of lane L: k1 = bitrev_R((L >> 2) + 8 q), k2 = (L & 3) + 4 m2
+    return bitrevc((lane >> 2) + 8 * (i >> 3), ilog2c(R)) + R * ((lane & 3) + 4 * (i & 7));
+  } else {
+    return R * brev5(lane) + bitrevc(i, ilog2c(R));
+  }
 }
 
 // Shared-memory slot of transform element e.  A warp writes its R registers
@@ -217,9 +313,9 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_fwd(const float* __rest
       const float b = (p1 < nplanes && n < cols_in) ? r1[n] : 0.f;
       v[i] = make_float2(a, b);
     }
-    warp_fft<P, false>(v, lane, s_tw);
+    warp_fft<P, false, false>(v, lane, s_tw, buf, 1);
 #pragma unroll
-    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
+    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P, false>(lane, i))] = v[i];
     __syncwarp();
     split_to_tile<P>(buf, lane, s_h, 2 * warp);
     __syncthreads();
@@ -249,9 +345,9 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const float2* __res
     __syncthreads();
     float2 v[R];
     load_pair_from_tile<P>(v, s_h, 2 * warp, lane);
-    warp_fft<P, true>(v, lane, s_tw);
+    warp_fft<P, true, false>(v, lane, s_tw, buf, 1);
 #pragma unroll
-    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
+    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P, false>(lane, i))] = v[i];
     __syncwarp();
     for (int c = lane; c < cols_out; c += 32) {
       const float2 z = buf[sw_pos<P>(c)];
@@ -291,9 +387,9 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restri
     __syncthreads();
     float2 v[R];
     load_pair_from_tile<P>(v, s_h, 2 * warp, lane);
-    warp_fft<P, true>(v, lane, s_tw);
+    warp_fft<P, true, false>(v, lane, s_tw, buf, 1);
 #pragma unroll
-    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
+    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P, false>(lane, i))] = v[i];
     __syncwarp();
 #pragma unroll
     for (int i = 0; i < R; ++i) {
@@ -319,9 +415,9 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restri
       v[i] = cc;
     }
     __syncwarp();
-    warp_fft<P, false>(v, lane, s_tw);
+    warp_fft<P, false, false>(v, lane, s_tw, buf, 1);
 #pragma unroll
-    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P>(lane, i))] = v[i];
+    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P, false>(lane, i))] = v[i];
     __syncwarp();
     __syncthreads();  // every warp is done reading s_h
     split_to_tile<P>(buf, lane, s_h, 2 * warp);
@@ -364,7 +460,7 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restri
       const int y = lane + 32 * i;
       v[i] = y < rows_in ? tile[y * LDT + c] : make_float2(0.f, 0.f);
     }
-    warp_fft<P, false>(v, lane, s_tw);
+    warp_fft<P, false>(v, lane, s_tw, tile + c, LDT);
 #pragma unroll
     for (int i = 0; i < R; ++i) tile[sw_pos<P>(out_pos<P>(lane, i)) * LDT + c] = v[i];
   }
@@ -404,7 +500,8 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restri
     float2 v[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) v[i] = tile[(lane + 32 * i) * LDT + c];
-    warp_fft<P, true>(v, lane, s_tw);
+    __syncwarp();
+    warp_fft<P, true>(v, lane, s_tw, tile + c, LDT);
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int y = out_pos<P>(lane, i);
