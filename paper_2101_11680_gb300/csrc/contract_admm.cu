@@ -51,6 +51,9 @@
 //   forward part: one warp per 16-row tile of t.
 #include <cuda_runtime.h>
 
+#include <algorithm>
+#include <vector>
+
 #include "ctof_internal.h"
 
 namespace {
@@ -509,95 +512,75 @@ __device__ __forceinline__ void mma_split_a_2acc(float (&dh)[4], float (&dl)[4],
   mma_tf32(dh, ah, bh0, bh1);
 }
 
-// KZ = forward K steps = ceil(nz / 8); MZ = 16-row z tiles = ceil(nz / 16).
-template <int KZ>
-__global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
-    PipePlan P, const float* __restrict__ what_o, const float* __restrict__ hinv_o, const float* __restrict__ lap,
-    const int* __restrict__ members, int nclass, const float2* c_hat, int ldt, const float2* s_hat, float2* x_hat,
-    int ldz, float2* __restrict__ kx_hat, float inv_s, int* status_flag, long long max_polls) {
-  constexpr int MZ = (KZ + 1) / 2;
-  extern __shared__ __align__(128) float4 sm_pipe[];
-  unsigned char* sm = reinterpret_cast<unsigned char*>(sm_pipe);
+// One problem of the pipelined x-update: its stage layout, tables and spectra.
+struct PipeProb {
+  PipePlan P;
+  const float* what_o;   // W_hat in the block layout [nclass][tm/8][zm/8][64]
+  const float* hinv_o;   // H^-1 in the block layout [nclass][zm/8][zm/8][64]
+  const float* lap;      // [nclass]
+  const int* members;    // [nclass][4]
+  int nclass;
+  const float2* c_hat;   // [nf][ldt]
+  const float2* s_hat;   // [nf][ldz]
+  float2* x_hat;         // [nf][ldz] in / out
+  float2* kx_hat;        // [nf][ldt] out
+  int ldt, ldz;
+  float inv_s;
+  int item0;             // first work-queue item of this problem
+};
+
+// Producer: class c of problem q into stage `st` (header, then the bulk copies
+// completing on `full`).
+__device__ __forceinline__ void produce_item(const PipeProb& q, int c, unsigned char* st, uint64_t* full) {
+  const PipePlan& P = q.P;
+  int f[4];
+  unsigned bytes = P.w_bytes + P.h_bytes;
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    f[m] = __ldg(q.members + 4 * c + m);
+    if (f[m] >= 0) bytes += P.c_bytes + 2 * P.v_bytes;
+  }
+  // the class header (members + 1, diagonal of L) for the consumers; the
+  // arrive below releases these stores to them.  Header words stay small
+  // non-negative integers or finite floats: in the many-problem kernel one
+  // problem's header may sit inside another's operand padding, which is then
+  // multiplied by zero.
+  int* hdr = reinterpret_cast<int*>(st + P.o_hdr);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) hdr[m] = f[m] + 1;
+  reinterpret_cast<float*>(hdr)[4] = __ldg(q.lap + c) + 1.0f;
+  mbar_expect_tx(full, bytes);
+  bulk_g2s(st + P.o_w, q.what_o + (size_t)c * P.tm * P.zm, P.w_bytes, full);
+  bulk_g2s(st + P.o_h, q.hinv_o + (size_t)c * P.zm * P.zm, P.h_bytes, full);
+#pragma unroll
+  for (int m = 0; m < 4; ++m) {
+    if (f[m] < 0) continue;
+    bulk_g2s(st + P.o_c + m * P.cs * 4, q.c_hat + (size_t)f[m] * q.ldt, P.c_bytes, full);
+    bulk_g2s(st + P.o_s + m * P.sz * 4, q.s_hat + (size_t)f[m] * q.ldz, P.v_bytes, full);
+    bulk_g2s(st + P.o_x + m * P.sz * 4, q.x_hat + (size_t)f[m] * q.ldz, P.v_bytes, full);
+  }
+}
+
+// Scratch of the consumers (per CTA, sized for ZMX padded depths).
+struct PipeScratch {
+  float* part;     // [warp][ZM][8] adjoint partial sums
+  unsigned* bh;    // [ZM][8] b, TF32 hi / raw lo
+  unsigned* bl;
+  unsigned* xh;    // [ZM][8] x_new, TF32 hi / raw lo
+  unsigned* xl;
+};
+
+// Consumers (8 warps): the x-update of the class in stage `st`.  KZC > 0 fixes
+// the forward K steps at compile time; KZC = 0 takes them from the problem
+// (at most 8), with the same operations in the same order.  `gave_up` is this
+// thread's full-barrier timeout; returns true when the CTA must stop.
+template <int KZC>
+__device__ __forceinline__ bool consume_item(const PipeProb& q, const unsigned char* st, const PipeScratch& scr,
+                                             int gave_up) {
+  constexpr int KZM = KZC > 0 ? KZC : 8;
+  constexpr int MZM = (KZM + 1) / 2;
+  const PipePlan& P = q.P;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int S = P.stages;
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + P.o_bar);
-  uint64_t* empty = full + S;
-  volatile int* s_abort = reinterpret_cast<volatile int*>(empty + S);
-  // zero everything below the barriers: padding rows/columns of the operand
-  // blocks and absent members' rows then read as finite zeros
-  for (int i = tid; i < P.o_bar / 16; i += PIPE_THREADS)
-    reinterpret_cast<float4*>(sm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
-  if (tid == 0) {
-    for (int s = 0; s < S; ++s) {
-      mbar_init(full + s, 1);
-      mbar_init(empty + s, PIPE_CONS_WARPS);
-    }
-    *s_abort = 0;
-    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-  }
-  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // zeroes before the bulk copies
-  __syncthreads();
-  const int mine = (int)blockIdx.x < nclass ? (nclass - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
-
-  if (warp == PIPE_CONS_WARPS) {
-    // ---------------- producer ----------------
-    if (lane != 0) return;
-    int issued = 0;
-    for (; issued < mine; ++issued) {
-      const int s = issued % S;
-      const uint32_t par = ((issued / S) & 1) ^ 1;  // a fresh barrier counts its parity-1 phase as done
-      bool ok = false;
-      for (long long i = 0; i < max_polls; ++i) {
-        if (mbar_try(empty + s, par)) {
-          ok = true;
-          break;
-        }
-        if (*s_abort) break;
-      }
-      if (!ok) {
-        if (!*s_abort) {
-          atomicExch(status_flag, 1);
-          *s_abort = 1;
-        }
-        break;
-      }
-      const int c = (int)blockIdx.x + issued * (int)gridDim.x;
-      unsigned char* st = sm + s * P.stage_bytes;
-      int f[4];
-      unsigned bytes = P.w_bytes + P.h_bytes;
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        f[m] = __ldg(members + 4 * c + m);
-        if (f[m] >= 0) bytes += P.c_bytes + 2 * P.v_bytes;
-      }
-      // the class header (members, diagonal of L) for the consumers; the
-      // arrive below releases these stores to them
-      int* hdr = reinterpret_cast<int*>(st + P.o_hdr);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) hdr[m] = f[m];
-      reinterpret_cast<float*>(hdr)[4] = __ldg(lap + c) + 1.0f;
-      mbar_expect_tx(full + s, bytes);
-      bulk_g2s(st + P.o_w, what_o + (size_t)c * P.tm * P.zm, P.w_bytes, full + s);
-      bulk_g2s(st + P.o_h, hinv_o + (size_t)c * P.zm * P.zm, P.h_bytes, full + s);
-#pragma unroll
-      for (int m = 0; m < 4; ++m) {
-        if (f[m] < 0) continue;
-        bulk_g2s(st + P.o_c + m * P.cs * 4, c_hat + (size_t)f[m] * ldt, P.c_bytes, full + s);
-        bulk_g2s(st + P.o_s + m * P.sz * 4, s_hat + (size_t)f[m] * ldz, P.v_bytes, full + s);
-        bulk_g2s(st + P.o_x + m * P.sz * 4, x_hat + (size_t)f[m] * ldz, P.v_bytes, full + s);
-      }
-    }
-    // no copy may be in flight when the CTA exits: wait for each stage's last fill
-    for (int s = 0; s < S; ++s) {
-      if (issued > s) {
-        const int last = s + ((issued - 1 - s) / S) * S;
-        mbar_wait_bounded(full + s, (uint32_t)((last / S) & 1), PIPE_DRAIN_POLLS);
-      }
-    }
-    return;
-  }
-
-  // ---------------- consumers ----------------
   const int g = lane >> 2, tg = lane & 3;
   const int hg = g >> 2;
   // word offsets of this lane's fragment elements inside an 8 x 8 block
@@ -606,129 +589,129 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
   const int offA0 = 32 * hg + 4 * ((tg + 4 * hg) & 7) + (g & 3);      // (row tg, column g)
   const int offA2 = 32 * hg + 4 * ((tg + 4 + 4 * hg) & 7) + (g & 3);  // (row tg + 4, column g)
   const int nt = P.nt, nz = P.nz;
-  constexpr int ZB = 2 * MZ, ZM = 16 * MZ;  // z blocks of 8, padded depth
+  const int KZ = KZC > 0 ? KZC : (nz + 7) >> 3;
+  const int MZ = (KZ + 1) >> 1, ZB = 2 * MZ, ZM = 16 * MZ;
   const int kt = (nt + 7) >> 3, mtt = P.tm >> 4;
-  float* part = reinterpret_cast<float*>(sm + P.o_part);      // [warp][ZM][8]
-  unsigned* s_bh = reinterpret_cast<unsigned*>(sm + P.o_bh);  // [ZM][8] b, TF32 hi / raw lo
-  unsigned* s_bl = reinterpret_cast<unsigned*>(sm + P.o_bl);
-  unsigned* s_xh = reinterpret_cast<unsigned*>(sm + P.o_xh);  // [ZM][8] x_new, TF32 hi / raw lo
-  unsigned* s_xl = reinterpret_cast<unsigned*>(sm + P.o_xl);
-  for (int k = 0; k < mine; ++k) {
-    const int s = k % S;
-    int gave_up = 0;
-    if (!mbar_wait_bounded(full + s, (uint32_t)((k / S) & 1), max_polls)) {
-      gave_up = 1;
-      atomicExch(status_flag, 1);
-    }
-    const unsigned char* st = sm + s * P.stage_bytes;
-    const float* W = reinterpret_cast<const float*>(st + P.o_w);
-    const float* H = reinterpret_cast<const float*>(st + P.o_h);
-    const float* C = reinterpret_cast<const float*>(st + P.o_c);
-    const float* SV = reinterpret_cast<const float*>(st + P.o_s);
-    const float* XV = reinterpret_cast<const float*>(st + P.o_x);
-    const int* hdr = reinterpret_cast<const int*>(st + P.o_hdr);
+  const float inv_s = q.inv_s;
+  const float* W = reinterpret_cast<const float*>(st + P.o_w);
+  const float* H = reinterpret_cast<const float*>(st + P.o_h);
+  const float* C = reinterpret_cast<const float*>(st + P.o_c);
+  const float* SV = reinterpret_cast<const float*>(st + P.o_s);
+  const float* XV = reinterpret_cast<const float*>(st + P.o_x);
+  const int* hdr = reinterpret_cast<const int*>(st + P.o_hdr);
 
-    // ---- A: adjoint partial sums y_w[z][r] = sum over this warp's t of W[t][z] c[t][r] ----
-    {
-      float acc[MZ][4];
+  // ---- A: adjoint partial sums y_w[z][r] = sum over this warp's t of W[t][z] c[t][r] ----
+  {
+    float acc[MZM][4];
 #pragma unroll
-      for (int mt = 0; mt < MZ; ++mt)
+    for (int mt = 0; mt < MZM; ++mt)
 #pragma unroll
-        for (int i = 0; i < 4; ++i) acc[mt][i] = 0.f;
-      const float* cr = C + (g >> 1) * P.cs + 2 * tg + (g & 1) + 16 * warp;  // t = 8 ks + tg
-      const float* wa0 = W + warp * ZB * 64 + offA0;
-      const float* wa2 = W + warp * ZB * 64 + offA2;
+      for (int i = 0; i < 4; ++i) acc[mt][i] = 0.f;
+    const float* cr = C + (g >> 1) * P.cs + 2 * tg + (g & 1) + 16 * warp;  // t = 8 ks + tg
+    const float* wa0 = W + warp * ZB * 64 + offA0;
+    const float* wa2 = W + warp * ZB * 64 + offA2;
 #pragma unroll 2
-      for (int ks = warp; ks < kt; ks += PIPE_CONS_WARPS) {
-        unsigned bh0, bl0, bh1, bl1;
-        split_fast(cr[0], bh0, bl0);
-        split_fast(cr[8], bh1, bl1);
+    for (int ks = warp; ks < kt; ks += PIPE_CONS_WARPS) {
+      unsigned bh0, bl0, bh1, bl1;
+      split_fast(cr[0], bh0, bl0);
+      split_fast(cr[8], bh1, bl1);
 #pragma unroll
-        for (int mt = 0; mt < MZ; ++mt) {
+      for (int mt = 0; mt < MZM; ++mt) {
+        if (mt < MZ) {
           const float a[4] = {wa0[128 * mt], wa0[128 * mt + 64], wa2[128 * mt], wa2[128 * mt + 64]};
           mma_split_a(acc[mt], a, bh0, bh1, bl0, bl1);
         }
-        cr += 16 * PIPE_CONS_WARPS;
-        wa0 += PIPE_CONS_WARPS * ZB * 64;
-        wa2 += PIPE_CONS_WARPS * ZB * 64;
       }
+      cr += 16 * PIPE_CONS_WARPS;
+      wa0 += PIPE_CONS_WARPS * ZB * 64;
+      wa2 += PIPE_CONS_WARPS * ZB * 64;
+    }
 #pragma unroll
-      for (int mt = 0; mt < MZ; ++mt) {
-        float* p = part + (warp * ZM + 16 * mt + g) * 8 + 2 * tg;
+    for (int mt = 0; mt < MZM; ++mt) {
+      if (mt < MZ) {
+        float* p = scr.part + (warp * ZM + 16 * mt + g) * 8 + 2 * tg;
         *reinterpret_cast<float2*>(p) = make_float2(acc[mt][0], acc[mt][1]);
         *reinterpret_cast<float2*>(p + 64) = make_float2(acc[mt][2], acc[mt][3]);
       }
     }
-    if (cons_sync_or(gave_up)) {
-      if (tid == 0) *s_abort = 1;
-      break;
-    }
-    // ---- B: b = y / s + s_hat - L x_prev, split for the H^-1 MMA ----
-    {
-      const float dl = reinterpret_cast<const float*>(hdr)[4];
-      for (int i = tid; i < nz * 8; i += PIPE_CONS_THREADS) {
-        const int z = i >> 3, r = i & 7, m = r >> 1, cp = r & 1;
-        float y = 0.f;
+  }
+  if (cons_sync_or(gave_up)) return true;
+  // ---- B: b = y / s + s_hat - L x_prev, split for the H^-1 MMA ----
+  {
+    const float dl = reinterpret_cast<const float*>(hdr)[4];
+    for (int i = tid; i < nz * 8; i += PIPE_CONS_THREADS) {
+      const int z = i >> 3, r = i & 7, m = r >> 1, cp = r & 1;
+      float y = 0.f;
 #pragma unroll
-        for (int w = 0; w < PIPE_CONS_WARPS; ++w) y += part[w * ZM * 8 + i];
-        const float* xm = XV + m * P.sz + cp + 2 * z;
-        const float xz = xm[0];
-        float lx = dl * xz;
-        if (z > 0) lx += xz - xm[-2];
-        if (z < nz - 1) lx -= xm[2] - xz;
-        unsigned h, l;
-        split_fast(y * inv_s + SV[m * P.sz + 2 * z + cp] - lx, h, l);
-        s_bh[i] = h;
-        s_bl[i] = l;
-      }
+      for (int w = 0; w < PIPE_CONS_WARPS; ++w) y += scr.part[w * ZM * 8 + i];
+      const float* xm = XV + m * P.sz + cp + 2 * z;
+      const float xz = xm[0];
+      float lx = dl * xz;
+      if (z > 0) lx += xz - xm[-2];
+      if (z < nz - 1) lx -= xm[2] - xz;
+      unsigned h, l;
+      split_fast(y * inv_s + SV[m * P.sz + 2 * z + cp] - lx, h, l);
+      scr.bh[i] = h;
+      scr.bl[i] = l;
     }
-    cons_sync();
-    const int mem_tg = hdr[tg];  // this lane's output member (D columns 2 tg, 2 tg + 1)
-    // ---- C: x_new = x_prev + H^-1 b; one warp per 16-row z tile ----
-    if (warp < MZ) {
-      float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
-      const float* h0 = H + 2 * warp * ZB * 64;  // block (z / 8 = 2 warp, w / 8 = 0)
+    // rows z in [nz, ZM) of b stay zero (this problem's padding)
+    for (int i = nz * 8 + tid; i < ZM * 8; i += PIPE_CONS_THREADS) {
+      scr.bh[i] = 0u;
+      scr.bl[i] = 0u;
+    }
+  }
+  cons_sync();
+  const int mem_tg = hdr[tg] - 1;  // this lane's output member (D columns 2 tg, 2 tg + 1)
+  // ---- C: x_new = x_prev + H^-1 b; one warp per 16-row z tile ----
+  if (warp < MZ) {
+    float ah[4] = {0.f, 0.f, 0.f, 0.f}, al[4] = {0.f, 0.f, 0.f, 0.f};
+    const float* h0 = H + 2 * warp * ZB * 64;  // block (z / 8 = 2 warp, w / 8 = 0)
 #pragma unroll
-      for (int ks = 0; ks < ZB; ++ks) {
+    for (int ks = 0; ks < 2 * MZM; ++ks) {
+      if (ks < ZB) {
         const float* hb = h0 + ks * 64;
         const float a[4] = {hb[offF0], hb[ZB * 64 + offF0], hb[offF2], hb[ZB * 64 + offF2]};
         const int b0 = (8 * ks + tg) * 8 + g, b1 = b0 + 32;
-        mma_split_a_2acc(ah, al, a, s_bh[b0], s_bh[b1], s_bl[b0], s_bl[b1]);
-      }
-#pragma unroll
-      for (int hf = 0; hf < 2; ++hf) {
-        const int z = 16 * warp + g + 8 * hf;
-        const float2 xp = z < nz ? *reinterpret_cast<const float2*>(XV + tg * P.sz + 2 * z) : make_float2(0.f, 0.f);
-        const float2 xn = make_float2(xp.x + (ah[2 * hf] + al[2 * hf]), xp.y + (ah[2 * hf + 1] + al[2 * hf + 1]));
-        if (z < nz && mem_tg >= 0) x_hat[(size_t)mem_tg * ldz + z] = xn;
-        unsigned h0b, l0b, h1b, l1b;
-        split_fast(xn.x, h0b, l0b);
-        split_fast(xn.y, h1b, l1b);
-        *reinterpret_cast<uint2*>(s_xh + z * 8 + 2 * tg) = make_uint2(h0b, h1b);
-        *reinterpret_cast<uint2*>(s_xl + z * 8 + 2 * tg) = make_uint2(l0b, l1b);
+        mma_split_a_2acc(ah, al, a, scr.bh[b0], scr.bh[b1], scr.bl[b0], scr.bl[b1]);
       }
     }
-    cons_sync();
-    // ---- D: Kx[t][r] = sum_z W[t][z] x_new[z][r] / s; each warp two 16-row t tiles at a time ----
-    {
-      unsigned xb[KZ][4];  // B fragments (hi0, hi1, lo0, lo1) of every K step, shared by the tiles
 #pragma unroll
-      for (int ks = 0; ks < KZ; ++ks) {
+    for (int hf = 0; hf < 2; ++hf) {
+      const int z = 16 * warp + g + 8 * hf;
+      const float2 xp = z < nz ? *reinterpret_cast<const float2*>(XV + tg * P.sz + 2 * z) : make_float2(0.f, 0.f);
+      const float2 xn = make_float2(xp.x + (ah[2 * hf] + al[2 * hf]), xp.y + (ah[2 * hf + 1] + al[2 * hf + 1]));
+      if (z < nz && mem_tg >= 0) q.x_hat[(size_t)mem_tg * q.ldz + z] = xn;
+      unsigned h0b, l0b, h1b, l1b;
+      split_fast(xn.x, h0b, l0b);
+      split_fast(xn.y, h1b, l1b);
+      *reinterpret_cast<uint2*>(scr.xh + z * 8 + 2 * tg) = make_uint2(h0b, h1b);
+      *reinterpret_cast<uint2*>(scr.xl + z * 8 + 2 * tg) = make_uint2(l0b, l1b);
+    }
+  }
+  cons_sync();
+  // ---- D: Kx[t][r] = sum_z W[t][z] x_new[z][r] / s; each warp two 16-row t tiles at a time ----
+  {
+    unsigned xb[KZM][4];  // B fragments (hi0, hi1, lo0, lo1) of every K step, shared by the tiles
+#pragma unroll
+    for (int ks = 0; ks < KZM; ++ks) {
+      if (ks < KZ) {
         const int b0 = (8 * ks + tg) * 8 + g;
-        xb[ks][0] = s_xh[b0];
-        xb[ks][1] = s_xh[b0 + 32];
-        xb[ks][2] = s_xl[b0];
-        xb[ks][3] = s_xl[b0 + 32];
+        xb[ks][0] = scr.xh[b0];
+        xb[ks][1] = scr.xh[b0 + 32];
+        xb[ks][2] = scr.xl[b0];
+        xb[ks][3] = scr.xl[b0 + 32];
       }
-      float2* dst = mem_tg >= 0 ? kx_hat + (size_t)mem_tg * ldt : nullptr;
-      for (int mt = warp; mt < mtt; mt += 2 * PIPE_CONS_WARPS) {
-        const int mt2 = mt + PIPE_CONS_WARPS;
-        const bool two = mt2 < mtt;
-        float dh[2][4] = {}, dlo[2][4] = {};
-        const float* w0 = W + 2 * mt * ZB * 64;   // block (t / 8 = 2 mt, z / 8 = 0)
-        const float* w1 = W + 2 * mt2 * ZB * 64;
+    }
+    float2* dst = mem_tg >= 0 ? q.kx_hat + (size_t)mem_tg * q.ldt : nullptr;
+    for (int mt = warp; mt < mtt; mt += 2 * PIPE_CONS_WARPS) {
+      const int mt2 = mt + PIPE_CONS_WARPS;
+      const bool two = mt2 < mtt;
+      float dh[2][4] = {}, dlo[2][4] = {};
+      const float* w0 = W + 2 * mt * ZB * 64;  // block (t / 8 = 2 mt, z / 8 = 0)
+      const float* w1 = W + 2 * mt2 * ZB * 64;
 #pragma unroll
-        for (int ks = 0; ks < KZ; ++ks) {
+      for (int ks = 0; ks < KZM; ++ks) {
+        if (ks < KZ) {
           const float a0[4] = {w0[ks * 64 + offF0], w0[(ZB + ks) * 64 + offF0], w0[ks * 64 + offF2],
                                w0[(ZB + ks) * 64 + offF2]};
           mma_split_a_2acc(dh[0], dlo[0], a0, xb[ks][0], xb[ks][1], xb[ks][2], xb[ks][3]);
@@ -738,16 +721,185 @@ __global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(
             mma_split_a_2acc(dh[1], dlo[1], a1, xb[ks][0], xb[ks][1], xb[ks][2], xb[ks][3]);
           }
         }
-        if (dst) {
+      }
+      if (dst) {
 #pragma unroll
-          for (int u = 0; u < 2; ++u) {
-            if (u == 1 && !two) break;
-            const int t = 16 * (u ? mt2 : mt) + g;
-            if (t < nt) dst[t] = make_float2((dh[u][0] + dlo[u][0]) * inv_s, (dh[u][1] + dlo[u][1]) * inv_s);
-            if (t + 8 < nt) dst[t + 8] = make_float2((dh[u][2] + dlo[u][2]) * inv_s, (dh[u][3] + dlo[u][3]) * inv_s);
-          }
+        for (int u = 0; u < 2; ++u) {
+          if (u == 1 && !two) break;
+          const int t = 16 * (u ? mt2 : mt) + g;
+          if (t < nt) dst[t] = make_float2((dh[u][0] + dlo[u][0]) * inv_s, (dh[u][1] + dlo[u][1]) * inv_s);
+          if (t + 8 < nt) dst[t + 8] = make_float2((dh[u][2] + dlo[u][2]) * inv_s, (dh[u][3] + dlo[u][3]) * inv_s);
         }
       }
+    }
+  }
+  return false;
+}
+
+// Shared set-up of both pipelined kernels: zero `zero_bytes` of shared memory
+// (operand padding then reads as zeros), initialise the stage barriers.
+__device__ __forceinline__ void pipe_setup(unsigned char* sm, int zero_bytes, uint64_t* full, uint64_t* empty, int S,
+                                           volatile int* s_abort) {
+  for (int i = threadIdx.x; i < zero_bytes / 16; i += PIPE_THREADS)
+    reinterpret_cast<float4*>(sm)[i] = make_float4(0.f, 0.f, 0.f, 0.f);
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < S; ++s) {
+      mbar_init(full + s, 1);
+      mbar_init(empty + s, PIPE_CONS_WARPS);
+    }
+    *s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // zeroes before the bulk copies
+  __syncthreads();
+}
+
+// Producer wait for a free stage: bounded, and it stops early once the
+// consumers have given up.  Returns false (after flagging a timeout of its
+// own) when no more stages must be filled.
+__device__ __forceinline__ bool wait_free(uint64_t* empty, uint32_t par, long long max_polls, volatile int* s_abort,
+                                          int* status_flag) {
+  for (long long i = 0; i < max_polls; ++i) {
+    if (mbar_try(empty, par)) return true;
+    if (*s_abort) return false;
+  }
+  if (!*s_abort) {
+    atomicExch(status_flag, 1);
+    *s_abort = 1;
+  }
+  return false;
+}
+
+// No copy may be in flight when the CTA exits: wait for each stage's last fill.
+__device__ __forceinline__ void drain_fills(uint64_t* full, int S, int issued) {
+  for (int s = 0; s < S; ++s) {
+    if (issued > s) {
+      const int last = s + ((issued - 1 - s) / S) * S;
+      mbar_wait_bounded(full + s, (uint32_t)((last / S) & 1), PIPE_DRAIN_POLLS);
+    }
+  }
+}
+
+// Single problem: CTA b takes classes b, b + grid, ...
+// KZ = forward K steps = ceil(nz / 8); MZ = 16-row z tiles = ceil(nz / 16).
+template <int KZ>
+__global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_pipe(PipeProb q, int* status_flag,
+                                                                        long long max_polls) {
+  extern __shared__ __align__(128) float4 sm_pipe[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(sm_pipe);
+  const PipePlan& P = q.P;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int S = P.stages;
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + P.o_bar);
+  uint64_t* empty = full + S;
+  volatile int* s_abort = reinterpret_cast<volatile int*>(empty + S);
+  pipe_setup(sm, P.o_bar, full, empty, S, s_abort);
+  const int nclass = q.nclass;
+  const int mine = (int)blockIdx.x < nclass ? (nclass - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  if (warp == PIPE_CONS_WARPS) {
+    if (lane != 0) return;
+    int issued = 0;
+    for (; issued < mine; ++issued) {
+      const int s = issued % S;
+      if (!wait_free(empty + s, ((issued / S) & 1) ^ 1, max_polls, s_abort, status_flag)) break;
+      produce_item(q, (int)blockIdx.x + issued * (int)gridDim.x, sm + s * P.stage_bytes, full + s);
+    }
+    drain_fills(full, S, issued);
+    return;
+  }
+  const PipeScratch scr{reinterpret_cast<float*>(sm + P.o_part), reinterpret_cast<unsigned*>(sm + P.o_bh),
+                        reinterpret_cast<unsigned*>(sm + P.o_bl), reinterpret_cast<unsigned*>(sm + P.o_xh),
+                        reinterpret_cast<unsigned*>(sm + P.o_xl)};
+  for (int k = 0; k < mine; ++k) {
+    const int s = k % S;
+    int gave_up = 0;
+    if (!mbar_wait_bounded(full + s, (uint32_t)((k / S) & 1), max_polls)) {
+      gave_up = 1;
+      atomicExch(status_flag, 1);
+    }
+    if (consume_item<KZ>(q, sm + s * P.stage_bytes, scr, gave_up)) {
+      if (threadIdx.x == 0) *s_abort = 1;
+      break;
+    }
+    __syncwarp();
+    if (lane == 0) mbar_arrive(empty + s);
+  }
+}
+
+// Many problems, one persistent launch: the producer of each CTA takes items
+// (problem, class) from a device work queue (an atomic counter, QCHUNK items
+// per grab; problems in the queue in the caller's order, largest class blocks
+// first), so that CTAs done with one problem's classes go on with the next.
+// Stages are sized for the largest problem plus a 32-byte tail whose first
+// word names the item's problem + 1 (0: the queue is empty, the consumers stop).
+constexpr int QCHUNK = 8;
+
+__global__ void __launch_bounds__(PIPE_THREADS, 1) k_contract_admm_queue(const PipeProb* __restrict__ probs, int nprob,
+                                                                         int total, int* queue, int stage_bytes,
+                                                                         int S, int o_scr, int zm_max,
+                                                                         int* status_flag, long long max_polls) {
+  extern __shared__ __align__(128) float4 sm_pipe[];
+  unsigned char* sm = reinterpret_cast<unsigned char*>(sm_pipe);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // layout: S stages | consumer scratch | problem table | barriers
+  const int o_part = o_scr, o_bh = o_part + PIPE_CONS_WARPS * zm_max * 32, o_bl = o_bh + zm_max * 32,
+            o_xh = o_bl + zm_max * 32, o_xl = o_xh + zm_max * 32, o_tab = o_xl + zm_max * 32;
+  PipeProb* tab = reinterpret_cast<PipeProb*>(sm + o_tab);
+  const int o_bar = o_tab + ((nprob * (int)sizeof(PipeProb) + 15) & ~15);
+  uint64_t* full = reinterpret_cast<uint64_t*>(sm + o_bar);
+  uint64_t* empty = full + S;
+  volatile int* s_abort = reinterpret_cast<volatile int*>(empty + S);
+  for (int i = threadIdx.x; i < nprob * (int)sizeof(PipeProb) / 4; i += PIPE_THREADS)
+    reinterpret_cast<int*>(tab)[i] = reinterpret_cast<const int*>(probs)[i];
+  pipe_setup(sm, o_tab, full, empty, S, s_abort);
+  if (warp == PIPE_CONS_WARPS) {
+    if (lane != 0) return;
+    int issued = 0, cur = 0, end = 0, pi = 0;
+    for (;;) {
+      if (cur >= end) {
+        cur = atomicAdd(queue, QCHUNK);
+        end = min(cur + QCHUNK, total);
+      }
+      const bool more = cur < total;
+      const int s = issued % S;
+      if (!wait_free(empty + s, ((issued / S) & 1) ^ 1, max_polls, s_abort, status_flag)) break;
+      unsigned char* st = sm + s * stage_bytes;
+      int* slot = reinterpret_cast<int*>(st + stage_bytes - 16);  // the item's problem + 1, 0 = queue empty
+      if (!more) {
+        *slot = 0;
+        mbar_arrive(full + s);
+        ++issued;
+        break;
+      }
+      while (pi + 1 < nprob && tab[pi + 1].item0 <= cur) ++pi;  // items come in increasing order
+      *slot = pi + 1;
+      produce_item(tab[pi], cur - tab[pi].item0, st, full + s);
+      ++cur;
+      ++issued;
+    }
+    drain_fills(full, S, issued);
+    return;
+  }
+  const PipeScratch scr{reinterpret_cast<float*>(sm + o_part), reinterpret_cast<unsigned*>(sm + o_bh),
+                        reinterpret_cast<unsigned*>(sm + o_bl), reinterpret_cast<unsigned*>(sm + o_xh),
+                        reinterpret_cast<unsigned*>(sm + o_xl)};
+  for (int k = 0;; ++k) {
+    const int s = k % S;
+    int gave_up = 0;
+    if (!mbar_wait_bounded(full + s, (uint32_t)((k / S) & 1), max_polls)) {
+      gave_up = 1;
+      atomicExch(status_flag, 1);
+    }
+    const unsigned char* st = sm + s * stage_bytes;
+    const int pi = *reinterpret_cast<const int*>(st + stage_bytes - 16) - 1;
+    if (cons_sync_or(gave_up)) {
+      if (threadIdx.x == 0) *s_abort = 1;
+      break;
+    }
+    if (pi < 0) break;
+    if (consume_item<0>(tab[pi], st, scr, 0)) {
+      if (threadIdx.x == 0) *s_abort = 1;
+      break;
     }
     __syncwarp();
     if (lane == 0) mbar_arrive(empty + s);
@@ -759,10 +911,22 @@ ctof_status launch_pipe(const ctof_kernel_s* k, const PipePlan& P, int grid, con
                         float2* x_hat, float2* kx_hat, float inv_scale, cudaStream_t st) {
   CTOF_CUDA_TRY(
       cudaFuncSetAttribute(k_contract_admm_pipe<KZ>, cudaFuncAttributeMaxDynamicSharedMemorySize, P.total));
-  k_contract_admm_pipe<KZ><<<grid, PIPE_THREADS, P.total, st>>>(P, k->d_what_admm, k->d_hinv_admm, k->d_lap,
-                                                                 k->d_members, k->nclass, c_hat, k->ldt, s_hat,
-                                                                 x_hat, k->ldz, kx_hat, inv_scale, k->d_flags,
-                                                                 k->max_polls);
+  PipeProb q{};
+  q.P = P;
+  q.what_o = k->d_what_admm;
+  q.hinv_o = k->d_hinv_admm;
+  q.lap = k->d_lap;
+  q.members = k->d_members;
+  q.nclass = k->nclass;
+  q.c_hat = c_hat;
+  q.s_hat = s_hat;
+  q.x_hat = x_hat;
+  q.kx_hat = kx_hat;
+  q.ldt = k->ldt;
+  q.ldz = k->ldz;
+  q.inv_s = inv_scale;
+  q.item0 = 0;
+  k_contract_admm_pipe<KZ><<<grid, PIPE_THREADS, P.total, st>>>(q, k->d_flags, k->max_polls);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
@@ -828,4 +992,125 @@ ctof_status contract_admm(const ctof_kernel_s* k, const float2* c_hat, const flo
                                                 k->ldt, s_hat, x_hat, k->ldz, kx_hat, inv_scale);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
+}
+
+// ---- many problems in one persistent launch --------------------------------
+
+namespace {
+
+struct QueueLayout {
+  int stage_bytes, stages, o_scr, zm_max, smem;
+};
+
+QueueLayout queue_layout(int max_layout, int zm_max, int nprob, int stages) {
+  QueueLayout L;
+  L.stage_bytes = rup(max_layout + 32, 128);
+  L.stages = stages;
+  L.zm_max = zm_max;
+  L.o_scr = stages * L.stage_bytes;
+  const int scratch = PIPE_CONS_WARPS * zm_max * 32 + 4 * zm_max * 32;
+  const int table = (nprob * (int)sizeof(PipeProb) + 15) & ~15;
+  L.smem = L.o_scr + scratch + table + 2 * stages * 8 + 16;
+  return L;
+}
+
+// The device work-queue counter sits after the problem table.
+size_t queue_counter_offset(int nprob) { return ((size_t)nprob * sizeof(PipeProb) + 255) & ~(size_t)255; }
+
+}  // namespace
+
+ctof_status admm_queue_build(int count, ctof_kernel_s* const* ks, AdmmQueue* out) {
+  admm_queue_free(out);
+  struct Cand {
+    int idx, layout, zm;
+  };
+  std::vector<Cand> cand;
+  for (int i = 0; i < count; ++i) {
+    const ctof_kernel_s* k = ks[i];
+    if (!k->d_what_admm || !pipe_stages(k->nt, k->nz)) continue;
+    const PipePlan P = make_pipe_plan(k->nt, k->nz, 2);
+    cand.push_back({i, P.stage_bytes, P.zm});
+  }
+  // the largest set, taken from the smallest class blocks up, whose two stages fit
+  std::sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.layout < b.layout; });
+  int take = 0, max_layout = 0, zm_max = 16;
+  for (int j = 0; j < (int)cand.size(); ++j) {
+    const int ml = std::max(max_layout, cand[j].layout), zm = std::max(zm_max, cand[j].zm);
+    if (queue_layout(ml, zm, j + 1, 2).smem > PIPE_SMEM_LIMIT) break;
+    max_layout = ml;
+    zm_max = zm;
+    take = j + 1;
+  }
+  if (take < 2) return CTOF_OK;  // nothing to gain: every problem keeps its own launch
+  cand.resize(take);
+  // queue order: largest class blocks first, so that small ones fill in at the end
+  std::sort(cand.begin(), cand.end(), [](const Cand& a, const Cand& b) { return a.layout > b.layout; });
+  int stages = 2;
+  while (stages < 4 && queue_layout(max_layout, zm_max, take, stages + 1).smem <= PIPE_SMEM_LIMIT) ++stages;
+  const QueueLayout L = queue_layout(max_layout, zm_max, take, stages);
+  std::vector<PipeProb> tab(take);
+  int items = 0;
+  for (int j = 0; j < take; ++j) {
+    const ctof_kernel_s* k = ks[cand[j].idx];
+    PipeProb& q = tab[j];
+    q.P = make_pipe_plan(k->nt, k->nz, 2);
+    q.what_o = k->d_what_admm;
+    q.hinv_o = k->d_hinv_admm;
+    q.lap = k->d_lap;
+    q.members = k->d_members;
+    q.nclass = k->nclass;
+    q.c_hat = k->d_spec_t2;
+    q.s_hat = k->d_spec_z;
+    q.x_hat = k->d_spec_z2;
+    q.kx_hat = k->d_spec_t;
+    q.ldt = k->ldt;
+    q.ldz = k->ldz;
+    q.inv_s = (float)(1.0 / k->scale);
+    q.item0 = items;
+    items += k->nclass;
+  }
+  void* d = nullptr;
+  const size_t tbytes = (size_t)take * sizeof(PipeProb);
+  if (cudaMalloc(&d, queue_counter_offset(take) + 256) != cudaSuccess) {
+    cudaGetLastError();
+    return CTOF_ENOMEM;
+  }
+  out->d_mem = d;
+  if (cudaMemcpy(d, tab.data(), tbytes, cudaMemcpyHostToDevice) != cudaSuccess) {
+    admm_queue_free(out);
+    return CTOF_ECUDA;
+  }
+  for (int j = 0; j < take; ++j) out->members.push_back(cand[j].idx);
+  out->nprob = take;
+  out->total = items;
+  out->stage_bytes = L.stage_bytes;
+  out->stages = L.stages;
+  out->o_scr = L.o_scr;
+  out->zm_max = L.zm_max;
+  out->smem = L.smem;
+  out->flag = ks[cand[0].idx]->d_flags;
+  out->max_polls = ks[cand[0].idx]->max_polls;
+  out->nsm = 152;
+  cudaDeviceGetAttribute(&out->nsm, cudaDevAttrMultiProcessorCount, ks[cand[0].idx]->device);
+  return CTOF_OK;
+}
+
+ctof_status admm_queue_launch(const AdmmQueue& q, cudaStream_t st) {
+  if (q.nprob == 0) return CTOF_OK;
+  const PipeProb* tab = static_cast<const PipeProb*>(q.d_mem);
+  int* ctr = reinterpret_cast<int*>(static_cast<char*>(q.d_mem) + queue_counter_offset(q.nprob));
+  CTOF_CUDA_TRY(cudaMemsetAsync(ctr, 0, sizeof(int), st));
+  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_contract_admm_queue, cudaFuncAttributeMaxDynamicSharedMemorySize, q.smem));
+  k_contract_admm_queue<<<q.nsm, PIPE_THREADS, q.smem, st>>>(tab, q.nprob, q.total, ctr, q.stage_bytes, q.stages,
+                                                            q.o_scr, q.zm_max, q.flag, q.max_polls);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+void admm_queue_free(AdmmQueue* q) {
+  if (q->d_mem) cudaFree(q->d_mem);
+  q->d_mem = nullptr;
+  q->nprob = 0;
+  q->total = 0;
+  q->members.clear();
 }

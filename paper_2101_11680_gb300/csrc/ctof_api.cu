@@ -129,12 +129,10 @@ ctof_status adjoint_impl(ctof_kernel_s* k, const float* m, float* vol, cudaStrea
   return fft_inverse_planes(k, k->d_spec_z, k->ldz, k->nz, k->n, k->n, k->d_inter_z, vol, k->n, st);
 }
 
-// ADMM on the staged measurement d_mstage; result (crop of v3) in d_vstage.
-ctof_status admm_enqueue(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st, bool timed) {
+// ADMM set-up on the staged measurement d_mstage: the TV weight and the state reset.
+ctof_status admm_setup(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st) {
   const int nt = k->nt, nz = k->nz, n = k->n, P = k->p;
   const size_t pp = (size_t)P * P;
-  const float inv_s = (float)(1.0 / k->scale);
-  const float rho = (float)prm->rho;
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_scalars, 0, 16 * sizeof(double), st));
   if (prm->tv_beta < 0) {
     CTOF_TRY(adjoint_impl(k, k->d_mstage, k->d_vstage, st));
@@ -147,30 +145,50 @@ ctof_status admm_enqueue(ctof_kernel_s* k, const ctof_solver_params* prm, cudaSt
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_u1, 0, (size_t)nt * n * n * sizeof(float), st));
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_u2a, 0, 3 * nz * pp * sizeof(float), st));
   CTOF_CUDA_TRY(cudaMemsetAsync(k->d_u3, 0, nz * pp * sizeof(float), st));
+  return CTOF_OK;
+}
+
+// The x-update of iteration `it` (per frequency class) and K x.
+ctof_status admm_contract(ctof_kernel_s* k, cudaStream_t st) {
+  return contract_admm(k, k->d_spec_t2, k->d_spec_z, k->d_spec_z2, k->d_spec_t, (float)(1.0 / k->scale), st);
+}
+
+// The rest of iteration `it`: T side (K x -> v1/u1 -> c_hat; not after the
+// last iteration) and Z side (x -> TV / nonnegativity prox -> s_hat; the last
+// iteration writes the crop of v3 to d_vstage).  `ev_mid` (optional) is
+// recorded between the two.
+ctof_status admm_side(ctof_kernel_s* k, const ctof_solver_params* prm, int it, cudaStream_t st, cudaEvent_t ev_mid) {
+  const int nt = k->nt, nz = k->nz, n = k->n, P = k->p;
+  const float inv_s = (float)(1.0 / k->scale);
+  const float rho = (float)prm->rho;
+  const bool last = it == prm->iters - 1;
+  if (!last) {
+    CTOF_TRY(fft_cols_inverse(k, k->d_spec_t, k->ldt, nt, n, k->d_inter_t, st));
+    CTOF_TRY(fft_rows_admm_t(k, k->d_inter_t, k->d_mstage, k->d_u1, inv_s, rho, st));
+    CTOF_TRY(fft_cols_forward(k, k->d_inter_t, nt, n, k->d_spec_t2, k->ldt, st));
+  }
+  if (ev_mid) CTOF_CUDA_TRY(cudaEventRecordWithFlags(ev_mid, st, cudaEventRecordExternal));
   float* u2[2] = {k->d_u2a, k->d_u2b};
+  CTOF_TRY(fft_cols_inverse(k, k->d_spec_z2, k->ldz, nz, P, k->d_inter_z, st));
+  CTOF_TRY(fft_rows_inverse(k, k->d_inter_z, nz, P, P, k->d_xs, P, st));
+  CTOF_TRY(admm_tv_stencil(k, k->d_xs, u2[it & 1], u2[(it + 1) & 1], k->d_u3, k->d_s, k->d_scalars, rho,
+                           last ? k->d_vstage : nullptr, st));
+  if (!last) {
+    CTOF_TRY(fft_rows_forward(k, k->d_s, nz, P, P, P, k->d_inter_z, st));
+    CTOF_TRY(fft_cols_forward(k, k->d_inter_z, nz, P, k->d_spec_z, k->ldz, st));
+  }
+  return CTOF_OK;
+}
+
+// ADMM on the staged measurement d_mstage; result (crop of v3) in d_vstage.
+ctof_status admm_enqueue(ctof_kernel_s* k, const ctof_solver_params* prm, cudaStream_t st, bool timed) {
+  CTOF_TRY(admm_setup(k, prm, st));
   cudaEvent_t* ev = (timed && k->timing) ? k->events : nullptr;
   for (int it = 0; it < prm->iters; ++it) {
-    const bool last = it == prm->iters - 1;
     if (ev) CTOF_CUDA_TRY(cudaEventRecordWithFlags(ev[4 * it + 0], st, cudaEventRecordExternal));
-    // x-update (per frequency class) and K x
-    CTOF_TRY(contract_admm(k, k->d_spec_t2, k->d_spec_z, k->d_spec_z2, k->d_spec_t, inv_s, st));
+    CTOF_TRY(admm_contract(k, st));
     if (ev) CTOF_CUDA_TRY(cudaEventRecordWithFlags(ev[4 * it + 1], st, cudaEventRecordExternal));
-    if (!last) {
-      // T side: K x -> v1/u1 -> c_hat
-      CTOF_TRY(fft_cols_inverse(k, k->d_spec_t, k->ldt, nt, n, k->d_inter_t, st));
-      CTOF_TRY(fft_rows_admm_t(k, k->d_inter_t, k->d_mstage, k->d_u1, inv_s, rho, st));
-      CTOF_TRY(fft_cols_forward(k, k->d_inter_t, nt, n, k->d_spec_t2, k->ldt, st));
-    }
-    if (ev) CTOF_CUDA_TRY(cudaEventRecordWithFlags(ev[4 * it + 2], st, cudaEventRecordExternal));
-    // Z side: x -> TV / nonnegativity prox -> s_hat
-    CTOF_TRY(fft_cols_inverse(k, k->d_spec_z2, k->ldz, nz, P, k->d_inter_z, st));
-    CTOF_TRY(fft_rows_inverse(k, k->d_inter_z, nz, P, P, k->d_xs, P, st));
-    CTOF_TRY(admm_tv_stencil(k, k->d_xs, u2[it & 1], u2[(it + 1) & 1], k->d_u3, k->d_s, k->d_scalars, rho,
-                             last ? k->d_vstage : nullptr, st));
-    if (!last) {
-      CTOF_TRY(fft_rows_forward(k, k->d_s, nz, P, P, P, k->d_inter_z, st));
-      CTOF_TRY(fft_cols_forward(k, k->d_inter_z, nz, P, k->d_spec_z, k->ldz, st));
-    }
+    CTOF_TRY(admm_side(k, prm, it, st, ev ? ev[4 * it + 2] : nullptr));
     if (ev) CTOF_CUDA_TRY(cudaEventRecordWithFlags(ev[4 * it + 3], st, cudaEventRecordExternal));
   }
   return CTOF_OK;
@@ -462,6 +480,7 @@ struct BatchGraph {
   int iters = 0;
   double rho = 0, beta = 0, beta_rel = 0;
   cudaGraphExec_t exec = nullptr;
+  AdmmQueue queue;  // the batched x-update's problem table and work-queue counter
 };
 std::mutex g_batch_mutex;
 BatchGraph g_batch;
@@ -496,28 +515,58 @@ ctof_status batch_graph_run(int count, const ctof_kernel* ks, const float* const
       CTOF_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
       g_side_events.push_back(e);
     }
+    // problems whose x-update runs in the one persistent queue launch per iteration
+    CTOF_TRY(admm_queue_build(count, const_cast<ctof_kernel_s* const*>(ks), &g_batch.queue));
+    std::vector<char> queued(count, 0);
+    for (int i : g_batch.queue.members) queued[i] = 1;
     cudaStream_t cap = nullptr;
     CTOF_CUDA_TRY(cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking));
     cudaGraph_t graph = nullptr;
     cudaError_t e = cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed);
     ctof_status s = e == cudaSuccess ? CTOF_OK : CTOF_ECUDA;
-    if (s == CTOF_OK && cudaEventRecord(g_side_events[nside], cap) != cudaSuccess) s = CTOF_ECUDA;
-    for (int j = 0; j < nside && s == CTOF_OK; ++j)
-      if (cudaStreamWaitEvent(g_side_streams[j], g_side_events[nside], 0) != cudaSuccess) s = CTOF_ECUDA;
+    // fork the side streams off `cap`, or join them back into it
+    auto fork = [&]() {
+      if (s == CTOF_OK && cudaEventRecord(g_side_events[nside], cap) != cudaSuccess) s = CTOF_ECUDA;
+      for (int j = 0; j < nside && s == CTOF_OK; ++j)
+        if (cudaStreamWaitEvent(g_side_streams[j], g_side_events[nside], 0) != cudaSuccess) s = CTOF_ECUDA;
+    };
+    auto join = [&]() {
+      for (int j = 0; j < nside && s == CTOF_OK; ++j) {
+        if (cudaEventRecord(g_side_events[j], g_side_streams[j]) != cudaSuccess ||
+            cudaStreamWaitEvent(cap, g_side_events[j], 0) != cudaSuccess)
+          s = CTOF_ECUDA;
+      }
+    };
+    fork();
     for (int i = 0; i < count && s == CTOF_OK; ++i) {
       ctof_kernel_s* k = ks[i];
       cudaStream_t side = g_side_streams[i % nside];
-      const size_t mb = (size_t)k->nt * k->n * k->n * sizeof(float), vb = (size_t)k->nz * k->n * k->n * sizeof(float);
+      const size_t mb = (size_t)k->nt * k->n * k->n * sizeof(float);
       if (cudaMemcpyAsync(k->d_mstage, d_m[i], mb, cudaMemcpyDeviceToDevice, side) != cudaSuccess) s = CTOF_ECUDA;
-      if (s == CTOF_OK) s = admm_enqueue(k, prm, side, false);
-      if (s == CTOF_OK && cudaMemcpyAsync(d_mu[i], k->d_vstage, vb, cudaMemcpyDeviceToDevice, side) != cudaSuccess)
+      if (s == CTOF_OK) s = admm_setup(k, prm, side);
+    }
+    join();
+    // iterations in lockstep: the queued x-updates of all problems as one launch,
+    // then every problem's own x-update (if not queued) and T / Z sides on its stream
+    for (int it = 0; it < prm->iters && s == CTOF_OK; ++it) {
+      s = admm_queue_launch(g_batch.queue, cap);
+      fork();
+      for (int i = 0; i < count && s == CTOF_OK; ++i) {
+        cudaStream_t side = g_side_streams[i % nside];
+        if (!queued[i]) s = admm_contract(ks[i], side);
+        if (s == CTOF_OK) s = admm_side(ks[i], prm, it, side, nullptr);
+      }
+      join();
+    }
+    fork();
+    for (int i = 0; i < count && s == CTOF_OK; ++i) {
+      ctof_kernel_s* k = ks[i];
+      const size_t vb = (size_t)k->nz * k->n * k->n * sizeof(float);
+      if (cudaMemcpyAsync(d_mu[i], k->d_vstage, vb, cudaMemcpyDeviceToDevice, g_side_streams[i % nside]) !=
+          cudaSuccess)
         s = CTOF_ECUDA;
     }
-    for (int j = 0; j < nside && s == CTOF_OK; ++j) {
-      if (cudaEventRecord(g_side_events[j], g_side_streams[j]) != cudaSuccess ||
-          cudaStreamWaitEvent(cap, g_side_events[j], 0) != cudaSuccess)
-        s = CTOF_ECUDA;
-    }
+    join();
     e = cudaStreamEndCapture(cap, &graph);
     cudaStreamDestroy(cap);
     if (s == CTOF_OK && e != cudaSuccess) s = CTOF_ECUDA;

@@ -5,6 +5,8 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <vector>
+
 #include "common.cuh"
 
 // Device workspaces are carved from one allocation per handle.
@@ -197,6 +199,22 @@ size_t contract_admm_pipe_floats(int nt, int nz, int which);
 int contract_admm_pipe_stages(int nt, int nz);
 // Fill the pipelined kernel's copies from d_what / d_hinv (after the build).
 ctof_status contract_admm_prepare(ctof_kernel_s* k, cudaStream_t st);
+
+// Batched x-update: the problems of a batch whose class blocks fit two shared
+// stages of the largest among them, in one persistent launch fed by a device
+// work queue.  `members` lists their indices in the batch (queue order); the
+// other problems keep their own contract_admm launch.  Timeouts are reported
+// on the first queued problem's handle.
+struct AdmmQueue {
+  int nprob = 0, total = 0, stage_bytes = 0, stages = 0, o_scr = 0, zm_max = 0, smem = 0, nsm = 152;
+  void* d_mem = nullptr;  // problem table, then the queue counter
+  int* flag = nullptr;
+  long long max_polls = 0;
+  std::vector<int> members;
+};
+ctof_status admm_queue_build(int count, ctof_kernel_s* const* ks, AdmmQueue* out);
+ctof_status admm_queue_launch(const AdmmQueue& q, cudaStream_t st);
+void admm_queue_free(AdmmQueue* q);
 
 // ---- batch_tikhonov.cu ----------------------------------------------------
 size_t batch_tikhonov_smem_bytes(int nt, int nz);

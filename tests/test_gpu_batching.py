@@ -1,5 +1,8 @@
 """Batching form: several ADMM problems of uneven sizes and optics in one
-captured multi-stream graph, with autotuned column-FFT tiles.
+captured graph: per iteration, the x-updates of all problems whose class
+blocks fit the shared stages run as one persistent launch fed by a device work
+queue, the FFT / TV stages of every problem on forked streams; column-FFT
+tiles are autotuned.
 
 Each problem of the batch must match the FP64 oracle (rel-L2 <= 1e-5, the
 FP32 bound) and be bit-identical to the same problem reconstructed alone; a
