@@ -30,9 +30,9 @@
 // time: 16 volumes x 4 members x re/im = 128 right-hand sides = the M side of
 // the GEMM D[n][z] = sum_t m[n][t] W[t][z] (M = 128, N = Z rounded up to 16,
 // K = t in chunks of 32).  Each t chunk of m_hat rows and W_hat rows streams
-// into one of two raw shared-memory stages with 16-byte cp.async copies while
-// the previous chunk is split into its terms (W^T through 4 x 4 register
-// transposes) and multiplied; the term buffers are double-buffered as well,
+// into a ring of four raw shared-memory stages with cp.async copies, three
+// chunks ahead of the one being split into its terms (W^T read down padded
+// columns) and multiplied; the term buffers are double-buffered as well,
 // each set guarded by its own MMA-completion mbarrier.  After the last chunk
 // the refinement runs on the TMEM accumulators: each thread owns one
 // right-hand side (a TMEM lane) and half of its Z columns.  Every wait is
@@ -52,7 +52,8 @@ constexpr int BT_THREADS = 256;
 constexpr int VB = 16;             // volumes per chunk
 constexpr int NR = 8 * VB;         // right-hand sides per chunk (the GEMM's M = 128)
 constexpr int TCH = 32;            // t values per K chunk
-constexpr int RCS = TCH * 8 + 16;  // raw stage bytes per (volume, member) row
+constexpr int RCS = TCH * 8 + 8;   // raw stage bytes per (volume, member) row: 66 words, rows 2 banks apart
+constexpr int RAW_STAGES = 4;      // raw copies run this many t chunks ahead, minus one
 constexpr long long DRAIN_POLLS = 1ll << 24;
 constexpr float E4M3_MAX = 448.f;
 
@@ -83,8 +84,8 @@ BtPlan make_plan(int nt, int nz, int fp8, int batch) {
   P.a_term = NR * TCH * P.esize;
   P.b_term = P.zn * TCH * P.esize;
   P.set_bytes = P.nterm * (P.a_term + P.b_term);
-  P.raw_c = 4 * VB * RCS;
-  P.raw_stage = P.raw_c + TCH * P.z4 * 4;
+  P.raw_c = rup(4 * VB * RCS, 16);
+  P.raw_stage = P.raw_c + TCH * (P.z4 + 4) * 4;  // W rows padded by 4 floats: column reads on distinct banks
   P.tab_bytes = 4 * P.zn * P.zn * 4;
   P.x_tile = NR * P.zn * 4;
   P.batch = batch;
@@ -95,10 +96,11 @@ BtPlan make_plan(int nt, int nz, int fp8, int batch) {
     return at;
   };
   P.off_set = take(2 * P.set_bytes);
-  P.off_raw = take(2 * P.raw_stage);
+  P.off_raw = take(RAW_STAGES * P.raw_stage);
   P.off_tab = take(P.tab_bytes);
-  P.off_xh = take(P.x_tile);
-  P.off_xl = take(P.x_tile);
+  // the solve's operands reuse the term sets and raw stages (idle by then)
+  P.off_xh = P.off_set;
+  P.off_xl = P.off_set + rup(P.x_tile, 128);
   P.off_sn = take(NR * 4);
   P.off_bar = take(64);
   P.total = off;
@@ -206,7 +208,9 @@ __device__ __forceinline__ void cp_async8z(void* smem, const void* gmem, int byt
                : "memory");
 }
 __device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-__device__ __forceinline__ void cp_wait1() { asm volatile("cp.async.wait_group 1;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_wait_ahead() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(RAW_STAGES - 1) : "memory");
+}
 __device__ __forceinline__ void cp_wait0() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
 
 __device__ __forceinline__ int pick(const int (&mem)[4], int m) {
@@ -214,112 +218,109 @@ __device__ __forceinline__ int pick(const int (&mem)[4], int m) {
 }
 
 // Raw copies of one t chunk: 64 (volume, member) rows of TCH complex m_hat
-// values and TCH rows of W_hat (zero fill beyond nt, absent members, v >= nv).
+// values (8-byte copies: rows RCS bytes apart) and TCH rows of W_hat (16-byte
+// copies, rows z4 + 4 floats apart); zero fill beyond nt, for absent members
+// and for v >= nv.
 __device__ __forceinline__ void issue_raw(const BtPlan& P, unsigned char* raw, const int (&mem)[4], int v0, int nv,
                                           int t0, const float* __restrict__ wc, const float2* __restrict__ m_hat,
                                           int ldm) {
   const int nt = P.nt;
-  if ((nt & 1) == 0) {  // volume rows start on 16-byte boundaries: two complex values per copy
-    for (int i = threadIdx.x; i < 4 * VB * (TCH / 2); i += BT_THREADS) {
-      const int vm = i / (TCH / 2), p = i - vm * (TCH / 2);
-      const int v = vm >> 2, f = pick(mem, vm & 3), t = t0 + 2 * p;
-      const int bytes = (f < 0 || v >= nv) ? 0 : (t + 2 <= nt ? 16 : (t < nt ? 8 : 0));
-      const float2* src = bytes ? m_hat + (size_t)f * ldm + (size_t)(v0 + v) * nt + t : m_hat;
-      cp_async16z(raw + vm * RCS + p * 16, src, bytes);
-    }
-  } else {  // odd nt: rows of odd volumes start 8 bytes off, one complex value per copy
-    for (int i = threadIdx.x; i < 4 * VB * TCH; i += BT_THREADS) {
-      const int vm = i / TCH, p = i - vm * TCH;
-      const int v = vm >> 2, f = pick(mem, vm & 3), t = t0 + p;
-      const int bytes = (f < 0 || v >= nv || t >= nt) ? 0 : 8;
-      const float2* src = bytes ? m_hat + (size_t)f * ldm + (size_t)(v0 + v) * nt + t : m_hat;
-      cp_async8z(raw + vm * RCS + p * 8, src, bytes);
-    }
+  for (int i = threadIdx.x; i < 4 * VB * TCH; i += BT_THREADS) {
+    const int vm = i / TCH, p = i - vm * TCH;
+    const int v = vm >> 2, f = pick(mem, vm & 3), t = t0 + p;
+    const int bytes = (f < 0 || v >= nv || t >= nt) ? 0 : 8;
+    const float2* src = bytes ? m_hat + (size_t)f * ldm + (size_t)(v0 + v) * nt + t : m_hat;
+    cp_async8z(raw + vm * RCS + p * 8, src, bytes);
   }
   unsigned char* rw = raw + P.raw_c;
-  const int q4 = P.z4 >> 2;
+  const int q4 = P.z4 >> 2, ws = P.z4 + 4;
   for (int i = threadIdx.x; i < TCH * q4; i += BT_THREADS) {
     const int tl = i / q4, k4 = i - tl * q4, t = t0 + tl;
     const int bytes = t < nt ? 16 : 0;
-    cp_async16z(rw + i * 16, bytes ? wc + (size_t)t * P.z4 + 4 * k4 : wc, bytes);
+    cp_async16z(rw + (tl * ws + 4 * k4) * 4, bytes ? wc + (size_t)t * P.z4 + 4 * k4 : wc, bytes);
   }
 }
 
 // Split the raw chunk into its terms: A = m rows (n = 8 v + 2 member + re/im,
 // K = t), B = W^T rows (z, K = t).  s_n: per right-hand-side scales (FP8).
+// A item = (volume-member row, group of epc t): one float2 read per t gives
+// both the real (row 2 vm) and imaginary (row 2 vm + 1) right-hand sides;
+// B item = (z, group of epc t), read down a padded W column.  Consecutive
+// threads take consecutive rows, so reads and 16-byte term stores hit
+// distinct banks.
 __device__ __forceinline__ void convert_chunk(const BtPlan& P, const unsigned char* raw, unsigned char* set,
                                               const float* s_n, float inv_sw) {
-  const int epc = P.epc;
+  const int epc = P.epc, groups = TCH / epc;
   unsigned char* a = set;                       // nterm A terms
   unsigned char* b = set + P.nterm * P.a_term;  // nterm B terms
-  // A: item = (row n, group g of epc t values); consecutive threads on consecutive rows
-  const int groups = TCH / epc;
-  for (int i = threadIdx.x; i < NR * groups; i += BT_THREADS) {
-    const int n = i & (NR - 1), gI = i >> 7;
-    const float* row = reinterpret_cast<const float*>(raw + (n >> 1) * RCS) + 2 * gI * epc + (n & 1);
-    const uint32_t o = kchunk(NR, n, gI * epc, epc);
+  for (int i = threadIdx.x; i < 4 * VB * groups; i += BT_THREADS) {
+    const int vm = i & (4 * VB - 1), gI = i / (4 * VB);
+    const float2* row = reinterpret_cast<const float2*>(raw + vm * RCS) + gI * epc;
+    const uint32_t o_re = kchunk(NR, 2 * vm, gI * epc, epc), o_im = kchunk(NR, 2 * vm + 1, gI * epc, epc);
     if (P.fp8) {
-      const float sc = 1.f / s_n[n];
-      float v[16];
-#pragma unroll
-      for (int e = 0; e < 16; ++e) v[e] = row[2 * e] * sc;
-      uint4 t0, t1, t2;
-      split16_e4m3(v, t0, t1, t2);
-      *reinterpret_cast<uint4*>(a + o) = t0;
-      *reinterpret_cast<uint4*>(a + P.a_term + o) = t1;
-      *reinterpret_cast<uint4*>(a + 2 * P.a_term + o) = t2;
-    } else {
-      float v[8];
-#pragma unroll
-      for (int e = 0; e < 8; ++e) v[e] = row[2 * e];
-      uint4 hi, lo;
-      split8_bf16(v, hi, lo);
-      *reinterpret_cast<uint4*>(a + o) = hi;
-      *reinterpret_cast<uint4*>(a + P.a_term + o) = lo;
-    }
-  }
-  // B: item = (4 z, group of epc t), read as epc float4 rows and transposed in registers
-  const unsigned char* rw = raw + P.raw_c;
-  const int q4 = P.z4 >> 2;
-  for (int i = threadIdx.x; i < q4 * groups; i += BT_THREADS) {
-    const int k4 = i % q4, gI = i / q4;
-    if (P.fp8) {
-      float w[4][16];
+      const float sr = 1.f / s_n[2 * vm], si = 1.f / s_n[2 * vm + 1];
+      float vr[16], vi[16];
 #pragma unroll
       for (int e = 0; e < 16; ++e) {
-        const float4 x = *reinterpret_cast<const float4*>(rw + ((gI * 16 + e) * q4 + k4) * 16);
-        w[0][e] = x.x * inv_sw;
-        w[1][e] = x.y * inv_sw;
-        w[2][e] = x.z * inv_sw;
-        w[3][e] = x.w * inv_sw;
+        const float2 x = row[e];
+        vr[e] = x.x * sr;
+        vi[e] = x.y * si;
       }
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        uint4 t0, t1, t2;
-        split16_e4m3(w[r], t0, t1, t2);
-        const uint32_t o = kchunk(P.zn, 4 * k4 + r, gI * 16, 16);
-        *reinterpret_cast<uint4*>(b + o) = t0;
-        *reinterpret_cast<uint4*>(b + P.b_term + o) = t1;
-        *reinterpret_cast<uint4*>(b + 2 * P.b_term + o) = t2;
-      }
+      uint4 t0, t1, t2;
+      split16_e4m3(vr, t0, t1, t2);
+      *reinterpret_cast<uint4*>(a + o_re) = t0;
+      *reinterpret_cast<uint4*>(a + P.a_term + o_re) = t1;
+      *reinterpret_cast<uint4*>(a + 2 * P.a_term + o_re) = t2;
+      split16_e4m3(vi, t0, t1, t2);
+      *reinterpret_cast<uint4*>(a + o_im) = t0;
+      *reinterpret_cast<uint4*>(a + P.a_term + o_im) = t1;
+      *reinterpret_cast<uint4*>(a + 2 * P.a_term + o_im) = t2;
     } else {
-      float w[4][8];
+      float vr[8], vi[8];
 #pragma unroll
       for (int e = 0; e < 8; ++e) {
-        const float4 x = *reinterpret_cast<const float4*>(rw + ((gI * 8 + e) * q4 + k4) * 16);
-        w[0][e] = x.x;
-        w[1][e] = x.y;
-        w[2][e] = x.z;
-        w[3][e] = x.w;
+        const float2 x = row[e];
+        vr[e] = x.x;
+        vi[e] = x.y;
       }
+      uint4 hi, lo;
+      split8_bf16(vr, hi, lo);
+      *reinterpret_cast<uint4*>(a + o_re) = hi;
+      *reinterpret_cast<uint4*>(a + P.a_term + o_re) = lo;
+      split8_bf16(vi, hi, lo);
+      *reinterpret_cast<uint4*>(a + o_im) = hi;
+      *reinterpret_cast<uint4*>(a + P.a_term + o_im) = lo;
+    }
+  }
+  // B rows z in [z4, zn) stay zero: the solve's operands share this memory
+  for (int i = threadIdx.x; i < (P.zn - P.z4) * groups; i += BT_THREADS) {
+    const int z = P.z4 + i % (P.zn - P.z4), gI = i / (P.zn - P.z4);
+    const uint32_t o = kchunk(P.zn, z, gI * epc, epc);
+    for (int tI = 0; tI < P.nterm; ++tI) *reinterpret_cast<uint4*>(b + tI * P.b_term + o) = make_uint4(0u, 0u, 0u, 0u);
+  }
+  const float* rw = reinterpret_cast<const float*>(raw + P.raw_c);
+  const int ws = P.z4 + 4;
+  for (int i = threadIdx.x; i < P.z4 * groups; i += BT_THREADS) {
+    const int z = i % P.z4, gI = i / P.z4;
+    const float* col = rw + gI * epc * ws + z;
+    const uint32_t o = kchunk(P.zn, z, gI * epc, epc);
+    if (P.fp8) {
+      float w[16];
 #pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        uint4 hi, lo;
-        split8_bf16(w[r], hi, lo);
-        const uint32_t o = kchunk(P.zn, 4 * k4 + r, gI * 8, 8);
-        *reinterpret_cast<uint4*>(b + o) = hi;
-        *reinterpret_cast<uint4*>(b + P.b_term + o) = lo;
-      }
+      for (int e = 0; e < 16; ++e) w[e] = col[e * ws] * inv_sw;
+      uint4 t0, t1, t2;
+      split16_e4m3(w, t0, t1, t2);
+      *reinterpret_cast<uint4*>(b + o) = t0;
+      *reinterpret_cast<uint4*>(b + P.b_term + o) = t1;
+      *reinterpret_cast<uint4*>(b + 2 * P.b_term + o) = t2;
+    } else {
+      float w[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) w[e] = col[e * ws];
+      uint4 hi, lo;
+      split8_bf16(w, hi, lo);
+      *reinterpret_cast<uint4*>(b + o) = hi;
+      *reinterpret_cast<uint4*>(b + P.b_term + o) = lo;
     }
   }
 }
@@ -452,13 +453,17 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_tikhonov_tc(
         }
         __syncthreads();
       }
-      issue_raw(P, sm + P.off_raw, mem, v0, nv, 0, wc, m_hat, ldm);
-      cp_commit();
-      for (int kc = 0; kc < nchunks; ++kc) {
-        if (kc + 1 < nchunks)
-          issue_raw(P, sm + P.off_raw + ((kc + 1) & 1) * P.raw_stage, mem, v0, nv, (kc + 1) * TCH, wc, m_hat, ldm);
+      for (int kc = 0; kc < RAW_STAGES - 1; ++kc) {
+        if (kc < nchunks) issue_raw(P, sm + P.off_raw + kc * P.raw_stage, mem, v0, nv, kc * TCH, wc, m_hat, ldm);
         cp_commit();
-        cp_wait1();
+      }
+      for (int kc = 0; kc < nchunks; ++kc) {
+        const int ahead = kc + RAW_STAGES - 1;
+        if (ahead < nchunks)
+          issue_raw(P, sm + P.off_raw + (ahead % RAW_STAGES) * P.raw_stage, mem, v0, nv, ahead * TCH, wc, m_hat,
+                    ldm);
+        cp_commit();
+        cp_wait_ahead();  // chunk kc has landed
         __syncthreads();
         const int set = kc & 1;
         if (pend[set]) {  // the MMAs that last read this term set
@@ -469,7 +474,7 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_tikhonov_tc(
           pend[set] = 0;
         }
         unsigned char* sb = sm + P.off_set + set * P.set_bytes;
-        convert_chunk(P, sm + P.off_raw + (kc & 1) * P.raw_stage, sb, s_n, inv_sw);
+        convert_chunk(P, sm + P.off_raw + (kc % RAW_STAGES) * P.raw_stage, sb, s_n, inv_sw);
         publish();
         if (tid == 0) {
           const uint32_t a0 = sbase + P.off_set + set * P.set_bytes;
