@@ -608,7 +608,9 @@ def learned_comparison(cfg, count, warmup, batch=None, kern=None):
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record()
+    torch.cuda.nvtx.range_push("learned_timed")
     fallback = learned_pass(0, count)
+    torch.cuda.nvtx.range_pop()
     e1.record()
     torch.cuda.synchronize()
     t_learned = e0.elapsed_time(e1)
