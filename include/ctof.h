@@ -311,15 +311,22 @@ ctof_status ctof_learned_reconstruct(ctof_learned net, ctof_kernel k, int batch,
 
 /* Batching form: ADMM reconstructions of `count` independent problems of
  * uneven sizes and optics (one handle each, distinct handles), d_m[i] ->
- * d_mu[i] with the layouts of ctof_reconstruct, all with `params`.  The
- * problems' iteration chains are captured into one CUDA graph, each on its
- * own forked stream so that they run concurrently; the graph is kept and
- * replayed while the same handles, buffers and parameters come back (one
- * cached batch graph per process).  Handles not yet tuned are autotuned first
- * (see ctof_kernel_autotune), so the first call synchronises and must not be
- * made inside a stream capture.  The batch must not overlap other calls on
- * its handles.  Asynchronous after the first call.  Errors: EINVAL (bad or
- * repeated handle, null buffer, handles on different devices), ECUDA. */
+ * d_mu[i] with the layouts of ctof_reconstruct, all with `params`.  The batch
+ * is one captured CUDA graph: per iteration, the x-update of every problem
+ * whose class blocks fit the shared stages of the largest of them runs as one
+ * persistent launch whose thread blocks take (problem, frequency class) items
+ * from a device work queue; the other problems' x-updates and every problem's
+ * FFT / TV stages run on forked streams.  The graph is kept and replayed
+ * while the same handles, buffers and parameters come back (one cached batch
+ * graph per process); results are bit-identical to reconstructing each
+ * problem alone.  Handles not yet tuned are autotuned first (see
+ * ctof_kernel_autotune), so the first call synchronises and must not be made
+ * inside a stream capture.  The batch must not overlap other calls on its
+ * handles.  Asynchronous after the first call; a bounded wait that runs out
+ * in the queued launch is reported on the first queued handle (the wait limit
+ * in force when the graph was made applies).  Errors: EINVAL (bad or
+ * repeated handle, null buffer, handles on different devices), ENOMEM,
+ * ECUDA. */
 ctof_status ctof_reconstruct_batch(int count, const ctof_kernel* ks, const float* const* d_m,
                                    const ctof_solver_params* params, float* const* d_mu, void* stream);
 
@@ -337,16 +344,24 @@ ctof_status ctof_kernel_get_tuning(ctof_kernel k, int* h_pb4);
 /* Precision form: Tikhonov reconstruction of `batch` volumes that share the
  * kernel (the per-frequency regularised inverse of Eq. 7 applied to B
  * measurements at once).  d_m [batch][nt][ny][nx] -> d_mu [batch][nz][ny][nx].
- * CTOF_BF16: b = W_hat^T m_hat on BF16 tensor cores with W_hat and m_hat split
- * into BF16 high and remainder parts (three products, FP32 accumulation);
- * x0 = C b0 from the high-part product alone, then `refine_steps` steps of
+ * CTOF_BF16 / CTOF_FP8E4M3: per frequency class and 16 volumes, b = W_hat^T
+ * m_hat as one tcgen05 tensor-core GEMM with FP32 accumulation, the operands
+ * split into terms whose sum reproduces the FP32 values (BF16: high +
+ * remainder, three products; FP8 e4m3: s (q0 + q1/16 + q2/256) with s
+ * mapping the block's largest magnitude to 448, per frequency class for
+ * W_hat and per right-hand side for m_hat, six products); x0 = C b0 from the
+ * first product alone, then `refine_steps` steps of
  * x += C (b - (G + lambda I) x) with C = (G + lambda I)^-1 from the FP64
- * Cholesky factor (stored FP32).  CTOF_FP32: the plain FP32 per-volume path
- * (ctof_reconstruct with CTOF_SOLVER_TIKHONOV) for comparison.  CTOF_FP8E4M3:
- * EUNSUPPORTED (not built).  lambda = lambda_rel * gram_max_diag; *lambda_out
- * (optional) receives it.  The first BF16 call builds the BF16 tables (2 x 2
- * bytes per W_hat entry); the batch workspace (spectra of batch x nt planes)
- * is allocated on first use and kept.  Asynchronous. */
+ * Cholesky factor, those products in TF32 hi/lo on the tensor cores
+ * (FP32-level).  CTOF_FP32: the plain FP32 per-volume path
+ * (ctof_reconstruct with CTOF_SOLVER_TIKHONOV) for comparison.
+ * lambda = lambda_rel * gram_max_diag; *lambda_out (optional) receives it.
+ * The first BF16 / FP8 call for a lambda makes C, G + lambda I and their
+ * tensor-core tables (per class ~4 nz^2 x 4 bytes plus 2 nz z4 x 4); the batch
+ * workspace (spectra of batch x nt planes) is allocated on first use and
+ * kept.  Asynchronous; a bounded device wait that runs out is reported by
+ * ctof_sync_status.  Errors: EINVAL, EUNSUPPORTED (class block too large for
+ * the kernel's shared memory), ENOMEM, ECUDA. */
 ctof_status ctof_reconstruct_batch_tikhonov(ctof_kernel k, int batch, const float* d_m, int precision,
                                             int refine_steps, double lambda_rel, float* d_mu,
                                             double* lambda_out, void* stream);
