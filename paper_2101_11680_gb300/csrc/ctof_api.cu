@@ -222,7 +222,8 @@ ctof_status ensure_events(ctof_kernel_s* k, int count) {
 // and keeps the fastest.  Synchronous; must run outside stream capture.
 ctof_status autotune(ctof_kernel_s* k, cudaStream_t st) {
   if (k->tuned) return CTOF_OK;
-  const int cands[3] = {8, 16, 32};
+  // tile codes: 8 / 16 / 32 planes in 32-column tiles, 100 + 8 / 16 in 16-column tiles
+  const int cands[5] = {8, 16, 32, 108, 116};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CTOF_CUDA_TRY(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -239,7 +240,7 @@ ctof_status autotune(ctof_kernel_s* k, cudaStream_t st) {
   for (int use = 0; use < 4 && s == CTOF_OK; ++use) {
     float best_ms = 1e30f;
     int best = 16;
-    for (int ci = 0; ci < 3 && s == CTOF_OK; ++ci) {
+    for (int ci = 0; ci < 5 && s == CTOF_OK; ++ci) {
       const int pb = cands[ci];
       auto launch = [&]() -> ctof_status {
         switch (use) {

@@ -30,9 +30,10 @@
 
 namespace {
 
-// Column-pass tiles hold NC = 32 columns: KB kx-columns x PB planes, with
-// PB in {8, 16, 32} chosen per handle and use by the autotuner.
-constexpr int NC = 32;
+// Column-pass tiles hold NC = 32 or 16 columns: KB kx-columns x PB planes;
+// the tile shape (NC, PB) is chosen per handle and use by the autotuner
+// (tile code PB for NC = 32, 100 + PB for NC = 16: smaller tiles, more CTAs
+// per SM).
 constexpr int COL_THREADS = 256;
 constexpr int ROW_WARPS = 8;
 
@@ -430,7 +431,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restri
 // ------------------------------------------------------------- columns ----
 
 // Forward C2C along y: inter[row][kx][LP] (rows_in rows, zero beyond) -> out[ky h + kx][ldf].
-template <int P, int PB>
+template <int P, int PB, int NC>
 __global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restrict__ inter, int nplanes,
                                                           int rows_in, int h, int hp,
                                                           float2* __restrict__ out, int ldf,
@@ -473,7 +474,7 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restri
 }
 
 // Inverse C2C along y: in[ky h + kx][ldf] -> inter[row][kx][LP] for the first rows_out rows.
-template <int P, int PB>
+template <int P, int PB, int NC>
 __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restrict__ in, int ldf, int nplanes,
                                                           int rows_out, int h, int hp,
                                                           float2* __restrict__ inter,
@@ -521,7 +522,7 @@ __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restri
 size_t row_smem(int p) {
   return (size_t)(tw_count(p) + (p / 2 + 1) * SH_LD + ROW_WARPS * (p + 2)) * sizeof(float2);
 }
-size_t col_smem(int p) { return (size_t)(tw_count(p) + p * (NC + 1)) * sizeof(float2); }
+size_t col_smem(int p, int nc) { return (size_t)(tw_count(p) + p * (nc + 1)) * sizeof(float2); }
 
 template <typename F>
 cudaError_t allow_smem(F* fn, size_t bytes) {
@@ -585,30 +586,48 @@ ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* 
   return CTOF_OK;
 }
 
+#define CTOF_COLS_LAUNCH(KERN, ...)                                                          \
+  do {                                                                                       \
+    const int pb = code >= 100 ? code - 100 : code, nc = code >= 100 ? 16 : 32;              \
+    const size_t sm = col_smem(k->p, nc);                                                    \
+    dim3 grid(ctof_div_up(k->h, nc / pb), ctof_div_up(nplanes, pb));                        \
+    switch (code) {                                                                          \
+      case 32:                                                                               \
+        CTOF_P_SWITCH(k->p, {                                                                \
+          CTOF_CUDA_TRY(allow_smem(KERN<P_, 32, 32>, sm));                                   \
+          KERN<P_, 32, 32><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__);                      \
+        });                                                                                  \
+        break;                                                                               \
+      case 16:                                                                               \
+        CTOF_P_SWITCH(k->p, {                                                                \
+          CTOF_CUDA_TRY(allow_smem(KERN<P_, 16, 32>, sm));                                   \
+          KERN<P_, 16, 32><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__);                      \
+        });                                                                                  \
+        break;                                                                               \
+      case 116:                                                                              \
+        CTOF_P_SWITCH(k->p, {                                                                \
+          CTOF_CUDA_TRY(allow_smem(KERN<P_, 16, 16>, sm));                                   \
+          KERN<P_, 16, 16><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__);                      \
+        });                                                                                  \
+        break;                                                                               \
+      case 108:                                                                              \
+        CTOF_P_SWITCH(k->p, {                                                                \
+          CTOF_CUDA_TRY(allow_smem(KERN<P_, 8, 16>, sm));                                    \
+          KERN<P_, 8, 16><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__);                       \
+        });                                                                                  \
+        break;                                                                               \
+      default:                                                                               \
+        CTOF_P_SWITCH(k->p, {                                                                \
+          CTOF_CUDA_TRY(allow_smem(KERN<P_, 8, 32>, sm));                                    \
+          KERN<P_, 8, 32><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__);                       \
+        });                                                                                  \
+    }                                                                                        \
+  } while (0)
+
 ctof_status fft_cols_forward_pb(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows_in, float2* out,
-                                int ldf, int pb, cudaStream_t st) {
+                                int ldf, int code, cudaStream_t st) {
   if (nplanes <= 0) return CTOF_OK;
-  const size_t sm = col_smem(k->p);
-  dim3 grid(ctof_div_up(k->h, NC / pb), ctof_div_up(nplanes, pb));
-  switch (pb) {
-    case 32:
-      CTOF_P_SWITCH(k->p, {
-        CTOF_CUDA_TRY(allow_smem(k_cols_fwd<P_, 32>, sm));
-        k_cols_fwd<P_, 32><<<grid, COL_THREADS, sm, st>>>(inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
-      });
-      break;
-    case 16:
-      CTOF_P_SWITCH(k->p, {
-        CTOF_CUDA_TRY(allow_smem(k_cols_fwd<P_, 16>, sm));
-        k_cols_fwd<P_, 16><<<grid, COL_THREADS, sm, st>>>(inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
-      });
-      break;
-    default:
-      CTOF_P_SWITCH(k->p, {
-        CTOF_CUDA_TRY(allow_smem(k_cols_fwd<P_, 8>, sm));
-        k_cols_fwd<P_, 8><<<grid, COL_THREADS, sm, st>>>(inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
-      });
-  }
+  CTOF_COLS_LAUNCH(k_cols_fwd, inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
@@ -620,29 +639,9 @@ ctof_status fft_cols_forward(const ctof_kernel_s* k, const float2* inter, int np
 }
 
 ctof_status fft_cols_inverse_pb(const ctof_kernel_s* k, const float2* in, int ldf, int nplanes, int rows_out,
-                                float2* inter, int pb, cudaStream_t st) {
+                                float2* inter, int code, cudaStream_t st) {
   if (nplanes <= 0) return CTOF_OK;
-  const size_t sm = col_smem(k->p);
-  dim3 grid(ctof_div_up(k->h, NC / pb), ctof_div_up(nplanes, pb));
-  switch (pb) {
-    case 32:
-      CTOF_P_SWITCH(k->p, {
-        CTOF_CUDA_TRY(allow_smem(k_cols_inv<P_, 32>, sm));
-        k_cols_inv<P_, 32><<<grid, COL_THREADS, sm, st>>>(in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
-      });
-      break;
-    case 16:
-      CTOF_P_SWITCH(k->p, {
-        CTOF_CUDA_TRY(allow_smem(k_cols_inv<P_, 16>, sm));
-        k_cols_inv<P_, 16><<<grid, COL_THREADS, sm, st>>>(in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
-      });
-      break;
-    default:
-      CTOF_P_SWITCH(k->p, {
-        CTOF_CUDA_TRY(allow_smem(k_cols_inv<P_, 8>, sm));
-        k_cols_inv<P_, 8><<<grid, COL_THREADS, sm, st>>>(in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
-      });
-  }
+  CTOF_COLS_LAUNCH(k_cols_inv, in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
