@@ -704,7 +704,7 @@ ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, 
   const size_t wa_per = contract_admm_pipe_floats(nt, nz, 0), ha_per = contract_admm_pipe_floats(nt, nz, 1);
   const size_t o_wa = wa_per ? cv.take<float>((size_t)k->nclass * wa_per) : 0;
   const size_t o_ha = wa_per ? cv.take<float>((size_t)k->nclass * ha_per) : 0;
-  const size_t o_tw = cv.take<float2>(P);
+  const size_t o_tw = cv.take<float2>(fft_twiddle_count(P));
   const size_t o_st = cv.take<float2>((size_t)k->nf * k->ldt);
   const size_t o_st2 = cv.take<float2>((size_t)k->nf * k->ldt);
   const size_t o_sz = cv.take<float2>((size_t)k->nf * k->ldz);
@@ -762,9 +762,8 @@ ctof_status build_any(const ctof_optics* optics, const ctof_emission* emission, 
     k->d_w = static_cast<double*>(p);
   }
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  std::vector<float2> tw(P);
-  const double two_pi = 6.283185307179586476925286766559;
-  for (int j = 0; j < P; ++j) tw[j] = make_float2((float)cos(two_pi * j / P), (float)-sin(two_pi * j / P));
+  std::vector<float2> tw(fft_twiddle_count(P));
+  fft_twiddle_table(P, tw.data());
   ctof_status s = CTOF_OK;
   do {
     if (cudaMemsetAsync(k->d_scalars, 0, 16 * sizeof(double), st) != cudaSuccess ||

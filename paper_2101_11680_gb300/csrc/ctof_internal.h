@@ -47,7 +47,7 @@ struct ctof_kernel_s {
   float* d_hinv;       // [nclass][nz][z4]  (ADMM normal matrix inverse, normalised units)
   float* d_what_admm;  // W_hat in the ADMM kernel's block layout [nclass][tm/8][zm/8][64] (or null)
   float* d_hinv_admm;  // H^-1 in the same layout [nclass][zm/8][zm/8][64] (or null)
-  float2* d_tw;        // [p] forward twiddles exp(-2 pi i j / P)
+  float2* d_tw;        // FFT twiddle table (fft_twiddle_table layout)
   double* d_w;         // optional FP64 kernel table [nt][nz][q][q]
 
   float2* d_spec_t;    // [nf][ldt]
@@ -129,6 +129,10 @@ ctof_status take_device_status(ctof_kernel_s* k, cudaStream_t st);
 // ---- fft.cu -------------------------------------------------------------
 // Complex elements of a row-pass intermediate for `rows` rows of `nplanes` planes.
 size_t fft_inter_elems(const ctof_kernel_s* k, int nplanes, int rows);
+// Twiddle table of the lateral FFTs for size p: its length and its host-side
+// construction (FP64 roots rounded to FP32, in the layout the kernels stage).
+int fft_twiddle_count(int p);
+void fft_twiddle_table(int p, float2* out);
 // Forward R2C of planes of real rows [nplanes][rows_in][ld_in] (first cols_in
 // columns used, the rest of the P-wide row is zero) into frequency-major
 // spectra out[f][ldf] (plane index fastest).  Zero rows beyond rows_in.

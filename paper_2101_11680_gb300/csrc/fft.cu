@@ -26,6 +26,9 @@
 // host in double precision and staged in shared memory.
 #include <cuda_runtime.h>
 
+#include <math.h>
+
+#include "bulk.cuh"
 #include "ctof_internal.h"
 
 namespace {
@@ -52,102 +55,186 @@ __device__ __forceinline__ float2 tw_get(const float2* tw, int j) {
   return INV ? make_float2(w.x, -w.y) : w;
 }
 
-// Shared twiddle table: the P roots w^j, then per-lane copies of the values
-// the lanes need at the same time, so that those reads hit distinct banks:
+// Twiddle table, built on the host in this layout and copied to shared memory
+// as is: the P roots w^j, then per-lane copies of the values the lanes need at
+// the same time, so that those reads hit distinct banks:
 // [P + s - 1 + l] = w^(l P / 2s) for the cross-lane stage s (l < s), and
-// [P + 31 + 32 (k2 - 1) + lane] = w^(lane k2) for the register twiddles.
+// [P + 31 + 32 (k - 1) + lane] = w^(lane k) for the register twiddles;
+// padded to an even count (a multiple of 16 bytes).
 __host__ __device__ constexpr int tw_count(int P) { return P + 31 + 32 * (P / 32 - 1); }
+__host__ __device__ constexpr int tw_pad(int P) { return (tw_count(P) + 1) & ~1; }
 
 template <bool INV>
 __device__ __forceinline__ float2 tw_conj(float2 w) {
   return INV ? make_float2(w.x, -w.y) : w;
 }
 
-// 4- and 8-point DFTs in registers, natural order in and out (w = exp(-2 pi i / n),
-// conjugated when INV).
+// Transform values: one column (float2) or two adjacent columns handled by
+// the same lane (cpair, one 16-byte shared-memory access).
+struct cpair {
+  float2 a, b;
+};
+__device__ __forceinline__ float2 vadd(float2 x, float2 y) { return cadd(x, y); }
+__device__ __forceinline__ cpair vadd(cpair x, cpair y) { return {cadd(x.a, y.a), cadd(x.b, y.b)}; }
+__device__ __forceinline__ float2 vsub(float2 x, float2 y) { return csub(x, y); }
+__device__ __forceinline__ cpair vsub(cpair x, cpair y) { return {csub(x.a, y.a), csub(x.b, y.b)}; }
+__device__ __forceinline__ float2 vmul(float2 x, float2 w) { return cmul(x, w); }
+__device__ __forceinline__ cpair vmul(cpair x, float2 w) { return {cmul(x.a, w), cmul(x.b, w)}; }
 template <bool INV>
 __device__ __forceinline__ float2 mul_mi(float2 a) {  // a * (-i), or a * (+i) when INV
   return INV ? make_float2(-a.y, a.x) : make_float2(a.y, -a.x);
 }
-
 template <bool INV>
-__device__ __forceinline__ void dft4(float2& x0, float2& x1, float2& x2, float2& x3) {
-  const float2 s02 = cadd(x0, x2), d02 = csub(x0, x2), s13 = cadd(x1, x3), d13 = mul_mi<INV>(csub(x1, x3));
-  x0 = cadd(s02, s13);
-  x2 = csub(s02, s13);
-  x1 = cadd(d02, d13);
-  x3 = csub(d02, d13);
+__device__ __forceinline__ float2 vmi(float2 a) {
+  return mul_mi<INV>(a);
+}
+template <bool INV>
+__device__ __forceinline__ cpair vmi(cpair a) {
+  return {mul_mi<INV>(a.a), mul_mi<INV>(a.b)};
+}
+__device__ __forceinline__ void vld(float2& v, const float2* p) { v = *p; }
+__device__ __forceinline__ void vld(cpair& v, const float2* p) {
+  const float4 q = *reinterpret_cast<const float4*>(p);
+  v.a = make_float2(q.x, q.y);
+  v.b = make_float2(q.z, q.w);
+}
+__device__ __forceinline__ void vst(float2* p, float2 v) { *p = v; }
+__device__ __forceinline__ void vst(float2* p, cpair v) {
+  *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
+}
+__device__ __forceinline__ void vzero(float2& v) { v = make_float2(0.f, 0.f); }
+__device__ __forceinline__ void vzero(cpair& v) { v.a = v.b = make_float2(0.f, 0.f); }
+__device__ __forceinline__ float2 shfl2(float2 v, int s) {
+  return make_float2(__shfl_xor_sync(0xffffffffu, v.x, s), __shfl_xor_sync(0xffffffffu, v.y, s));
+}
+__device__ __forceinline__ float2 vshfl(float2 v, int s) { return shfl2(v, s); }
+__device__ __forceinline__ cpair vshfl(cpair v, int s) { return {shfl2(v.a, s), shfl2(v.b, s)}; }
+
+// exp(-2 pi i j / n) given as (re, im); conjugated when INV.
+template <bool INV>
+__device__ __forceinline__ float2 root(float re, float im) {
+  return make_float2(re, INV ? -im : im);
 }
 
-template <bool INV>
-__device__ __forceinline__ void dft8(float2 (&x)[8]) {
-  float2 e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6], o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
+// 2-, 4-, 8- and 16-point DFTs in registers with constant twiddles, natural
+// order in and out (w = exp(-2 pi i / n), conjugated when INV).
+template <bool INV, typename T>
+__device__ __forceinline__ void dft2(T& x0, T& x1) {
+  const T s = vadd(x0, x1);
+  x1 = vsub(x0, x1);
+  x0 = s;
+}
+
+template <bool INV, typename T>
+__device__ __forceinline__ void dft4(T& x0, T& x1, T& x2, T& x3) {
+  const T s02 = vadd(x0, x2), d02 = vsub(x0, x2), s13 = vadd(x1, x3), d13 = vmi<INV>(vsub(x1, x3));
+  x0 = vadd(s02, s13);
+  x2 = vsub(s02, s13);
+  x1 = vadd(d02, d13);
+  x3 = vsub(d02, d13);
+}
+
+// Radix-2 step over the 4-point DFTs E, O of the even and odd samples:
+// X[k] = E[k] + w8^k O[k], X[k + 4] = E[k] - w8^k O[k].
+template <bool INV, typename T>
+__device__ __forceinline__ void dft8(T (&x)[8]) {
+  T e0 = x[0], e1 = x[2], e2 = x[4], e3 = x[6], o0 = x[1], o1 = x[3], o2 = x[5], o3 = x[7];
   dft4<INV>(e0, e1, e2, e3);
   dft4<INV>(o0, o1, o2, o3);
-  const float h = 0.70710678118654752f;
-  // w8 o1, w8^2 o2, w8^3 o3 with w8 = (1 - i)/sqrt(2) (conjugated when INV)
-  const float2 t1 = INV ? make_float2(h * (o1.x - o1.y), h * (o1.x + o1.y))
-                        : make_float2(h * (o1.x + o1.y), h * (o1.y - o1.x));
-  const float2 t2 = mul_mi<INV>(o2);
-  const float2 t3 = INV ? make_float2(-h * (o3.x + o3.y), h * (o3.x - o3.y))
-                        : make_float2(h * (o3.y - o3.x), -h * (o3.x + o3.y));
-  x[0] = cadd(e0, o0);
-  x[4] = csub(e0, o0);
-  x[1] = cadd(e1, t1);
-  x[5] = csub(e1, t1);
-  x[2] = cadd(e2, t2);
-  x[6] = csub(e2, t2);
-  x[3] = cadd(e3, t3);
-  x[7] = csub(e3, t3);
+  constexpr float h = 0.70710678118654752f;
+  o1 = vmul(o1, root<INV>(h, -h));
+  o2 = vmi<INV>(o2);
+  o3 = vmul(o3, root<INV>(-h, -h));
+  x[0] = vadd(e0, o0);
+  x[4] = vsub(e0, o0);
+  x[1] = vadd(e1, o1);
+  x[5] = vsub(e1, o1);
+  x[2] = vadd(e2, o2);
+  x[6] = vsub(e2, o2);
+  x[3] = vadd(e3, o3);
+  x[7] = vsub(e3, o3);
+}
+
+// 4 x 4: X[k1 + 4 k2] = sum_n2 w4^(n2 k2) w16^(n2 k1) sum_n1 x[4 n1 + n2] w4^(n1 k1).
+template <bool INV, typename T>
+__device__ __forceinline__ void dft16(T (&x)[16]) {
+#pragma unroll
+  for (int n2 = 0; n2 < 4; ++n2) dft4<INV>(x[n2], x[4 + n2], x[8 + n2], x[12 + n2]);
+  // x[n2 + 4 k1] now holds the inner sum for (n2, k1)
+  constexpr float c1 = 0.92387953251128676f, s1 = 0.38268343236508977f, h = 0.70710678118654752f;
+  x[5] = vmul(x[5], root<INV>(c1, -s1));    // w16^1
+  x[9] = vmul(x[9], root<INV>(h, -h));      // w16^2
+  x[13] = vmul(x[13], root<INV>(s1, -c1));  // w16^3
+  x[6] = vmul(x[6], root<INV>(h, -h));      // w16^2
+  x[10] = vmi<INV>(x[10]);                  // w16^4
+  x[14] = vmul(x[14], root<INV>(-h, -h));   // w16^6
+  x[7] = vmul(x[7], root<INV>(s1, -c1));    // w16^3
+  x[11] = vmul(x[11], root<INV>(-h, -h));   // w16^6
+  x[15] = vmul(x[15], root<INV>(-c1, s1));  // w16^9
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) dft4<INV>(x[4 * k1], x[4 * k1 + 1], x[4 * k1 + 2], x[4 * k1 + 3]);
+  T y[16];
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1)
+#pragma unroll
+    for (int k2 = 0; k2 < 4; ++k2) y[k1 + 4 * k2] = x[4 * k1 + k2];
+#pragma unroll
+  for (int i = 0; i < 16; ++i) x[i] = y[i];
+}
+
+template <int R, bool INV, typename T>
+__device__ __forceinline__ void reg_dft(T (&v)[R]) {
+  if constexpr (R == 2) {
+    dft2<INV>(v[0], v[1]);
+  } else if constexpr (R == 4) {
+    dft4<INV>(v[0], v[1], v[2], v[3]);
+  } else if constexpr (R == 8) {
+    dft8<INV>(v);
+  } else if constexpr (R == 16) {
+    dft16<INV>(v);
+  }
 }
 
 // Scratch slots of the 32-point step for P >= 256 (each a permutation of
-// [0, P)): S[i][l] (register i, lane l) and S2[i][m1][b]; the rotations keep a
-// half-warp's 8-byte accesses on distinct banks (at most 2-way conflicts).
+// [0, P)): S[i][l] (register i, lane l) and S2[i][m1][b].  Eight consecutive
+// lanes always touch eight slots that are distinct mod 8 (conflict-free
+// 16-byte accesses on the column tile's pitch); the rotation in S keeps a
+// half-warp's 8-byte accesses on distinct banks for odd pitches.
 __device__ __forceinline__ int slot_a(int i, int l) { return i * 32 + ((l + 8 * (i & 1)) & 31); }
 __device__ __forceinline__ int slot_c(int i, int m1, int b) {
   const int t = 4 * i + m1;
   return t * 8 + (b ^ (t & 7));
 }
 
-// Length-P DFT held by one warp (see file comment).  INV selects exp(+...).
+// Length-P DFT held by one warp, P = 32 R: lane l register i holds element
+// l + 32 i (of one column, or of each of two columns).  X[k1 + R k2] =
+// sum_l w32^(l k2) w_P^(l k1) sum_i x[l + 32 i] w_R^(i k1): an R-point DFT
+// over the registers (register i then holds k1 = i), the twiddle w_P^(l k1),
+// and a 32-point DFT across the lanes.  INV selects exp(+...).
 // With SCRATCH and P >= 256 (the column passes, whose warps own a tile column
-// to use as scratch) the 32-point DFT across the lanes runs as 4 x 8 points in
-// registers, with two passes through the scratch (P slots `stride` float2
-// apart), instead of five shuffle stages (measured ~10 % faster there; the
-// row passes keep the shuffles, which measured faster for them):
-//   Z[m1 + 4 m2] = sum_b w8^(b m2) w32^(b m1) sum_a y[b + 8 a] w4^(a m1).
-template <int P, bool INV, bool SCRATCH = true>
-__device__ __forceinline__ void warp_fft(float2 (&v)[P / 32], int lane, const float2* tw, float2* scr, int stride) {
+// pair to use as scratch) the 32-point DFT across the lanes runs as 4 x 8
+// points in registers with two passes through the scratch (P slots `stride`
+// float2 apart):
+//   Z[m1 + 4 m2] = sum_b w8^(b m2) w32^(b m1) sum_a y[b + 8 a] w4^(a m1);
+// otherwise as five shuffle stages (DIF, outputs in bit-reversed lane order).
+template <int P, bool INV, bool SCRATCH = true, typename T>
+__device__ __forceinline__ void warp_fft(T (&v)[P / 32], int lane, const float2* tw, float2* scr, int stride) {
   constexpr int R = P / 32;
+  reg_dft<R, INV>(v);
 #pragma unroll
-  for (int s = R / 2; s >= 1; s >>= 1) {
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
-      if ((i & s) == 0) {
-        const float2 a = v[i], b = v[i + s];
-        v[i] = cadd(a, b);
-        v[i + s] = cmul(csub(a, b), tw_get<P, INV>(tw, (i & (s - 1)) * (P / (2 * s))));
-      }
-    }
-  }
-#pragma unroll
-  for (int i = 1; i < R; ++i) {
-    const int k2 = bitrevc(i, ilog2c(R));
-    v[i] = cmul(v[i], tw_conj<INV>(tw[P + 31 + 32 * (k2 - 1) + lane]));
-  }
+  for (int i = 1; i < R; ++i) v[i] = vmul(v[i], tw_conj<INV>(tw[P + 31 + 32 * (i - 1) + lane]));
   if constexpr (SCRATCH && R >= 8) {
     __syncwarp();  // every lane has read its inputs (callers may pass their input column as scratch)
 #pragma unroll
-    for (int i = 0; i < R; ++i) scr[slot_a(i, lane) * stride] = v[i];
+    for (int i = 0; i < R; ++i) vst(scr + slot_a(i, lane) * stride, v[i]);
     __syncwarp();
     const int b = lane & 7;
-    float2 t[R / 4][4];
+    T t[R / 4][4];
 #pragma unroll
     for (int q = 0; q < R / 4; ++q) {
       const int i = (lane >> 3) + 4 * q;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) t[q][a] = scr[slot_a(i, b + 8 * a) * stride];
+      for (int a = 0; a < 4; ++a) vld(t[q][a], scr + slot_a(i, b + 8 * a) * stride);
     }
     __syncwarp();
 #pragma unroll
@@ -155,18 +242,18 @@ __device__ __forceinline__ void warp_fft(float2 (&v)[P / 32], int lane, const fl
       const int i = (lane >> 3) + 4 * q;
       dft4<INV>(t[q][0], t[q][1], t[q][2], t[q][3]);
 #pragma unroll
-      for (int m1 = 1; m1 < 4; ++m1) t[q][m1] = cmul(t[q][m1], tw_get<P, INV>(tw, R * b * m1));
+      for (int m1 = 1; m1 < 4; ++m1) t[q][m1] = vmul(t[q][m1], tw_get<P, INV>(tw, R * b * m1));
 #pragma unroll
-      for (int m1 = 0; m1 < 4; ++m1) scr[slot_c(i, m1, b) * stride] = t[q][m1];
+      for (int m1 = 0; m1 < 4; ++m1) vst(scr + slot_c(i, m1, b) * stride, t[q][m1]);
     }
     __syncwarp();
     const int m1 = lane & 3;
 #pragma unroll
     for (int q = 0; q < R / 8; ++q) {
       const int i = (lane >> 2) + 8 * q;
-      float2 u[8];
+      T u[8];
 #pragma unroll
-      for (int bb = 0; bb < 8; ++bb) u[bb] = scr[slot_c(i, m1, bb) * stride];
+      for (int bb = 0; bb < 8; ++bb) vld(u[bb], scr + slot_c(i, m1, bb) * stride);
       dft8<INV>(u);
 #pragma unroll
       for (int m2 = 0; m2 < 8; ++m2) v[8 * q + m2] = u[m2];
@@ -179,10 +266,8 @@ __device__ __forceinline__ void warp_fft(float2 (&v)[P / 32], int lane, const fl
       const float2 w = tw_conj<INV>(tw[P + s - 1 + (lane & (s - 1))]);
 #pragma unroll
       for (int i = 0; i < R; ++i) {
-        float2 o;
-        o.x = __shfl_xor_sync(0xffffffffu, v[i].x, s);
-        o.y = __shfl_xor_sync(0xffffffffu, v[i].y, s);
-        v[i] = upper ? cmul(csub(o, v[i]), w) : cadd(v[i], o);
+        const T o = vshfl(v[i], s);
+        v[i] = upper ? vmul(vsub(o, v[i]), w) : vadd(v[i], o);
       }
     }
   }
@@ -193,10 +278,10 @@ template <int P, bool SCRATCH = true>
 __device__ __forceinline__ int out_pos(int lane, int i) {
   constexpr int R = P / 32;
   if constexpr (SCRATCH && R >= 8) {
-    // register 8 q + m2 of lane L: k1 = bitrev_R((L >> 2) + 8 q), k2 = (L & 3) + 4 m2
-    return bitrevc((lane >> 2) + 8 * (i >> 3), ilog2c(R)) + R * ((lane & 3) + 4 * (i & 7));
+    // register 8 q + m2 of lane L: k1 = (L >> 2) + 8 q, k2 = (L & 3) + 4 m2
+    return (lane >> 2) + 8 * (i >> 3) + R * ((lane & 3) + 4 * (i & 7));
   } else {
-    return R * brev5(lane) + bitrevc(i, ilog2c(R));
+    return i + R * brev5(lane);
   }
 }
 
@@ -212,21 +297,7 @@ __device__ __forceinline__ int sw_pos(int e) {
 
 template <int P>
 __device__ __forceinline__ void stage_twiddles(float2* s_tw, const float2* tw) {
-  for (int i = threadIdx.x; i < tw_count(P); i += blockDim.x) {
-    int j;
-    if (i < P) {
-      j = i;
-    } else if (i < P + 31) {
-      const int e = i - P;
-      int s = 1;
-      while (2 * s - 1 <= e) s *= 2;  // stage s holds entries s-1 .. 2s-2
-      j = (e - (s - 1)) * (P / (2 * s));
-    } else {
-      const int e = i - P - 31;
-      j = ((e & 31) * (e / 32 + 1)) & (P - 1);
-    }
-    s_tw[i] = tw[j];
-  }
+  for (int i = threadIdx.x; i < tw_pad(P); i += blockDim.x) s_tw[i] = tw[i];
 }
 
 // ---------------------------------------------------------------- rows ----
@@ -295,7 +366,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_fwd(const float* __rest
   constexpr int R = P / 32;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
-  float2* s_h = smem + tw_count(P);
+  float2* s_h = smem + tw_pad(P);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* buf = s_h + (P / 2 + 1) * SH_LD + warp * (P + 2);
   stage_twiddles<P>(s_tw, tw);
@@ -334,7 +405,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const float2* __res
   constexpr int R = P / 32;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
-  float2* s_h = smem + tw_count(P);
+  float2* s_h = smem + tw_pad(P);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* buf = s_h + (P / 2 + 1) * SH_LD + warp * (P + 2);
   stage_twiddles<P>(s_tw, tw);
@@ -374,7 +445,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restri
   constexpr int R = P / 32;
   extern __shared__ float2 smem[];
   float2* s_tw = smem;
-  float2* s_h = smem + tw_count(P);
+  float2* s_h = smem + tw_pad(P);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   float2* buf = s_h + (P / 2 + 1) * SH_LD + warp * (P + 2);
   stage_twiddles<P>(s_tw, tw);
@@ -430,99 +501,225 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restri
 
 // ------------------------------------------------------------- columns ----
 
+// Column-pass tile: P rows x NC columns (KB = NC / PB kx-columns x PB
+// consecutive planes), row pitch NC + 2 float2: rows start on 16-byte
+// boundaries (targets and sources of bulk copies), and eight rows that are
+// distinct mod 8 put a quarter-warp's 16-byte accesses on distinct bank
+// groups.  Each warp transforms two adjacent columns at once (cpair).
+template <int NC>
+__host__ __device__ constexpr int col_ld() {
+  return NC + 2;
+}
+
+// Tile row of transform output e: a permutation of [0, P) under which the
+// eight outputs that eight consecutive lanes write with one register land in
+// rows distinct mod 8.  4 x 8 path (R >= 8): e = k1 + R k2 with k1 = (L >> 2)
+// + 8 q and k2 = (L & 3) + 4 m2, so bits 1-2 of k1 (zero there) take k2's low
+// bits.  Shuffle path: e = i + 4 R rev3(L), so the low bits take the three
+// bits above 4 R.
+template <int P>
+__device__ __forceinline__ int col_row(int e) {
+  constexpr int R = P / 32;
+  if constexpr (R >= 8) {
+    return e ^ (((e / R) & 3) << 1);
+  } else if constexpr (R >= 2) {
+    return e ^ ((e >> (ilog2c(R) + 2)) & 7);
+  } else {
+    return e ^ ((e >> 3) & 3);
+  }
+}
+
+// Shared memory of a column pass: [mbarrier, 16 B][twiddles][tile].
+__host__ __device__ constexpr size_t col_smem_bytes(int P, int NC) {
+  return 16 + ((size_t)tw_pad(P) + (size_t)P * (NC + 2)) * sizeof(float2);
+}
+
+// Stages the tile's runs (`nrun` runs of `run` bytes; run r goes from
+// src(r) to dst(r)) and the twiddles by bulk copies completing on one
+// mbarrier.  Block-wide; false (and the handle's status flag set) when the
+// copies did not land within max_polls polls.
+template <int P, typename Src, typename Dst>
+__device__ __forceinline__ bool col_stage_in(uint64_t* bar, float2* s_tw, const float2* tw, int nrun, unsigned run,
+                                             Src src, Dst dst, int* flag, long long max_polls) {
+  if (threadIdx.x == 0) {
+    bulk::bar_init(bar, 1);
+    bulk::arrive_expect(bar, (unsigned)nrun * run + tw_pad(P) * (unsigned)sizeof(float2));
+    bulk::g2s(s_tw, tw, tw_pad(P) * sizeof(float2), bar);
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < nrun; r += COL_THREADS) bulk::g2s(dst(r), src(r), run, bar);
+  const bool ok = __syncthreads_and(bulk::wait(bar, 0, max_polls));
+  if (!ok) {
+    if (threadIdx.x == 0) atomicOr(flag, 1);
+    bulk::wait(bar, 0, bulk::DRAIN_POLLS);
+  }
+  return ok;
+}
+
+// Writes the tile's runs back: `nrun` runs of np planes, run r from src(r) to
+// dst(r); the even part by bulk copies, an odd last plane by a plain store.
+template <typename Src, typename Dst>
+__device__ __forceinline__ void col_stage_out(int nrun, int np, Src src, Dst dst) {
+  bulk::fence_smem();  // the tile writes of this thread, before the copies read them
+  __syncthreads();
+  const int ne = np & ~1;
+  bool issued = false;
+  for (int r = threadIdx.x; r < nrun; r += COL_THREADS) {
+    const float2* s = src(r);
+    float2* d = dst(r);
+    if (ne) {
+      bulk::s2g(d, s, (unsigned)ne * sizeof(float2));
+      issued = true;
+    }
+    if (np & 1) d[ne] = s[ne];
+  }
+  if (issued) {
+    bulk::commit();
+    bulk::wait_read_all();
+  }
+}
+
 // Forward C2C along y: inter[row][kx][LP] (rows_in rows, zero beyond) -> out[ky h + kx][ldf].
-template <int P, int PB, int NC>
+// BULK: tile staged in and out by bulk copies (16-byte aligned buffers, even
+// ldf); otherwise element by element.
+template <int P, int PB, int NC, bool BULK>
 __global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restrict__ inter, int nplanes,
                                                           int rows_in, int h, int hp,
                                                           float2* __restrict__ out, int ldf,
-                                                          const float2* __restrict__ tw) {
+                                                          const float2* __restrict__ tw, int* __restrict__ flag,
+                                                          long long max_polls) {
   constexpr int R = P / 32;
   constexpr int KB = NC / PB;
-  constexpr int LDT = NC + 1;
-  extern __shared__ float2 smem[];
-  float2* s_tw = smem;
-  float2* tile = smem + tw_count(P);
+  constexpr int LDT = col_ld<NC>();
+  extern __shared__ float4 col_smem4[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(col_smem4);
+  float2* s_tw = reinterpret_cast<float2*>(col_smem4 + 1);
+  float2* tile = s_tw + tw_pad(P);
   const int kx0 = blockIdx.x * KB, pl0 = blockIdx.y * PB;
   const int LP = plane_ld(nplanes);
-  stage_twiddles<P>(s_tw, tw);
-  for (int idx = threadIdx.x; idx < rows_in * NC; idx += COL_THREADS) {
-    const int row = idx / NC, cc = idx % NC;
-    const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
-    float2 val = make_float2(0.f, 0.f);
-    if (kx < h && pl < nplanes) val = inter[((size_t)row * hp + kx) * LP + pl];
-    tile[row * LDT + cc] = val;
+  const int kb = min(KB, h - kx0), np = min(PB, nplanes - pl0);
+  if constexpr (BULK) {
+    const unsigned run = (unsigned)((np + 1) & ~1) * sizeof(float2);
+    if (!col_stage_in<P>(
+            bar, s_tw, tw, rows_in * kb, run,
+            [&](int r) { return inter + ((size_t)(r / kb) * hp + kx0 + r % kb) * LP + pl0; },
+            [&](int r) { return tile + (r / kb) * LDT + (r % kb) * PB; }, flag, max_polls))
+      return;
+  } else {
+    for (int i = threadIdx.x; i < tw_pad(P); i += COL_THREADS) s_tw[i] = tw[i];
+    for (int idx = threadIdx.x; idx < rows_in * NC; idx += COL_THREADS) {
+      const int row = idx / NC, cc = idx % NC;
+      const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
+      float2 val = make_float2(0.f, 0.f);
+      if (kx < h && pl < nplanes) val = inter[((size_t)row * hp + kx) * LP + pl];
+      tile[row * LDT + cc] = val;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int c = warp; c < NC; c += COL_THREADS / 32) {
-    float2 v[R];
+  for (int c = 2 * warp; c < NC; c += 2 * (COL_THREADS / 32)) {
+    cpair v[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int y = lane + 32 * i;
-      v[i] = y < rows_in ? tile[y * LDT + c] : make_float2(0.f, 0.f);
+      if (y < rows_in)
+        vld(v[i], tile + y * LDT + c);
+      else
+        vzero(v[i]);
     }
     warp_fft<P, false>(v, lane, s_tw, tile + c, LDT);
 #pragma unroll
-    for (int i = 0; i < R; ++i) tile[sw_pos<P>(out_pos<P>(lane, i)) * LDT + c] = v[i];
+    for (int i = 0; i < R; ++i) vst(tile + col_row<P>(out_pos<P>(lane, i)) * LDT + c, v[i]);
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
-    const int ky = idx / NC, cc = idx % NC;
-    const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
-    if (kx < h && pl < nplanes) out[((size_t)ky * h + kx) * ldf + pl] = tile[sw_pos<P>(ky) * LDT + cc];
+  if constexpr (BULK) {
+    col_stage_out(
+        P * kb, np, [&](int r) { return tile + col_row<P>(r / kb) * LDT + (r % kb) * PB; },
+        [&](int r) { return out + ((size_t)(r / kb) * h + kx0 + r % kb) * ldf + pl0; });
+  } else {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
+      const int ky = idx / NC, cc = idx % NC;
+      const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
+      if (kx < h && pl < nplanes) out[((size_t)ky * h + kx) * ldf + pl] = tile[col_row<P>(ky) * LDT + cc];
+    }
   }
 }
 
 // Inverse C2C along y: in[ky h + kx][ldf] -> inter[row][kx][LP] for the first rows_out rows.
-template <int P, int PB, int NC>
+template <int P, int PB, int NC, bool BULK>
 __global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restrict__ in, int ldf, int nplanes,
                                                           int rows_out, int h, int hp,
                                                           float2* __restrict__ inter,
-                                                          const float2* __restrict__ tw) {
+                                                          const float2* __restrict__ tw, int* __restrict__ flag,
+                                                          long long max_polls) {
   constexpr int R = P / 32;
   constexpr int KB = NC / PB;
-  constexpr int LDT = NC + 1;
-  extern __shared__ float2 smem[];
-  float2* s_tw = smem;
-  float2* tile = smem + tw_count(P);
+  constexpr int LDT = col_ld<NC>();
+  extern __shared__ float4 col_smem4[];
+  uint64_t* bar = reinterpret_cast<uint64_t*>(col_smem4);
+  float2* s_tw = reinterpret_cast<float2*>(col_smem4 + 1);
+  float2* tile = s_tw + tw_pad(P);
   const int kx0 = blockIdx.x * KB, pl0 = blockIdx.y * PB;
   const int LP = plane_ld(nplanes);
-  stage_twiddles<P>(s_tw, tw);
-  for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
-    const int ky = idx / NC, cc = idx % NC;
-    const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
-    float2 val = make_float2(0.f, 0.f);
-    if (kx < h && pl < nplanes) val = in[((size_t)ky * h + kx) * ldf + pl];
-    tile[ky * LDT + cc] = val;
+  const int kb = min(KB, h - kx0), np = min(PB, nplanes - pl0);
+  if constexpr (BULK) {
+    // runs rounded up to an even plane count stay inside the ldf pitch (a multiple of 8)
+    const unsigned run = (unsigned)((np + 1) & ~1) * sizeof(float2);
+    if (!col_stage_in<P>(
+            bar, s_tw, tw, P * kb, run,
+            [&](int r) { return in + ((size_t)(r / kb) * h + kx0 + r % kb) * ldf + pl0; },
+            [&](int r) { return tile + (r / kb) * LDT + (r % kb) * PB; }, flag, max_polls))
+      return;
+  } else {
+    for (int i = threadIdx.x; i < tw_pad(P); i += COL_THREADS) s_tw[i] = tw[i];
+    for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
+      const int ky = idx / NC, cc = idx % NC;
+      const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
+      float2 val = make_float2(0.f, 0.f);
+      if (kx < h && pl < nplanes) val = in[((size_t)ky * h + kx) * ldf + pl];
+      tile[ky * LDT + cc] = val;
+    }
+    __syncthreads();
   }
-  __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int c = warp; c < NC; c += COL_THREADS / 32) {
-    float2 v[R];
+  for (int c = 2 * warp; c < NC; c += 2 * (COL_THREADS / 32)) {
+    cpair v[R];
 #pragma unroll
-    for (int i = 0; i < R; ++i) v[i] = tile[(lane + 32 * i) * LDT + c];
-    __syncwarp();
+    for (int i = 0; i < R; ++i) vld(v[i], tile + (lane + 32 * i) * LDT + c);
     warp_fft<P, true>(v, lane, s_tw, tile + c, LDT);
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int y = out_pos<P>(lane, i);
-      if (y < rows_out) tile[sw_pos<P>(y) * LDT + c] = v[i];
+      if (y < rows_out) vst(tile + col_row<P>(y) * LDT + c, v[i]);
     }
   }
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < rows_out * NC; idx += COL_THREADS) {
-    const int row = idx / NC, cc = idx % NC;
-    const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
-    if (kx < h && pl < nplanes) inter[((size_t)row * hp + kx) * LP + pl] = tile[sw_pos<P>(row) * LDT + cc];
+  if constexpr (BULK) {
+    col_stage_out(
+        rows_out * kb, np, [&](int r) { return tile + col_row<P>(r / kb) * LDT + (r % kb) * PB; },
+        [&](int r) { return inter + ((size_t)(r / kb) * hp + kx0 + r % kb) * LP + pl0; });
+  } else {
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < rows_out * NC; idx += COL_THREADS) {
+      const int row = idx / NC, cc = idx % NC;
+      const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
+      if (kx < h && pl < nplanes) inter[((size_t)row * hp + kx) * LP + pl] = tile[col_row<P>(row) * LDT + cc];
+    }
   }
 }
 
 // ------------------------------------------------------------ launchers ----
 
 size_t row_smem(int p) {
-  return (size_t)(tw_count(p) + (p / 2 + 1) * SH_LD + ROW_WARPS * (p + 2)) * sizeof(float2);
+  return (size_t)(tw_pad(p) + (p / 2 + 1) * SH_LD + ROW_WARPS * (p + 2)) * sizeof(float2);
 }
-size_t col_smem(int p, int nc) { return (size_t)(tw_count(p) + p * (nc + 1)) * sizeof(float2); }
+
+// Bulk staging needs 16-byte aligned buffers and an even spectrum pitch (the
+// intermediate's plane pitch is a multiple of 16).
+bool cols_bulk_ok(const void* a, const void* b, const void* tw, int ldf) {
+  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(tw)) &
+          15) == 0 &&
+         (ldf & 1) == 0;
+}
 
 template <typename F>
 cudaError_t allow_smem(F* fn, size_t bytes) {
@@ -586,48 +783,35 @@ ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* 
   return CTOF_OK;
 }
 
-#define CTOF_COLS_LAUNCH(KERN, ...)                                                          \
-  do {                                                                                       \
-    const int pb = code >= 100 ? code - 100 : code, nc = code >= 100 ? 16 : 32;              \
-    const size_t sm = col_smem(k->p, nc);                                                    \
-    dim3 grid(ctof_div_up(k->h, nc / pb), ctof_div_up(nplanes, pb));                        \
-    switch (code) {                                                                          \
-      case 32:                                                                               \
-        CTOF_P_SWITCH(k->p, {                                                                \
-          CTOF_CUDA_TRY(allow_smem(KERN<P_, 32, 32>, sm));                                   \
-          KERN<P_, 32, 32><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__);                      \
-        });                                                                                  \
-        break;                                                                               \
-      case 16:                                                                               \
-        CTOF_P_SWITCH(k->p, {                                                                \
-          CTOF_CUDA_TRY(allow_smem(KERN<P_, 16, 32>, sm));                                   \
-          KERN<P_, 16, 32><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__);                      \
-        });                                                                                  \
-        break;                                                                               \
-      case 116:                                                                              \
-        CTOF_P_SWITCH(k->p, {                                                                \
-          CTOF_CUDA_TRY(allow_smem(KERN<P_, 16, 16>, sm));                                   \
-          KERN<P_, 16, 16><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__);                      \
-        });                                                                                  \
-        break;                                                                               \
-      case 108:                                                                              \
-        CTOF_P_SWITCH(k->p, {                                                                \
-          CTOF_CUDA_TRY(allow_smem(KERN<P_, 8, 16>, sm));                                    \
-          KERN<P_, 8, 16><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__);                       \
-        });                                                                                  \
-        break;                                                                               \
-      default:                                                                               \
-        CTOF_P_SWITCH(k->p, {                                                                \
-          CTOF_CUDA_TRY(allow_smem(KERN<P_, 8, 32>, sm));                                    \
-          KERN<P_, 8, 32><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__);                       \
-        });                                                                                  \
-    }                                                                                        \
+// Tile codes: PB for NC = 32 (8, 16, 32), 100 + PB for NC = 16 (108, 116);
+// code 0 = the element-wise variant (NC = 32, PB = 8) for buffers the bulk
+// copies cannot take.
+#define CTOF_COLS_CASE(KERN, PB_, NC_, BULK_, ...)                       \
+  CTOF_P_SWITCH(k->p, {                                                  \
+    CTOF_CUDA_TRY(allow_smem(KERN<P_, PB_, NC_, BULK_>, sm));            \
+    KERN<P_, PB_, NC_, BULK_><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__); \
+  })
+
+#define CTOF_COLS_LAUNCH(KERN, ...)                                                         \
+  do {                                                                                      \
+    const int pb = code == 0 ? 8 : (code >= 100 ? code - 100 : code), nc = code >= 100 ? 16 : 32; \
+    const size_t sm = col_smem_bytes(k->p, nc);                                             \
+    dim3 grid(ctof_div_up(k->h, nc / pb), ctof_div_up(nplanes, pb));                       \
+    switch (code) {                                                                         \
+      case 0: CTOF_COLS_CASE(KERN, 8, 32, false, __VA_ARGS__); break;                       \
+      case 32: CTOF_COLS_CASE(KERN, 32, 32, true, __VA_ARGS__); break;                      \
+      case 16: CTOF_COLS_CASE(KERN, 16, 32, true, __VA_ARGS__); break;                      \
+      case 116: CTOF_COLS_CASE(KERN, 16, 16, true, __VA_ARGS__); break;                     \
+      case 108: CTOF_COLS_CASE(KERN, 8, 16, true, __VA_ARGS__); break;                      \
+      default: CTOF_COLS_CASE(KERN, 8, 32, true, __VA_ARGS__);                              \
+    }                                                                                       \
   } while (0)
 
 ctof_status fft_cols_forward_pb(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows_in, float2* out,
                                 int ldf, int code, cudaStream_t st) {
   if (nplanes <= 0) return CTOF_OK;
-  CTOF_COLS_LAUNCH(k_cols_fwd, inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw);
+  if (!cols_bulk_ok(inter, out, k->d_tw, ldf)) code = 0;
+  CTOF_COLS_LAUNCH(k_cols_fwd, inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw, k->d_flags, k->max_polls);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
@@ -641,7 +825,8 @@ ctof_status fft_cols_forward(const ctof_kernel_s* k, const float2* inter, int np
 ctof_status fft_cols_inverse_pb(const ctof_kernel_s* k, const float2* in, int ldf, int nplanes, int rows_out,
                                 float2* inter, int code, cudaStream_t st) {
   if (nplanes <= 0) return CTOF_OK;
-  CTOF_COLS_LAUNCH(k_cols_inv, in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw);
+  if (!cols_bulk_ok(in, inter, k->d_tw, ldf)) code = 0;
+  CTOF_COLS_LAUNCH(k_cols_inv, in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw, k->d_flags, k->max_polls);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
@@ -650,6 +835,27 @@ ctof_status fft_cols_inverse(const ctof_kernel_s* k, const float2* in, int ldf, 
                              float2* inter, cudaStream_t st) {
   const int pb = (nplanes == k->nt) ? k->tune_pb[1] : k->tune_pb[3];
   return fft_cols_inverse_pb(k, in, ldf, nplanes, rows_out, inter, pb, st);
+}
+
+int fft_twiddle_count(int p) { return tw_pad(p); }
+
+void fft_twiddle_table(int p, float2* out) {
+  const double two_pi = 6.283185307179586476925286766559;
+  for (int i = 0; i < tw_pad(p); ++i) {
+    int j = 0;
+    if (i < p) {
+      j = i;
+    } else if (i < p + 31) {
+      const int e = i - p;
+      int s = 1;
+      while (2 * s - 1 <= e) s *= 2;  // stage s holds entries s-1 .. 2s-2
+      j = (e - (s - 1)) * (p / (2 * s));
+    } else if (i < tw_count(p)) {
+      const int e = i - p - 31;
+      j = ((e & 31) * (e / 32 + 1)) & (p - 1);
+    }
+    out[i] = make_float2((float)cos(two_pi * j / p), (float)-sin(two_pi * j / p));
+  }
 }
 
 size_t fft_inter_elems(const ctof_kernel_s* k, int nplanes, int rows) {
