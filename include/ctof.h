@@ -330,8 +330,7 @@ ctof_status ctof_learned_reconstruct(ctof_learned net, ctof_kernel k, int batch,
 ctof_status ctof_reconstruct_batch(int count, const ctof_kernel* ks, const float* const* d_m,
                                    const ctof_solver_params* params, float* const* d_mu, void* stream);
 
-/* Autotuner: times the column-FFT tile (32 columns of 8, 16 or 32 planes, or
- * 16 columns of 8 or 16 planes) for each of the four column-pass shapes of an
+/* Autotuner: times the column-FFT tile (32 or 16 columns of 8 or 16 planes) for each of the four column-pass shapes of an
  * ADMM iteration on this handle and keeps the fastest; the results are
  * bit-identical for every tile, only the speed changes.  Runs automatically
  * before the first ADMM graph capture of a handle.  Synchronous; not inside a
@@ -339,7 +338,7 @@ ctof_status ctof_reconstruct_batch(int count, const ctof_kernel* ks, const float
 ctof_status ctof_kernel_autotune(ctof_kernel k, void* stream);
 
 /* The tuned tiles [T-side forward, T-side inverse, Z-side forward, Z-side
- * inverse] as tile codes: 8 / 16 / 32 = 32-column tiles of that many planes,
+ * inverse] as tile codes: 8 / 16 = 32-column tiles of that many planes,
  * 108 / 116 = 16-column tiles of 8 / 16 planes; EUNSUPPORTED (defaults 16
  * reported) if not tuned yet. */
 ctof_status ctof_kernel_get_tuning(ctof_kernel k, int* h_pb4);

@@ -1,7 +1,7 @@
 // Bulk-copy (TMA engine) helpers: mbarrier-completed global -> shared copies
-// and bulk-group shared -> global copies (PTX cp.async.bulk, sm_90 and later).
-// Addresses and sizes of every copy are multiples of 16 bytes.  Internal
-// header: not part of the C ABI.
+// and bulk-group shared -> global copies (PTX cp.async.bulk and
+// cp.async.bulk.tensor, sm_90 and later).  Addresses and sizes of every plain
+// bulk copy are multiples of 16 bytes.  Internal header: not part of the C ABI.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -47,6 +47,17 @@ __device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity, long long m
   return false;
 }
 
+// Block-wide wait: thread 0 polls (at most max_polls times) while the other
+// threads sleep at the block barrier; after it each thread acquires the
+// completed phase with one poll of its own.  True when the phase completed.
+__device__ __forceinline__ bool block_wait(uint64_t* bar, uint32_t parity, long long max_polls) {
+  int ok = 1;
+  if (threadIdx.x == 0) ok = wait(bar, parity, max_polls) ? 1 : 0;
+  ok = __syncthreads_and(ok);
+  if (ok && threadIdx.x != 0) (void)try_wait(bar, parity);
+  return ok != 0;
+}
+
 // Global -> shared, completing `bytes` on bar.
 __device__ __forceinline__ void g2s(void* dst, const void* src, unsigned bytes, uint64_t* bar) {
   asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
@@ -61,10 +72,33 @@ __device__ __forceinline__ void s2g(void* dst, const void* src, unsigned bytes) 
                : "memory");
 }
 
+// Tensor-map (tiled) copies of a 3-D box at element coordinates (c0, c1, c2);
+// `map` is the address of a __grid_constant__ CUtensorMap kernel parameter.
+// c0 * element size must be a multiple of 16 bytes; out-of-range elements are
+// zero-filled on loads and skipped on stores.
+__device__ __forceinline__ void tensor_g2s(void* dst, const void* map, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], "
+      "[%5];\n" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(saddr(bar))
+      : "memory");
+}
+
+__device__ __forceinline__ void tensor_s2g(const void* map, int c0, int c1, int c2, const void* src) {
+  asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(c0), "r"(c1), "r"(c2), "r"(saddr(src))
+               : "memory");
+}
+
 __device__ __forceinline__ void commit() { asm volatile("cp.async.bulk.commit_group;\n" ::: "memory"); }
 
-// Until the thread's committed shared -> global copies have read their source.
-__device__ __forceinline__ void wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;\n" ::: "memory"); }
+// Until all but the N most recent of the thread's committed shared -> global
+// bulk groups have read their source.
+template <int N>
+__device__ __forceinline__ void wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;\n" ::"n"(N) : "memory");
+}
 
 // Orders this thread's generic-proxy shared-memory writes before later bulk copies.
 __device__ __forceinline__ void fence_smem() { asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory"); }

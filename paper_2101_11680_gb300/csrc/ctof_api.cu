@@ -217,13 +217,14 @@ ctof_status ensure_events(ctof_kernel_s* k, int count) {
   return CTOF_OK;
 }
 
-// Autotuner: times each column-pass plane tile (8, 16, 32 planes) on the
-// handle's own buffers for the four column-pass shapes of an ADMM iteration
-// and keeps the fastest.  Synchronous; must run outside stream capture.
+// Autotuner: times each column-pass tile (32 columns of 8 or 16 planes, 16
+// columns of 8 or 16 planes) on the handle's own buffers for the four
+// column-pass shapes of an ADMM iteration and keeps the fastest.
+// Synchronous; must run outside stream capture.
 ctof_status autotune(ctof_kernel_s* k, cudaStream_t st) {
   if (k->tuned) return CTOF_OK;
-  // tile codes: 8 / 16 / 32 planes in 32-column tiles, 100 + 8 / 16 in 16-column tiles
-  const int cands[5] = {8, 16, 32, 108, 116};
+  // tile codes: 8 / 16 planes in 32-column tiles, 100 + 8 / 16 in 16-column tiles
+  const int cands[4] = {8, 16, 108, 116};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   CTOF_CUDA_TRY(cudaEventCreate(&e0));
   if (cudaEventCreate(&e1) != cudaSuccess) {
@@ -240,7 +241,7 @@ ctof_status autotune(ctof_kernel_s* k, cudaStream_t st) {
   for (int use = 0; use < 4 && s == CTOF_OK; ++use) {
     float best_ms = 1e30f;
     int best = 16;
-    for (int ci = 0; ci < 5 && s == CTOF_OK; ++ci) {
+    for (int ci = 0; ci < 4 && s == CTOF_OK; ++ci) {
       const int pb = cands[ci];
       auto launch = [&]() -> ctof_status {
         switch (use) {

@@ -26,6 +26,8 @@
 // host in double precision and staged in shared memory.
 #include <cuda_runtime.h>
 
+#include <cuda.h>
+#include <cudaTypedefs.h>
 #include <math.h>
 
 #include "bulk.cuh"
@@ -41,27 +43,18 @@ constexpr int COL_THREADS = 256;
 constexpr int ROW_WARPS = 8;
 
 __host__ __device__ constexpr int ilog2c(int x) { return x <= 1 ? 0 : 1 + ilog2c(x >> 1); }
-__host__ __device__ constexpr int bitrevc(int i, int bits) {
-  int r = 0;
-  for (int b = 0; b < bits; ++b) r = (r << 1) | ((i >> b) & 1);
-  return r;
-}
 
 __device__ __forceinline__ int brev5(int l) { return (int)(__brev((unsigned)l) >> 27); }
 
-template <int P, bool INV>
-__device__ __forceinline__ float2 tw_get(const float2* tw, int j) {
-  float2 w = tw[j & (P - 1)];
-  return INV ? make_float2(w.x, -w.y) : w;
-}
-
 // Twiddle table, built on the host in this layout and copied to shared memory
-// as is: the P roots w^j, then per-lane copies of the values the lanes need at
+// as is: the P roots w^j, then copies of the values that the lanes need at
 // the same time, so that those reads hit distinct banks:
-// [P + s - 1 + l] = w^(l P / 2s) for the cross-lane stage s (l < s), and
-// [P + 31 + 32 (k - 1) + lane] = w^(lane k) for the register twiddles;
-// padded to an even count (a multiple of 16 bytes).
-__host__ __device__ constexpr int tw_count(int P) { return P + 31 + 32 * (P / 32 - 1); }
+// [P + s - 1 + l] = w^(l P / 2s) for the cross-lane stage s (l < s),
+// [P + 31 + 32 (k - 1) + lane] = w^(lane k) for the register twiddles, and
+// [tw4_base(P) + 8 (m1 - 1) + b] = w^(R b m1) for the 4 x 8 step (m1 = 1..3,
+// b < 8); padded to an even count (a multiple of 16 bytes).
+__host__ __device__ constexpr int tw4_base(int P) { return P + 31 + 32 * (P / 32 - 1); }
+__host__ __device__ constexpr int tw_count(int P) { return tw4_base(P) + 24; }
 __host__ __device__ constexpr int tw_pad(int P) { return (tw_count(P) + 1) & ~1; }
 
 template <bool INV>
@@ -93,16 +86,15 @@ __device__ __forceinline__ cpair vmi(cpair a) {
   return {mul_mi<INV>(a.a), mul_mi<INV>(a.b)};
 }
 __device__ __forceinline__ void vld(float2& v, const float2* p) { v = *p; }
+__device__ __forceinline__ void vst(float2* p, float2 v) { *p = v; }
 __device__ __forceinline__ void vld(cpair& v, const float2* p) {
   const float4 q = *reinterpret_cast<const float4*>(p);
   v.a = make_float2(q.x, q.y);
   v.b = make_float2(q.z, q.w);
 }
-__device__ __forceinline__ void vst(float2* p, float2 v) { *p = v; }
 __device__ __forceinline__ void vst(float2* p, cpair v) {
   *reinterpret_cast<float4*>(p) = make_float4(v.a.x, v.a.y, v.b.x, v.b.y);
 }
-__device__ __forceinline__ void vzero(float2& v) { v = make_float2(0.f, 0.f); }
 __device__ __forceinline__ void vzero(cpair& v) { v.a = v.b = make_float2(0.f, 0.f); }
 __device__ __forceinline__ float2 shfl2(float2 v, int s) {
   return make_float2(__shfl_xor_sync(0xffffffffu, v.x, s), __shfl_xor_sync(0xffffffffu, v.y, s));
@@ -196,37 +188,46 @@ __device__ __forceinline__ void reg_dft(T (&v)[R]) {
 }
 
 // Scratch slots of the 32-point step for P >= 256 (each a permutation of
-// [0, P)): S[i][l] (register i, lane l) and S2[i][m1][b].  Eight consecutive
-// lanes always touch eight slots that are distinct mod 8 (conflict-free
-// 16-byte accesses on the column tile's pitch); the rotation in S keeps a
-// half-warp's 8-byte accesses on distinct banks for odd pitches.
+// [0, P)): S[i][l] (register i, lane l) and S2[i][m1][b].  Column tiles
+// (16-byte accesses, swizzled rows): eight consecutive lanes touch eight
+// slots that are distinct mod 8.  Row buffers (8-byte accesses, unit stride):
+// sixteen consecutive lanes touch sixteen slots that are distinct mod 16.
 __device__ __forceinline__ int slot_a(int i, int l) { return i * 32 + ((l + 8 * (i & 1)) & 31); }
-__device__ __forceinline__ int slot_c(int i, int m1, int b) {
+__device__ __forceinline__ int slot_c_tile(int i, int m1, int b) { return (4 * i + m1) * 8 + (b ^ (i & 7)); }
+__device__ __forceinline__ int slot_c_row(int i, int m1, int b) {
   const int t = 4 * i + m1;
-  return t * 8 + (b ^ (t & 7));
+  return (t >> 4) * 128 + b * 16 + ((t & 15) ^ ((b & 3) | ((b & 4) << 1)));
 }
+
+// Where a warp transform keeps its intermediate values: FFT_SHFL (five
+// shuffle stages), FFT_TILE (a column pair of the column-pass tile) or
+// FFT_ROWBUF (the warp's own row buffer); the last two run the 4 x 8 step
+// when P >= 256 and the shuffles otherwise.  They differ in which lanes
+// finish which outputs: FFT_TILE gives eight consecutive lanes eight k1
+// values that are distinct mod 8 (outputs go to natural tile rows),
+// FFT_ROWBUF four k1 x four k2 per half-warp.
+constexpr int FFT_SHFL = 0, FFT_TILE = 1, FFT_ROWBUF = 2;
 
 // Length-P DFT held by one warp, P = 32 R: lane l register i holds element
 // l + 32 i (of one column, or of each of two columns).  X[k1 + R k2] =
 // sum_l w32^(l k2) w_P^(l k1) sum_i x[l + 32 i] w_R^(i k1): an R-point DFT
 // over the registers (register i then holds k1 = i), the twiddle w_P^(l k1),
 // and a 32-point DFT across the lanes.  INV selects exp(+...).
-// With SCRATCH and P >= 256 (the column passes, whose warps own a tile column
-// pair to use as scratch) the 32-point DFT across the lanes runs as 4 x 8
-// points in registers with two passes through the scratch (P slots `stride`
-// float2 apart):
+// With a scratch MODE and P >= 256 the 32-point DFT across the lanes runs as
+// 4 x 8 points in registers with two passes through the scratch (scr(s) is
+// the address of slot s, s < P):
 //   Z[m1 + 4 m2] = sum_b w8^(b m2) w32^(b m1) sum_a y[b + 8 a] w4^(a m1);
 // otherwise as five shuffle stages (DIF, outputs in bit-reversed lane order).
-template <int P, bool INV, bool SCRATCH = true, typename T>
-__device__ __forceinline__ void warp_fft(T (&v)[P / 32], int lane, const float2* tw, float2* scr, int stride) {
+template <int P, bool INV, int MODE, typename T, typename Scr>
+__device__ __forceinline__ void warp_fft(T (&v)[P / 32], int lane, const float2* tw, const Scr& scr) {
   constexpr int R = P / 32;
   reg_dft<R, INV>(v);
 #pragma unroll
   for (int i = 1; i < R; ++i) v[i] = vmul(v[i], tw_conj<INV>(tw[P + 31 + 32 * (i - 1) + lane]));
-  if constexpr (SCRATCH && R >= 8) {
+  if constexpr (MODE != FFT_SHFL && R >= 8) {
     __syncwarp();  // every lane has read its inputs (callers may pass their input column as scratch)
 #pragma unroll
-    for (int i = 0; i < R; ++i) vst(scr + slot_a(i, lane) * stride, v[i]);
+    for (int i = 0; i < R; ++i) vst(scr(slot_a(i, lane)), v[i]);
     __syncwarp();
     const int b = lane & 7;
     T t[R / 4][4];
@@ -234,7 +235,7 @@ __device__ __forceinline__ void warp_fft(T (&v)[P / 32], int lane, const float2*
     for (int q = 0; q < R / 4; ++q) {
       const int i = (lane >> 3) + 4 * q;
 #pragma unroll
-      for (int a = 0; a < 4; ++a) vld(t[q][a], scr + slot_a(i, b + 8 * a) * stride);
+      for (int a = 0; a < 4; ++a) vld(t[q][a], scr(slot_a(i, b + 8 * a)));
     }
     __syncwarp();
 #pragma unroll
@@ -242,18 +243,22 @@ __device__ __forceinline__ void warp_fft(T (&v)[P / 32], int lane, const float2*
       const int i = (lane >> 3) + 4 * q;
       dft4<INV>(t[q][0], t[q][1], t[q][2], t[q][3]);
 #pragma unroll
-      for (int m1 = 1; m1 < 4; ++m1) t[q][m1] = vmul(t[q][m1], tw_get<P, INV>(tw, R * b * m1));
+      for (int m1 = 1; m1 < 4; ++m1) t[q][m1] = vmul(t[q][m1], tw_conj<INV>(tw[tw4_base(P) + 8 * (m1 - 1) + b]));
 #pragma unroll
-      for (int m1 = 0; m1 < 4; ++m1) vst(scr + slot_c(i, m1, b) * stride, t[q][m1]);
+      for (int m1 = 0; m1 < 4; ++m1) {
+        const int s = MODE == FFT_TILE ? slot_c_tile(i, m1, b) : slot_c_row(i, m1, b);
+        vst(scr(s), t[q][m1]);
+      }
     }
     __syncwarp();
-    const int m1 = lane & 3;
+    const int m1 = MODE == FFT_TILE ? lane >> 3 : lane & 3;
 #pragma unroll
     for (int q = 0; q < R / 8; ++q) {
-      const int i = (lane >> 2) + 8 * q;
+      const int i = (MODE == FFT_TILE ? (lane & 7) : (lane >> 2)) + 8 * q;
       T u[8];
 #pragma unroll
-      for (int bb = 0; bb < 8; ++bb) vld(u[bb], scr + slot_c(i, m1, bb) * stride);
+      for (int bb = 0; bb < 8; ++bb)
+        vld(u[bb], scr(MODE == FFT_TILE ? slot_c_tile(i, m1, bb) : slot_c_row(i, m1, bb)));
       dft8<INV>(u);
 #pragma unroll
       for (int m2 = 0; m2 < 8; ++m2) v[8 * q + m2] = u[m2];
@@ -273,11 +278,14 @@ __device__ __forceinline__ void warp_fft(T (&v)[P / 32], int lane, const float2*
   }
 }
 
-// Output position of register i of lane `lane` after warp_fft<P, INV, SCRATCH>.
-template <int P, bool SCRATCH = true>
+// Output position of register i of lane `lane` after warp_fft<P, INV, MODE>.
+template <int P, int MODE>
 __device__ __forceinline__ int out_pos(int lane, int i) {
   constexpr int R = P / 32;
-  if constexpr (SCRATCH && R >= 8) {
+  if constexpr (MODE == FFT_TILE && R >= 8) {
+    // register 8 q + m2 of lane L: k1 = (L & 7) + 8 q, k2 = (L >> 3) + 4 m2
+    return (lane & 7) + 8 * (i >> 3) + R * ((lane >> 3) + 4 * (i & 7));
+  } else if constexpr (MODE == FFT_ROWBUF && R >= 8) {
     // register 8 q + m2 of lane L: k1 = (L >> 2) + 8 q, k2 = (L & 3) + 4 m2
     return (lane >> 2) + 8 * (i >> 3) + R * ((lane & 3) + 4 * (i & 7));
   } else {
@@ -285,20 +293,11 @@ __device__ __forceinline__ int out_pos(int lane, int i) {
   }
 }
 
-// Shared-memory slot of transform element e.  A warp writes its R registers
-// to elements R*bitrev5(lane) + i', i.e. 32 elements R apart, which would all
-// fall in two banks; XOR-ing the low log2(R) bits with the next ones spreads
-// them over all banks.  A permutation within each aligned block of R elements.
-template <int P>
-__device__ __forceinline__ int sw_pos(int e) {
-  constexpr int R = P / 32;
-  return e ^ ((e / R) & (R - 1));
-}
-
-template <int P>
-__device__ __forceinline__ void stage_twiddles(float2* s_tw, const float2* tw) {
-  for (int i = threadIdx.x; i < tw_pad(P); i += blockDim.x) s_tw[i] = tw[i];
-}
+// Unit-stride scratch (a warp's row buffer).
+struct LinearScr {
+  float2* p;
+  __device__ __forceinline__ float2* operator()(int s) const { return p + s; }
+};
 
 // ---------------------------------------------------------------- rows ----
 
@@ -306,75 +305,196 @@ constexpr int RP = 2 * ROW_WARPS;  // planes per row-pass CTA
 
 __host__ __device__ inline int plane_ld(int nplanes) { return (nplanes + RP - 1) / RP * RP; }
 
-// Half spectra of the CTA's planes for one row: s_h[kx][plane] (pitch RP + 1).
-constexpr int SH_LD = RP + 1;
+// Half spectra of the CTA's planes for one row: s_h[kx][plane], 16 planes =
+// 128 bytes per kx, in the TMA 128-byte swizzle (the 16-byte chunk of planes
+// 2c, 2c + 1 of row s sits at chunk c ^ (s & 7)), so that a warp's plane pair
+// is one conflict-free 16-byte access for consecutive kx.  Loaded and stored
+// as boxes of RKX(P) kx; for P = 512 the second box starts at s_h row
+// RKX_GAP(P) (1024-byte aligned).  Two buffers: the copies of the next job
+// land in one while the CTA works on the other.
+__host__ __device__ constexpr int rkx(int P) { return P / 2 + 1 <= 256 ? P / 2 + 1 : P / 4 + 1; }
+__host__ __device__ constexpr int rkx_boxes(int P) { return P / 2 + 1 <= 256 ? 1 : 2; }
+__host__ __device__ constexpr int rkx_second(int P) { return (rkx(P) + 7) / 8 * 8; }  // s_h row of box 2
+__host__ __device__ constexpr int sh_rows(int P) { return rkx_boxes(P) == 1 ? rkx(P) : rkx_second(P) + rkx(P); }
+__host__ __device__ constexpr int sh_bytes(int P) { return (sh_rows(P) * 128 + 1023) / 1024 * 1024; }
 
 template <int P>
-__device__ __forceinline__ void split_to_tile(const float2* buf, int lane, float2* s_h, int c0) {
-  for (int kk = lane; kk <= P / 2; kk += 32) {
-    const float2 zk = buf[sw_pos<P>(kk)];
-    const float2 zm = buf[sw_pos<P>((P - kk) & (P - 1))];
-    s_h[kk * SH_LD + c0] = make_float2(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y));
-    s_h[kk * SH_LD + c0 + 1] = make_float2(0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+__device__ __forceinline__ int sh_row(int kx) {
+  if constexpr (rkx_boxes(P) == 1) {
+    return kx;
+  } else {
+    return kx < rkx(P) ? kx : kx - rkx(P) + rkx_second(P);
   }
 }
 
-// Z[n] = A[n] + i B[n] from the half spectra in tile columns c0, c0 + 1.
+// Address of the plane pair (2 c, 2 c + 1) of kx in an s_h buffer.
 template <int P>
-__device__ __forceinline__ void load_pair_from_tile(float2 (&v)[P / 32], const float2* s_h, int c0, int lane) {
+__device__ __forceinline__ float2* sh_at(float2* s_h, int kx, int c) {
+  const int s = sh_row<P>(kx);
+  return s_h + s * 16 + ((c ^ (s & 7)) << 1);
+}
+
+// The row transforms run the 4 x 8 step in the warp's buffer from P = 256 on.
+template <int P>
+__host__ __device__ constexpr int row_mode() {
+  return P >= 256 ? FFT_ROWBUF : FFT_SHFL;
+}
+
+// Row-buffer slot of transform output e: a permutation of [0, P) under which
+// the sixteen outputs that a half-warp writes with one register, and sixteen
+// consecutive outputs, fall on distinct 8-byte banks (4 x 8 path: XOR of
+// bits 2-3 with bits log2 R .. log2 R + 1; shuffle path: the low log2 R bits
+// with the next ones).
+template <int P>
+__device__ __forceinline__ int row_pos(int e) {
+  constexpr int R = P / 32;
+  if constexpr (row_mode<P>() == FFT_ROWBUF) {
+    return e ^ (((e / R) & 3) << 2);
+  } else {
+    return e ^ ((e / R) & (R - 1));
+  }
+}
+
+// Row-pass shared memory (from a 1024-byte aligned base):
+// [s_h x 2][twiddles][per-warp buffers of P + 2][2 mbarriers].
+__host__ __device__ constexpr size_t row_smem_bytes(int P) {
+  return 1024 + 2 * (size_t)sh_bytes(P) + ((size_t)tw_pad(P) + (size_t)ROW_WARPS * (P + 2)) * sizeof(float2) + 16;
+}
+
+struct RowSmem {
+  float2* s_h;  // buffer b at s_h + b * sh_bytes / 8
+  float2* s_tw;
+  float2* buf;
+  uint64_t* bar;
+};
+
+__device__ __forceinline__ char* align1024(void* p) {
+  const uint32_t s = bulk::saddr(p);
+  return static_cast<char*>(p) + (((s + 1023u) & ~1023u) - s);
+}
+
+template <int P>
+__device__ __forceinline__ RowSmem row_carve(float4* raw, int warp) {
+  RowSmem m;
+  char* base = align1024(raw);
+  m.s_h = reinterpret_cast<float2*>(base);
+  m.s_tw = reinterpret_cast<float2*>(base + 2 * sh_bytes(P));
+  float2* bufs = m.s_tw + tw_pad(P);
+  m.buf = bufs + warp * (P + 2);
+  m.bar = reinterpret_cast<uint64_t*>(bufs + ROW_WARPS * (P + 2));
+  return m;
+}
+
+template <int P>
+__device__ __forceinline__ float2* sh_buf(const RowSmem& S, int b) {
+  return S.s_h + b * (sh_bytes(P) / (int)sizeof(float2));
+}
+
+// Block-wide prologue: barriers (one per s_h buffer) and twiddles.
+template <int P>
+__device__ __forceinline__ void row_prologue(const RowSmem& S, const float2* tw) {
+  if (threadIdx.x == 0) {
+    bulk::bar_init(S.bar, 1);
+    bulk::bar_init(S.bar + 1, 1);
+  }
+  for (int i = threadIdx.x; i < tw_pad(P); i += blockDim.x) S.s_tw[i] = tw[i];
+  __syncthreads();  // barriers initialised and twiddles staged before any use
+}
+
+// Block-wide wait for the copies into buffer (it & 1) of iteration `it`
+// (phase it / 2 of that buffer's barrier); false, with the handle's status
+// flag set, when they did not land within max_polls polls.
+__device__ __forceinline__ bool row_wait(uint64_t* bar, int it, int* flag, long long max_polls) {
+  const uint32_t parity = (uint32_t)(it >> 1) & 1u;
+  const bool ok = bulk::block_wait(bar, parity, max_polls);
+  if (!ok && threadIdx.x == 0) {
+    atomicOr(flag, 1);
+    bulk::wait(bar, parity, bulk::DRAIN_POLLS);
+  }
+  return ok;
+}
+
+// One thread: row r, planes pl0.. of the intermediate into buffer s_h as
+// rkx_boxes tensor copies, completing on bar.
+template <int P>
+__device__ __forceinline__ void row_load_issue(uint64_t* bar, float2* s_h, const CUtensorMap* map, int r, int pl0) {
+  bulk::arrive_expect(bar, rkx_boxes(P) * rkx(P) * 128u);
+  bulk::tensor_g2s(s_h, map, pl0, 0, r, bar);
+  if constexpr (rkx_boxes(P) == 2) bulk::tensor_g2s(s_h + rkx_second(P) * 16, map, pl0, rkx(P), r, bar);
+}
+
+// Block-wide: buffer s_h back to row r of the intermediate (one thread issues
+// the tensor copies into its bulk group); planes past the last and kx past h
+// are skipped by the copy.
+template <int P>
+__device__ __forceinline__ void row_store(const float2* s_h, const CUtensorMap* map, int r, int pl0) {
+  bulk::fence_smem();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    bulk::tensor_s2g(map, pl0, 0, r, s_h);
+    if constexpr (rkx_boxes(P) == 2) bulk::tensor_s2g(map, pl0, rkx(P), r, s_h + rkx_second(P) * 16);
+    bulk::commit();
+  }
+}
+
+template <int P>
+__device__ __forceinline__ void split_to_tile(const float2* buf, int lane, float2* s_h, int c) {
+  for (int kk = lane; kk <= P / 2; kk += 32) {
+    const float2 zk = buf[row_pos<P>(kk)];
+    const float2 zm = buf[row_pos<P>((P - kk) & (P - 1))];
+    *reinterpret_cast<float4*>(sh_at<P>(s_h, kk, c)) =
+        make_float4(0.5f * (zk.x + zm.x), 0.5f * (zk.y - zm.y), 0.5f * (zk.y + zm.y), -0.5f * (zk.x - zm.x));
+  }
+}
+
+// Z[n] = A[n] + i B[n] from the half spectra of plane pair c (zero for planes
+// past the last: has0 / has1 false).
+template <int P>
+__device__ __forceinline__ void load_pair_from_tile(float2 (&v)[P / 32], float2* s_h, int c, int lane, bool has0,
+                                                    bool has1) {
   constexpr int R = P / 32;
 #pragma unroll
   for (int i = 0; i < R; ++i) {
     const int n = lane + 32 * i;
-    float2 A, B;
-    if (n <= P / 2) {
-      A = s_h[n * SH_LD + c0];
-      B = s_h[n * SH_LD + c0 + 1];
-    } else {
-      A = cconj(s_h[(P - n) * SH_LD + c0]);
-      B = cconj(s_h[(P - n) * SH_LD + c0 + 1]);
+    float4 q = *reinterpret_cast<const float4*>(sh_at<P>(s_h, n <= P / 2 ? n : P - n, c));
+    if (n > P / 2) {
+      q.y = -q.y;
+      q.w = -q.w;
     }
-    v[i] = make_float2(A.x - B.y, A.y + B.x);
+    if (!has0) q.x = q.y = 0.f;
+    if (!has1) q.z = q.w = 0.f;
+    v[i] = make_float2(q.x - q.w, q.y + q.z);
   }
 }
 
-template <int P>
-__device__ __forceinline__ void store_tile(const float2* s_h, float2* __restrict__ inter, int r, int hp, int LP,
-                                           int pl0, int nplanes) {
-  for (int idx = threadIdx.x; idx < (P / 2 + 1) * RP; idx += blockDim.x) {
-    const int kk = idx / RP, pl = idx - kk * RP;
-    if (pl0 + pl < nplanes) inter[((size_t)r * hp + kk) * LP + pl0 + pl] = s_h[kk * SH_LD + pl];
-  }
-}
-
-template <int P>
-__device__ __forceinline__ void load_tile(float2* s_h, const float2* __restrict__ inter, int r, int hp, int LP,
-                                          int pl0, int nplanes) {
-  for (int idx = threadIdx.x; idx < (P / 2 + 1) * RP; idx += blockDim.x) {
-    const int kk = idx / RP, pl = idx - kk * RP;
-    s_h[kk * SH_LD + pl] =
-        pl0 + pl < nplanes ? inter[((size_t)r * hp + kk) * LP + pl0 + pl] : make_float2(0.f, 0.f);
-  }
+// One warp transform of a packed row pair, results left in the warp's buffer
+// at row_pos slots.
+template <int P, bool INV>
+__device__ __forceinline__ void row_transform(float2 (&v)[P / 32], int lane, const RowSmem& S) {
+  constexpr int R = P / 32;
+  warp_fft<P, INV, row_mode<P>()>(v, lane, S.s_tw, LinearScr{S.buf});
+#pragma unroll
+  for (int i = 0; i < R; ++i) S.buf[row_pos<P>(out_pos<P, row_mode<P>()>(lane, i))] = v[i];
+  __syncwarp();
 }
 
 // Forward R2C of rows: in[plane][row][ld_in] (first cols_in columns, zero beyond)
-// -> inter[row][kx][LP].
+// -> inter[row][kx][plane] (tensor map `dst`: nplanes x h x rows).
 template <int P>
-__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_fwd(const float* __restrict__ in, int nplanes, int rows,
-                                                             int cols_in, int ld_in, float2* __restrict__ inter,
-                                                             int hp, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_fwd(const __grid_constant__ CUtensorMap dst,
+                                                             const float* __restrict__ in, int nplanes, int rows,
+                                                             int cols_in, int ld_in, const float2* __restrict__ tw) {
   constexpr int R = P / 32;
-  extern __shared__ float2 smem[];
-  float2* s_tw = smem;
-  float2* s_h = smem + tw_pad(P);
+  extern __shared__ float4 row_smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* buf = s_h + (P / 2 + 1) * SH_LD + warp * (P + 2);
-  stage_twiddles<P>(s_tw, tw);
-  __syncthreads();
-  const int LP = plane_ld(nplanes), nblk = LP / RP;
-  for (int job = blockIdx.x; job < rows * nblk; job += gridDim.x) {
+  const RowSmem S = row_carve<P>(row_smem4, warp);
+  row_prologue<P>(S, tw);
+  const int nblk = plane_ld(nplanes) / RP;
+  int it = 0;
+  for (int job = blockIdx.x; job < rows * nblk; job += gridDim.x, ++it) {
     const int r = job / nblk, pl0 = (job - r * nblk) * RP;
     const int p0 = pl0 + 2 * warp, p1 = p0 + 1;
+    float2* s_h = sh_buf<P>(S, it & 1);
     const float* r0 = in + ((size_t)p0 * rows + r) * ld_in;
     const float* r1 = in + ((size_t)p1 * rows + r) * ld_in;
     float2 v[R];
@@ -385,47 +505,54 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_fwd(const float* __rest
       const float b = (p1 < nplanes && n < cols_in) ? r1[n] : 0.f;
       v[i] = make_float2(a, b);
     }
-    warp_fft<P, false, false>(v, lane, s_tw, buf, 1);
-#pragma unroll
-    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P, false>(lane, i))] = v[i];
-    __syncwarp();
-    split_to_tile<P>(buf, lane, s_h, 2 * warp);
+    row_transform<P, false>(v, lane, S);
+    if (threadIdx.x == 0) bulk::wait_read<1>();  // the copy out of this buffer two jobs ago has read it
     __syncthreads();
-    store_tile<P>(s_h, inter, r, hp, LP, pl0, nplanes);
-    __syncthreads();
+    split_to_tile<P>(S.buf, lane, s_h, warp);
+    row_store<P>(s_h, &dst, r, pl0);
   }
+  if (threadIdx.x == 0) bulk::wait_read<0>();
 }
 
-// Inverse C2R of rows: inter[row][kx][LP] -> out[plane][row][ld_out] (first cols_out columns), x scale.
+// Inverse C2R of rows: inter[row][kx][plane] (tensor map `src`) ->
+// out[plane][row][ld_out] (first cols_out columns), x scale.
 template <int P>
-__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const float2* __restrict__ inter, int nplanes,
-                                                             int rows, int hp, int cols_out, float* __restrict__ out,
+__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const __grid_constant__ CUtensorMap src, int nplanes,
+                                                             int rows, int cols_out, float* __restrict__ out,
                                                              int ld_out, float scale,
-                                                             const float2* __restrict__ tw) {
+                                                             const float2* __restrict__ tw, int* __restrict__ flag,
+                                                             long long max_polls) {
   constexpr int R = P / 32;
-  extern __shared__ float2 smem[];
-  float2* s_tw = smem;
-  float2* s_h = smem + tw_pad(P);
+  extern __shared__ float4 row_smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* buf = s_h + (P / 2 + 1) * SH_LD + warp * (P + 2);
-  stage_twiddles<P>(s_tw, tw);
-  const int LP = plane_ld(nplanes), nblk = LP / RP;
-  for (int job = blockIdx.x; job < rows * nblk; job += gridDim.x) {
+  const RowSmem S = row_carve<P>(row_smem4, warp);
+  row_prologue<P>(S, tw);
+  const int nblk = plane_ld(nplanes) / RP, njobs = rows * nblk;
+  auto issue = [&](int job, int it) {
+    const int r = job / nblk;
+    row_load_issue<P>(S.bar + (it & 1), sh_buf<P>(S, it & 1), &src, r, (job - r * nblk) * RP);
+  };
+  if (threadIdx.x == 0 && (int)blockIdx.x < njobs) issue(blockIdx.x, 0);
+  int it = 0;
+  for (int job = blockIdx.x; job < njobs; job += gridDim.x, ++it) {
     const int r = job / nblk, pl0 = (job - r * nblk) * RP;
     const int p0 = pl0 + 2 * warp, p1 = p0 + 1;
-    load_tile<P>(s_h, inter, r, hp, LP, pl0, nplanes);
-    __syncthreads();
+    // the other buffer was last read in the previous iteration, before its closing barrier
+    if (threadIdx.x == 0 && job + (int)gridDim.x < njobs) issue(job + gridDim.x, it + 1);
+    if (!row_wait(S.bar + (it & 1), it, flag, max_polls)) {
+      if (threadIdx.x == 0 && job + (int)gridDim.x < njobs)  // the next job's copies are in flight too
+        bulk::wait(S.bar + ((it + 1) & 1), (uint32_t)((it + 1) >> 1) & 1u, bulk::DRAIN_POLLS);
+      return;
+    }
     float2 v[R];
-    load_pair_from_tile<P>(v, s_h, 2 * warp, lane);
-    warp_fft<P, true, false>(v, lane, s_tw, buf, 1);
-#pragma unroll
-    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P, false>(lane, i))] = v[i];
-    __syncwarp();
+    load_pair_from_tile<P>(v, sh_buf<P>(S, it & 1), warp, lane, p0 < nplanes, p1 < nplanes);
+    row_transform<P, true>(v, lane, S);
     for (int c = lane; c < cols_out; c += 32) {
-      const float2 z = buf[sw_pos<P>(c)];
+      const float2 z = S.buf[row_pos<P>(c)];
       if (p0 < nplanes) out[((size_t)p0 * rows + r) * ld_out + c] = z.x * scale;
       if (p1 < nplanes) out[((size_t)p1 * rows + r) * ld_out + c] = z.y * scale;
     }
+    bulk::fence_smem();  // this job's reads of its buffer, before later copies overwrite it
     __syncthreads();
   }
 }
@@ -436,290 +563,236 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const float2* __res
 //   c    = (v1 - u1) - Kx = 2 v1 - a1 - Kx      (zero off the scan)
 //   row spectra <- R2C(c zero-padded to P)
 // so that FFT(v1 - u1) = K x_hat + c_hat without a transform of the full
-// P x P plane.  m, u1: [nt][n][n]; inter: [n][kx][LP] in place.
+// P x P plane.  m, u1: [nt][n][n]; inter: [n][kx][plane] in place (tensor
+// map `map`).  The m and u1 values of a lane are loaded before its tile is
+// waited for; the next job's tile is requested once the copy out of its
+// buffer has read it.
 template <int P>
-__global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_admm_t(float2* __restrict__ inter, int nplanes, int n,
-                                                                int hp, const float* __restrict__ m,
-                                                                float* __restrict__ u1, float scale, float inv_s,
-                                                                float rho, const float2* __restrict__ tw) {
+__global__ void __launch_bounds__(ROW_WARPS * 32, P >= 512 ? 2 : 3)
+    k_rows_admm_t(const __grid_constant__ CUtensorMap map, int nplanes, int n, const float* __restrict__ m,
+                  float* __restrict__ u1, float scale, float inv_s, float rho, const float2* __restrict__ tw,
+                  int* __restrict__ flag, long long max_polls) {
   constexpr int R = P / 32;
-  extern __shared__ float2 smem[];
-  float2* s_tw = smem;
-  float2* s_h = smem + tw_pad(P);
+  constexpr int RN = R / 2 > 0 ? R / 2 : 1;  // registers that can hold scan columns (n <= P / 2)
+  extern __shared__ float4 row_smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  float2* buf = s_h + (P / 2 + 1) * SH_LD + warp * (P + 2);
-  stage_twiddles<P>(s_tw, tw);
+  const RowSmem S = row_carve<P>(row_smem4, warp);
+  row_prologue<P>(S, tw);
   const float inv1r = 1.0f / (1.0f + rho);
-  const int LP = plane_ld(nplanes), nblk = LP / RP;
-  for (int job = blockIdx.x; job < n * nblk; job += gridDim.x) {
+  const int nblk = plane_ld(nplanes) / RP, njobs = n * nblk;
+  auto issue = [&](int job, int it) {
+    const int r = job / nblk;
+    row_load_issue<P>(S.bar + (it & 1), sh_buf<P>(S, it & 1), &map, r, (job - r * nblk) * RP);
+  };
+  if (threadIdx.x == 0 && (int)blockIdx.x < njobs) issue(blockIdx.x, 0);
+  int it = 0;
+  for (int job = blockIdx.x; job < njobs; job += gridDim.x, ++it) {
     const int r = job / nblk, pl0 = (job - r * nblk) * RP;
     const int p0 = pl0 + 2 * warp, p1 = p0 + 1;
     const bool has0 = p0 < nplanes, has1 = p1 < nplanes;
-    load_tile<P>(s_h, inter, r, hp, LP, pl0, nplanes);
-    __syncthreads();
-    float2 v[R];
-    load_pair_from_tile<P>(v, s_h, 2 * warp, lane);
-    warp_fft<P, true, false>(v, lane, s_tw, buf, 1);
+    float2* s_h = sh_buf<P>(S, it & 1);
+    float mv0[RN], mv1[RN], uv0[RN], uv1[RN];
+    const size_t row0 = ((size_t)p0 * n + r) * n, row1 = ((size_t)p1 * n + r) * n;
 #pragma unroll
-    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P, false>(lane, i))] = v[i];
-    __syncwarp();
-#pragma unroll
-    for (int i = 0; i < R; ++i) {
+    for (int i = 0; i < RN; ++i) {
       const int c = lane + 32 * i;
-      float2 cc = make_float2(0.f, 0.f);
+      mv0[i] = uv0[i] = mv1[i] = uv1[i] = 0.f;
+      if (c < n && has0) {
+        mv0[i] = m[row0 + c];
+        uv0[i] = u1[row0 + c];
+      }
+      if (c < n && has1) {
+        mv1[i] = m[row1 + c];
+        uv1[i] = u1[row1 + c];
+      }
+    }
+    if (!row_wait(S.bar + (it & 1), it, flag, max_polls)) {
+      if (threadIdx.x == 0) bulk::wait_read<0>();  // the previous job's copy out of shared memory
+      return;
+    }
+    float2 v[R];
+    load_pair_from_tile<P>(v, s_h, warp, lane, has0, has1);
+    row_transform<P, true>(v, lane, S);
+    if (threadIdx.x == 0) {
+      bulk::wait_read<0>();  // the previous job's copy has read the other buffer
+      if (job + (int)gridDim.x < njobs) issue(job + gridDim.x, it + 1);
+    }
+#pragma unroll
+    for (int i = 0; i < R; ++i) v[i] = make_float2(0.f, 0.f);
+#pragma unroll
+    for (int i = 0; i < RN; ++i) {
+      const int c = lane + 32 * i;
       if (c < n) {
-        const float2 kx = cscale(buf[sw_pos<P>(c)], scale);
+        const float2 kx = cscale(S.buf[row_pos<P>(c)], scale);
         if (has0) {
-          const size_t idx = ((size_t)p0 * n + r) * n + c;
-          const float a1 = kx.x + u1[idx];
-          const float v1 = (m[idx] * inv_s + rho * a1) * inv1r;
-          u1[idx] = a1 - v1;
-          cc.x = 2.f * v1 - a1 - kx.x;
+          const float a1 = kx.x + uv0[i];
+          const float v1 = (mv0[i] * inv_s + rho * a1) * inv1r;
+          u1[row0 + c] = a1 - v1;
+          v[i].x = 2.f * v1 - a1 - kx.x;
         }
         if (has1) {
-          const size_t idx = ((size_t)p1 * n + r) * n + c;
-          const float a1 = kx.y + u1[idx];
-          const float v1 = (m[idx] * inv_s + rho * a1) * inv1r;
-          u1[idx] = a1 - v1;
-          cc.y = 2.f * v1 - a1 - kx.y;
+          const float a1 = kx.y + uv1[i];
+          const float v1 = (mv1[i] * inv_s + rho * a1) * inv1r;
+          u1[row1 + c] = a1 - v1;
+          v[i].y = 2.f * v1 - a1 - kx.y;
         }
       }
-      v[i] = cc;
     }
     __syncwarp();
-    warp_fft<P, false, false>(v, lane, s_tw, buf, 1);
-#pragma unroll
-    for (int i = 0; i < R; ++i) buf[sw_pos<P>(out_pos<P, false>(lane, i))] = v[i];
-    __syncwarp();
-    __syncthreads();  // every warp is done reading s_h
-    split_to_tile<P>(buf, lane, s_h, 2 * warp);
-    __syncthreads();
-    store_tile<P>(s_h, inter, r, hp, LP, pl0, nplanes);
-    __syncthreads();
+    row_transform<P, false>(v, lane, S);
+    __syncthreads();  // every warp is done reading this job's buffer
+    split_to_tile<P>(S.buf, lane, s_h, warp);
+    row_store<P>(s_h, &map, r, pl0);
   }
+  if (threadIdx.x == 0) bulk::wait_read<0>();
 }
 
 // ------------------------------------------------------------- columns ----
 
-// Column-pass tile: P rows x NC columns (KB = NC / PB kx-columns x PB
-// consecutive planes), row pitch NC + 2 float2: rows start on 16-byte
-// boundaries (targets and sources of bulk copies), and eight rows that are
-// distinct mod 8 put a quarter-warp's 16-byte accesses on distinct bank
-// groups.  Each warp transforms two adjacent columns at once (cpair).
-template <int NC>
-__host__ __device__ constexpr int col_ld() {
-  return NC + 2;
-}
-
-// Tile row of transform output e: a permutation of [0, P) under which the
-// eight outputs that eight consecutive lanes write with one register land in
-// rows distinct mod 8.  4 x 8 path (R >= 8): e = k1 + R k2 with k1 = (L >> 2)
-// + 8 q and k2 = (L & 3) + 4 m2, so bits 1-2 of k1 (zero there) take k2's low
-// bits.  Shuffle path: e = i + 4 R rev3(L), so the low bits take the three
-// bits above 4 R.
+// Column-pass tile: NC columns = KB kx-columns x PB consecutive planes, all
+// P rows; kx-column j is a region [row][PB planes] loaded and stored as
+// tensor boxes of RB = min(P, 256) rows, in the TMA swizzle of its row size
+// (PB = 16: 128-byte rows, the 16-byte chunk c of row r at c ^ (r & 7);
+// PB = 8: 64-byte rows, chunk c at c ^ ((r >> 1) & 3)), so that eight rows
+// that are distinct mod 8 put a quarter-warp's 16-byte accesses on distinct
+// bank groups.  Each warp transforms two adjacent columns at once (cpair).
 template <int P>
-__device__ __forceinline__ int col_row(int e) {
-  constexpr int R = P / 32;
-  if constexpr (R >= 8) {
-    return e ^ (((e / R) & 3) << 1);
-  } else if constexpr (R >= 2) {
-    return e ^ ((e >> (ilog2c(R) + 2)) & 7);
-  } else {
-    return e ^ ((e >> 3) & 3);
-  }
+__host__ __device__ constexpr int col_rb() {
+  return P < 256 ? P : 256;
 }
 
-// Shared memory of a column pass: [mbarrier, 16 B][twiddles][tile].
+template <int PB>
+struct ColPair {
+  float2* region;  // the kx-column's region
+  int c;           // the pair's 16-byte chunk within a row
+  __device__ __forceinline__ float2* operator()(int r) const {
+    if constexpr (PB == 16) {
+      return region + r * 16 + ((c ^ (r & 7)) << 1);
+    } else {
+      return region + r * 8 + ((c ^ ((r >> 1) & 3)) << 1);
+    }
+  }
+};
+
+// Shared memory of a column pass (from a 1024-byte aligned base): [tile][twiddles][mbarrier].
 __host__ __device__ constexpr size_t col_smem_bytes(int P, int NC) {
-  return 16 + ((size_t)tw_pad(P) + (size_t)P * (NC + 2)) * sizeof(float2);
+  return 1024 + ((size_t)P * NC + (size_t)tw_pad(P)) * sizeof(float2) + 16;
 }
 
-// Stages the tile's runs (`nrun` runs of `run` bytes; run r goes from
-// src(r) to dst(r)) and the twiddles by bulk copies completing on one
-// mbarrier.  Block-wide; false (and the handle's status flag set) when the
-// copies did not land within max_polls polls.
-template <int P, typename Src, typename Dst>
-__device__ __forceinline__ bool col_stage_in(uint64_t* bar, float2* s_tw, const float2* tw, int nrun, unsigned run,
-                                             Src src, Dst dst, int* flag, long long max_polls) {
-  if (threadIdx.x == 0) {
-    bulk::bar_init(bar, 1);
-    bulk::arrive_expect(bar, (unsigned)nrun * run + tw_pad(P) * (unsigned)sizeof(float2));
-    bulk::g2s(s_tw, tw, tw_pad(P) * sizeof(float2), bar);
-  }
-  __syncthreads();
-  for (int r = threadIdx.x; r < nrun; r += COL_THREADS) bulk::g2s(dst(r), src(r), run, bar);
-  const bool ok = __syncthreads_and(bulk::wait(bar, 0, max_polls));
-  if (!ok) {
-    if (threadIdx.x == 0) atomicOr(flag, 1);
+// One thread: the twiddles and the tile's boxes (kx-columns j < kb, row boxes
+// rb < nrb of map `src` at planes pl0, kx0 + j, rows rb RB) into shared memory,
+// completing on bar.
+template <int P, int PB>
+__device__ __forceinline__ void col_load_issue(uint64_t* bar, float2* tile, float2* s_tw, const float2* tw,
+                                               const CUtensorMap* src, int pl0, int kx0, int kb, int nrb) {
+  constexpr int RB = col_rb<P>();
+  bulk::bar_init(bar, 1);
+  bulk::arrive_expect(bar, (unsigned)(kb * nrb * RB * PB) * (unsigned)sizeof(float2) +
+                               tw_pad(P) * (unsigned)sizeof(float2));
+  bulk::g2s(s_tw, tw, tw_pad(P) * sizeof(float2), bar);
+  for (int j = 0; j < kb; ++j)
+    for (int rb = 0; rb < nrb; ++rb) bulk::tensor_g2s(tile + (j * P + rb * RB) * PB, src, pl0, kx0 + j, rb * RB, bar);
+}
+
+// Block-wide wait for col_load_issue's copies; false (status flag set) on timeout.
+__device__ __forceinline__ bool col_wait(uint64_t* bar, int* flag, long long max_polls) {
+  const bool ok = bulk::block_wait(bar, 0, max_polls);
+  if (!ok && threadIdx.x == 0) {
+    atomicOr(flag, 1);
     bulk::wait(bar, 0, bulk::DRAIN_POLLS);
   }
   return ok;
 }
 
-// Writes the tile's runs back: `nrun` runs of np planes, run r from src(r) to
-// dst(r); the even part by bulk copies, an odd last plane by a plain store.
-template <typename Src, typename Dst>
-__device__ __forceinline__ void col_stage_out(int nrun, int np, Src src, Dst dst) {
-  bulk::fence_smem();  // the tile writes of this thread, before the copies read them
+// Block-wide: the tile's boxes (kx-columns j < kb, row boxes rb < nrb) to map
+// `dst` at planes pl0, kx0 + j, rows rb RB; one thread issues and waits until
+// the copies have read shared memory.
+template <int P, int PB>
+__device__ __forceinline__ void col_store(const float2* tile, const CUtensorMap* dst, int pl0, int kx0, int kb,
+                                          int nrb) {
+  constexpr int RB = col_rb<P>();
+  bulk::fence_smem();
   __syncthreads();
-  const int ne = np & ~1;
-  bool issued = false;
-  for (int r = threadIdx.x; r < nrun; r += COL_THREADS) {
-    const float2* s = src(r);
-    float2* d = dst(r);
-    if (ne) {
-      bulk::s2g(d, s, (unsigned)ne * sizeof(float2));
-      issued = true;
-    }
-    if (np & 1) d[ne] = s[ne];
-  }
-  if (issued) {
+  if (threadIdx.x == 0) {
+    for (int j = 0; j < kb; ++j)
+      for (int rb = 0; rb < nrb; ++rb) bulk::tensor_s2g(dst, pl0, kx0 + j, rb * RB, tile + (j * P + rb * RB) * PB);
     bulk::commit();
-    bulk::wait_read_all();
+    bulk::wait_read<0>();
   }
 }
 
-// Forward C2C along y: inter[row][kx][LP] (rows_in rows, zero beyond) -> out[ky h + kx][ldf].
-// BULK: tile staged in and out by bulk copies (16-byte aligned buffers, even
-// ldf); otherwise element by element.
-template <int P, int PB, int NC, bool BULK>
-__global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const float2* __restrict__ inter, int nplanes,
-                                                          int rows_in, int h, int hp,
-                                                          float2* __restrict__ out, int ldf,
-                                                          const float2* __restrict__ tw, int* __restrict__ flag,
-                                                          long long max_polls) {
+// Forward C2C along y: inter[row][kx][plane] (map `src`: nplanes x h x
+// rows_in, zero beyond) -> spectra [ky][kx][plane] (map `dst`: nplanes x h x P).
+template <int P, int PB, int NC>
+__global__ void __launch_bounds__(COL_THREADS) k_cols_fwd(const __grid_constant__ CUtensorMap src,
+                                                          const __grid_constant__ CUtensorMap dst, int rows_in,
+                                                          int h, const float2* __restrict__ tw,
+                                                          int* __restrict__ flag, long long max_polls) {
   constexpr int R = P / 32;
   constexpr int KB = NC / PB;
-  constexpr int LDT = col_ld<NC>();
+  constexpr int RB = col_rb<P>();
   extern __shared__ float4 col_smem4[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(col_smem4);
-  float2* s_tw = reinterpret_cast<float2*>(col_smem4 + 1);
-  float2* tile = s_tw + tw_pad(P);
+  float2* tile = reinterpret_cast<float2*>(align1024(col_smem4));
+  float2* s_tw = tile + P * NC;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_tw + tw_pad(P));
   const int kx0 = blockIdx.x * KB, pl0 = blockIdx.y * PB;
-  const int LP = plane_ld(nplanes);
-  const int kb = min(KB, h - kx0), np = min(PB, nplanes - pl0);
-  if constexpr (BULK) {
-    const unsigned run = (unsigned)((np + 1) & ~1) * sizeof(float2);
-    if (!col_stage_in<P>(
-            bar, s_tw, tw, rows_in * kb, run,
-            [&](int r) { return inter + ((size_t)(r / kb) * hp + kx0 + r % kb) * LP + pl0; },
-            [&](int r) { return tile + (r / kb) * LDT + (r % kb) * PB; }, flag, max_polls))
-      return;
-  } else {
-    for (int i = threadIdx.x; i < tw_pad(P); i += COL_THREADS) s_tw[i] = tw[i];
-    for (int idx = threadIdx.x; idx < rows_in * NC; idx += COL_THREADS) {
-      const int row = idx / NC, cc = idx % NC;
-      const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
-      float2 val = make_float2(0.f, 0.f);
-      if (kx < h && pl < nplanes) val = inter[((size_t)row * hp + kx) * LP + pl];
-      tile[row * LDT + cc] = val;
-    }
-    __syncthreads();
-  }
+  const int kb = min(KB, h - kx0);
+  if (threadIdx.x == 0) col_load_issue<P, PB>(bar, tile, s_tw, tw, &src, pl0, kx0, kb, (rows_in + RB - 1) / RB);
+  if (!col_wait(bar, flag, max_polls)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = 2 * warp; c < NC; c += 2 * (COL_THREADS / 32)) {
+    const ColPair<PB> A{tile + (c / PB) * P * PB, (c % PB) >> 1};
     cpair v[R];
 #pragma unroll
     for (int i = 0; i < R; ++i) {
       const int y = lane + 32 * i;
       if (y < rows_in)
-        vld(v[i], tile + y * LDT + c);
+        vld(v[i], A(y));
       else
         vzero(v[i]);
     }
-    warp_fft<P, false>(v, lane, s_tw, tile + c, LDT);
+    warp_fft<P, false, FFT_TILE>(v, lane, s_tw, A);
 #pragma unroll
-    for (int i = 0; i < R; ++i) vst(tile + col_row<P>(out_pos<P>(lane, i)) * LDT + c, v[i]);
+    for (int i = 0; i < R; ++i) vst(A(out_pos<P, FFT_TILE>(lane, i)), v[i]);
   }
-  if constexpr (BULK) {
-    col_stage_out(
-        P * kb, np, [&](int r) { return tile + col_row<P>(r / kb) * LDT + (r % kb) * PB; },
-        [&](int r) { return out + ((size_t)(r / kb) * h + kx0 + r % kb) * ldf + pl0; });
-  } else {
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
-      const int ky = idx / NC, cc = idx % NC;
-      const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
-      if (kx < h && pl < nplanes) out[((size_t)ky * h + kx) * ldf + pl] = tile[col_row<P>(ky) * LDT + cc];
-    }
-  }
+  col_store<P, PB>(tile, &dst, pl0, kx0, kb, P / RB);
 }
 
-// Inverse C2C along y: in[ky h + kx][ldf] -> inter[row][kx][LP] for the first rows_out rows.
-template <int P, int PB, int NC, bool BULK>
-__global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const float2* __restrict__ in, int ldf, int nplanes,
-                                                          int rows_out, int h, int hp,
-                                                          float2* __restrict__ inter,
-                                                          const float2* __restrict__ tw, int* __restrict__ flag,
-                                                          long long max_polls) {
+// Inverse C2C along y: spectra [ky][kx][plane] (map `src`: nplanes x h x P) ->
+// inter[row][kx][plane] for the first rows_out rows (map `dst`: nplanes x h x rows_out).
+template <int P, int PB, int NC>
+__global__ void __launch_bounds__(COL_THREADS) k_cols_inv(const __grid_constant__ CUtensorMap src,
+                                                          const __grid_constant__ CUtensorMap dst, int rows_out,
+                                                          int h, const float2* __restrict__ tw,
+                                                          int* __restrict__ flag, long long max_polls) {
   constexpr int R = P / 32;
   constexpr int KB = NC / PB;
-  constexpr int LDT = col_ld<NC>();
+  constexpr int RB = col_rb<P>();
   extern __shared__ float4 col_smem4[];
-  uint64_t* bar = reinterpret_cast<uint64_t*>(col_smem4);
-  float2* s_tw = reinterpret_cast<float2*>(col_smem4 + 1);
-  float2* tile = s_tw + tw_pad(P);
+  float2* tile = reinterpret_cast<float2*>(align1024(col_smem4));
+  float2* s_tw = tile + P * NC;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_tw + tw_pad(P));
   const int kx0 = blockIdx.x * KB, pl0 = blockIdx.y * PB;
-  const int LP = plane_ld(nplanes);
-  const int kb = min(KB, h - kx0), np = min(PB, nplanes - pl0);
-  if constexpr (BULK) {
-    // runs rounded up to an even plane count stay inside the ldf pitch (a multiple of 8)
-    const unsigned run = (unsigned)((np + 1) & ~1) * sizeof(float2);
-    if (!col_stage_in<P>(
-            bar, s_tw, tw, P * kb, run,
-            [&](int r) { return in + ((size_t)(r / kb) * h + kx0 + r % kb) * ldf + pl0; },
-            [&](int r) { return tile + (r / kb) * LDT + (r % kb) * PB; }, flag, max_polls))
-      return;
-  } else {
-    for (int i = threadIdx.x; i < tw_pad(P); i += COL_THREADS) s_tw[i] = tw[i];
-    for (int idx = threadIdx.x; idx < P * NC; idx += COL_THREADS) {
-      const int ky = idx / NC, cc = idx % NC;
-      const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
-      float2 val = make_float2(0.f, 0.f);
-      if (kx < h && pl < nplanes) val = in[((size_t)ky * h + kx) * ldf + pl];
-      tile[ky * LDT + cc] = val;
-    }
-    __syncthreads();
-  }
+  const int kb = min(KB, h - kx0);
+  if (threadIdx.x == 0) col_load_issue<P, PB>(bar, tile, s_tw, tw, &src, pl0, kx0, kb, P / RB);
+  if (!col_wait(bar, flag, max_polls)) return;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int c = 2 * warp; c < NC; c += 2 * (COL_THREADS / 32)) {
+    const ColPair<PB> A{tile + (c / PB) * P * PB, (c % PB) >> 1};
     cpair v[R];
 #pragma unroll
-    for (int i = 0; i < R; ++i) vld(v[i], tile + (lane + 32 * i) * LDT + c);
-    warp_fft<P, true>(v, lane, s_tw, tile + c, LDT);
+    for (int i = 0; i < R; ++i) vld(v[i], A(lane + 32 * i));
+    warp_fft<P, true, FFT_TILE>(v, lane, s_tw, A);
 #pragma unroll
     for (int i = 0; i < R; ++i) {
-      const int y = out_pos<P>(lane, i);
-      if (y < rows_out) vst(tile + col_row<P>(y) * LDT + c, v[i]);
+      const int y = out_pos<P, FFT_TILE>(lane, i);
+      if (y < rows_out) vst(A(y), v[i]);
     }
   }
-  if constexpr (BULK) {
-    col_stage_out(
-        rows_out * kb, np, [&](int r) { return tile + col_row<P>(r / kb) * LDT + (r % kb) * PB; },
-        [&](int r) { return inter + ((size_t)(r / kb) * hp + kx0 + r % kb) * LP + pl0; });
-  } else {
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < rows_out * NC; idx += COL_THREADS) {
-      const int row = idx / NC, cc = idx % NC;
-      const int kx = kx0 + cc / PB, pl = pl0 + cc % PB;
-      if (kx < h && pl < nplanes) inter[((size_t)row * hp + kx) * LP + pl] = tile[col_row<P>(row) * LDT + cc];
-    }
-  }
+  col_store<P, PB>(tile, &dst, pl0, kx0, kb, (rows_out + RB - 1) / RB);
 }
 
 // ------------------------------------------------------------ launchers ----
-
-size_t row_smem(int p) {
-  return (size_t)(tw_pad(p) + (p / 2 + 1) * SH_LD + ROW_WARPS * (p + 2)) * sizeof(float2);
-}
-
-// Bulk staging needs 16-byte aligned buffers and an even spectrum pitch (the
-// intermediate's plane pitch is a multiple of 16).
-bool cols_bulk_ok(const void* a, const void* b, const void* tw, int ldf) {
-  return ((reinterpret_cast<uintptr_t>(a) | reinterpret_cast<uintptr_t>(b) | reinterpret_cast<uintptr_t>(tw)) &
-          15) == 0 &&
-         (ldf & 1) == 0;
-}
 
 template <typename F>
 cudaError_t allow_smem(F* fn, size_t bytes) {
@@ -732,6 +805,48 @@ int row_grid(int rows, int nplanes) {
   return jobs < 1 ? 1 : (jobs > cap ? cap : jobs);
 }
 
+// cuTensorMapEncodeTiled from the driver, looked up once through the runtime.
+PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess) {
+      cudaGetLastError();
+      p = nullptr;
+    }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
+  return fn;
+}
+
+// 3-D tensor map over 8-byte elements (a float2 each): planes (contiguous,
+// nplanes of them), kx (h, pitch ld_kx elements), rows (pitch ld_row
+// elements); box {b0, b1, b2}; swizzle = the box's inner size in bytes (64
+// or 128).
+ctof_status plane_map(CUtensorMap* m, const float2* base, int nplanes, int h, int rows, size_t ld_kx, size_t ld_row,
+                      int b0, int b1, int b2) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) {
+    ctof_set_last_error_text("cuTensorMapEncodeTiled is not available from the driver");
+    return CTOF_ECUDA;
+  }
+  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld_kx & 1) || (ld_row & 1)) return CTOF_EINVAL;
+  const cuuint64_t dims[3] = {(cuuint64_t)nplanes, (cuuint64_t)h, (cuuint64_t)rows};
+  const cuuint64_t strides[2] = {(cuuint64_t)(ld_kx * sizeof(float2)), (cuuint64_t)(ld_row * sizeof(float2))};
+  const cuuint32_t box[3] = {(cuuint32_t)b0, (cuuint32_t)b1, (cuuint32_t)b2};
+  const cuuint32_t es[3] = {1, 1, 1};
+  const CUtensorMapSwizzle sw = b0 * sizeof(float2) == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2*>(base), dims, strides, box, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    ctof_set_last_error_text("cuTensorMapEncodeTiled rejected an FFT plane map");
+    return CTOF_ECUDA;
+  }
+  return CTOF_OK;
+}
+
 #define CTOF_P_SWITCH(p, ...)                                    \
   switch (p) {                                                   \
     case 32: { constexpr int P_ = 32; __VA_ARGS__; } break;      \
@@ -741,16 +856,25 @@ int row_grid(int rows, int nplanes) {
     case 512: { constexpr int P_ = 512; __VA_ARGS__; } break;    \
     default: return CTOF_EUNSUPPORTED;                           \
   }
+
+// Row-pass map over inter[row][kx][plane]: boxes of 16 planes x rkx(P) kx x 1 row.
+ctof_status row_map(const ctof_kernel_s* k, CUtensorMap* m, const float2* inter, int nplanes, int rows) {
+  const size_t LP = plane_ld(nplanes);
+  return plane_map(m, inter, nplanes, k->h, rows, LP, (size_t)k->hp * LP, RP, rkx(k->p), 1);
+}
+
 }  // namespace
 
 ctof_status fft_rows_forward(const ctof_kernel_s* k, const float* in, int nplanes, int rows, int cols_in,
                              int ld_in, float2* inter, cudaStream_t st) {
   if (nplanes <= 0 || rows <= 0) return CTOF_OK;
-  const size_t sm = row_smem(k->p);
+  CUtensorMap map;
+  CTOF_TRY(row_map(k, &map, inter, nplanes, rows));
+  const size_t sm = row_smem_bytes(k->p);
   CTOF_P_SWITCH(k->p, {
     CTOF_CUDA_TRY(allow_smem(k_rows_fwd<P_>, sm));
-    k_rows_fwd<P_><<<row_grid(rows, nplanes), ROW_WARPS * 32, sm, st>>>(in, nplanes, rows, cols_in, ld_in, inter,
-                                                                         k->hp, k->d_tw);
+    k_rows_fwd<P_><<<row_grid(rows, nplanes), ROW_WARPS * 32, sm, st>>>(map, in, nplanes, rows, cols_in, ld_in,
+                                                                         k->d_tw);
   });
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
@@ -759,12 +883,14 @@ ctof_status fft_rows_forward(const ctof_kernel_s* k, const float* in, int nplane
 ctof_status fft_rows_inverse(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows, int cols_out,
                              float* out, int ld_out, cudaStream_t st) {
   if (nplanes <= 0 || rows <= 0) return CTOF_OK;
-  const size_t sm = row_smem(k->p);
+  CUtensorMap map;
+  CTOF_TRY(row_map(k, &map, inter, nplanes, rows));
+  const size_t sm = row_smem_bytes(k->p);
   const float scale = 1.0f / ((float)k->p * (float)k->p);
   CTOF_P_SWITCH(k->p, {
     CTOF_CUDA_TRY(allow_smem(k_rows_inv<P_>, sm));
-    k_rows_inv<P_><<<row_grid(rows, nplanes), ROW_WARPS * 32, sm, st>>>(inter, nplanes, rows, k->hp, cols_out, out,
-                                                                         ld_out, scale, k->d_tw);
+    k_rows_inv<P_><<<row_grid(rows, nplanes), ROW_WARPS * 32, sm, st>>>(map, nplanes, rows, cols_out, out, ld_out,
+                                                                         scale, k->d_tw, k->d_flags, k->max_polls);
   });
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
@@ -772,46 +898,60 @@ ctof_status fft_rows_inverse(const ctof_kernel_s* k, const float2* inter, int np
 
 ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* m, float* u1, float inv_scale,
                             float rho, cudaStream_t st) {
-  const size_t sm = row_smem(k->p);
+  CUtensorMap map;
+  CTOF_TRY(row_map(k, &map, inter, k->nt, k->n));
+  const size_t sm = row_smem_bytes(k->p);
   const float scale = 1.0f / ((float)k->p * (float)k->p);
   CTOF_P_SWITCH(k->p, {
     CTOF_CUDA_TRY(allow_smem(k_rows_admm_t<P_>, sm));
-    k_rows_admm_t<P_><<<row_grid(k->n, k->nt), ROW_WARPS * 32, sm, st>>>(inter, k->nt, k->n, k->hp, m, u1, scale,
-                                                                          inv_scale, rho, k->d_tw);
+    k_rows_admm_t<P_><<<row_grid(k->n, k->nt), ROW_WARPS * 32, sm, st>>>(map, k->nt, k->n, m, u1, scale, inv_scale,
+                                                                          rho, k->d_tw, k->d_flags, k->max_polls);
   });
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
 
-// Tile codes: PB for NC = 32 (8, 16, 32), 100 + PB for NC = 16 (108, 116);
-// code 0 = the element-wise variant (NC = 32, PB = 8) for buffers the bulk
-// copies cannot take.
-#define CTOF_COLS_CASE(KERN, PB_, NC_, BULK_, ...)                       \
-  CTOF_P_SWITCH(k->p, {                                                  \
-    CTOF_CUDA_TRY(allow_smem(KERN<P_, PB_, NC_, BULK_>, sm));            \
-    KERN<P_, PB_, NC_, BULK_><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__); \
+namespace {
+
+// Tile codes: PB for NC = 32 (8, 16), 100 + PB for NC = 16 (108, 116).
+#define CTOF_COLS_CASE(KERN, PB_, NC_, ...)                                \
+  CTOF_P_SWITCH(k->p, {                                                    \
+    CTOF_CUDA_TRY(allow_smem(KERN<P_, PB_, NC_>, sm));                     \
+    KERN<P_, PB_, NC_><<<grid, COL_THREADS, sm, st>>>(__VA_ARGS__);        \
   })
 
-#define CTOF_COLS_LAUNCH(KERN, ...)                                                         \
-  do {                                                                                      \
-    const int pb = code == 0 ? 8 : (code >= 100 ? code - 100 : code), nc = code >= 100 ? 16 : 32; \
-    const size_t sm = col_smem_bytes(k->p, nc);                                             \
-    dim3 grid(ctof_div_up(k->h, nc / pb), ctof_div_up(nplanes, pb));                       \
-    switch (code) {                                                                         \
-      case 0: CTOF_COLS_CASE(KERN, 8, 32, false, __VA_ARGS__); break;                       \
-      case 32: CTOF_COLS_CASE(KERN, 32, 32, true, __VA_ARGS__); break;                      \
-      case 16: CTOF_COLS_CASE(KERN, 16, 32, true, __VA_ARGS__); break;                      \
-      case 116: CTOF_COLS_CASE(KERN, 16, 16, true, __VA_ARGS__); break;                     \
-      case 108: CTOF_COLS_CASE(KERN, 8, 16, true, __VA_ARGS__); break;                      \
-      default: CTOF_COLS_CASE(KERN, 8, 32, true, __VA_ARGS__);                              \
-    }                                                                                       \
+#define CTOF_COLS_LAUNCH(KERN, ...)                                                      \
+  do {                                                                                   \
+    const size_t sm = col_smem_bytes(k->p, nc);                                          \
+    dim3 grid(ctof_div_up(k->h, nc / pb), ctof_div_up(nplanes, pb));                     \
+    switch (code) {                                                                      \
+      case 16: CTOF_COLS_CASE(KERN, 16, 32, __VA_ARGS__); break;                         \
+      case 116: CTOF_COLS_CASE(KERN, 16, 16, __VA_ARGS__); break;                        \
+      case 108: CTOF_COLS_CASE(KERN, 8, 16, __VA_ARGS__); break;                         \
+      default: CTOF_COLS_CASE(KERN, 8, 32, __VA_ARGS__);                                 \
+    }                                                                                    \
   } while (0)
+
+// Plane tile (planes per tile, columns per tile) of a tile code.
+void tile_of(int& code, int& pb, int& nc) {
+  if (code != 16 && code != 108 && code != 116) code = 8;
+  pb = code >= 100 ? code - 100 : code;
+  nc = code >= 100 ? 16 : 32;
+}
+
+}  // namespace
 
 ctof_status fft_cols_forward_pb(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows_in, float2* out,
                                 int ldf, int code, cudaStream_t st) {
   if (nplanes <= 0) return CTOF_OK;
-  if (!cols_bulk_ok(inter, out, k->d_tw, ldf)) code = 0;
-  CTOF_COLS_LAUNCH(k_cols_fwd, inter, nplanes, rows_in, k->h, k->hp, out, ldf, k->d_tw, k->d_flags, k->max_polls);
+  int pb, nc;
+  tile_of(code, pb, nc);
+  const int P = k->p, rb = P < 256 ? P : 256;
+  const size_t LP = plane_ld(nplanes);
+  CUtensorMap src, dst;
+  CTOF_TRY(plane_map(&src, inter, nplanes, k->h, rows_in, LP, (size_t)k->hp * LP, pb, 1, rb));
+  CTOF_TRY(plane_map(&dst, out, nplanes, k->h, P, ldf, (size_t)k->h * ldf, pb, 1, rb));
+  CTOF_COLS_LAUNCH(k_cols_fwd, src, dst, rows_in, k->h, k->d_tw, k->d_flags, k->max_polls);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
@@ -825,8 +965,14 @@ ctof_status fft_cols_forward(const ctof_kernel_s* k, const float2* inter, int np
 ctof_status fft_cols_inverse_pb(const ctof_kernel_s* k, const float2* in, int ldf, int nplanes, int rows_out,
                                 float2* inter, int code, cudaStream_t st) {
   if (nplanes <= 0) return CTOF_OK;
-  if (!cols_bulk_ok(in, inter, k->d_tw, ldf)) code = 0;
-  CTOF_COLS_LAUNCH(k_cols_inv, in, ldf, nplanes, rows_out, k->h, k->hp, inter, k->d_tw, k->d_flags, k->max_polls);
+  int pb, nc;
+  tile_of(code, pb, nc);
+  const int P = k->p, rb = P < 256 ? P : 256;
+  const size_t LP = plane_ld(nplanes);
+  CUtensorMap src, dst;
+  CTOF_TRY(plane_map(&src, in, nplanes, k->h, P, ldf, (size_t)k->h * ldf, pb, 1, rb));
+  CTOF_TRY(plane_map(&dst, inter, nplanes, k->h, rows_out, LP, (size_t)k->hp * LP, pb, 1, rb));
+  CTOF_COLS_LAUNCH(k_cols_inv, src, dst, rows_out, k->h, k->d_tw, k->d_flags, k->max_polls);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
@@ -850,9 +996,12 @@ void fft_twiddle_table(int p, float2* out) {
       int s = 1;
       while (2 * s - 1 <= e) s *= 2;  // stage s holds entries s-1 .. 2s-2
       j = (e - (s - 1)) * (p / (2 * s));
-    } else if (i < tw_count(p)) {
+    } else if (i < tw4_base(p)) {
       const int e = i - p - 31;
       j = ((e & 31) * (e / 32 + 1)) & (p - 1);
+    } else if (i < tw_count(p)) {
+      const int e = i - tw4_base(p);
+      j = ((p / 32) * (e & 7) * (e / 8 + 1)) & (p - 1);
     }
     out[i] = make_float2((float)cos(two_pi * j / p), (float)-sin(two_pi * j / p));
   }

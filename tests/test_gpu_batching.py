@@ -70,7 +70,7 @@ def test_autotuner_choices(batch):
     kernels, _, _ = batch
     for k in kernels:
         t = k.tuning()
-        assert all(v in (8, 16, 32, 108, 116) for v in t)
+        assert all(v in (8, 16, 108, 116) for v in t)
 
 
 def test_batch_rejects_repeated_handle(batch):
