@@ -8,22 +8,28 @@
 // Two passes per direction, through an intermediate inter[row][kx][plane]
 // (plane fastest, plane pitch LP = nplanes rounded up to 16):
 //   rows    (x axis, real <-> complex): a CTA takes one row index for 16
-//           planes; each warp transforms the rows of two planes packed as one
-//           complex row and splits them with the Hermitian identities; the 16
-//           planes' half spectra leave through shared memory as 128-byte runs
-//           of consecutive planes.
-//   columns (y axis, complex): a CTA stages 32 columns (32/PB kx x PB
-//           consecutive planes) of all rows in shared memory, each warp
-//           transforms whole columns; both the intermediate and the
-//           frequency-major spectra are read and written in runs of PB planes
-//           (PB = 8, 16 or 32, picked per handle by the autotuner).  The
-//           transpose between plane-major input planes and frequency-major
-//           spectra happens in the row pass's shared-memory tile.
-// Each 1-D transform of length P = 32 R lives in one warp: lane l register r
-// holds element l + 32 r; an R-point DIF over registers, a twiddle by
-// w_P^(l k2), and a 32-point DIF across lanes (shuffles) give element
-// R*bitrev5(l) + bitrev_R(r).  Twiddles exp(-2 pi i j/P) are computed on the
-// host in double precision and staged in shared memory.
+//           planes at a time (persistent over jobs); each warp transforms the
+//           rows of two planes packed as one complex row and splits them with
+//           the Hermitian identities; the 16 planes' half spectra of the row
+//           move between the intermediate and shared memory as tensor-map
+//           boxes (16 planes x up to 256 kx), double-buffered so that the next
+//           job's box is in flight while the CTA works on the current one.
+//   columns (y axis, complex): a CTA holds NC columns (NC/PB kx x PB
+//           consecutive planes, PB = 8 or 16, NC = 16 or 32, picked per handle
+//           by the autotuner) of all rows, loaded and stored as tensor-map
+//           boxes (PB planes x 1 kx x up to 256 rows); each warp transforms two
+//           columns at once.  The transpose between plane-major input planes
+//           and frequency-major spectra happens in the row pass.
+// Shared-memory tiles use the copy engine's 64/128-byte swizzle, under which
+// the 16-byte accesses of a quarter-warp to eight rows that are distinct mod 8
+// are conflict-free; out-of-range planes, kx and rows are zero-filled by the
+// loads and skipped by the stores.
+// Each 1-D transform of length P = 32 R lives in one warp: lane l register i
+// holds element l + 32 i; an R-point DFT over the registers (constant
+// twiddles), a twiddle by w_P^(l k1), and a 32-point DFT across the lanes,
+// from P = 256 on as 4 x 8 points in registers through the warp's scratch,
+// below as five shuffle stages.  Twiddles are computed on the host in double
+// precision and staged in shared memory.
 #include <cuda_runtime.h>
 
 #include <cuda.h>
@@ -37,8 +43,7 @@ namespace {
 
 // Column-pass tiles hold NC = 32 or 16 columns: KB kx-columns x PB planes;
 // the tile shape (NC, PB) is chosen per handle and use by the autotuner
-// (tile code PB for NC = 32, 100 + PB for NC = 16: smaller tiles, more CTAs
-// per SM).
+// (tile code PB for NC = 32, 100 + PB for NC = 16).
 constexpr int COL_THREADS = 256;
 constexpr int ROW_WARPS = 8;
 
