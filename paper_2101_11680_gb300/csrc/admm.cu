@@ -4,7 +4,7 @@
 //   v3 = max(a3, 0) on the scan support S (0 off S),  u3 <- a3 - v3,  w3 = 2 v3 - a3
 //   s  = D^T w2 + w3      (the Z-side part of the next x-update right-hand side)
 // D: forward differences, lateral periodic on the P x P grid, axial Neumann
-// (Z-1 differences).  One CTA owns a 32 x 8 lateral tile of one depth plane;
+// (Z-1 differences).  One CTA owns a 32 x 8 lateral tile of four depth planes;
 // the backward differences of D^T need w2 of the left/upper/previous-plane
 // neighbours, which are recomputed from the previous u2 (hence u2 is double
 // buffered: blocks read the old copy, write the new one).
@@ -21,84 +21,121 @@ __device__ __forceinline__ float soft(float a, float thr) {
   return m > 0.f ? copysignf(m, a) : 0.f;
 }
 
-// One CTA per (32 x 8 lateral tile, depth plane j).  The axial backward
-// difference needs w2z of plane j-1, which is pointwise in (x[j-1], x[j],
-// u2z[j-1]) and is recomputed here rather than carried across planes.
+// One CTA per (32 x 8 lateral tile, ZP consecutive depth planes j0 ..); each
+// thread handles its (x, y) in all ZP planes at once: every load of the block
+// is issued before the first use, and the axial neighbours of planes inside
+// the group come from the staged tiles and registers.  The axial backward
+// difference of plane j0 needs w2z of plane j0 - 1, which is pointwise in
+// (x[j0-1], x[j0], u2z[j0-1]) and is recomputed here.
+constexpr int ZP = 4;
+
 __global__ void __launch_bounds__(TX* TY) k_tv_stencil(const float* __restrict__ x, const float* __restrict__ u2o,
                                                        float* __restrict__ u2n, float* __restrict__ u3,
                                                        float* __restrict__ s_out, const double* __restrict__ beta,
                                                        float inv_rho, int P, int nz, int n,
                                                        float* __restrict__ out_crop) {
-  __shared__ float sX[TY + 2][TX + 2];
-  __shared__ float sW2x[TY][TX + 1];
-  __shared__ float sW2y[TY + 1][TX];
+  __shared__ float sX[ZP][TY + 2][TX + 2];
+  __shared__ float sW2x[ZP][TY][TX + 1];
+  __shared__ float sW2y[ZP][TY + 1][TX];
   const int tx = threadIdx.x, ty = threadIdx.y;
-  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, j = blockIdx.z;
+  const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY, j0 = blockIdx.z * ZP;
   const int gx = x0 + tx, gy = y0 + ty;
   const size_t plane = (size_t)P * P;
   const float thr = (float)(beta[0]) * inv_rho;
   const bool in_s = gx < n && gy < n;
   const int tid = ty * TX + tx;
-  const float* xp = x + (size_t)j * plane;
-  for (int i = tid; i < (TY + 2) * (TX + 2); i += TX * TY) {
-    const int ly = i / (TX + 2), lx = i - ly * (TX + 2);
-    const int yy = (y0 + ly - 1 + P) & (P - 1), xx = (x0 + lx - 1 + P) & (P - 1);
-    sX[ly][lx] = xp[(size_t)yy * P + xx];
-  }
-  const size_t pix = (size_t)gy * P + gx;
-  const size_t idx = (size_t)j * plane + pix;
   const float* u2oy = u2o + plane * nz;
   const float* u2oz = u2o + 2 * plane * nz;
-  // w2z of the plane above (j-1), pointwise
+  const int xl = (gx - 1 + P) & (P - 1), yu = (gy - 1 + P) & (P - 1);
+  for (int i = tid; i < ZP * (TY + 2) * (TX + 2); i += TX * TY) {
+    const int q = i / ((TY + 2) * (TX + 2)), r = i - q * ((TY + 2) * (TX + 2));
+    const int ly = r / (TX + 2), lx = r - ly * (TX + 2);
+    const int yy = (y0 + ly - 1 + P) & (P - 1), xx = (x0 + lx - 1 + P) & (P - 1);
+    if (j0 + q < nz) sX[q][ly][lx] = x[(size_t)(j0 + q) * plane + (size_t)yy * P + xx];
+  }
+  const float* base = x + (size_t)gy * P + gx;
+  const size_t pix = (size_t)gy * P + gx;
+  float vu2x[ZP], vu2y[ZP], vu2z[ZP], vu3[ZP], vlx[ZP], vuy[ZP];
+#pragma unroll
+  for (int q = 0; q < ZP; ++q) {
+    vu2x[q] = vu2y[q] = vu2z[q] = vu3[q] = vlx[q] = vuy[q] = 0.f;
+    if (j0 + q < nz) {
+      const size_t jp = (size_t)(j0 + q) * plane;
+      vu2x[q] = u2o[jp + pix];
+      vu2y[q] = u2oy[jp + pix];
+      vu2z[q] = u2oz[jp + pix];
+      vu3[q] = u3[jp + pix];
+      if (tx == 0) vlx[q] = u2o[jp + (size_t)gy * P + xl];
+      if (ty == 0) vuy[q] = u2oy[jp + (size_t)yu * P + gx];
+    }
+  }
+  // axial neighbours outside the group: x[j0 - 1], u2z[j0 - 1] and x[j0 + ZP]
+  const float xm = j0 > 0 ? base[(size_t)(j0 - 1) * plane] : 0.f;
+  const float u2zm = j0 > 0 ? u2oz[(size_t)(j0 - 1) * plane + pix] : 0.f;
+  const float xp = j0 + ZP < nz ? base[(size_t)(j0 + ZP) * plane] : 0.f;
+  __syncthreads();
   float w2z_prev = 0.f;
-  if (j > 0) {
-    const float a = (x[idx] - x[idx - plane]) + u2oz[idx - plane];
+  if (j0 > 0) {
+    const float a = (sX[0][ty + 1][tx + 1] - xm) + u2zm;
     w2z_prev = 2.f * soft(a, thr) - a;
   }
+  float vs[ZP], vv3[ZP];
+#pragma unroll
+  for (int q = 0; q < ZP; ++q) {
+    const int j = j0 + q;
+    vs[q] = vv3[q] = 0.f;
+    if (j >= nz) continue;
+    const size_t idx = (size_t)j * plane + pix;
+    const float c = sX[q][ty + 1][tx + 1];
+    float w2x, w2y, w2z;
+    {
+      const float a = (sX[q][ty + 1][tx + 2] - c) + vu2x[q];
+      const float v = soft(a, thr);
+      u2n[idx] = a - v;
+      w2x = 2.f * v - a;
+    }
+    {
+      const float a = (sX[q][ty + 2][tx + 1] - c) + vu2y[q];
+      const float v = soft(a, thr);
+      u2n[plane * nz + idx] = a - v;
+      w2y = 2.f * v - a;
+    }
+    if (j < nz - 1) {
+      const float xn = q + 1 < ZP ? sX[q + 1 < ZP ? q + 1 : 0][ty + 1][tx + 1] : xp;
+      const float a = (xn - c) + vu2z[q];
+      const float v = soft(a, thr);
+      u2n[2 * plane * nz + idx] = a - v;
+      w2z = 2.f * v - a;
+    } else {
+      u2n[2 * plane * nz + idx] = 0.f;
+      w2z = 0.f;
+    }
+    const float a3 = c + vu3[q];
+    const float v3 = in_s ? fmaxf(a3, 0.f) : 0.f;
+    u3[idx] = a3 - v3;
+    vv3[q] = v3;
+    sW2x[q][ty][tx + 1] = w2x;
+    sW2y[q][ty + 1][tx] = w2y;
+    if (tx == 0) {
+      const float a = (c - sX[q][ty + 1][0]) + vlx[q];
+      sW2x[q][ty][0] = 2.f * soft(a, thr) - a;
+    }
+    if (ty == 0) {
+      const float a = (c - sX[q][0][tx + 1]) + vuy[q];
+      sW2y[q][0][tx] = 2.f * soft(a, thr) - a;
+    }
+    vs[q] = (w2z_prev - w2z) + (2.f * v3 - a3);
+    w2z_prev = w2z;
+  }
   __syncthreads();
-  const float c = sX[ty + 1][tx + 1];
-  float w2x, w2y, w2z;
-  {
-    const float a = (sX[ty + 1][tx + 2] - c) + u2o[idx];
-    const float v = soft(a, thr);
-    u2n[idx] = a - v;
-    w2x = 2.f * v - a;
+#pragma unroll
+  for (int q = 0; q < ZP; ++q) {
+    const int j = j0 + q;
+    if (j >= nz) continue;
+    const size_t idx = (size_t)j * plane + pix;
+    s_out[idx] = (sW2x[q][ty][tx] - sW2x[q][ty][tx + 1]) + (sW2y[q][ty][tx] - sW2y[q][ty + 1][tx]) + vs[q];
+    if (out_crop && in_s) out_crop[((size_t)j * n + gy) * n + gx] = vv3[q];
   }
-  {
-    const float a = (sX[ty + 2][tx + 1] - c) + u2oy[idx];
-    const float v = soft(a, thr);
-    u2n[plane * nz + idx] = a - v;
-    w2y = 2.f * v - a;
-  }
-  if (j < nz - 1) {
-    const float a = (x[idx + plane] - c) + u2oz[idx];
-    const float v = soft(a, thr);
-    u2n[2 * plane * nz + idx] = a - v;
-    w2z = 2.f * v - a;
-  } else {
-    u2n[2 * plane * nz + idx] = 0.f;
-    w2z = 0.f;
-  }
-  const float a3 = c + u3[idx];
-  const float v3 = in_s ? fmaxf(a3, 0.f) : 0.f;
-  u3[idx] = a3 - v3;
-  const float w3 = 2.f * v3 - a3;
-  sW2x[ty][tx + 1] = w2x;
-  sW2y[ty + 1][tx] = w2y;
-  if (tx == 0) {
-    const int xl = (gx - 1 + P) & (P - 1);
-    const float a = (c - sX[ty + 1][0]) + u2o[(size_t)j * plane + (size_t)gy * P + xl];
-    sW2x[ty][0] = 2.f * soft(a, thr) - a;
-  }
-  if (ty == 0) {
-    const int yu = (gy - 1 + P) & (P - 1);
-    const float a = (c - sX[0][tx + 1]) + u2oy[(size_t)j * plane + (size_t)yu * P + gx];
-    sW2y[0][tx] = 2.f * soft(a, thr) - a;
-  }
-  __syncthreads();
-  const float s = (sW2x[ty][tx] - sW2x[ty][tx + 1]) + (sW2y[ty][tx] - sW2y[ty + 1][tx]) + (w2z_prev - w2z) + w3;
-  s_out[idx] = s;
-  if (out_crop && in_s) out_crop[((size_t)j * n + gy) * n + gx] = v3;
 }
 
 __global__ void k_max_abs(const float* __restrict__ v, size_t count, unsigned int* __restrict__ out) {
@@ -213,7 +250,7 @@ int grid_elem(size_t count) {
 ctof_status admm_tv_stencil(const ctof_kernel_s* k, const float* x, const float* u2_old, float* u2_new, float* u3,
                             float* s, const double* beta_dev, float rho, float* out_crop, cudaStream_t st) {
   dim3 block(TX, TY);
-  dim3 grid(k->p / TX, k->p / TY, k->nz);
+  dim3 grid(k->p / TX, k->p / TY, ctof_div_up(k->nz, ZP));
   k_tv_stencil<<<grid, block, 0, st>>>(x, u2_old, u2_new, u3, s, beta_dev, 1.0f / rho, k->p, k->nz, k->n, out_crop);
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
