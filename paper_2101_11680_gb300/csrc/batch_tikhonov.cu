@@ -43,6 +43,7 @@
 #include <cuda_fp8.h>
 #include <cuda_runtime.h>
 
+#include "bulk.cuh"
 #include "ctof_internal.h"
 #include "umma.cuh"
 
@@ -634,6 +635,569 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_tikhonov_tc(
   if (warp == 0) umma::tmem_dealloc(taddr, 256);
 }
 
+// ======================= warp-specialised kernel (even nt) =======================
+//
+// Roles (14 warps): warp 0 (one thread) stages each t chunk with tensor-map
+// copies (m_hat boxes of 16 volumes x 16 t per member, W_hat boxes of 32 t x
+// 32 z, both in the 128-byte swizzle) into two raw stages; warps 1-8 split a
+// staged chunk into its narrow-format terms (two term sets); warp 9 (one
+// thread) issues the tcgen05 MMAs of each term set into one of two TMEM
+// accumulator sets; warps 10-13 run the solve and the refinement of one
+// (class, volume chunk) item from its accumulator set while the next item
+// streams through the others.  Hand-offs go through mbarriers (raw full /
+// empty, term full / empty, accumulators full / empty, class tables, solve
+// MMAs); every wait is bounded, a wait that runs out sets the handle's flag
+// and a shared abort word, and every role then leaves its loop.
+// GEMM rows: right-hand side n = 32 member + 16 re/im + volume.
+
+constexpr int WS_CONV = 8;      // converter warps 1 .. 8
+constexpr int WS_MMA_WARP = 9;  // MMA issuer
+constexpr int WS_EPI0 = 10;     // epilogue warps 10 .. 13
+constexpr int WS_EPI = 4;
+constexpr int WS_THREADS = (WS_EPI0 + WS_EPI) * 32;
+constexpr int WS_MBOX = 16 * 16 * 8;  // m_hat box: 16 volumes x 16 t x 8 bytes
+constexpr int WS_WBOX = 32 * 32 * 4;  // W_hat box: 32 t x 32 z x 4 bytes
+
+struct WsPlan {
+  int nt, nz, z4, zn, fp8, nterm, nacc, esize, epc;
+  int a_term, b_term, set_bytes;
+  int nwb;        // W boxes per chunk
+  int raw_stage;  // bytes of one raw stage (1024-byte multiple)
+  int tab_bytes, x_tile;
+  int off_raw, off_set, off_tab, off_xh, off_xl, off_sn, off_bar, total;
+  int batch, nvc;
+};
+
+WsPlan make_ws_plan(int nt, int nz, int fp8, int batch) {
+  WsPlan P{};
+  P.nt = nt;
+  P.nz = nz;
+  P.z4 = rup(nz, 4);
+  P.zn = rup(nz, 16);
+  P.fp8 = fp8;
+  P.nterm = fp8 ? 3 : 2;
+  P.nacc = fp8 ? 3 : 2;
+  P.esize = fp8 ? 1 : 2;
+  P.epc = 16 / P.esize;
+  P.a_term = NR * TCH * P.esize;
+  P.b_term = P.zn * TCH * P.esize;
+  P.set_bytes = P.nterm * (P.a_term + P.b_term);
+  P.nwb = P.z4 <= 32 ? 1 : 2;
+  P.raw_stage = rup(8 * WS_MBOX + P.nwb * WS_WBOX, 1024);
+  P.tab_bytes = 4 * P.zn * P.zn * 4;
+  P.x_tile = NR * P.zn * 4;
+  P.batch = batch;
+  P.nvc = (batch + VB - 1) / VB;
+  int off = 0;
+  auto take = [&](int bytes, int align) {
+    off = rup(off, align);
+    const int at = off;
+    off += bytes;
+    return at;
+  };
+  P.off_raw = take(2 * P.raw_stage, 1024);
+  P.off_set = take(2 * P.set_bytes, 128);
+  P.off_tab = take(P.tab_bytes, 128);
+  P.off_xh = take(P.x_tile, 128);
+  P.off_xl = take(P.x_tile, 128);
+  P.off_sn = take(2 * NR * 4, 16);
+  P.off_bar = take(256, 16);
+  P.total = off + 1024;  // room to align the dynamic shared memory base to 1024 bytes
+  return P;
+}
+
+__device__ __forceinline__ int ws_row(int v, int m, int ri) { return 32 * m + 16 * ri + v; }
+
+// Bounded wait that also stops once another role has given up.
+__device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, long long max_polls, volatile int* abort_w,
+                                        int* flag) {
+  for (long long i = 0; i < max_polls; ++i) {
+    if (bulk::try_wait(bar, parity)) return true;
+    if (*abort_w) return false;
+  }
+  if (!*abort_w) {
+    *abort_w = 1;
+    atomicExch(flag, 1);
+  }
+  return false;
+}
+
+// Warp-level: lane 0 waits, the warp learns the outcome, every lane acquires.
+__device__ __forceinline__ bool ws_wait_warp(uint64_t* bar, uint32_t parity, long long max_polls,
+                                             volatile int* abort_w, int* flag, int lane) {
+  int ok = 1;
+  if (lane == 0) ok = ws_wait(bar, parity, max_polls, abort_w, flag) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (ok && lane != 0) (void)bulk::try_wait(bar, parity);
+  return ok != 0;
+}
+
+// Named barrier over `count` threads with an OR vote (true when any thread votes).
+__device__ __forceinline__ bool ws_sync_or(int id, int count, bool vote) {
+  uint32_t r;
+  asm volatile(
+      "{\n"
+      ".reg .pred p, q;\n"
+      "setp.ne.u32 p, %1, 0;\n"
+      "bar.red.or.pred q, %2, %3, p;\n"
+      "selp.u32 %0, 1, 0, q;\n"
+      "}\n"
+      : "=r"(r)
+      : "r"((uint32_t)vote), "r"(id), "r"(count)
+      : "memory");
+  return r != 0;
+}
+
+// Split one staged chunk into its terms (converter thread ct of 256).
+// m stage: member m, half h (t 16 h ..): rows v of 16 t in the 128-byte
+// swizzle (the 16-byte pair chunk c of row v at c ^ (v & 7)); W stage: box b
+// (z 32 b ..): rows t of 32 z in the same swizzle.  Eight consecutive
+// threads take eight consecutive volumes (A) or z (B).
+__device__ __forceinline__ void ws_convert(const WsPlan& P, const unsigned char* raw, unsigned char* set,
+                                           const int (&mem)[4], const float* s_n, float inv_sw, int ct) {
+  const int epc = P.epc, groups = TCH / epc;
+  unsigned char* a = set;
+  unsigned char* b = set + P.nterm * P.a_term;
+  for (int i = ct; i < 64 * groups; i += WS_CONV * 32) {
+    const int v = i & 15, m = (i >> 4) & 3, gI = i >> 6;
+    const int nre = ws_row(v, m, 0), nim = ws_row(v, m, 1);
+    const uint32_t o_re = kchunk(NR, nre, gI * epc, epc), o_im = kchunk(NR, nim, gI * epc, epc);
+    if (pick(mem, m) < 0) {
+      for (int tI = 0; tI < P.nterm; ++tI) {
+        *reinterpret_cast<uint4*>(a + tI * P.a_term + o_re) = make_uint4(0u, 0u, 0u, 0u);
+        *reinterpret_cast<uint4*>(a + tI * P.a_term + o_im) = make_uint4(0u, 0u, 0u, 0u);
+      }
+      continue;
+    }
+    const int t0 = gI * epc;  // epc t of one 16-t half
+    const unsigned char* rowp = raw + (2 * m + (t0 >> 4)) * WS_MBOX + v * 128;
+    if (P.fp8) {
+      const float sr = 1.f / s_n[nre], si = 1.f / s_n[nim];
+      float vr[16], vi[16];
+#pragma unroll
+      for (int e = 0; e < 16; e += 2) {
+        const int tt = (t0 & 15) + e;
+        const float4 q = *reinterpret_cast<const float4*>(rowp + (((tt >> 1) ^ (v & 7)) << 4));
+        vr[e] = q.x * sr;
+        vi[e] = q.y * si;
+        vr[e + 1] = q.z * sr;
+        vi[e + 1] = q.w * si;
+      }
+      uint4 t0v, t1v, t2v;
+      split16_e4m3(vr, t0v, t1v, t2v);
+      *reinterpret_cast<uint4*>(a + o_re) = t0v;
+      *reinterpret_cast<uint4*>(a + P.a_term + o_re) = t1v;
+      *reinterpret_cast<uint4*>(a + 2 * P.a_term + o_re) = t2v;
+      split16_e4m3(vi, t0v, t1v, t2v);
+      *reinterpret_cast<uint4*>(a + o_im) = t0v;
+      *reinterpret_cast<uint4*>(a + P.a_term + o_im) = t1v;
+      *reinterpret_cast<uint4*>(a + 2 * P.a_term + o_im) = t2v;
+    } else {
+      float vr[8], vi[8];
+#pragma unroll
+      for (int e = 0; e < 8; e += 2) {
+        const int tt = (t0 & 15) + e;
+        const float4 q = *reinterpret_cast<const float4*>(rowp + (((tt >> 1) ^ (v & 7)) << 4));
+        vr[e] = q.x;
+        vi[e] = q.y;
+        vr[e + 1] = q.z;
+        vi[e + 1] = q.w;
+      }
+      uint4 hi, lo;
+      split8_bf16(vr, hi, lo);
+      *reinterpret_cast<uint4*>(a + o_re) = hi;
+      *reinterpret_cast<uint4*>(a + P.a_term + o_re) = lo;
+      split8_bf16(vi, hi, lo);
+      *reinterpret_cast<uint4*>(a + o_im) = hi;
+      *reinterpret_cast<uint4*>(a + P.a_term + o_im) = lo;
+    }
+  }
+  // B = W^T rows z < zn (z >= z4 reads the boxes' zero fill)
+  const unsigned char* rw = raw + 8 * WS_MBOX;
+  for (int i = ct; i < P.zn * groups; i += WS_CONV * 32) {
+    const int z = i % P.zn, gI = i / P.zn;
+    const unsigned char* box = rw + (z >> 5) * WS_WBOX + (z & 3) * 4;
+    const int zc = (z & 31) >> 2;
+    const uint32_t o = kchunk(P.zn, z, gI * epc, epc);
+    if (P.fp8) {
+      float w[16];
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        const int t = gI * 16 + e;
+        w[e] = *reinterpret_cast<const float*>(box + t * 128 + ((zc ^ (t & 7)) << 4)) * inv_sw;
+      }
+      uint4 t0v, t1v, t2v;
+      split16_e4m3(w, t0v, t1v, t2v);
+      *reinterpret_cast<uint4*>(b + o) = t0v;
+      *reinterpret_cast<uint4*>(b + P.b_term + o) = t1v;
+      *reinterpret_cast<uint4*>(b + 2 * P.b_term + o) = t2v;
+    } else {
+      float w[8];
+#pragma unroll
+      for (int e = 0; e < 8; ++e) {
+        const int t = gI * 8 + e;
+        w[e] = *reinterpret_cast<const float*>(box + t * 128 + ((zc ^ (t & 7)) << 4));
+      }
+      uint4 hi, lo;
+      split8_bf16(w, hi, lo);
+      *reinterpret_cast<uint4*>(b + o) = hi;
+      *reinterpret_cast<uint4*>(b + P.b_term + o) = lo;
+    }
+  }
+}
+
+__global__ void __launch_bounds__(WS_THREADS, 1)
+    k_batch_tikhonov_ws(const __grid_constant__ CUtensorMap mmap, const __grid_constant__ CUtensorMap wmap, WsPlan P,
+                        const unsigned char* __restrict__ tabs, const float* __restrict__ class_scale,
+                        const int* __restrict__ members, int nclass, const float2* __restrict__ m_hat, int ldm,
+                        float2* __restrict__ x_hat, int ldx, int refine, int* flag, long long max_polls) {
+  extern __shared__ float4 ws_smem4[];
+  unsigned char* sm;
+  {
+    const uint32_t s = bulk::saddr(ws_smem4);
+    sm = reinterpret_cast<unsigned char*>(ws_smem4) + (((s + 1023u) & ~1023u) - s);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = P.nt, nz = P.nz, zn = P.zn;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.off_bar);
+  uint64_t* raw_full = bar + 0;    // [2], one arrival + the copies' bytes
+  uint64_t* raw_empty = bar + 2;   // [2], one arrival per converter warp
+  uint64_t* term_full = bar + 4;   // [2], one arrival per converter warp
+  uint64_t* term_empty = bar + 6;  // [2], the MMAs that read the set (commit)
+  uint64_t* acc_full = bar + 8;    // [2], the item's MMAs (commit)
+  uint64_t* acc_empty = bar + 10;  // [2], one arrival per epilogue warp
+  uint64_t* tab_full = bar + 12;   // the class tables' copy
+  uint64_t* solve_bar = bar + 13;  // the solve MMAs (commit)
+  uint64_t* drain_bar = bar + 14;  // every MMA issued (commit), before TMEM is freed
+  uint64_t* sn_ready = bar + 15;   // [2] (FP8), one arrival per converter warp
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 17);
+  volatile int* abort_w = reinterpret_cast<volatile int*>(bar + 18);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < 2; ++i) {
+      bulk::bar_init(raw_full + i, 1);
+      bulk::bar_init(raw_empty + i, WS_CONV);
+      bulk::bar_init(term_full + i, WS_CONV);
+      bulk::bar_init(term_empty + i, 1);
+      bulk::bar_init(acc_full + i, 1);
+      bulk::bar_init(acc_empty + i, WS_EPI);
+      bulk::bar_init(sn_ready + i, WS_CONV);
+    }
+    bulk::bar_init(tab_full, 1);
+    bulk::bar_init(solve_bar, 1);
+    bulk::bar_init(drain_bar, 1);
+    *abort_w = 0;
+  }
+  if (warp == 0) umma::tmem_alloc(tslot, 512);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t taddr = *tslot;
+  const uint32_t sbase = bulk::saddr(sm);
+  const int nchunks = (nt + TCH - 1) / TCH;
+  const int nvc = P.nvc;
+  const int acc_cols = P.nacc * zn, col_work = 2 * acc_cols;
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int gk = 0, n0 = 0, n1 = 0;  // chunks staged; loads into stages 0 / 1
+      bool ok = true;
+      for (int c = blockIdx.x; c < nclass && ok; c += gridDim.x) {
+        int mem[4];
+        for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
+        int present = 0;
+        for (int m = 0; m < 4; ++m) present += mem[m] >= 0;
+        for (int vc = 0; vc < nvc && ok; ++vc)
+          for (int kc = 0; kc < nchunks; ++kc, ++gk) {
+            const int s = gk & 1;
+            if (gk >= 2 && !ws_wait(raw_empty + s, (uint32_t)((gk >> 1) + 1) & 1u, max_polls, abort_w, flag)) {
+              ok = false;
+              break;
+            }
+            unsigned char* st = sm + P.off_raw + s * P.raw_stage;
+            bulk::arrive_expect(raw_full + s, (unsigned)(present * 2 * WS_MBOX + P.nwb * WS_WBOX));
+            for (int m = 0; m < 4; ++m)
+              if (mem[m] >= 0)
+                for (int h = 0; h < 2; ++h)
+                  bulk::tensor_g2s(st + (2 * m + h) * WS_MBOX, &mmap, kc * TCH + 16 * h, vc * VB, mem[m],
+                                   raw_full + s);
+            for (int wb = 0; wb < P.nwb; ++wb)
+              bulk::tensor_g2s_2d(st + 8 * WS_MBOX + wb * WS_WBOX, &wmap, 32 * wb, c * nt + kc * TCH, raw_full + s);
+            if (s)
+              ++n1;
+            else
+              ++n0;
+          }
+      }
+      // no copy may still be landing when the CTA ends
+      if (n0) bulk::wait(raw_full, (uint32_t)(n0 - 1) & 1u, DRAIN_POLLS);
+      if (n1) bulk::wait(raw_full + 1, (uint32_t)(n1 - 1) & 1u, DRAIN_POLLS);
+    }
+  } else if (warp <= WS_CONV) {
+    // ---------------- converters ----------------
+    const int ct = threadIdx.x - 32;
+    int gk = 0, it = 0;
+    bool ok = true;
+    for (int c = blockIdx.x; c < nclass && ok; c += gridDim.x) {
+      int mem[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
+      const float inv_sw = P.fp8 ? 1.f / __ldg(class_scale + c) : 1.f;
+      for (int vc = 0; vc < nvc && ok; ++vc, ++it) {
+        const int a = it & 1, v0 = vc * VB, nv = P.batch - v0 < VB ? P.batch - v0 : VB;
+        float* s_n = reinterpret_cast<float*>(sm + P.off_sn) + a * NR;
+        if (P.fp8) {
+          // the epilogue is done with this scale buffer (item it - 2); then the
+          // per-right-hand-side scales: the largest magnitude over t maps to 448
+          if (it >= 2 &&
+              !ws_wait_warp(acc_empty + a, (uint32_t)((it >> 1) + 1) & 1u, max_polls, abort_w, flag, lane)) {
+            ok = false;
+            break;
+          }
+          const int vm = ct >> 2, part = ct & 3, v = vm >> 2, m = vm & 3, f = pick(mem, m);
+          float mr = 0.f, mi = 0.f;
+          if (f >= 0 && v < nv) {
+            const float2* src = m_hat + (size_t)f * ldm + (size_t)(v0 + v) * nt;
+            for (int t = part; t < nt; t += 4) {
+              const float2 x = __ldg(src + t);
+              mr = fmaxf(mr, fabsf(x.x));
+              mi = fmaxf(mi, fabsf(x.y));
+            }
+          }
+          mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, 1));
+          mr = fmaxf(mr, __shfl_xor_sync(0xffffffffu, mr, 2));
+          mi = fmaxf(mi, __shfl_xor_sync(0xffffffffu, mi, 1));
+          mi = fmaxf(mi, __shfl_xor_sync(0xffffffffu, mi, 2));
+          if (part == 0) {
+            s_n[ws_row(v, m, 0)] = mr > 0.f ? mr / E4M3_MAX : 1.f;
+            s_n[ws_row(v, m, 1)] = mi > 0.f ? mi / E4M3_MAX : 1.f;
+          }
+          __syncwarp();
+          if (lane == 0) bulk::arrive(sn_ready + a);
+          if (!ws_wait_warp(sn_ready + a, (uint32_t)(it >> 1) & 1u, max_polls, abort_w, flag, lane)) {
+            ok = false;
+            break;
+          }
+        }
+        for (int kc = 0; kc < nchunks; ++kc, ++gk) {
+          const int s = gk & 1;
+          if (!ws_wait_warp(raw_full + s, (uint32_t)(gk >> 1) & 1u, max_polls, abort_w, flag, lane) ||
+              (gk >= 2 &&
+               !ws_wait_warp(term_empty + s, (uint32_t)((gk >> 1) + 1) & 1u, max_polls, abort_w, flag, lane))) {
+            ok = false;
+            break;
+          }
+          ws_convert(P, sm + P.off_raw + s * P.raw_stage, sm + P.off_set + s * P.set_bytes, mem, s_n, inv_sw, ct);
+          umma::fence_proxy_async();  // this lane's term writes, before the MMAs read them
+          __syncwarp();
+          if (lane == 0) {
+            bulk::arrive(raw_empty + s);
+            bulk::arrive(term_full + s);
+          }
+        }
+      }
+    }
+  } else if (warp == WS_MMA_WARP) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc_main = P.fp8 ? idesc_e4m3(NR, zn) : idesc_bf16(NR, zn);
+      int gk = 0, it = 0;
+      bool ok = true;
+      for (int c = blockIdx.x; c < nclass && ok; c += gridDim.x)
+        for (int vc = 0; vc < nvc && ok; ++vc, ++it) {
+          const int a = it & 1;
+          if (it >= 2 && !ws_wait(acc_empty + a, (uint32_t)((it >> 1) + 1) & 1u, max_polls, abort_w, flag)) {
+            ok = false;
+            break;
+          }
+          umma::fence_after_sync();
+          const uint32_t acc = taddr + (uint32_t)(a * acc_cols);
+          for (int kc = 0; kc < nchunks; ++kc, ++gk) {
+            const int s = gk & 1;
+            if (!ws_wait(term_full + s, (uint32_t)(gk >> 1) & 1u, max_polls, abort_w, flag)) {
+              ok = false;
+              break;
+            }
+            umma::fence_after_sync();
+            const uint32_t a0 = sbase + P.off_set + s * P.set_bytes;
+            const uint32_t b0 = a0 + P.nterm * P.a_term;
+            const int ksteps = TCH * P.esize / 32;  // K steps of 32 bytes per row
+            for (int ks = 0; ks < ksteps; ++ks) {
+              const uint32_t oa = ks * 2 * NR * 16, ob = ks * 2 * zn * 16;
+              uint64_t A[3], B[3];
+#pragma unroll
+              for (int i = 0; i < 3; ++i) {
+                A[i] = umma::desc(a0 + i * P.a_term + oa, NR * 16, 128);
+                B[i] = umma::desc(b0 + i * P.b_term + ob, zn * 16, 128);
+              }
+              const uint32_t first = (kc > 0 || ks > 0) ? 1u : 0u;
+              if (P.fp8) {
+                mma_e4m3(acc, A[0], B[0], idesc_main, first);
+                mma_e4m3(acc + zn, A[0], B[1], idesc_main, first);
+                mma_e4m3(acc + zn, A[1], B[0], idesc_main, 1);
+                mma_e4m3(acc + 2 * zn, A[0], B[2], idesc_main, first);
+                mma_e4m3(acc + 2 * zn, A[1], B[1], idesc_main, 1);
+                mma_e4m3(acc + 2 * zn, A[2], B[0], idesc_main, 1);
+              } else {
+                mma_bf16(acc, A[0], B[0], idesc_main, first);
+                mma_bf16(acc + zn, A[0], B[1], idesc_main, first);
+                mma_bf16(acc + zn, A[1], B[0], idesc_main, 1);
+              }
+            }
+            umma::commit(term_empty + s);
+          }
+          if (ok) umma::commit(acc_full + a);
+        }
+      // every MMA this thread issued has finished before TMEM is freed
+      umma::commit(drain_bar);
+      bulk::wait(drain_bar, 0, DRAIN_POLLS);
+    }
+  } else {
+    // ---------------- epilogue: solve and refinement ----------------
+    const int et = threadIdx.x - WS_EPI0 * 32;
+    const int n = 32 * (warp & 3) + lane;  // TMEM lane = right-hand side
+    const uint32_t trow = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
+    const int v = n & 15, ri = (n >> 4) & 1, m = n >> 5;
+    unsigned char* xh = sm + P.off_xh;
+    unsigned char* xl = sm + P.off_xl;
+    const uint32_t t_ch = sbase + P.off_tab, t_cl = t_ch + zn * zn * 4, t_gh = t_cl + zn * zn * 4,
+                   t_gl = t_gh + zn * zn * 4;
+    int tab_loads = 0;
+    auto load_tables = [&](int c) {
+      bulk::arrive_expect(tab_full, (unsigned)P.tab_bytes);
+      bulk::g2s(sm + P.off_tab, tabs + (size_t)c * P.tab_bytes, (unsigned)P.tab_bytes, tab_full);
+      ++tab_loads;
+    };
+    if (et == 0 && (int)blockIdx.x < nclass) load_tables(blockIdx.x);
+    uint32_t sph = 0;  // solve barrier parity
+    // the solve MMAs: one thread issues after every epilogue thread has written X
+    auto solve = [&](uint32_t th, uint32_t tl) -> bool {
+      umma::fence_proxy_async();
+      umma::fence_before_sync();
+      ws_sync_or(2, WS_EPI * 32, false);
+      umma::fence_after_sync();
+      if (et == 0) {
+        issue_solve3(taddr + col_work, sbase + P.off_xh, sbase + P.off_xl, th, tl, zn);
+        umma::commit(solve_bar);
+      }
+      const bool w_ok = ws_wait_warp(solve_bar, sph, max_polls, abort_w, flag, lane);
+      sph ^= 1u;
+      umma::fence_after_sync();
+      return !ws_sync_or(2, WS_EPI * 32, !w_ok);
+    };
+    int it = 0, ci = 0;
+    bool ok = true;
+    for (int c = blockIdx.x; c < nclass && ok; c += gridDim.x, ++ci) {
+      int mem[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) mem[q] = __ldg(members + 4 * c + q);
+      const float sw = P.fp8 ? __ldg(class_scale + c) : 1.f;
+      for (int vc = 0; vc < nvc && ok; ++vc, ++it) {
+        const int a = it & 1, v0 = vc * VB, nv = P.batch - v0 < VB ? P.batch - v0 : VB;
+        bool w_ok = ws_wait_warp(acc_full + a, (uint32_t)(it >> 1) & 1u, max_polls, abort_w, flag, lane);
+        if (w_ok && vc == 0) w_ok = ws_wait_warp(tab_full, (uint32_t)ci & 1u, max_polls, abort_w, flag, lane);
+        if (ws_sync_or(2, WS_EPI * 32, !w_ok)) {
+          ok = false;
+          break;
+        }
+        umma::fence_after_sync();
+        const uint32_t acc = (uint32_t)(a * acc_cols);
+        const float sn = P.fp8 ? reinterpret_cast<const float*>(sm + P.off_sn)[a * NR + n] * sw : 1.f;
+        float x[4][16];
+        // x0 = C b0
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (16 * j < zn) {
+            float val[16];
+            umma::tmem_ld16(trow + acc + 16 * j, val);
+#pragma unroll
+            for (int e = 0; e < 16; ++e) val[e] *= sn;
+            put_x16(xh, xl, n, j, val);
+          }
+        }
+        if (!solve(t_ch, t_cl)) {
+          ok = false;
+          break;
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j)
+          if (16 * j < zn) umma::tmem_ld16(trow + col_work + 16 * j, x[j]);
+        for (int r = 0; r < refine && ok; ++r) {
+          // r = b - G' x
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (16 * j < zn) put_x16(xh, xl, n, j, x[j]);
+          if (!solve(t_gh, t_gl)) {
+            ok = false;
+            break;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (16 * j < zn) {
+              float gx[16], d0[16], d1[16], d2[16];
+              umma::tmem_ld16(trow + col_work + 16 * j, gx);
+              umma::tmem_ld16(trow + acc + 16 * j, d0);
+              umma::tmem_ld16(trow + acc + zn + 16 * j, d1);
+              if (P.fp8) umma::tmem_ld16(trow + acc + 2 * zn + 16 * j, d2);
+              float rr[16];
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                const float bb = P.fp8 ? sn * (d0[e] + 0.0625f * d1[e] + 0.00390625f * d2[e]) : d0[e] + d1[e];
+                rr[e] = bb - gx[e];
+              }
+              put_x16(xh, xl, n, j, rr);
+            }
+          }
+          // x += C r
+          if (!solve(t_ch, t_cl)) {
+            ok = false;
+            break;
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (16 * j < zn) {
+              float cr[16];
+              umma::tmem_ld16(trow + col_work + 16 * j, cr);
+#pragma unroll
+              for (int e = 0; e < 16; ++e) x[j][e] += cr[e];
+            }
+          }
+        }
+        if (!ok) break;
+        // the accumulators are read: the MMAs of item it + 2 may overwrite them
+        umma::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) bulk::arrive(acc_empty + a);
+        // x_hat[f][v * nz + z]: lanes 0-15 hold the real parts, lanes 16-31 the imaginary ones
+        {
+          const int fm = pick(mem, m);
+          const bool writer = ri == 0 && v < nv && fm >= 0;
+          float2* dst = x_hat + (size_t)(fm >= 0 ? fm : 0) * ldx + (size_t)(v0 + (v < nv ? v : 0)) * nz;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            if (16 * j < zn) {
+#pragma unroll
+              for (int e = 0; e < 16; ++e) {
+                const float im = __shfl_down_sync(0xffffffffu, x[j][e], 16);
+                const int z = 16 * j + e;
+                if (writer && z < nz) dst[z] = make_float2(x[j][e], im);
+              }
+            }
+          }
+        }
+      }
+      // every solve MMA of this class has completed: the tables may be replaced
+      if (ok && et == 0 && c + (int)gridDim.x < nclass) load_tables(c + gridDim.x);
+    }
+    if (et == 0 && tab_loads) bulk::wait(tab_full, (uint32_t)(tab_loads - 1) & 1u, DRAIN_POLLS);
+  }
+  __syncwarp();
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  if (warp == 0) umma::tmem_dealloc(taddr, 512);
+}
+
 // Per-class FP8 scale of W_hat: max |W| / 448.
 __global__ void k_class_absmax(const float* __restrict__ what, int per_class, int nclass, float* __restrict__ out) {
   __shared__ float red[32];
@@ -777,12 +1341,38 @@ ctof_status batch_tikhonov_prepare(ctof_kernel_s* k, double lambda, cudaStream_t
 
 ctof_status batch_tikhonov_contract(const ctof_kernel_s* k, int precision, int batch, const float2* m_hat, int ldm,
                                     float2* x_hat, int ldx, int refine, cudaStream_t st) {
-  const BtPlan P = make_plan(k->nt, k->nz, precision == CTOF_FP8E4M3 ? 1 : 0, batch);
-  if (P.total > 227 * 1024) return CTOF_EUNSUPPORTED;
-  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_batch_tikhonov_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, P.total));
+  const int fp8 = precision == CTOF_FP8E4M3 ? 1 : 0;
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
   const int grid = k->nclass < nsm ? k->nclass : nsm;
+  if ((k->nt & 1) == 0 && rup(k->nz, 16) <= 64) {
+    // warp-specialised kernel: m_hat [f][v][t] and W_hat [c t][z] staged by tensor maps
+    const WsPlan W = make_ws_plan(k->nt, k->nz, fp8, batch);
+    if (W.total <= 227 * 1024) {
+      CUtensorMap mmap, wmap;
+      const unsigned long long mdims[3] = {(unsigned long long)k->nt, (unsigned long long)batch,
+                                           (unsigned long long)k->nf};
+      const unsigned long long mstr[2] = {(unsigned long long)k->nt * 8, (unsigned long long)ldm * 8};
+      const unsigned mbox[3] = {16, VB, 1};
+      const unsigned long long wdims[2] = {(unsigned long long)k->z4, (unsigned long long)k->nt * k->nclass};
+      const unsigned long long wstr[1] = {(unsigned long long)k->z4 * 4};
+      const unsigned wbox[2] = {32, TCH};
+      if (ctof_encode_map(&mmap, 8, 3, m_hat, mdims, mstr, mbox, 128) == CTOF_OK &&
+          ctof_encode_map(&wmap, 4, 2, k->d_what, wdims, wstr, wbox, 128) == CTOF_OK) {
+        CTOF_CUDA_TRY(
+          cudaFuncSetAttribute(k_batch_tikhonov_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, W.total));
+        k_batch_tikhonov_ws<<<grid, WS_THREADS, W.total, st>>>(mmap, wmap, W, k->d_bt_tab, k->d_bt_sw,
+                                                               k->d_members, k->nclass, m_hat, ldm, x_hat, ldx, refine,
+                                                               k->d_flags, k->max_polls);
+        CTOF_CUDA_TRY(cudaGetLastError());
+        return CTOF_OK;
+      }
+      ctof_set_last_error_text("");  // a buffer the maps cannot take: the kernel below stages by plain copies
+    }
+  }
+  const BtPlan P = make_plan(k->nt, k->nz, fp8, batch);
+  if (P.total > 227 * 1024) return CTOF_EUNSUPPORTED;
+  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_batch_tikhonov_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, P.total));
   k_batch_tikhonov_tc<<<grid, BT_THREADS, P.total, st>>>(P, k->d_what, k->d_bt_tab, k->d_bt_sw, k->d_members,
                                                           k->nclass, m_hat, ldm, x_hat, ldx, refine, k->d_flags,
                                                           k->max_polls);

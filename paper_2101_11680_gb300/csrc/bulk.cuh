@@ -84,6 +84,19 @@ __device__ __forceinline__ void tensor_g2s(void* dst, const void* map, int c0, i
       : "memory");
 }
 
+__device__ __forceinline__ void tensor_g2s_2d(void* dst, const void* map, int c0, int c1, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];\n" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(saddr(bar))
+      : "memory");
+}
+
+// Plain arrival (one of the barrier's expected arrivals).
+__device__ __forceinline__ void arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(saddr(bar)) : "memory");
+}
+
 __device__ __forceinline__ void tensor_s2g(const void* map, int c0, int c1, int c2, const void* src) {
   asm volatile("cp.async.bulk.tensor.3d.global.shared::cta.tile.bulk_group [%0, {%1, %2, %3}], [%4];\n" ::"l"(
                    reinterpret_cast<uint64_t>(map)),

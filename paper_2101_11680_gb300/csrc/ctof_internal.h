@@ -2,6 +2,7 @@
 // provides.  Not part of the C ABI.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <stddef.h>
 
@@ -133,6 +134,15 @@ size_t fft_inter_elems(const ctof_kernel_s* k, int nplanes, int rows);
 // construction (FP64 roots rounded to FP32, in the layout the kernels stage).
 int fft_twiddle_count(int p);
 void fft_twiddle_table(int p, float2* out);
+
+// Tiled tensor map (TMA descriptor) over `rank` dimensions of `elem_bytes`
+// elements: dims innermost first, strides in bytes of dimensions 1 .. rank-1,
+// box in elements, swizzle 0 / 32 / 64 / 128 bytes; out-of-range elements
+// read as zero.  EINVAL for a misaligned base or stride, ECUDA when the driver
+// rejects the map.
+ctof_status ctof_encode_map(CUtensorMap* map, int elem_bytes, int rank, const void* base,
+                            const unsigned long long* dims, const unsigned long long* strides_bytes,
+                            const unsigned* box, int swizzle_bytes);
 // Forward R2C of planes of real rows [nplanes][rows_in][ld_in] (first cols_in
 // columns used, the rest of the P-wide row is zero) into frequency-major
 // spectra out[f][ldf] (plane index fastest).  Zero rows beyond rows_in.

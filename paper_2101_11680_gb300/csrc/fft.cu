@@ -831,25 +831,10 @@ PFN_cuTensorMapEncodeTiled_v12000 tensor_map_encoder() {
 // or 128).
 ctof_status plane_map(CUtensorMap* m, const float2* base, int nplanes, int h, int rows, size_t ld_kx, size_t ld_row,
                       int b0, int b1, int b2) {
-  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
-  if (!enc) {
-    ctof_set_last_error_text("cuTensorMapEncodeTiled is not available from the driver");
-    return CTOF_ECUDA;
-  }
-  if ((reinterpret_cast<uintptr_t>(base) & 15) || (ld_kx & 1) || (ld_row & 1)) return CTOF_EINVAL;
-  const cuuint64_t dims[3] = {(cuuint64_t)nplanes, (cuuint64_t)h, (cuuint64_t)rows};
-  const cuuint64_t strides[2] = {(cuuint64_t)(ld_kx * sizeof(float2)), (cuuint64_t)(ld_row * sizeof(float2))};
-  const cuuint32_t box[3] = {(cuuint32_t)b0, (cuuint32_t)b1, (cuuint32_t)b2};
-  const cuuint32_t es[3] = {1, 1, 1};
-  const CUtensorMapSwizzle sw = b0 * sizeof(float2) == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B;
-  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 3, const_cast<float2*>(base), dims, strides, box, es,
-                         CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
-                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  if (r != CUDA_SUCCESS) {
-    ctof_set_last_error_text("cuTensorMapEncodeTiled rejected an FFT plane map");
-    return CTOF_ECUDA;
-  }
-  return CTOF_OK;
+  const unsigned long long dims[3] = {(unsigned long long)nplanes, (unsigned long long)h, (unsigned long long)rows};
+  const unsigned long long strides[2] = {ld_kx * sizeof(float2), ld_row * sizeof(float2)};
+  const unsigned box[3] = {(unsigned)b0, (unsigned)b1, (unsigned)b2};
+  return ctof_encode_map(m, 8, 3, base, dims, strides, box, b0 * (int)sizeof(float2));
 }
 
 #define CTOF_P_SWITCH(p, ...)                                    \
@@ -869,6 +854,44 @@ ctof_status row_map(const ctof_kernel_s* k, CUtensorMap* m, const float2* inter,
 }
 
 }  // namespace
+
+ctof_status ctof_encode_map(CUtensorMap* map, int elem_bytes, int rank, const void* base,
+                            const unsigned long long* dims, const unsigned long long* strides_bytes,
+                            const unsigned* box, int swizzle_bytes) {
+  const PFN_cuTensorMapEncodeTiled_v12000 enc = tensor_map_encoder();
+  if (!enc) {
+    ctof_set_last_error_text("cuTensorMapEncodeTiled is not available from the driver");
+    return CTOF_ECUDA;
+  }
+  if (rank < 1 || rank > 5 || (reinterpret_cast<uintptr_t>(base) & 15)) return CTOF_EINVAL;
+  cuuint64_t d[5], s[4];
+  cuuint32_t b[5], es[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    b[i] = box[i];
+    es[i] = 1;
+    if (i + 1 < rank) {
+      if (strides_bytes[i] & 15) return CTOF_EINVAL;
+      s[i] = strides_bytes[i];
+    }
+  }
+  const CUtensorMapDataType dt = elem_bytes == 8   ? CU_TENSOR_MAP_DATA_TYPE_UINT64
+                                 : elem_bytes == 4 ? CU_TENSOR_MAP_DATA_TYPE_UINT32
+                                 : elem_bytes == 2 ? CU_TENSOR_MAP_DATA_TYPE_UINT16
+                                                   : CU_TENSOR_MAP_DATA_TYPE_UINT8;
+  const CUtensorMapSwizzle sw = swizzle_bytes == 128  ? CU_TENSOR_MAP_SWIZZLE_128B
+                                : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B
+                                : swizzle_bytes == 32 ? CU_TENSOR_MAP_SWIZZLE_32B
+                                                      : CU_TENSOR_MAP_SWIZZLE_NONE;
+  const CUresult r = enc(map, dt, (cuuint32_t)rank, const_cast<void*>(base), d, s, b, es,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, sw, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    ctof_set_last_error_text("cuTensorMapEncodeTiled rejected a tensor map");
+    return CTOF_ECUDA;
+  }
+  return CTOF_OK;
+}
 
 ctof_status fft_rows_forward(const ctof_kernel_s* k, const float* in, int nplanes, int rows, int cols_in,
                              int ld_in, float2* inter, cudaStream_t st) {
