@@ -635,12 +635,15 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_tikhonov_tc(
   if (warp == 0) umma::tmem_dealloc(taddr, 256);
 }
 
-// ======================= warp-specialised kernel (even nt) =======================
+// ======================= warp-specialised kernel (nt a multiple of 16) =======================
 //
-// Roles (14 warps): warp 0 (one thread) stages each t chunk with tensor-map
-// copies (m_hat boxes of 16 volumes x 16 t per member, W_hat boxes of 32 t x
-// 32 z, both in the 128-byte swizzle) into two raw stages; warps 1-8 split a
-// staged chunk into its narrow-format terms (two term sets); warp 9 (one
+// Roles (14 warps): warp 0 (one thread) stages each chunk of TC t values with
+// tensor-map copies (per member one m_hat box of TC/16 halves x 16 volumes x
+// 16 t, W_hat boxes of TC t x 32 z, both in the 128-byte swizzle) into NS raw
+// stages (TC = 32; NS = 2 at 64 depths, where shared memory holds no more;
+// 16-t chunks with four stages measured slower: the hand-offs per chunk
+// dominate); warps 1-8
+// split a staged chunk into its narrow-format terms (NS term sets); warp 9 (one
 // thread) issues the tcgen05 MMAs of each term set into one of two TMEM
 // accumulator sets; warps 10-13 run the solve and the refinement of one
 // (class, volume chunk) item from its accumulator set while the next item
@@ -660,6 +663,7 @@ constexpr int WS_WBOX = 32 * 32 * 4;  // W_hat box: 32 t x 32 z x 4 bytes
 
 struct WsPlan {
   int nt, nz, z4, zn, fp8, nterm, nacc, esize, epc;
+  int tc, ns;     // t values per chunk, raw stages = term sets
   int a_term, b_term, set_bytes;
   int nwb;        // W boxes per chunk
   int raw_stage;  // bytes of one raw stage (1024-byte multiple)
@@ -679,41 +683,48 @@ WsPlan make_ws_plan(int nt, int nz, int fp8, int batch) {
   P.nacc = fp8 ? 3 : 2;
   P.esize = fp8 ? 1 : 2;
   P.epc = 16 / P.esize;
-  P.a_term = NR * TCH * P.esize;
-  P.b_term = P.zn * TCH * P.esize;
+  P.tc = 32;
+  P.a_term = NR * P.tc * P.esize;
+  P.b_term = P.zn * P.tc * P.esize;
   P.set_bytes = P.nterm * (P.a_term + P.b_term);
   P.nwb = P.z4 <= 32 ? 1 : 2;
-  P.raw_stage = rup(8 * WS_MBOX + P.nwb * WS_WBOX, 1024);
+  P.raw_stage = rup(4 * (P.tc / 16) * WS_MBOX + P.nwb * 32 * P.tc * 4, 1024);
   P.tab_bytes = 4 * P.zn * P.zn * 4;
   P.x_tile = NR * P.zn * 4;
   P.batch = batch;
   P.nvc = (batch + VB - 1) / VB;
-  int off = 0;
-  auto take = [&](int bytes, int align) {
-    off = rup(off, align);
-    const int at = off;
-    off += bytes;
-    return at;
-  };
-  P.off_raw = take(2 * P.raw_stage, 1024);
-  P.off_set = take(2 * P.set_bytes, 128);
-  P.off_tab = take(P.tab_bytes, 128);
-  P.off_xh = take(P.x_tile, 128);
-  P.off_xl = take(P.x_tile, 128);
-  P.off_sn = take(2 * NR * 4, 16);
-  P.off_bar = take(256, 16);
-  P.total = off + 1024;  // room to align the dynamic shared memory base to 1024 bytes
+  for (P.ns = 4; P.ns >= 2; --P.ns) {  // the deepest pipeline that fits
+    int off = 0;
+    auto take = [&](int bytes, int align) {
+      off = rup(off, align);
+      const int at = off;
+      off += bytes;
+      return at;
+    };
+    P.off_raw = take(P.ns * P.raw_stage, 1024);
+    P.off_set = take(P.ns * P.set_bytes, 128);
+    P.off_tab = take(P.tab_bytes, 128);
+    P.off_xh = take(P.x_tile, 128);
+    P.off_xl = take(P.x_tile, 128);
+    P.off_sn = take(2 * NR * 4, 16);
+    P.off_bar = take(512, 16);
+    P.total = off + 1024;  // room to align the dynamic shared memory base to 1024 bytes
+    if (P.total <= 227 * 1024) break;
+  }
   return P;
 }
 
 __device__ __forceinline__ int ws_row(int v, int m, int ri) { return 32 * m + 16 * ri + v; }
 
-// Bounded wait that also stops once another role has given up.
+// Bounded wait that also stops once another role has given up; after a few
+// polls it sleeps between polls so that waiting warps leave the issue slots
+// to the working ones.
 __device__ __forceinline__ bool ws_wait(uint64_t* bar, uint32_t parity, long long max_polls, volatile int* abort_w,
                                         int* flag) {
   for (long long i = 0; i < max_polls; ++i) {
     if (bulk::try_wait(bar, parity)) return true;
     if (*abort_w) return false;
+    if (i >= 8) __nanosleep(32);
   }
   if (!*abort_w) {
     *abort_w = 1;
@@ -751,11 +762,12 @@ __device__ __forceinline__ bool ws_sync_or(int id, int count, bool vote) {
 // Split one staged chunk into its terms (converter thread ct of 256).
 // m stage: member m, half h (t 16 h ..): rows v of 16 t in the 128-byte
 // swizzle (the 16-byte pair chunk c of row v at c ^ (v & 7)); W stage: box b
-// (z 32 b ..): rows t of 32 z in the same swizzle.  Eight consecutive
+// (z 32 b ..): rows t of 32 z in the same swizzle.  TC t values per chunk.  Eight consecutive
 // threads take eight consecutive volumes (A) or z (B).
+template <int TC>
 __device__ __forceinline__ void ws_convert(const WsPlan& P, const unsigned char* raw, unsigned char* set,
                                            const int (&mem)[4], const float* s_n, float inv_sw, int ct) {
-  const int epc = P.epc, groups = TCH / epc;
+  const int epc = P.epc, groups = TC / epc;
   unsigned char* a = set;
   unsigned char* b = set + P.nterm * P.a_term;
   for (int i = ct; i < 64 * groups; i += WS_CONV * 32) {
@@ -770,7 +782,7 @@ __device__ __forceinline__ void ws_convert(const WsPlan& P, const unsigned char*
       continue;
     }
     const int t0 = gI * epc;  // epc t of one 16-t half
-    const unsigned char* rowp = raw + (2 * m + (t0 >> 4)) * WS_MBOX + v * 128;
+    const unsigned char* rowp = raw + ((TC / 16) * m + (t0 >> 4)) * WS_MBOX + v * 128;
     if (P.fp8) {
       const float sr = 1.f / s_n[nre], si = 1.f / s_n[nim];
       float vr[16], vi[16];
@@ -813,10 +825,10 @@ __device__ __forceinline__ void ws_convert(const WsPlan& P, const unsigned char*
     }
   }
   // B = W^T rows z < zn (z >= z4 reads the boxes' zero fill)
-  const unsigned char* rw = raw + 8 * WS_MBOX;
+  const unsigned char* rw = raw + 4 * (TC / 16) * WS_MBOX;
   for (int i = ct; i < P.zn * groups; i += WS_CONV * 32) {
     const int z = i % P.zn, gI = i / P.zn;
-    const unsigned char* box = rw + (z >> 5) * WS_WBOX + (z & 3) * 4;
+    const unsigned char* box = rw + (z >> 5) * (32 * TC * 4) + (z & 3) * 4;
     const int zc = (z & 31) >> 2;
     const uint32_t o = kchunk(P.zn, z, gI * epc, epc);
     if (P.fp8) {
@@ -846,6 +858,7 @@ __device__ __forceinline__ void ws_convert(const WsPlan& P, const unsigned char*
   }
 }
 
+template <int TC>
 __global__ void __launch_bounds__(WS_THREADS, 1)
     k_batch_tikhonov_ws(const __grid_constant__ CUtensorMap mmap, const __grid_constant__ CUtensorMap wmap, WsPlan P,
                         const unsigned char* __restrict__ tabs, const float* __restrict__ class_scale,
@@ -859,25 +872,28 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
   }
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int nt = P.nt, nz = P.nz, zn = P.zn;
+  const int NS = P.ns;
   uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.off_bar);
-  uint64_t* raw_full = bar + 0;    // [2], one arrival + the copies' bytes
-  uint64_t* raw_empty = bar + 2;   // [2], one arrival per converter warp
-  uint64_t* term_full = bar + 4;   // [2], one arrival per converter warp
-  uint64_t* term_empty = bar + 6;  // [2], the MMAs that read the set (commit)
-  uint64_t* acc_full = bar + 8;    // [2], the item's MMAs (commit)
-  uint64_t* acc_empty = bar + 10;  // [2], one arrival per epilogue warp
-  uint64_t* tab_full = bar + 12;   // the class tables' copy
-  uint64_t* solve_bar = bar + 13;  // the solve MMAs (commit)
-  uint64_t* drain_bar = bar + 14;  // every MMA issued (commit), before TMEM is freed
-  uint64_t* sn_ready = bar + 15;   // [2] (FP8), one arrival per converter warp
-  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 17);
-  volatile int* abort_w = reinterpret_cast<volatile int*>(bar + 18);
+  uint64_t* raw_full = bar + 0;     // [NS], one arrival + the copies' bytes
+  uint64_t* raw_empty = bar + 4;    // [NS], one arrival per converter warp
+  uint64_t* term_full = bar + 8;    // [NS], one arrival per converter warp
+  uint64_t* term_empty = bar + 12;  // [NS], the MMAs that read the set (commit)
+  uint64_t* acc_full = bar + 16;    // [2], the item's MMAs (commit)
+  uint64_t* acc_empty = bar + 18;   // [2], one arrival per epilogue warp
+  uint64_t* tab_full = bar + 20;    // the class tables' copy
+  uint64_t* solve_bar = bar + 21;   // the solve MMAs (commit)
+  uint64_t* drain_bar = bar + 22;   // every MMA issued (commit), before TMEM is freed
+  uint64_t* sn_ready = bar + 23;    // [2] (FP8), one arrival per converter warp
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 25);
+  volatile int* abort_w = reinterpret_cast<volatile int*>(bar + 26);
   if (threadIdx.x == 0) {
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < NS; ++i) {
       bulk::bar_init(raw_full + i, 1);
       bulk::bar_init(raw_empty + i, WS_CONV);
       bulk::bar_init(term_full + i, WS_CONV);
       bulk::bar_init(term_empty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
       bulk::bar_init(acc_full + i, 1);
       bulk::bar_init(acc_empty + i, WS_EPI);
       bulk::bar_init(sn_ready + i, WS_CONV);
@@ -893,14 +909,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
   umma::fence_after_sync();
   const uint32_t taddr = *tslot;
   const uint32_t sbase = bulk::saddr(sm);
-  const int nchunks = (nt + TCH - 1) / TCH;
+  const int nchunks = (nt + TC - 1) / TC;
   const int nvc = P.nvc;
   const int acc_cols = P.nacc * zn, col_work = 2 * acc_cols;
 
   if (warp == 0) {
     // ---------------- producer ----------------
     if (lane == 0) {
-      int gk = 0, n0 = 0, n1 = 0;  // chunks staged; loads into stages 0 / 1
+      int gk = 0;  // chunks staged
       bool ok = true;
       for (int c = blockIdx.x; c < nclass && ok; c += gridDim.x) {
         int mem[4];
@@ -909,29 +925,25 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
         for (int m = 0; m < 4; ++m) present += mem[m] >= 0;
         for (int vc = 0; vc < nvc && ok; ++vc)
           for (int kc = 0; kc < nchunks; ++kc, ++gk) {
-            const int s = gk & 1;
-            if (gk >= 2 && !ws_wait(raw_empty + s, (uint32_t)((gk >> 1) + 1) & 1u, max_polls, abort_w, flag)) {
+            const int s = gk % NS;
+            if (gk >= NS && !ws_wait(raw_empty + s, (uint32_t)((gk / NS) + 1) & 1u, max_polls, abort_w, flag)) {
               ok = false;
               break;
             }
             unsigned char* st = sm + P.off_raw + s * P.raw_stage;
-            bulk::arrive_expect(raw_full + s, (unsigned)(present * 2 * WS_MBOX + P.nwb * WS_WBOX));
-            for (int m = 0; m < 4; ++m)
+            bulk::arrive_expect(raw_full + s, (unsigned)(present * (TC / 16) * WS_MBOX + P.nwb * 32 * TC * 4));
+            for (int m = 0; m < 4; ++m)  // the chunk's 16-t halves: [half][volume][16 t]
               if (mem[m] >= 0)
-                for (int h = 0; h < 2; ++h)
-                  bulk::tensor_g2s(st + (2 * m + h) * WS_MBOX, &mmap, kc * TCH + 16 * h, vc * VB, mem[m],
-                                   raw_full + s);
+                bulk::tensor_g2s_4d(st + (TC / 16) * m * WS_MBOX, &mmap, 0, vc * VB, kc * (TC / 16), mem[m],
+                                    raw_full + s);
             for (int wb = 0; wb < P.nwb; ++wb)
-              bulk::tensor_g2s_2d(st + 8 * WS_MBOX + wb * WS_WBOX, &wmap, 32 * wb, c * nt + kc * TCH, raw_full + s);
-            if (s)
-              ++n1;
-            else
-              ++n0;
+              bulk::tensor_g2s_2d(st + 4 * (TC / 16) * WS_MBOX + wb * 32 * TC * 4, &wmap, 32 * wb, c * nt + kc * TC,
+                                  raw_full + s);
           }
       }
-      // no copy may still be landing when the CTA ends
-      if (n0) bulk::wait(raw_full, (uint32_t)(n0 - 1) & 1u, DRAIN_POLLS);
-      if (n1) bulk::wait(raw_full + 1, (uint32_t)(n1 - 1) & 1u, DRAIN_POLLS);
+      // no copy may still be landing when the CTA ends: the last load into each stage
+      for (int s = 0; s < NS && s < gk; ++s)
+        bulk::wait(raw_full + s, (uint32_t)((gk - 1 - s) / NS) & 1u, DRAIN_POLLS);
     }
   } else if (warp <= WS_CONV) {
     // ---------------- converters ----------------
@@ -980,14 +992,14 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
           }
         }
         for (int kc = 0; kc < nchunks; ++kc, ++gk) {
-          const int s = gk & 1;
-          if (!ws_wait_warp(raw_full + s, (uint32_t)(gk >> 1) & 1u, max_polls, abort_w, flag, lane) ||
-              (gk >= 2 &&
-               !ws_wait_warp(term_empty + s, (uint32_t)((gk >> 1) + 1) & 1u, max_polls, abort_w, flag, lane))) {
+          const int s = gk % NS;
+          if (!ws_wait_warp(raw_full + s, (uint32_t)(gk / NS) & 1u, max_polls, abort_w, flag, lane) ||
+              (gk >= NS &&
+               !ws_wait_warp(term_empty + s, (uint32_t)((gk / NS) + 1) & 1u, max_polls, abort_w, flag, lane))) {
             ok = false;
             break;
           }
-          ws_convert(P, sm + P.off_raw + s * P.raw_stage, sm + P.off_set + s * P.set_bytes, mem, s_n, inv_sw, ct);
+          ws_convert<TC>(P, sm + P.off_raw + s * P.raw_stage, sm + P.off_set + s * P.set_bytes, mem, s_n, inv_sw, ct);
           umma::fence_proxy_async();  // this lane's term writes, before the MMAs read them
           __syncwarp();
           if (lane == 0) {
@@ -1013,15 +1025,15 @@ __global__ void __launch_bounds__(WS_THREADS, 1)
           umma::fence_after_sync();
           const uint32_t acc = taddr + (uint32_t)(a * acc_cols);
           for (int kc = 0; kc < nchunks; ++kc, ++gk) {
-            const int s = gk & 1;
-            if (!ws_wait(term_full + s, (uint32_t)(gk >> 1) & 1u, max_polls, abort_w, flag)) {
+            const int s = gk % NS;
+            if (!ws_wait(term_full + s, (uint32_t)(gk / NS) & 1u, max_polls, abort_w, flag)) {
               ok = false;
               break;
             }
             umma::fence_after_sync();
             const uint32_t a0 = sbase + P.off_set + s * P.set_bytes;
             const uint32_t b0 = a0 + P.nterm * P.a_term;
-            const int ksteps = TCH * P.esize / 32;  // K steps of 32 bytes per row
+            const int ksteps = TC * P.esize / 32;  // K steps of 32 bytes per row
             for (int ks = 0; ks < ksteps; ++ks) {
               const uint32_t oa = ks * 2 * NR * 16, ob = ks * 2 * zn * 16;
               uint64_t A[3], B[3];
@@ -1345,25 +1357,26 @@ ctof_status batch_tikhonov_contract(const ctof_kernel_s* k, int precision, int b
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
   const int grid = k->nclass < nsm ? k->nclass : nsm;
-  if ((k->nt & 1) == 0 && rup(k->nz, 16) <= 64) {
+  if (k->nt % 16 == 0 && rup(k->nz, 16) <= 64) {
     // warp-specialised kernel: m_hat [f][v][t] and W_hat [c t][z] staged by tensor maps
     const WsPlan W = make_ws_plan(k->nt, k->nz, fp8, batch);
     if (W.total <= 227 * 1024) {
+      // m_hat element (t = 16 h + tt, v, f) as a 4-D tensor (tt, v, h, f): one box
+      // of 16 tt x 16 volumes x TC/16 halves per member lands as [half][volume][16 t]
       CUtensorMap mmap, wmap;
-      const unsigned long long mdims[3] = {(unsigned long long)k->nt, (unsigned long long)batch,
+      const unsigned long long mdims[4] = {16, (unsigned long long)batch, (unsigned long long)k->nt / 16,
                                            (unsigned long long)k->nf};
-      const unsigned long long mstr[2] = {(unsigned long long)k->nt * 8, (unsigned long long)ldm * 8};
-      const unsigned mbox[3] = {16, VB, 1};
+      const unsigned long long mstr[3] = {(unsigned long long)k->nt * 8, 16 * 8, (unsigned long long)ldm * 8};
+      const unsigned mbox[4] = {16, VB, (unsigned)W.tc / 16, 1};
       const unsigned long long wdims[2] = {(unsigned long long)k->z4, (unsigned long long)k->nt * k->nclass};
       const unsigned long long wstr[1] = {(unsigned long long)k->z4 * 4};
-      const unsigned wbox[2] = {32, TCH};
-      if (ctof_encode_map(&mmap, 8, 3, m_hat, mdims, mstr, mbox, 128) == CTOF_OK &&
+      const unsigned wbox[2] = {32, (unsigned)W.tc};
+      if (ctof_encode_map(&mmap, 8, 4, m_hat, mdims, mstr, mbox, 128) == CTOF_OK &&
           ctof_encode_map(&wmap, 4, 2, k->d_what, wdims, wstr, wbox, 128) == CTOF_OK) {
-        CTOF_CUDA_TRY(
-          cudaFuncSetAttribute(k_batch_tikhonov_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, W.total));
-        k_batch_tikhonov_ws<<<grid, WS_THREADS, W.total, st>>>(mmap, wmap, W, k->d_bt_tab, k->d_bt_sw,
-                                                               k->d_members, k->nclass, m_hat, ldm, x_hat, ldx, refine,
-                                                               k->d_flags, k->max_polls);
+        auto kern = k_batch_tikhonov_ws<32>;
+        CTOF_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, W.total));
+        kern<<<grid, WS_THREADS, W.total, st>>>(mmap, wmap, W, k->d_bt_tab, k->d_bt_sw, k->d_members, k->nclass,
+                                                m_hat, ldm, x_hat, ldx, refine, k->d_flags, k->max_polls);
         CTOF_CUDA_TRY(cudaGetLastError());
         return CTOF_OK;
       }
