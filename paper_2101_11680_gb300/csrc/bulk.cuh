@@ -93,6 +93,15 @@ __device__ __forceinline__ void tensor_g2s_4d(void* dst, const void* map, int c0
       : "memory");
 }
 
+__device__ __forceinline__ void tensor_g2s_5d(void* dst, const void* map, int c0, int c1, int c2, int c3, int c4,
+                                              uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4, "
+      "%5, %6}], [%7];\n" ::"r"(saddr(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(saddr(bar))
+      : "memory");
+}
+
 __device__ __forceinline__ void tensor_g2s_2d(void* dst, const void* map, int c0, int c1, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "

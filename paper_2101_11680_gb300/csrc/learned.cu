@@ -25,7 +25,9 @@
 #include <new>
 #include <vector>
 
+#include "bulk.cuh"
 #include "ctof_internal.h"
+#include "umma.cuh"
 
 namespace {
 
@@ -218,12 +220,247 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d(const __nv_bfloat16* __re
   }
 }
 
+// ---- hidden layers at inference on tcgen05 ----
+//
+// out[v][co] = act(bias[co] + sum_tap sum_ci W[tap][co][ci] in[v + off(tap)][ci]) as
+// 27 accumulating MMAs per row of 128 output voxels along x (M = 128 voxels,
+// N = 16 output channels, K = 16 input channels; the input is stored after
+// its ReLU).  A work unit is TCV_YB output rows of one (volume, depth, x
+// segment); warp 0 (one thread) streams the unit's input rows (y - 1 .. y +
+// TCV_YB, each as its three depth planes, each plane as two 8-channel K
+// groups of 130 voxels: x0 - 1 .. x0 + 128) into a ring of TCV_RING slots by
+// tensor-map copies (zero fill outside the volume); warp 1 (one thread) issues
+// the MMAs of each output row into one of two TMEM accumulators, the three
+// x-shifted views of a staged plane being descriptor offsets of 16 bytes
+// (no-swizzle K-major layout: voxel rows 16 bytes apart, K groups TCV_KG
+// bytes apart); warps 4-7 add the bias, apply ReLU (or the fused residual
+// step x = z + mu0 bf16(out[v][0])) and store.  mbarrier hand-offs, bounded
+// waits.
+constexpr int TCV_RING = 4;
+constexpr int TCV_YB = 32;
+constexpr int TCV_KG = 144 * 16;                // bytes of one K-group region (130 voxel rows, padded)
+constexpr int TCV_SLOT = 3 * 2 * TCV_KG;        // one staged input row: 3 depth planes x 2 K groups
+constexpr int TCV_WB = 27 * 512;                // weights: [tap][K group][16 co][16 bytes]
+constexpr int TCV_THREADS = 256;
+constexpr int TCV_LOAD = 6 * 130 * 16;          // bytes landing per staged row
+constexpr size_t TCV_SMEM = 1024 + TCV_RING * TCV_SLOT + TCV_WB + 64 + 256;
+
+__host__ __device__ constexpr uint32_t tcv_idesc() {  // kind::f16: D F32, A / B BF16, N = 16, M = 128
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+}
+
+__device__ __forceinline__ void tcv_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n"
+      ".reg .pred p;\n"
+      "setp.ne.b32 p, %4, 0;\n"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+      "}\n" ::"r"(d),
+      "l"(a), "l"(b), "r"(tcv_idesc()), "r"(acc)
+      : "memory");
+}
+
+__device__ __forceinline__ bool tcv_wait(uint64_t* bar, uint32_t parity, long long max_polls, volatile int* abort_w,
+                                         int* flag) {
+  for (long long i = 0; i < max_polls; ++i) {
+    if (bulk::try_wait(bar, parity)) return true;
+    if (*abort_w) return false;
+    if (i >= 8) __nanosleep(32);
+  }
+  if (!*abort_w) {
+    *abort_w = 1;
+    atomicExch(flag, 1);
+  }
+  return false;
+}
+
+template <bool PROX>
+__global__ void __launch_bounds__(TCV_THREADS, 1)
+    k_conv3d_tc(const __grid_constant__ CUtensorMap amap, const __nv_bfloat16* __restrict__ w,
+                const float* __restrict__ bias, __nv_bfloat16* __restrict__ out, const float* __restrict__ z,
+                float* __restrict__ x_out, Geo G, int* flag, long long max_polls) {
+  extern __shared__ float4 tcv_smem4[];
+  unsigned char* sm;
+  {
+    const uint32_t s = bulk::saddr(tcv_smem4);
+    sm = reinterpret_cast<unsigned char*>(tcv_smem4) + (((s + 1023u) & ~1023u) - s);
+  }
+  unsigned char* ring = sm;
+  unsigned char* s_w = sm + TCV_RING * TCV_SLOT;
+  float* s_bias = reinterpret_cast<float*>(s_w + TCV_WB);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(s_bias + 16);
+  uint64_t* slot_full = bar;                 // [RING], one arrival + the copies' bytes
+  uint64_t* slot_empty = bar + TCV_RING;     // [RING], the MMAs that read the row (commit)
+  uint64_t* acc_full = bar + 2 * TCV_RING;   // [2], the row's MMAs (commit)
+  uint64_t* acc_empty = acc_full + 2;        // [2], one arrival per epilogue warp
+  uint64_t* drain_bar = acc_empty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain_bar + 1);
+  volatile int* abort_w = reinterpret_cast<volatile int*>(drain_bar + 2);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // weights into the canonical K-major layout of the B operand: element (co, ci)
+  // of tap t at t 512 + (ci / 8) 256 + co 16 + (ci % 8) 2
+  for (int i = threadIdx.x; i < 27 * 16 * 2; i += TCV_THREADS) {
+    const int t = i >> 5, co = (i >> 1) & 15, g = i & 1;
+    *reinterpret_cast<uint4*>(s_w + t * 512 + g * 256 + co * 16) =
+        *reinterpret_cast<const uint4*>(w + ((size_t)t * CH + co) * CH + 8 * g);
+  }
+  if (threadIdx.x < 16) s_bias[threadIdx.x] = bias ? bias[threadIdx.x] : 0.f;
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < TCV_RING; ++i) {
+      bulk::bar_init(slot_full + i, 1);
+      bulk::bar_init(slot_empty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      bulk::bar_init(acc_full + i, 1);
+      bulk::bar_init(acc_empty + i, 4);
+    }
+    bulk::bar_init(drain_bar, 1);
+    *abort_w = 0;
+  }
+  if (warp == 0) umma::tmem_alloc(tslot, 32);
+  umma::fence_proxy_async();  // the weights, before the MMAs read them
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t taddr = *tslot;
+  const int nseg = (G.x + 127) / 128, nyb = (G.y + TCV_YB - 1) / TCV_YB;
+  const int nunits = G.b * G.z * nyb * nseg;
+  auto unit_at = [&](int u, int& bb, int& zz, int& y0, int& x0) {
+    x0 = (u % nseg) * 128;
+    int r = u / nseg;
+    y0 = (r % nyb) * TCV_YB;
+    r /= nyb;
+    zz = r % G.z;
+    bb = r / G.z;
+  };
+
+  if (warp == 0) {
+    // ---------------- producer: input rows y0 - 1 .. y0 + TCV_YB of each unit ----------------
+    if (lane == 0) {
+      int gr = 0;  // rows staged
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        int bb, zz, y0, x0;
+        unit_at(u, bb, zz, y0, x0);
+        for (int j = 0; j < TCV_YB + 2; ++j, ++gr) {
+          const int s = gr % TCV_RING;
+          if (gr >= TCV_RING &&
+              !tcv_wait(slot_empty + s, (uint32_t)((gr / TCV_RING) + 1) & 1u, max_polls, abort_w, flag)) {
+            ok = false;
+            break;
+          }
+          unsigned char* dst = ring + s * TCV_SLOT;
+          bulk::arrive_expect(slot_full + s, TCV_LOAD);
+          for (int dz = 0; dz < 3; ++dz)
+            for (int g = 0; g < 2; ++g)
+              bulk::tensor_g2s_5d(dst + (dz * 2 + g) * TCV_KG, &amap, 8 * g, x0 - 1, y0 - 1 + j, zz - 1 + dz, bb,
+                                  slot_full + s);
+        }
+      }
+      // no copy may still be landing when the CTA ends: the last load into each slot
+      for (int s = 0; s < TCV_RING && s < gr; ++s)
+        bulk::wait(slot_full + s, (uint32_t)((gr - 1 - s) / TCV_RING) & 1u, bulk::DRAIN_POLLS);
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t sbase = bulk::saddr(ring), wbase = bulk::saddr(s_w);
+      int gr = 0, go = 0;  // rows waited for, output rows issued
+      bool ok = true;
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+        const int r0 = gr;  // this unit's first staged row
+        for (int j = 0; j < TCV_YB && ok; ++j, ++go) {
+          // rows r0 + j .. r0 + j + 2 must have landed (each waited for once)
+          while (gr <= r0 + j + 2) {
+            if (!tcv_wait(slot_full + gr % TCV_RING, (uint32_t)(gr / TCV_RING) & 1u, max_polls, abort_w, flag)) {
+              ok = false;
+              break;
+            }
+            ++gr;
+          }
+          if (!ok) break;
+          const int a = go & 1;
+          if (go >= 2 && !tcv_wait(acc_empty + a, (uint32_t)((go >> 1) + 1) & 1u, max_polls, abort_w, flag)) {
+            ok = false;
+            break;
+          }
+          umma::fence_after_sync();
+          for (int tap = 0; tap < 27; ++tap) {
+            const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+            const uint32_t arow = sbase + ((r0 + j + dy) % TCV_RING) * TCV_SLOT + dz * 2 * TCV_KG + dx * 16;
+            const uint64_t ad = umma::desc(arow, TCV_KG, 128);
+            const uint64_t bd = umma::desc(wbase + tap * 512, 256, 128);
+            tcv_mma(taddr + 16 * a, ad, bd, tap > 0 ? 1u : 0u);
+          }
+          umma::commit(acc_full + a);
+          umma::commit(slot_empty + (r0 + j) % TCV_RING);  // input row y0 - 1 + j is read for the last time
+        }
+        if (ok) {  // the unit's last two rows
+          umma::commit(slot_empty + (r0 + TCV_YB) % TCV_RING);
+          umma::commit(slot_empty + (r0 + TCV_YB + 1) % TCV_RING);
+        }
+      }
+      umma::commit(drain_bar);
+      bulk::wait(drain_bar, 0, bulk::DRAIN_POLLS);
+    }
+  } else if (warp >= 4) {
+    // ---------------- epilogue: bias, activation, store ----------------
+    const int r = 32 * (warp & 3) + lane;  // TMEM lane = voxel of the 128-row
+    const uint32_t trow = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
+    int go = 0;
+    bool ok = true;
+    for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
+      int bb, zz, y0, x0;
+      unit_at(u, bb, zz, y0, x0);
+      for (int j = 0; j < TCV_YB; ++j, ++go) {
+        const int a = go & 1;
+        int w_ok = 1;
+        if (lane == 0) w_ok = tcv_wait(acc_full + a, (uint32_t)(go >> 1) & 1u, max_polls, abort_w, flag) ? 1 : 0;
+        w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
+        if (!w_ok) {
+          ok = false;
+          break;
+        }
+        if (lane != 0) (void)bulk::try_wait(acc_full + a, (uint32_t)(go >> 1) & 1u);
+        umma::fence_after_sync();
+        float d[16];
+        umma::tmem_ld16(trow + 16 * a, d);
+        umma::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) bulk::arrive(acc_empty + a);
+        const int yy = y0 + j, xx = x0 + r;
+        if (yy < G.y && xx < G.x) {
+          const long long v = (((long long)bb * G.z + zz) * G.y + yy) * G.x + xx;
+          if (PROX) {
+            const float f0 = __bfloat162float(__float2bfloat16_rn(d[0] + s_bias[0]));
+            x_out[v] = z[v] + MU0 * f0;
+          } else {
+            unsigned p[8];
+#pragma unroll
+            for (int e = 0; e < 8; ++e)
+              p[e] = pack2(__float2bfloat16_rn(fmaxf(d[2 * e] + s_bias[2 * e], 0.f)),
+                           __float2bfloat16_rn(fmaxf(d[2 * e + 1] + s_bias[2 * e + 1], 0.f)));
+            uint4* o = reinterpret_cast<uint4*>(out + v * CH);
+            o[0] = make_uint4(p[0], p[1], p[2], p[3]);
+            o[1] = make_uint4(p[4], p[5], p[6], p[7]);
+          }
+        }
+      }
+    }
+  }
+  __syncwarp();
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  if (warp == 0) umma::tmem_dealloc(taddr, 32);
+}
+
 // First layer at inference: one input channel (z / mu0), so the 27 taps (padded
 // to 32) form the MMA's K dimension instead of 27 K = 16 channel blocks with
 // 15 zero channels: 2 x 2 MMAs per 16-voxel job instead of 27 x 2.  The input
 // tile holds one BF16 value per voxel; A fragments are gathered from it tap by
 // tap, B fragments (W1[co][tap]) sit in registers for the whole CTA.
-template <int TXC>
+template <int TXC, bool RELU_OUT>
 __global__ void __launch_bounds__(CV_THREADS) k_conv_first(const float* __restrict__ zin, float in_scale,
                                                            const __nv_bfloat16* __restrict__ w,
                                                            const float* __restrict__ bias,
@@ -296,10 +533,16 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv_first(const float* __restri
 #pragma unroll
     for (int nt = 0; nt < 2; ++nt) {
       const int co = nt * 8 + 2 * tg;
-      outw[v0 * 8 + (co >> 1)] =
-          pack2(__float2bfloat16_rn(acc[j][nt][0] + bias[co]), __float2bfloat16_rn(acc[j][nt][1] + bias[co + 1]));
-      outw[v1 * 8 + (co >> 1)] =
-          pack2(__float2bfloat16_rn(acc[j][nt][2] + bias[co]), __float2bfloat16_rn(acc[j][nt][3] + bias[co + 1]));
+      float r0 = acc[j][nt][0] + bias[co], r1 = acc[j][nt][1] + bias[co + 1];
+      float r2 = acc[j][nt][2] + bias[co], r3 = acc[j][nt][3] + bias[co + 1];
+      if (RELU_OUT) {
+        r0 = fmaxf(r0, 0.f);
+        r1 = fmaxf(r1, 0.f);
+        r2 = fmaxf(r2, 0.f);
+        r3 = fmaxf(r3, 0.f);
+      }
+      outw[v0 * 8 + (co >> 1)] = pack2(__float2bfloat16_rn(r0), __float2bfloat16_rn(r1));
+      outw[v1 * 8 + (co >> 1)] = pack2(__float2bfloat16_rn(r2), __float2bfloat16_rn(r3));
     }
   }
 }
@@ -654,16 +897,57 @@ ctof_status conv_launch(const __nv_bfloat16* in, const float* in_f, float in_sca
   return CTOF_OK;
 }
 
+// relu_out: store ReLU(out) (the next layer applies ReLU to its input, so
+// storing it after the ReLU gives that layer the same values).
 ctof_status conv_first(const float* z, float in_scale, const __nv_bfloat16* wt, const float* bias,
-                       __nv_bfloat16* out, Geo G, cudaStream_t st) {
+                       __nv_bfloat16* out, Geo G, bool relu_out, cudaStream_t st) {
   const int txc = G.x % 64 == 0 ? 4 : (G.x % 32 == 0 ? 2 : 1);
   const dim3 grid(G.x / (16 * txc), G.y / CV_TY, G.b * G.z);
-  if (txc == 4)
-    k_conv_first<4><<<grid, CV_THREADS, 0, st>>>(z, in_scale, wt, bias, out, G);
-  else if (txc == 2)
-    k_conv_first<2><<<grid, CV_THREADS, 0, st>>>(z, in_scale, wt, bias, out, G);
-  else
-    k_conv_first<1><<<grid, CV_THREADS, 0, st>>>(z, in_scale, wt, bias, out, G);
+#define CTOF_FIRST_CASE(T)                                                                                    \
+  if (relu_out)                                                                                               \
+    k_conv_first<T, true><<<grid, CV_THREADS, 0, st>>>(z, in_scale, wt, bias, out, G);                      \
+  else                                                                                                        \
+    k_conv_first<T, false><<<grid, CV_THREADS, 0, st>>>(z, in_scale, wt, bias, out, G);
+  if (txc == 4) {
+    CTOF_FIRST_CASE(4)
+  } else if (txc == 2) {
+    CTOF_FIRST_CASE(2)
+  } else {
+    CTOF_FIRST_CASE(1)
+  }
+#undef CTOF_FIRST_CASE
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+// Inference hidden / last layer on tcgen05 (input stored after its ReLU):
+// out = ReLU(conv(in) + bias), or with prox x_out = z + mu0 bf16(conv(in)[0] + bias[0]).
+// EUNSUPPORTED when the activation cannot be described by a tensor map.
+ctof_status conv_tc(const ctof_kernel_s* k, const __nv_bfloat16* in, const __nv_bfloat16* wt, const float* bias,
+                    __nv_bfloat16* out, const float* z, float* x_out, Geo G, bool prox, cudaStream_t st) {
+  CUtensorMap amap;
+  const unsigned long long X = G.x, Y = G.y, Z = G.z;
+  const unsigned long long dims[5] = {16, X, Y, Z, (unsigned long long)G.b};
+  const unsigned long long strides[4] = {32, X * 32, Y * X * 32, Z * Y * X * 32};
+  const unsigned box[5] = {8, 130, 1, 1, 1};
+  if (ctof_encode_map(&amap, 2, 5, in, dims, strides, box, 0) != CTOF_OK) {
+    ctof_set_last_error_text("");
+    return CTOF_EUNSUPPORTED;
+  }
+  const int nunits = G.b * G.z * ((G.y + TCV_YB - 1) / TCV_YB) * ((G.x + 127) / 128);
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
+  const int grid = nunits < 3 * nsm ? nunits : 3 * nsm;
+  if (prox) {
+    CTOF_CUDA_TRY(cudaFuncSetAttribute(k_conv3d_tc<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCV_SMEM));
+    k_conv3d_tc<true><<<grid, TCV_THREADS, TCV_SMEM, st>>>(amap, wt, bias, out, z, x_out, G, k->d_flags,
+                                                           k->max_polls);
+  } else {
+    CTOF_CUDA_TRY(
+        cudaFuncSetAttribute(k_conv3d_tc<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)TCV_SMEM));
+    k_conv3d_tc<false><<<grid, TCV_THREADS, TCV_SMEM, st>>>(amap, wt, bias, out, z, x_out, G, k->d_flags,
+                                                            k->max_polls);
+  }
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
 }
@@ -769,7 +1053,16 @@ ctof_status unrolled_forward(ctof_learned_s* L, ctof_kernel_s* k, int batch, con
       CTOF_CUDA_TRY(cudaGetLastError());
       CTOF_TRY(conv(u, 0, L->d_wf + 0 * 27 * CH * CH, L->d_bias + 0 * CH, nullptr, y1, G, st));
     } else {
-      CTOF_TRY(conv_first(z, 1.0f / MU0, L->d_wf, L->d_bias, y1, G, st));
+      // inference: activations stored after their ReLU; hidden and last layers on tcgen05
+      CTOF_TRY(conv_first(z, 1.0f / MU0, L->d_wf, L->d_bias, y1, G, true, st));
+      const ctof_status s2 = conv_tc(k, y1, L->d_wf + 1 * 27 * CH * CH, L->d_bias + 1 * CH, y2, nullptr, nullptr, G,
+                                     false, st);
+      if (s2 == CTOF_OK) {
+        CTOF_TRY(conv_tc(k, y2, L->d_wf + 2 * 27 * CH * CH, L->d_bias + 2 * CH, y3, nullptr, nullptr, G, false, st));
+        CTOF_TRY(conv_tc(k, y3, L->d_wf + 3 * 27 * CH * CH, L->d_bias + 3 * CH, nullptr, z, w.x, G, true, st));
+        continue;
+      }
+      if (s2 != CTOF_EUNSUPPORTED) return s2;
     }
     CTOF_TRY(conv(y1, 1, L->d_wf + 1 * 27 * CH * CH, L->d_bias + 1 * CH, nullptr, y2, G, st));
     CTOF_TRY(conv(y2, 1, L->d_wf + 2 * 27 * CH * CH, L->d_bias + 2 * CH, nullptr, y3, G, st));
