@@ -235,7 +235,11 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d(const __nv_bfloat16* __re
 // (no-swizzle K-major layout: voxel rows 16 bytes apart, K groups TCV_KG
 // bytes apart); warps 4-7 add the bias, apply ReLU (or the fused residual
 // step x = z + mu0 bf16(out[v][0])) and store.  mbarrier hand-offs, bounded
-// waits.
+// waits.  Three CTAs share an SM.  Each MMA (N = 16) reads its 4 KB A tile
+// from shared memory, which bounds the kernel (~36 cycles of shared-memory
+// bandwidth per MMA); a variant that stacked the three dy taps into one
+// N = 48 operand (a third of the A reads, output rows accumulating in a
+// 32-slot TMEM ring, one CTA per SM) measured slower.
 constexpr int TCV_RING = 4;
 constexpr int TCV_YB = 32;
 constexpr int TCV_KG = 144 * 16;                // bytes of one K-group region (130 voxel rows, padded)
@@ -364,7 +368,8 @@ __global__ void __launch_bounds__(TCV_THREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint32_t sbase = bulk::saddr(ring), wbase = bulk::saddr(s_w);
+      const uint64_t a_desc0 = umma::desc(bulk::saddr(ring), TCV_KG, 128);  // slot 0, plane 0, x shift 0
+      const uint64_t b_desc0 = umma::desc(bulk::saddr(s_w), 256, 128);      // tap 0
       int gr = 0, go = 0;  // rows waited for, output rows issued
       bool ok = true;
       for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
@@ -385,12 +390,17 @@ __global__ void __launch_bounds__(TCV_THREADS, 1)
             break;
           }
           umma::fence_after_sync();
+          // descriptors are linear in the start address (16-byte units in the low bits)
+          uint64_t arow[3];
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy)
+            arow[dy] = a_desc0 + (uint64_t)(((unsigned)(r0 + j + dy) & (TCV_RING - 1)) * (TCV_SLOT >> 4));
+          const uint32_t d_acc = taddr + 16 * a;
+#pragma unroll
           for (int tap = 0; tap < 27; ++tap) {
             const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-            const uint32_t arow = sbase + ((r0 + j + dy) % TCV_RING) * TCV_SLOT + dz * 2 * TCV_KG + dx * 16;
-            const uint64_t ad = umma::desc(arow, TCV_KG, 128);
-            const uint64_t bd = umma::desc(wbase + tap * 512, 256, 128);
-            tcv_mma(taddr + 16 * a, ad, bd, tap > 0 ? 1u : 0u);
+            tcv_mma(d_acc, arow[dy] + (uint64_t)((dz * 2 * TCV_KG + dx * 16) >> 4), b_desc0 + (uint64_t)(tap * 32),
+                    tap > 0 ? 1u : 0u);
           }
           umma::commit(acc_full + a);
           umma::commit(slot_empty + (r0 + j) % TCV_RING);  // input row y0 - 1 + j is read for the last time
