@@ -539,23 +539,49 @@ ctof_status batch_graph_run(int count, const ctof_kernel* ks, const float* const
           s = CTOF_ECUDA;
       }
     };
+    // side streams: the problems with their own x-update launch get streams of
+    // their own (they run beside the queue launch), the queued ones share the rest
+    std::vector<int> stream_of(count);
+    {
+      int nown = 0;
+      for (int i = 0; i < count; ++i) nown += !queued[i];
+      const int own_streams = nown < nside / 2 ? nown : nside / 2;
+      int a = 0, b = 0;
+      for (int i = 0; i < count; ++i) {
+        if (!queued[i] && own_streams > 0)
+          stream_of[i] = (a++) % own_streams;
+        else
+          stream_of[i] = own_streams + (b++) % (nside - own_streams > 0 ? nside - own_streams : 1);
+        if (stream_of[i] >= nside) stream_of[i] = nside - 1;
+      }
+    }
     fork();
     for (int i = 0; i < count && s == CTOF_OK; ++i) {
       ctof_kernel_s* k = ks[i];
-      cudaStream_t side = g_side_streams[i % nside];
+      cudaStream_t side = g_side_streams[stream_of[i]];
       const size_t mb = (size_t)k->nt * k->n * k->n * sizeof(float);
       if (cudaMemcpyAsync(k->d_mstage, d_m[i], mb, cudaMemcpyDeviceToDevice, side) != cudaSuccess) s = CTOF_ECUDA;
       if (s == CTOF_OK) s = admm_setup(k, prm, side);
     }
     join();
-    // iterations in lockstep: the queued x-updates of all problems as one launch,
-    // then every problem's own x-update (if not queued) and T / Z sides on its stream
+    // iterations in lockstep: the problems with their own x-update run it and their
+    // T / Z sides from the iteration's start; beside them the queued x-updates of
+    // all other problems run as one launch, after which their T / Z sides follow
+    cudaEvent_t ev_q = g_side_events[nside];
     for (int it = 0; it < prm->iters && s == CTOF_OK; ++it) {
-      s = admm_queue_launch(g_batch.queue, cap);
       fork();
       for (int i = 0; i < count && s == CTOF_OK; ++i) {
-        cudaStream_t side = g_side_streams[i % nside];
-        if (!queued[i]) s = admm_contract(ks[i], side);
+        if (queued[i]) continue;
+        cudaStream_t side = g_side_streams[stream_of[i]];
+        s = admm_contract(ks[i], side);
+        if (s == CTOF_OK) s = admm_side(ks[i], prm, it, side, nullptr);
+      }
+      if (s == CTOF_OK) s = admm_queue_launch(g_batch.queue, cap);
+      if (s == CTOF_OK && cudaEventRecord(ev_q, cap) != cudaSuccess) s = CTOF_ECUDA;
+      for (int i = 0; i < count && s == CTOF_OK; ++i) {
+        if (!queued[i]) continue;
+        cudaStream_t side = g_side_streams[stream_of[i]];
+        if (cudaStreamWaitEvent(side, ev_q, 0) != cudaSuccess) s = CTOF_ECUDA;
         if (s == CTOF_OK) s = admm_side(ks[i], prm, it, side, nullptr);
       }
       join();
@@ -564,7 +590,7 @@ ctof_status batch_graph_run(int count, const ctof_kernel* ks, const float* const
     for (int i = 0; i < count && s == CTOF_OK; ++i) {
       ctof_kernel_s* k = ks[i];
       const size_t vb = (size_t)k->nz * k->n * k->n * sizeof(float);
-      if (cudaMemcpyAsync(d_mu[i], k->d_vstage, vb, cudaMemcpyDeviceToDevice, g_side_streams[i % nside]) !=
+      if (cudaMemcpyAsync(d_mu[i], k->d_vstage, vb, cudaMemcpyDeviceToDevice, g_side_streams[stream_of[i]]) !=
           cudaSuccess)
         s = CTOF_ECUDA;
     }
