@@ -25,6 +25,7 @@
 // synchronising call.
 #include <cuda_runtime.h>
 
+#include "bulk.cuh"
 #include "ctof_internal.h"
 #include "umma.cuh"
 
@@ -486,6 +487,319 @@ __global__ void __launch_bounds__(TC_THREADS, 2) k_contract_tc_adj(TcPlan P, con
   tc_teardown(taddr, P);
 }
 
+// ---- warp-specialised adjoint (bins a multiple of 16) ----
+//
+// D[n][z] = sum_t C[n][t] W[t][z] for (class, 16-volume chunk) items, with
+// n = 32 m + 16 c + v (member, real / imaginary, volume).  Warp 0 (one
+// thread) stages each chunk of 32 t with tensor-map copies (per member one
+// box of 2 halves x 16 volumes x 16 t of r_hat [v][f][t], two W_hat boxes of
+// 32 t x 32 z; 128-byte swizzle) into AW_STAGES raw stages; warps 1-8 split a
+// staged chunk into TF32 high parts and FP32 remainders in the K-major
+// layout (as many term sets as raw stages); warp 9 (one thread) issues three
+// MMAs per K = 8 step into one of two TMEM accumulators; warps 12-15 write
+// the finished item out.  mbarrier hand-offs; every wait is bounded, a wait
+// that runs out sets the handle's flag and a shared abort word and every
+// role leaves its loop.
+constexpr int AW_CONV = 8;
+constexpr int AW_MMA_WARP = 9;
+constexpr int AW_EPI0 = 12;
+constexpr int AW_THREADS = (AW_EPI0 + 4) * 32;
+constexpr int AW_STAGES = 3;
+constexpr int AW_MBOX = 16 * 16 * 8;  // r_hat box of one member and one 16-t half
+constexpr int AW_WBOX = 32 * 32 * 4;  // W_hat box: 32 t x 32 z
+
+struct AwPlan {
+  int nt, nz, z4, zn, nwb;
+  int a_term, b_term, set_bytes, raw_stage;
+  int off_raw, off_set, off_bar, total;
+};
+
+AwPlan make_aw_plan(int nt, int nz) {
+  AwPlan P{};
+  P.nt = nt;
+  P.nz = nz;
+  P.z4 = rup(nz, 4);
+  P.zn = rup(nz, 16);
+  P.nwb = P.z4 <= 32 ? 1 : 2;
+  P.a_term = NR * TCH * 4;
+  P.b_term = P.zn * TCH * 4;
+  P.set_bytes = 2 * (P.a_term + P.b_term);
+  P.raw_stage = rup(8 * AW_MBOX + P.nwb * AW_WBOX, 1024);
+  P.off_raw = 0;
+  P.off_set = AW_STAGES * P.raw_stage;
+  P.off_bar = P.off_set + AW_STAGES * P.set_bytes;
+  P.total = P.off_bar + 256 + 1024;  // + room to align the base to 1024 bytes
+  return P;
+}
+
+__device__ __forceinline__ bool aw_wait(uint64_t* bar, uint32_t parity, long long max_polls, volatile int* abort_w,
+                                        int* flag) {
+  for (long long i = 0; i < max_polls; ++i) {
+    if (bulk::try_wait(bar, parity)) return true;
+    if (*abort_w) return false;
+    if (i >= 8) __nanosleep(32);
+  }
+  if (!*abort_w) {
+    *abort_w = 1;
+    atomicExch(flag, 1);
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool aw_wait_warp(uint64_t* bar, uint32_t parity, long long max_polls,
+                                             volatile int* abort_w, int* flag, int lane) {
+  int ok = 1;
+  if (lane == 0) ok = aw_wait(bar, parity, max_polls, abort_w, flag) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (ok && lane != 0) (void)bulk::try_wait(bar, parity);
+  return ok != 0;
+}
+
+// Split one staged chunk (converter thread ct of 256): A rows n (K = t) and
+// B = W^T rows z (K = t), TF32 high part and FP32 remainder each.
+__device__ __forceinline__ void aw_convert(const AwPlan& P, const unsigned char* raw, unsigned char* set,
+                                           const int (&mem)[4], int ct) {
+  unsigned char* ahi = set;
+  unsigned char* alo = set + P.a_term;
+  unsigned char* bhi = set + 2 * P.a_term;
+  unsigned char* blo = bhi + P.b_term;
+  for (int i = ct; i < 64 * (TCH / 4); i += AW_CONV * 32) {
+    const int v = i & 15, m = (i >> 4) & 3, gI = i >> 6;  // 4 t values 4 gI ..
+    const int nre = 32 * m + v, nim = nre + 16;
+    const uint32_t o_re = umma::kmajor_off(NR, nre, 4 * gI), o_im = umma::kmajor_off(NR, nim, 4 * gI);
+    float4 re = make_float4(0.f, 0.f, 0.f, 0.f), im = re;
+    if (pick(mem, m) >= 0) {
+      const int t0 = 4 * gI;
+      const unsigned char* rowp = raw + (2 * m + (t0 >> 4)) * AW_MBOX + v * 128;
+      const int c0 = (t0 & 15) >> 1;
+      const float4 q0 = *reinterpret_cast<const float4*>(rowp + ((c0 ^ (v & 7)) << 4));
+      const float4 q1 = *reinterpret_cast<const float4*>(rowp + (((c0 + 1) ^ (v & 7)) << 4));
+      re = make_float4(q0.x, q0.z, q1.x, q1.z);
+      im = make_float4(q0.y, q0.w, q1.y, q1.w);
+    }
+    float4 h, l;
+    umma::split_tf32(re.x, h.x, l.x);
+    umma::split_tf32(re.y, h.y, l.y);
+    umma::split_tf32(re.z, h.z, l.z);
+    umma::split_tf32(re.w, h.w, l.w);
+    *reinterpret_cast<float4*>(ahi + o_re) = h;
+    *reinterpret_cast<float4*>(alo + o_re) = l;
+    umma::split_tf32(im.x, h.x, l.x);
+    umma::split_tf32(im.y, h.y, l.y);
+    umma::split_tf32(im.z, h.z, l.z);
+    umma::split_tf32(im.w, h.w, l.w);
+    *reinterpret_cast<float4*>(ahi + o_im) = h;
+    *reinterpret_cast<float4*>(alo + o_im) = l;
+  }
+  const unsigned char* rw = raw + 8 * AW_MBOX;
+  for (int i = ct; i < P.zn * (TCH / 4); i += AW_CONV * 32) {
+    const int z = i % P.zn, gI = i / P.zn;
+    const unsigned char* box = rw + (z >> 5) * AW_WBOX + (z & 3) * 4;
+    const int zc = (z & 31) >> 2;
+    float w[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int t = 4 * gI + e;
+      w[e] = *reinterpret_cast<const float*>(box + t * 128 + ((zc ^ (t & 7)) << 4));
+    }
+    float4 h, l;
+    umma::split_tf32(w[0], h.x, l.x);
+    umma::split_tf32(w[1], h.y, l.y);
+    umma::split_tf32(w[2], h.z, l.z);
+    umma::split_tf32(w[3], h.w, l.w);
+    const uint32_t o = umma::kmajor_off(P.zn, z, 4 * gI);
+    *reinterpret_cast<float4*>(bhi + o) = h;
+    *reinterpret_cast<float4*>(blo + o) = l;
+  }
+}
+
+__global__ void __launch_bounds__(AW_THREADS, 1)
+    k_contract_tc_adj_ws(const __grid_constant__ CUtensorMap cmap, const __grid_constant__ CUtensorMap wmap,
+                         AwPlan P, const int* __restrict__ members, int nclass, int nvol,
+                         float2* __restrict__ vout, int ld_out, size_t out_vstride, int* flag, long long max_polls) {
+  extern __shared__ float4 aw_smem4[];
+  unsigned char* sm;
+  {
+    const uint32_t s = bulk::saddr(aw_smem4);
+    sm = reinterpret_cast<unsigned char*>(aw_smem4) + (((s + 1023u) & ~1023u) - s);
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nt = P.nt, nz = P.nz, zn = P.zn;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(sm + P.off_bar);
+  uint64_t* raw_full = bar;                       // [S] one arrival + the copies' bytes
+  uint64_t* raw_empty = bar + AW_STAGES;          // [S] one arrival per converter warp
+  uint64_t* term_full = bar + 2 * AW_STAGES;      // [S] one arrival per converter warp
+  uint64_t* term_empty = bar + 3 * AW_STAGES;     // [S] the MMAs that read the set (commit)
+  uint64_t* acc_full = bar + 4 * AW_STAGES;       // [2] the item's MMAs (commit)
+  uint64_t* acc_empty = acc_full + 2;             // [2] one arrival per epilogue warp
+  uint64_t* drain_bar = acc_empty + 2;
+  uint32_t* tslot = reinterpret_cast<uint32_t*>(drain_bar + 1);
+  volatile int* abort_w = reinterpret_cast<volatile int*>(drain_bar + 2);
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < AW_STAGES; ++i) {
+      bulk::bar_init(raw_full + i, 1);
+      bulk::bar_init(raw_empty + i, AW_CONV);
+      bulk::bar_init(term_full + i, AW_CONV);
+      bulk::bar_init(term_empty + i, 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      bulk::bar_init(acc_full + i, 1);
+      bulk::bar_init(acc_empty + i, 4);
+    }
+    bulk::bar_init(drain_bar, 1);
+    *abort_w = 0;
+  }
+  if (warp == 0) umma::tmem_alloc(tslot, 128);
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  const uint32_t taddr = *tslot;
+  const int nchunks = (nt + TCH - 1) / TCH, nvc = (nvol + VB - 1) / VB;
+
+  if (warp == 0) {
+    // ---------------- producer ----------------
+    if (lane == 0) {
+      int gk = 0;
+      bool ok = true;
+      for (int c = blockIdx.x; c < nclass && ok; c += gridDim.x) {
+        int mem[4];
+        int present = 0;
+        for (int m = 0; m < 4; ++m) {
+          mem[m] = __ldg(members + 4 * c + m);
+          present += mem[m] >= 0;
+        }
+        for (int vc = 0; vc < nvc && ok; ++vc)
+          for (int kc = 0; kc < nchunks; ++kc, ++gk) {
+            const int s = gk % AW_STAGES;
+            if (gk >= AW_STAGES &&
+                !aw_wait(raw_empty + s, (uint32_t)((gk / AW_STAGES) + 1) & 1u, max_polls, abort_w, flag)) {
+              ok = false;
+              break;
+            }
+            unsigned char* st = sm + P.off_raw + s * P.raw_stage;
+            bulk::arrive_expect(raw_full + s, (unsigned)(present * 2 * AW_MBOX + P.nwb * AW_WBOX));
+            for (int m = 0; m < 4; ++m)
+              if (mem[m] >= 0)
+                bulk::tensor_g2s_4d(st + 2 * m * AW_MBOX, &cmap, 0, vc * VB, 2 * kc, mem[m], raw_full + s);
+            for (int wb = 0; wb < P.nwb; ++wb)
+              bulk::tensor_g2s_2d(st + 8 * AW_MBOX + wb * AW_WBOX, &wmap, 32 * wb, c * nt + kc * TCH, raw_full + s);
+          }
+      }
+      for (int s = 0; s < AW_STAGES && s < gk; ++s)
+        bulk::wait(raw_full + s, (uint32_t)((gk - 1 - s) / AW_STAGES) & 1u, DRAIN_POLLS);
+    }
+  } else if (warp <= AW_CONV) {
+    // ---------------- converters ----------------
+    const int ct = threadIdx.x - 32;
+    int gk = 0;
+    bool ok = true;
+    for (int c = blockIdx.x; c < nclass && ok; c += gridDim.x) {
+      int mem[4];
+#pragma unroll
+      for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
+      for (int vc = 0; vc < nvc && ok; ++vc)
+        for (int kc = 0; kc < nchunks; ++kc, ++gk) {
+          const int s = gk % AW_STAGES;
+          if (!aw_wait_warp(raw_full + s, (uint32_t)(gk / AW_STAGES) & 1u, max_polls, abort_w, flag, lane) ||
+              (gk >= AW_STAGES && !aw_wait_warp(term_empty + s, (uint32_t)((gk / AW_STAGES) + 1) & 1u, max_polls,
+                                                abort_w, flag, lane))) {
+            ok = false;
+            break;
+          }
+          aw_convert(P, sm + P.off_raw + s * P.raw_stage, sm + P.off_set + s * P.set_bytes, mem, ct);
+          umma::fence_proxy_async();  // this lane's term writes, before the MMAs read them
+          __syncwarp();
+          if (lane == 0) {
+            bulk::arrive(raw_empty + s);
+            bulk::arrive(term_full + s);
+          }
+        }
+    }
+  } else if (warp == AW_MMA_WARP) {
+    // ---------------- MMA issuer ----------------
+    if (lane == 0) {
+      const uint32_t idesc = umma::idesc_tf32(NR, zn);
+      const uint32_t sbase = bulk::saddr(sm);
+      int gk = 0, it = 0;
+      bool ok = true;
+      for (int c = blockIdx.x; c < nclass && ok; c += gridDim.x)
+        for (int vc = 0; vc < nvc && ok; ++vc, ++it) {
+          const int a = it & 1;
+          if (it >= 2 && !aw_wait(acc_empty + a, (uint32_t)((it >> 1) + 1) & 1u, max_polls, abort_w, flag)) {
+            ok = false;
+            break;
+          }
+          umma::fence_after_sync();
+          const uint32_t acc = taddr + (uint32_t)(a * 64);
+          for (int kc = 0; kc < nchunks; ++kc, ++gk) {
+            const int s = gk % AW_STAGES;
+            if (!aw_wait(term_full + s, (uint32_t)(gk / AW_STAGES) & 1u, max_polls, abort_w, flag)) {
+              ok = false;
+              break;
+            }
+            umma::fence_after_sync();
+            const uint32_t a0 = sbase + P.off_set + s * P.set_bytes;
+            const uint32_t b0 = a0 + 2 * P.a_term;
+            for (int k = 0; k < TCH / 8; ++k) {
+              const uint64_t ah = umma::desc(a0 + k * 2 * NR * 16, NR * 16, 128);
+              const uint64_t al = umma::desc(a0 + P.a_term + k * 2 * NR * 16, NR * 16, 128);
+              const uint64_t bh = umma::desc(b0 + k * 2 * zn * 16, zn * 16, 128);
+              const uint64_t bl = umma::desc(b0 + P.b_term + k * 2 * zn * 16, zn * 16, 128);
+              umma::mma_tf32(acc, al, bh, idesc, (kc > 0 || k > 0) ? 1u : 0u);
+              umma::mma_tf32(acc, ah, bl, idesc, 1);
+              umma::mma_tf32(acc, ah, bh, idesc, 1);
+            }
+            umma::commit(term_empty + s);
+          }
+          if (ok) umma::commit(acc_full + a);
+        }
+      umma::commit(drain_bar);
+      bulk::wait(drain_bar, 0, DRAIN_POLLS);
+    }
+  } else if (warp >= AW_EPI0) {
+    // ---------------- epilogue: write the item's D ----------------
+    const int n = 32 * (warp & 3) + lane;  // TMEM lane = right-hand side
+    const uint32_t trow = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
+    const int v = n & 15, ri = (n >> 4) & 1, m = n >> 5;
+    int it = 0;
+    bool ok = true;
+    for (int c = blockIdx.x; c < nclass && ok; c += gridDim.x) {
+      int mem[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) mem[q] = __ldg(members + 4 * c + q);
+      for (int vc = 0; vc < nvc && ok; ++vc, ++it) {
+        const int a = it & 1, v0 = vc * VB, nv = nvol - v0 < VB ? nvol - v0 : VB;
+        if (!aw_wait_warp(acc_full + a, (uint32_t)(it >> 1) & 1u, max_polls, abort_w, flag, lane)) {
+          ok = false;
+          break;
+        }
+        umma::fence_after_sync();
+        const int fm = pick(mem, m);
+        const bool writer = ri == 0 && v < nv && fm >= 0;
+        float2* dst = vout + (size_t)(v0 + (v < nv ? v : 0)) * out_vstride + (size_t)(fm >= 0 ? fm : 0) * ld_out;
+        for (int j = 0; j < zn / 16; ++j) {
+          float d[16];
+          umma::tmem_ld16(trow + (uint32_t)(a * 64 + 16 * j), d);
+#pragma unroll
+          for (int e = 0; e < 16; ++e) {
+            const float im = __shfl_down_sync(0xffffffffu, d[e], 16);
+            const int z = 16 * j + e;
+            if (writer && z < nz) dst[z] = make_float2(d[e], im);
+          }
+        }
+        umma::fence_before_sync();
+        __syncwarp();
+        if (lane == 0) bulk::arrive(acc_empty + a);
+      }
+    }
+  }
+  __syncwarp();
+  umma::fence_before_sync();
+  __syncthreads();
+  umma::fence_after_sync();
+  if (warp == 0) umma::tmem_dealloc(taddr, 128);
+}
+
 template <typename K>
 ctof_status launch_tc(K kern, const TcPlan& P, const ctof_kernel_s* k, int nvol, const float2* vin, int ld_in,
                       size_t in_vstride, float2* vout, int ld_out, size_t out_vstride, cudaStream_t st) {
@@ -512,6 +826,37 @@ ctof_status launch_tc(K kern, const TcPlan& P, const ctof_kernel_s* k, int nvol,
   return CTOF_OK;
 }
 
+// The warp-specialised adjoint when the bins are a multiple of 16 (tensor-map
+// staging) and its buffers take tensor maps; EUNSUPPORTED otherwise.
+ctof_status launch_adj_ws(const ctof_kernel_s* k, int nvol, const float2* vin, int ld_in, size_t in_vstride,
+                          float2* vout, int ld_out, size_t out_vstride, cudaStream_t st) {
+  if (k->nt % 16 != 0 || rup(k->nz, 16) > 64) return CTOF_EUNSUPPORTED;
+  const AwPlan P = make_aw_plan(k->nt, k->nz);
+  if (P.total > 227 * 1024) return CTOF_EUNSUPPORTED;
+  CUtensorMap cmap, wmap;
+  // r_hat element (t = 16 h + tt, v, f) as a 4-D tensor (tt, v, h, f)
+  const unsigned long long cdims[4] = {16, (unsigned long long)nvol, (unsigned long long)k->nt / 16,
+                                       (unsigned long long)k->nf};
+  const unsigned long long cstr[3] = {(unsigned long long)in_vstride * 8, 16 * 8, (unsigned long long)ld_in * 8};
+  const unsigned cbox[4] = {16, VB, 2, 1};
+  const unsigned long long wdims[2] = {(unsigned long long)k->z4, (unsigned long long)k->nt * k->nclass};
+  const unsigned long long wstr[1] = {(unsigned long long)k->z4 * 4};
+  const unsigned wbox[2] = {32, TCH};
+  if (ctof_encode_map(&cmap, 8, 4, vin, cdims, cstr, cbox, 128) != CTOF_OK ||
+      ctof_encode_map(&wmap, 4, 2, k->d_what, wdims, wstr, wbox, 128) != CTOF_OK) {
+    ctof_set_last_error_text("");
+    return CTOF_EUNSUPPORTED;
+  }
+  CTOF_CUDA_TRY(cudaFuncSetAttribute(k_contract_tc_adj_ws, cudaFuncAttributeMaxDynamicSharedMemorySize, P.total));
+  int nsm = 152;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);
+  const int grid = k->nclass < nsm ? k->nclass : nsm;
+  k_contract_tc_adj_ws<<<grid, AW_THREADS, P.total, st>>>(cmap, wmap, P, k->d_members, k->nclass, nvol, vout, ld_out,
+                                                          out_vstride, k->d_flags, k->max_polls);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
 }  // namespace
 
 ctof_status contract_tc_forward(const ctof_kernel_s* k, int nvol, const float2* in_z, float2* out_t,
@@ -524,6 +869,9 @@ ctof_status contract_tc_forward(const ctof_kernel_s* k, int nvol, const float2* 
 ctof_status contract_tc_adjoint(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z,
                                 cudaStream_t st) {
   if (nvol < 1) return CTOF_EINVAL;
+  const ctof_status s =
+      launch_adj_ws(k, nvol, in_t, k->ldt, (size_t)k->nf * k->ldt, out_z, k->ldz, (size_t)k->nf * k->ldz, st);
+  if (s != CTOF_EUNSUPPORTED) return s;
   return launch_tc(k_contract_tc_adj, plan_adj(k->nt, k->nz), k, nvol, in_t, k->ldt, (size_t)k->nf * k->ldt, out_z,
                    k->ldz, (size_t)k->nf * k->ldz, st);
 }
@@ -538,6 +886,8 @@ ctof_status contract_tc_forward_zb(const ctof_kernel_s* k, int nvol, const float
 ctof_status contract_tc_adjoint_zb(const ctof_kernel_s* k, int nvol, const float2* in_t, float2* out_z, int ldzb,
                                    cudaStream_t st) {
   if (nvol < 1 || (k->nz & 1) || (ldzb & 7) || ldzb < nvol * k->nz) return CTOF_EINVAL;
+  const ctof_status s = launch_adj_ws(k, nvol, in_t, k->ldt, (size_t)k->nf * k->ldt, out_z, ldzb, (size_t)k->nz, st);
+  if (s != CTOF_EUNSUPPORTED) return s;
   return launch_tc(k_contract_tc_adj, plan_adj(k->nt, k->nz), k, nvol, in_t, k->ldt, (size_t)k->nf * k->ldt, out_z,
                    ldzb, (size_t)k->nz, st);
 }
