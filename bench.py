@@ -582,17 +582,13 @@ def learned_comparison(cfg, count, warmup, batch=None, kern=None):
     ms = torch.stack([m for m, _ in data])
     outs = torch.empty((len(data), cfg["nz"], cfg["n"], cfg["n"]), device="cuda")
     res = torch.empty(len(data), device="cuda", dtype=torch.float64)
-    m_norm = torch.stack([m.double().norm() for m, _ in data])
-    pred = torch.empty((cfg["nt"], cfg["n"], cfg["n"]), device="cuda")
     lb = batch or count
 
     def learned_pass(lo, hi):
+        # the solver and its data-residual check in one call per batch
         for c in range(lo, hi, lb):
             e = min(hi, c + lb)
-            net.reconstruct(kern, ms[c:e], out=outs[c:e])
-        for i in range(lo, hi):
-            kern.forward(outs[i], out=pred)
-            res[i] = (pred.double() - ms[i].double()).norm() / m_norm[i]
+            net.reconstruct_checked(kern, ms[c:e], out=outs[c:e], res=res[c:e])
         r = res[lo:hi].cpu()
         fb = [lo + j for j in range(hi - lo) if not (float(r[j]) <= threshold)]
         for i in fb:

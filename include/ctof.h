@@ -308,6 +308,16 @@ ctof_status ctof_learned_train_step(ctof_learned net, ctof_kernel k, int batch, 
  * d_m [batch][nt][n][n] -> d_mu [batch][nz][n][n].  Asynchronous. */
 ctof_status ctof_learned_reconstruct(ctof_learned net, ctof_kernel k, int batch, const float* d_m,
                                      float* d_mu, void* stream);
+/* Inference followed by the data-residual check that decides the ADMM
+ * fallback: d_res[b] (device, batch doubles) = ||A mu_b - m_b||_2 / ||m_b||_2
+ * with A the forward operator of Eq. 11 (m_b = 0 gives 0 for A mu_b = 0, else
+ * +inf).  The check adds one batched forward contraction and, per member, one
+ * inverse transform of the time planes that compares with m_b as it goes;
+ * sums in FP64 of the FP32 values.  Asynchronous; the caller reads d_res and
+ * reconstructs the members above its threshold another way (ctof_reconstruct).
+ * Errors as ctof_learned_reconstruct, EINVAL for a null d_res. */
+ctof_status ctof_learned_reconstruct_checked(ctof_learned net, ctof_kernel k, int batch, const float* d_m,
+                                             float* d_mu, double* d_res, void* stream);
 
 /* Batching form: ADMM reconstructions of `count` independent problems of
  * uneven sizes and optics (one handle each, distinct handles), d_m[i] ->

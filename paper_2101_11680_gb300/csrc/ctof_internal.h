@@ -171,6 +171,13 @@ ctof_status fft_rows_inverse(const ctof_kernel_s* k, const float2* inter, int np
 // the correction c, in place in `inter` ([nt][n][hp]).
 ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* m, float* u1,
                             float inv_scale, float rho, cudaStream_t st);
+// Learned-solver T side, in place on inter [n][kx][nt planes]: inverse rows,
+// crop to the scan, c = Kx - m (Kx when m is null), forward rows of c.
+ctof_status fft_rows_resid_t(const ctof_kernel_s* k, float2* inter, const float* m, cudaStream_t st);
+// Inverse rows without a store: acc[0] += sum (z - ref)^2, acc[1] += sum ref^2
+// over the first cols_out columns (ref laid out like fft_rows_inverse's out).
+ctof_status fft_rows_inverse_norm(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows, int cols_out,
+                                  const float* ref, int ld_ref, double* acc, cudaStream_t st);
 
 // ---- contract.cu --------------------------------------------------------
 // shared memory the contraction kernels need at this size (single-buffered worst case)

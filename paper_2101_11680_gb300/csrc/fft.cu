@@ -520,13 +520,16 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_fwd(const __grid_consta
 }
 
 // Inverse C2R of rows: inter[row][kx][plane] (tensor map `src`) ->
-// out[plane][row][ld_out] (first cols_out columns), x scale.
-template <int P>
+// out[plane][row][ld_out] (first cols_out columns), x scale.  With NORM
+// nothing is stored: `out` is read as a reference y of the same layout and
+// the block adds sum (scale z - y)^2 and sum y^2 over the kept columns to
+// acc[0] and acc[1].
+template <int P, bool NORM>
 __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const __grid_constant__ CUtensorMap src, int nplanes,
                                                              int rows, int cols_out, float* __restrict__ out,
                                                              int ld_out, float scale,
                                                              const float2* __restrict__ tw, int* __restrict__ flag,
-                                                             long long max_polls) {
+                                                             long long max_polls, double* __restrict__ acc) {
   constexpr int R = P / 32;
   extern __shared__ float4 row_smem4[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -537,6 +540,7 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const __grid_consta
     const int r = job / nblk;
     row_load_issue<P>(S.bar + (it & 1), sh_buf<P>(S, it & 1), &src, r, (job - r * nblk) * RP);
   };
+  float sr = 0.f, sy = 0.f;  // NORM partial sums of this lane
   if (threadIdx.x == 0 && (int)blockIdx.x < njobs) issue(blockIdx.x, 0);
   int it = 0;
   for (int job = blockIdx.x; job < njobs; job += gridDim.x, ++it) {
@@ -554,11 +558,36 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const __grid_consta
     row_transform<P, true>(v, lane, S);
     for (int c = lane; c < cols_out; c += 32) {
       const float2 z = S.buf[row_pos<P>(c)];
-      if (p0 < nplanes) out[((size_t)p0 * rows + r) * ld_out + c] = z.x * scale;
-      if (p1 < nplanes) out[((size_t)p1 * rows + r) * ld_out + c] = z.y * scale;
+      const size_t o0 = ((size_t)p0 * rows + r) * ld_out + c, o1 = ((size_t)p1 * rows + r) * ld_out + c;
+      if constexpr (NORM) {
+        if (p0 < nplanes) {
+          const float y = out[o0], d = z.x * scale - y;
+          sr = fmaf(d, d, sr);
+          sy = fmaf(y, y, sy);
+        }
+        if (p1 < nplanes) {
+          const float y = out[o1], d = z.y * scale - y;
+          sr = fmaf(d, d, sr);
+          sy = fmaf(y, y, sy);
+        }
+      } else {
+        if (p0 < nplanes) out[o0] = z.x * scale;
+        if (p1 < nplanes) out[o1] = z.y * scale;
+      }
     }
     bulk::fence_smem();  // this job's reads of its buffer, before later copies overwrite it
     __syncthreads();
+  }
+  if constexpr (NORM) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      sr += __shfl_xor_sync(0xffffffffu, sr, o);
+      sy += __shfl_xor_sync(0xffffffffu, sy, o);
+    }
+    if (lane == 0) {
+      atomicAdd(acc, (double)sr);
+      atomicAdd(acc + 1, (double)sy);
+    }
   }
 }
 
@@ -568,11 +597,13 @@ __global__ void __launch_bounds__(ROW_WARPS * 32) k_rows_inv(const __grid_consta
 //   c    = (v1 - u1) - Kx = 2 v1 - a1 - Kx      (zero off the scan)
 //   row spectra <- R2C(c zero-padded to P)
 // so that FFT(v1 - u1) = K x_hat + c_hat without a transform of the full
-// P x P plane.  m, u1: [nt][n][n]; inter: [n][kx][plane] in place (tensor
-// map `map`).  The m and u1 values of a lane are loaded before its tile is
-// waited for; the next job's tile is requested once the copy out of its
-// buffer has read it.
-template <int P>
+// P x P plane.  With RESID the update is the data residual of the gradient
+// A^T (A x - m) instead: c = Kx - m on the scan (Kx alone when m is null;
+// u1, inv_s and rho unused).  m, u1: [nt][n][n]; inter: [n][kx][plane] in
+// place (tensor map `map`).  The m and u1 values of a lane are loaded before
+// its tile is waited for; the next job's tile is requested once the copy out
+// of its buffer has read it.
+template <int P, bool RESID>
 __global__ void __launch_bounds__(ROW_WARPS * 32, P >= 512 ? 2 : 3)
     k_rows_admm_t(const __grid_constant__ CUtensorMap map, int nplanes, int n, const float* __restrict__ m,
                   float* __restrict__ u1, float scale, float inv_s, float rho, const float2* __restrict__ tw,
@@ -602,13 +633,20 @@ __global__ void __launch_bounds__(ROW_WARPS * 32, P >= 512 ? 2 : 3)
     for (int i = 0; i < RN; ++i) {
       const int c = lane + 32 * i;
       mv0[i] = uv0[i] = mv1[i] = uv1[i] = 0.f;
-      if (c < n && has0) {
-        mv0[i] = m[row0 + c];
-        uv0[i] = u1[row0 + c];
-      }
-      if (c < n && has1) {
-        mv1[i] = m[row1 + c];
-        uv1[i] = u1[row1 + c];
+      if constexpr (RESID) {
+        if (m != nullptr && c < n) {
+          if (has0) mv0[i] = m[row0 + c];
+          if (has1) mv1[i] = m[row1 + c];
+        }
+      } else {
+        if (c < n && has0) {
+          mv0[i] = m[row0 + c];
+          uv0[i] = u1[row0 + c];
+        }
+        if (c < n && has1) {
+          mv1[i] = m[row1 + c];
+          uv1[i] = u1[row1 + c];
+        }
       }
     }
     if (!row_wait(S.bar + (it & 1), it, flag, max_polls)) {
@@ -629,6 +667,11 @@ __global__ void __launch_bounds__(ROW_WARPS * 32, P >= 512 ? 2 : 3)
       const int c = lane + 32 * i;
       if (c < n) {
         const float2 kx = cscale(S.buf[row_pos<P>(c)], scale);
+        if constexpr (RESID) {
+          if (has0) v[i].x = kx.x - mv0[i];
+          if (has1) v[i].y = kx.y - mv1[i];
+          continue;
+        }
         if (has0) {
           const float a1 = kx.x + uv0[i];
           const float v1 = (mv0[i] * inv_s + rho * a1) * inv1r;
@@ -916,9 +959,26 @@ ctof_status fft_rows_inverse(const ctof_kernel_s* k, const float2* inter, int np
   const size_t sm = row_smem_bytes(k->p);
   const float scale = 1.0f / ((float)k->p * (float)k->p);
   CTOF_P_SWITCH(k->p, {
-    CTOF_CUDA_TRY(allow_smem(k_rows_inv<P_>, sm));
-    k_rows_inv<P_><<<row_grid(rows, nplanes), ROW_WARPS * 32, sm, st>>>(map, nplanes, rows, cols_out, out, ld_out,
-                                                                         scale, k->d_tw, k->d_flags, k->max_polls);
+    CTOF_CUDA_TRY(allow_smem(k_rows_inv<P_, false>, sm));
+    k_rows_inv<P_, false><<<row_grid(rows, nplanes), ROW_WARPS * 32, sm, st>>>(
+        map, nplanes, rows, cols_out, out, ld_out, scale, k->d_tw, k->d_flags, k->max_polls, nullptr);
+  });
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status fft_rows_inverse_norm(const ctof_kernel_s* k, const float2* inter, int nplanes, int rows, int cols_out,
+                                  const float* ref, int ld_ref, double* acc, cudaStream_t st) {
+  if (nplanes <= 0 || rows <= 0) return CTOF_OK;
+  CUtensorMap map;
+  CTOF_TRY(row_map(k, &map, inter, nplanes, rows));
+  const size_t sm = row_smem_bytes(k->p);
+  const float scale = 1.0f / ((float)k->p * (float)k->p);
+  CTOF_P_SWITCH(k->p, {
+    CTOF_CUDA_TRY(allow_smem(k_rows_inv<P_, true>, sm));
+    k_rows_inv<P_, true><<<row_grid(rows, nplanes), ROW_WARPS * 32, sm, st>>>(
+        map, nplanes, rows, cols_out, const_cast<float*>(ref), ld_ref, scale, k->d_tw, k->d_flags, k->max_polls,
+        acc);
   });
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;
@@ -931,9 +991,23 @@ ctof_status fft_rows_admm_t(const ctof_kernel_s* k, float2* inter, const float* 
   const size_t sm = row_smem_bytes(k->p);
   const float scale = 1.0f / ((float)k->p * (float)k->p);
   CTOF_P_SWITCH(k->p, {
-    CTOF_CUDA_TRY(allow_smem(k_rows_admm_t<P_>, sm));
-    k_rows_admm_t<P_><<<row_grid(k->n, k->nt), ROW_WARPS * 32, sm, st>>>(map, k->nt, k->n, m, u1, scale, inv_scale,
-                                                                          rho, k->d_tw, k->d_flags, k->max_polls);
+    CTOF_CUDA_TRY(allow_smem(k_rows_admm_t<P_, false>, sm));
+    k_rows_admm_t<P_, false><<<row_grid(k->n, k->nt), ROW_WARPS * 32, sm, st>>>(
+        map, k->nt, k->n, m, u1, scale, inv_scale, rho, k->d_tw, k->d_flags, k->max_polls);
+  });
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
+}
+
+ctof_status fft_rows_resid_t(const ctof_kernel_s* k, float2* inter, const float* m, cudaStream_t st) {
+  CUtensorMap map;
+  CTOF_TRY(row_map(k, &map, inter, k->nt, k->n));
+  const size_t sm = row_smem_bytes(k->p);
+  const float scale = 1.0f / ((float)k->p * (float)k->p);
+  CTOF_P_SWITCH(k->p, {
+    CTOF_CUDA_TRY(allow_smem(k_rows_admm_t<P_, true>, sm));
+    k_rows_admm_t<P_, true><<<row_grid(k->n, k->nt), ROW_WARPS * 32, sm, st>>>(
+        map, k->nt, k->n, m, nullptr, scale, 0.f, 0.f, k->d_tw, k->d_flags, k->max_polls);
   });
   CTOF_CUDA_TRY(cudaGetLastError());
   return CTOF_OK;

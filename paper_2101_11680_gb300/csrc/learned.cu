@@ -686,6 +686,15 @@ __global__ void k_sub4(float4* __restrict__ a, const float4* __restrict__ b, lon
   }
 }
 
+// res[b] = sqrt(acc[2b] / acc[2b + 1]); a zero reference gives 0 for a zero
+// residual and +inf otherwise.
+__global__ void k_ratio_sqrt(const double* __restrict__ acc, int n, double* __restrict__ res) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  if (b >= n) return;
+  const double r2 = acc[2 * b], m2 = acc[2 * b + 1];
+  res[b] = m2 > 0.0 ? sqrt(r2 / m2) : (r2 > 0.0 ? (double)INFINITY : 0.0);
+}
+
 // r = (x - mu)/mu0; loss partial sums; gx = 2 r / (mu0 * ntot)
 __global__ void k_loss(const float* __restrict__ x, const float* __restrict__ mu, long long n, float* __restrict__ gx,
                        double* __restrict__ loss_sum) {
@@ -815,7 +824,8 @@ ctof_status learned_prep(ctof_learned_s* L, cudaStream_t st) {
 }
 
 struct Ws {
-  float *x, *tmpT, *gx, *gz, *h;
+  float *x, *gx, *gz, *h;
+  double* acc;                  // [batch][2] data-residual sums
   float *z, *g;                 // [S][V]
   __nv_bfloat16 *u, *y1, *y2, *y3;  // [S][V][16]
   __nv_bfloat16 *da, *db_;  // [V][16]
@@ -830,7 +840,6 @@ struct Ws {
 
 ctof_status learned_workspace(ctof_learned_s* L, const ctof_kernel_s* k, int batch, bool train, Ws* w) {
   const long long V = (long long)batch * k->nz * k->n * k->n;
-  const long long T = (long long)batch * k->nt * k->n * k->n;
   const int S = train ? L->stages : 1;
   const long long rows = (long long)batch * k->nz * k->n;
   const int nblk = (int)((rows + WG_ROWS - 1) / WG_ROWS);
@@ -840,7 +849,7 @@ ctof_status learned_workspace(ctof_learned_s* L, const ctof_kernel_s* k, int bat
     need += (b + 255) & ~(size_t)255;
     return at;
   };
-  const size_t o_x = add(V * 4), o_t = add(T * 4), o_gx = add(V * 4), o_gz = add(V * 4), o_h = add(V * 4);
+  const size_t o_x = add(V * 4), o_acc = add((size_t)batch * 2 * 8), o_gx = add(V * 4), o_gz = add(V * 4), o_h = add(V * 4);
   const size_t o_z = add((size_t)S * V * 4), o_g = add((size_t)S * V * 4);
   const size_t o_u = add((size_t)S * V * CH * 2), o_y1 = add((size_t)S * V * CH * 2), o_y2 = add((size_t)S * V * CH * 2),
                o_y3 = add((size_t)S * V * CH * 2);
@@ -861,7 +870,7 @@ ctof_status learned_workspace(ctof_learned_s* L, const ctof_kernel_s* k, int bat
   }
   char* b = static_cast<char*>(L->d_ws);
   w->x = reinterpret_cast<float*>(b + o_x);
-  w->tmpT = reinterpret_cast<float*>(b + o_t);
+  w->acc = reinterpret_cast<double*>(b + o_acc);
   w->gx = reinterpret_cast<float*>(b + o_gx);
   w->gz = reinterpret_cast<float*>(b + o_gz);
   w->h = reinterpret_cast<float*>(b + o_h);
@@ -976,33 +985,28 @@ ctof_status wgrad(const __nv_bfloat16* dy, const __nv_bfloat16* x, int relu_in, 
   return CTOF_OK;
 }
 
-// Operator applications for the whole batch: per-volume lateral FFTs, one
-// contraction launch per direction that reads W_hat once for all volumes.
-ctof_status op_forward(ctof_kernel_s* k, int batch, const float* x, float* meas, const Ws& w, cudaStream_t st) {
-  const size_t vol = (size_t)k->nz * k->n * k->n, mt = (size_t)k->nt * k->n * k->n;
-  const size_t sz = (size_t)k->nf * k->ldz, stt = (size_t)k->nf * k->ldt;
+// Operator applications for the whole batch: one contraction launch per
+// direction that reads W_hat once for all volumes; lateral FFTs of the depth
+// planes as one plane-batched transform (w.inter_zb) or per volume, of the
+// time planes per volume.
+
+// T-side spectra of A x for every batch member: w.spec_t [batch][nf][ldt].
+ctof_status spectra_forward(ctof_kernel_s* k, int batch, const float* x, const Ws& w, cudaStream_t st) {
+  const size_t vol = (size_t)k->nz * k->n * k->n, sz = (size_t)k->nf * k->ldz;
   if (w.inter_zb) {  // all volumes' depth planes as one transform
     CTOF_TRY(fft_forward_planes(k, x, batch * k->nz, k->n, k->n, k->n, w.inter_zb, w.spec_z, w.ldzb, st));
-    CTOF_TRY(contract_tc_forward_zb(k, batch, w.spec_z, w.ldzb, w.spec_t, st));
-  } else {
-    for (int b = 0; b < batch; ++b)
-      CTOF_TRY(fft_forward_planes(k, x + b * vol, k->nz, k->n, k->n, k->n, k->d_inter_z, w.spec_z + b * sz, k->ldz,
-                                  st));
-    CTOF_TRY(contract_forward_batch(k, batch, w.spec_z, w.spec_t, st));
+    return contract_tc_forward_zb(k, batch, w.spec_z, w.ldzb, w.spec_t, st);
   }
   for (int b = 0; b < batch; ++b)
-    CTOF_TRY(fft_inverse_planes(k, w.spec_t + b * stt, k->ldt, k->nt, k->n, k->n, k->d_inter_t, meas + b * mt, k->n,
-                                st));
-  return CTOF_OK;
+    CTOF_TRY(fft_forward_planes(k, x + b * vol, k->nz, k->n, k->n, k->n, k->d_inter_z, w.spec_z + b * sz, k->ldz, st));
+  return contract_forward_batch(k, batch, w.spec_z, w.spec_t, st);
 }
 
-// out = A^T r (tik_hinv null) or the Tikhonov solve T r = (G + lambda I)^-1 W^T r (per frequency)
-ctof_status op_adjoint(ctof_kernel_s* k, int batch, const float* r, float* out, const float* tik_hinv, const Ws& w,
-                       cudaStream_t st) {
-  const size_t vol = (size_t)k->nz * k->n * k->n, mt = (size_t)k->nt * k->n * k->n;
-  const size_t sz = (size_t)k->nf * k->ldz, stt = (size_t)k->nf * k->ldt;
-  for (int b = 0; b < batch; ++b)
-    CTOF_TRY(fft_forward_planes(k, r + b * mt, k->nt, k->n, k->n, k->n, k->d_inter_t, w.spec_t + b * stt, k->ldt, st));
+// out = A^T r (tik_hinv null) or the Tikhonov solve T r = (G + lambda I)^-1 W^T r
+// (per frequency), from the T-side spectra of r in w.spec_t.
+ctof_status spectra_adjoint(ctof_kernel_s* k, int batch, float* out, const float* tik_hinv, const Ws& w,
+                            cudaStream_t st) {
+  const size_t vol = (size_t)k->nz * k->n * k->n, sz = (size_t)k->nf * k->ldz;
   if (w.inter_zb) {  // all volumes' depth planes as one transform
     if (tik_hinv)
       CTOF_TRY(contract_tikhonov_zb(k, batch, tik_hinv, w.spec_t, w.spec_z, w.ldzb, st));
@@ -1020,15 +1024,48 @@ ctof_status op_adjoint(ctof_kernel_s* k, int batch, const float* r, float* out, 
   return CTOF_OK;
 }
 
-// g_raw = A^T (A x - m) for every batch member (unnormalised operator; m may be null)
-ctof_status normal_residual(ctof_kernel_s* k, int batch, const float* x, const float* m, float* out, const Ws& w,
-                            cudaStream_t st) {
-  CTOF_TRY(op_forward(k, batch, x, w.tmpT, w, st));
-  if (m) {
-    const long long mt = (long long)batch * k->nt * k->n * k->n;
-    CTOF_CUDA_TRY(sub_inplace(w.tmpT, m, mt, st));
+// out = A^T r or T r for measurements r [batch][nt][n][n].
+ctof_status op_adjoint(ctof_kernel_s* k, int batch, const float* r, float* out, const float* tik_hinv, const Ws& w,
+                       cudaStream_t st) {
+  const size_t mt = (size_t)k->nt * k->n * k->n, stt = (size_t)k->nf * k->ldt;
+  for (int b = 0; b < batch; ++b)
+    CTOF_TRY(fft_forward_planes(k, r + b * mt, k->nt, k->n, k->n, k->n, k->d_inter_t, w.spec_t + b * stt, k->ldt, st));
+  return spectra_adjoint(k, batch, out, tik_hinv, w, st);
+}
+
+// out = A^T (A x - m) (tik_hinv null) or T (A x - m), unnormalised operator, m
+// may be null.  The residual never exists in the measurement domain: each
+// volume's T side is one inverse column pass of the spectra of A x, one row
+// pass that transforms back, crops to the scan, subtracts m and transforms
+// forward again, and one forward column pass (Eq. 11 and its adjoint).
+ctof_status residual_back(ctof_kernel_s* k, int batch, const float* x, const float* m, float* out,
+                          const float* tik_hinv, const Ws& w, cudaStream_t st) {
+  const size_t mt = (size_t)k->nt * k->n * k->n, stt = (size_t)k->nf * k->ldt;
+  CTOF_TRY(spectra_forward(k, batch, x, w, st));
+  for (int b = 0; b < batch; ++b) {
+    float2* spec = w.spec_t + b * stt;
+    CTOF_TRY(fft_cols_inverse(k, spec, k->ldt, k->nt, k->n, k->d_inter_t, st));
+    CTOF_TRY(fft_rows_resid_t(k, k->d_inter_t, m ? m + b * mt : nullptr, st));
+    CTOF_TRY(fft_cols_forward(k, k->d_inter_t, k->nt, k->n, spec, k->ldt, st));
   }
-  return op_adjoint(k, batch, w.tmpT, out, nullptr, w, st);
+  return spectra_adjoint(k, batch, out, tik_hinv, w, st);
+}
+
+// Relative data residuals res[b] = ||A x_b - m_b|| / ||m_b|| (FP64 sums of the
+// FP32 values), the spectra of A x transformed back one volume at a time and
+// compared with m inside the row pass.
+ctof_status data_residuals(ctof_kernel_s* k, int batch, const float* x, const float* m, double* res, const Ws& w,
+                           cudaStream_t st) {
+  const size_t mt = (size_t)k->nt * k->n * k->n, stt = (size_t)k->nf * k->ldt;
+  CTOF_CUDA_TRY(cudaMemsetAsync(w.acc, 0, (size_t)batch * 2 * sizeof(double), st));
+  CTOF_TRY(spectra_forward(k, batch, x, w, st));
+  for (int b = 0; b < batch; ++b) {
+    CTOF_TRY(fft_cols_inverse(k, w.spec_t + b * stt, k->ldt, k->nt, k->n, k->d_inter_t, st));
+    CTOF_TRY(fft_rows_inverse_norm(k, k->d_inter_t, k->nt, k->n, k->n, m + b * mt, k->n, w.acc + 2 * b, st));
+  }
+  k_ratio_sqrt<<<(batch + 127) / 128, 128, 0, st>>>(w.acc, batch, res);
+  CTOF_CUDA_TRY(cudaGetLastError());
+  return CTOF_OK;
 }
 
 // Forward pass of the unrolled solver; with `train` every stage's activations are kept.
@@ -1055,7 +1092,7 @@ ctof_status unrolled_forward(ctof_learned_s* L, ctof_kernel_s* k, int batch, con
     __nv_bfloat16* y1 = w.y1 + (size_t)j * V * CH;
     __nv_bfloat16* y2 = w.y2 + (size_t)j * V * CH;
     __nv_bfloat16* y3 = w.y3 + (size_t)j * V * CH;
-    CTOF_TRY(normal_residual(k, batch, w.x, m, g, w, st));
+    CTOF_TRY(residual_back(k, batch, w.x, m, g, nullptr, w, st));
     k_zstep<<<grid_for(V), 256, 0, st>>>(w.x, g, eta, s, inv_s2, V, z);
     CTOF_CUDA_TRY(cudaGetLastError());
     if (train) {  // the backward pass needs the network input u
@@ -1084,11 +1121,8 @@ ctof_status unrolled_forward(ctof_learned_s* L, ctof_kernel_s* k, int batch, con
     // x <- x - T(A x - m): the residual goes through the Tikhonov solve into w.h
     const float* hinv = nullptr;
     CTOF_TRY(tikhonov_inverse(k, L->opt.dc_lambda_rel * k->gram_max, &hinv, st));
-    const long long mt = (long long)batch * k->nt * k->n * k->n;
     for (int d = 0; d < L->opt.dc_steps; ++d) {
-      CTOF_TRY(op_forward(k, batch, w.x, w.tmpT, w, st));
-      CTOF_CUDA_TRY(sub_inplace(w.tmpT, m, mt, st));
-      CTOF_TRY(op_adjoint(k, batch, w.tmpT, w.h, hinv, w, st));
+      CTOF_TRY(residual_back(k, batch, w.x, m, w.h, hinv, w, st));
       CTOF_CUDA_TRY(sub_inplace(w.x, w.h, V, st));
     }
   }
@@ -1136,7 +1170,7 @@ ctof_status unrolled_backward(ctof_learned_s* L, ctof_kernel_s* k, int batch, co
     // cur holds dL/du (channel 0); z = x - eta g,  g = A_n^T (A_n x - m_n)
     k_gz<<<grid_for(V) < 304 ? grid_for(V) : 304, 256, 0, st>>>(w.gx, cur, g, V, w.gz, deta, s);
     CTOF_CUDA_TRY(cudaGetLastError());
-    CTOF_TRY(normal_residual(k, batch, w.gz, nullptr, w.h, w, st));
+    CTOF_TRY(residual_back(k, batch, w.gz, nullptr, w.h, nullptr, w, st));
     k_gx<<<grid_for(V), 256, 0, st>>>(w.gz, w.h, eta, s, inv_s2, V, w.gx);
     CTOF_CUDA_TRY(cudaGetLastError());
   }
@@ -1293,6 +1327,22 @@ ctof_status ctof_learned_reconstruct(ctof_learned L, ctof_kernel k, int batch, c
   Ws w;
   CTOF_TRY(learned_workspace(L, k, batch, false, &w));
   CTOF_TRY(unrolled_forward(L, k, batch, d_m, w, false, st));
+  CTOF_CUDA_TRY(cudaMemcpyAsync(d_mu, w.x, (size_t)batch * k->nz * k->n * k->n * 4, cudaMemcpyDeviceToDevice, st));
+  return CTOF_OK;
+}
+
+ctof_status ctof_learned_reconstruct_checked(ctof_learned L, ctof_kernel k, int batch, const float* d_m,
+                                             float* d_mu, double* d_res, void* stream) {
+  if (!L || !k || !d_m || !d_mu || !d_res || batch < 1) return CTOF_EINVAL;
+  CTOF_TRY(check_geometry(k));
+  if (L->device != k->device) return CTOF_EINVAL;
+  DeviceGuard dg(k->device);
+  if (!dg.ok) return CTOF_ECUDA;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  Ws w;
+  CTOF_TRY(learned_workspace(L, k, batch, false, &w));
+  CTOF_TRY(unrolled_forward(L, k, batch, d_m, w, false, st));
+  CTOF_TRY(data_residuals(k, batch, w.x, d_m, d_res, w, st));
   CTOF_CUDA_TRY(cudaMemcpyAsync(d_mu, w.x, (size_t)batch * k->nz * k->n * k->n * 4, cudaMemcpyDeviceToDevice, st));
   return CTOF_OK;
 }

@@ -110,6 +110,7 @@ _SIGNATURES = {
     "ctof_learned_train_step": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, ctypes.c_double,
                                                ctypes.POINTER(ctypes.c_double), _P]),
     "ctof_learned_reconstruct": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P]),
+    "ctof_learned_reconstruct_checked": (ctypes.c_int, [_P, _P, ctypes.c_int, _P, _P, _P, _P]),
     "ctof_kernel_get_tuning": (ctypes.c_int, [_P, _P]),
     "ctof_set_timing": (ctypes.c_int, [_P, ctypes.c_int]),
     "ctof_set_wait_limit": (ctypes.c_int, [_P, ctypes.c_longlong]),
@@ -256,6 +257,24 @@ class Learned:
             self._h, kernel._h, b, _dev_ptr(m, (b,) + kernel._meas_shape(), "m"),
             _dev_ptr(out, (b,) + kernel._vol_shape(), "out"), _stream_handle(stream)), "ctof_learned_reconstruct")
         return out
+
+    def reconstruct_checked(self, kernel, m, out=None, res=None, stream=None):
+        """Inference plus each member's relative data residual ||A mu - m|| / ||m||
+        (float64 CUDA tensor [batch]); returns (out, res)."""
+        import torch
+        b = int(m.shape[0])
+        if out is None:
+            out = torch.empty((b,) + kernel._vol_shape(), device=m.device, dtype=torch.float32)
+        if res is None:
+            res = torch.empty(b, device=m.device, dtype=torch.float64)
+        if (not isinstance(res, torch.Tensor) or not res.is_cuda or res.dtype != torch.float64
+                or not res.is_contiguous() or tuple(res.shape) != (b,)):
+            raise TypeError("res must be a contiguous float64 CUDA tensor of shape (batch,)")
+        _check(self._lib.ctof_learned_reconstruct_checked(
+            self._h, kernel._h, b, _dev_ptr(m, (b,) + kernel._meas_shape(), "m"),
+            _dev_ptr(out, (b,) + kernel._vol_shape(), "out"), ctypes.c_void_p(res.data_ptr()),
+            _stream_handle(stream)), "ctof_learned_reconstruct_checked")
+        return out, res
 
 
 def reconstruct_batch(kernels, ms, params, outs=None, stream=None):

@@ -195,6 +195,40 @@ def test_learned_batch_of_five_matches_oracle():
     net.close()
 
 
+@pytest.mark.parametrize("batch", [1, 5])
+def test_learned_reconstruct_checked_residuals(batch):
+    """ctof_learned_reconstruct_checked: the volumes equal ctof_learned_reconstruct's,
+    and each member's ||A mu - m|| / ||m|| matches the FP64 oracle's forward operator
+    (Eq. 11) applied to the returned volume, to 1e-4 relative (the device forms
+    A mu in FP32; the residual is a tenth of ||m|| or more, so its FP32 error stays
+    near 1e-5).  An all-zero measurement gives +inf when the oracle's A mu is
+    non-zero (the network's biases make it so)."""
+    k = device_kernel(CASE)
+    g, _, wh = oracle_kernel(CASE)
+    theta = _on_bf16_grid(_params(28))
+    net = ctof.Learned(STAGES, theta, x0_lambda_rel=1e-3, dc_steps=1, dc_lambda_rel=1e-4)
+    ms = [_problem(900 + i)[1] for i in range(batch)]
+    if batch > 1:
+        ms[-1] = np.zeros_like(ms[-1])
+    d_m = torch.tensor(np.stack(ms), dtype=torch.float32, device="cuda")
+    plain = net.reconstruct(k, d_m)
+    got, res = net.reconstruct_checked(k, d_m)
+    torch.cuda.synchronize()
+    assert torch.equal(got, plain)
+    x = got.cpu().numpy().astype(np.float64)
+    res = res.cpu().numpy()
+    for b, m in enumerate(ms):
+        r = np.linalg.norm(op.forward_fft(wh, x[b], g) - m)
+        if np.linalg.norm(m) == 0.0:
+            assert r > 0.0 and np.isinf(res[b]), (b, res[b])
+        else:
+            want = r / np.linalg.norm(m)
+            assert abs(res[b] - want) <= 1e-4 * want, (b, res[b], want)
+    with pytest.raises(TypeError):
+        net.reconstruct_checked(k, d_m, res=torch.empty(batch, device="cuda", dtype=torch.float32))
+    net.close()
+
+
 def test_trained_network_gains_over_untrained_and_admm():
     """The shipped parameters, on held-out seeded phantoms at the training geometry
     (64 x 64 scan at 0.5 mm, 48 depths, 256 bins of 25 ps, Poisson peak 1e5): the
