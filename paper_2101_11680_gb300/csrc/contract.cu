@@ -307,41 +307,68 @@ constexpr size_t SMEM_LIMIT = 227 * 1024;
 // In-place application of the per-class Tikhonov inverse to batched adjoint
 // results: x[v][f][i] = sum_j Hinv_c[j][i] x[v][f][j] for every member f of
 // class c and volume v (Hinv symmetric, FP32, formed in FP64).  A CTA stages
-// the class's inverse and up to 16 volumes' member vectors in shared memory;
-// consecutive threads take consecutive i, so the inverse is read along its
-// rows without bank conflicts and each vector entry is a broadcast.
+// the class's inverse and up to 16 volumes' member vectors in shared memory,
+// then each thread accumulates a 4 x 4 block (4 consecutive outputs i of 4
+// member vectors) in registers: per j one 16-byte read of the inverse row and
+// four 8-byte vector reads feed 32 FMAs.  Vector rows are padded to nz + 1
+// entries so that the three vector groups a warp reads fall on distinct banks.
 constexpr int HV = 16;  // volumes per staged chunk
 
-__global__ void __launch_bounds__(256) k_apply_hinv(const float* __restrict__ hinv, const int* __restrict__ members,
-                                                    int nclass, int nz, int z4, int nvol, float2* __restrict__ x,
-                                                    int ldz, size_t vstride) {
+__global__ void __launch_bounds__(256, 4) k_apply_hinv(const float* __restrict__ hinv,
+                                                       const int* __restrict__ members, int nclass, int nz, int z4,
+                                                       int nvol, float2* __restrict__ x, int ldz, size_t vstride) {
   extern __shared__ __align__(16) float hsm[];
-  float* sH = hsm;                                          // [nz][z4]
-  float2* sV = reinterpret_cast<float2*>(hsm + nz * z4);    // [HV * 4][nz]
+  const int nzp = nz + 1;
+  float* sH = hsm;                                          // [nz][z4], columns nz..z4-1 zero
+  float2* sV = reinterpret_cast<float2*>(hsm + nz * z4);    // [HV * 4][nzp]
+  const int nig = z4 >> 2;
   for (int c = blockIdx.x; c < nclass; c += gridDim.x) {
-    int mem[4];
-#pragma unroll
-    for (int m = 0; m < 4; ++m) mem[m] = __ldg(members + 4 * c + m);
+    const int4 mem = __ldg(reinterpret_cast<const int4*>(members) + c);
+    auto member = [&](int q) { return q == 0 ? mem.x : q == 1 ? mem.y : q == 2 ? mem.z : mem.w; };
     __syncthreads();  // the previous class's reads of sH / sV are done
     for (int i = threadIdx.x; i < nz * z4; i += blockDim.x) sH[i] = __ldg(hinv + (size_t)c * nz * z4 + i);
     for (int v0 = 0; v0 < nvol; v0 += HV) {
       const int nv = nvol - v0 < HV ? nvol - v0 : HV;
-      for (int o = threadIdx.x; o < nv * 4 * nz; o += blockDim.x) {
-        const int r = o / nz, j = o - r * nz, f = mem[r & 3];
-        sV[r * nz + j] = f >= 0 ? x[(v0 + (r >> 2)) * vstride + (size_t)f * ldz + j] : make_float2(0.f, 0.f);
+      const int R = nv * 4;
+      for (int o = threadIdx.x; o < R * nz; o += blockDim.x) {
+        const int r = o / nz, j = o - r * nz, f = member(r & 3);
+        sV[r * nzp + j] = f >= 0 ? x[(v0 + (r >> 2)) * vstride + (size_t)f * ldz + j] : make_float2(0.f, 0.f);
       }
       __syncthreads();
-      for (int o = threadIdx.x; o < nv * 4 * nz; o += blockDim.x) {
-        const int r = o / nz, i = o - r * nz, f = mem[r & 3];
-        if (f < 0) continue;
-        const float2* vr = sV + r * nz;
-        float re = 0.f, im = 0.f;
+      const int ntask = nig * (R >> 2);
+      for (int t = threadIdx.x; t < ntask; t += blockDim.x) {
+        const int rg = t / nig, ig = t - rg * nig;
+        float2 acc[4][4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+#pragma unroll
+          for (int p = 0; p < 4; ++p) acc[q][p] = make_float2(0.f, 0.f);
+        const float2* v0p = sV + (4 * rg) * nzp;
+        const float* hp = sH + 4 * ig;
         for (int j = 0; j < nz; ++j) {
-          const float h = sH[j * z4 + i];
-          re = fmaf(h, vr[j].x, re);
-          im = fmaf(h, vr[j].y, im);
+          const float4 h = *reinterpret_cast<const float4*>(hp + j * z4);
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 v = v0p[q * nzp + j];
+            acc[q][0].x = fmaf(h.x, v.x, acc[q][0].x);
+            acc[q][0].y = fmaf(h.x, v.y, acc[q][0].y);
+            acc[q][1].x = fmaf(h.y, v.x, acc[q][1].x);
+            acc[q][1].y = fmaf(h.y, v.y, acc[q][1].y);
+            acc[q][2].x = fmaf(h.z, v.x, acc[q][2].x);
+            acc[q][2].y = fmaf(h.z, v.y, acc[q][2].y);
+            acc[q][3].x = fmaf(h.w, v.x, acc[q][3].x);
+            acc[q][3].y = fmaf(h.w, v.y, acc[q][3].y);
+          }
         }
-        x[(v0 + (r >> 2)) * vstride + (size_t)f * ldz + i] = make_float2(re, im);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int r = 4 * rg + q, f = member(q);  // r & 3 == q
+          if (f < 0) continue;
+          float2* xo = x + (v0 + (r >> 2)) * vstride + (size_t)f * ldz;
+#pragma unroll
+          for (int p = 0; p < 4; ++p)
+            if (4 * ig + p < nz) xo[4 * ig + p] = acc[q][p];
+        }
       }
       __syncthreads();
     }
@@ -441,7 +468,7 @@ namespace {
 ctof_status apply_hinv(const ctof_kernel_s* k, int nvol, const float* hinv, float2* x, int ld, size_t vstride,
                        cudaStream_t st) {
   const int z4 = (k->nz + 3) & ~3;
-  const size_t sm = (size_t)k->nz * z4 * 4 + (size_t)HV * 4 * k->nz * 8;
+  const size_t sm = (size_t)k->nz * z4 * 4 + (size_t)HV * 4 * (k->nz + 1) * 8;
   CTOF_CUDA_TRY(cudaFuncSetAttribute(k_apply_hinv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm));
   int nsm = 152;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, k->device);

@@ -222,45 +222,49 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d(const __nv_bfloat16* __re
 
 // ---- hidden layers at inference on tcgen05 ----
 //
-// out[v][co] = act(bias[co] + sum_tap sum_ci W[tap][co][ci] in[v + off(tap)][ci]) as
-// 27 accumulating MMAs per row of 128 output voxels along x (M = 128 voxels,
-// N = 16 output channels, K = 16 input channels; the input is stored after
-// its ReLU).  A work unit is TCV_YB output rows of one (volume, depth, x
-// segment); warp 0 (one thread) streams the unit's input rows (y - 1 .. y +
-// TCV_YB, each as its three depth planes, each plane as two 8-channel K
-// groups of 130 voxels: x0 - 1 .. x0 + 128) into a ring of TCV_RING slots by
-// tensor-map copies (zero fill outside the volume); warp 1 (one thread) issues
-// the MMAs of each output row into one of two TMEM accumulators, the three
-// x-shifted views of a staged plane being descriptor offsets of 16 bytes
-// (no-swizzle K-major layout: voxel rows 16 bytes apart, K groups TCV_KG
-// bytes apart); warps 4-7 add the bias, apply ReLU (or the fused residual
-// step x = z + mu0 bf16(out[v][0])) and store.  mbarrier hand-offs, bounded
-// waits.  Three CTAs share an SM.  Each MMA (N = 16) reads its 4 KB A tile
-// from shared memory, which bounds the kernel (~36 cycles of shared-memory
-// bandwidth per MMA); a variant that stacked the three dy taps into one
-// N = 48 operand (a third of the A reads, output rows accumulating in a
-// 32-slot TMEM ring, one CTA per SM) measured slower.
+// out[v][co] = act(bias[co] + sum_tap sum_ci W[tap][co][ci] in[v + off(tap)][ci])
+// on the tensor cores, M = 128 voxels along x, K = 16 input channels (the
+// input is stored after its ReLU).  A work unit is TCV_YB output rows of one
+// (volume, depth, x segment); warp 0 (one thread) streams the unit's input rows
+// (y0 - 1 .. y0 + TCV_YB, each as its three depth planes, each plane as two
+// 8-channel K groups of 130 voxels x0 - 1 .. x0 + 128) into a ring of TCV_RING
+// slots by tensor-map copies (zero fill outside the volume).  Warp 1 (one
+// thread) issues the MMAs input row by input row: each of the row's nine
+// (depth, x shift) A views (descriptor offsets into the staged row: voxel rows
+// 16 bytes apart, K groups TCV_KG bytes apart) is multiplied by the weights of
+// its three dy taps stacked along N, so one MMA (N = 48) feeds output rows
+// j - 2, j - 1, j of input row j, held in three consecutive accumulators of a
+// TCV_NACC-slot TMEM ring (split into two MMAs where they wrap around the
+// ring).  An M = 128, K = 16 MMA costs the same issue time for every N up to
+// about 90, so nine N = 48 MMAs per input row replace the 27 N = 16 MMAs per
+// output row of a tap-by-tap loop.  Every MMA accumulates: warps 4-7 drain an
+// accumulator (bias, ReLU or the fused residual step x = z + mu0 bf16(out[v][0]),
+// store) and zero it, and zero all slots at the start.  mbarrier hand-offs with
+// bounded waits; 96 TMEM columns, three CTAs per SM.
 constexpr int TCV_RING = 4;
 constexpr int TCV_YB = 32;
+constexpr int TCV_NACC = 6;                     // accumulator ring slots (16 columns each)
 constexpr int TCV_KG = 144 * 16;                // bytes of one K-group region (130 voxel rows, padded)
 constexpr int TCV_SLOT = 3 * 2 * TCV_KG;        // one staged input row: 3 depth planes x 2 K groups
-constexpr int TCV_WB = 27 * 512;                // weights: [tap][K group][16 co][16 bytes]
+constexpr int TCV_BT = 48 * 32;                 // bytes of one stacked weight tile (48 rows x 16 ci)
+constexpr int TCV_WB = 9 * TCV_BT;
 constexpr int TCV_THREADS = 256;
 constexpr int TCV_LOAD = 6 * 130 * 16;          // bytes landing per staged row
 constexpr size_t TCV_SMEM = 1024 + TCV_RING * TCV_SLOT + TCV_WB + 64 + 256;
 
-__host__ __device__ constexpr uint32_t tcv_idesc() {  // kind::f16: D F32, A / B BF16, N = 16, M = 128
-  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(16 >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
+__host__ __device__ constexpr uint32_t tcv_idesc(int n) {  // kind::f16: D F32, A / B BF16, M = 128
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(128 >> 4) << 24);
 }
 
-__device__ __forceinline__ void tcv_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t acc) {
+// D += A x B, both from shared memory; always accumulating.
+__device__ __forceinline__ void tcv_mma(uint32_t d, uint64_t a, uint64_t b, uint32_t idesc) {
   asm volatile(
       "{\n"
       ".reg .pred p;\n"
       "setp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
       "}\n" ::"r"(d),
-      "l"(a), "l"(b), "r"(tcv_idesc()), "r"(acc)
+      "l"(a), "l"(b), "r"(idesc), "r"(1u)
       : "memory");
 }
 
@@ -278,6 +282,22 @@ __device__ __forceinline__ bool tcv_wait(uint64_t* bar, uint32_t parity, long lo
   return false;
 }
 
+// Warp-level bounded wait: lane 0 polls, the others acquire with one poll.
+__device__ __forceinline__ bool tcv_wait_warp(uint64_t* bar, uint32_t parity, long long max_polls,
+                                              volatile int* abort_w, int* flag, int lane) {
+  int ok = 1;
+  if (lane == 0) ok = tcv_wait(bar, parity, max_polls, abort_w, flag) ? 1 : 0;
+  ok = __shfl_sync(0xffffffffu, ok, 0);
+  if (ok && lane != 0) (void)bulk::try_wait(bar, parity);
+  return ok != 0;
+}
+
+__device__ __forceinline__ void tcv_zero16(uint32_t taddr) {
+  const uint32_t zero[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+  umma::tmem_st8(taddr, zero);
+  umma::tmem_st8(taddr + 8, zero);
+}
+
 template <bool PROX>
 __global__ void __launch_bounds__(TCV_THREADS, 1)
     k_conv3d_tc(const __grid_constant__ CUtensorMap amap, const __nv_bfloat16* __restrict__ w,
@@ -293,19 +313,21 @@ __global__ void __launch_bounds__(TCV_THREADS, 1)
   unsigned char* s_w = sm + TCV_RING * TCV_SLOT;
   float* s_bias = reinterpret_cast<float*>(s_w + TCV_WB);
   uint64_t* bar = reinterpret_cast<uint64_t*>(s_bias + 16);
-  uint64_t* slot_full = bar;                 // [RING], one arrival + the copies' bytes
-  uint64_t* slot_empty = bar + TCV_RING;     // [RING], the MMAs that read the row (commit)
-  uint64_t* acc_full = bar + 2 * TCV_RING;   // [2], the row's MMAs (commit)
-  uint64_t* acc_empty = acc_full + 2;        // [2], one arrival per epilogue warp
-  uint64_t* drain_bar = acc_empty + 2;
+  uint64_t* slot_full = bar;                   // [RING], one arrival + the copies' bytes
+  uint64_t* slot_empty = bar + TCV_RING;       // [RING], the MMAs that read the row (commit)
+  uint64_t* acc_full = bar + 2 * TCV_RING;     // [NACC], the row's last MMAs (commit)
+  uint64_t* acc_empty = acc_full + TCV_NACC;   // [NACC], one arrival per epilogue warp (slot zeroed)
+  uint64_t* drain_bar = acc_empty + TCV_NACC;
   uint32_t* tslot = reinterpret_cast<uint32_t*>(drain_bar + 1);
   volatile int* abort_w = reinterpret_cast<volatile int*>(drain_bar + 2);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // weights into the canonical K-major layout of the B operand: element (co, ci)
-  // of tap t at t 512 + (ci / 8) 256 + co 16 + (ci % 8) 2
+  // stacked weights, K-major B operand of 48 rows in the 32-byte swizzle: tile
+  // (dz, dx) holds rows n = 16 blk + co with dy = 2 - blk, row n at n 32 bytes,
+  // its 16-byte half g (input channels 8 g ..) at half g ^ ((n / 4) & 1)
   for (int i = threadIdx.x; i < 27 * 16 * 2; i += TCV_THREADS) {
     const int t = i >> 5, co = (i >> 1) & 15, g = i & 1;
-    *reinterpret_cast<uint4*>(s_w + t * 512 + g * 256 + co * 16) =
+    const int dz = t / 9, dy = (t / 3) % 3, dx = t % 3, n = (2 - dy) * 16 + co;
+    *reinterpret_cast<uint4*>(s_w + (dz * 3 + dx) * TCV_BT + n * 32 + ((g ^ ((n >> 2) & 1)) << 4)) =
         *reinterpret_cast<const uint4*>(w + ((size_t)t * CH + co) * CH + 8 * g);
   }
   if (threadIdx.x < 16) s_bias[threadIdx.x] = bias ? bias[threadIdx.x] : 0.f;
@@ -314,14 +336,14 @@ __global__ void __launch_bounds__(TCV_THREADS, 1)
       bulk::bar_init(slot_full + i, 1);
       bulk::bar_init(slot_empty + i, 1);
     }
-    for (int i = 0; i < 2; ++i) {
+    for (int i = 0; i < TCV_NACC; ++i) {
       bulk::bar_init(acc_full + i, 1);
       bulk::bar_init(acc_empty + i, 4);
     }
     bulk::bar_init(drain_bar, 1);
     *abort_w = 0;
   }
-  if (warp == 0) umma::tmem_alloc(tslot, 32);
+  if (warp == 0) umma::tmem_alloc(tslot, 128);
   umma::fence_proxy_async();  // the weights, before the MMAs read them
   umma::fence_before_sync();
   __syncthreads();
@@ -369,72 +391,75 @@ __global__ void __launch_bounds__(TCV_THREADS, 1)
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
       const uint64_t a_desc0 = umma::desc(bulk::saddr(ring), TCV_KG, 128);  // slot 0, plane 0, x shift 0
-      const uint64_t b_desc0 = umma::desc(bulk::saddr(s_w), 256, 128);      // tap 0
-      int gr = 0, go = 0;  // rows waited for, output rows issued
+      // tile (0, 0) from output row j - 2; 8-row groups 256 bytes apart, 32-byte swizzle (layout 6)
+      const uint64_t b_desc0 = umma::desc(bulk::saddr(s_w), 16, 256) | (6ull << 61);
+      int gr = 0, gbase = 0;  // input rows consumed, first output row of the unit
       bool ok = true;
-      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
-        const int r0 = gr;  // this unit's first staged row
-        for (int j = 0; j < TCV_YB && ok; ++j, ++go) {
-          // rows r0 + j .. r0 + j + 2 must have landed (each waited for once)
-          while (gr <= r0 + j + 2) {
-            if (!tcv_wait(slot_full + gr % TCV_RING, (uint32_t)(gr / TCV_RING) & 1u, max_polls, abort_w, flag)) {
+      for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x, gbase += TCV_YB) {
+        for (int j = 0; j < TCV_YB + 2 && ok; ++j, ++gr) {
+          const int s = gr % TCV_RING;
+          if (j < TCV_YB) {  // output row j enters: its accumulator is drained and zeroed
+            const int gi = gbase + j;
+            if (!tcv_wait(acc_empty + gi % TCV_NACC, (uint32_t)(gi / TCV_NACC) & 1u, max_polls, abort_w, flag)) {
               ok = false;
               break;
             }
-            ++gr;
           }
-          if (!ok) break;
-          const int a = go & 1;
-          if (go >= 2 && !tcv_wait(acc_empty + a, (uint32_t)((go >> 1) + 1) & 1u, max_polls, abort_w, flag)) {
+          if (!tcv_wait(slot_full + s, (uint32_t)(gr / TCV_RING) & 1u, max_polls, abort_w, flag)) {
             ok = false;
             break;
           }
           umma::fence_after_sync();
-          // descriptors are linear in the start address (16-byte units in the low bits)
-          uint64_t arow[3];
+          const int lo = j - 2 > 0 ? j - 2 : 0, hi = j < TCV_YB - 1 ? j : TCV_YB - 1;
+          const int cnt = hi - lo + 1, s0 = (gbase + lo) % TCV_NACC;
+          const int first = cnt < TCV_NACC - s0 ? cnt : TCV_NACC - s0;
+          const uint32_t d0 = taddr + 16 * s0, id0 = tcv_idesc(16 * first);
+          const uint32_t id1 = tcv_idesc(16 * (cnt - first > 0 ? cnt - first : 1));
+          const uint64_t boff0 = (uint64_t)((512 * (lo - j + 2)) >> 4);  // 16 rows = 512 bytes
+          const uint64_t boff1 = (uint64_t)((512 * (lo + first - j + 2)) >> 4);
+          const uint64_t arow = a_desc0 + (uint64_t)((s * TCV_SLOT) >> 4);
 #pragma unroll
-          for (int dy = 0; dy < 3; ++dy)
-            arow[dy] = a_desc0 + (uint64_t)(((unsigned)(r0 + j + dy) & (TCV_RING - 1)) * (TCV_SLOT >> 4));
-          const uint32_t d_acc = taddr + 16 * a;
+          for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
-          for (int tap = 0; tap < 27; ++tap) {
-            const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-            tcv_mma(d_acc, arow[dy] + (uint64_t)((dz * 2 * TCV_KG + dx * 16) >> 4), b_desc0 + (uint64_t)(tap * 32),
-                    tap > 0 ? 1u : 0u);
-          }
-          umma::commit(acc_full + a);
-          umma::commit(slot_empty + (r0 + j) % TCV_RING);  // input row y0 - 1 + j is read for the last time
-        }
-        if (ok) {  // the unit's last two rows
-          umma::commit(slot_empty + (r0 + TCV_YB) % TCV_RING);
-          umma::commit(slot_empty + (r0 + TCV_YB + 1) % TCV_RING);
+            for (int dx = 0; dx < 3; ++dx) {
+              const uint64_t av = arow + (uint64_t)((dz * 2 * TCV_KG + dx * 16) >> 4);
+              const uint64_t bt = b_desc0 + (uint64_t)(((dz * 3 + dx) * TCV_BT) >> 4);
+              tcv_mma(d0, av, bt + boff0, id0);
+              if (first < cnt) tcv_mma(taddr, av, bt + boff1, id1);
+            }
+          umma::commit(slot_empty + s);                                    // the staged row is read
+          if (j >= 2) umma::commit(acc_full + (gbase + j - 2) % TCV_NACC);  // output row j - 2 is complete
         }
       }
       umma::commit(drain_bar);
       bulk::wait(drain_bar, 0, bulk::DRAIN_POLLS);
     }
   } else if (warp >= 4) {
-    // ---------------- epilogue: bias, activation, store ----------------
+    // ---------------- epilogue: bias, activation, store; zero the accumulator ----------------
     const int r = 32 * (warp & 3) + lane;  // TMEM lane = voxel of the 128-row
     const uint32_t trow = taddr + ((uint32_t)(32 * (warp & 3)) << 16);
+    for (int a = 0; a < TCV_NACC; ++a) tcv_zero16(trow + 16 * a);
+    umma::tmem_wait_st();
+    umma::fence_before_sync();
+    __syncwarp();
+    if (lane == 0)
+      for (int a = 0; a < TCV_NACC; ++a) bulk::arrive(acc_empty + a);
     int go = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < nunits && ok; u += gridDim.x) {
       int bb, zz, y0, x0;
       unit_at(u, bb, zz, y0, x0);
       for (int j = 0; j < TCV_YB; ++j, ++go) {
-        const int a = go & 1;
-        int w_ok = 1;
-        if (lane == 0) w_ok = tcv_wait(acc_full + a, (uint32_t)(go >> 1) & 1u, max_polls, abort_w, flag) ? 1 : 0;
-        w_ok = __shfl_sync(0xffffffffu, w_ok, 0);
-        if (!w_ok) {
+        const int a = go % TCV_NACC;
+        if (!tcv_wait_warp(acc_full + a, (uint32_t)(go / TCV_NACC) & 1u, max_polls, abort_w, flag, lane)) {
           ok = false;
           break;
         }
-        if (lane != 0) (void)bulk::try_wait(acc_full + a, (uint32_t)(go >> 1) & 1u);
         umma::fence_after_sync();
         float d[16];
         umma::tmem_ld16(trow + 16 * a, d);
+        tcv_zero16(trow + 16 * a);
+        umma::tmem_wait_st();
         umma::fence_before_sync();
         __syncwarp();
         if (lane == 0) bulk::arrive(acc_empty + a);
@@ -462,7 +487,7 @@ __global__ void __launch_bounds__(TCV_THREADS, 1)
   umma::fence_before_sync();
   __syncthreads();
   umma::fence_after_sync();
-  if (warp == 0) umma::tmem_dealloc(taddr, 32);
+  if (warp == 0) umma::tmem_dealloc(taddr, 128);
 }
 
 // First layer at inference: one input channel (z / mu0), so the 27 taps (padded

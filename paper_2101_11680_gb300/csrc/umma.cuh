@@ -115,6 +115,17 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float (&v)[16]) {
   for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// Warp-wide: lane l writes r[0..7] to 8 consecutive 32-bit columns of TMEM
+// lane (taddr >> 16) + l from column taddr & 0xFFFF (same lane quarter rule as
+// tmem_ld16).  Complete (and visible to later tcgen05 operations of other
+// threads) after tmem_wait_st and a fence_before_sync / barrier hand-off.
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t (&r)[8]) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};\n" ::"r"(taddr), "r"(r[0]),
+               "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7])
+               : "memory");
+}
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;\n" ::: "memory"); }
+
 // Byte offset of element (r, k) in a K-major no-swizzle tile of `rows` rows.
 __host__ __device__ constexpr uint32_t kmajor_off(int rows, int r, int k) {
   return (uint32_t)((((k >> 2) * rows + r) << 4) + ((k & 3) << 2));

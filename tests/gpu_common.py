@@ -24,6 +24,8 @@ CASES = {
     "circ": dict(n=32, nz=4, nt=12, dx=1.0, dz=1.0, z_first=1.0, dt=50.0, mode="circular"),
     # small ADMM case (P = 32)
     "admm16": dict(n=16, nz=6, nt=32, dx=1.0, dz=1.0, z_first=1.0, dt=50.0),
+    # full 128-voxel rows (the learned CNN's M tile), four 32-row bands, few depths and bins
+    "wide128": dict(n=128, nz=4, nt=32, dx=1.0, dz=1.0, z_first=1.0, dt=50.0),
 }
 
 

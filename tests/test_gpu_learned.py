@@ -229,6 +229,44 @@ def test_learned_reconstruct_checked_residuals(batch):
     net.close()
 
 
+def test_learned_full_width_rows_match_oracle():
+    """Scan rows of 128 voxels fill the convolution's 128-row tensor-core tile
+    exactly (x - 1 and x + 128 from the zero padding), 128 rows make four row
+    bands, 4 depths put every plane next to a border: a batch of four (the
+    batched tensor-core contractions and the plane-batched depth FFTs) through the
+    Tikhonov start, two stages and one data-consistency step matches the FP64
+    oracle with BF16 storage points to 2e-3 per member, as at the small sizes."""
+    case = "wide128"
+    kw = CASES[case]
+    k = device_kernel(case)
+    g, _, wh = oracle_kernel(case)
+    s = so.spectral_norm(wh)
+    fwd = lambda v: op.forward_fft(wh / s, v, g)
+    adj = lambda r: op.adjoint_fft(wh / s, r, g)
+    stages = 2
+    theta = synth.learned_init(stages, 31)
+    rng = np.random.default_rng(31)
+    off = 0
+    for ci, co in synth.LEARNED_LAYERS:
+        theta[off:off + co * ci * 27] = ln.bf16(theta[off:off + co * ci * 27])
+        off += co * ci * 27
+        theta[off:off + co] = rng.normal(0.0, 0.05, co)
+        off += co
+    theta[-stages:] = rng.uniform(0.7, 1.3, stages)
+    net = ctof.Learned(stages, theta, x0_lambda_rel=1e-3, dc_steps=1, dc_lambda_rel=1e-4)
+    ms = []
+    for i in range(4):
+        mu = synth.phantom_shapes(kw["n"], kw["nz"], kw["dx"], kw["dz"], kw["z_first"], seed=950 + i, max_shapes=6)
+        ms.append(synth.poisson_noise(np.clip(op.forward_fft(wh, mu, g), 0.0, None), 1e5, seed=960 + i))
+    got = net.reconstruct(k, torch.tensor(np.stack(ms), dtype=torch.float32, device="cuda")).cpu().numpy()
+    tik = lambda r: so.tikhonov(wh / s, r, g, 1e-4)[0]
+    for b, m in enumerate(ms):
+        x0 = so.tikhonov(wh, m, g, 1e-3)[0]
+        want = ln.unrolled(theta, stages, fwd, adj, m / s, rnd=ln.bf16, x0=x0, dc_steps=1, dc_solve=tik)
+        assert rel_l2(got[b], want) <= 2e-3, (b, rel_l2(got[b], want))
+    net.close()
+
+
 def test_trained_network_gains_over_untrained_and_admm():
     """The shipped parameters, on held-out seeded phantoms at the training geometry
     (64 x 64 scan at 0.5 mm, 48 depths, 256 bins of 25 ps, Poisson peak 1e5): the
