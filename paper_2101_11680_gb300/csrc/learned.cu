@@ -226,12 +226,13 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d(const __nv_bfloat16* __re
 // on the tensor cores, M = 128 voxels along x, K = 16 input channels (the
 // input is stored after its ReLU).  A work unit is TCV_YB output rows of one
 // (volume, depth, x segment); warp 0 (one thread) streams the unit's input rows
-// (y0 - 1 .. y0 + TCV_YB, each as its three depth planes, each plane as two
-// 8-channel K groups of 130 voxels x0 - 1 .. x0 + 128) into a ring of TCV_RING
-// slots by tensor-map copies (zero fill outside the volume).  Warp 1 (one
-// thread) issues the MMAs input row by input row: each of the row's nine
-// (depth, x shift) A views (descriptor offsets into the staged row: voxel rows
-// 16 bytes apart, K groups TCV_KG bytes apart) is multiplied by the weights of
+// (y0 - 1 .. y0 + TCV_YB, each as its three depth planes of 130 voxels x0 - 1 ..
+// x0 + 128, one tensor-map box of 32-byte voxel rows per plane in the copy
+// engine's 32-byte swizzle) into a ring of TCV_RING slots (zero fill outside
+// the volume).  Warp 1 (one thread) issues the MMAs input row by input row:
+// each of the row's nine (depth, x shift) A views (the plane's voxel rows as a
+// K-major operand in the same swizzle, the x shift a 32-byte start offset) is
+// multiplied by the weights of
 // its three dy taps stacked along N, so one MMA (N = 48) feeds output rows
 // j - 2, j - 1, j of input row j, held in three consecutive accumulators of a
 // TCV_NACC-slot TMEM ring (split into two MMAs where they wrap around the
@@ -244,12 +245,12 @@ __global__ void __launch_bounds__(CV_THREADS) k_conv3d(const __nv_bfloat16* __re
 constexpr int TCV_RING = 4;
 constexpr int TCV_YB = 32;
 constexpr int TCV_NACC = 6;                     // accumulator ring slots (16 columns each)
-constexpr int TCV_KG = 144 * 16;                // bytes of one K-group region (130 voxel rows, padded)
-constexpr int TCV_SLOT = 3 * 2 * TCV_KG;        // one staged input row: 3 depth planes x 2 K groups
+constexpr int TCV_PL = 17 * 256;                // bytes of one staged plane (130 voxel rows of 32 bytes, padded)
+constexpr int TCV_SLOT = 3 * TCV_PL;            // one staged input row: 3 depth planes
 constexpr int TCV_BT = 48 * 32;                 // bytes of one stacked weight tile (48 rows x 16 ci)
 constexpr int TCV_WB = 9 * TCV_BT;
 constexpr int TCV_THREADS = 256;
-constexpr int TCV_LOAD = 6 * 130 * 16;          // bytes landing per staged row
+constexpr int TCV_LOAD = 3 * 130 * 32;          // bytes landing per staged row
 constexpr size_t TCV_SMEM = 1024 + TCV_RING * TCV_SLOT + TCV_WB + 64 + 256;
 
 __host__ __device__ constexpr uint32_t tcv_idesc(int n) {  // kind::f16: D F32, A / B BF16, M = 128
@@ -378,9 +379,7 @@ __global__ void __launch_bounds__(TCV_THREADS, 1)
           unsigned char* dst = ring + s * TCV_SLOT;
           bulk::arrive_expect(slot_full + s, TCV_LOAD);
           for (int dz = 0; dz < 3; ++dz)
-            for (int g = 0; g < 2; ++g)
-              bulk::tensor_g2s_5d(dst + (dz * 2 + g) * TCV_KG, &amap, 8 * g, x0 - 1, y0 - 1 + j, zz - 1 + dz, bb,
-                                  slot_full + s);
+            bulk::tensor_g2s_5d(dst + dz * TCV_PL, &amap, 0, x0 - 1, y0 - 1 + j, zz - 1 + dz, bb, slot_full + s);
         }
       }
       // no copy may still be landing when the CTA ends: the last load into each slot
@@ -390,7 +389,8 @@ __global__ void __launch_bounds__(TCV_THREADS, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer ----------------
     if (lane == 0) {
-      const uint64_t a_desc0 = umma::desc(bulk::saddr(ring), TCV_KG, 128);  // slot 0, plane 0, x shift 0
+      // slot 0, plane 0, x shift 0: 32-byte voxel rows, 8-row groups 256 bytes apart, 32-byte swizzle
+      const uint64_t a_desc0 = umma::desc(bulk::saddr(ring), 16, 256) | (6ull << 61);
       // tile (0, 0) from output row j - 2; 8-row groups 256 bytes apart, 32-byte swizzle (layout 6)
       const uint64_t b_desc0 = umma::desc(bulk::saddr(s_w), 16, 256) | (6ull << 61);
       int gr = 0, gbase = 0;  // input rows consumed, first output row of the unit
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(TCV_THREADS, 1)
           for (int dz = 0; dz < 3; ++dz)
 #pragma unroll
             for (int dx = 0; dx < 3; ++dx) {
-              const uint64_t av = arow + (uint64_t)((dz * 2 * TCV_KG + dx * 16) >> 4);
+              const uint64_t av = arow + (uint64_t)((dz * TCV_PL + dx * 32) >> 4);
               const uint64_t bt = b_desc0 + (uint64_t)(((dz * 3 + dx) * TCV_BT) >> 4);
               tcv_mma(d0, av, bt + boff0, id0);
               if (first < cnt) tcv_mma(taddr, av, bt + boff1, id1);
@@ -973,8 +973,8 @@ ctof_status conv_tc(const ctof_kernel_s* k, const __nv_bfloat16* in, const __nv_
   const unsigned long long X = G.x, Y = G.y, Z = G.z;
   const unsigned long long dims[5] = {16, X, Y, Z, (unsigned long long)G.b};
   const unsigned long long strides[4] = {32, X * 32, Y * X * 32, Z * Y * X * 32};
-  const unsigned box[5] = {8, 130, 1, 1, 1};
-  if (ctof_encode_map(&amap, 2, 5, in, dims, strides, box, 0) != CTOF_OK) {
+  const unsigned box[5] = {16, 130, 1, 1, 1};
+  if (ctof_encode_map(&amap, 2, 5, in, dims, strides, box, 32) != CTOF_OK) {
     ctof_set_last_error_text("");
     return CTOF_EUNSUPPORTED;
   }
