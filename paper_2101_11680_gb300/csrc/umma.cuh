@@ -2,9 +2,11 @@
 // sm_100a / sm_103a: shared-memory matrix descriptors for the no-swizzle
 // K-major layout, the TF32 instruction descriptor, the MMA issue and its
 // completion through an mbarrier, tensor-memory (TMEM) allocation, and the
-// 32-lane TMEM loads of the epilogue.
+// 32-lane TMEM loads and stores of the epilogues.  (The learned CNN's
+// convolution ORs the 32-byte swizzle mode, 6, into bits 61-63 of a
+// descriptor for its 32-byte operand rows; see learned.cu.)
 //
-// Operand layout used throughout (no swizzle, K-major): a tile of R rows
+// Operand layout used by the contractions (no swizzle, K-major): a tile of R rows
 // (R a multiple of 8) and K FP32 columns (K a multiple of 4) stores element
 // (r, k) at byte ((k / 4) * R + r) * 16 + (k % 4) * 4: for each group of four
 // k, the R rows follow each other as 16-byte rows.  A core matrix (8 rows x
