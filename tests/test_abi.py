@@ -93,6 +93,17 @@ def test_learned_parameter_count_matches_oracle(lib):
     assert lib.ctof_learned_create(3, p.ctypes.data_as(ctypes.c_void_p), ctypes.byref(bad), ctypes.byref(out)) != 0
 
 
+def test_learned_checked_reconstruct_rejects_bad_arguments(lib):
+    """ctof_learned_reconstruct_checked validates its pointers and batch size before any device call."""
+    fake = ctypes.c_void_p(16)  # never dereferenced: the checks fail first
+    assert lib.ctof_learned_reconstruct_checked(None, fake, 1, fake, fake, fake, None) == ctof.EINVAL
+    assert lib.ctof_learned_reconstruct_checked(fake, None, 1, fake, fake, fake, None) == ctof.EINVAL
+    assert lib.ctof_learned_reconstruct_checked(fake, fake, 0, fake, fake, fake, None) == ctof.EINVAL
+    assert lib.ctof_learned_reconstruct_checked(fake, fake, 1, None, fake, fake, None) == ctof.EINVAL
+    assert lib.ctof_learned_reconstruct_checked(fake, fake, 1, fake, None, fake, None) == ctof.EINVAL
+    assert lib.ctof_learned_reconstruct_checked(fake, fake, 1, fake, fake, None, None) == ctof.EINVAL
+
+
 def test_fluorescence_build_rejects_bad_emission(lib):
     """Argument checks of ctof_build_kernel_fluorescence run before any device call."""
     o = ctof.make_optics()
